@@ -1,0 +1,181 @@
+/*
+ * slr.h - C ABI of the GB300 (sm_103a) Schur-complement Low-Rank (SLR)
+ * preconditioner and SLR-preconditioned CG.
+ *
+ * Method: R. Li, Y. Xi, Y. Saad, "Schur complement based domain
+ * decomposition preconditioners with low-rank corrections", arXiv 1505.04340.
+ *
+ *   A x = b, A sparse symmetric positive definite (Section 1, Eq. 1.1).
+ *   A vertex-based partition (Section 2.1) splits the unknowns into interiors
+ *   u_1..u_p and interfaces y; in that order P A P^T = [[B, E], [E^T, C]]
+ *   with B = diag(B_i) (Eqs. 2.2-2.3).  C = L L^T, H = L^{-1} E^T B^{-1} E L^{-T}
+ *   (Eqs. 3.1-3.2), the k largest eigenpairs (U_k, Lambda_k) of H come from
+ *   Lanczos (Section 5.1), and the preconditioner is
+ *     M = [[I, 0], [E^T B^{-1}, I]] [[B, E], [0, S~]]                  (Eq. 4.1)
+ *     S~^{-1} = L^{-T} ( I/(1-theta) + U_k [(I-Lambda_k)^{-1} - I/(1-theta)] U_k^T ) L^{-1}
+ *   (Eq. 4.7 with Lambda~ of Eq. 4.11; theta = lambda_{k+1} or 0 (Eq. 4.10)).
+ *
+ * Conventions used by every entry point:
+ *  - "DD order" is the order of Eq. 2.2: interiors of part 0, ..., part p-1,
+ *    then interfaces of part 0, ..., part p-1; inside each group nodes keep
+ *    ascending original index.  A node is an interface node iff A couples it
+ *    to a node of another part.
+ *  - Multi-column vectors are column-major with leading dimension ld >= rows;
+ *    *_dev pointers are caller-owned device memory (e.g. torch tensors) on
+ *    the device that was current at slr_setup, *_host pointers are host memory.
+ *  - stream is a cudaStream_t (NULL = legacy default stream).  Device work is
+ *    enqueued on it; entry points that return host results synchronise it.
+ *  - Every call returns an slr_status; nothing throws or aborts.  On failure
+ *    slr_last_error_message() describes the cause (thread-local).
+ *  - The handle owns all device memory it allocates (factors, U, workspaces);
+ *    the caller's host arrays are copied and may be freed after the call.
+ */
+#ifndef SLR_H
+#define SLR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct slr_handle_s* slr_handle;
+
+typedef enum {
+    SLR_OK = 0,
+    SLR_ERR_INVALID_ARG = 1,   /* bad size, pointer, CSR structure or option     */
+    SLR_ERR_NOT_SPD = 2,       /* a Cholesky pivot of some B_i or of C was <= 0  */
+    SLR_ERR_OOM = 3,           /* device or host allocation failed               */
+    SLR_ERR_CUDA = 4,          /* a CUDA runtime call or kernel launch failed    */
+    SLR_ERR_NOT_CONVERGED = 5, /* PCG hit maxit; iterations/relres are filled    */
+    SLR_ERR_BREAKDOWN = 6,     /* PCG saw p^T A p <= 0 or rho <= 0               */
+    SLR_ERR_TIMEOUT = 7,       /* a bounded device-side wait expired             */
+    SLR_ERR_UNSUPPORTED = 8    /* a size beyond what the kernels are built for   */
+} slr_status;
+
+enum { SLR_THETA_LAMBDA_K1 = 0, SLR_THETA_ZERO = 1 };   /* Eq. 4.11 / Eq. 4.10      */
+enum { SLR_PREC_FP64 = 0, SLR_PREC_MIXED = 1 };         /* apply in FP64 / in FP32  */
+
+typedef struct {
+    int32_t k;              /* rank of the correction (Section 4); clamped to s           */
+    int32_t lanczos_steps;  /* m Lanczos steps; 0 => 5k (Section 6)                       */
+    int32_t theta_mode;     /* SLR_THETA_LAMBDA_K1 (default) or SLR_THETA_ZERO            */
+    int32_t precision;      /* SLR_PREC_FP64: factors, E, U and apply in FP64.
+                               SLR_PREC_MIXED: apply with FP32 factors/E/U and FP32
+                               arithmetic; PCG, Lanczos and the (1-lambda)^{-1} scaling
+                               stay FP64                                               */
+    int32_t nrhs_max;       /* widest right-hand-side block later calls may pass; 0 => 1 */
+    int32_t flexible_cg;    /* 1: Polak-Ribiere beta in PCG (for the FP32 apply)          */
+    uint64_t seed;          /* SplitMix64 stream of the Lanczos start vector z: v_1 is
+                               L^{-1} C z normalised, z_i = 2 u_i - 1 in DD interface
+                               order, u_i = (x_i >> 11) 2^-53, x_i output i of the stream */
+    int32_t c_leaf;         /* nested-dissection leaf size for C's ordering; 0 => 64     */
+    int32_t verbose;        /* 1: setup prints timings to stderr                          */
+    int32_t reserved[6];
+} slr_opts;
+
+typedef struct {
+    int64_t n, n_interior, s, nparts, k, lanczos_steps;   /* sizes; k after clamping      */
+    int64_t nnz_A, nnz_E, nnz_C;                          /* nnz(E) counts E only, not E^T */
+    int64_t band_entries;        /* stored B-factor entries, sum c_i w_i (w_i + 1)         */
+    int64_t c_diag_entries;      /* stored entries of the inverted supernode diagonal blocks */
+    int64_t c_panel_entries;     /* stored entries of the supernode off-diagonal panels      */
+    int64_t c_supernodes, c_levels;
+    int64_t bytes_per_apply;     /* algorithmic bytes one apply reads/writes per RHS column */
+    int64_t flops_per_apply;     /* multiply-adds x 2 of one apply per RHS column          */
+    int64_t device_bytes;        /* device memory the handle holds                          */
+    double theta;                /* theta used in S~^{-1}                                  */
+    double setup_seconds[5];     /* analysis, B factor, C factor, upload, Lanczos          */
+    int32_t precision, theta_mode;
+} slr_info;
+
+/* Fill *opts with defaults: k = 16, m = 5k, theta = lambda_{k+1}, FP64, 1 RHS, seed 1. */
+void slr_default_opts(slr_opts* opts);
+
+/* Build the SLR preconditioner of A (Sections 2-5).
+ * n, rowptr[n+1], colind[nnz], val[nnz]: host CSR of the FULL symmetric matrix
+ *   (both triangles, sorted or unsorted columns, no duplicates), 0-based, n < 2^31.
+ * nparts, part[n]: host partition, part[i] in [0, nparts) (vertex-based, Section 2.1).
+ * opts: NULL => defaults.  stream: where the setup's device work runs.
+ * *out: new handle on success, NULL on failure.  Errors: INVALID_ARG (sizes,
+ * structure, part out of range), NOT_SPD (a pivot <= 0 in B_i or C), OOM, CUDA. */
+slr_status slr_setup(int32_t n, const int32_t* rowptr, const int32_t* colind, const double* val,
+                     int32_t nparts, const int32_t* part, const slr_opts* opts, void* stream,
+                     slr_handle* out);
+
+/* z = M^{-1} r (Eq. 4.1 with the block LU of Eq. 2.4), both in DD order:
+ *   t = B^{-1} f;  g' = g - E^T t;  y = S~^{-1} g';  u = t - B^{-1} E y;  z = [u; y].
+ * r_dev, z_dev: n x nrhs FP64, leading dimension ld >= n, must not overlap.
+ * 1 <= nrhs <= opts.nrhs_max.  Asynchronous on stream. */
+slr_status slr_apply(slr_handle h, const double* r_dev, double* z_dev, int32_t nrhs, int32_t ld,
+                     void* stream);
+
+/* Solve A x = b with SLR-preconditioned CG (Section 6): x_0 = 0, stop column j
+ * when ||r_j|| <= tol ||b_j|| (recurrence residual) or after maxit iterations.
+ * b_dev, x_dev: n x nrhs FP64 in ORIGINAL order, leading dimension ld.  Columns
+ * are independent CG runs advanced together.  iters_out[nrhs], relres_out[nrhs]:
+ * host arrays (may be NULL).  Synchronises stream.  Returns NOT_CONVERGED if a
+ * column reached maxit, BREAKDOWN if p^T A p <= 0 for a column. */
+slr_status slr_pcg_solve(slr_handle h, const double* b_dev, double* x_dev, int32_t nrhs, int32_t ld,
+                         double tol, int32_t maxit, void* stream, int32_t* iters_out,
+                         double* relres_out);
+
+/* t = B^{-1} f for the interior block (Section 5.2), DD interior order,
+ * f_dev/t_dev: n_interior x nrhs FP64, leading dimension ld.  May alias. */
+slr_status slr_bsolve(slr_handle h, const double* f_dev, double* t_dev, int32_t nrhs, int32_t ld,
+                      void* stream);
+
+/* y = C^{-1} g = L^{-T} L^{-1} g for the interface block (Section 5.2),
+ * DD interface order, s x nrhs FP64, leading dimension ld.  May alias. */
+slr_status slr_csolve(slr_handle h, const double* g_dev, double* y_dev, int32_t nrhs, int32_t ld,
+                      void* stream);
+
+/* y = S~^{-1} g (Eq. 4.7), DD interface order, s x nrhs FP64, leading dim ld. */
+slr_status slr_stilde_solve(slr_handle h, const double* g_dev, double* y_dev, int32_t nrhs,
+                            int32_t ld, void* stream);
+
+/* Replace the low-rank part by caller-given eigenpairs (Section 5.3: an SLR
+ * preconditioner is improved by changing its vectors, not its factors).
+ * Z_host: s x k column-major, DD interface order, C-orthonormal columns
+ * Z_k = L^{-T} U_k of Proposition 4.3 (independent of how C is ordered);
+ * lam_host[k]: lambda_1..lambda_k, each in [0, 1); theta in [0, 1).
+ * 0 <= k <= s.  The handle stores U_k = L^{-1} C Z_k in its own ordering.
+ * Synchronises stream. */
+slr_status slr_set_lowrank(slr_handle h, int32_t k, const double* Z_host, const double* lam_host,
+                           double theta, void* stream);
+
+/* Export the low-rank part: Z_host (s x k column-major, DD interface order,
+ * may be NULL), lam_host[k+1] (Ritz values lambda_1..lambda_{k+1} from Lanczos,
+ * the last 0 when unavailable; may be NULL), *theta_out (may be NULL). */
+slr_status slr_get_lowrank(slr_handle h, double* Z_host, double* lam_host, double* theta_out,
+                           void* stream);
+
+/* All Ritz values of the setup Lanczos run, descending; lam_host has room for
+ * info.lanczos_steps values; *count_out gets how many were produced. */
+slr_status slr_get_ritz(slr_handle h, double* lam_host, int32_t* count_out);
+
+/* perm_host[n]: DD position -> original index (new -> old), Eq. 2.2. */
+slr_status slr_get_perm(slr_handle h, int32_t* perm_host);
+
+slr_status slr_get_info(slr_handle h, slr_info* info);
+
+/* Host-only analysis (no GPU needed): interface detection and the DD order
+ * of Eq. 2.2.  perm_out[n] (new -> old), int_off[nparts+1] and
+ * ifc_off[nparts+1] (offsets of u_i in u and of y_i in y), *s_out = interface
+ * size.  Any output pointer may be NULL. */
+slr_status slr_dd_order(int32_t n, const int32_t* rowptr, const int32_t* colind, int32_t nparts,
+                        const int32_t* part, int32_t* perm_out, int32_t* int_off, int32_t* ifc_off,
+                        int32_t* s_out);
+
+/* Number of CUDA kernels this library has launched in this process so far
+ * (all handles, all devices).  Lets a caller count the launches of a region. */
+int64_t slr_kernel_launches(void);
+
+void slr_destroy(slr_handle h);
+const char* slr_status_str(slr_status s);
+const char* slr_last_error_message(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SLR_H */

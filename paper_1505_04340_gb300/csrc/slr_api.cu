@@ -1,0 +1,686 @@
+// The C ABI of include/slr.h: setup orchestration (host analysis, upload,
+// device Lanczos), the SLR apply, SLR-preconditioned CG and the accessors.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "slr_device.h"
+
+using namespace slr;
+
+namespace {
+
+#define CK(...)                                                                            \
+    do {                                                                                   \
+        cudaError_t e_ = (__VA_ARGS__);                                                    \
+        if (e_ != cudaSuccess) {                                                           \
+            set_error(std::string(#__VA_ARGS__) + ": " + cudaGetErrorString(e_));          \
+            return SLR_ERR_CUDA;                                                           \
+        }                                                                                  \
+    } while (0)
+#define CS(...)                                    \
+    do {                                           \
+        slr_status s_ = (__VA_ARGS__);             \
+        if (s_ != SLR_OK) return s_;               \
+    } while (0)
+
+double now_s() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+    int old = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&old);
+        if (old != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (old >= 0 && cur != old) cudaSetDevice(old);
+    }
+};
+
+template <typename T>
+slr_status dalloc(slr_handle h, T** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) return SLR_OK;
+    cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error("cudaMalloc of " + std::to_string(count * sizeof(T)) + " bytes failed: " + cudaGetErrorString(e));
+        return SLR_ERR_OOM;
+    }
+    h->allocs.push_back((void*)*p);
+    h->device_bytes += (int64_t)(count * sizeof(T));
+    return SLR_OK;
+}
+
+template <typename T>
+void dfree(slr_handle h, T*& p, size_t count) {
+    if (!p) return;
+    auto it = std::find(h->allocs.begin(), h->allocs.end(), (void*)p);
+    if (it != h->allocs.end()) h->allocs.erase(it);
+    cudaFree(p);
+    h->device_bytes -= (int64_t)(count * sizeof(T));
+    p = nullptr;
+}
+
+template <typename TD, typename TS>
+slr_status upload(slr_handle h, TD** p, const std::vector<TS>& v) {
+    CS(dalloc(h, p, v.size()));
+    if (v.empty()) return SLR_OK;
+    if constexpr (std::is_same<TD, TS>::value) {
+        CK(cudaMemcpy(*p, v.data(), v.size() * sizeof(TD), cudaMemcpyHostToDevice));
+    } else {
+        std::vector<TD> tmp(v.begin(), v.end());
+        CK(cudaMemcpy(*p, tmp.data(), tmp.size() * sizeof(TD), cudaMemcpyHostToDevice));
+    }
+    return SLR_OK;
+}
+
+template <typename T>
+slr_status upload_operator(slr_handle h, DevOperator<T>& op, bool with_band) {
+    const HostSetup& hs = h->hs;
+    const int32_t r = std::max(1, h->opts.nrhs_max);
+    CS(upload(h, &op.band, hs.band));
+    if (with_band) CS(upload(h, &op.bfac, hs.bfac));
+    CS(upload(h, &op.e_rp, hs.e_rp));
+    CS(upload(h, &op.e_ci, hs.e_ci));
+    CS(upload(h, &op.e_v, hs.e_v));
+    CS(upload(h, &op.et_rp, hs.et_rp));
+    CS(upload(h, &op.et_ci, hs.et_ci));
+    CS(upload(h, &op.et_v, hs.et_v));
+    const CFactorHost& c = hs.cf;
+    DevCFactor<T>& d = op.cf;
+    d.s = c.s;
+    d.ns = c.ns;
+    d.nlev = c.nlev;
+    d.lev_task_ptr = c.lev_task_ptr;
+    CS(upload(h, &d.cperm, c.cperm));
+    CS(upload(h, &d.c0, c.c0));
+    CS(upload(h, &d.r_off, c.r_off));
+    CS(upload(h, &d.rows, c.rows));
+    CS(upload(h, &d.pan_off, c.pan_off));
+    CS(upload(h, &d.panel, c.panel));
+    CS(upload(h, &d.dinv_off, c.dinv_off));
+    CS(upload(h, &d.dinv, c.dinv));
+    CS(upload(h, &d.seg_ptr, c.seg_ptr));
+    CS(upload(h, &d.seg_val, c.seg_val));
+    CS(upload(h, &d.seg_x, c.seg_x));
+    CS(upload(h, &d.seg_len, c.seg_len));
+    CS(dalloc(h, &d.tasks, c.tasks.size() / 4));
+    if (!c.tasks.empty()) CK(cudaMemcpy(d.tasks, c.tasks.data(), c.tasks.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    const int64_t n = hs.n, nI = hs.nI, s = hs.s;
+    if constexpr (!std::is_same<T, double>::value) {
+        CS(dalloc(h, &op.wr, (size_t)n * r));
+        CS(dalloc(h, &op.wz, (size_t)n * r));
+    }
+    CS(dalloc(h, &op.tB, (size_t)std::max<int64_t>(nI, 1) * r));
+    CS(dalloc(h, &op.eb, (size_t)std::max<int64_t>(nI, 1) * r));
+    CS(dalloc(h, &op.gp, (size_t)std::max<int64_t>(s, 1) * r));
+    CS(dalloc(h, &op.wf, (size_t)std::max<int64_t>(s, 1) * r));
+    CS(dalloc(h, &op.tf, (size_t)std::max<int64_t>(s, 1) * r));
+    CS(dalloc(h, &op.xf, (size_t)std::max<int64_t>(s, 1) * r));
+    return SLR_OK;
+}
+
+// Low-rank data of one operator: U (s x k, factor order), d, 1/(1-theta).
+template <typename T>
+slr_status set_operator_lowrank(slr_handle h, DevOperator<T>& op, const double* U64_dev, int32_t k_old,
+                                int32_t k, const std::vector<double>& lam, double theta) {
+    const int64_t s = h->hs.s;
+    const int32_t r = std::max(1, h->opts.nrhs_max);
+    if (op.U && k_old != k) {
+        dfree(h, op.U, (size_t)s * k_old);
+        dfree(h, op.dvec, (size_t)k_old);
+        dfree(h, op.vk, (size_t)k_old * r);
+        dfree(h, op.part, (size_t)k_old * r * kRedBlocks);
+    }
+    if (!op.U && k > 0) {
+        CS(dalloc(h, &op.U, (size_t)s * k));
+        CS(dalloc(h, &op.dvec, (size_t)k));
+        CS(dalloc(h, &op.vk, (size_t)k * r));
+        CS(dalloc(h, &op.part, (size_t)k * r * kRedBlocks));
+    }
+    if (k > 0) {
+        if constexpr (std::is_same<T, double>::value) {
+            if ((void*)op.U != (void*)U64_dev) CK(cudaMemcpy(op.U, U64_dev, sizeof(double) * s * k, cudaMemcpyDeviceToDevice));
+        } else {
+            CK(launch_convert<double, float>(s, k, U64_dev, s, op.U, s, 0));
+            CK(cudaDeviceSynchronize());
+        }
+        // d_i = (1 - lambda_i)^{-1} - (1 - theta)^{-1}, formed in FP64 (cancellation near 1)
+        std::vector<double> d(k);
+        for (int32_t i = 0; i < k; ++i) d[i] = 1.0 / (1.0 - lam[i]) - 1.0 / (1.0 - theta);
+        std::vector<T> dt(d.begin(), d.end());
+        CK(cudaMemcpy(op.dvec, dt.data(), sizeof(T) * k, cudaMemcpyHostToDevice));
+    }
+    op.cinv = (T)(1.0 / (1.0 - theta));
+    return SLR_OK;
+}
+
+// z = M^{-1} r in precision T; r, z in DD order (Eq. 4.1 with the block LU of Eq. 2.4)
+template <typename T>
+slr_status run_apply(slr_handle h, DevOperator<T>& op, const T* r, int64_t ldr, T* z, int64_t ldz,
+                     int32_t nrhs, cudaStream_t st) {
+    const HostSetup& hs = h->hs;
+    const int32_t nI = hs.nI, s = hs.s;
+    CK(launch_band_solve<T>(op, hs.p, hs.wmax, r, ldr, op.tB, nI, nullptr, 0, nrhs, st));   // t = B^{-1} f
+    CK(launch_gather_et<T>(op, s, r + nI, ldr, op.tB, nI, op.gp, s, nrhs, st));              // g' = g - E^T t
+    CK(launch_c_forward<T>(op.cf, op.gp, s, op.tf, op.wf, nrhs, st));                        // w = L^{-1} g'
+    CK(launch_lowrank<T>(op, s, h->k, op.wf, nrhs, st));                                     // w' (Eq. 4.7)
+    CK(launch_c_backward<T>(op.cf, op.wf, op.xf, z + nI, ldz, nrhs, st));                    // y = L^{-T} w'
+    CK(launch_spmv_e<T>(op, nI, z + nI, ldz, op.eb, nI, nrhs, st));                          // E y
+    CK(launch_band_solve<T>(op, hs.p, hs.wmax, op.eb, nI, z, ldz, op.tB, nI, nrhs, st));    // u = t - B^{-1} E y
+    return SLR_OK;
+}
+
+slr_status apply_any(slr_handle h, const double* r, int64_t ldr, double* z, int64_t ldz, int32_t nrhs,
+                     cudaStream_t st) {
+    if (h->opts.precision == SLR_PREC_FP64) return run_apply<double>(h, h->op64, r, ldr, z, ldz, nrhs, st);
+    DevOperator<float>& op = h->op32;
+    const int64_t n = h->hs.n;
+    CK(launch_convert<double, float>(n, nrhs, r, ldr, op.wr, n, st));
+    CS(run_apply<float>(h, op, op.wr, n, op.wz, n, nrhs, st));
+    CK(launch_convert<float, double>(n, nrhs, op.wz, n, z, ldz, st));
+    return SLR_OK;
+}
+
+// w = H v, H = L^{-1} E^T B^{-1} E L^{-T} (Eq. 3.2), FP64, v and w in factor order (length s)
+slr_status h_apply(slr_handle h, const double* v, double* w, cudaStream_t st) {
+    DevOperator<double>& op = h->op64;
+    const int32_t nI = h->hs.nI, s = h->hs.s;
+    CK(cudaMemcpyAsync(op.tf, v, sizeof(double) * s, cudaMemcpyDeviceToDevice, st));
+    CK(launch_c_backward<double>(op.cf, op.tf, op.xf, op.gp, s, 1, st));   // y = L^{-T} v (DD in gp)
+    CK(launch_spmv_e<double>(op, nI, op.gp, s, op.eb, nI, 1, st));         // E y
+    CK(launch_band_solve<double>(op, h->hs.p, h->hs.wmax, op.eb, nI, op.tB, nI, nullptr, 0, 1, st));
+    CK(launch_gather_et<double>(op, s, nullptr, 0, op.tB, nI, op.gp, s, 1, st));  // E^T B^{-1} E y
+    CK(launch_c_forward<double>(op.cf, op.gp, s, op.tf, w, 1, st));         // L^{-1} (...)
+    return SLR_OK;
+}
+
+double read_scalar(const double* dev, cudaStream_t st, slr_status* err) {
+    double v = 0.0;
+    if (cudaMemcpyAsync(&v, dev, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+        *err = SLR_ERR_CUDA;
+        set_error("device to host copy failed");
+    }
+    return v;
+}
+
+// Section 5.1: m steps of Lanczos with full reorthogonalisation on H, Ritz pairs,
+// U_k = V Y_k, theta.  Start vector v_1 = L^{-1} C z / ||.||, z from SplitMix64.
+slr_status run_lanczos(slr_handle h, cudaStream_t st) {
+    const int32_t s = h->hs.s;
+    int32_t k = std::min(h->opts.k, s);
+    if (k <= 0 || s == 0) {
+        h->k = 0;
+        h->theta = 0.0;
+        h->nritz = 0;
+        return SLR_OK;
+    }
+    const int32_t m = std::min(h->opts.lanczos_steps > 0 ? h->opts.lanczos_steps : 5 * k, s);
+    DevOperator<double>& op = h->op64;
+    double *V = nullptr, *w = nullptr, *hv = nullptr, *part = nullptr, *sc = nullptr, *Yd = nullptr, *Ud = nullptr;
+    CS(dalloc(h, &V, (size_t)s * m));
+    CS(dalloc(h, &w, (size_t)s));
+    CS(dalloc(h, &hv, (size_t)m));
+    CS(dalloc(h, &part, (size_t)m * kRedBlocks));
+    CS(dalloc(h, &sc, 4));
+    std::vector<double> z(s);
+    for (int32_t i = 0; i < s; ++i) z[i] = splitmix_pm1(h->opts.seed, (uint64_t)i);
+    CK(cudaMemcpy(w, z.data(), sizeof(double) * s, cudaMemcpyHostToDevice));
+    CK(launch_csr_spmv(s, h->c_rp, h->c_ci, h->c_v, w, s, op.gp, s, 1, st));     // C z (DD order)
+    CK(launch_c_forward<double>(op.cf, op.gp, s, op.tf, V, 1, st));              // L^{-1} C z
+    slr_status err = SLR_OK;
+    CK(launch_dots(s, 1, V, s, V, s, part, sc, 1, st));
+    double nrm = std::sqrt(read_scalar(sc, st, &err));
+    CS(err);
+    if (!(nrm > 0.0)) { set_error("Lanczos start vector is zero"); return SLR_ERR_BREAKDOWN; }
+    CK(launch_axpby(s, 0.0, V, 1.0 / nrm, V, st));
+    std::vector<double> alpha(m), beta(m);
+    int32_t m_eff = m;
+    double amax = 0.0;
+    for (int32_t j = 0; j < m; ++j) {
+        double* vj = V + (int64_t)j * s;
+        CS(h_apply(h, vj, w, st));
+        if (j > 0) CK(launch_axpby(s, -beta[j - 1], V + (int64_t)(j - 1) * s, 1.0, w, st));
+        CK(launch_dots(s, 1, vj, s, w, s, part, sc, 1, st));
+        alpha[j] = read_scalar(sc, st, &err);
+        CS(err);
+        amax = std::max(amax, std::fabs(alpha[j]));
+        CK(launch_axpby(s, -alpha[j], vj, 1.0, w, st));
+        for (int pass = 0; pass < 2; ++pass) {                       // full reorthogonalisation
+            CK(launch_gemv_t(s, j + 1, V, w, part, hv, st));
+            CK(launch_gemv_n_sub(s, j + 1, V, hv, w, st));
+        }
+        CK(launch_dots(s, 1, w, s, w, s, part, sc, 1, st));
+        beta[j] = std::sqrt(read_scalar(sc, st, &err));
+        CS(err);
+        if (j + 1 == m) break;
+        if (beta[j] <= 1e-12 * amax) { m_eff = j + 1; break; }
+        CK(launch_axpby(s, 1.0 / beta[j], w, 0.0, V + (int64_t)(j + 1) * s, st));
+    }
+    std::vector<double> lam(m_eff), Y((size_t)m_eff * m_eff);
+    host_tridiag_eig(m_eff, alpha.data(), beta.data(), lam.data(), Y.data());
+    k = std::min(k, m_eff);
+    h->ritz = lam;
+    h->nritz = m_eff;
+    h->m_steps = m_eff;
+    h->theta = (h->opts.theta_mode == SLR_THETA_LAMBDA_K1 && m_eff > k) ? lam[k] : 0.0;
+    h->lam.assign(lam.begin(), lam.begin() + k);
+    CS(dalloc(h, &Yd, (size_t)m_eff * k));
+    CK(cudaMemcpy(Yd, Y.data(), sizeof(double) * m_eff * k, cudaMemcpyHostToDevice));
+    CS(dalloc(h, &Ud, (size_t)s * k));
+    CK(launch_gemm_nn(s, m_eff, k, V, Yd, Ud, st));
+    CK(cudaStreamSynchronize(st));
+    CS(set_operator_lowrank<double>(h, op, Ud, 0, k, h->lam, h->theta));
+    h->k = k;
+    dfree(h, Ud, (size_t)s * k);
+    dfree(h, Yd, (size_t)m_eff * k);
+    dfree(h, V, (size_t)s * m);
+    dfree(h, w, (size_t)s);
+    dfree(h, hv, (size_t)m);
+    dfree(h, part, (size_t)m * kRedBlocks);
+    dfree(h, sc, 4);
+    return SLR_OK;
+}
+
+void account(slr_handle h) {
+    const HostSetup& hs = h->hs;
+    const bool fp64 = h->opts.precision == SLR_PREC_FP64;
+    const int64_t wf = fp64 ? 8 : 4, wv = fp64 ? 8 : 4;
+    int64_t band = 0;
+    for (const BandBlock& b : hs.band) band += (int64_t)b.c * b.w * (b.w + 1);
+    const int64_t nnzE = (int64_t)hs.e_v.size();
+    const int64_t cvals = (hs.cf.pan_off.empty() ? 0 : hs.cf.pan_off.back()) +
+                          (hs.cf.dinv_off.empty() ? 0 : hs.cf.dinv_off.back());
+    const int64_t nseg = hs.cf.seg_ptr.empty() ? 0 : hs.cf.seg_ptr.back();
+    const int64_t nrow = (int64_t)hs.cf.rows.size();
+    const int64_t s = hs.s, k = h->k;
+    h->bytes_per_apply = 4 * band * wf + 2 * nnzE * (wf + 4) + 2 * cvals * wf + nseg * 16 + nrow * 4 +
+                         2 * s * k * wf + (2 * (int64_t)hs.n + 2 * (int64_t)hs.nI) * wv;
+    h->flops_per_apply = 2 * (4 * band + 2 * nnzE + 2 * cvals + 2 * s * k);
+}
+
+slr_status setup_impl(slr_handle h, int32_t n, const int32_t* rowptr, const int32_t* colind, const double* val,
+                      int32_t nparts, const int32_t* part, cudaStream_t st) {
+    HostSetup& hs = h->hs;
+    const bool vb = h->opts.verbose != 0;
+    double t0 = now_s();
+    CS(host_validate_csr(n, rowptr, colind, val, nparts, part));
+    CS(host_dd_order(n, rowptr, colind, nparts, part, hs));
+    CS(host_split_blocks(rowptr, colind, val, hs));
+    double t1 = now_s();
+    CS(host_band_factor(hs));
+    double t2 = now_s();
+    CS(host_c_factor(hs, h->opts.c_leaf > 0 ? h->opts.c_leaf : 64, 128));
+    double t3 = now_s();
+    if (vb)
+        fprintf(stderr, "[slr] n=%d nI=%d s=%d p=%d wmax=%d band=%zu cvals=%zu sn=%d lev=%d | analysis %.3fs B %.3fs C %.3fs\n",
+                hs.n, hs.nI, hs.s, hs.p, hs.wmax, hs.bfac.size(), hs.cf.panel.size() + hs.cf.dinv.size(), hs.cf.ns,
+                hs.cf.nlev, t1 - t0, t2 - t1, t3 - t2);
+    // the band kernel keeps two plane vectors per RHS in shared memory
+    if (2ull * hs.wmax * sizeof(double) > 200 * 1024) {
+        set_error("a B_i has plane width " + std::to_string(hs.wmax) + " beyond the kernel's limit");
+        return SLR_ERR_UNSUPPORTED;
+    }
+    CK(cudaGetDevice(&h->device));
+    CS(upload(h, &h->perm, hs.perm));
+    CS(upload(h, &h->a_rp, hs.a_rp));
+    CS(upload(h, &h->a_ci, hs.a_ci));
+    CS(upload(h, &h->a_v, hs.a_v));
+    CS(upload(h, &h->c_rp, hs.c_rp));
+    CS(upload(h, &h->c_ci, hs.c_ci));
+    CS(upload(h, &h->c_v, hs.c_v));
+    CS(upload_operator<double>(h, h->op64, true));
+    const int32_t r = std::max(1, h->opts.nrhs_max);
+    const size_t nr = (size_t)std::max(1, n) * r;
+    CS(dalloc(h, &h->px, nr));
+    CS(dalloc(h, &h->pr, nr));
+    CS(dalloc(h, &h->pz, nr));
+    CS(dalloc(h, &h->pp, nr));
+    CS(dalloc(h, &h->pq, nr));
+    if (h->opts.flexible_cg) CS(dalloc(h, &h->pzold, nr));
+    CS(dalloc(h, &h->scal, (size_t)8 * r));
+    CS(dalloc(h, &h->iflags, (size_t)4 * r + 4));
+    CS(dalloc(h, &h->dpart, (size_t)kRedBlocks * r));
+    CK(cudaDeviceSynchronize());
+    double t4 = now_s();
+    CS(run_lanczos(h, st));
+    CK(cudaStreamSynchronize(st));
+    double t5 = now_s();
+    if (h->opts.precision == SLR_PREC_MIXED) {
+        CS(upload_operator<float>(h, h->op32, true));
+        CS(set_operator_lowrank<float>(h, h->op32, h->op64.U, 0, h->k, h->lam, h->theta));
+        // the FP64 band factor served the FP64 Lanczos only
+        dfree(h, h->op64.bfac, hs.bfac.size());
+    }
+    CK(cudaDeviceSynchronize());
+    double t6 = now_s();
+    h->setup_seconds[0] = t1 - t0;
+    h->setup_seconds[1] = t2 - t1;
+    h->setup_seconds[2] = t3 - t2;
+    h->setup_seconds[3] = (t4 - t3) + (t6 - t5);
+    h->setup_seconds[4] = t5 - t4;
+    account(h);
+    if (vb)
+        fprintf(stderr, "[slr] upload %.3fs lanczos %.3fs (m=%d k=%d theta=%.6g) device %.1f MB\n", t4 - t3 + t6 - t5,
+                t5 - t4, h->m_steps, h->k, h->theta, h->device_bytes / 1e6);
+    // host copies of the big factors are no longer needed
+    std::vector<double>().swap(hs.bfac);
+    std::vector<double>().swap(hs.cf.panel);
+    std::vector<double>().swap(hs.cf.dinv);
+    h->op64.ready = true;
+    h->op32.ready = h->opts.precision == SLR_PREC_MIXED;
+    return SLR_OK;
+}
+
+slr_status check_handle(slr_handle h) {
+    if (!h || !h->op64.ready) { set_error("invalid handle"); return SLR_ERR_INVALID_ARG; }
+    return SLR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+slr_status slr_setup(int32_t n, const int32_t* rowptr, const int32_t* colind, const double* val, int32_t nparts,
+                     const int32_t* part, const slr_opts* opts, void* stream, slr_handle* out) {
+    if (!out) { set_error("out is NULL"); return SLR_ERR_INVALID_ARG; }
+    *out = nullptr;
+    slr_handle h = new (std::nothrow) slr_handle_s();
+    if (!h) { set_error("host allocation failed"); return SLR_ERR_OOM; }
+    if (opts) h->opts = *opts; else slr_default_opts(&h->opts);
+    if (h->opts.k < 0 || h->opts.lanczos_steps < 0 || h->opts.nrhs_max < 0 || h->opts.nrhs_max > 64 ||
+        (h->opts.precision != SLR_PREC_FP64 && h->opts.precision != SLR_PREC_MIXED) ||
+        (h->opts.theta_mode != SLR_THETA_LAMBDA_K1 && h->opts.theta_mode != SLR_THETA_ZERO)) {
+        set_error("invalid options");
+        delete h;
+        return SLR_ERR_INVALID_ARG;
+    }
+    if (h->opts.nrhs_max == 0) h->opts.nrhs_max = 1;
+    slr_status s;
+    try {
+        s = setup_impl(h, n, rowptr, colind, val, nparts, part, (cudaStream_t)stream);
+    } catch (const std::bad_alloc&) {
+        set_error("host allocation failed");
+        s = SLR_ERR_OOM;
+    }
+    if (s != SLR_OK) {
+        slr_destroy(h);
+        return s;
+    }
+    *out = h;
+    return SLR_OK;
+}
+
+slr_status slr_apply(slr_handle h, const double* r, double* z, int32_t nrhs, int32_t ld, void* stream) {
+    CS(check_handle(h));
+    if (nrhs < 1 || nrhs > h->opts.nrhs_max || ld < h->hs.n || !r || !z) {
+        set_error("slr_apply: bad nrhs, ld or pointer");
+        return SLR_ERR_INVALID_ARG;
+    }
+    DeviceGuard g(h->device);
+    return apply_any(h, r, ld, z, ld, nrhs, (cudaStream_t)stream);
+}
+
+slr_status slr_bsolve(slr_handle h, const double* f, double* t, int32_t nrhs, int32_t ld, void* stream) {
+    CS(check_handle(h));
+    const int32_t nI = h->hs.nI;
+    if (nrhs < 1 || nrhs > h->opts.nrhs_max || ld < nI || (!f && nI) || (!t && nI)) {
+        set_error("slr_bsolve: bad arguments");
+        return SLR_ERR_INVALID_ARG;
+    }
+    DeviceGuard g(h->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (h->opts.precision == SLR_PREC_FP64) {
+        CK(launch_band_solve<double>(h->op64, h->hs.p, h->hs.wmax, f, ld, t, ld, nullptr, 0, nrhs, st));
+        return SLR_OK;
+    }
+    DevOperator<float>& op = h->op32;
+    CK(launch_convert<double, float>(nI, nrhs, f, ld, op.wr, nI, st));
+    CK(launch_band_solve<float>(op, h->hs.p, h->hs.wmax, op.wr, nI, op.wz, nI, nullptr, 0, nrhs, st));
+    CK(launch_convert<float, double>(nI, nrhs, op.wz, nI, t, ld, st));
+    return SLR_OK;
+}
+
+static slr_status interface_solve(slr_handle h, const double* g, double* y, int32_t nrhs, int32_t ld, bool lowrank,
+                                  cudaStream_t st) {
+    CS(check_handle(h));
+    const int32_t s = h->hs.s;
+    if (nrhs < 1 || nrhs > h->opts.nrhs_max || ld < s || (s && (!g || !y))) {
+        set_error("interface solve: bad arguments");
+        return SLR_ERR_INVALID_ARG;
+    }
+    if (s == 0) return SLR_OK;
+    DeviceGuard gd(h->device);
+    if (h->opts.precision == SLR_PREC_FP64) {
+        DevOperator<double>& op = h->op64;
+        CK(launch_c_forward<double>(op.cf, g, ld, op.tf, op.wf, nrhs, st));
+        if (lowrank) CK(launch_lowrank<double>(op, s, h->k, op.wf, nrhs, st));
+        CK(launch_c_backward<double>(op.cf, op.wf, op.xf, y, ld, nrhs, st));
+        return SLR_OK;
+    }
+    DevOperator<float>& op = h->op32;
+    CK(launch_convert<double, float>(s, nrhs, g, ld, op.gp, s, st));
+    CK(launch_c_forward<float>(op.cf, op.gp, s, op.tf, op.wf, nrhs, st));
+    if (lowrank) CK(launch_lowrank<float>(op, s, h->k, op.wf, nrhs, st));
+    CK(launch_c_backward<float>(op.cf, op.wf, op.xf, op.gp, s, nrhs, st));
+    CK(launch_convert<float, double>(s, nrhs, op.gp, s, y, ld, st));
+    return SLR_OK;
+}
+
+slr_status slr_csolve(slr_handle h, const double* g, double* y, int32_t nrhs, int32_t ld, void* stream) {
+    return interface_solve(h, g, y, nrhs, ld, false, (cudaStream_t)stream);
+}
+
+slr_status slr_stilde_solve(slr_handle h, const double* g, double* y, int32_t nrhs, int32_t ld, void* stream) {
+    return interface_solve(h, g, y, nrhs, ld, true, (cudaStream_t)stream);
+}
+
+slr_status slr_pcg_solve(slr_handle h, const double* b, double* x, int32_t nrhs, int32_t ld, double tol,
+                         int32_t maxit, void* stream, int32_t* iters_out, double* relres_out) {
+    CS(check_handle(h));
+    const int32_t n = h->hs.n;
+    if (nrhs < 1 || nrhs > h->opts.nrhs_max || ld < n || !b || !x || maxit < 0 || !(tol >= 0.0)) {
+        set_error("slr_pcg_solve: bad arguments");
+        return SLR_ERR_INVALID_ARG;
+    }
+    DeviceGuard g(h->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t nn = n;
+    double *X = h->px, *R = h->pr, *Z = h->pz, *P = h->pp, *Q = h->pq;
+    CK(launch_permute(n, nrhs, h->perm, b, ld, R, nn, true, st));                  // r = P b (DD order)
+    CK(cudaMemsetAsync(X, 0, sizeof(double) * nn * nrhs, st));
+    CK(launch_dots(nn, nrhs, R, nn, R, nn, h->dpart, h->scal + 4, 8, st));        // b.b
+    // flags: active = 1 unless b = 0 (then converged in 0 iterations)
+    {
+        std::vector<double> sc(8 * nrhs);
+        CK(cudaMemcpyAsync(sc.data(), h->scal, sizeof(double) * 8 * nrhs, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        std::vector<int32_t> fl(4 * nrhs + 4, 0);
+        int32_t act = 0;
+        for (int j = 0; j < nrhs; ++j) {
+            bool zero = !(sc[8 * j + 4] > 0.0);
+            fl[4 * j] = zero ? 0 : 1;
+            fl[4 * j + 2] = zero ? 1 : 0;
+            act += !zero;
+        }
+        fl[4 * nrhs] = act;
+        CK(cudaMemcpyAsync(h->iflags, fl.data(), sizeof(int32_t) * fl.size(), cudaMemcpyHostToDevice, st));
+        CK(cudaStreamSynchronize(st));
+    }
+    CS(apply_any(h, R, nn, Z, nn, nrhs, st));                                        // z = M^{-1} r
+    CK(launch_dots(nn, nrhs, R, nn, Z, nn, h->dpart, h->scal + 0, 8, st));         // rho = r.z
+    CK(cudaMemcpyAsync(P, Z, sizeof(double) * nn * nrhs, cudaMemcpyDeviceToDevice, st));
+    int32_t active = 1;
+    for (int32_t it = 1; it <= maxit; ++it) {
+        CK(launch_csr_spmv(n, h->a_rp, h->a_ci, h->a_v, P, nn, Q, nn, nrhs, st));  // q = A p
+        CK(launch_dots(nn, nrhs, P, nn, Q, nn, h->dpart, h->scal + 1, 8, st));     // p.q
+        CK(launch_pcg_alpha(nrhs, h->scal, h->iflags, st));
+        CK(launch_pcg_update_xr(n, nrhs, X, R, P, Q, h->scal, h->iflags, st));
+        CK(launch_dots(nn, nrhs, R, nn, R, nn, h->dpart, h->scal + 3, 8, st));     // r.r
+        CK(launch_pcg_check(nrhs, h->scal, h->iflags, it, tol, st));
+        CK(cudaMemcpyAsync(&active, h->iflags + 4 * nrhs, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (active == 0) break;
+        if (h->opts.flexible_cg)
+            CK(cudaMemcpyAsync(h->pzold, Z, sizeof(double) * nn * nrhs, cudaMemcpyDeviceToDevice, st));
+        CS(apply_any(h, R, nn, Z, nn, nrhs, st));
+        CK(launch_dots(nn, nrhs, R, nn, Z, nn, h->dpart, h->scal + 6, 8, st));     // rho_new
+        if (h->opts.flexible_cg) CK(launch_dots(nn, nrhs, R, nn, h->pzold, nn, h->dpart, h->scal + 7, 8, st));
+        CK(launch_pcg_beta(nrhs, h->scal, h->iflags, h->opts.flexible_cg, st));
+        CK(launch_pcg_update_p(n, nrhs, P, Z, h->scal, h->iflags, st));
+    }
+    CK(launch_permute(n, nrhs, h->perm, X, nn, x, ld, false, st));                 // x = P^T x_dd
+    std::vector<double> sc(8 * nrhs);
+    std::vector<int32_t> fl(4 * nrhs + 4);
+    CK(cudaMemcpyAsync(sc.data(), h->scal, sizeof(double) * 8 * nrhs, cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(fl.data(), h->iflags, sizeof(int32_t) * fl.size(), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    slr_status ret = SLR_OK;
+    for (int j = 0; j < nrhs; ++j) {
+        if (iters_out) iters_out[j] = fl[4 * j + 1];
+        double bb = sc[8 * j + 4];
+        if (relres_out) relres_out[j] = bb > 0 ? std::sqrt(std::max(sc[8 * j + 3], 0.0) / bb) : 0.0;
+        if (fl[4 * j + 2] == 2) ret = SLR_ERR_BREAKDOWN;
+        else if (fl[4 * j + 2] == 0 && ret == SLR_OK) ret = SLR_ERR_NOT_CONVERGED;
+    }
+    if (ret == SLR_ERR_BREAKDOWN) set_error("PCG breakdown: p^T A p <= 0");
+    if (ret == SLR_ERR_NOT_CONVERGED) set_error("PCG reached maxit");
+    return ret;
+}
+
+slr_status slr_set_lowrank(slr_handle h, int32_t k, const double* Z, const double* lam, double theta, void* stream) {
+    CS(check_handle(h));
+    const int32_t s = h->hs.s;
+    if (k < 0 || k > s || (k > 0 && (!Z || !lam)) || !(theta >= 0.0 && theta < 1.0)) {
+        set_error("slr_set_lowrank: bad arguments");
+        return SLR_ERR_INVALID_ARG;
+    }
+    for (int32_t i = 0; i < k; ++i)
+        if (!(lam[i] < 1.0)) { set_error("slr_set_lowrank: lambda must be < 1"); return SLR_ERR_INVALID_ARG; }
+    DeviceGuard g(h->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    double *Zd = nullptr, *CZ = nullptr, *U = nullptr, *T1 = nullptr;
+    if (k > 0) {
+        CS(dalloc(h, &Zd, (size_t)s * k));
+        CS(dalloc(h, &CZ, (size_t)s * k));
+        CS(dalloc(h, &U, (size_t)s * k));
+        CS(dalloc(h, &T1, (size_t)s * k));
+        CK(cudaMemcpy(Zd, Z, sizeof(double) * s * k, cudaMemcpyHostToDevice));
+        CK(launch_csr_spmv(s, h->c_rp, h->c_ci, h->c_v, Zd, s, CZ, s, k, st));       // C Z
+        CK(launch_c_forward<double>(h->op64.cf, CZ, s, T1, U, k, st));              // U = L^{-1} C Z
+        CK(cudaStreamSynchronize(st));
+    }
+    std::vector<double> lv(lam, lam + k);
+    const int32_t k_old = h->k;
+    CS(set_operator_lowrank<double>(h, h->op64, U, k_old, k, lv, theta));
+    if (h->opts.precision == SLR_PREC_MIXED) CS(set_operator_lowrank<float>(h, h->op32, U, k_old, k, lv, theta));
+    h->k = k;
+    h->lam = lv;
+    h->theta = theta;
+    if (k > 0) {
+        dfree(h, Zd, (size_t)s * k);
+        dfree(h, CZ, (size_t)s * k);
+        dfree(h, U, (size_t)s * k);
+        dfree(h, T1, (size_t)s * k);
+    }
+    account(h);
+    return SLR_OK;
+}
+
+slr_status slr_get_lowrank(slr_handle h, double* Z, double* lam, double* theta_out, void* stream) {
+    CS(check_handle(h));
+    DeviceGuard g(h->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int32_t s = h->hs.s, k = h->k;
+    if (Z && k > 0) {
+        double *T1 = nullptr, *X1 = nullptr, *Y1 = nullptr;
+        CS(dalloc(h, &T1, (size_t)s * k));
+        CS(dalloc(h, &X1, (size_t)s * k));
+        CS(dalloc(h, &Y1, (size_t)s * k));
+        CK(cudaMemcpyAsync(T1, h->op64.U, sizeof(double) * s * k, cudaMemcpyDeviceToDevice, st));
+        CK(launch_c_backward<double>(h->op64.cf, T1, X1, Y1, s, k, st));           // Z = L^{-T} U (DD order)
+        CK(cudaMemcpyAsync(Z, Y1, sizeof(double) * s * k, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        dfree(h, T1, (size_t)s * k);
+        dfree(h, X1, (size_t)s * k);
+        dfree(h, Y1, (size_t)s * k);
+    }
+    if (lam) {
+        for (int32_t i = 0; i < k; ++i) lam[i] = h->lam[i];
+        lam[k] = (int32_t)h->ritz.size() > k ? h->ritz[k] : 0.0;
+    }
+    if (theta_out) *theta_out = h->theta;
+    return SLR_OK;
+}
+
+slr_status slr_get_ritz(slr_handle h, double* lam, int32_t* count) {
+    CS(check_handle(h));
+    if (lam) for (size_t i = 0; i < h->ritz.size(); ++i) lam[i] = h->ritz[i];
+    if (count) *count = (int32_t)h->ritz.size();
+    return SLR_OK;
+}
+
+slr_status slr_get_perm(slr_handle h, int32_t* perm) {
+    CS(check_handle(h));
+    if (!perm) { set_error("perm is NULL"); return SLR_ERR_INVALID_ARG; }
+    std::memcpy(perm, h->hs.perm.data(), sizeof(int32_t) * h->hs.n);
+    return SLR_OK;
+}
+
+slr_status slr_get_info(slr_handle h, slr_info* info) {
+    CS(check_handle(h));
+    if (!info) { set_error("info is NULL"); return SLR_ERR_INVALID_ARG; }
+    std::memset(info, 0, sizeof(*info));
+    const HostSetup& hs = h->hs;
+    info->n = hs.n;
+    info->n_interior = hs.nI;
+    info->s = hs.s;
+    info->nparts = hs.p;
+    info->k = h->k;
+    info->lanczos_steps = h->m_steps;
+    info->nnz_A = (int64_t)hs.a_v.size();
+    info->nnz_E = (int64_t)hs.e_v.size();
+    info->nnz_C = (int64_t)hs.c_v.size();
+    int64_t band = 0;
+    for (const BandBlock& b : hs.band) band += (int64_t)b.c * b.w * (b.w + 1);
+    info->band_entries = band;
+    info->c_diag_entries = hs.cf.dinv_off.empty() ? 0 : hs.cf.dinv_off.back();
+    info->c_panel_entries = hs.cf.pan_off.empty() ? 0 : hs.cf.pan_off.back();
+    info->c_supernodes = hs.cf.ns;
+    info->c_levels = hs.cf.nlev;
+    info->bytes_per_apply = h->bytes_per_apply;
+    info->flops_per_apply = h->flops_per_apply;
+    info->device_bytes = h->device_bytes;
+    info->theta = h->theta;
+    for (int i = 0; i < 5; ++i) info->setup_seconds[i] = h->setup_seconds[i];
+    info->precision = h->opts.precision;
+    info->theta_mode = h->opts.theta_mode;
+    return SLR_OK;
+}
+
+void slr_destroy(slr_handle h) {
+    if (!h) return;
+    int old = -1;
+    cudaGetDevice(&old);
+    if (old != h->device) cudaSetDevice(h->device);
+    for (void* p : h->allocs) cudaFree(p);
+    if (old >= 0 && old != h->device) cudaSetDevice(old);
+    delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,140 @@
+// Device-resident SLR handle and the launchers of the hot-path kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "slr_internal.h"
+
+namespace slr {
+
+// Supernodal factor of C on the device, values in precision T.
+template <typename T>
+struct DevCFactor {
+    int32_t s = 0, ns = 0, nlev = 0;
+    int32_t* cperm = nullptr;      // factor position -> DD interface index
+    int32_t* c0 = nullptr;         // [ns+1]
+    int64_t* r_off = nullptr;      // [ns+1]
+    int32_t* rows = nullptr;       // R_J
+    int64_t* pan_off = nullptr;    // [ns+1]
+    T* panel = nullptr;            // row-major |R_J| x n_J
+    int64_t* dinv_off = nullptr;   // [ns+1]
+    T* dinv = nullptr;             // packed lower, column-major
+    int64_t* seg_ptr = nullptr;    // [s+1]
+    int64_t* seg_val = nullptr;
+    int32_t* seg_x = nullptr;
+    int32_t* seg_len = nullptr;
+    int4* tasks = nullptr;         // (supernode, first, count, 0)
+    std::vector<int32_t> lev_task_ptr;   // host copy, [nlev+1]
+};
+
+// Everything one apply needs in precision T (double: FP64 path; float: mixed).
+template <typename T>
+struct DevOperator {
+    BandBlock* band = nullptr;     // [p]
+    T* bfac = nullptr;
+    int32_t *e_rp = nullptr, *e_ci = nullptr;  T* e_v = nullptr;     // E   (nI x s)
+    int32_t *et_rp = nullptr, *et_ci = nullptr; T* et_v = nullptr;   // E^T (s x nI)
+    DevCFactor<T> cf;
+    T* U = nullptr;                // s x k column-major, factor order
+    T* dvec = nullptr;             // [k] (1-lambda_i)^{-1} - (1-theta)^{-1}, from FP64
+    T cinv = 1;                    // (1-theta)^{-1}
+    // workspaces, nrhs_max columns each, leading dimension = rows
+    T *wr = nullptr, *wz = nullptr;          // n: converted input / output (mixed only)
+    T *tB = nullptr, *eb = nullptr;          // nI
+    T *gp = nullptr, *wf = nullptr, *tf = nullptr, *xf = nullptr;   // s
+    T *vk = nullptr, *part = nullptr;        // k x r, partial sums
+    bool ready = false;
+};
+
+}  // namespace slr
+
+struct slr_handle_s {
+    int device = 0;
+    slr_opts opts;
+    slr::HostSetup hs;               // sizes, permutation, CSR blocks (host copies)
+    int32_t k = 0, m_steps = 0, nritz = 0;
+    double theta = 0.0;
+    std::vector<double> ritz;        // all Ritz values, descending
+    std::vector<double> lam;         // lambda_1..lambda_k
+    slr::DevOperator<double> op64;
+    slr::DevOperator<float> op32;
+    // FP64 extras: C in DD interface order (for the start vector and set_lowrank)
+    int32_t *c_rp = nullptr, *c_ci = nullptr; double* c_v = nullptr;
+    // PCG state (DD order, n x nrhs_max) and scalars
+    int32_t *perm = nullptr, *a_rp = nullptr, *a_ci = nullptr; double* a_v = nullptr;
+    double *px = nullptr, *pr = nullptr, *pz = nullptr, *pp = nullptr, *pq = nullptr, *pzold = nullptr;
+    double *scal = nullptr;          // per-column scalars, see slr_api.cu
+    double *dpart = nullptr;         // reduction partials
+    int32_t *iflags = nullptr;       // per-column status words
+    std::vector<void*> allocs;       // every device allocation, freed by slr_destroy
+    int64_t device_bytes = 0;
+    double setup_seconds[5] = {0, 0, 0, 0, 0};
+    int64_t bytes_per_apply = 0, flops_per_apply = 0;
+};
+
+namespace slr {
+
+constexpr int kRedBlocks = 256;     // fixed grid of the deterministic reductions
+
+// ---- K1: batched banded B_i solves (out = B^{-1} in, or out = base - B^{-1} in)
+template <typename T>
+cudaError_t launch_band_solve(const DevOperator<T>& op, int32_t p, int32_t wmax, const T* in, int64_t ldi,
+                              T* out, int64_t ldo, const T* base, int64_t ldb, int32_t nrhs,
+                              cudaStream_t st);
+// ---- K2: gp = g - E^T t (g == NULL: gp = E^T t) ;  eb = E y
+template <typename T>
+cudaError_t launch_gather_et(const DevOperator<T>& op, int32_t s, const T* g, int64_t ldg, const T* t,
+                             int64_t ldt, T* gp, int64_t ldgp, int32_t nrhs, cudaStream_t st);
+template <typename T>
+cudaError_t launch_spmv_e(const DevOperator<T>& op, int32_t nI, const T* y, int64_t ldy, T* out,
+                          int64_t ldo, int32_t nrhs, cudaStream_t st);
+// ---- K3: C solves.  fwd: xf = L^{-1} P g (g in DD order, xf in factor order)
+//              bwd: xf = L^{-T} yf (factor order), optional scatter to DD order y_dd
+template <typename T>
+cudaError_t launch_c_forward(const DevCFactor<T>& cf, const T* g_dd, int64_t ldg, T* tf, T* xf,
+                             int32_t nrhs, cudaStream_t st);
+template <typename T>
+cudaError_t launch_c_backward(const DevCFactor<T>& cf, T* yf_inout, T* xf, T* y_dd, int64_t ldy,
+                              int32_t nrhs, cudaStream_t st);
+// ---- K4: w' = cinv w + U (d o (U^T w)) in factor order (in place on w)
+template <typename T>
+cudaError_t launch_lowrank(const DevOperator<T>& op, int32_t s, int32_t k, T* w, int32_t nrhs,
+                           cudaStream_t st);
+// ---- helpers
+template <typename TS, typename TD>
+cudaError_t launch_convert(int64_t rows, int32_t cols, const TS* src, int64_t lds, TD* dst, int64_t ldd,
+                           cudaStream_t st);
+cudaError_t launch_permute(int32_t n, int32_t nrhs, const int32_t* idx, const double* src, int64_t lds,
+                           double* dst, int64_t ldd, bool gather, cudaStream_t st);
+cudaError_t launch_csr_spmv(int32_t n, const int32_t* rp, const int32_t* ci, const double* v,
+                            const double* x, int64_t ldx, double* y, int64_t ldy, int32_t nrhs,
+                            cudaStream_t st);
+// dots: out[j] = sum_i a[i + j lda] b[i + j ldb], deterministic two-stage reduction
+cudaError_t launch_dots(int64_t n, int32_t cols, const double* a, int64_t lda, const double* b,
+                        int64_t ldb, double* part, double* out, int32_t out_stride, cudaStream_t st);
+// Lanczos helpers: h = V[:, :j]^T w ; w -= V[:, :j] h  (V column-major, ld = s)
+cudaError_t launch_gemv_t(int32_t s, int32_t j, const double* V, const double* w, double* part,
+                          double* h, cudaStream_t st);
+cudaError_t launch_gemv_n_sub(int32_t s, int32_t j, const double* V, const double* h, double* w,
+                              cudaStream_t st);
+cudaError_t launch_axpby(int64_t n, double a, const double* x, double b, double* y, cudaStream_t st);
+// U (s x k) = V (s x m) Y (m x k), column-major
+cudaError_t launch_gemm_nn(int32_t s, int32_t m, int32_t k, const double* V, const double* Y, double* U,
+                           cudaStream_t st);
+
+// ---- PCG (DD order), per-column scalars; see slr_api.cu for the scalar layout
+cudaError_t launch_pcg_alpha(int32_t nrhs, double* scal, int32_t* flags, cudaStream_t st);
+cudaError_t launch_pcg_update_xr(int32_t n, int32_t nrhs, double* x, double* r, const double* p,
+                                 const double* q, const double* scal, const int32_t* flags,
+                                 cudaStream_t st);
+cudaError_t launch_pcg_check(int32_t nrhs, double* scal, int32_t* flags, int32_t it, double tol,
+                             cudaStream_t st);
+cudaError_t launch_pcg_beta(int32_t nrhs, double* scal, int32_t* flags, int32_t flexible,
+                            cudaStream_t st);
+cudaError_t launch_pcg_update_p(int32_t n, int32_t nrhs, double* p, const double* z, const double* scal,
+                                const int32_t* flags, cudaStream_t st);
+
+}  // namespace slr

@@ -1,0 +1,721 @@
+// Host-side setup of the SLR preconditioner: everything that runs once per
+// matrix before the device takes over (Sections 2.1, 3.1 and 5.2 of Li, Xi &
+// Saad, arXiv 1505.04340).
+//
+//  * host_validate_csr  - CSR structure, symmetry and partition checks
+//  * host_dd_order      - interface detection of a vertex-based partition and
+//                         the global ordering [u_1..u_p, y_1..y_p] (Eqs. 2.2-2.3)
+//  * host_split_blocks  - P A P^T, E, E^T and C in CSR
+//  * host_band_factor   - exact banded Cholesky of every B_i (Section 5.2),
+//                         repacked plane by plane with inverted diagonal blocks
+//  * host_c_factor      - exact Cholesky C = L L^T (Eq. 3.1) in a nested
+//                         dissection order, supernodal, with inverted diagonal
+//                         blocks and a level schedule for the device solves
+//  * host_tridiag_eig   - eigenpairs of the Lanczos tridiagonal (Section 5.1)
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#include "slr_internal.h"
+
+namespace slr {
+
+static thread_local std::string g_last_error;
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+double splitmix_pm1(uint64_t seed, uint64_t i) {
+    // SplitMix64 (Steele, Lea & Flood 2014) as a counter-based generator.
+    uint64_t z = seed + (i + 1) * 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    z ^= z >> 31;
+    double u = (double)(z >> 11) * (1.0 / 9007199254740992.0);
+    return 2.0 * u - 1.0;
+}
+
+// ------------------------------------------------------------------ checks
+
+slr_status host_validate_csr(int32_t n, const int32_t* rowptr, const int32_t* colind,
+                             const double* val, int32_t nparts, const int32_t* part) {
+    if (n < 0 || (n > 0 && (!rowptr || !part)) || nparts < 1) {
+        set_error("invalid sizes or NULL pointers");
+        return SLR_ERR_INVALID_ARG;
+    }
+    if (n == 0) return SLR_OK;
+    if (rowptr[0] != 0) { set_error("rowptr[0] != 0"); return SLR_ERR_INVALID_ARG; }
+    for (int32_t i = 0; i < n; ++i)
+        if (rowptr[i + 1] < rowptr[i]) { set_error("rowptr not monotone"); return SLR_ERR_INVALID_ARG; }
+    int64_t nnz = rowptr[n];
+    if (nnz > 0 && (!colind || !val)) { set_error("NULL colind/val"); return SLR_ERR_INVALID_ARG; }
+    for (int32_t i = 0; i < n; ++i)
+        if (part[i] < 0 || part[i] >= nparts) {
+            set_error("part[" + std::to_string(i) + "] out of range");
+            return SLR_ERR_INVALID_ARG;
+        }
+    // per-row sorted copy of the columns to check duplicates and symmetry
+    std::vector<std::pair<int32_t, double>> row;
+    std::vector<int32_t> sc(nnz);
+    std::vector<double> sv(nnz);
+    for (int32_t i = 0; i < n; ++i) {
+        row.clear();
+        for (int32_t q = rowptr[i]; q < rowptr[i + 1]; ++q) {
+            if (colind[q] < 0 || colind[q] >= n) {
+                set_error("column index out of range in row " + std::to_string(i));
+                return SLR_ERR_INVALID_ARG;
+            }
+            row.emplace_back(colind[q], val[q]);
+        }
+        std::sort(row.begin(), row.end(),
+                  [](const std::pair<int32_t, double>& a, const std::pair<int32_t, double>& b) {
+                      return a.first < b.first;
+                  });
+        for (size_t t = 0; t < row.size(); ++t) {
+            if (t && row[t].first == row[t - 1].first) {
+                set_error("duplicate entry in row " + std::to_string(i));
+                return SLR_ERR_INVALID_ARG;
+            }
+            sc[rowptr[i] + t] = row[t].first;
+            sv[rowptr[i] + t] = row[t].second;
+        }
+    }
+    for (int32_t i = 0; i < n; ++i)
+        for (int32_t q = rowptr[i]; q < rowptr[i + 1]; ++q) {
+            int32_t j = sc[q];
+            const int32_t* b = sc.data() + rowptr[j];
+            const int32_t* e = sc.data() + rowptr[j + 1];
+            const int32_t* f = std::lower_bound(b, e, i);
+            if (f == e || *f != i) {
+                set_error("pattern not symmetric at (" + std::to_string(i) + "," + std::to_string(j) + ")");
+                return SLR_ERR_INVALID_ARG;
+            }
+            double a = sv[q], c = sv[f - sc.data()];
+            if (std::fabs(a - c) > 1e-12 * std::max(std::fabs(a), std::fabs(c))) {
+                set_error("values not symmetric at (" + std::to_string(i) + "," + std::to_string(j) + ")");
+                return SLR_ERR_INVALID_ARG;
+            }
+        }
+    return SLR_OK;
+}
+
+// ------------------------------------------------------------------ Section 2.1
+
+slr_status host_dd_order(int32_t n, const int32_t* rowptr, const int32_t* colind, int32_t nparts,
+                         const int32_t* part, HostSetup& hs) {
+    hs.n = n;
+    hs.p = nparts;
+    std::vector<char> iface(n, 0);
+    for (int32_t i = 0; i < n; ++i)
+        for (int32_t q = rowptr[i]; q < rowptr[i + 1]; ++q) {
+            int32_t j = colind[q];
+            if (j != i && part[j] != part[i]) { iface[i] = 1; break; }
+        }
+    // counting sort by (is_interface, part), stable in the original index
+    std::vector<int64_t> cnt(2 * (int64_t)nparts + 1, 0);
+    for (int32_t i = 0; i < n; ++i) cnt[1 + (int64_t)iface[i] * nparts + part[i]]++;
+    for (size_t t = 1; t < cnt.size(); ++t) cnt[t] += cnt[t - 1];
+    hs.int_off.assign(nparts + 1, 0);
+    hs.ifc_off.assign(nparts + 1, 0);
+    for (int32_t q = 0; q <= nparts; ++q) hs.int_off[q] = (int32_t)cnt[q];
+    hs.nI = hs.int_off[nparts];
+    for (int32_t q = 0; q <= nparts; ++q) hs.ifc_off[q] = (int32_t)(cnt[nparts + q] - hs.nI);
+    hs.s = n - hs.nI;
+    hs.perm.assign(n, 0);
+    hs.iperm.assign(n, 0);
+    std::vector<int64_t> pos(cnt.begin(), cnt.end() - 1);
+    for (int32_t i = 0; i < n; ++i) {
+        int64_t key = (int64_t)iface[i] * nparts + part[i];
+        int32_t d = (int32_t)pos[key]++;
+        hs.perm[d] = i;
+        hs.iperm[i] = d;
+    }
+    return SLR_OK;
+}
+
+slr_status host_split_blocks(const int32_t* rowptr, const int32_t* colind, const double* val,
+                             HostSetup& hs) {
+    const int32_t n = hs.n, nI = hs.nI, s = hs.s;
+    hs.a_rp.assign(n + 1, 0);
+    hs.a_ci.resize(rowptr[n]);
+    hs.a_v.resize(rowptr[n]);
+    std::vector<std::pair<int32_t, double>> row;
+    for (int32_t a = 0; a < n; ++a) {
+        int32_t i = hs.perm[a];
+        row.clear();
+        for (int32_t q = rowptr[i]; q < rowptr[i + 1]; ++q) row.emplace_back(hs.iperm[colind[q]], val[q]);
+        std::sort(row.begin(), row.end(),
+                  [](const std::pair<int32_t, double>& x, const std::pair<int32_t, double>& y) {
+                      return x.first < y.first;
+                  });
+        int32_t o = hs.a_rp[a];
+        for (auto& e : row) { hs.a_ci[o] = e.first; hs.a_v[o] = e.second; ++o; }
+        hs.a_rp[a + 1] = o;
+    }
+    auto block = [&](int32_t r0, int32_t r1, int32_t c0, int32_t c1, std::vector<int32_t>& rp,
+                     std::vector<int32_t>& ci, std::vector<double>& v) {
+        rp.assign(r1 - r0 + 1, 0);
+        ci.clear();
+        v.clear();
+        for (int32_t a = r0; a < r1; ++a) {
+            for (int32_t q = hs.a_rp[a]; q < hs.a_rp[a + 1]; ++q) {
+                int32_t c = hs.a_ci[q];
+                if (c >= c0 && c < c1) { ci.push_back(c - c0); v.push_back(hs.a_v[q]); }
+            }
+            rp[a - r0 + 1] = (int32_t)ci.size();
+        }
+    };
+    block(0, nI, nI, n, hs.e_rp, hs.e_ci, hs.e_v);
+    block(nI, n, 0, nI, hs.et_rp, hs.et_ci, hs.et_v);
+    block(nI, n, nI, n, hs.c_rp, hs.c_ci, hs.c_v);
+    (void)s;
+    return SLR_OK;
+}
+
+// ------------------------------------------------------------------ Section 5.2: B_i
+
+// Lower-triangular inverse of the W x W matrix D (row-major), into X (row-major).
+static void tri_inverse(int W, const double* D, double* X) {
+    for (int i = 0; i < W * W; ++i) X[i] = 0.0;
+    for (int c = 0; c < W; ++c) {
+        X[c * W + c] = 1.0 / D[c * W + c];
+        for (int r = c + 1; r < W; ++r) {
+            double s = 0.0;
+            for (int q = c; q < r; ++q) s += D[r * W + q] * X[q * W + c];
+            X[r * W + c] = -s / D[r * W + r];
+        }
+    }
+}
+
+slr_status host_band_factor(HostSetup& hs) {
+    const int32_t p = hs.p;
+    hs.band.assign(p, BandBlock());
+    std::vector<int32_t> bw(p, 0);
+    int64_t off = 0;
+    hs.wmax = 0;
+    for (int32_t i = 0; i < p; ++i) {
+        int32_t r0 = hs.int_off[i], m = hs.int_off[i + 1] - r0, w = 0;
+        for (int32_t a = r0; a < r0 + m; ++a)
+            for (int32_t q = hs.a_rp[a]; q < hs.a_rp[a + 1]; ++q) {
+                int32_t c = hs.a_ci[q];
+                if (c >= r0 && c < r0 + m) w = std::max(w, std::abs(a - c));
+            }
+        bw[i] = w;
+        BandBlock& b = hs.band[i];
+        b.m = m;
+        b.row0 = r0;
+        b.w = m ? std::max(w, 1) : 0;
+        b.c = m ? (m + b.w - 1) / b.w : 0;
+        b.foff = off;
+        off += (int64_t)b.c * b.w * (b.w + 1);
+        hs.wmax = std::max(hs.wmax, b.w);
+    }
+    hs.bfac.assign(off, 0.0);
+    int bad = -1;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int32_t i = 0; i < p; ++i) {
+        const BandBlock& b = hs.band[i];
+        const int32_t m = b.m, w = bw[i], W = b.w, r0 = b.row0;
+        if (m == 0) continue;
+        const int32_t lw = w + 1;
+        std::vector<double> Lb((size_t)m * lw, 0.0);  // Lb[l*lw + (k - l + w)] = L[l][k]
+        for (int32_t l = 0; l < m; ++l)
+            for (int32_t q = hs.a_rp[r0 + l]; q < hs.a_rp[r0 + l + 1]; ++q) {
+                int32_t k = hs.a_ci[q] - r0;
+                if (k >= 0 && k <= l) Lb[(size_t)l * lw + (k - l + w)] = hs.a_v[q];
+            }
+        bool ok = true;
+        for (int32_t l = 0; l < m && ok; ++l) {
+            double* Ll = &Lb[(size_t)l * lw + (w - l)];   // Ll[k] = L[l][k]
+            int32_t jlo = std::max(0, l - w);
+            for (int32_t j = jlo; j <= l; ++j) {
+                const double* Lj = &Lb[(size_t)j * lw + (w - j)];
+                int32_t klo = std::max(jlo, j - w);
+                double s = Ll[j];
+                for (int32_t k = klo; k < j; ++k) s -= Ll[k] * Lj[k];
+                if (j < l) {
+                    Ll[j] = s / Lj[j];
+                } else {
+                    if (!(s > 0.0)) { ok = false; break; }
+                    Ll[l] = std::sqrt(s);
+                }
+            }
+        }
+        if (!ok) {
+#pragma omp critical
+            bad = i;
+            continue;
+        }
+        auto Lat = [&](int32_t l, int32_t k) -> double {   // L[l][k] inside the band, else 0
+            if (l < 0 || l >= m || k < 0 || k > l || l - k > w) return 0.0;
+            return Lb[(size_t)l * lw + (k - l + w)];
+        };
+        std::vector<double> D((size_t)W * W), X((size_t)W * W);
+        for (int32_t J = 0; J < b.c; ++J) {
+            double* P = &hs.bfac[b.foff + (int64_t)J * W * (W + 1)];
+            for (int32_t r = 0; r < W; ++r)
+                for (int32_t c = 0; c < W; ++c) {
+                    int32_t l = J * W + r;
+                    D[(size_t)r * W + c] = (l >= m) ? (r == c ? 1.0 : 0.0) : (c <= r ? Lat(l, J * W + c) : 0.0);
+                }
+            tri_inverse(W, D.data(), X.data());
+            for (int32_t r = 0; r < W; ++r) {
+                int32_t l = J * W + r;
+                for (int32_t q = 0; q <= W; ++q) {
+                    double v;
+                    if (q <= r && q < W) v = X[(size_t)r * W + q];
+                    else v = (J > 0 && l < m) ? Lat(l, (J - 1) * W + (q - 1)) : 0.0;
+                    P[(size_t)q * W + r] = v;
+                }
+            }
+        }
+    }
+    if (bad >= 0) {
+        set_error("B_" + std::to_string(bad) + " is not positive definite (Cholesky pivot <= 0)");
+        return SLR_ERR_NOT_SPD;
+    }
+    return SLR_OK;
+}
+
+// ------------------------------------------------------------------ Section 3.1: C = L L^T
+
+namespace {
+
+// Nested dissection by breadth-first level structures: a subset is split at the
+// middle level of a BFS from a pseudo-peripheral node; both halves are ordered
+// first (recursively), the separator last.  Subsets of at most `leaf` nodes,
+// and subsets without three levels, become one supernode each.
+struct NestedDissection {
+    const std::vector<int32_t>& rp;
+    const std::vector<int32_t>& ci;
+    int32_t leaf;
+    std::vector<int32_t> stamp, lev;
+    int32_t cur = 0;
+    std::vector<int32_t> out_nodes, out_ptr;
+
+    NestedDissection(const std::vector<int32_t>& r, const std::vector<int32_t>& c, int32_t s, int32_t lf)
+        : rp(r), ci(c), leaf(lf), stamp(s, 0), lev(s, -1) { out_ptr.push_back(0); }
+
+    void emit(const std::vector<int32_t>& nodes) {
+        if (nodes.empty()) return;
+        out_nodes.insert(out_nodes.end(), nodes.begin(), nodes.end());
+        out_ptr.push_back((int32_t)out_nodes.size());
+    }
+    int32_t degree(int32_t v) const {
+        int32_t d = 0;
+        for (int32_t q = rp[v]; q < rp[v + 1]; ++q) d += (stamp[ci[q]] == cur);
+        return d;
+    }
+    // BFS inside the current subset; `order` gets the visit order, lptr level starts.
+    void bfs(int32_t root, std::vector<int32_t>& order, std::vector<int32_t>& lptr, int32_t tag) {
+        order.clear();
+        lptr.clear();
+        order.push_back(root);
+        lev[root] = tag;
+        lptr.push_back(0);
+        size_t head = 0;
+        while (head < order.size()) {
+            size_t end = order.size();
+            lptr.push_back((int32_t)end);
+            for (; head < end; ++head) {
+                int32_t v = order[head];
+                for (int32_t q = rp[v]; q < rp[v + 1]; ++q) {
+                    int32_t u = ci[q];
+                    if (stamp[u] == cur && lev[u] != tag) { lev[u] = tag; order.push_back(u); }
+                }
+            }
+        }
+        if (lptr.back() != (int32_t)order.size()) lptr.push_back((int32_t)order.size());
+        // remove a trailing empty level marker
+        while (lptr.size() >= 2 && lptr[lptr.size() - 1] == lptr[lptr.size() - 2]) lptr.pop_back();
+    }
+    int32_t tag_counter = 0;
+
+    void run(std::vector<int32_t> nodes) {
+        if ((int32_t)nodes.size() <= leaf) { emit(nodes); return; }
+        ++cur;
+        for (int32_t v : nodes) stamp[v] = cur;
+        std::vector<int32_t> order, lptr;
+        int32_t tag = ++tag_counter;
+        bfs(nodes[0], order, lptr, tag);
+        if (order.size() < nodes.size()) {   // several components: order each on its own
+            std::vector<std::vector<int32_t>> comps;
+            comps.push_back(order);
+            for (int32_t v : nodes)
+                if (lev[v] != tag) {
+                    std::vector<int32_t> o2, l2;
+                    bfs(v, o2, l2, tag);
+                    comps.push_back(o2);
+                }
+            for (auto& c : comps) run(c);
+            return;
+        }
+        // pseudo-peripheral root (George & Liu): move to a minimum-degree node of
+        // the last level while the eccentricity grows
+        int32_t nlev = (int32_t)lptr.size() - 1;
+        for (int it = 0; it < 6; ++it) {
+            int32_t best = -1, bd = 1 << 30;
+            for (int32_t t = lptr[nlev - 1]; t < lptr[nlev]; ++t) {
+                int32_t d = degree(order[t]);
+                if (d < bd) { bd = d; best = order[t]; }
+            }
+            std::vector<int32_t> o2, l2;
+            int32_t tg = ++tag_counter;
+            bfs(best, o2, l2, tg);
+            int32_t nl2 = (int32_t)l2.size() - 1;
+            if (nl2 > nlev) { order.swap(o2); lptr.swap(l2); nlev = nl2; }
+            else break;
+        }
+        if (nlev < 3) { emit(nodes); return; }
+        int32_t half = (int32_t)nodes.size() / 2, mid = 1;
+        for (int32_t l = 0; l < nlev; ++l)
+            if (lptr[l + 1] > half) { mid = l; break; }
+        mid = std::min(std::max(mid, 1), nlev - 2);
+        std::vector<int32_t> A(order.begin(), order.begin() + lptr[mid]);
+        std::vector<int32_t> S(order.begin() + lptr[mid], order.begin() + lptr[mid + 1]);
+        std::vector<int32_t> B(order.begin() + lptr[mid + 1], order.end());
+        run(std::move(A));
+        run(std::move(B));
+        emit(S);
+    }
+};
+
+}  // namespace
+
+slr_status host_c_factor(HostSetup& hs, int32_t leaf, int32_t task_rows) {
+    CFactorHost& cf = hs.cf;
+    const int32_t s = hs.s;
+    cf = CFactorHost();
+    cf.s = s;
+    if (s == 0) {
+        cf.c0.assign(1, 0);
+        cf.r_off.assign(1, 0);
+        cf.pan_off.assign(1, 0);
+        cf.dinv_off.assign(1, 0);
+        cf.seg_ptr.assign(1, 0);
+        cf.lev_task_ptr.assign(1, 0);
+        return SLR_OK;
+    }
+    // graph of C without its diagonal
+    std::vector<int32_t> grp(s + 1, 0), gci;
+    for (int32_t a = 0; a < s; ++a) {
+        for (int32_t q = hs.c_rp[a]; q < hs.c_rp[a + 1]; ++q)
+            if (hs.c_ci[q] != a) gci.push_back(hs.c_ci[q]);
+        grp[a + 1] = (int32_t)gci.size();
+    }
+    NestedDissection nd(grp, gci, s, std::max(leaf, 1));
+    {
+        std::vector<int32_t> all(s);
+        std::iota(all.begin(), all.end(), 0);
+        nd.run(std::move(all));
+    }
+    cf.cperm = nd.out_nodes;
+    cf.c0 = nd.out_ptr;
+    cf.ns = (int32_t)cf.c0.size() - 1;
+    const int32_t ns = cf.ns;
+    std::vector<int32_t> ipos(s), snof(s);
+    for (int32_t t = 0; t < s; ++t) ipos[cf.cperm[t]] = t;
+    for (int32_t J = 0; J < ns; ++J)
+        for (int32_t t = cf.c0[J]; t < cf.c0[J + 1]; ++t) snof[t] = J;
+
+    // symbolic: R_J = rows of C below J's columns plus the children's R_K
+    cf.parent.assign(ns, -1);
+    cf.level.assign(ns, 0);
+    cf.r_off.assign(ns + 1, 0);
+    std::vector<std::vector<int32_t>> children(ns);
+    std::vector<int32_t> mark(s, -1), R;
+    for (int32_t J = 0; J < ns; ++J) {
+        const int32_t a0 = cf.c0[J], a1 = cf.c0[J + 1];
+        R.clear();
+        for (int32_t t = a0; t < a1; ++t) {
+            int32_t v = cf.cperm[t];
+            for (int32_t q = grp[v]; q < grp[v + 1]; ++q) {
+                int32_t r = ipos[gci[q]];
+                if (r >= a1 && mark[r] != J) { mark[r] = J; R.push_back(r); }
+            }
+        }
+        int32_t lv = 0;
+        for (int32_t K : children[J]) {
+            lv = std::max(lv, cf.level[K] + 1);
+            for (int64_t t = cf.r_off[K]; t < cf.r_off[K + 1]; ++t) {
+                int32_t r = cf.rows[t];
+                if (r >= a1 && mark[r] != J) { mark[r] = J; R.push_back(r); }
+            }
+        }
+        std::sort(R.begin(), R.end());
+        cf.level[J] = lv;
+        cf.rows.insert(cf.rows.end(), R.begin(), R.end());
+        cf.r_off[J + 1] = (int64_t)cf.rows.size();
+        if (!R.empty()) {
+            cf.parent[J] = snof[R[0]];
+            children[cf.parent[J]].push_back(J);
+        }
+    }
+    // numeric: right-looking supernodal Cholesky on dense panels
+    // F_J: (n_J + |R_J|) x n_J row-major; the first n_J rows are the diagonal block
+    std::vector<int64_t> fo(ns + 1, 0);
+    for (int32_t J = 0; J < ns; ++J) {
+        int64_t nJ = cf.c0[J + 1] - cf.c0[J], nr = cf.r_off[J + 1] - cf.r_off[J];
+        fo[J + 1] = fo[J] + (nJ + nr) * nJ;
+    }
+    std::vector<double> F(fo[ns], 0.0);
+    auto rowpos = [&](int32_t T, int32_t r) -> int64_t {   // row of position r inside F_T
+        if (r < cf.c0[T + 1]) return r - cf.c0[T];
+        const int32_t* b = cf.rows.data() + cf.r_off[T];
+        const int32_t* e = cf.rows.data() + cf.r_off[T + 1];
+        const int32_t* f = std::lower_bound(b, e, r);
+        return (cf.c0[T + 1] - cf.c0[T]) + (f - b);
+    };
+    for (int32_t J = 0; J < ns; ++J) {
+        const int32_t a0 = cf.c0[J], nJ = cf.c0[J + 1] - a0;
+        for (int32_t t = a0; t < a0 + nJ; ++t) {
+            int32_t v = cf.cperm[t];
+            for (int32_t q = hs.c_rp[v]; q < hs.c_rp[v + 1]; ++q) {
+                int32_t r = ipos[hs.c_ci[q]];
+                if (r < t) continue;
+                F[fo[J] + rowpos(J, r) * nJ + (t - a0)] += hs.c_v[q];
+            }
+        }
+    }
+    int bad = -1;
+    for (int32_t J = 0; J < ns && bad < 0; ++J) {
+        const int32_t a0 = cf.c0[J], nJ = cf.c0[J + 1] - a0;
+        const int64_t nr = cf.r_off[J + 1] - cf.r_off[J];
+        double* Fj = F.data() + fo[J];
+        for (int32_t i = 0; i < nJ && bad < 0; ++i) {
+            double* Fi = Fj + (int64_t)i * nJ;
+            for (int32_t j = 0; j <= i; ++j) {
+                const double* Fr = Fj + (int64_t)j * nJ;
+                double sum = Fi[j];
+                for (int32_t k = 0; k < j; ++k) sum -= Fi[k] * Fr[k];
+                if (j < i) Fi[j] = sum / Fr[j];
+                else if (sum > 0.0) Fi[i] = std::sqrt(sum);
+                else { bad = J; break; }
+            }
+        }
+        if (bad >= 0) break;
+#pragma omp parallel for schedule(static) if (nr * nJ > 4096)
+        for (int64_t pr = 0; pr < nr; ++pr) {
+            double* Fp = Fj + (nJ + pr) * nJ;
+            for (int32_t j = 0; j < nJ; ++j) {
+                const double* Fr = Fj + (int64_t)j * nJ;
+                double sum = Fp[j];
+                for (int32_t k = 0; k < j; ++k) sum -= Fp[k] * Fr[k];
+                Fp[j] = sum / Fr[j];
+            }
+        }
+        // update the ancestors: F_T[R_J[a], R_J[b]] -= L[R_J[a], J] . L[R_J[b], J]
+        const int32_t* RJ = cf.rows.data() + cf.r_off[J];
+        int64_t b0 = 0;
+        while (b0 < nr) {
+            const int32_t T = snof[RJ[b0]];
+            int64_t b1 = b0;
+            while (b1 < nr && RJ[b1] < cf.c0[T + 1]) ++b1;
+            const int32_t nT = cf.c0[T + 1] - cf.c0[T];
+            double* FT = F.data() + fo[T];
+#pragma omp parallel for schedule(dynamic, 16) if ((nr - b0) * (b1 - b0) * nJ > 100000)
+            for (int64_t a = b0; a < nr; ++a) {
+                const double* La = Fj + (nJ + a) * nJ;
+                const int64_t tr = rowpos(T, RJ[a]);
+                const int64_t bend = std::min(a + 1, b1);
+                for (int64_t b = b0; b < bend; ++b) {
+                    const double* Lbr = Fj + (nJ + b) * nJ;
+                    double dot = 0.0;
+                    for (int32_t k = 0; k < nJ; ++k) dot += La[k] * Lbr[k];
+                    FT[tr * nT + (RJ[b] - cf.c0[T])] -= dot;
+                }
+            }
+            b0 = b1;
+        }
+    }
+    if (bad >= 0) {
+        set_error("C is not positive definite (Cholesky pivot <= 0 in supernode " + std::to_string(bad) + ")");
+        return SLR_ERR_NOT_SPD;
+    }
+    // inverted diagonal blocks (packed lower, column-major) and row-major panels
+    cf.dinv_off.assign(ns + 1, 0);
+    cf.pan_off.assign(ns + 1, 0);
+    for (int32_t J = 0; J < ns; ++J) {
+        int64_t nJ = cf.c0[J + 1] - cf.c0[J], nr = cf.r_off[J + 1] - cf.r_off[J];
+        cf.dinv_off[J + 1] = cf.dinv_off[J] + nJ * (nJ + 1) / 2;
+        cf.pan_off[J + 1] = cf.pan_off[J] + nr * nJ;
+    }
+    cf.dinv.assign(cf.dinv_off[ns], 0.0);
+    cf.panel.assign(cf.pan_off[ns], 0.0);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int32_t J = 0; J < ns; ++J) {
+        const int32_t nJ = cf.c0[J + 1] - cf.c0[J];
+        const int64_t nr = cf.r_off[J + 1] - cf.r_off[J];
+        const double* Fj = F.data() + fo[J];
+        std::vector<double> X((size_t)nJ * nJ);
+        tri_inverse(nJ, Fj, X.data());   // Fj's upper part is zero: it is never written
+        double* Dv = cf.dinv.data() + cf.dinv_off[J];
+        for (int32_t j = 0; j < nJ; ++j) {
+            int64_t cs = (int64_t)j * nJ - (int64_t)j * (j - 1) / 2;
+            for (int32_t i = j; i < nJ; ++i) Dv[cs + (i - j)] = X[(size_t)i * nJ + j];
+        }
+        std::memcpy(cf.panel.data() + cf.pan_off[J], Fj + (int64_t)nJ * nJ, sizeof(double) * nr * nJ);
+    }
+    // forward-gather segments: row i of L left of its diagonal block is the union
+    // of rows R_K[p] = i of the descendants' panels, each n_K contiguous values
+    cf.seg_ptr.assign(s + 1, 0);
+    for (int32_t J = 0; J < ns; ++J)
+        for (int64_t t = cf.r_off[J]; t < cf.r_off[J + 1]; ++t) cf.seg_ptr[cf.rows[t] + 1]++;
+    for (int32_t i = 0; i < s; ++i) cf.seg_ptr[i + 1] += cf.seg_ptr[i];
+    const int64_t nseg = cf.seg_ptr[s];
+    cf.seg_val.assign(nseg, 0);
+    cf.seg_x.assign(nseg, 0);
+    cf.seg_len.assign(nseg, 0);
+    {
+        std::vector<int64_t> fill(cf.seg_ptr.begin(), cf.seg_ptr.end() - 1);
+        for (int32_t J = 0; J < ns; ++J) {
+            const int32_t nJ = cf.c0[J + 1] - cf.c0[J];
+            for (int64_t t = cf.r_off[J]; t < cf.r_off[J + 1]; ++t) {
+                int64_t d = fill[cf.rows[t]]++;
+                cf.seg_val[d] = cf.pan_off[J] + (t - cf.r_off[J]) * nJ;
+                cf.seg_x[d] = cf.c0[J];
+                cf.seg_len[d] = nJ;
+            }
+        }
+    }
+    // level schedule: tasks of at most task_rows rows of one supernode
+    cf.nlev = 0;
+    for (int32_t J = 0; J < ns; ++J) cf.nlev = std::max(cf.nlev, cf.level[J] + 1);
+    std::vector<std::vector<int32_t>> bylev(cf.nlev);
+    for (int32_t J = 0; J < ns; ++J) bylev[cf.level[J]].push_back(J);
+    cf.lev_task_ptr.assign(cf.nlev + 1, 0);
+    cf.tasks.clear();
+    for (int32_t l = 0; l < cf.nlev; ++l) {
+        for (int32_t J : bylev[l]) {
+            int32_t nJ = cf.c0[J + 1] - cf.c0[J];
+            for (int32_t f = 0; f < nJ; f += task_rows) {
+                cf.tasks.push_back(J);
+                cf.tasks.push_back(f);
+                cf.tasks.push_back(std::min(task_rows, nJ - f));
+                cf.tasks.push_back(0);
+            }
+        }
+        cf.lev_task_ptr[l + 1] = (int32_t)(cf.tasks.size() / 4);
+    }
+    return SLR_OK;
+}
+
+// ------------------------------------------------------------------ Section 5.1: T = Y diag(lam) Y^T
+
+void host_tridiag_eig(int32_t m, const double* alpha, const double* beta, double* lam, double* Y) {
+    // cyclic Jacobi on the dense symmetric T; A row-major, V accumulates rotations
+    std::vector<double> A((size_t)m * m, 0.0), V((size_t)m * m, 0.0);
+    for (int32_t i = 0; i < m; ++i) {
+        A[(size_t)i * m + i] = alpha[i];
+        V[(size_t)i * m + i] = 1.0;
+        if (i + 1 < m) A[(size_t)i * m + i + 1] = A[(size_t)(i + 1) * m + i] = beta[i];
+    }
+    double scale = 0.0;
+    for (int32_t i = 0; i < m * m; ++i) scale += A[i] * A[i];
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0;
+        for (int32_t i = 0; i < m; ++i)
+            for (int32_t j = i + 1; j < m; ++j) off += A[(size_t)i * m + j] * A[(size_t)i * m + j];
+        if (off <= 1e-32 * scale) break;
+        for (int32_t p = 0; p < m; ++p)
+            for (int32_t q = p + 1; q < m; ++q) {
+                double apq = A[(size_t)p * m + q];
+                if (std::fabs(apq) < 1e-300) continue;
+                double app = A[(size_t)p * m + p], aqq = A[(size_t)q * m + q];
+                // rotation angle phi with tan(2 phi) = 2 a_pq / (a_qq - a_pp); t = tan(phi)
+                double tau = (aqq - app) / (2.0 * apq);
+                double t = (tau >= 0 ? 1.0 : -1.0) / (std::fabs(tau) + std::sqrt(1.0 + tau * tau));
+                double c = 1.0 / std::sqrt(1.0 + t * t), sn = t * c;
+                for (int32_t k = 0; k < m; ++k) {   // A <- A G (columns p, q)
+                    double akp = A[(size_t)k * m + p], akq = A[(size_t)k * m + q];
+                    A[(size_t)k * m + p] = c * akp - sn * akq;
+                    A[(size_t)k * m + q] = sn * akp + c * akq;
+                }
+                for (int32_t k = 0; k < m; ++k) {   // A <- G^T A (rows p, q)
+                    double apk = A[(size_t)p * m + k], aqk = A[(size_t)q * m + k];
+                    A[(size_t)p * m + k] = c * apk - sn * aqk;
+                    A[(size_t)q * m + k] = sn * apk + c * aqk;
+                }
+                for (int32_t k = 0; k < m; ++k) {   // V <- V G
+                    double vkp = V[(size_t)k * m + p], vkq = V[(size_t)k * m + q];
+                    V[(size_t)k * m + p] = c * vkp - sn * vkq;
+                    V[(size_t)k * m + q] = sn * vkp + c * vkq;
+                }
+            }
+    }
+    std::vector<int32_t> idx(m);
+    std::iota(idx.begin(), idx.end(), 0);
+    std::stable_sort(idx.begin(), idx.end(), [&](int32_t a, int32_t b) {
+        return A[(size_t)a * m + a] > A[(size_t)b * m + b];
+    });
+    for (int32_t j = 0; j < m; ++j) {
+        lam[j] = A[(size_t)idx[j] * m + idx[j]];
+        for (int32_t i = 0; i < m; ++i) Y[(size_t)j * m + i] = V[(size_t)i * m + idx[j]];
+    }
+}
+
+}  // namespace slr
+
+// ------------------------------------------------------------------ host-only ABI entries
+
+extern "C" {
+
+void slr_default_opts(slr_opts* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->k = 16;
+    o->lanczos_steps = 0;
+    o->theta_mode = SLR_THETA_LAMBDA_K1;
+    o->precision = SLR_PREC_FP64;
+    o->nrhs_max = 1;
+    o->flexible_cg = 0;
+    o->seed = 1;
+    o->c_leaf = 64;
+}
+
+const char* slr_status_str(slr_status s) {
+    switch (s) {
+        case SLR_OK: return "SLR_OK";
+        case SLR_ERR_INVALID_ARG: return "SLR_ERR_INVALID_ARG";
+        case SLR_ERR_NOT_SPD: return "SLR_ERR_NOT_SPD";
+        case SLR_ERR_OOM: return "SLR_ERR_OOM";
+        case SLR_ERR_CUDA: return "SLR_ERR_CUDA";
+        case SLR_ERR_NOT_CONVERGED: return "SLR_ERR_NOT_CONVERGED";
+        case SLR_ERR_BREAKDOWN: return "SLR_ERR_BREAKDOWN";
+        case SLR_ERR_TIMEOUT: return "SLR_ERR_TIMEOUT";
+        case SLR_ERR_UNSUPPORTED: return "SLR_ERR_UNSUPPORTED";
+    }
+    return "SLR_ERR_UNKNOWN";
+}
+
+const char* slr_last_error_message(void) { return slr::g_last_error.c_str(); }
+
+slr_status slr_dd_order(int32_t n, const int32_t* rowptr, const int32_t* colind, int32_t nparts,
+                        const int32_t* part, int32_t* perm_out, int32_t* int_off, int32_t* ifc_off,
+                        int32_t* s_out) {
+    if (n < 0 || nparts < 1 || (n > 0 && (!rowptr || !part || (rowptr[n] > 0 && !colind)))) {
+        slr::set_error("invalid arguments");
+        return SLR_ERR_INVALID_ARG;
+    }
+    for (int32_t i = 0; i < n; ++i)
+        if (part[i] < 0 || part[i] >= nparts) { slr::set_error("part out of range"); return SLR_ERR_INVALID_ARG; }
+    for (int32_t i = 0; i < n; ++i)
+        for (int32_t q = rowptr[i]; q < rowptr[i + 1]; ++q)
+            if (colind[q] < 0 || colind[q] >= n) { slr::set_error("column out of range"); return SLR_ERR_INVALID_ARG; }
+    slr::HostSetup hs;
+    slr_status st = slr::host_dd_order(n, rowptr, colind, nparts, part, hs);
+    if (st != SLR_OK) return st;
+    if (perm_out) std::memcpy(perm_out, hs.perm.data(), sizeof(int32_t) * n);
+    if (int_off) std::memcpy(int_off, hs.int_off.data(), sizeof(int32_t) * (nparts + 1));
+    if (ifc_off) std::memcpy(ifc_off, hs.ifc_off.data(), sizeof(int32_t) * (nparts + 1));
+    if (s_out) *s_out = hs.s;
+    return SLR_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,84 @@
+// Internal structures of the SLR library: host-side setup results and the
+// device-resident handle.  Not part of the public ABI (see include/slr.h).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/slr.h"
+
+namespace slr {
+
+// ---------------------------------------------------------------- host setup
+
+// One interior block B_i of the partition (Section 5.2).  Its Cholesky factor
+// L_i is banded with half-bandwidth w (natural, ascending-index order).  Rows
+// are grouped in planes of W = clamp(w, 1, m) rows; plane J holds
+//   D_J = L_i[plane J, plane J]      (lower triangular, stored INVERTED),
+//   O_J = L_i[plane J, plane J-1]    (upper triangular incl. diagonal),
+// packed in one W x (W+1) column-major block P: slot q <= r holds D_J^{-1}[r][q],
+// slot q > r holds O_J[r][q-1].  The last plane is padded with identity rows.
+struct BandBlock {
+    int32_t m = 0;        // rows of B_i
+    int32_t w = 0;        // plane width W
+    int32_t c = 0;        // planes, c * W >= m
+    int32_t row0 = 0;     // first row of B_i inside u (DD interior order)
+    int64_t foff = 0;     // offset of plane 0 in the factor array (elements)
+};
+
+// Supernodal Cholesky factor of the interface matrix C (Eq. 3.1) in a
+// nested-dissection order.  Supernode J owns factor positions [c0[J], c0[J+1]).
+struct CFactorHost {
+    int32_t s = 0, ns = 0;
+    std::vector<int32_t> cperm;        // factor position -> DD interface index
+    std::vector<int32_t> c0;           // [ns+1]
+    std::vector<int32_t> parent;       // [ns], -1 at a root
+    std::vector<int32_t> level;        // [ns], 0 at leaves
+    std::vector<int64_t> r_off;        // [ns+1] offsets of R_J in rows
+    std::vector<int32_t> rows;         // R_J: factor positions below the diagonal block
+    std::vector<int64_t> pan_off;      // [ns+1] offsets of the row-major |R_J| x n_J panels
+    std::vector<double> panel;         // L[R_J, J]
+    std::vector<int64_t> dinv_off;     // [ns+1] offsets of the packed inverse blocks
+    std::vector<double> dinv;          // L_JJ^{-1}: lower triangle, column-major, packed
+    std::vector<int64_t> seg_ptr;      // [s+1] forward-gather segments of each position
+    std::vector<int64_t> seg_val;      // offset of the segment's values in panel
+    std::vector<int32_t> seg_x;        // first factor position of the segment's columns
+    std::vector<int32_t> seg_len;      // segment length (n_K)
+    int32_t nlev = 0;
+    std::vector<int32_t> lev_task_ptr; // [nlev+1] task ranges per level
+    std::vector<int32_t> tasks;        // 4 ints each: supernode, first, count, 0
+};
+
+struct HostSetup {
+    int32_t n = 0, nI = 0, s = 0, p = 0;
+    std::vector<int32_t> perm, iperm, int_off, ifc_off;
+    std::vector<int32_t> a_rp, a_ci;  std::vector<double> a_v;    // P A P^T, CSR
+    std::vector<int32_t> e_rp, e_ci;  std::vector<double> e_v;    // E   (nI x s)
+    std::vector<int32_t> et_rp, et_ci; std::vector<double> et_v;  // E^T (s x nI)
+    std::vector<int32_t> c_rp, c_ci;  std::vector<double> c_v;    // C   (s x s)
+    std::vector<BandBlock> band;
+    std::vector<double> bfac;
+    int32_t wmax = 0;
+    CFactorHost cf;
+};
+
+// Thread-local error text for slr_last_error_message().
+void set_error(const std::string& msg);
+
+// Host setup steps (slr_host.cpp).  Each returns SLR_OK or an error status.
+slr_status host_dd_order(int32_t n, const int32_t* rowptr, const int32_t* colind, int32_t nparts,
+                         const int32_t* part, HostSetup& hs);
+slr_status host_validate_csr(int32_t n, const int32_t* rowptr, const int32_t* colind,
+                             const double* val, int32_t nparts, const int32_t* part);
+slr_status host_split_blocks(const int32_t* rowptr, const int32_t* colind, const double* val,
+                             HostSetup& hs);
+slr_status host_band_factor(HostSetup& hs);
+slr_status host_c_factor(HostSetup& hs, int32_t leaf, int32_t task_rows);
+// Symmetric eigen-decomposition of the m x m tridiagonal T (Jacobi rotations):
+// eigenvalues descending in lam[m], eigenvectors as columns of Y (column-major m x m).
+void host_tridiag_eig(int32_t m, const double* alpha, const double* beta, double* lam, double* Y);
+// SplitMix64 output i (0-based) of stream seed, as a double in [-1, 1).
+double splitmix_pm1(uint64_t seed, uint64_t i);
+
+}  // namespace slr

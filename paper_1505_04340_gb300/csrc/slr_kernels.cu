@@ -1,0 +1,667 @@
+// Hot-path kernels of the SLR apply (Eq. 4.1 with S~^{-1} of Eq. 4.7) and of
+// the setup Lanczos on H (Eq. 3.2, Section 5.1), written for sm_103a.
+//
+//  K1  band solve      t = B^{-1} f, p independent banded Cholesky solves
+//  K2  coupling SpMVs  g' = g - E^T t,  b = E y
+//  K3  C solves        L^{-1} and L^{-T} with a supernodal, level-scheduled factor
+//  K4  low rank        w' = w/(1-theta) + U_k (d o U_k^T w)
+//  K5  PCG             A p, dots, axpys, scalar updates (FP64)
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cstdint>
+
+#include "slr_device.h"
+
+namespace slr {
+
+std::atomic<int64_t> g_kernel_launches{0};
+
+namespace {
+
+constexpr int kThreads = 256;
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// ------------------------------------------------------------------ K1
+// One CTA per block B_i.  Plane J of the factor is a W x (W+1) column-major
+// block P: P[q W + r] = D_J^{-1}[r][q] (q <= r) and O_J[r][q-1] (q > r).
+//   forward  (L y = f):   t = f_J - O_J y_{J-1};  y_J = D_J^{-1} t
+//   backward (L^T x = y): t = y_J - O_{J+1}^T x_{J+1};  x_J = D_J^{-T} t
+// The forward pass leaves y in `out`; the backward pass reads it back (same
+// CTA, ordered by __syncthreads) and writes x, or base - x.
+template <typename T, int NR>
+__global__ void __launch_bounds__(kThreads)
+k_band_solve(const BandBlock* __restrict__ blocks, const T* __restrict__ fac, const T* in, int64_t ldi,
+             T* out, int64_t ldo, const T* base, int64_t ldb) {
+    extern __shared__ unsigned char smem_raw[];
+    const BandBlock b = blocks[blockIdx.x];
+    const int m = b.m, W = b.w, c = b.c;
+    if (m == 0) return;
+    T* ys = reinterpret_cast<T*>(smem_raw);      // [NR][W]: y_{J-1} (fwd) / x_{J+1} (bwd)
+    T* ts = ys + (size_t)NR * W;                 // [NR][W]
+    const T* F = fac + b.foff;
+    const int64_t plane = (int64_t)W * (W + 1);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+
+    for (int J = 0; J < c; ++J) {
+        const T* P = F + J * plane;
+        for (int r = tid; r < W; r += blockDim.x) {
+            const int row = J * W + r;
+            T acc[NR];
+#pragma unroll
+            for (int j = 0; j < NR; ++j) acc[j] = (row < m) ? in[b.row0 + row + j * ldi] : T(0);
+            if (J > 0) {
+                for (int q = r + 1; q <= W; ++q) {
+                    const T a = P[(int64_t)q * W + r];
+#pragma unroll
+                    for (int j = 0; j < NR; ++j) acc[j] -= a * ys[j * W + q - 1];
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < NR; ++j) ts[j * W + r] = acc[j];
+        }
+        __syncthreads();
+        for (int r = tid; r < W; r += blockDim.x) {
+            const int row = J * W + r;
+            T acc[NR];
+#pragma unroll
+            for (int j = 0; j < NR; ++j) acc[j] = T(0);
+            for (int q = 0; q <= r; ++q) {
+                const T a = P[(int64_t)q * W + r];
+#pragma unroll
+                for (int j = 0; j < NR; ++j) acc[j] += a * ts[j * W + q];
+            }
+#pragma unroll
+            for (int j = 0; j < NR; ++j) {
+                ys[j * W + r] = acc[j];
+                if (row < m) out[b.row0 + row + j * ldo] = acc[j];
+            }
+        }
+        __syncthreads();
+    }
+    for (int J = c - 1; J >= 0; --J) {
+        const T* P = F + J * plane;
+        const T* P1 = F + (J + 1) * plane;
+        for (int col = warp; col < W; col += nwarp) {
+            T acc[NR];
+#pragma unroll
+            for (int j = 0; j < NR; ++j) acc[j] = T(0);
+            if (J + 1 < c) {
+                for (int r = lane; r <= col; r += 32) {
+                    const T a = P1[(int64_t)(col + 1) * W + r];
+#pragma unroll
+                    for (int j = 0; j < NR; ++j) acc[j] += a * ys[j * W + r];
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < NR; ++j) acc[j] = warp_sum(acc[j]);
+            if (lane == 0) {
+                const int row = J * W + col;
+#pragma unroll
+                for (int j = 0; j < NR; ++j) {
+                    const T y = (row < m) ? out[b.row0 + row + j * ldo] : T(0);
+                    ts[j * W + col] = y - acc[j];
+                }
+            }
+        }
+        __syncthreads();
+        for (int col = warp; col < W; col += nwarp) {
+            T acc[NR];
+#pragma unroll
+            for (int j = 0; j < NR; ++j) acc[j] = T(0);
+            for (int r = col + lane; r < W; r += 32) {
+                const T a = P[(int64_t)col * W + r];
+#pragma unroll
+                for (int j = 0; j < NR; ++j) acc[j] += a * ts[j * W + r];
+            }
+#pragma unroll
+            for (int j = 0; j < NR; ++j) acc[j] = warp_sum(acc[j]);
+            if (lane == 0) {
+                const int row = J * W + col;
+#pragma unroll
+                for (int j = 0; j < NR; ++j) {
+                    ys[j * W + col] = acc[j];
+                    if (row < m) {
+                        const int64_t g = b.row0 + row;
+                        out[g + j * ldo] = base ? base[g + j * ldb] - acc[j] : acc[j];
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ K2
+template <typename T>
+__global__ void k_gather_et(int32_t s, int32_t nrhs, const int32_t* __restrict__ rp,
+                            const int32_t* __restrict__ ci, const T* __restrict__ v, const T* g, int64_t ldg,
+                            const T* t, int64_t ldt, T* gp, int64_t ldgp) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)s * nrhs) return;
+    const int32_t i = (int32_t)(idx % s), j = (int32_t)(idx / s);
+    T acc = T(0);
+    for (int32_t q = rp[i]; q < rp[i + 1]; ++q) acc += v[q] * t[ci[q] + j * ldt];
+    gp[i + j * ldgp] = g ? g[i + j * ldg] - acc : acc;
+}
+
+template <typename T>
+__global__ void k_spmv(int32_t rows, int32_t nrhs, const int32_t* __restrict__ rp,
+                       const int32_t* __restrict__ ci, const T* __restrict__ v, const T* x, int64_t ldx,
+                       T* y, int64_t ldy) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)rows * nrhs) return;
+    const int32_t i = (int32_t)(idx % rows), j = (int32_t)(idx / rows);
+    T acc = T(0);
+    for (int32_t q = rp[i]; q < rp[i + 1]; ++q) acc += v[q] * x[ci[q] + j * ldx];
+    y[i + j * ldy] = acc;
+}
+
+// ------------------------------------------------------------------ K3
+// Supernode J owns factor positions [c0[J], c0[J+1]).  A task is (J, first, count).
+// forward, phase A: t_i = g[cperm[i]] - sum over segments of L[i, K] x_K   (warp per row)
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_cfwd_gather(const int4* __restrict__ tasks, const int32_t* __restrict__ c0, const int32_t* __restrict__ cperm,
+              const int64_t* __restrict__ seg_ptr, const int64_t* __restrict__ seg_val,
+              const int32_t* __restrict__ seg_x, const int32_t* __restrict__ seg_len, const T* __restrict__ panel,
+              const T* g, int64_t ldg, const T* xf, T* tf, int32_t s, int32_t nrhs) {
+    const int4 tk = tasks[blockIdx.x];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    for (int rr = warp; rr < tk.z; rr += nwarp) {
+        const int32_t i = c0[tk.x] + tk.y + rr;
+        for (int j = 0; j < nrhs; ++j) {
+            T acc = T(0);
+            for (int64_t sg = seg_ptr[i]; sg < seg_ptr[i + 1]; ++sg) {
+                const T* val = panel + seg_val[sg];
+                const T* xx = xf + seg_x[sg] + (int64_t)j * s;
+                const int len = seg_len[sg];
+                for (int e = lane; e < len; e += 32) acc += val[e] * xx[e];
+            }
+            acc = warp_sum(acc);
+            if (lane == 0) tf[i + (int64_t)j * s] = g[cperm[i] + j * ldg] - acc;
+        }
+    }
+}
+
+// forward, phase B: x_J = L_JJ^{-1} t_J (thread per row of the task)
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_cfwd_diag(const int4* __restrict__ tasks, const int32_t* __restrict__ c0, const int64_t* __restrict__ dinv_off,
+            const T* __restrict__ dinv, const T* tf, T* xf, int32_t s, int32_t nrhs) {
+    const int4 tk = tasks[blockIdx.x];
+    const int il = tk.y + threadIdx.x;
+    if (threadIdx.x >= tk.z) return;
+    const int32_t a0 = c0[tk.x], nJ = c0[tk.x + 1] - a0;
+    const T* D = dinv + dinv_off[tk.x];
+    for (int j = 0; j < nrhs; ++j) {
+        const T* t = tf + a0 + (int64_t)j * s;
+        T acc = T(0);
+        for (int jj = 0; jj <= il; ++jj) {
+            const int64_t cs = (int64_t)jj * nJ - (int64_t)jj * (jj - 1) / 2;
+            acc += D[cs + (il - jj)] * t[jj];
+        }
+        xf[a0 + il + (int64_t)j * s] = acc;
+    }
+}
+
+// backward, phase A: t_j = y_j - sum_p L[R_J[p], j] x[R_J[p]] (thread per column)
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_cbwd_gather(const int4* __restrict__ tasks, const int32_t* __restrict__ c0, const int64_t* __restrict__ r_off,
+              const int32_t* __restrict__ rows, const int64_t* __restrict__ pan_off, const T* __restrict__ panel,
+              T* yf, const T* xf, int32_t s, int32_t nrhs) {
+    const int4 tk = tasks[blockIdx.x];
+    if (threadIdx.x >= tk.z) return;
+    const int32_t a0 = c0[tk.x], nJ = c0[tk.x + 1] - a0, jl = tk.y + threadIdx.x;
+    const int64_t nr = r_off[tk.x + 1] - r_off[tk.x];
+    const int32_t* R = rows + r_off[tk.x];
+    const T* Pn = panel + pan_off[tk.x] + jl;
+    for (int j = 0; j < nrhs; ++j) {
+        const T* x = xf + (int64_t)j * s;
+        T acc = T(0);
+        for (int64_t p = 0; p < nr; ++p) acc += Pn[p * nJ] * x[R[p]];
+        yf[a0 + jl + (int64_t)j * s] -= acc;
+    }
+}
+
+// backward, phase B: x_J = L_JJ^{-T} t_J (warp per column), optional scatter to DD order
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_cbwd_diag(const int4* __restrict__ tasks, const int32_t* __restrict__ c0, const int64_t* __restrict__ dinv_off,
+            const T* __restrict__ dinv, const int32_t* __restrict__ cperm, const T* tf, T* xf, T* y_dd,
+            int64_t ldy, int32_t s, int32_t nrhs) {
+    const int4 tk = tasks[blockIdx.x];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    const int32_t a0 = c0[tk.x], nJ = c0[tk.x + 1] - a0;
+    const T* D = dinv + dinv_off[tk.x];
+    for (int cc = warp; cc < tk.z; cc += nwarp) {
+        const int jl = tk.y + cc;
+        const int64_t cs = (int64_t)jl * nJ - (int64_t)jl * (jl - 1) / 2;
+        for (int j = 0; j < nrhs; ++j) {
+            const T* t = tf + a0 + (int64_t)j * s;
+            T acc = T(0);
+            for (int i = jl + lane; i < nJ; i += 32) acc += D[cs + (i - jl)] * t[i];
+            acc = warp_sum(acc);
+            if (lane == 0) {
+                xf[a0 + jl + (int64_t)j * s] = acc;
+                if (y_dd) y_dd[cperm[a0 + jl] + j * ldy] = acc;
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ K4
+// part[(j k + kk) G + b] = partial of U[:, kk] . w[:, j] over block b's rows
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_ut_partial(int32_t s, int32_t k, const T* __restrict__ U, const T* __restrict__ w, T* part) {
+    __shared__ T red[kThreads / 32];
+    const int kk = blockIdx.y, j = blockIdx.z;
+    const T* u = U + (int64_t)kk * s;
+    const T* x = w + (int64_t)j * s;
+    T acc = T(0);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < s; i += (int64_t)gridDim.x * blockDim.x)
+        acc += u[i] * x[i];
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        T v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : T(0);
+        v = warp_sum(v);
+        if (threadIdx.x == 0) part[((int64_t)j * k + kk) * gridDim.x + blockIdx.x] = v;
+    }
+}
+
+// vk[kk + j k] = d[kk] * sum_b part[...]   (one warp per (kk, j))
+template <typename T>
+__global__ void k_ut_final(int32_t k, int32_t nrhs, int32_t G, const T* part, const T* __restrict__ dvec,
+                           T* vk) {
+    const int id = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (id >= k * nrhs) return;
+    const T* pp = part + (int64_t)id * G;
+    T acc = T(0);
+    for (int b = lane; b < G; b += 32) acc += pp[b];
+    acc = warp_sum(acc);
+    if (lane == 0) vk[id] = dvec[id % k] * acc;
+}
+
+template <typename T>
+__global__ void k_lowrank_update(int32_t s, int32_t k, int32_t nrhs, const T* __restrict__ U, const T* vk,
+                                 T cinv, T* w) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)s * nrhs) return;
+    const int32_t i = (int32_t)(idx % s), j = (int32_t)(idx / s);
+    const T* v = vk + (int64_t)j * k;
+    T acc = cinv * w[i + (int64_t)j * s];
+    for (int kk = 0; kk < k; ++kk) acc += U[i + (int64_t)kk * s] * v[kk];
+    w[i + (int64_t)j * s] = acc;
+}
+
+// ------------------------------------------------------------------ helpers
+template <typename TS, typename TD>
+__global__ void k_convert(int64_t rows, int32_t cols, const TS* src, int64_t lds, TD* dst, int64_t ldd) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= rows * cols) return;
+    const int64_t i = idx % rows, j = idx / rows;
+    dst[i + j * ldd] = (TD)src[i + j * lds];
+}
+
+__global__ void k_permute(int32_t n, int32_t nrhs, const int32_t* __restrict__ idx, const double* src, int64_t lds,
+                          double* dst, int64_t ldd, int gather) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)n * nrhs) return;
+    const int32_t a = (int32_t)(t % n), j = (int32_t)(t / n);
+    if (gather) dst[a + j * ldd] = src[idx[a] + j * lds];
+    else dst[idx[a] + j * ldd] = src[a + j * lds];
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_dot_partial(int64_t n, const double* a, int64_t lda, const double* b, int64_t ldb, double* part) {
+    __shared__ double red[kThreads / 32];
+    const int j = blockIdx.y;
+    const double* x = a + j * lda;
+    const double* y = b + j * ldb;
+    double acc = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        acc += x[i] * y[i];
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+        v = warp_sum(v);
+        if (threadIdx.x == 0) part[(int64_t)j * gridDim.x + blockIdx.x] = v;
+    }
+}
+
+__global__ void k_dot_final(int32_t cols, int32_t G, const double* part, double* out, int32_t stride) {
+    const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (j >= cols) return;
+    double acc = 0.0;
+    for (int b = lane; b < G; b += 32) acc += part[(int64_t)j * G + b];
+    acc = warp_sum(acc);
+    if (lane == 0) out[(int64_t)j * stride] = acc;
+}
+
+__global__ void k_gemv_n_sub(int32_t s, int32_t jn, const double* __restrict__ V, const double* __restrict__ h,
+                             double* w) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= s) return;
+    double acc = 0.0;
+    for (int q = 0; q < jn; ++q) acc += V[i + (int64_t)q * s] * h[q];
+    w[i] -= acc;
+}
+
+__global__ void k_axpby(int64_t n, double a, const double* x, double b, double* y) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = (b == 0.0) ? a * x[i] : a * x[i] + b * y[i];   // b = 0: y is not read
+}
+
+__global__ void k_gemm_nn(int32_t s, int32_t m, int32_t k, const double* __restrict__ V,
+                          const double* __restrict__ Y, double* U) {
+    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)s * k) return;
+    const int32_t i = (int32_t)(idx % s), kk = (int32_t)(idx / s);
+    double acc = 0.0;
+    for (int q = 0; q < m; ++q) acc += V[i + (int64_t)q * s] * Y[q + (int64_t)kk * m];
+    U[i + (int64_t)kk * s] = acc;
+}
+
+// ------------------------------------------------------------------ K5 scalars
+// scal[8 j + ...]: 0 rho, 1 p.q, 2 alpha, 3 r.r, 4 b.b, 5 beta, 6 rho_new, 7 r.z_old
+// flags[4 j + ...]: 0 active, 1 iterations, 2 status (0 running, 1 converged,
+// 2 breakdown); flags[4 nrhs] = number of active columns
+__global__ void k_pcg_alpha(int32_t nrhs, double* scal, int32_t* flags) {
+    const int j = threadIdx.x;
+    if (j >= nrhs || !flags[4 * j]) return;
+    double* sc = scal + 8 * j;
+    if (!(sc[1] > 0.0)) {
+        flags[4 * j] = 0;
+        flags[4 * j + 2] = 2;
+        sc[2] = 0.0;
+        return;
+    }
+    sc[2] = sc[0] / sc[1];
+}
+
+__global__ void k_pcg_update_xr(int32_t n, int32_t nrhs, double* x, double* r, const double* p, const double* q,
+                                const double* scal, const int32_t* flags) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)n * nrhs) return;
+    const int32_t j = (int32_t)(t / n);
+    if (!flags[4 * j]) return;
+    const double a = scal[8 * j + 2];
+    x[t] += a * p[t];
+    r[t] -= a * q[t];
+}
+
+__global__ void k_pcg_check(int32_t nrhs, double* scal, int32_t* flags, int32_t it, double tol) {
+    if (threadIdx.x != 0) return;
+    int32_t active = 0;
+    for (int j = 0; j < nrhs; ++j) {
+        if (!flags[4 * j]) continue;
+        const double* sc = scal + 8 * j;
+        flags[4 * j + 1] = it;
+        if (sc[3] <= tol * tol * sc[4]) {
+            flags[4 * j] = 0;
+            flags[4 * j + 2] = 1;
+        } else {
+            ++active;
+        }
+    }
+    flags[4 * nrhs] = active;
+}
+
+__global__ void k_pcg_beta(int32_t nrhs, double* scal, const int32_t* flags, int32_t flexible) {
+    const int j = threadIdx.x;
+    if (j >= nrhs || !flags[4 * j]) return;
+    double* sc = scal + 8 * j;
+    const double num = flexible ? sc[6] - sc[7] : sc[6];
+    sc[5] = num / sc[0];
+    sc[0] = sc[6];
+}
+
+__global__ void k_pcg_update_p(int32_t n, int32_t nrhs, double* p, const double* z, const double* scal,
+                               const int32_t* flags) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)n * nrhs) return;
+    const int32_t j = (int32_t)(t / n);
+    if (!flags[4 * j]) return;
+    p[t] = z[t] + scal[8 * j + 5] * p[t];
+}
+
+inline unsigned blocks_for(int64_t n, int t = kThreads) { return (unsigned)((n + t - 1) / t); }
+
+// every kernel launch of the library goes through this counter
+inline void counted(int n = 1) { g_kernel_launches.fetch_add(n, std::memory_order_relaxed); }
+
+template <typename T, int NR>
+cudaError_t band_pass(const DevOperator<T>& op, int32_t p, int32_t wmax, const T* in, int64_t ldi, T* out,
+                      int64_t ldo, const T* base, int64_t ldb, cudaStream_t st) {
+    size_t smem = 2ull * NR * wmax * sizeof(T);
+    auto kern = k_band_solve<T, NR>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    kern<<<p, kThreads, smem, st>>>(op.band, op.bfac, in, ldi, out, ldo, base, ldb);
+    counted();
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ launchers
+
+template <typename T>
+cudaError_t launch_band_solve(const DevOperator<T>& op, int32_t p, int32_t wmax, const T* in, int64_t ldi,
+                              T* out, int64_t ldo, const T* base, int64_t ldb, int32_t nrhs, cudaStream_t st) {
+    if (p == 0) return cudaSuccess;
+    for (int32_t c = 0; c < nrhs;) {
+        int32_t left = nrhs - c;
+        size_t per = 2ull * wmax * sizeof(T);
+        int nr = left >= 8 && per * 8 <= 200 * 1024 ? 8 : left >= 4 && per * 4 <= 200 * 1024 ? 4
+                 : left >= 2 && per * 2 <= 200 * 1024 ? 2 : 1;
+        const T* bs = base ? base + c * ldb : nullptr;
+        cudaError_t e;
+        switch (nr) {
+            case 8: e = band_pass<T, 8>(op, p, wmax, in + c * ldi, ldi, out + c * ldo, ldo, bs, ldb, st); break;
+            case 4: e = band_pass<T, 4>(op, p, wmax, in + c * ldi, ldi, out + c * ldo, ldo, bs, ldb, st); break;
+            case 2: e = band_pass<T, 2>(op, p, wmax, in + c * ldi, ldi, out + c * ldo, ldo, bs, ldb, st); break;
+            default: e = band_pass<T, 1>(op, p, wmax, in + c * ldi, ldi, out + c * ldo, ldo, bs, ldb, st); break;
+        }
+        if (e != cudaSuccess) return e;
+        c += nr;
+    }
+    return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t launch_gather_et(const DevOperator<T>& op, int32_t s, const T* g, int64_t ldg, const T* t,
+                             int64_t ldt, T* gp, int64_t ldgp, int32_t nrhs, cudaStream_t st) {
+    if (s == 0) return cudaSuccess;
+    k_gather_et<T><<<blocks_for((int64_t)s * nrhs), kThreads, 0, st>>>(s, nrhs, op.et_rp, op.et_ci, op.et_v, g,
+                                                                        ldg, t, ldt, gp, ldgp);
+    counted();
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_spmv_e(const DevOperator<T>& op, int32_t nI, const T* y, int64_t ldy, T* out, int64_t ldo,
+                          int32_t nrhs, cudaStream_t st) {
+    if (nI == 0) return cudaSuccess;
+    k_spmv<T><<<blocks_for((int64_t)nI * nrhs), kThreads, 0, st>>>(nI, nrhs, op.e_rp, op.e_ci, op.e_v, y, ldy,
+                                                                    out, ldo);
+    counted();
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_c_forward(const DevCFactor<T>& cf, const T* g_dd, int64_t ldg, T* tf, T* xf, int32_t nrhs,
+                             cudaStream_t st) {
+    for (int l = 0; l < cf.nlev; ++l) {
+        const int t0 = cf.lev_task_ptr[l], nt = cf.lev_task_ptr[l + 1] - t0;
+        if (nt == 0) continue;
+        k_cfwd_gather<T><<<nt, kThreads, 0, st>>>(cf.tasks + t0, cf.c0, cf.cperm, cf.seg_ptr, cf.seg_val, cf.seg_x,
+                                                  cf.seg_len, cf.panel, g_dd, ldg, xf, tf, cf.s, nrhs);
+        counted();
+        k_cfwd_diag<T><<<nt, kThreads, 0, st>>>(cf.tasks + t0, cf.c0, cf.dinv_off, cf.dinv, tf, xf, cf.s, nrhs);
+        counted();
+    }
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_c_backward(const DevCFactor<T>& cf, T* yf, T* xf, T* y_dd, int64_t ldy, int32_t nrhs,
+                              cudaStream_t st) {
+    for (int l = cf.nlev - 1; l >= 0; --l) {
+        const int t0 = cf.lev_task_ptr[l], nt = cf.lev_task_ptr[l + 1] - t0;
+        if (nt == 0) continue;
+        k_cbwd_gather<T><<<nt, kThreads, 0, st>>>(cf.tasks + t0, cf.c0, cf.r_off, cf.rows, cf.pan_off, cf.panel,
+                                                  yf, xf, cf.s, nrhs);
+        counted();
+        k_cbwd_diag<T><<<nt, kThreads, 0, st>>>(cf.tasks + t0, cf.c0, cf.dinv_off, cf.dinv, cf.cperm, yf, xf,
+                                                y_dd, ldy, cf.s, nrhs);
+        counted();
+    }
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_lowrank(const DevOperator<T>& op, int32_t s, int32_t k, T* w, int32_t nrhs, cudaStream_t st) {
+    if (s == 0) return cudaSuccess;
+    if (k > 0) {
+        const int G = kRedBlocks;
+        k_ut_partial<T><<<dim3(G, k, nrhs), kThreads, 0, st>>>(s, k, op.U, w, op.part);
+        counted();
+        k_ut_final<T><<<blocks_for((int64_t)k * nrhs * 32), kThreads, 0, st>>>(k, nrhs, G, op.part, op.dvec, op.vk);
+        counted();
+    }
+    k_lowrank_update<T><<<blocks_for((int64_t)s * nrhs), kThreads, 0, st>>>(s, k, nrhs, op.U, op.vk, op.cinv, w);
+    counted();
+    return cudaGetLastError();
+}
+
+template <typename TS, typename TD>
+cudaError_t launch_convert(int64_t rows, int32_t cols, const TS* src, int64_t lds, TD* dst, int64_t ldd,
+                           cudaStream_t st) {
+    if (rows * cols == 0) return cudaSuccess;
+    k_convert<TS, TD><<<blocks_for(rows * cols), kThreads, 0, st>>>(rows, cols, src, lds, dst, ldd);
+    counted();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_permute(int32_t n, int32_t nrhs, const int32_t* idx, const double* src, int64_t lds,
+                           double* dst, int64_t ldd, bool gather, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    k_permute<<<blocks_for((int64_t)n * nrhs), kThreads, 0, st>>>(n, nrhs, idx, src, lds, dst, ldd, gather);
+    counted();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_csr_spmv(int32_t n, const int32_t* rp, const int32_t* ci, const double* v, const double* x,
+                            int64_t ldx, double* y, int64_t ldy, int32_t nrhs, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    k_spmv<double><<<blocks_for((int64_t)n * nrhs), kThreads, 0, st>>>(n, nrhs, rp, ci, v, x, ldx, y, ldy);
+    counted();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dots(int64_t n, int32_t cols, const double* a, int64_t lda, const double* b, int64_t ldb,
+                        double* part, double* out, int32_t out_stride, cudaStream_t st) {
+    if (cols == 0) return cudaSuccess;
+    k_dot_partial<<<dim3(kRedBlocks, cols), kThreads, 0, st>>>(n, a, lda, b, ldb, part);
+    counted();
+    k_dot_final<<<blocks_for((int64_t)cols * 32), kThreads, 0, st>>>(cols, kRedBlocks, part, out, out_stride);
+    counted();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gemv_t(int32_t s, int32_t j, const double* V, const double* w, double* part, double* h,
+                          cudaStream_t st) {
+    return launch_dots(s, j, V, s, w, 0, part, h, 1, st);
+}
+
+cudaError_t launch_gemv_n_sub(int32_t s, int32_t j, const double* V, const double* h, double* w, cudaStream_t st) {
+    if (s == 0) return cudaSuccess;
+    k_gemv_n_sub<<<blocks_for(s), kThreads, 0, st>>>(s, j, V, h, w);
+    counted();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_axpby(int64_t n, double a, const double* x, double b, double* y, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    k_axpby<<<blocks_for(n), kThreads, 0, st>>>(n, a, x, b, y);
+    counted();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gemm_nn(int32_t s, int32_t m, int32_t k, const double* V, const double* Y, double* U,
+                           cudaStream_t st) {
+    if ((int64_t)s * k == 0) return cudaSuccess;
+    k_gemm_nn<<<blocks_for((int64_t)s * k), kThreads, 0, st>>>(s, m, k, V, Y, U);
+    counted();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pcg_alpha(int32_t nrhs, double* scal, int32_t* flags, cudaStream_t st) {
+    k_pcg_alpha<<<1, 64, 0, st>>>(nrhs, scal, flags);
+    counted();
+    return cudaGetLastError();
+}
+cudaError_t launch_pcg_update_xr(int32_t n, int32_t nrhs, double* x, double* r, const double* p, const double* q,
+                                 const double* scal, const int32_t* flags, cudaStream_t st) {
+    k_pcg_update_xr<<<blocks_for((int64_t)n * nrhs), kThreads, 0, st>>>(n, nrhs, x, r, p, q, scal, flags);
+    counted();
+    return cudaGetLastError();
+}
+cudaError_t launch_pcg_check(int32_t nrhs, double* scal, int32_t* flags, int32_t it, double tol, cudaStream_t st) {
+    k_pcg_check<<<1, 32, 0, st>>>(nrhs, scal, flags, it, tol);
+    counted();
+    return cudaGetLastError();
+}
+cudaError_t launch_pcg_beta(int32_t nrhs, double* scal, int32_t* flags, int32_t flexible, cudaStream_t st) {
+    k_pcg_beta<<<1, 64, 0, st>>>(nrhs, scal, flags, flexible);
+    counted();
+    return cudaGetLastError();
+}
+cudaError_t launch_pcg_update_p(int32_t n, int32_t nrhs, double* p, const double* z, const double* scal,
+                                const int32_t* flags, cudaStream_t st) {
+    k_pcg_update_p<<<blocks_for((int64_t)n * nrhs), kThreads, 0, st>>>(n, nrhs, p, z, scal, flags);
+    counted();
+    return cudaGetLastError();
+}
+
+// explicit instantiations for the two precisions of the apply
+#define SLR_INST(T)                                                                                             \
+    template cudaError_t launch_band_solve<T>(const DevOperator<T>&, int32_t, int32_t, const T*, int64_t, T*,   \
+                                              int64_t, const T*, int64_t, int32_t, cudaStream_t);               \
+    template cudaError_t launch_gather_et<T>(const DevOperator<T>&, int32_t, const T*, int64_t, const T*,       \
+                                             int64_t, T*, int64_t, int32_t, cudaStream_t);                      \
+    template cudaError_t launch_spmv_e<T>(const DevOperator<T>&, int32_t, const T*, int64_t, T*, int64_t,       \
+                                          int32_t, cudaStream_t);                                               \
+    template cudaError_t launch_c_forward<T>(const DevCFactor<T>&, const T*, int64_t, T*, T*, int32_t,          \
+                                             cudaStream_t);                                                     \
+    template cudaError_t launch_c_backward<T>(const DevCFactor<T>&, T*, T*, T*, int64_t, int32_t, cudaStream_t); \
+    template cudaError_t launch_lowrank<T>(const DevOperator<T>&, int32_t, int32_t, T*, int32_t, cudaStream_t);
+SLR_INST(double)
+SLR_INST(float)
+#undef SLR_INST
+template cudaError_t launch_convert<double, float>(int64_t, int32_t, const double*, int64_t, float*, int64_t,
+                                                   cudaStream_t);
+template cudaError_t launch_convert<float, double>(int64_t, int32_t, const float*, int64_t, double*, int64_t,
+                                                   cudaStream_t);
+template cudaError_t launch_convert<double, double>(int64_t, int32_t, const double*, int64_t, double*, int64_t,
+                                                    cudaStream_t);
+
+}  // namespace slr
+
+extern "C" int64_t slr_kernel_launches(void) { return slr::g_kernel_launches.load(); }

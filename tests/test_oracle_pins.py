@@ -342,3 +342,15 @@ def test_pcg_identity_preconditioner_is_cg():
     b = rng.standard_normal(12)
     x, it, rel, ok = pcg(A, b, lambda r: r.copy(), tol=1e-12)
     assert ok and it <= 12 and np.allclose(A @ x, b, atol=1e-10)
+
+
+def test_lanczos_three_term_recurrence_without_reorth():
+    """Before orthogonality is lost the plain recurrence gives V^T H V = T (Section 5.1)."""
+    P = small_fv()
+    slr = SLR(P.rowptr, P.colind, P.val, P.part, P.nparts, 0)
+    H = slr.h_dense()
+    a, b, V = lanczos(lambda v: H @ v, np.random.default_rng(2).standard_normal(H.shape[0]), 6,
+                      reorth_passes=0)
+    T = np.diag(a) + np.diag(b[:-1], 1) + np.diag(b[:-1], -1)
+    assert np.allclose(V.T @ H @ V, T, atol=1e-12)
+    assert np.allclose(V.T @ V, np.eye(6), atol=1e-12)
