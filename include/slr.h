@@ -71,7 +71,8 @@ typedef struct {
                                order, u_i = (x_i >> 11) 2^-53, x_i output i of the stream */
     int32_t c_leaf;         /* nested-dissection leaf size for C's ordering; 0 => 64     */
     int32_t verbose;        /* 1: setup prints timings to stderr                          */
-    int32_t reserved[6];
+    int32_t reserved[6];    /* reserved[0]: CTAs per subdomain in the band solve (1, 2, 4;
+                               0 = automatic); the rest must be 0                       */
 } slr_opts;
 
 typedef struct {

@@ -94,6 +94,9 @@ slr_status upload_operator(slr_handle h, DevOperator<T>& op, bool with_band) {
     const int32_t r = std::max(1, h->opts.nrhs_max);
     CS(upload(h, &op.band, hs.band));
     if (with_band) CS(upload(h, &op.bfac, hs.bfac));
+    op.band_G = hs.band_G;
+    CS(dalloc(h, &op.err, 1));
+    CK(cudaMemset(op.err, 0, sizeof(int32_t)));
     CS(upload(h, &op.e_rp, hs.e_rp));
     CS(upload(h, &op.e_ci, hs.e_ci));
     CS(upload(h, &op.e_v, hs.e_v));
@@ -115,11 +118,14 @@ slr_status upload_operator(slr_handle h, DevOperator<T>& op, bool with_band) {
     CS(upload(h, &d.dinv_off, c.dinv_off));
     CS(upload(h, &d.dinv, c.dinv));
     CS(upload(h, &d.seg_ptr, c.seg_ptr));
-    CS(upload(h, &d.seg_val, c.seg_val));
-    CS(upload(h, &d.seg_x, c.seg_x));
-    CS(upload(h, &d.seg_len, c.seg_len));
+    CS(upload(h, &d.seg_row, c.seg_row));
+    d.lev_ptask_ptr = c.lev_ptask_ptr;
+    d.nrow = (int64_t)c.rows.size();
     CS(dalloc(h, &d.tasks, c.tasks.size() / 4));
     if (!c.tasks.empty()) CK(cudaMemcpy(d.tasks, c.tasks.data(), c.tasks.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    CS(dalloc(h, &d.ptasks, c.ptasks.size() / 4));
+    if (!c.ptasks.empty()) CK(cudaMemcpy(d.ptasks, c.ptasks.data(), c.ptasks.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    CS(dalloc(h, &d.wbuf, (size_t)std::max<int64_t>(d.nrow, 1) * r));
     const int64_t n = hs.n, nI = hs.nI, s = hs.s;
     if constexpr (!std::is_same<T, double>::value) {
         CS(dalloc(h, &op.wr, (size_t)n * r));
@@ -307,9 +313,9 @@ void account(slr_handle h) {
     const int64_t cvals = (hs.cf.pan_off.empty() ? 0 : hs.cf.pan_off.back()) +
                           (hs.cf.dinv_off.empty() ? 0 : hs.cf.dinv_off.back());
     const int64_t nseg = hs.cf.seg_ptr.empty() ? 0 : hs.cf.seg_ptr.back();
-    const int64_t nrow = (int64_t)hs.cf.rows.size();
+    const int64_t nrow = (int64_t)hs.cf.rows.size();   // also the w values written and gathered
     const int64_t s = hs.s, k = h->k;
-    h->bytes_per_apply = 4 * band * wf + 2 * nnzE * (wf + 4) + 2 * cvals * wf + nseg * 16 + nrow * 4 +
+    h->bytes_per_apply = 4 * band * wf + 2 * nnzE * (wf + 4) + 2 * cvals * wf + nseg * (4 + wf) + nrow * (4 + wf) +
                          2 * s * k * wf + (2 * (int64_t)hs.n + 2 * (int64_t)hs.nI) * wv;
     h->flops_per_apply = 2 * (4 * band + 2 * nnzE + 2 * cvals + 2 * s * k);
 }
@@ -323,19 +329,44 @@ slr_status setup_impl(slr_handle h, int32_t n, const int32_t* rowptr, const int3
     CS(host_dd_order(n, rowptr, colind, nparts, part, hs));
     CS(host_split_blocks(rowptr, colind, val, hs));
     double t1 = now_s();
-    CS(host_band_factor(hs));
+    // CTAs per subdomain in the band solve: a slice holds at most 256 rows of a
+    // plane; with few subdomains two CTAs (a cluster) share each one so that
+    // more SMs stream the factor
+    {
+        int32_t G = 1;
+        int dev = 0, nsm = 152;
+        if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        // the widest plane decides the minimum split
+        int32_t wmx = 0;
+        for (int32_t q = 0; q < nparts; ++q) {
+            int32_t r0 = hs.int_off[q], m = hs.int_off[q + 1] - r0, w = 0;
+            for (int32_t a = r0; a < r0 + m; ++a)
+                for (int32_t t = hs.a_rp[a]; t < hs.a_rp[a + 1]; ++t) {
+                    int32_t cc = hs.a_ci[t];
+                    if (cc >= r0 && cc < r0 + m) w = std::max(w, std::abs(a - cc));
+                }
+            wmx = std::max(wmx, w);
+        }
+        while ((wmx + G - 1) / G > 256 && G < 4) G *= 2;
+        if ((wmx + G - 1) / G > 256) {
+            set_error("a B_i has plane width " + std::to_string(wmx) + " beyond the band kernel's limit (1024)");
+            return SLR_ERR_UNSUPPORTED;
+        }
+        const int32_t req = h->opts.reserved[0];        // opts.band_split, 0 = automatic
+        if (req == 1 || req == 2 || req == 4) {
+            if ((wmx + req - 1) / req <= 256) G = req;
+        } else if (G == 1 && 2 * nparts <= nsm && wmx >= 32) {
+            G = 2;
+        }
+        CS(host_band_factor(hs, G));
+    }
     double t2 = now_s();
-    CS(host_c_factor(hs, h->opts.c_leaf > 0 ? h->opts.c_leaf : 64, 128));
+    CS(host_c_factor(hs, h->opts.c_leaf > 0 ? h->opts.c_leaf : 64, 32));
     double t3 = now_s();
     if (vb)
         fprintf(stderr, "[slr] n=%d nI=%d s=%d p=%d wmax=%d band=%zu cvals=%zu sn=%d lev=%d | analysis %.3fs B %.3fs C %.3fs\n",
                 hs.n, hs.nI, hs.s, hs.p, hs.wmax, hs.bfac.size(), hs.cf.panel.size() + hs.cf.dinv.size(), hs.cf.ns,
                 hs.cf.nlev, t1 - t0, t2 - t1, t3 - t2);
-    // the band kernel keeps two plane vectors per RHS in shared memory
-    if (2ull * hs.wmax * sizeof(double) > 200 * 1024) {
-        set_error("a B_i has plane width " + std::to_string(hs.wmax) + " beyond the kernel's limit");
-        return SLR_ERR_UNSUPPORTED;
-    }
     CK(cudaGetDevice(&h->device));
     CS(upload(h, &h->perm, hs.perm));
     CS(upload(h, &h->a_rp, hs.a_rp));
@@ -551,6 +582,15 @@ slr_status slr_pcg_solve(slr_handle h, const double* b, double* x, int32_t nrhs,
     CK(cudaMemcpyAsync(fl.data(), h->iflags, sizeof(int32_t) * fl.size(), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     slr_status ret = SLR_OK;
+    {
+        int32_t e = 0;
+        const int32_t* ep = h->opts.precision == SLR_PREC_FP64 ? h->op64.err : h->op32.err;
+        CK(cudaMemcpy(&e, ep, sizeof(int32_t), cudaMemcpyDeviceToHost));
+        if (e) {
+            set_error("a bounded device wait expired in the band solve");
+            return SLR_ERR_TIMEOUT;
+        }
+    }
     for (int j = 0; j < nrhs; ++j) {
         if (iters_out) iters_out[j] = fl[4 * j + 1];
         double bb = sc[8 * j + 4];

@@ -23,11 +23,13 @@ struct DevCFactor {
     int64_t* dinv_off = nullptr;   // [ns+1]
     T* dinv = nullptr;             // packed lower, column-major
     int64_t* seg_ptr = nullptr;    // [s+1]
-    int64_t* seg_val = nullptr;
-    int32_t* seg_x = nullptr;
-    int32_t* seg_len = nullptr;
-    int4* tasks = nullptr;         // (supernode, first, count, 0)
-    std::vector<int32_t> lev_task_ptr;   // host copy, [nlev+1]
+    int32_t* seg_row = nullptr;    // panel rows holding each position
+    int64_t nrow = 0;              // panel rows in total
+    T* wbuf = nullptr;             // [nrow x nrhs_max] panel products of the forward solve
+    int4* tasks = nullptr;         // (supernode, first column, count <= 32, 0)
+    int4* ptasks = nullptr;        // (supernode, first panel row, count <= 32, 0)
+    std::vector<int32_t> lev_task_ptr;    // host copies, [nlev+1]
+    std::vector<int32_t> lev_ptask_ptr;
 };
 
 // Everything one apply needs in precision T (double: FP64 path; float: mixed).
@@ -35,6 +37,8 @@ template <typename T>
 struct DevOperator {
     BandBlock* band = nullptr;     // [p]
     T* bfac = nullptr;
+    int32_t band_G = 1;            // CTAs per subdomain (thread-block cluster size)
+    int32_t* err = nullptr;        // device status word: 1 = a bounded wait expired
     int32_t *e_rp = nullptr, *e_ci = nullptr;  T* e_v = nullptr;     // E   (nI x s)
     int32_t *et_rp = nullptr, *et_ci = nullptr; T* et_v = nullptr;   // E^T (s x nI)
     DevCFactor<T> cf;
@@ -84,6 +88,8 @@ template <typename T>
 cudaError_t launch_band_solve(const DevOperator<T>& op, int32_t p, int32_t wmax, const T* in, int64_t ldi,
                               T* out, int64_t ldo, const T* base, int64_t ldb, int32_t nrhs,
                               cudaStream_t st);
+// shared memory one band-solve CTA needs for plane width wmax and nr columns per pass
+size_t band_smem_bytes(int32_t wmax, int32_t G, int32_t nr, size_t elem);
 // ---- K2: gp = g - E^T t (g == NULL: gp = E^T t) ;  eb = E y
 template <typename T>
 cudaError_t launch_gather_et(const DevOperator<T>& op, int32_t s, const T* g, int64_t ldg, const T* t,

@@ -193,7 +193,7 @@ static void tri_inverse(int W, const double* D, double* X) {
     }
 }
 
-slr_status host_band_factor(HostSetup& hs) {
+slr_status host_band_factor(HostSetup& hs, int32_t G) {
     const int32_t p = hs.p;
     hs.band.assign(p, BandBlock());
     std::vector<int32_t> bw(p, 0);
@@ -212,11 +212,24 @@ slr_status host_band_factor(HostSetup& hs) {
         b.row0 = r0;
         b.w = m ? std::max(w, 1) : 0;
         b.c = m ? (m + b.w - 1) / b.w : 0;
+        int so = 0, sd = 0;
+        for (int g = 0; g < G; ++g) {
+            int a = 0, d = 0, nrg = band_slice_rows(b.w, G, g);
+            for (int cc = 0; cc < b.w; ++cc) {
+                a += band_cnt_O(cc, G, g);
+                d += nrg - std::min(nrg, band_lr0_D(cc, G, g));
+            }
+            so = std::max(so, a);
+            sd = std::max(sd, d);
+        }
+        b.SO = (so + 31) / 32 * 32;
+        b.SD = (sd + 31) / 32 * 32;
         b.foff = off;
-        off += (int64_t)b.c * b.w * (b.w + 1);
+        off += (int64_t)b.c * G * (b.SO + b.SD);
         hs.wmax = std::max(hs.wmax, b.w);
     }
-    hs.bfac.assign(off, 0.0);
+    hs.band_G = G;
+    hs.bfac.assign(off + 64, 0.0);   // tail slack: bulk copies round up to 16 bytes
     int bad = -1;
 #pragma omp parallel for schedule(dynamic, 1)
     for (int32_t i = 0; i < p; ++i) {
@@ -258,20 +271,27 @@ slr_status host_band_factor(HostSetup& hs) {
         };
         std::vector<double> D((size_t)W * W), X((size_t)W * W);
         for (int32_t J = 0; J < b.c; ++J) {
-            double* P = &hs.bfac[b.foff + (int64_t)J * W * (W + 1)];
             for (int32_t r = 0; r < W; ++r)
                 for (int32_t c = 0; c < W; ++c) {
                     int32_t l = J * W + r;
                     D[(size_t)r * W + c] = (l >= m) ? (r == c ? 1.0 : 0.0) : (c <= r ? Lat(l, J * W + c) : 0.0);
                 }
             tri_inverse(W, D.data(), X.data());
-            for (int32_t r = 0; r < W; ++r) {
-                int32_t l = J * W + r;
-                for (int32_t q = 0; q <= W; ++q) {
-                    double v;
-                    if (q <= r && q < W) v = X[(size_t)r * W + q];
-                    else v = (J > 0 && l < m) ? Lat(l, (J - 1) * W + (q - 1)) : 0.0;
-                    P[(size_t)q * W + r] = v;
+            double* plane = &hs.bfac[b.foff + (int64_t)J * G * (b.SO + b.SD)];
+            for (int g = 0; g < G; ++g) {
+                double* PO = plane + (int64_t)g * (b.SO + b.SD);
+                double* PD = PO + b.SO;
+                const int nrg = band_slice_rows(W, G, g);
+                int64_t o = 0, d = 0;
+                for (int cc = 0; cc < W; ++cc) {
+                    for (int lr = 0; lr < band_cnt_O(cc, G, g); ++lr) {     // O_J[r][cc], r <= cc
+                        const int r = lr * G + g, l = J * W + r;
+                        PO[o++] = (J > 0 && l < m) ? Lat(l, (J - 1) * W + cc) : 0.0;
+                    }
+                    for (int lr = std::min(nrg, band_lr0_D(cc, G, g)); lr < nrg; ++lr) {   // D_J^{-1}[r][cc], r >= cc
+                        const int r = lr * G + g;
+                        PD[d++] = X[(size_t)r * W + cc];
+                    }
                 }
             }
         }
@@ -400,6 +420,7 @@ slr_status host_c_factor(HostSetup& hs, int32_t leaf, int32_t task_rows) {
         cf.dinv_off.assign(1, 0);
         cf.seg_ptr.assign(1, 0);
         cf.lev_task_ptr.assign(1, 0);
+        cf.lev_ptask_ptr.assign(1, 0);
         return SLR_OK;
     }
     // graph of C without its diagonal
@@ -562,46 +583,42 @@ slr_status host_c_factor(HostSetup& hs, int32_t leaf, int32_t task_rows) {
         }
         std::memcpy(cf.panel.data() + cf.pan_off[J], Fj + (int64_t)nJ * nJ, sizeof(double) * nr * nJ);
     }
-    // forward-gather segments: row i of L left of its diagonal block is the union
-    // of rows R_K[p] = i of the descendants' panels, each n_K contiguous values
+    // forward gather lists: row i of L left of its diagonal block is the union of
+    // the panel rows R_K[p] = i of its descendants K
     cf.seg_ptr.assign(s + 1, 0);
     for (int32_t J = 0; J < ns; ++J)
         for (int64_t t = cf.r_off[J]; t < cf.r_off[J + 1]; ++t) cf.seg_ptr[cf.rows[t] + 1]++;
     for (int32_t i = 0; i < s; ++i) cf.seg_ptr[i + 1] += cf.seg_ptr[i];
-    const int64_t nseg = cf.seg_ptr[s];
-    cf.seg_val.assign(nseg, 0);
-    cf.seg_x.assign(nseg, 0);
-    cf.seg_len.assign(nseg, 0);
+    cf.seg_row.assign(cf.seg_ptr[s], 0);
     {
         std::vector<int64_t> fill(cf.seg_ptr.begin(), cf.seg_ptr.end() - 1);
-        for (int32_t J = 0; J < ns; ++J) {
-            const int32_t nJ = cf.c0[J + 1] - cf.c0[J];
-            for (int64_t t = cf.r_off[J]; t < cf.r_off[J + 1]; ++t) {
-                int64_t d = fill[cf.rows[t]]++;
-                cf.seg_val[d] = cf.pan_off[J] + (t - cf.r_off[J]) * nJ;
-                cf.seg_x[d] = cf.c0[J];
-                cf.seg_len[d] = nJ;
-            }
-        }
+        for (int32_t J = 0; J < ns; ++J)
+            for (int64_t t = cf.r_off[J]; t < cf.r_off[J + 1]; ++t) cf.seg_row[fill[cf.rows[t]]++] = (int32_t)t;
     }
-    // level schedule: tasks of at most task_rows rows of one supernode
+    // level schedule: column blocks and panel-row blocks of at most task_rows
     cf.nlev = 0;
     for (int32_t J = 0; J < ns; ++J) cf.nlev = std::max(cf.nlev, cf.level[J] + 1);
     std::vector<std::vector<int32_t>> bylev(cf.nlev);
     for (int32_t J = 0; J < ns; ++J) bylev[cf.level[J]].push_back(J);
     cf.lev_task_ptr.assign(cf.nlev + 1, 0);
+    cf.lev_ptask_ptr.assign(cf.nlev + 1, 0);
     cf.tasks.clear();
+    cf.ptasks.clear();
+    auto add = [&](std::vector<int32_t>& v, int32_t J, int32_t n) {
+        for (int32_t f = 0; f < n; f += task_rows) {
+            v.push_back(J);
+            v.push_back(f);
+            v.push_back(std::min(task_rows, n - f));
+            v.push_back(0);
+        }
+    };
     for (int32_t l = 0; l < cf.nlev; ++l) {
         for (int32_t J : bylev[l]) {
-            int32_t nJ = cf.c0[J + 1] - cf.c0[J];
-            for (int32_t f = 0; f < nJ; f += task_rows) {
-                cf.tasks.push_back(J);
-                cf.tasks.push_back(f);
-                cf.tasks.push_back(std::min(task_rows, nJ - f));
-                cf.tasks.push_back(0);
-            }
+            add(cf.tasks, J, cf.c0[J + 1] - cf.c0[J]);
+            add(cf.ptasks, J, (int32_t)(cf.r_off[J + 1] - cf.r_off[J]));
         }
         cf.lev_task_ptr[l + 1] = (int32_t)(cf.tasks.size() / 4);
+        cf.lev_ptask_ptr[l + 1] = (int32_t)(cf.ptasks.size() / 4);
     }
     return SLR_OK;
 }

@@ -14,18 +14,28 @@ namespace slr {
 
 // One interior block B_i of the partition (Section 5.2).  Its Cholesky factor
 // L_i is banded with half-bandwidth w (natural, ascending-index order).  Rows
-// are grouped in planes of W = clamp(w, 1, m) rows; plane J holds
-//   D_J = L_i[plane J, plane J]      (lower triangular, stored INVERTED),
-//   O_J = L_i[plane J, plane J-1]    (upper triangular incl. diagonal),
-// packed in one W x (W+1) column-major block P: slot q <= r holds D_J^{-1}[r][q],
-// slot q > r holds O_J[r][q-1].  The last plane is padded with identity rows.
+// are grouped in planes of W = clamp(w, 1, m) rows; for plane J
+//   O_J = L_i[plane J, plane J-1]     upper triangular incl. diagonal,
+//   D_J = L_i[plane J, plane J]^{-1}  lower triangular incl. diagonal (inverted).
+// Rows r of a plane are dealt to G slices (r mod G); slice g of each block is
+// packed column-major: column c of O holds the slice's rows r <= c, column q of
+// D its rows r >= q.  A plane occupies G (SO + SD) elements: slice g's O block
+// at g (SO + SD), its D block SO after that.  The last plane is padded with
+// identity rows.  (Layout shared with the band-solve kernel, slr_band.cu.)
 struct BandBlock {
     int32_t m = 0;        // rows of B_i
     int32_t w = 0;        // plane width W
     int32_t c = 0;        // planes, c * W >= m
     int32_t row0 = 0;     // first row of B_i inside u (DD interior order)
     int64_t foff = 0;     // offset of plane 0 in the factor array (elements)
+    int32_t SO = 0;       // elements of one O slice block (padded to 32)
+    int32_t SD = 0;       // elements of one D slice block (padded to 32)
 };
+
+// Slice geometry of the band layout (host packer and device kernel agree on it).
+inline int band_slice_rows(int W, int G, int g) { return g < W ? (W - 1 - g) / G + 1 : 0; }
+inline int band_cnt_O(int c, int G, int g) { return c >= g ? (c - g) / G + 1 : 0; }
+inline int band_lr0_D(int q, int G, int g) { return q <= g ? 0 : (q - g + G - 1) / G; }
 
 // Supernodal Cholesky factor of the interface matrix C (Eq. 3.1) in a
 // nested-dissection order.  Supernode J owns factor positions [c0[J], c0[J+1]).
@@ -41,13 +51,15 @@ struct CFactorHost {
     std::vector<double> panel;         // L[R_J, J]
     std::vector<int64_t> dinv_off;     // [ns+1] offsets of the packed inverse blocks
     std::vector<double> dinv;          // L_JJ^{-1}: lower triangle, column-major, packed
-    std::vector<int64_t> seg_ptr;      // [s+1] forward-gather segments of each position
-    std::vector<int64_t> seg_val;      // offset of the segment's values in panel
-    std::vector<int32_t> seg_x;        // first factor position of the segment's columns
-    std::vector<int32_t> seg_len;      // segment length (n_K)
+    // Forward solve: after level l, w[r_off[K] + p] = L[R_K[p], K] x_K for its supernodes K;
+    // position i then needs the sum of w over the panel rows that hold row i.
+    std::vector<int64_t> seg_ptr;      // [s+1] panel rows of each position, CSR
+    std::vector<int32_t> seg_row;      // global panel-row index r_off[K] + p
     int32_t nlev = 0;
-    std::vector<int32_t> lev_task_ptr; // [nlev+1] task ranges per level
-    std::vector<int32_t> tasks;        // 4 ints each: supernode, first, count, 0
+    std::vector<int32_t> lev_task_ptr; // [nlev+1] column-block tasks per level
+    std::vector<int32_t> tasks;        // 4 ints each: supernode, first column, count (<= 32), 0
+    std::vector<int32_t> lev_ptask_ptr;// [nlev+1] panel-row tasks per level
+    std::vector<int32_t> ptasks;       // 4 ints each: supernode, first panel row, count (<= 32), 0
 };
 
 struct HostSetup {
@@ -60,6 +72,7 @@ struct HostSetup {
     std::vector<BandBlock> band;
     std::vector<double> bfac;
     int32_t wmax = 0;
+    int32_t band_G = 1;   // CTAs (slices) per subdomain in the band solve
     CFactorHost cf;
 };
 
@@ -73,7 +86,7 @@ slr_status host_validate_csr(int32_t n, const int32_t* rowptr, const int32_t* co
                              const double* val, int32_t nparts, const int32_t* part);
 slr_status host_split_blocks(const int32_t* rowptr, const int32_t* colind, const double* val,
                              HostSetup& hs);
-slr_status host_band_factor(HostSetup& hs);
+slr_status host_band_factor(HostSetup& hs, int32_t G);
 slr_status host_c_factor(HostSetup& hs, int32_t leaf, int32_t task_rows);
 // Symmetric eigen-decomposition of the m x m tridiagonal T (Jacobi rotations):
 // eigenvalues descending in lam[m], eigenvectors as columns of Y (column-major m x m).

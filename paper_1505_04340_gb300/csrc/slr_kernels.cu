@@ -29,115 +29,7 @@ __device__ __forceinline__ T warp_sum(T v) {
     return v;
 }
 
-// ------------------------------------------------------------------ K1
-// One CTA per block B_i.  Plane J of the factor is a W x (W+1) column-major
-// block P: P[q W + r] = D_J^{-1}[r][q] (q <= r) and O_J[r][q-1] (q > r).
-//   forward  (L y = f):   t = f_J - O_J y_{J-1};  y_J = D_J^{-1} t
-//   backward (L^T x = y): t = y_J - O_{J+1}^T x_{J+1};  x_J = D_J^{-T} t
-// The forward pass leaves y in `out`; the backward pass reads it back (same
-// CTA, ordered by __syncthreads) and writes x, or base - x.
-template <typename T, int NR>
-__global__ void __launch_bounds__(kThreads)
-k_band_solve(const BandBlock* __restrict__ blocks, const T* __restrict__ fac, const T* in, int64_t ldi,
-             T* out, int64_t ldo, const T* base, int64_t ldb) {
-    extern __shared__ unsigned char smem_raw[];
-    const BandBlock b = blocks[blockIdx.x];
-    const int m = b.m, W = b.w, c = b.c;
-    if (m == 0) return;
-    T* ys = reinterpret_cast<T*>(smem_raw);      // [NR][W]: y_{J-1} (fwd) / x_{J+1} (bwd)
-    T* ts = ys + (size_t)NR * W;                 // [NR][W]
-    const T* F = fac + b.foff;
-    const int64_t plane = (int64_t)W * (W + 1);
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
-
-    for (int J = 0; J < c; ++J) {
-        const T* P = F + J * plane;
-        for (int r = tid; r < W; r += blockDim.x) {
-            const int row = J * W + r;
-            T acc[NR];
-#pragma unroll
-            for (int j = 0; j < NR; ++j) acc[j] = (row < m) ? in[b.row0 + row + j * ldi] : T(0);
-            if (J > 0) {
-                for (int q = r + 1; q <= W; ++q) {
-                    const T a = P[(int64_t)q * W + r];
-#pragma unroll
-                    for (int j = 0; j < NR; ++j) acc[j] -= a * ys[j * W + q - 1];
-                }
-            }
-#pragma unroll
-            for (int j = 0; j < NR; ++j) ts[j * W + r] = acc[j];
-        }
-        __syncthreads();
-        for (int r = tid; r < W; r += blockDim.x) {
-            const int row = J * W + r;
-            T acc[NR];
-#pragma unroll
-            for (int j = 0; j < NR; ++j) acc[j] = T(0);
-            for (int q = 0; q <= r; ++q) {
-                const T a = P[(int64_t)q * W + r];
-#pragma unroll
-                for (int j = 0; j < NR; ++j) acc[j] += a * ts[j * W + q];
-            }
-#pragma unroll
-            for (int j = 0; j < NR; ++j) {
-                ys[j * W + r] = acc[j];
-                if (row < m) out[b.row0 + row + j * ldo] = acc[j];
-            }
-        }
-        __syncthreads();
-    }
-    for (int J = c - 1; J >= 0; --J) {
-        const T* P = F + J * plane;
-        const T* P1 = F + (J + 1) * plane;
-        for (int col = warp; col < W; col += nwarp) {
-            T acc[NR];
-#pragma unroll
-            for (int j = 0; j < NR; ++j) acc[j] = T(0);
-            if (J + 1 < c) {
-                for (int r = lane; r <= col; r += 32) {
-                    const T a = P1[(int64_t)(col + 1) * W + r];
-#pragma unroll
-                    for (int j = 0; j < NR; ++j) acc[j] += a * ys[j * W + r];
-                }
-            }
-#pragma unroll
-            for (int j = 0; j < NR; ++j) acc[j] = warp_sum(acc[j]);
-            if (lane == 0) {
-                const int row = J * W + col;
-#pragma unroll
-                for (int j = 0; j < NR; ++j) {
-                    const T y = (row < m) ? out[b.row0 + row + j * ldo] : T(0);
-                    ts[j * W + col] = y - acc[j];
-                }
-            }
-        }
-        __syncthreads();
-        for (int col = warp; col < W; col += nwarp) {
-            T acc[NR];
-#pragma unroll
-            for (int j = 0; j < NR; ++j) acc[j] = T(0);
-            for (int r = col + lane; r < W; r += 32) {
-                const T a = P[(int64_t)col * W + r];
-#pragma unroll
-                for (int j = 0; j < NR; ++j) acc[j] += a * ts[j * W + r];
-            }
-#pragma unroll
-            for (int j = 0; j < NR; ++j) acc[j] = warp_sum(acc[j]);
-            if (lane == 0) {
-                const int row = J * W + col;
-#pragma unroll
-                for (int j = 0; j < NR; ++j) {
-                    ys[j * W + col] = acc[j];
-                    if (row < m) {
-                        const int64_t g = b.row0 + row;
-                        out[g + j * ldo] = base ? base[g + j * ldb] - acc[j] : acc[j];
-                    }
-                }
-            }
-        }
-        __syncthreads();
-    }
-}
+// K1 (the batched band solve) lives in slr_band.cu.
 
 // ------------------------------------------------------------------ K2
 template <typename T>
@@ -165,74 +57,136 @@ __global__ void k_spmv(int32_t rows, int32_t nrhs, const int32_t* __restrict__ r
 }
 
 // ------------------------------------------------------------------ K3
-// Supernode J owns factor positions [c0[J], c0[J+1]).  A task is (J, first, count).
-// forward, phase A: t_i = g[cperm[i]] - sum over segments of L[i, K] x_K   (warp per row)
+// Supernode J owns factor positions [c0[J], c0[J+1]) (n_J of them); its
+// off-diagonal rows R_J carry the row-major panel L[R_J, J] (|R_J| x n_J) and
+// its diagonal block is stored inverted (packed lower, column-major: column j
+// starts at cs(j) = j n_J - j (j-1) / 2).  Levels go leaves -> root.
+// A column task is (J, first, count <= 32); a panel task is (J, first row, count <= 32).
+__device__ __forceinline__ int64_t packed_col(int j, int n) { return (int64_t)j * n - (int64_t)j * (j - 1) / 2; }
+
+// forward, phase 1: t_i = g[cperm[i]] - sum of the panel products w that hold row i
 template <typename T>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(32)
 k_cfwd_gather(const int4* __restrict__ tasks, const int32_t* __restrict__ c0, const int32_t* __restrict__ cperm,
-              const int64_t* __restrict__ seg_ptr, const int64_t* __restrict__ seg_val,
-              const int32_t* __restrict__ seg_x, const int32_t* __restrict__ seg_len, const T* __restrict__ panel,
-              const T* g, int64_t ldg, const T* xf, T* tf, int32_t s, int32_t nrhs) {
+              const int64_t* __restrict__ seg_ptr, const int32_t* __restrict__ seg_row, const T* wbuf,
+              int64_t nrow, const T* g, int64_t ldg, T* tf, int32_t s, int32_t nrhs) {
     const int4 tk = tasks[blockIdx.x];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    for (int rr = warp; rr < tk.z; rr += nwarp) {
-        const int32_t i = c0[tk.x] + tk.y + rr;
-        for (int j = 0; j < nrhs; ++j) {
-            T acc = T(0);
-            for (int64_t sg = seg_ptr[i]; sg < seg_ptr[i + 1]; ++sg) {
-                const T* val = panel + seg_val[sg];
-                const T* xx = xf + seg_x[sg] + (int64_t)j * s;
-                const int len = seg_len[sg];
-                for (int e = lane; e < len; e += 32) acc += val[e] * xx[e];
-            }
-            acc = warp_sum(acc);
-            if (lane == 0) tf[i + (int64_t)j * s] = g[cperm[i] + j * ldg] - acc;
-        }
+    if ((int)threadIdx.x >= tk.z) return;
+    const int32_t i = c0[tk.x] + tk.y + threadIdx.x;
+    const int64_t e0 = seg_ptr[i], e1 = seg_ptr[i + 1];
+    for (int j = 0; j < nrhs; ++j) {
+        const T* w = wbuf + (int64_t)j * nrow;
+        T acc = T(0);
+        for (int64_t e = e0; e < e1; ++e) acc += w[seg_row[e]];
+        tf[i + (int64_t)j * s] = g[cperm[i] + j * ldg] - acc;
     }
 }
 
-// forward, phase B: x_J = L_JJ^{-1} t_J (thread per row of the task)
+// forward, phase 2: x_J = L_JJ^{-1} t_J for a block of <= 32 rows; 8 warps split
+// the reduction over columns, lane = row
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
 k_cfwd_diag(const int4* __restrict__ tasks, const int32_t* __restrict__ c0, const int64_t* __restrict__ dinv_off,
             const T* __restrict__ dinv, const T* tf, T* xf, int32_t s, int32_t nrhs) {
+    __shared__ T red[kThreads / 32][32];
     const int4 tk = tasks[blockIdx.x];
-    const int il = tk.y + threadIdx.x;
-    if (threadIdx.x >= tk.z) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = kThreads / 32;
     const int32_t a0 = c0[tk.x], nJ = c0[tk.x + 1] - a0;
+    const int il = tk.y + lane;
+    const int ncol = tk.y + tk.z;                  // columns 0 .. ncol-1 reach these rows
+    const int chunk = (ncol + nw - 1) / nw;
+    const int jb = warp * chunk, je = min(ncol, jb + chunk);
     const T* D = dinv + dinv_off[tk.x];
     for (int j = 0; j < nrhs; ++j) {
         const T* t = tf + a0 + (int64_t)j * s;
         T acc = T(0);
-        for (int jj = 0; jj <= il; ++jj) {
-            const int64_t cs = (int64_t)jj * nJ - (int64_t)jj * (jj - 1) / 2;
-            acc += D[cs + (il - jj)] * t[jj];
+        if (lane < tk.z) {
+            const int jend = min(je, il + 1);
+            int jj = jb;
+            for (; jj + 3 < jend; jj += 4) {
+                acc += D[packed_col(jj, nJ) + (il - jj)] * t[jj];
+                acc += D[packed_col(jj + 1, nJ) + (il - jj - 1)] * t[jj + 1];
+                acc += D[packed_col(jj + 2, nJ) + (il - jj - 2)] * t[jj + 2];
+                acc += D[packed_col(jj + 3, nJ) + (il - jj - 3)] * t[jj + 3];
+            }
+            for (; jj < jend; ++jj) acc += D[packed_col(jj, nJ) + (il - jj)] * t[jj];
         }
-        xf[a0 + il + (int64_t)j * s] = acc;
+        red[warp][lane] = acc;
+        __syncthreads();
+        if (warp == 0 && lane < tk.z) {
+            T v = T(0);
+#pragma unroll
+            for (int w = 0; w < nw; ++w) v += red[w][lane];
+            xf[a0 + il + (int64_t)j * s] = v;
+        }
+        __syncthreads();
     }
 }
 
-// backward, phase A: t_j = y_j - sum_p L[R_J[p], j] x[R_J[p]] (thread per column)
+// forward, phase 3: w[r_off[J] + p] = L[R_J[p], J] . x_J (warp per panel row, lanes over columns)
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
-k_cbwd_gather(const int4* __restrict__ tasks, const int32_t* __restrict__ c0, const int64_t* __restrict__ r_off,
-              const int32_t* __restrict__ rows, const int64_t* __restrict__ pan_off, const T* __restrict__ panel,
-              T* yf, const T* xf, int32_t s, int32_t nrhs) {
+k_cfwd_panel(const int4* __restrict__ ptasks, const int32_t* __restrict__ c0, const int64_t* __restrict__ r_off,
+             const int64_t* __restrict__ pan_off, const T* __restrict__ panel, const T* xf, T* wbuf, int64_t nrow,
+             int32_t s, int32_t nrhs) {
+    const int4 tk = ptasks[blockIdx.x];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = kThreads / 32;
+    const int32_t a0 = c0[tk.x], nJ = c0[tk.x + 1] - a0;
+    for (int pr = warp; pr < tk.z; pr += nw) {
+        const int64_t p = tk.y + pr;
+        const T* P = panel + pan_off[tk.x] + p * nJ;
+        for (int j = 0; j < nrhs; ++j) {
+            const T* x = xf + a0 + (int64_t)j * s;
+            T acc = T(0);
+            for (int c = lane; c < nJ; c += 32) acc += P[c] * x[c];
+            acc = warp_sum(acc);
+            if (lane == 0) wbuf[r_off[tk.x] + p + (int64_t)j * nrow] = acc;
+        }
+    }
+}
+
+// backward, phase 1: t_j = y_j - sum_p L[R_J[p], j] x[R_J[p]] for <= 32 columns
+// (lane = column); 8 warps split the panel rows
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_cbwd_panel(const int4* __restrict__ tasks, const int32_t* __restrict__ c0, const int64_t* __restrict__ r_off,
+             const int32_t* __restrict__ rows, const int64_t* __restrict__ pan_off, const T* __restrict__ panel,
+             T* yf, const T* xf, int32_t s, int32_t nrhs) {
+    __shared__ T red[kThreads / 32][32];
     const int4 tk = tasks[blockIdx.x];
-    if (threadIdx.x >= tk.z) return;
-    const int32_t a0 = c0[tk.x], nJ = c0[tk.x + 1] - a0, jl = tk.y + threadIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = kThreads / 32;
+    const int32_t a0 = c0[tk.x], nJ = c0[tk.x + 1] - a0, jl = tk.y + lane;
     const int64_t nr = r_off[tk.x + 1] - r_off[tk.x];
     const int32_t* R = rows + r_off[tk.x];
     const T* Pn = panel + pan_off[tk.x] + jl;
+    const int64_t chunk = (nr + nw - 1) / nw, pb = warp * chunk, pe = min(nr, pb + chunk);
     for (int j = 0; j < nrhs; ++j) {
         const T* x = xf + (int64_t)j * s;
         T acc = T(0);
-        for (int64_t p = 0; p < nr; ++p) acc += Pn[p * nJ] * x[R[p]];
-        yf[a0 + jl + (int64_t)j * s] -= acc;
+        if (lane < tk.z) {
+            int64_t p = pb;
+            for (; p + 3 < pe; p += 4) {
+                acc += Pn[p * nJ] * x[R[p]];
+                acc += Pn[(p + 1) * nJ] * x[R[p + 1]];
+                acc += Pn[(p + 2) * nJ] * x[R[p + 2]];
+                acc += Pn[(p + 3) * nJ] * x[R[p + 3]];
+            }
+            for (; p < pe; ++p) acc += Pn[p * nJ] * x[R[p]];
+        }
+        red[warp][lane] = acc;
+        __syncthreads();
+        if (warp == 0 && lane < tk.z) {
+            T v = T(0);
+#pragma unroll
+            for (int w = 0; w < nw; ++w) v += red[w][lane];
+            yf[a0 + jl + (int64_t)j * s] -= v;
+        }
+        __syncthreads();
     }
 }
 
-// backward, phase B: x_J = L_JJ^{-T} t_J (warp per column), optional scatter to DD order
+// backward, phase 2: x_J = L_JJ^{-T} t_J (warp per column, lanes over the column),
+// optional scatter to DD order
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
 k_cbwd_diag(const int4* __restrict__ tasks, const int32_t* __restrict__ c0, const int64_t* __restrict__ dinv_off,
@@ -244,11 +198,11 @@ k_cbwd_diag(const int4* __restrict__ tasks, const int32_t* __restrict__ c0, cons
     const T* D = dinv + dinv_off[tk.x];
     for (int cc = warp; cc < tk.z; cc += nwarp) {
         const int jl = tk.y + cc;
-        const int64_t cs = (int64_t)jl * nJ - (int64_t)jl * (jl - 1) / 2;
+        const T* Dc = D + packed_col(jl, nJ) - jl;
         for (int j = 0; j < nrhs; ++j) {
             const T* t = tf + a0 + (int64_t)j * s;
             T acc = T(0);
-            for (int i = jl + lane; i < nJ; i += 32) acc += D[cs + (i - jl)] * t[i];
+            for (int i = jl + lane; i < nJ; i += 32) acc += Dc[i] * t[i];
             acc = warp_sum(acc);
             if (lane == 0) {
                 xf[a0 + jl + (int64_t)j * s] = acc;
@@ -443,46 +397,9 @@ inline unsigned blocks_for(int64_t n, int t = kThreads) { return (unsigned)((n +
 // every kernel launch of the library goes through this counter
 inline void counted(int n = 1) { g_kernel_launches.fetch_add(n, std::memory_order_relaxed); }
 
-template <typename T, int NR>
-cudaError_t band_pass(const DevOperator<T>& op, int32_t p, int32_t wmax, const T* in, int64_t ldi, T* out,
-                      int64_t ldo, const T* base, int64_t ldb, cudaStream_t st) {
-    size_t smem = 2ull * NR * wmax * sizeof(T);
-    auto kern = k_band_solve<T, NR>;
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-    }
-    kern<<<p, kThreads, smem, st>>>(op.band, op.bfac, in, ldi, out, ldo, base, ldb);
-    counted();
-    return cudaGetLastError();
-}
-
 }  // namespace
 
 // ------------------------------------------------------------------ launchers
-
-template <typename T>
-cudaError_t launch_band_solve(const DevOperator<T>& op, int32_t p, int32_t wmax, const T* in, int64_t ldi,
-                              T* out, int64_t ldo, const T* base, int64_t ldb, int32_t nrhs, cudaStream_t st) {
-    if (p == 0) return cudaSuccess;
-    for (int32_t c = 0; c < nrhs;) {
-        int32_t left = nrhs - c;
-        size_t per = 2ull * wmax * sizeof(T);
-        int nr = left >= 8 && per * 8 <= 200 * 1024 ? 8 : left >= 4 && per * 4 <= 200 * 1024 ? 4
-                 : left >= 2 && per * 2 <= 200 * 1024 ? 2 : 1;
-        const T* bs = base ? base + c * ldb : nullptr;
-        cudaError_t e;
-        switch (nr) {
-            case 8: e = band_pass<T, 8>(op, p, wmax, in + c * ldi, ldi, out + c * ldo, ldo, bs, ldb, st); break;
-            case 4: e = band_pass<T, 4>(op, p, wmax, in + c * ldi, ldi, out + c * ldo, ldo, bs, ldb, st); break;
-            case 2: e = band_pass<T, 2>(op, p, wmax, in + c * ldi, ldi, out + c * ldo, ldo, bs, ldb, st); break;
-            default: e = band_pass<T, 1>(op, p, wmax, in + c * ldi, ldi, out + c * ldo, ldo, bs, ldb, st); break;
-        }
-        if (e != cudaSuccess) return e;
-        c += nr;
-    }
-    return cudaSuccess;
-}
 
 template <typename T>
 cudaError_t launch_gather_et(const DevOperator<T>& op, int32_t s, const T* g, int64_t ldg, const T* t,
@@ -509,12 +426,19 @@ cudaError_t launch_c_forward(const DevCFactor<T>& cf, const T* g_dd, int64_t ldg
                              cudaStream_t st) {
     for (int l = 0; l < cf.nlev; ++l) {
         const int t0 = cf.lev_task_ptr[l], nt = cf.lev_task_ptr[l + 1] - t0;
-        if (nt == 0) continue;
-        k_cfwd_gather<T><<<nt, kThreads, 0, st>>>(cf.tasks + t0, cf.c0, cf.cperm, cf.seg_ptr, cf.seg_val, cf.seg_x,
-                                                  cf.seg_len, cf.panel, g_dd, ldg, xf, tf, cf.s, nrhs);
-        counted();
-        k_cfwd_diag<T><<<nt, kThreads, 0, st>>>(cf.tasks + t0, cf.c0, cf.dinv_off, cf.dinv, tf, xf, cf.s, nrhs);
-        counted();
+        const int p0 = cf.lev_ptask_ptr[l], np = cf.lev_ptask_ptr[l + 1] - p0;
+        if (nt > 0) {
+            k_cfwd_gather<T><<<nt, 32, 0, st>>>(cf.tasks + t0, cf.c0, cf.cperm, cf.seg_ptr, cf.seg_row, cf.wbuf,
+                                                cf.nrow, g_dd, ldg, tf, cf.s, nrhs);
+            counted();
+            k_cfwd_diag<T><<<nt, kThreads, 0, st>>>(cf.tasks + t0, cf.c0, cf.dinv_off, cf.dinv, tf, xf, cf.s, nrhs);
+            counted();
+        }
+        if (np > 0) {
+            k_cfwd_panel<T><<<np, kThreads, 0, st>>>(cf.ptasks + p0, cf.c0, cf.r_off, cf.pan_off, cf.panel, xf,
+                                                     cf.wbuf, cf.nrow, cf.s, nrhs);
+            counted();
+        }
     }
     return cudaGetLastError();
 }
@@ -525,8 +449,8 @@ cudaError_t launch_c_backward(const DevCFactor<T>& cf, T* yf, T* xf, T* y_dd, in
     for (int l = cf.nlev - 1; l >= 0; --l) {
         const int t0 = cf.lev_task_ptr[l], nt = cf.lev_task_ptr[l + 1] - t0;
         if (nt == 0) continue;
-        k_cbwd_gather<T><<<nt, kThreads, 0, st>>>(cf.tasks + t0, cf.c0, cf.r_off, cf.rows, cf.pan_off, cf.panel,
-                                                  yf, xf, cf.s, nrhs);
+        k_cbwd_panel<T><<<nt, kThreads, 0, st>>>(cf.tasks + t0, cf.c0, cf.r_off, cf.rows, cf.pan_off, cf.panel,
+                                                 yf, xf, cf.s, nrhs);
         counted();
         k_cbwd_diag<T><<<nt, kThreads, 0, st>>>(cf.tasks + t0, cf.c0, cf.dinv_off, cf.dinv, cf.cperm, yf, xf,
                                                 y_dd, ldy, cf.s, nrhs);
@@ -642,8 +566,6 @@ cudaError_t launch_pcg_update_p(int32_t n, int32_t nrhs, double* p, const double
 
 // explicit instantiations for the two precisions of the apply
 #define SLR_INST(T)                                                                                             \
-    template cudaError_t launch_band_solve<T>(const DevOperator<T>&, int32_t, int32_t, const T*, int64_t, T*,   \
-                                              int64_t, const T*, int64_t, int32_t, cudaStream_t);               \
     template cudaError_t launch_gather_et<T>(const DevOperator<T>&, int32_t, const T*, int64_t, const T*,       \
                                              int64_t, T*, int64_t, int32_t, cudaStream_t);                      \
     template cudaError_t launch_spmv_e<T>(const DevOperator<T>&, int32_t, const T*, int64_t, T*, int64_t,       \
