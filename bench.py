@@ -186,6 +186,29 @@ def run_reference(args):
     }), flush=True)
 
 
+def run_profile(args):
+    """Setup, warm-up, then `steps` solves inside the NVTX range "timed" (for ncu)."""
+    import torch
+    import paper_1505_04340_gb300 as pkg
+    from paper_1505_04340_gb300 import SLR
+    pkg.load()
+    P, _ = build_problem(args.problem)
+    b = torch.tensor(P.b[:, 0], device="cuda")
+    h = SLR(P.rowptr, P.colind, P.val, P.part, P.nparts, k=P.k, lanczos_steps=P.lanczos_steps,
+            precision=args.precision, nrhs_max=1, flexible_cg=(args.precision == "mixed"))
+    for _ in range(args.warmup):
+        h.pcg(b)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("timed")
+    for _ in range(args.steps):
+        x, its, rel, st = h.pcg(b)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    print(json.dumps({"profile": args.precision, "iterations": int(its[0]), "relres": float(rel[0]),
+                      "launches_total": pkg.slr.kernel_launches()}))
+    h.close()
+
+
 def run_ours(args):
     import torch
     import paper_1505_04340_gb300 as pkg
@@ -370,8 +393,12 @@ def main():
     ap.add_argument("--ref-iters", type=int, default=36,
                     help="iterations of a full solve of the workload (measured by the GPU arm)")
     ap.add_argument("--ref-sample-its", type=int, default=2)
+    ap.add_argument("--profile", action="store_true", help="solves inside an NVTX range only (for ncu)")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.profile:
+        run_profile(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

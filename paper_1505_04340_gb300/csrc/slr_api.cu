@@ -622,7 +622,14 @@ slr_status slr_set_lowrank(slr_handle h, int32_t k, const double* Z, const doubl
         CS(dalloc(h, &T1, (size_t)s * k));
         CK(cudaMemcpy(Zd, Z, sizeof(double) * s * k, cudaMemcpyHostToDevice));
         CK(launch_csr_spmv(s, h->c_rp, h->c_ci, h->c_v, Zd, s, CZ, s, k, st));       // C Z
-        CK(launch_c_forward<double>(h->op64.cf, CZ, s, T1, U, k, st));              // U = L^{-1} C Z
+        // U = L^{-1} C Z, at most nrhs_max columns at a time (the forward solve's
+        // panel-product workspace holds nrhs_max columns)
+        const int32_t r = std::max(1, h->opts.nrhs_max);
+        for (int32_t c0 = 0; c0 < k; c0 += r) {
+            const int32_t nc = std::min(r, k - c0);
+            CK(launch_c_forward<double>(h->op64.cf, CZ + (int64_t)c0 * s, s, T1 + (int64_t)c0 * s,
+                                        U + (int64_t)c0 * s, nc, st));
+        }
         CK(cudaStreamSynchronize(st));
     }
     std::vector<double> lv(lam, lam + k);

@@ -99,6 +99,8 @@ cudaError_t launch_spmv_e(const DevOperator<T>& op, int32_t nI, const T* y, int6
                           int64_t ldo, int32_t nrhs, cudaStream_t st);
 // ---- K3: C solves.  fwd: xf = L^{-1} P g (g in DD order, xf in factor order)
 //              bwd: xf = L^{-T} yf (factor order), optional scatter to DD order y_dd
+// tf, xf, yf: s x nrhs (leading dimension s).  The forward solve also writes
+// cf.wbuf, which holds nrhs_max columns: callers pass nrhs <= opts.nrhs_max.
 template <typename T>
 cudaError_t launch_c_forward(const DevCFactor<T>& cf, const T* g_dd, int64_t ldg, T* tf, T* xf,
                              int32_t nrhs, cudaStream_t st);
