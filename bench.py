@@ -196,16 +196,23 @@ def run_profile(args):
     b = torch.tensor(P.b[:, 0], device="cuda")
     h = SLR(P.rowptr, P.colind, P.val, P.part, P.nparts, k=P.k, lanczos_steps=P.lanczos_steps,
             precision=args.precision, nrhs_max=1, flexible_cg=(args.precision == "mixed"))
+    info = h.get_info()
+    f = torch.randn(info["n_interior"], dtype=torch.float64, device="cuda")
+    g = torch.randn(info["s"], dtype=torch.float64, device="cuda")
+    r = torch.randn(P.n, dtype=torch.float64, device="cuda")
+    step = {"pcg": lambda: h.pcg(b), "bsolve": lambda: h.bsolve(f), "csolve": lambda: h.csolve(g),
+            "apply": lambda: h.apply(r)}[args.profile_kernel]
     for _ in range(args.warmup):
-        h.pcg(b)
+        step()
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_push("timed")
     for _ in range(args.steps):
-        x, its, rel, st = h.pcg(b)
+        step()
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_pop()
-    print(json.dumps({"profile": args.precision, "iterations": int(its[0]), "relres": float(rel[0]),
-                      "launches_total": pkg.slr.kernel_launches()}))
+    x, its, rel, st = h.pcg(b)
+    print(json.dumps({"profile": args.precision, "kernel": args.profile_kernel, "iterations": int(its[0]),
+                      "relres": float(rel[0]), "launches_total": pkg.slr.kernel_launches()}))
     h.close()
 
 
@@ -395,6 +402,7 @@ def main():
     ap.add_argument("--ref-sample-its", type=int, default=2)
     ap.add_argument("--profile", action="store_true", help="solves inside an NVTX range only (for ncu)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--profile-kernel", default="pcg", choices=["pcg", "bsolve", "csolve", "apply"])
     args = ap.parse_args()
     if args.profile:
         run_profile(args)

@@ -3,22 +3,22 @@
 //
 // Factor layout (built by host_band_factor): the Cholesky factor L_i is banded
 // with half-bandwidth w; rows are grouped in planes of W rows.  For plane J
-//   O_J = L_i[plane J, plane J-1]  upper triangular incl. diagonal,
-//   D_J = L_i[plane J, plane J]^{-1} lower triangular incl. diagonal (inverted on the host).
-// Rows r of a plane are dealt to cluster ranks g = r mod G ("slices"); slice g
-// of each block is stored column-major and packed: column c of O holds the
-// slice's rows r <= c, column q of D holds its rows r >= q.  Plane stride is
-// G (SO + SD) elements: slice g's O block at g (SO + SD), its D block SO later.
+//   O_J = L_i[plane J, plane J-1]    upper triangular incl. diagonal,
+//   D_J = L_i[plane J, plane J]^{-1} lower triangular incl. diagonal (inverted on the host),
+//   forward  (L y = f):    t = f_J - O_J y_{J-1};          y_J = D_J t
+//   backward (L^T x = y):  t = y_J - O_{J+1}^T x_{J+1};    x_J = D_J^T t
+// All four products are "output row = sum over columns" of a triangular
+// matrix (O_J, D_J^T upper; D_J, O_J^T lower), each stored on its own.  Output
+// rows are dealt to the G CTAs of a cluster (r mod G = rank); each CTA's
+// slice of a block is packed column-major (column c: its rows r <= c for an
+// upper block, r >= c for a lower one), so a CTA streams exactly its bytes.
 //
-//   forward  (L y = f):    t_J = f_J - O_J y_{J-1};       y_J = D_J t_J
-//   backward (L^T x = y):  t_J = y_J - O_{J+1}^T x_{J+1};  x_J = D_J^T t_J
-//
-// Each CTA streams the blocks of its slice through a ring of NBUF shared
-// buffers with 1-D bulk asynchronous copies completed on mbarriers (one
-// thread issues, everyone waits with a bounded spin).  Forward phases use
-// lanes = rows, warps = columns round-robin; backward phases use one warp per
-// column.  Vectors move between the CTAs of a cluster through distributed
-// shared memory, ordered by cluster barriers.
+// Each CTA streams its slices through a ring of kNBuf shared buffers with 1-D
+// bulk asynchronous copies completed on mbarriers (one thread issues,
+// everyone waits with a bounded spin that sets a device status word instead of
+// hanging).  Lanes own output rows, warps take columns round-robin, and the
+// per-warp partial sums are added once per phase.  The full input vector of a
+// phase is assembled in every CTA through distributed shared memory.
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
@@ -83,13 +83,6 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
 
-template <typename T>
-__device__ __forceinline__ T warp_sum_band(T v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
 template <int G>
 __device__ __forceinline__ void cluster_barrier() {
     if constexpr (G > 1) {
@@ -101,32 +94,29 @@ __device__ __forceinline__ void cluster_barrier() {
 
 struct Geom {
     int W, c, g, nrg;
-    int nO, nD;
-    int64_t base, PS, SO;
+    int nU, nL;
+    int64_t base, PS, SU, SL;
 };
 
-// Position of chunk k in the stream: forward  D_0, (O_J, D_J) J = 1..c-1,
-// then backward D_{c-1}, (O_{J+1}, D_J) J = c-2..0.  part: 0 = O, 1 = D.
-__device__ __forceinline__ void chunk_pos(const Geom& q, int k, int& part, int& plane, int& idx) {
-    const int per = q.nO + q.nD, fwd = q.nD + (q.c - 1) * per;
-    int kk = k < fwd ? k : k - fwd;
-    if (kk < q.nD) {
-        part = 1;
-        plane = k < fwd ? 0 : q.c - 1;
-        idx = kk;
+// Block types: 0 O_J (upper, fwd), 1 D_J (lower, fwd), 2 O_J^T (lower, bwd), 3 D_J^T (upper, bwd).
+// Stream: forward D_0, (O_J, D_J) J = 1..c-1; backward D_{c-1}^T, (O_{J+1}^T, D_J^T) J = c-2..0.
+__device__ __forceinline__ void chunk_pos(const Geom& q, int k, int& type, int& plane, int& idx) {
+    const int per = q.nU + q.nL, half = q.nL + (q.c - 1) * per;
+    if (k < half) {
+        if (k < q.nL) { type = 1; plane = 0; idx = k; return; }
+        const int kk = k - q.nL, pr = kk / per, r = kk % per;
+        plane = 1 + pr;
+        if (r < q.nU) { type = 0; idx = r; } else { type = 1; idx = r - q.nU; }
         return;
     }
-    kk -= q.nD;
-    const int pr = kk / per, r = kk % per;
-    if (k < fwd) {
-        plane = 1 + pr;
-        part = r < q.nO ? 0 : 1;
-        idx = r < q.nO ? r : r - q.nO;
-    } else {
-        part = r < q.nO ? 0 : 1;
-        plane = r < q.nO ? q.c - 1 - pr : q.c - 2 - pr;
-        idx = r < q.nO ? r : r - q.nO;
-    }
+    const int k2 = k - half;
+    if (k2 < q.nU) { type = 3; plane = q.c - 1; idx = k2; return; }
+    const int kk = k2 - q.nU, pr = kk / per, r = kk % per;
+    if (r < q.nL) { type = 2; plane = q.c - 1 - pr; idx = r; } else { type = 3; plane = q.c - 2 - pr; idx = r - q.nL; }
+}
+
+__device__ __forceinline__ int64_t block_off(const Geom& q, int type) {
+    return type == 0 ? 0 : type == 1 ? q.SU : type == 2 ? q.SU + q.SL : q.SU + 2 * q.SL;
 }
 
 }  // namespace
@@ -146,77 +136,73 @@ k_band_solve2(const BandBlock* __restrict__ blocks, const T* __restrict__ fac, c
     // ---- shared memory carve-up
     unsigned char* ring = smem;                                     // kNBuf x kChunk
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + kNBuf * kChunk);
-    int* colO = reinterpret_cast<int*>(full + kNBuf);              // [W+1]
-    int* colD = colO + (W + 1);                                    // [W+1]
-    int* chO = colD + (W + 1);                                     // [kMaxCh+1]
-    int* chD = chO + (kMaxCh + 1);                                 // [kMaxCh+1]
-    int* hdr = chD + (kMaxCh + 1);                                 // nO, nD
+    int* colU = reinterpret_cast<int*>(full + kNBuf);              // [W+1]
+    int* colL = colU + (W + 1);                                    // [W+1]
+    int* chU = colL + (W + 1);                                     // [kMaxCh+1]
+    int* chL = chU + (kMaxCh + 1);                                 // [kMaxCh+1]
+    int* hdr = chL + (kMaxCh + 1);                                 // nU, nL
     uintptr_t vp = reinterpret_cast<uintptr_t>(hdr + 4);
     vp = (vp + 15) & ~uintptr_t(15);
-    T* yfull = reinterpret_cast<T*>(vp);            // [NR][W]  y_{J-1} (forward)
-    T* tfull = yfull + NR * W;                      // [NR][W]  t_J (forward)
-    T* part = tfull + NR * W;                       // [kW][NR][256] per-warp partial sums
-    T* recvA = part + kW * NR * 256;                // [G][NR][W]
-    T* recvB = recvA + G * NR * W;                  // [2][G][NR][W]
-    T* xown = recvB + 2 * G * NR * W;               // [NR][256]
-    T* town = xown + NR * 256;                      // [NR][256]
+    T* vst = reinterpret_cast<T*>(vp);              // [NR][W] y_{J-1} (fwd) / x_{J+1} (bwd), whole plane
+    T* vt = vst + NR * W;                           // [NR][W] t, whole plane
+    T* part = vt + NR * W;                          // [kW][NR][256] per-warp partial sums
 
     Geom q;
     q.W = W;
     q.c = c;
     q.g = g;
     q.nrg = slice_rows(W, G, g);
-    q.PS = (int64_t)G * (b.SO + b.SD);
-    q.SO = b.SO;
-    q.base = b.foff + (int64_t)g * (b.SO + b.SD);
+    q.SU = b.SU;
+    q.SL = b.SL;
+    q.PS = (int64_t)G * 2 * (b.SU + b.SL);
+    q.base = b.foff + (int64_t)g * 2 * (b.SU + b.SL);
 
     if (tid == 0) {
         int a = 0, d = 0;
         for (int cc = 0; cc < W; ++cc) {
-            colO[cc] = a;
-            colD[cc] = d;
+            colU[cc] = a;
+            colL[cc] = d;
             a += cnt_O(cc, G, g);
             d += q.nrg - min(q.nrg, lr0_D(cc, G, g));
         }
-        colO[W] = a;
-        colD[W] = d;
+        colU[W] = a;
+        colL[W] = d;
         // greedy column chunks of at most kChunk - 32 bytes (room for 16-byte alignment)
         const int budget = (kChunk - 32) / (int)sizeof(T);
-        int n = 0, acc = 0;
-        chO[0] = 0;
-        for (int cc = 0; cc < W; ++cc) {
-            const int e = colO[cc + 1] - colO[cc];
-            if (acc > 0 && acc + e > budget) { chO[++n] = cc; acc = 0; }
-            acc += e;
+        for (int t = 0; t < 2; ++t) {
+            const int* col = t ? colL : colU;
+            int* ch = t ? chL : chU;
+            int n = 0, acc = 0;
+            ch[0] = 0;
+            for (int cc = 0; cc < W; ++cc) {
+                const int e = col[cc + 1] - col[cc];
+                if (acc > 0 && acc + e > budget) { ch[++n] = cc; acc = 0; }
+                acc += e;
+            }
+            ch[++n] = W;
+            hdr[t] = n;
         }
-        chO[++n] = W;
-        hdr[0] = n;
-        n = 0;
-        acc = 0;
-        chD[0] = 0;
-        for (int cc = 0; cc < W; ++cc) {
-            const int e = colD[cc + 1] - colD[cc];
-            if (acc > 0 && acc + e > budget) { chD[++n] = cc; acc = 0; }
-            acc += e;
-        }
-        chD[++n] = W;
-        hdr[1] = n;
         for (int i = 0; i < kNBuf; ++i) mbar_init(&full[i], 1);
         fence_mbar_init();
     }
     __syncthreads();
-    q.nO = hdr[0];
-    q.nD = hdr[1];
-    const int total = 2 * (q.nD + (c - 1) * (q.nO + q.nD));
+    q.nU = hdr[0];
+    q.nL = hdr[1];
+    const int total = 2 * (q.nL + (c - 1) * (q.nU + q.nL));
 
-    // chunk k -> (source, bytes, element shift) ; issued by thread 0 only
-    auto issue = [&](int k) {
-        int pt, pl, ix;
-        chunk_pos(q, k, pt, pl, ix);
-        const int* col = pt ? colD : colO;
-        const int* ch = pt ? chD : chO;
-        const int64_t e0 = q.base + (int64_t)pl * q.PS + (pt ? q.SO : 0) + col[ch[ix]];
-        const int64_t e1 = e0 + (col[ch[ix + 1]] - col[ch[ix]]);
+    auto src_of = [&](int k, int& type, int& ix, int64_t& e0, int64_t& e1) {
+        int pl;
+        chunk_pos(q, k, type, pl, ix);
+        const bool up = (type == 0 || type == 3);
+        const int* col = up ? colU : colL;
+        const int* ch = up ? chU : chL;
+        e0 = q.base + (int64_t)pl * q.PS + block_off(q, type) + col[ch[ix]];
+        e1 = e0 + (col[ch[ix + 1]] - col[ch[ix]]);
+    };
+    auto issue = [&](int k) {   // thread 0 only
+        int type, ix;
+        int64_t e0, e1;
+        src_of(k, type, ix, e0, e1);
         const uintptr_t a0 = reinterpret_cast<uintptr_t>(fac + e0), a1 = reinterpret_cast<uintptr_t>(fac + e1);
         const uintptr_t al0 = a0 & ~uintptr_t(15), al1 = (a1 + 15) & ~uintptr_t(15);
         uint64_t* bar = &full[k % kNBuf];
@@ -226,17 +212,6 @@ k_band_solve2(const BandBlock* __restrict__ blocks, const T* __restrict__ fac, c
         } else {
             mbar_arrive(bar);
         }
-    };
-    // consumer view of chunk k: pointer p with p[col[cc] + local] = element
-    auto view = [&](int k, int pt, int ix) -> const T* {
-        int ptc, pl, ixc;
-        chunk_pos(q, k, ptc, pl, ixc);
-        const int* col = pt ? colD : colO;
-        const int* ch = pt ? chD : chO;
-        const int64_t e0 = q.base + (int64_t)pl * q.PS + (pt ? q.SO : 0) + col[ch[ix]];
-        const uintptr_t a0 = reinterpret_cast<uintptr_t>(fac + e0);
-        const int shift = (int)((a0 & 15) / sizeof(T));
-        return reinterpret_cast<const T*>(ring + (k % kNBuf) * kChunk) + shift - col[ch[ix]];
     };
     auto wait_full = [&](int k) {
         uint64_t* bar = &full[k % kNBuf];
@@ -256,89 +231,50 @@ k_band_solve2(const BandBlock* __restrict__ blocks, const T* __restrict__ fac, c
             issue(k + kNBuf);
         }
     };
+    auto peer = [&](T* p, int r) -> T* {
+        if constexpr (G > 1) return cg::this_cluster().map_shared_rank(p, r);
+        return p;
+    };
 
     if (tid == 0)
         for (int k = 0; k < kNBuf && k < total; ++k) issue(k);
     // every CTA of the cluster is running before anyone stores into a peer's shared memory
     cluster_barrier<G>();
 
-    auto peer = [&](T* p, int r) -> T* {
-        if constexpr (G > 1) return cg::this_cluster().map_shared_rank(p, r);
-        return p;
-    };
-
     int k = 0;
     T acc[kRB][NR];
-    // =================================================================== forward
-    for (int J = 0; J < c; ++J) {
-        // ---- t_J = f_J - O_J y_{J-1}: lanes = rows, warps take columns round-robin
+    // acc[rb][j] += sum over the chunks of one block of M[lr][cc] * vin[j][cc], lanes = rows
+    auto run_block = [&](bool upper, const T* vin) {
 #pragma unroll
         for (int rb = 0; rb < kRB; ++rb)
 #pragma unroll
             for (int j = 0; j < NR; ++j) acc[rb][j] = T(0);
-        if (J > 0) {
-            for (int ix = 0; ix < q.nO; ++ix, ++k) {
-                wait_full(k);
-                const T* P = view(k, 0, ix);
-                for (int cc = chO[ix] + warp; cc < chO[ix + 1]; cc += kW) {
-                    const int n = cnt_O(cc, G, g);
-                    const T* Pc = P + colO[cc];
-                    T yv[NR];
-#pragma unroll
-                    for (int j = 0; j < NR; ++j) yv[j] = yfull[j * W + cc];
-#pragma unroll
-                    for (int rb = 0; rb < kRB; ++rb) {
-                        const int lr = rb * 32 + lane;
-                        if (rb * 32 < n && lr < n) {
-                            const T a = Pc[lr];
-#pragma unroll
-                            for (int j = 0; j < NR; ++j) acc[rb][j] += a * yv[j];
-                        }
-                    }
-                }
-                release(k);
-            }
-        }
-#pragma unroll
-        for (int rb = 0; rb < kRB; ++rb)
-#pragma unroll
-            for (int j = 0; j < NR; ++j) part[(warp * NR + j) * 256 + rb * 32 + lane] = acc[rb][j];
-        __syncthreads();
-        for (int lr = tid; lr < q.nrg; lr += kT) {
-            const int r = lr * G + g, row = J * W + r;
-#pragma unroll
-            for (int j = 0; j < NR; ++j) {
-                T s = T(0);
-#pragma unroll
-                for (int w = 0; w < kW; ++w) s += part[(w * NR + j) * 256 + lr];
-                const T f = row < m ? in[b.row0 + row + j * ldi] : T(0);
-                const T t = f - s;
-#pragma unroll
-                for (int pr = 0; pr < G; ++pr) peer(tfull, pr)[j * W + r] = t;
-            }
-        }
-        cluster_barrier<G>();
-        // ---- y_J = D_J t_J
-#pragma unroll
-        for (int rb = 0; rb < kRB; ++rb)
-#pragma unroll
-            for (int j = 0; j < NR; ++j) acc[rb][j] = T(0);
-        for (int ix = 0; ix < q.nD; ++ix, ++k) {
+        const int nch = upper ? q.nU : q.nL;
+        const int* col = upper ? colU : colL;
+        const int* ch = upper ? chU : chL;
+        for (int ix = 0; ix < nch; ++ix, ++k) {
             wait_full(k);
-            const T* P = view(k, 1, ix);
-            for (int cc = chD[ix] + warp; cc < chD[ix + 1]; cc += kW) {
-                const int l0 = min(q.nrg, lr0_D(cc, G, g));
-                const T* Pc = P + colD[cc] - l0;
-                T tv[NR];
+            int type, ixx;
+            int64_t e0, e1;
+            src_of(k, type, ixx, e0, e1);
+            const int shift = (int)((reinterpret_cast<uintptr_t>(fac + e0) & 15) / sizeof(T));
+            const T* P = reinterpret_cast<const T*>(ring + (k % kNBuf) * kChunk) + shift - col[ch[ix]];
+            for (int cc = ch[ix] + warp; cc < ch[ix + 1]; cc += kW) {
+                const int lo = upper ? 0 : min(q.nrg, lr0_D(cc, G, g));
+                const int hi = upper ? cnt_O(cc, G, g) : q.nrg;
+                const T* Pc = P + col[cc] - lo;
+                T v[NR];
 #pragma unroll
-                for (int j = 0; j < NR; ++j) tv[j] = tfull[j * W + cc];
+                for (int j = 0; j < NR; ++j) v[j] = vin[j * W + cc];
 #pragma unroll
                 for (int rb = 0; rb < kRB; ++rb) {
-                    const int lr = rb * 32 + lane;
-                    if (rb * 32 + 31 >= l0 && rb * 32 < q.nrg && lr >= l0 && lr < q.nrg) {
-                        const T a = Pc[lr];
+                    if (rb * 32 + 32 > lo && rb * 32 < hi) {
+                        const int lr = rb * 32 + lane;
+                        if (lr >= lo && lr < hi) {
+                            const T a = Pc[lr];
 #pragma unroll
-                        for (int j = 0; j < NR; ++j) acc[rb][j] += a * tv[j];
+                            for (int j = 0; j < NR; ++j) acc[rb][j] += a * v[j];
+                        }
                     }
                 }
             }
@@ -349,111 +285,81 @@ k_band_solve2(const BandBlock* __restrict__ blocks, const T* __restrict__ fac, c
 #pragma unroll
             for (int j = 0; j < NR; ++j) part[(warp * NR + j) * 256 + rb * 32 + lane] = acc[rb][j];
         __syncthreads();
+    };
+    auto zero_part = [&]() {
+        for (int i = tid; i < kW * NR * 256; i += kT) part[i] = T(0);
+        __syncthreads();
+    };
+    auto part_sum = [&](int lr, int j) -> T {
+        T s = T(0);
+#pragma unroll
+        for (int w = 0; w < kW; ++w) s += part[(w * NR + j) * 256 + lr];
+        return s;
+    };
+
+    // =================================================================== forward
+    for (int J = 0; J < c; ++J) {
+        if (J > 0) run_block(true, vst); else zero_part();                 // O_J y_{J-1}
         for (int lr = tid; lr < q.nrg; lr += kT) {
             const int r = lr * G + g, row = J * W + r;
 #pragma unroll
             for (int j = 0; j < NR; ++j) {
-                T s = T(0);
+                const T f = row < m ? in[b.row0 + row + j * ldi] : T(0);
+                const T t = f - part_sum(lr, j);
 #pragma unroll
-                for (int w = 0; w < kW; ++w) s += part[(w * NR + j) * 256 + lr];
-                if (row < m) out[b.row0 + row + j * ldo] = s;
+                for (int pr = 0; pr < G; ++pr) peer(vt, pr)[j * W + r] = t;
+            }
+        }
+        cluster_barrier<G>();
+        run_block(false, vt);                                              // D_J t
+        for (int lr = tid; lr < q.nrg; lr += kT) {
+            const int r = lr * G + g, row = J * W + r;
 #pragma unroll
-                for (int pr = 0; pr < G; ++pr) peer(yfull, pr)[j * W + r] = s;
+            for (int j = 0; j < NR; ++j) {
+                const T y = part_sum(lr, j);
+                if (row < m) out[b.row0 + row + j * ldo] = y;
+#pragma unroll
+                for (int pr = 0; pr < G; ++pr) peer(vst, pr)[j * W + r] = y;
             }
         }
         cluster_barrier<G>();
     }
     // =================================================================== backward
     for (int J = c - 1; J >= 0; --J) {
-        const int par = J & 1;
-        // ---- column partials of O_{J+1}^T x_{J+1} over this slice's rows
-        if (J < c - 1) {
-            for (int ix = 0; ix < q.nO; ++ix, ++k) {
-                wait_full(k);
-                const T* P = view(k, 0, ix);
-                for (int cc = chO[ix] + warp; cc < chO[ix + 1]; cc += kW) {
-                    const int n = cnt_O(cc, G, g);
-                    const T* Pc = P + colO[cc];
-                    T s[NR];
-#pragma unroll
-                    for (int j = 0; j < NR; ++j) s[j] = T(0);
-                    for (int lr = lane; lr < n; lr += 32) {
-                        const T a = Pc[lr];
-#pragma unroll
-                        for (int j = 0; j < NR; ++j) s[j] += a * xown[j * 256 + lr];
-                    }
-#pragma unroll
-                    for (int j = 0; j < NR; ++j) s[j] = warp_sum_band(s[j]);
-                    if (lane < G) {
-#pragma unroll
-                        for (int j = 0; j < NR; ++j) peer(recvA, lane)[(g * NR + j) * W + cc] = s[j];
-                    }
-                }
-                release(k);
-            }
-        }
-        cluster_barrier<G>();
+        if (J < c - 1) run_block(false, vst); else zero_part();            // O_{J+1}^T x_{J+1}
         for (int lr = tid; lr < q.nrg; lr += kT) {
             const int r = lr * G + g, row = J * W + r;
 #pragma unroll
             for (int j = 0; j < NR; ++j) {
-                T s = T(0);
-                if (J < c - 1) {
-#pragma unroll
-                    for (int pr = 0; pr < G; ++pr) s += recvA[(pr * NR + j) * W + r];
-                }
                 const T y = row < m ? out[b.row0 + row + j * ldo] : T(0);
-                town[j * 256 + lr] = y - s;
+                const T t = y - part_sum(lr, j);
+#pragma unroll
+                for (int pr = 0; pr < G; ++pr) peer(vt, pr)[j * W + r] = t;
             }
-        }
-        __syncthreads();
-        // ---- column partials of D_J^T t_J
-        T* rB = recvB + par * G * NR * W;
-        for (int ix = 0; ix < q.nD; ++ix, ++k) {
-            wait_full(k);
-            const T* P = view(k, 1, ix);
-            for (int cc = chD[ix] + warp; cc < chD[ix + 1]; cc += kW) {
-                const int l0 = min(q.nrg, lr0_D(cc, G, g));
-                const T* Pc = P + colD[cc] - l0;
-                T s[NR];
-#pragma unroll
-                for (int j = 0; j < NR; ++j) s[j] = T(0);
-                for (int lr = l0 + lane; lr < q.nrg; lr += 32) {
-                    const T a = Pc[lr];
-#pragma unroll
-                    for (int j = 0; j < NR; ++j) s[j] += a * town[j * 256 + lr];
-                }
-#pragma unroll
-                for (int j = 0; j < NR; ++j) s[j] = warp_sum_band(s[j]);
-                if (lane < G) {
-#pragma unroll
-                    for (int j = 0; j < NR; ++j) peer(rB, lane)[(g * NR + j) * W + cc] = s[j];
-                }
-            }
-            release(k);
         }
         cluster_barrier<G>();
+        run_block(true, vt);                                               // D_J^T t
         for (int lr = tid; lr < q.nrg; lr += kT) {
             const int r = lr * G + g, row = J * W + r;
 #pragma unroll
             for (int j = 0; j < NR; ++j) {
-                T x = T(0);
-#pragma unroll
-                for (int pr = 0; pr < G; ++pr) x += rB[(pr * NR + j) * W + r];
-                xown[j * 256 + lr] = x;
+                const T x = part_sum(lr, j);
                 if (row < m) {
                     const int64_t gi = b.row0 + row;
                     out[gi + j * ldo] = base ? base[gi + j * ldb] - x : x;
                 }
+#pragma unroll
+                for (int pr = 0; pr < G; ++pr) peer(vst, pr)[j * W + r] = x;
             }
         }
-        __syncthreads();
+        cluster_barrier<G>();
     }
 }
 
 size_t band_smem_bytes(int32_t wmax, int32_t G, int32_t nr, size_t elem) {
+    (void)G;
     size_t fixed = (size_t)kNBuf * kChunk + kNBuf * 8 + 2 * (wmax + 1) * 4 + 2 * (kMaxCh + 1) * 4 + 16 + 16;
-    size_t vec = (size_t)(2 * nr * wmax + kW * nr * 256 + G * nr * wmax + 2 * G * nr * wmax + 2 * nr * 256) * elem;
+    size_t vec = (size_t)(2 * nr * wmax + kW * nr * 256) * elem;
     return fixed + vec;
 }
 

@@ -222,10 +222,10 @@ slr_status host_band_factor(HostSetup& hs, int32_t G) {
             so = std::max(so, a);
             sd = std::max(sd, d);
         }
-        b.SO = (so + 31) / 32 * 32;
-        b.SD = (sd + 31) / 32 * 32;
+        b.SU = (so + 31) / 32 * 32;
+        b.SL = (sd + 31) / 32 * 32;
         b.foff = off;
-        off += (int64_t)b.c * G * (b.SO + b.SD);
+        off += (int64_t)b.c * G * 2 * (b.SU + b.SL);
         hs.wmax = std::max(hs.wmax, b.w);
     }
     hs.band_G = G;
@@ -277,20 +277,24 @@ slr_status host_band_factor(HostSetup& hs, int32_t G) {
                     D[(size_t)r * W + c] = (l >= m) ? (r == c ? 1.0 : 0.0) : (c <= r ? Lat(l, J * W + c) : 0.0);
                 }
             tri_inverse(W, D.data(), X.data());
-            double* plane = &hs.bfac[b.foff + (int64_t)J * G * (b.SO + b.SD)];
+            double* plane = &hs.bfac[b.foff + (int64_t)J * G * 2 * (b.SU + b.SL)];
             for (int g = 0; g < G; ++g) {
-                double* PO = plane + (int64_t)g * (b.SO + b.SD);
-                double* PD = PO + b.SO;
+                double* Uf = plane + (int64_t)g * 2 * (b.SU + b.SL);   // O_J      (upper)
+                double* Lf = Uf + b.SU;                                 // D_J      (lower)
+                double* Lb = Lf + b.SL;                                 // O_J^T    (lower)
+                double* Ub = Lb + b.SL;                                 // D_J^T    (upper)
                 const int nrg = band_slice_rows(W, G, g);
-                int64_t o = 0, d = 0;
+                int64_t u = 0, d = 0;
                 for (int cc = 0; cc < W; ++cc) {
-                    for (int lr = 0; lr < band_cnt_O(cc, G, g); ++lr) {     // O_J[r][cc], r <= cc
+                    for (int lr = 0; lr < band_cnt_O(cc, G, g); ++lr, ++u) {   // rows r <= cc
                         const int r = lr * G + g, l = J * W + r;
-                        PO[o++] = (J > 0 && l < m) ? Lat(l, (J - 1) * W + cc) : 0.0;
+                        Uf[u] = (J > 0 && l < m) ? Lat(l, (J - 1) * W + cc) : 0.0;   // O_J[r][cc]
+                        Ub[u] = X[(size_t)cc * W + r];                                // D_J^{-1}[cc][r]
                     }
-                    for (int lr = std::min(nrg, band_lr0_D(cc, G, g)); lr < nrg; ++lr) {   // D_J^{-1}[r][cc], r >= cc
-                        const int r = lr * G + g;
-                        PD[d++] = X[(size_t)r * W + cc];
+                    for (int lr = std::min(nrg, band_lr0_D(cc, G, g)); lr < nrg; ++lr, ++d) {   // rows r >= cc
+                        const int r = lr * G + g, lc = J * W + cc;
+                        Lf[d] = X[(size_t)r * W + cc];                                // D_J^{-1}[r][cc]
+                        Lb[d] = (J > 0 && lc < m) ? Lat(lc, (J - 1) * W + r) : 0.0;   // O_J[cc][r]
                     }
                 }
             }

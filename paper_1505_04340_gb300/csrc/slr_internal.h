@@ -17,19 +17,22 @@ namespace slr {
 // are grouped in planes of W = clamp(w, 1, m) rows; for plane J
 //   O_J = L_i[plane J, plane J-1]     upper triangular incl. diagonal,
 //   D_J = L_i[plane J, plane J]^{-1}  lower triangular incl. diagonal (inverted).
-// Rows r of a plane are dealt to G slices (r mod G); slice g of each block is
-// packed column-major: column c of O holds the slice's rows r <= c, column q of
-// D its rows r >= q.  A plane occupies G (SO + SD) elements: slice g's O block
-// at g (SO + SD), its D block SO after that.  The last plane is padded with
-// identity rows.  (Layout shared with the band-solve kernel, slr_band.cu.)
+// The forward solve applies O_J (upper) and D_J (lower); the backward solve
+// applies O_J^T (lower) and D_J^T (upper), stored separately so that both
+// passes compute "output row = sum over columns".  Output rows r of a plane are
+// dealt to G slices (r mod G).  A slice of an upper block is packed column-major
+// with column c holding the slice's rows r <= c; a slice of a lower block with
+// column q holding its rows r >= q.  Per plane and slice: [O_J | D_J | O_J^T |
+// D_J^T] = [SU | SL | SL | SU] elements; a plane occupies G * 2 (SU + SL).  The
+// last plane is padded with identity rows.  (Shared with slr_band.cu.)
 struct BandBlock {
     int32_t m = 0;        // rows of B_i
     int32_t w = 0;        // plane width W
     int32_t c = 0;        // planes, c * W >= m
     int32_t row0 = 0;     // first row of B_i inside u (DD interior order)
     int64_t foff = 0;     // offset of plane 0 in the factor array (elements)
-    int32_t SO = 0;       // elements of one O slice block (padded to 32)
-    int32_t SD = 0;       // elements of one D slice block (padded to 32)
+    int32_t SU = 0;       // elements of one upper slice block (padded to 32)
+    int32_t SL = 0;       // elements of one lower slice block (padded to 32)
 };
 
 // Slice geometry of the band layout (host packer and device kernel agree on it).
