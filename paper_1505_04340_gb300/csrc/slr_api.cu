@@ -121,6 +121,12 @@ slr_status upload_operator(slr_handle h, DevOperator<T>& op, bool with_band) {
     CS(upload(h, &d.seg_row, c.seg_row));
     d.lev_ptask_ptr = c.lev_ptask_ptr;
     d.nrow = (int64_t)c.rows.size();
+    d.max_n = 1;
+    for (int32_t J = 0; J < c.ns; ++J) d.max_n = std::max(d.max_n, c.c0[J + 1] - c.c0[J]);
+    if ((size_t)d.max_n * sizeof(T) > 48 * 1024) {
+        set_error("a separator of C has " + std::to_string(d.max_n) + " nodes, beyond the panel kernel's limit");
+        return SLR_ERR_UNSUPPORTED;
+    }
     CS(dalloc(h, &d.tasks, c.tasks.size() / 4));
     if (!c.tasks.empty()) CK(cudaMemcpy(d.tasks, c.tasks.data(), c.tasks.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
     CS(dalloc(h, &d.ptasks, c.ptasks.size() / 4));

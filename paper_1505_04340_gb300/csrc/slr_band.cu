@@ -259,21 +259,60 @@ k_band_solve2(const BandBlock* __restrict__ blocks, const T* __restrict__ fac, c
             src_of(k, type, ixx, e0, e1);
             const int shift = (int)((reinterpret_cast<uintptr_t>(fac + e0) & 15) / sizeof(T));
             const T* P = reinterpret_cast<const T*>(ring + (k % kNBuf) * kChunk) + shift - col[ch[ix]];
-            for (int cc = ch[ix] + warp; cc < ch[ix + 1]; cc += kW) {
-                const int lo = upper ? 0 : min(q.nrg, lr0_D(cc, G, g));
-                const int hi = upper ? cnt_O(cc, G, g) : q.nrg;
-                const T* Pc = P + col[cc] - lo;
-                T v[NR];
-#pragma unroll
-                for (int j = 0; j < NR; ++j) v[j] = vin[j * W + cc];
+            const int ca = ch[ix], cb = ch[ix + 1];
+            if constexpr (sizeof(T) == 8) {
+                // FP64: row block outer.  Row block rb (own rows 32 rb .. 32 rb + 31)
+                // meets column cc of an upper block iff cc >= G (32 rb) + g; a lower
+                // block holds rows >= lr0(cc), so rb meets columns cc <= G (32 rb + 31) + g.
+                // Separate loops per rb keep every DFMA unpredicated (an if-converted
+                // rb loop would issue all kRB of them per column on the slow FP64 pipe);
+                // four interleaved partial sums give each warp independent FMA chains.
 #pragma unroll
                 for (int rb = 0; rb < kRB; ++rb) {
-                    if (rb * 32 + 32 > lo && rb * 32 < hi) {
-                        const int lr = rb * 32 + lane;
-                        if (lr >= lo && lr < hi) {
-                            const T a = Pc[lr];
+                    if (rb * 32 >= q.nrg) break;
+                    const int lr = rb * 32 + lane;
+                    const int c0 = max(ca, upper ? G * (rb * 32) + g : ca);
+                    const int c1 = upper ? cb : min(cb, G * (rb * 32 + 31) + g + 1);
+                    int cc = ca + warp + ((c0 > ca + warp) ? ((c0 - ca - warp + kW - 1) / kW) * kW : 0);
+                    T s0[NR], s1[NR], s2[NR], s3[NR];
 #pragma unroll
-                            for (int j = 0; j < NR; ++j) acc[rb][j] += a * v[j];
+                    for (int j = 0; j < NR; ++j) s0[j] = s1[j] = s2[j] = s3[j] = T(0);
+                    auto term = [&](int c, T* sacc) {
+                        const int lo = upper ? 0 : min(q.nrg, lr0_D(c, G, g));
+                        const int hi = upper ? cnt_O(c, G, g) : q.nrg;
+                        const T a = (lr >= lo && lr < hi) ? P[col[c] - lo + lr] : T(0);
+#pragma unroll
+                        for (int j = 0; j < NR; ++j) sacc[j] = fma(a, vin[j * W + c], sacc[j]);
+                    };
+                    for (; cc + 3 * kW < c1; cc += 4 * kW) {
+                        term(cc, s0);
+                        term(cc + kW, s1);
+                        term(cc + 2 * kW, s2);
+                        term(cc + 3 * kW, s3);
+                    }
+                    for (; cc < c1; cc += kW) term(cc, s0);
+#pragma unroll
+                    for (int j = 0; j < NR; ++j) acc[rb][j] += (s0[j] + s1[j]) + (s2[j] + s3[j]);
+                }
+            } else {
+                // FP32: column outer, row blocks inner (the FP32 pipe absorbs the
+                // predicated-off lanes; this order issues the fewest instructions)
+                for (int cc = ca + warp; cc < cb; cc += kW) {
+                    const int lo = upper ? 0 : min(q.nrg, lr0_D(cc, G, g));
+                    const int hi = upper ? cnt_O(cc, G, g) : q.nrg;
+                    const T* Pc = P + col[cc] - lo;
+                    T v[NR];
+#pragma unroll
+                    for (int j = 0; j < NR; ++j) v[j] = vin[j * W + cc];
+#pragma unroll
+                    for (int rb = 0; rb < kRB; ++rb) {
+                        if (rb * 32 + 32 > lo && rb * 32 < hi) {
+                            const int lr = rb * 32 + lane;
+                            if (lr >= lo && lr < hi) {
+                                const T a = Pc[lr];
+#pragma unroll
+                                for (int j = 0; j < NR; ++j) acc[rb][j] += a * v[j];
+                            }
                         }
                     }
                 }

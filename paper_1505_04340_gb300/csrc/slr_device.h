@@ -25,6 +25,7 @@ struct DevCFactor {
     int64_t* seg_ptr = nullptr;    // [s+1]
     int32_t* seg_row = nullptr;    // panel rows holding each position
     int64_t nrow = 0;              // panel rows in total
+    int32_t max_n = 0;             // widest supernode (shared memory of the forward panel kernel)
     T* wbuf = nullptr;             // [nrow x nrhs_max] panel products of the forward solve
     int4* tasks = nullptr;         // (supernode, first column, count <= 32, 0)
     int4* ptasks = nullptr;        // (supernode, first panel row, count <= 32, 0)

@@ -82,15 +82,19 @@ k_cfwd_gather(const int4* __restrict__ tasks, const int32_t* __restrict__ c0, co
     }
 }
 
-// forward, phase 2: x_J = L_JJ^{-1} t_J for a block of <= 32 rows; 8 warps split
-// the reduction over columns, lane = row
+constexpr int kDiagT = 1024;   // threads of the diagonal-block kernels (32 warps)
+constexpr int kPanT = 512;     // threads of the panel kernels (16 warps)
+
+// forward, phase 2: x_J = L_JJ^{-1} t_J for a block of <= 32 rows; 32 warps
+// split the reduction over columns (lane = row), 8 loads in flight per lane
 template <typename T>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kDiagT)
 k_cfwd_diag(const int4* __restrict__ tasks, const int32_t* __restrict__ c0, const int64_t* __restrict__ dinv_off,
             const T* __restrict__ dinv, const T* tf, T* xf, int32_t s, int32_t nrhs) {
-    __shared__ T red[kThreads / 32][32];
+    constexpr int nw = kDiagT / 32;
+    __shared__ T red[nw][33];
     const int4 tk = tasks[blockIdx.x];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = kThreads / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int32_t a0 = c0[tk.x], nJ = c0[tk.x + 1] - a0;
     const int il = tk.y + lane;
     const int ncol = tk.y + tk.z;                  // columns 0 .. ncol-1 reach these rows
@@ -103,58 +107,73 @@ k_cfwd_diag(const int4* __restrict__ tasks, const int32_t* __restrict__ c0, cons
         if (lane < tk.z) {
             const int jend = min(je, il + 1);
             int jj = jb;
-            for (; jj + 3 < jend; jj += 4) {
-                acc += D[packed_col(jj, nJ) + (il - jj)] * t[jj];
-                acc += D[packed_col(jj + 1, nJ) + (il - jj - 1)] * t[jj + 1];
-                acc += D[packed_col(jj + 2, nJ) + (il - jj - 2)] * t[jj + 2];
-                acc += D[packed_col(jj + 3, nJ) + (il - jj - 3)] * t[jj + 3];
+            for (; jj + 7 < jend; jj += 8) {
+                T d[8], tv[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    d[u] = D[packed_col(jj + u, nJ) + (il - jj - u)];
+                    tv[u] = t[jj + u];
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) acc += d[u] * tv[u];
             }
             for (; jj < jend; ++jj) acc += D[packed_col(jj, nJ) + (il - jj)] * t[jj];
         }
         red[warp][lane] = acc;
         __syncthreads();
-        if (warp == 0 && lane < tk.z) {
+        if (warp == 0) {
             T v = T(0);
-#pragma unroll
+#pragma unroll 8
             for (int w = 0; w < nw; ++w) v += red[w][lane];
-            xf[a0 + il + (int64_t)j * s] = v;
+            if (lane < tk.z) xf[a0 + il + (int64_t)j * s] = v;
         }
         __syncthreads();
     }
 }
 
-// forward, phase 3: w[r_off[J] + p] = L[R_J[p], J] . x_J (warp per panel row, lanes over columns)
+// forward, phase 3: w[r_off[J] + p] = L[R_J[p], J] . x_J (warp per panel row,
+// lanes over columns); x_J staged in shared memory
 template <typename T>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kPanT)
 k_cfwd_panel(const int4* __restrict__ ptasks, const int32_t* __restrict__ c0, const int64_t* __restrict__ r_off,
              const int64_t* __restrict__ pan_off, const T* __restrict__ panel, const T* xf, T* wbuf, int64_t nrow,
              int32_t s, int32_t nrhs) {
+    extern __shared__ unsigned char csm[];
+    T* xs = reinterpret_cast<T*>(csm);
     const int4 tk = ptasks[blockIdx.x];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = kThreads / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = kPanT / 32;
     const int32_t a0 = c0[tk.x], nJ = c0[tk.x + 1] - a0;
-    for (int pr = warp; pr < tk.z; pr += nw) {
-        const int64_t p = tk.y + pr;
-        const T* P = panel + pan_off[tk.x] + p * nJ;
-        for (int j = 0; j < nrhs; ++j) {
-            const T* x = xf + a0 + (int64_t)j * s;
-            T acc = T(0);
-            for (int c = lane; c < nJ; c += 32) acc += P[c] * x[c];
-            acc = warp_sum(acc);
+    for (int j = 0; j < nrhs; ++j) {
+        for (int c = threadIdx.x; c < nJ; c += kPanT) xs[c] = xf[a0 + c + (int64_t)j * s];
+        __syncthreads();
+        for (int pr = warp; pr < tk.z; pr += nw) {
+            const int64_t p = tk.y + pr;
+            const T* P = panel + pan_off[tk.x] + p * nJ;
+            T acc0 = T(0), acc1 = T(0);
+            int c = lane;
+            for (; c + 32 < nJ; c += 64) {
+                acc0 += P[c] * xs[c];
+                acc1 += P[c + 32] * xs[c + 32];
+            }
+            if (c < nJ) acc0 += P[c] * xs[c];
+            const T acc = warp_sum(acc0 + acc1);
             if (lane == 0) wbuf[r_off[tk.x] + p + (int64_t)j * nrow] = acc;
         }
+        __syncthreads();
     }
 }
 
 // backward, phase 1: t_j = y_j - sum_p L[R_J[p], j] x[R_J[p]] for <= 32 columns
-// (lane = column); 8 warps split the panel rows
+// (lane = column); 16 warps split the panel rows, 8 loads in flight per lane
 template <typename T>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kPanT)
 k_cbwd_panel(const int4* __restrict__ tasks, const int32_t* __restrict__ c0, const int64_t* __restrict__ r_off,
              const int32_t* __restrict__ rows, const int64_t* __restrict__ pan_off, const T* __restrict__ panel,
              T* yf, const T* xf, int32_t s, int32_t nrhs) {
-    __shared__ T red[kThreads / 32][32];
+    constexpr int nw = kPanT / 32;
+    __shared__ T red[nw][33];
     const int4 tk = tasks[blockIdx.x];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = kThreads / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int32_t a0 = c0[tk.x], nJ = c0[tk.x + 1] - a0, jl = tk.y + lane;
     const int64_t nr = r_off[tk.x + 1] - r_off[tk.x];
     const int32_t* R = rows + r_off[tk.x];
@@ -165,11 +184,15 @@ k_cbwd_panel(const int4* __restrict__ tasks, const int32_t* __restrict__ c0, con
         T acc = T(0);
         if (lane < tk.z) {
             int64_t p = pb;
-            for (; p + 3 < pe; p += 4) {
-                acc += Pn[p * nJ] * x[R[p]];
-                acc += Pn[(p + 1) * nJ] * x[R[p + 1]];
-                acc += Pn[(p + 2) * nJ] * x[R[p + 2]];
-                acc += Pn[(p + 3) * nJ] * x[R[p + 3]];
+            for (; p + 7 < pe; p += 8) {
+                T pv[8], xv[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    pv[u] = Pn[(p + u) * nJ];
+                    xv[u] = x[R[p + u]];
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) acc += pv[u] * xv[u];
             }
             for (; p < pe; ++p) acc += Pn[p * nJ] * x[R[p]];
         }
@@ -185,10 +208,10 @@ k_cbwd_panel(const int4* __restrict__ tasks, const int32_t* __restrict__ c0, con
     }
 }
 
-// backward, phase 2: x_J = L_JJ^{-T} t_J (warp per column, lanes over the column),
-// optional scatter to DD order
+// backward, phase 2: x_J = L_JJ^{-T} t_J (warp per column, lanes over the column,
+// 8 loads in flight per lane), optional scatter to DD order
 template <typename T>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kDiagT)
 k_cbwd_diag(const int4* __restrict__ tasks, const int32_t* __restrict__ c0, const int64_t* __restrict__ dinv_off,
             const T* __restrict__ dinv, const int32_t* __restrict__ cperm, const T* tf, T* xf, T* y_dd,
             int64_t ldy, int32_t s, int32_t nrhs) {
@@ -202,7 +225,18 @@ k_cbwd_diag(const int4* __restrict__ tasks, const int32_t* __restrict__ c0, cons
         for (int j = 0; j < nrhs; ++j) {
             const T* t = tf + a0 + (int64_t)j * s;
             T acc = T(0);
-            for (int i = jl + lane; i < nJ; i += 32) acc += Dc[i] * t[i];
+            int i = jl + lane;
+            for (; i + 7 * 32 < nJ; i += 8 * 32) {
+                T d[8], tv[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    d[u] = Dc[i + 32 * u];
+                    tv[u] = t[i + 32 * u];
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) acc += d[u] * tv[u];
+            }
+            for (; i < nJ; i += 32) acc += Dc[i] * t[i];
             acc = warp_sum(acc);
             if (lane == 0) {
                 xf[a0 + jl + (int64_t)j * s] = acc;
@@ -431,12 +465,12 @@ cudaError_t launch_c_forward(const DevCFactor<T>& cf, const T* g_dd, int64_t ldg
             k_cfwd_gather<T><<<nt, 32, 0, st>>>(cf.tasks + t0, cf.c0, cf.cperm, cf.seg_ptr, cf.seg_row, cf.wbuf,
                                                 cf.nrow, g_dd, ldg, tf, cf.s, nrhs);
             counted();
-            k_cfwd_diag<T><<<nt, kThreads, 0, st>>>(cf.tasks + t0, cf.c0, cf.dinv_off, cf.dinv, tf, xf, cf.s, nrhs);
+            k_cfwd_diag<T><<<nt, kDiagT, 0, st>>>(cf.tasks + t0, cf.c0, cf.dinv_off, cf.dinv, tf, xf, cf.s, nrhs);
             counted();
         }
         if (np > 0) {
-            k_cfwd_panel<T><<<np, kThreads, 0, st>>>(cf.ptasks + p0, cf.c0, cf.r_off, cf.pan_off, cf.panel, xf,
-                                                     cf.wbuf, cf.nrow, cf.s, nrhs);
+            k_cfwd_panel<T><<<np, kPanT, cf.max_n * sizeof(T), st>>>(cf.ptasks + p0, cf.c0, cf.r_off, cf.pan_off,
+                                                                      cf.panel, xf, cf.wbuf, cf.nrow, cf.s, nrhs);
             counted();
         }
     }
@@ -449,11 +483,11 @@ cudaError_t launch_c_backward(const DevCFactor<T>& cf, T* yf, T* xf, T* y_dd, in
     for (int l = cf.nlev - 1; l >= 0; --l) {
         const int t0 = cf.lev_task_ptr[l], nt = cf.lev_task_ptr[l + 1] - t0;
         if (nt == 0) continue;
-        k_cbwd_panel<T><<<nt, kThreads, 0, st>>>(cf.tasks + t0, cf.c0, cf.r_off, cf.rows, cf.pan_off, cf.panel,
-                                                 yf, xf, cf.s, nrhs);
+        k_cbwd_panel<T><<<nt, kPanT, 0, st>>>(cf.tasks + t0, cf.c0, cf.r_off, cf.rows, cf.pan_off, cf.panel,
+                                              yf, xf, cf.s, nrhs);
         counted();
-        k_cbwd_diag<T><<<nt, kThreads, 0, st>>>(cf.tasks + t0, cf.c0, cf.dinv_off, cf.dinv, cf.cperm, yf, xf,
-                                                y_dd, ldy, cf.s, nrhs);
+        k_cbwd_diag<T><<<nt, kDiagT, 0, st>>>(cf.tasks + t0, cf.c0, cf.dinv_off, cf.dinv, cf.cperm, yf, xf,
+                                              y_dd, ldy, cf.s, nrhs);
         counted();
     }
     return cudaGetLastError();
