@@ -361,7 +361,9 @@ slr_status setup_impl(slr_handle h, int32_t n, const int32_t* rowptr, const int3
         const int32_t req = h->opts.reserved[0];        // opts.band_split, 0 = automatic
         if (req == 1 || req == 2 || req == 4) {
             if ((wmx + req - 1) / req <= 256) G = req;
-        } else if (G == 1 && 2 * nparts <= nsm && wmx >= 32) {
+        } else if (G == 1 && 2 * nparts <= nsm && wmx >= 32 && h->opts.precision == SLR_PREC_FP64) {
+            // the FP64 solve is bound by the SMs' FP64 units: use twice the SMs.
+            // The FP32 solve streams fast enough from one SM per subdomain.
             G = 2;
         }
         CS(host_band_factor(hs, G));

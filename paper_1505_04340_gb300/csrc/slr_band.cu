@@ -35,7 +35,7 @@ extern std::atomic<int64_t> g_kernel_launches;
 
 namespace {
 
-constexpr int kT = 256;            // threads per CTA
+constexpr int kT = 512;            // threads per CTA (4 warps per SM sub-partition hide the load->FMA latency)
 constexpr int kW = kT / 32;        // warps per CTA
 constexpr int kNBuf = 3;           // ring slots
 constexpr int kChunk = 48 * 1024;  // bytes per ring slot
@@ -265,8 +265,8 @@ k_band_solve2(const BandBlock* __restrict__ blocks, const T* __restrict__ fac, c
                 // meets column cc of an upper block iff cc >= G (32 rb) + g; a lower
                 // block holds rows >= lr0(cc), so rb meets columns cc <= G (32 rb + 31) + g.
                 // Separate loops per rb keep every DFMA unpredicated (an if-converted
-                // rb loop would issue all kRB of them per column on the slow FP64 pipe);
-                // four interleaved partial sums give each warp independent FMA chains.
+                // rb loop would issue all kRB of them per column on the slow FP64 pipe,
+                // which serves each SM sub-partition at a fixed rate).
 #pragma unroll
                 for (int rb = 0; rb < kRB; ++rb) {
                     if (rb * 32 >= q.nrg) break;
@@ -274,25 +274,18 @@ k_band_solve2(const BandBlock* __restrict__ blocks, const T* __restrict__ fac, c
                     const int c0 = max(ca, upper ? G * (rb * 32) + g : ca);
                     const int c1 = upper ? cb : min(cb, G * (rb * 32 + 31) + g + 1);
                     int cc = ca + warp + ((c0 > ca + warp) ? ((c0 - ca - warp + kW - 1) / kW) * kW : 0);
-                    T s0[NR], s1[NR], s2[NR], s3[NR];
-#pragma unroll
-                    for (int j = 0; j < NR; ++j) s0[j] = s1[j] = s2[j] = s3[j] = T(0);
-                    auto term = [&](int c, T* sacc) {
+                    auto term = [&](int c) {
                         const int lo = upper ? 0 : min(q.nrg, lr0_D(c, G, g));
                         const int hi = upper ? cnt_O(c, G, g) : q.nrg;
                         const T a = (lr >= lo && lr < hi) ? P[col[c] - lo + lr] : T(0);
 #pragma unroll
-                        for (int j = 0; j < NR; ++j) sacc[j] = fma(a, vin[j * W + c], sacc[j]);
+                        for (int j = 0; j < NR; ++j) acc[rb][j] = fma(a, vin[j * W + c], acc[rb][j]);
                     };
-                    for (; cc + 3 * kW < c1; cc += 4 * kW) {
-                        term(cc, s0);
-                        term(cc + kW, s1);
-                        term(cc + 2 * kW, s2);
-                        term(cc + 3 * kW, s3);
+                    for (; cc + kW < c1; cc += 2 * kW) {
+                        term(cc);
+                        term(cc + kW);
                     }
-                    for (; cc < c1; cc += kW) term(cc, s0);
-#pragma unroll
-                    for (int j = 0; j < NR; ++j) acc[rb][j] += (s0[j] + s1[j]) + (s2[j] + s3[j]);
+                    if (cc < c1) term(cc);
                 }
             } else {
                 // FP32: column outer, row blocks inner (the FP32 pipe absorbs the
