@@ -72,7 +72,9 @@ typedef struct {
     int32_t c_leaf;         /* nested-dissection leaf size for C's ordering; 0 => 64     */
     int32_t verbose;        /* 1: setup prints timings to stderr                          */
     int32_t reserved[6];    /* reserved[0]: CTAs per subdomain in the band solve (1, 2, 4;
-                               0 = automatic); the rest must be 0                       */
+                               0 = automatic).  reserved[1]: 1 = drive the CG loop from
+                               the host (one synchronisation per iteration) instead of
+                               one CUDA graph per solve.  The rest must be 0.            */
 } slr_opts;
 
 typedef struct {
@@ -113,6 +115,9 @@ slr_status slr_apply(slr_handle h, const double* r_dev, double* z_dev, int32_t n
 
 /* Solve A x = b with SLR-preconditioned CG (Section 6): x_0 = 0, stop column j
  * when ||r_j|| <= tol ||b_j|| (recurrence residual) or after maxit iterations.
+ * The iteration loop runs as one CUDA graph with a device-side WHILE node (built
+ * and cached per nrhs on first use, so the first call of each nrhs captures it;
+ * make that call outside any stream capture of your own).
  * b_dev, x_dev: n x nrhs FP64 in ORIGINAL order, leading dimension ld.  Columns
  * are independent CG runs advanced together.  iters_out[nrhs], relres_out[nrhs]:
  * host arrays (may be NULL).  Synchronises stream.  Returns NOT_CONVERGED if a

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -15,6 +16,10 @@
 #include "slr_device.h"
 
 using namespace slr;
+
+namespace slr {
+extern std::atomic<int64_t> g_kernel_launches;
+}
 
 namespace {
 
@@ -431,6 +436,121 @@ slr_status check_handle(slr_handle h) {
     return SLR_OK;
 }
 
+
+// One CG iteration is split in two parts (Section 6, preconditioned CG):
+//   update (every iteration after the first): z = M^{-1} r, rho' = r.z, beta, p = z + beta p
+//   test:   q = A p, alpha = rho / p.q, x += alpha p, r -= alpha q, r.r, convergence
+slr_status pcg_update_part(slr_handle h, int32_t nrhs, cudaStream_t st) {
+    const int64_t nn = h->hs.n;
+    if (h->opts.flexible_cg)
+        CK(cudaMemcpyAsync(h->pzold, h->pz, sizeof(double) * nn * nrhs, cudaMemcpyDeviceToDevice, st));
+    CS(apply_any(h, h->pr, nn, h->pz, nn, nrhs, st));
+    CK(launch_dots(nn, nrhs, h->pr, nn, h->pz, nn, h->dpart, h->scal + 6, 8, st));        // rho_new
+    if (h->opts.flexible_cg) CK(launch_dots(nn, nrhs, h->pr, nn, h->pzold, nn, h->dpart, h->scal + 7, 8, st));
+    CK(launch_pcg_beta(nrhs, h->scal, h->iflags, h->opts.flexible_cg, st));
+    CK(launch_pcg_update_p(h->hs.n, nrhs, h->pp, h->pz, h->scal, h->iflags, st));
+    return SLR_OK;
+}
+
+slr_status pcg_test_part(slr_handle h, int32_t nrhs, cudaStream_t st) {
+    const int64_t nn = h->hs.n;
+    CK(launch_csr_spmv(h->hs.n, h->a_rp, h->a_ci, h->a_v, h->pp, nn, h->pq, nn, nrhs, st));   // q = A p
+    CK(launch_dots(nn, nrhs, h->pp, nn, h->pq, nn, h->dpart, h->scal + 1, 8, st));           // p.q
+    CK(launch_pcg_alpha(nrhs, h->scal, h->iflags, st));
+    CK(launch_pcg_update_xr(h->hs.n, nrhs, h->px, h->pr, h->pp, h->pq, h->scal, h->iflags, st));
+    CK(launch_dots(nn, nrhs, h->pr, nn, h->pr, nn, h->dpart, h->scal + 3, 8, st));           // r.r
+    return SLR_OK;
+}
+
+// Host-driven loop: one stream synchronisation per iteration (kept for comparison).
+slr_status pcg_host_loop(slr_handle h, int32_t nrhs, double tol, int32_t maxit, cudaStream_t st) {
+    int32_t active = 1;
+    for (int32_t it = 1; it <= maxit; ++it) {
+        if (it > 1) CS(pcg_update_part(h, nrhs, st));
+        CS(pcg_test_part(h, nrhs, st));
+        CK(launch_pcg_check(nrhs, h->scal, h->iflags, it, tol, st));
+        CK(cudaMemcpyAsync(&active, h->iflags + 4 * nrhs, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (active == 0) break;
+    }
+    return SLR_OK;
+}
+
+// The whole CG loop as one CUDA graph: WHILE(active and it < maxit) { IF(it > 0) update; test }.
+// The test part's last kernel sets both conditions on the device.
+slr_status pcg_graph(slr_handle h, int32_t nrhs, slr_handle_s::PcgGraph** out) {
+    for (auto& gr : h->pcg_graphs)
+        if (gr.nrhs == nrhs) { *out = &gr; return SLR_OK; }
+    if (!h->ctl) CS(dalloc(h, &h->ctl, 2));
+    cudaStream_t cs = nullptr;
+    CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    struct StreamGuard {
+        cudaStream_t s;
+        ~StreamGuard() { if (s) cudaStreamDestroy(s); }
+    } sg{cs};
+    cudaGraph_t graph = nullptr;
+    CK(cudaGraphCreate(&graph, 0));
+    struct GraphGuard {
+        cudaGraph_t g;
+        ~GraphGuard() { if (g) cudaGraphDestroy(g); }
+    } gg{graph};
+    cudaGraphConditionalHandle hw, hi;
+    CK(cudaGraphConditionalHandleCreate(&hw, graph, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams wp = {};
+    wp.type = cudaGraphNodeTypeConditional;
+    wp.conditional.handle = hw;
+    wp.conditional.type = cudaGraphCondTypeWhile;
+    wp.conditional.size = 1;
+    cudaGraphNode_t wnode;
+    CK(cudaGraphAddNode(&wnode, graph, nullptr, nullptr, 0, &wp));
+    cudaGraph_t body = wp.conditional.phGraph_out[0];
+    CK(cudaGraphConditionalHandleCreate(&hi, body, 0, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams ip = {};
+    ip.type = cudaGraphNodeTypeConditional;
+    ip.conditional.handle = hi;
+    ip.conditional.type = cudaGraphCondTypeIf;
+    ip.conditional.size = 1;
+    cudaGraphNode_t inode;
+    CK(cudaGraphAddNode(&inode, body, nullptr, nullptr, 0, &ip));
+    cudaGraph_t ibody = ip.conditional.phGraph_out[0];
+    slr_handle_s::PcgGraph gr;
+    gr.nrhs = nrhs;
+    const int64_t l0 = g_kernel_launches.load();
+    CK(cudaStreamBeginCaptureToGraph(cs, ibody, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    slr_status s1 = pcg_update_part(h, nrhs, cs);
+    cudaGraph_t tmp = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(cs, &tmp);
+    if (s1 != SLR_OK) return s1;
+    CK(ce);
+    const int64_t l1 = g_kernel_launches.load();
+    CK(cudaStreamBeginCaptureToGraph(cs, body, &inode, nullptr, 1, cudaStreamCaptureModeRelaxed));
+    s1 = pcg_test_part(h, nrhs, cs);
+    if (s1 == SLR_OK) {
+        cudaError_t e2 = launch_pcg_check_graph(nrhs, h->scal, h->iflags, h->ctl, hw, hi, cs);
+        if (e2 != cudaSuccess) {
+            set_error(std::string("pcg check launch: ") + cudaGetErrorString(e2));
+            s1 = SLR_ERR_CUDA;
+        }
+    }
+    ce = cudaStreamEndCapture(cs, &tmp);
+    if (s1 != SLR_OK) return s1;
+    CK(ce);
+    const int64_t l2 = g_kernel_launches.load();
+    gr.kB = l1 - l0;
+    gr.kA = l2 - l1;
+    g_kernel_launches.fetch_sub(l2 - l0);     // captured, not run
+    CK(cudaGraphInstantiate(&gr.exec, graph, 0));
+    h->pcg_graphs.push_back(gr);
+    *out = &h->pcg_graphs.back();
+    return SLR_OK;
+}
+
+void drop_graphs(slr_handle h) {
+    for (auto& gr : h->pcg_graphs)
+        if (gr.exec) cudaGraphExecDestroy(gr.exec);
+    h->pcg_graphs.clear();
+}
+
 }  // namespace
 
 extern "C" {
@@ -540,50 +660,31 @@ slr_status slr_pcg_solve(slr_handle h, const double* b, double* x, int32_t nrhs,
     DeviceGuard g(h->device);
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t nn = n;
-    double *X = h->px, *R = h->pr, *Z = h->pz, *P = h->pp, *Q = h->pq;
-    CK(launch_permute(n, nrhs, h->perm, b, ld, R, nn, true, st));                  // r = P b (DD order)
-    CK(cudaMemsetAsync(X, 0, sizeof(double) * nn * nrhs, st));
-    CK(launch_dots(nn, nrhs, R, nn, R, nn, h->dpart, h->scal + 4, 8, st));        // b.b
-    // flags: active = 1 unless b = 0 (then converged in 0 iterations)
-    {
-        std::vector<double> sc(8 * nrhs);
-        CK(cudaMemcpyAsync(sc.data(), h->scal, sizeof(double) * 8 * nrhs, cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        std::vector<int32_t> fl(4 * nrhs + 4, 0);
-        int32_t act = 0;
-        for (int j = 0; j < nrhs; ++j) {
-            bool zero = !(sc[8 * j + 4] > 0.0);
-            fl[4 * j] = zero ? 0 : 1;
-            fl[4 * j + 2] = zero ? 1 : 0;
-            act += !zero;
+    // start: r = P b (DD order), x = 0, b.b, flags, z = M^{-1} r, rho = r.z, p = z
+    CK(launch_permute(n, nrhs, h->perm, b, ld, h->pr, nn, true, st));
+    CK(cudaMemsetAsync(h->px, 0, sizeof(double) * nn * nrhs, st));
+    CK(launch_dots(nn, nrhs, h->pr, nn, h->pr, nn, h->dpart, h->scal + 4, 8, st));
+    CK(launch_pcg_init(nrhs, h->scal, h->iflags, st));
+    CS(apply_any(h, h->pr, nn, h->pz, nn, nrhs, st));
+    CK(launch_dots(nn, nrhs, h->pr, nn, h->pz, nn, h->dpart, h->scal + 0, 8, st));
+    CK(cudaMemcpyAsync(h->pp, h->pz, sizeof(double) * nn * nrhs, cudaMemcpyDeviceToDevice, st));
+    if (maxit > 0) {
+        if (h->opts.reserved[1] == 1) {
+            CS(pcg_host_loop(h, nrhs, tol, maxit, st));
+        } else {
+            slr_handle_s::PcgGraph* gr = nullptr;
+            CS(pcg_graph(h, nrhs, &gr));
+            const double ctl[2] = {tol * tol, (double)maxit};
+            CK(cudaMemcpyAsync(h->ctl, ctl, sizeof(ctl), cudaMemcpyHostToDevice, st));
+            CK(cudaGraphLaunch(gr->exec, st));
+            int32_t its = 0;
+            CK(cudaMemcpyAsync(&its, h->iflags + 4 * nrhs + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            // kernels the graph ran: the test part every iteration, the update part from the second on
+            g_kernel_launches.fetch_add(its * gr->kA + std::max(0, its - 1) * gr->kB);
         }
-        fl[4 * nrhs] = act;
-        CK(cudaMemcpyAsync(h->iflags, fl.data(), sizeof(int32_t) * fl.size(), cudaMemcpyHostToDevice, st));
-        CK(cudaStreamSynchronize(st));
     }
-    CS(apply_any(h, R, nn, Z, nn, nrhs, st));                                        // z = M^{-1} r
-    CK(launch_dots(nn, nrhs, R, nn, Z, nn, h->dpart, h->scal + 0, 8, st));         // rho = r.z
-    CK(cudaMemcpyAsync(P, Z, sizeof(double) * nn * nrhs, cudaMemcpyDeviceToDevice, st));
-    int32_t active = 1;
-    for (int32_t it = 1; it <= maxit; ++it) {
-        CK(launch_csr_spmv(n, h->a_rp, h->a_ci, h->a_v, P, nn, Q, nn, nrhs, st));  // q = A p
-        CK(launch_dots(nn, nrhs, P, nn, Q, nn, h->dpart, h->scal + 1, 8, st));     // p.q
-        CK(launch_pcg_alpha(nrhs, h->scal, h->iflags, st));
-        CK(launch_pcg_update_xr(n, nrhs, X, R, P, Q, h->scal, h->iflags, st));
-        CK(launch_dots(nn, nrhs, R, nn, R, nn, h->dpart, h->scal + 3, 8, st));     // r.r
-        CK(launch_pcg_check(nrhs, h->scal, h->iflags, it, tol, st));
-        CK(cudaMemcpyAsync(&active, h->iflags + 4 * nrhs, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        if (active == 0) break;
-        if (h->opts.flexible_cg)
-            CK(cudaMemcpyAsync(h->pzold, Z, sizeof(double) * nn * nrhs, cudaMemcpyDeviceToDevice, st));
-        CS(apply_any(h, R, nn, Z, nn, nrhs, st));
-        CK(launch_dots(nn, nrhs, R, nn, Z, nn, h->dpart, h->scal + 6, 8, st));     // rho_new
-        if (h->opts.flexible_cg) CK(launch_dots(nn, nrhs, R, nn, h->pzold, nn, h->dpart, h->scal + 7, 8, st));
-        CK(launch_pcg_beta(nrhs, h->scal, h->iflags, h->opts.flexible_cg, st));
-        CK(launch_pcg_update_p(n, nrhs, P, Z, h->scal, h->iflags, st));
-    }
-    CK(launch_permute(n, nrhs, h->perm, X, nn, x, ld, false, st));                 // x = P^T x_dd
+    CK(launch_permute(n, nrhs, h->perm, h->px, nn, x, ld, false, st));                 // x = P^T x_dd
     std::vector<double> sc(8 * nrhs);
     std::vector<int32_t> fl(4 * nrhs + 4);
     CK(cudaMemcpyAsync(sc.data(), h->scal, sizeof(double) * 8 * nrhs, cudaMemcpyDeviceToHost, st));
@@ -642,6 +743,7 @@ slr_status slr_set_lowrank(slr_handle h, int32_t k, const double* Z, const doubl
     }
     std::vector<double> lv(lam, lam + k);
     const int32_t k_old = h->k;
+    drop_graphs(h);
     CS(set_operator_lowrank<double>(h, h->op64, U, k_old, k, lv, theta));
     if (h->opts.precision == SLR_PREC_MIXED) CS(set_operator_lowrank<float>(h, h->op32, U, k_old, k, lv, theta));
     h->k = k;
@@ -733,6 +835,7 @@ void slr_destroy(slr_handle h) {
     int old = -1;
     cudaGetDevice(&old);
     if (old != h->device) cudaSetDevice(h->device);
+    drop_graphs(h);
     for (void* p : h->allocs) cudaFree(p);
     if (old >= 0 && old != h->device) cudaSetDevice(old);
     delete h;

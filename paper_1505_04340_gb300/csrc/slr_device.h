@@ -74,6 +74,13 @@ struct slr_handle_s {
     double *scal = nullptr;          // per-column scalars, see slr_api.cu
     double *dpart = nullptr;         // reduction partials
     int32_t *iflags = nullptr;       // per-column status words
+    double* ctl = nullptr;           // PCG graph controls: tol^2, maxit
+    struct PcgGraph {
+        int32_t nrhs = 0;
+        cudaGraphExec_t exec = nullptr;
+        int64_t kA = 0, kB = 0;      // kernels per iteration: test part, update part
+    };
+    std::vector<PcgGraph> pcg_graphs;   // one per right-hand-side count, built on first use
     std::vector<void*> allocs;       // every device allocation, freed by slr_destroy
     int64_t device_bytes = 0;
     double setup_seconds[5] = {0, 0, 0, 0, 0};
@@ -143,6 +150,10 @@ cudaError_t launch_pcg_check(int32_t nrhs, double* scal, int32_t* flags, int32_t
                              cudaStream_t st);
 cudaError_t launch_pcg_beta(int32_t nrhs, double* scal, int32_t* flags, int32_t flexible,
                             cudaStream_t st);
+cudaError_t launch_pcg_init(int32_t nrhs, const double* scal, int32_t* flags, cudaStream_t st);
+cudaError_t launch_pcg_check_graph(int32_t nrhs, const double* scal, int32_t* flags, const double* ctl,
+                                   cudaGraphConditionalHandle hw, cudaGraphConditionalHandle hi,
+                                   cudaStream_t st);
 cudaError_t launch_pcg_update_p(int32_t n, int32_t nrhs, double* p, const double* z, const double* scal,
                                 const int32_t* flags, cudaStream_t st);
 

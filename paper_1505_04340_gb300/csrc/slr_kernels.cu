@@ -408,6 +408,46 @@ __global__ void k_pcg_check(int32_t nrhs, double* scal, int32_t* flags, int32_t 
     flags[4 * nrhs] = active;
 }
 
+// PCG start: a column is active unless its right-hand side is zero; iteration counter 0
+__global__ void k_pcg_init(int32_t nrhs, const double* scal, int32_t* flags) {
+    if (threadIdx.x != 0) return;
+    int32_t act = 0;
+    for (int j = 0; j < nrhs; ++j) {
+        const bool zero = !(scal[8 * j + 4] > 0.0);
+        flags[4 * j] = zero ? 0 : 1;
+        flags[4 * j + 1] = 0;
+        flags[4 * j + 2] = zero ? 1 : 0;
+        flags[4 * j + 3] = 0;
+        act += !zero;
+    }
+    flags[4 * nrhs] = act;
+    flags[4 * nrhs + 1] = 0;
+}
+
+// Convergence test inside the PCG graph: ctl = [tol^2, maxit].  Sets the WHILE
+// condition (another iteration is needed) and the IF condition that runs the
+// preconditioner update at the top of every iteration after the first.
+__global__ void k_pcg_check_graph(int32_t nrhs, const double* scal, int32_t* flags, const double* ctl,
+                                  cudaGraphConditionalHandle h_while, cudaGraphConditionalHandle h_if) {
+    if (threadIdx.x != 0) return;
+    const int32_t it = ++flags[4 * nrhs + 1];
+    int32_t active = 0;
+    for (int j = 0; j < nrhs; ++j) {
+        if (!flags[4 * j]) continue;
+        const double* sc = scal + 8 * j;
+        flags[4 * j + 1] = it;
+        if (sc[3] <= ctl[0] * sc[4]) {
+            flags[4 * j] = 0;
+            flags[4 * j + 2] = 1;
+        } else {
+            ++active;
+        }
+    }
+    flags[4 * nrhs] = active;
+    cudaGraphSetConditional(h_while, (active > 0 && it < (int32_t)ctl[1]) ? 1u : 0u);
+    cudaGraphSetConditional(h_if, 1u);
+}
+
 __global__ void k_pcg_beta(int32_t nrhs, double* scal, const int32_t* flags, int32_t flexible) {
     const int j = threadIdx.x;
     if (j >= nrhs || !flags[4 * j]) return;
@@ -583,6 +623,17 @@ cudaError_t launch_pcg_update_xr(int32_t n, int32_t nrhs, double* x, double* r, 
 }
 cudaError_t launch_pcg_check(int32_t nrhs, double* scal, int32_t* flags, int32_t it, double tol, cudaStream_t st) {
     k_pcg_check<<<1, 32, 0, st>>>(nrhs, scal, flags, it, tol);
+    counted();
+    return cudaGetLastError();
+}
+cudaError_t launch_pcg_init(int32_t nrhs, const double* scal, int32_t* flags, cudaStream_t st) {
+    k_pcg_init<<<1, 32, 0, st>>>(nrhs, scal, flags);
+    counted();
+    return cudaGetLastError();
+}
+cudaError_t launch_pcg_check_graph(int32_t nrhs, const double* scal, int32_t* flags, const double* ctl,
+                                   cudaGraphConditionalHandle hw, cudaGraphConditionalHandle hi, cudaStream_t st) {
+    k_pcg_check_graph<<<1, 32, 0, st>>>(nrhs, scal, flags, ctl, hw, hi);
     counted();
     return cudaGetLastError();
 }

@@ -223,6 +223,20 @@ def test_mixed_pcg_reaches_1e8(name, flexible):
         assert diff <= 1e-7
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_graph_loop_equals_host_loop(precision):
+    """The CUDA-graph CG loop runs the same kernels in the same order as the host loop."""
+    P = make("3d-lap", nrhs=3)
+    a = gpu_handle(P, precision, flexible_cg=(precision == "mixed"))
+    b = gpu_handle(P, precision, flexible_cg=(precision == "mixed"), host_loop=True)
+    xa, ia, ra, sa = a.pcg(cu(P.b))
+    xb, ib, rb, sb = b.pcg(cu(P.b))
+    assert sa == sb == 0 and np.array_equal(ia, ib)
+    assert torch.equal(xa, xb) and np.array_equal(ra, rb)
+    xa2, ia2, _, _ = a.pcg(cu(P.b))                 # cached graph, second launch
+    assert torch.equal(xa, xa2) and np.array_equal(ia, ia2)
+
+
 def test_pcg_rhs_zero_and_maxit():
     P = make("c1-lap32")
     g = gpu_handle(P)
