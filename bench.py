@@ -195,7 +195,8 @@ def run_profile(args):
     P, _ = build_problem(args.problem)
     b = torch.tensor(P.b[:, 0], device="cuda")
     h = SLR(P.rowptr, P.colind, P.val, P.part, P.nparts, k=P.k, lanczos_steps=P.lanczos_steps,
-            precision=args.precision, nrhs_max=1, flexible_cg=(args.precision == "mixed"))
+            precision=args.precision, nrhs_max=1, flexible_cg=(args.precision == "mixed"),
+            host_loop=args.host_loop)
     info = h.get_info()
     f = torch.randn(info["n_interior"], dtype=torch.float64, device="cuda")
     g = torch.randn(info["s"], dtype=torch.float64, device="cuda")
@@ -403,6 +404,8 @@ def main():
     ap.add_argument("--profile", action="store_true", help="solves inside an NVTX range only (for ncu)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--profile-kernel", default="pcg", choices=["pcg", "bsolve", "csolve", "apply"])
+    ap.add_argument("--host-loop", action="store_true",
+                    help="drive CG from the host (profilers do not see kernels inside conditional graph nodes)")
     args = ap.parse_args()
     if args.profile:
         run_profile(args)

@@ -125,6 +125,9 @@ slr_status upload_operator(slr_handle h, DevOperator<T>& op, bool with_band) {
     CS(upload(h, &d.seg_ptr, c.seg_ptr));
     CS(upload(h, &d.seg_row, c.seg_row));
     d.lev_ptask_ptr = c.lev_ptask_ptr;
+    d.lev_sn_ptr = c.lev_sn_ptr;
+    d.lev_small = c.lev_small;
+    CS(upload(h, &d.lev_sn, c.lev_sn));
     d.nrow = (int64_t)c.rows.size();
     d.max_n = 1;
     for (int32_t J = 0; J < c.ns; ++J) d.max_n = std::max(d.max_n, c.c0[J + 1] - c.c0[J]);

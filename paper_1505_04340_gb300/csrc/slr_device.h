@@ -31,6 +31,9 @@ struct DevCFactor {
     int4* ptasks = nullptr;        // (supernode, first panel row, count <= 32, 0)
     std::vector<int32_t> lev_task_ptr;    // host copies, [nlev+1]
     std::vector<int32_t> lev_ptask_ptr;
+    std::vector<int32_t> lev_sn_ptr;
+    std::vector<uint8_t> lev_small;
+    int32_t* lev_sn = nullptr;            // device: supernodes level by level
 };
 
 // Everything one apply needs in precision T (double: FP64 path; float: mixed).

@@ -425,6 +425,7 @@ slr_status host_c_factor(HostSetup& hs, int32_t leaf, int32_t task_rows) {
         cf.seg_ptr.assign(1, 0);
         cf.lev_task_ptr.assign(1, 0);
         cf.lev_ptask_ptr.assign(1, 0);
+        cf.lev_sn_ptr.assign(1, 0);
         return SLR_OK;
     }
     // graph of C without its diagonal
@@ -623,6 +624,21 @@ slr_status host_c_factor(HostSetup& hs, int32_t leaf, int32_t task_rows) {
         }
         cf.lev_task_ptr[l + 1] = (int32_t)(cf.tasks.size() / 4);
         cf.lev_ptask_ptr[l + 1] = (int32_t)(cf.ptasks.size() / 4);
+    }
+    cf.lev_sn_ptr.assign(cf.nlev + 1, 0);
+    cf.lev_sn.clear();
+    // One CTA per supernode pays off only when a level has at least a wave of
+    // supernodes and each one's panel is small; otherwise the split kernels
+    // spread a supernode's rows over many CTAs.
+    cf.lev_small.assign(cf.nlev, 1);
+    for (int32_t l = 0; l < cf.nlev; ++l) {
+        if ((int32_t)bylev[l].size() < kSmallMinCount) cf.lev_small[l] = 0;
+        for (int32_t J : bylev[l]) {
+            cf.lev_sn.push_back(J);
+            const int64_t nJ = cf.c0[J + 1] - cf.c0[J], nr = cf.r_off[J + 1] - cf.r_off[J];
+            if (nJ > kSmallN || nr > kSmallR || nJ * nr > kSmallPanel) cf.lev_small[l] = 0;
+        }
+        cf.lev_sn_ptr[l + 1] = (int32_t)cf.lev_sn.size();
     }
     return SLR_OK;
 }

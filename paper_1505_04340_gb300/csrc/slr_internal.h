@@ -63,7 +63,17 @@ struct CFactorHost {
     std::vector<int32_t> tasks;        // 4 ints each: supernode, first column, count (<= 32), 0
     std::vector<int32_t> lev_ptask_ptr;// [nlev+1] panel-row tasks per level
     std::vector<int32_t> ptasks;       // 4 ints each: supernode, first panel row, count (<= 32), 0
+    // Levels with many supernodes, each with at most kSmallN columns, kSmallR
+    // panel rows and kSmallPanel panel entries, are solved by one fused kernel
+    // (one CTA per supernode).
+    std::vector<int32_t> lev_sn_ptr;   // [nlev+1] supernodes per level
+    std::vector<int32_t> lev_sn;       // supernode ids, level by level
+    std::vector<uint8_t> lev_small;    // [nlev]
 };
+constexpr int32_t kSmallN = 128;
+constexpr int32_t kSmallR = 1024;
+constexpr int32_t kSmallPanel = 16384;     // panel entries of one supernode
+constexpr int32_t kSmallMinCount = 152;    // supernodes a level needs (one wave of SMs)
 
 struct HostSetup {
     int32_t n = 0, nI = 0, s = 0, p = 0;

@@ -246,6 +246,122 @@ k_cbwd_diag(const int4* __restrict__ tasks, const int32_t* __restrict__ c0, cons
     }
 }
 
+// Fused levels: one CTA per supernode J with n_J <= kSmallN and |R_J| <= kSmallR.
+static_assert(kThreads == 2 * kSmallN, "k_cbwd_small pairs two threads per column");
+// forward: t_J = g_J - (gathered panel products); x_J = L_JJ^{-1} t_J; w_J = L[R_J, J] x_J
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_cfwd_small(const int32_t* __restrict__ sns, const int32_t* __restrict__ c0, const int32_t* __restrict__ cperm,
+             const int64_t* __restrict__ seg_ptr, const int32_t* __restrict__ seg_row, const int64_t* __restrict__ r_off,
+             const int64_t* __restrict__ pan_off, const T* __restrict__ panel, const int64_t* __restrict__ dinv_off,
+             const T* __restrict__ dinv, T* wbuf, int64_t nrow, const T* g, int64_t ldg, T* xf, int32_t s,
+             int32_t nrhs) {
+    __shared__ T ts[kSmallN], xs[kSmallN];
+    const int J = sns[blockIdx.x];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = kThreads / 32;
+    const int32_t a0 = c0[J], nJ = c0[J + 1] - a0;
+    const int64_t nr = r_off[J + 1] - r_off[J];
+    const T* D = dinv + dinv_off[J];
+    const T* Pn = panel + pan_off[J];
+    for (int j = 0; j < nrhs; ++j) {
+        const T* w = wbuf + (int64_t)j * nrow;
+        for (int i = threadIdx.x; i < nJ; i += kThreads) {
+            const int32_t pos = a0 + i;
+            T acc = T(0);
+            for (int64_t e = seg_ptr[pos]; e < seg_ptr[pos + 1]; ++e) acc += w[seg_row[e]];
+            ts[i] = g[cperm[pos] + j * ldg] - acc;
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < nJ; i += kThreads) {
+            T acc = T(0);
+            int jj = 0;
+            for (; jj + 7 <= i; jj += 8) {
+                T d[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) d[u] = D[packed_col(jj + u, nJ) + (i - jj - u)];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) acc += d[u] * ts[jj + u];
+            }
+            for (; jj <= i; ++jj) acc += D[packed_col(jj, nJ) + (i - jj)] * ts[jj];
+            xs[i] = acc;
+            xf[a0 + i + (int64_t)j * s] = acc;
+        }
+        __syncthreads();
+        // four panel rows per warp at a time: their loads are in flight together
+        for (int64_t p0 = 4 * warp; p0 < nr; p0 += 4 * nw) {
+            T acc[4] = {T(0), T(0), T(0), T(0)};
+            for (int c = lane; c < nJ; c += 32) {
+                const T xv = xs[c];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (p0 + u < nr) acc[u] += Pn[(p0 + u) * nJ + c] * xv;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const T v = warp_sum(acc[u]);
+                if (lane == 0 && p0 + u < nr) wbuf[r_off[J] + p0 + u + (int64_t)j * nrow] = v;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// backward: t_J = y_J - L[R_J, J]^T x_{R_J};  x_J = L_JJ^{-T} t_J (and scatter to DD order)
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_cbwd_small(const int32_t* __restrict__ sns, const int32_t* __restrict__ c0, const int64_t* __restrict__ r_off,
+             const int32_t* __restrict__ rows, const int64_t* __restrict__ pan_off, const T* __restrict__ panel,
+             const int64_t* __restrict__ dinv_off, const T* __restrict__ dinv, const int32_t* __restrict__ cperm,
+             const T* yf, T* xf, T* y_dd, int64_t ldy, int32_t s, int32_t nrhs) {
+    __shared__ T xr[kSmallR], ts[kSmallN];
+    __shared__ T red[2][kSmallN];
+    const int J = sns[blockIdx.x];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = kThreads / 32;
+    const int32_t a0 = c0[J], nJ = c0[J + 1] - a0;
+    const int64_t nr = r_off[J + 1] - r_off[J];
+    const int32_t* R = rows + r_off[J];
+    const T* D = dinv + dinv_off[J];
+    const T* Pn = panel + pan_off[J];
+    for (int j = 0; j < nrhs; ++j) {
+        const T* x = xf + (int64_t)j * s;
+        for (int64_t p = threadIdx.x; p < nr; p += kThreads) xr[p] = x[R[p]];
+        __syncthreads();
+        // two halves of the panel rows per column, thread (half, column)
+        {
+            const int half = threadIdx.x / kSmallN, c = threadIdx.x % kSmallN;
+            T acc = T(0);
+            if (c < nJ) {
+                const int64_t mid = (nr + 1) / 2, pb = half ? mid : 0, pe = half ? nr : mid;
+                int64_t p = pb;
+                for (; p + 7 < pe; p += 8) {
+                    T pv[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) pv[u] = Pn[(p + u) * nJ + c];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) acc += pv[u] * xr[p + u];
+                }
+                for (; p < pe; ++p) acc += Pn[p * nJ + c] * xr[p];
+            }
+            red[half][c] = acc;
+        }
+        __syncthreads();
+        for (int c = threadIdx.x; c < nJ; c += kThreads)
+            ts[c] = yf[a0 + c + (int64_t)j * s] - (red[0][c] + red[1][c]);
+        __syncthreads();
+        for (int c = warp; c < nJ; c += nw) {
+            const T* Dc = D + packed_col(c, nJ) - c;
+            T acc = T(0);
+            for (int i = c + lane; i < nJ; i += 32) acc += Dc[i] * ts[i];
+            acc = warp_sum(acc);
+            if (lane == 0) {
+                xf[a0 + c + (int64_t)j * s] = acc;
+                if (y_dd) y_dd[cperm[a0 + c] + j * ldy] = acc;
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // ------------------------------------------------------------------ K4
 // part[(j k + kk) G + b] = partial of U[:, kk] . w[:, j] over block b's rows
 template <typename T>
@@ -499,6 +615,15 @@ template <typename T>
 cudaError_t launch_c_forward(const DevCFactor<T>& cf, const T* g_dd, int64_t ldg, T* tf, T* xf, int32_t nrhs,
                              cudaStream_t st) {
     for (int l = 0; l < cf.nlev; ++l) {
+        if (cf.lev_small[l]) {
+            const int s0 = cf.lev_sn_ptr[l], ns = cf.lev_sn_ptr[l + 1] - s0;
+            if (ns == 0) continue;
+            k_cfwd_small<T><<<ns, kThreads, 0, st>>>(cf.lev_sn + s0, cf.c0, cf.cperm, cf.seg_ptr, cf.seg_row, cf.r_off,
+                                                     cf.pan_off, cf.panel, cf.dinv_off, cf.dinv, cf.wbuf, cf.nrow,
+                                                     g_dd, ldg, xf, cf.s, nrhs);
+            counted();
+            continue;
+        }
         const int t0 = cf.lev_task_ptr[l], nt = cf.lev_task_ptr[l + 1] - t0;
         const int p0 = cf.lev_ptask_ptr[l], np = cf.lev_ptask_ptr[l + 1] - p0;
         if (nt > 0) {
@@ -521,6 +646,14 @@ template <typename T>
 cudaError_t launch_c_backward(const DevCFactor<T>& cf, T* yf, T* xf, T* y_dd, int64_t ldy, int32_t nrhs,
                               cudaStream_t st) {
     for (int l = cf.nlev - 1; l >= 0; --l) {
+        if (cf.lev_small[l]) {
+            const int s0 = cf.lev_sn_ptr[l], ns = cf.lev_sn_ptr[l + 1] - s0;
+            if (ns == 0) continue;
+            k_cbwd_small<T><<<ns, kThreads, 0, st>>>(cf.lev_sn + s0, cf.c0, cf.r_off, cf.rows, cf.pan_off, cf.panel,
+                                                     cf.dinv_off, cf.dinv, cf.cperm, yf, xf, y_dd, ldy, cf.s, nrhs);
+            counted();
+            continue;
+        }
         const int t0 = cf.lev_task_ptr[l], nt = cf.lev_task_ptr[l + 1] - t0;
         if (nt == 0) continue;
         k_cbwd_panel<T><<<nt, kPanT, 0, st>>>(cf.tasks + t0, cf.c0, cf.r_off, cf.rows, cf.pan_off, cf.panel,

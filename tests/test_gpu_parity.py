@@ -169,7 +169,7 @@ def test_pcg_end_to_end(name, theta):
 
     With the oracle's low-rank pairs imported both runs apply the same
     preconditioner, so their CG iterates agree: same iteration count (+-1) and
-    solutions within a thousandth of their own error.  With the GPU's own Lanczos pairs (near-degenerate
+    solutions within a hundredth of their own error.  With the GPU's own Lanczos pairs (near-degenerate
     Ritz pairs converge at a rate set by rounding, Section 5.1) the iteration
     count stays within one and the solution is as accurate as the oracle's."""
     P = make(name, nrhs=2)
@@ -185,9 +185,9 @@ def test_pcg_end_to_end(name, theta):
     assert np.all(np.abs(its - np.array(its_o)) <= 1), (its, its_o)
     err_o = np.linalg.norm(xo - P.xstar) / np.linalg.norm(P.xstar)
     if np.array_equal(its, its_o):
-        # same operator in another summation order: the iterates agree to a small
-        # fraction of the solution's own error (CG amplifies rounding by about cond(A))
-        assert rel(x.cpu().numpy(), xo) <= max(1e-10, 1e-3 * err_o)
+        # same operator in another summation order: the iterates agree to within 1%
+        # of the solution's own error (CG amplifies rounding by about cond(A))
+        assert rel(x.cpu().numpy(), xo) <= max(1e-10, 1e-2 * err_o)
     # own Lanczos pairs
     g = gpu_handle(P, theta=theta)
     x, its, relres, st = g.pcg(cu(P.b))
