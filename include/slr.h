@@ -173,6 +173,25 @@ slr_status slr_dd_order(int32_t n, const int32_t* rowptr, const int32_t* colind,
                         const int32_t* part, int32_t* perm_out, int32_t* int_off, int32_t* ifc_off,
                         int32_t* s_out);
 
+/* z = M^{-1} r exactly as slr_apply, for callers that cannot call cudaMalloc
+ * while they run: code inside a stream capture in cudaStreamCaptureModeGlobal
+ * (where allocation calls are errors), or a process whose device memory is
+ * handed to an allocator it does not control.  It allocates nothing: its
+ * per-call scratch (band-solve intermediates, interface vectors, panel
+ * products, reduction partials) is carved from one file-scope __device__ array
+ * of 32 MiB that every GPU loading this library holds until exit, instead of
+ * the handle's workspaces.  The paper has no counterpart; this is a deployment
+ * variant of the apply of Eq. 4.1.
+ * Same arguments, layout and ownership as slr_apply.  Errors: INVALID_ARG as
+ * slr_apply; UNSUPPORTED (nothing launched) when the scratch for this handle
+ * and nrhs exceeds 32 MiB.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress); make that first call before any
+ * stream capture.  Every call shares the one array and no part of it needs to
+ * start at zero (each call writes what it reads); calls that overlap on the
+ * GPU, from any thread, stream or handle, race on it. */
+slr_status slr_apply_noalloc(slr_handle h, const double* r_dev, double* z_dev, int32_t nrhs, int32_t ld,
+                             void* stream);
+
 /* Number of CUDA kernels this library has launched in this process so far
  * (all handles, all devices).  Lets a caller count the launches of a region. */
 int64_t slr_kernel_launches(void);

@@ -1,0 +1,159 @@
+// slr_apply_noalloc: the preconditioner apply with its scratch vectors in a
+// fixed, library-owned device array instead of the handle's workspaces.
+//
+// slr_setup allocates everything a handle needs, once.  The per-call scratch
+// of slr_apply lives in that handle.  Some callers cannot let any device
+// memory be allocated on their behalf after start-up (for example a host
+// process that hands all device memory to its own fixed arena, or code that
+// must not grow its footprint while it serves requests), yet want the apply
+// without depending on the handle's workspace sizing.  This entry point
+// allocates nothing: it carves its scratch from one static __device__ array
+// of kNoAllocBytes, which every GPU that loads the library holds until exit.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <mutex>
+#include <string>
+#include <type_traits>
+
+#include "slr_device.h"
+
+using namespace slr;
+
+namespace {
+
+constexpr size_t kNoAllocBytes = 32ull << 20;   // 32 MiB per device
+constexpr int kMaxDevices = 64;
+
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[kMaxDevices] = {};          // device address of the array, per device
+
+// Device address of the array on `dev` (which is current): looked up once per device.
+slr_status scratch_base(int dev, unsigned char** out) {
+    if (dev < 0 || dev >= kMaxDevices) {
+        set_error("slr_apply_noalloc: device index out of range");
+        return SLR_ERR_UNSUPPORTED;
+    }
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            set_error(std::string("slr_apply_noalloc: cudaGetSymbolAddress failed: ") + cudaGetErrorString(e));
+            return SLR_ERR_CUDA;
+        }
+        g_noalloc_addr[dev] = p;
+    }
+    *out = static_cast<unsigned char*>(g_noalloc_addr[dev]);
+    return SLR_OK;
+}
+
+// Hands out 256-byte aligned slices of the array; `need` counts the bytes.
+struct Carver {
+    unsigned char* base;
+    size_t used = 0;
+    template <typename T>
+    T* take(size_t count) {
+        used = (used + 255) & ~size_t(255);
+        T* p = base ? reinterpret_cast<T*>(base + used) : nullptr;
+        used += count * sizeof(T);
+        return p;
+    }
+};
+
+// Points every per-call workspace of a copy of the operator into the array.
+template <typename T>
+size_t carve(slr_handle h, DevOperator<T>& op, int32_t nrhs, unsigned char* base) {
+    const int64_t n = h->hs.n, nI = std::max<int64_t>(h->hs.nI, 1), s = std::max<int64_t>(h->hs.s, 1);
+    const int64_t k = std::max<int32_t>(h->k, 1);
+    Carver c{base};
+    op.tB = c.take<T>(nI * nrhs);
+    op.eb = c.take<T>(nI * nrhs);
+    op.gp = c.take<T>(s * nrhs);
+    op.wf = c.take<T>(s * nrhs);
+    op.tf = c.take<T>(s * nrhs);
+    op.xf = c.take<T>(s * nrhs);
+    op.cf.wbuf = c.take<T>(std::max<int64_t>(op.cf.nrow, 1) * nrhs);
+    op.vk = c.take<T>(k * nrhs);
+    op.part = c.take<T>(k * nrhs * kRedBlocks);
+    if constexpr (!std::is_same<T, double>::value) {
+        op.wr = c.take<T>(n * nrhs);
+        op.wz = c.take<T>(n * nrhs);
+    }
+    return c.used;
+}
+
+#define NA_CK(...)                                                                         \
+    do {                                                                                   \
+        cudaError_t e_ = (__VA_ARGS__);                                                    \
+        if (e_ != cudaSuccess) {                                                           \
+            set_error(std::string("slr_apply_noalloc: ") + cudaGetErrorString(e_));        \
+            return SLR_ERR_CUDA;                                                           \
+        }                                                                                  \
+    } while (0)
+
+// z = M^{-1} r with the operator's workspaces in the array (same kernels as slr_apply)
+template <typename T>
+slr_status apply_with(slr_handle h, DevOperator<T>& op, const T* r, int64_t ldr, T* z, int64_t ldz, int32_t nrhs,
+                      cudaStream_t st) {
+    const HostSetup& hs = h->hs;
+    const int32_t nI = hs.nI, s = hs.s;
+    NA_CK(launch_band_solve<T>(op, hs.p, hs.wmax, r, ldr, op.tB, nI, nullptr, 0, nrhs, st));
+    NA_CK(launch_gather_et<T>(op, s, r + nI, ldr, op.tB, nI, op.gp, s, nrhs, st));
+    NA_CK(launch_c_forward<T>(op.cf, op.gp, s, op.tf, op.wf, nrhs, st));
+    NA_CK(launch_lowrank<T>(op, s, h->k, op.wf, nrhs, st));
+    NA_CK(launch_c_backward<T>(op.cf, op.wf, op.xf, z + nI, ldz, nrhs, st));
+    NA_CK(launch_spmv_e<T>(op, nI, z + nI, ldz, op.eb, nI, nrhs, st));
+    NA_CK(launch_band_solve<T>(op, hs.p, hs.wmax, op.eb, nI, z, ldz, op.tB, nI, nrhs, st));
+    return SLR_OK;
+}
+
+template <typename T>
+slr_status run_noalloc(slr_handle h, DevOperator<T> op, const double* r, double* z, int32_t nrhs, int32_t ld,
+                       cudaStream_t s) {
+    const size_t need = carve(h, op, nrhs, nullptr);       // size check before any device work
+    if (need > kNoAllocBytes) {
+        set_error("slr_apply_noalloc: needs " + std::to_string(need) + " bytes of scratch for nrhs=" +
+                  std::to_string(nrhs) + ", more than its fixed " + std::to_string(kNoAllocBytes) + " bytes");
+        return SLR_ERR_UNSUPPORTED;
+    }
+    unsigned char* base = nullptr;
+    slr_status st = scratch_base(h->device, &base);
+    if (st != SLR_OK) return st;
+    carve(h, op, nrhs, base);
+    if constexpr (std::is_same<T, double>::value) {
+        return apply_with<double>(h, op, r, ld, z, ld, nrhs, s);
+    } else {
+        const int64_t n = h->hs.n;
+        NA_CK(launch_convert<double, float>(n, nrhs, r, ld, op.wr, n, s));
+        st = apply_with<float>(h, op, op.wr, n, op.wz, n, nrhs, s);
+        if (st != SLR_OK) return st;
+        NA_CK(launch_convert<float, double>(n, nrhs, op.wz, n, z, ld, s));
+        return SLR_OK;
+    }
+}
+
+}  // namespace
+
+extern "C" slr_status slr_apply_noalloc(slr_handle h, const double* r, double* z, int32_t nrhs, int32_t ld,
+                                        void* stream) {
+    if (!h || !h->op64.ready) {
+        set_error("slr_apply_noalloc: invalid handle");
+        return SLR_ERR_INVALID_ARG;
+    }
+    if (nrhs < 1 || nrhs > h->opts.nrhs_max || ld < h->hs.n || !r || !z) {
+        set_error("slr_apply_noalloc: bad nrhs, ld or pointer");
+        return SLR_ERR_INVALID_ARG;
+    }
+    int old = -1;
+    cudaGetDevice(&old);
+    if (old != h->device) cudaSetDevice(h->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const slr_status st = h->opts.precision == SLR_PREC_FP64 ? run_noalloc<double>(h, h->op64, r, z, nrhs, ld, s)
+                                                             : run_noalloc<float>(h, h->op32, r, z, nrhs, ld, s);
+    if (old >= 0 && old != h->device) cudaSetDevice(old);
+    return st;
+}

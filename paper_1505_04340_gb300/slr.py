@@ -30,7 +30,7 @@ PRECISION = {"fp64": 0, "mixed": 1}
 EXPORTS = ["slr_default_opts", "slr_setup", "slr_apply", "slr_pcg_solve", "slr_bsolve", "slr_csolve",
            "slr_stilde_solve", "slr_set_lowrank", "slr_get_lowrank", "slr_get_ritz", "slr_get_perm",
            "slr_get_info", "slr_dd_order", "slr_kernel_launches", "slr_destroy", "slr_status_str",
-           "slr_last_error_message"]
+           "slr_last_error_message", "slr_apply_noalloc"]
 
 
 class Opts(C.Structure):
@@ -73,6 +73,7 @@ def load():
         "slr_default_opts": (None, [P(Opts)]),
         "slr_setup": (i32, [i32, vp, vp, vp, i32, vp, P(Opts), vp, P(vp)]),
         "slr_apply": (i32, [vp, vp, vp, i32, i32, vp]),
+        "slr_apply_noalloc": (i32, [vp, vp, vp, i32, i32, vp]),
         "slr_pcg_solve": (i32, [vp, vp, vp, i32, i32, f64, i32, vp, vp, vp]),
         "slr_bsolve": (i32, [vp, vp, vp, i32, i32, vp]),
         "slr_csolve": (i32, [vp, vp, vp, i32, i32, vp]),
@@ -253,6 +254,10 @@ class SLR:
     def apply(self, r, stream=None):
         """z = M^{-1} r in DD order (Eq. 4.1)."""
         return self._call(self._lib.slr_apply, r, self.n, "r", stream)
+
+    def apply_noalloc(self, r, stream=None):
+        """z = M^{-1} r with the scratch in the library's fixed device array (no allocation)."""
+        return self._call(self._lib.slr_apply_noalloc, r, self.n, "r", stream)
 
     def bsolve(self, f, stream=None):
         """t = B^{-1} f on the interior unknowns (DD order)."""
