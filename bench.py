@@ -21,6 +21,7 @@ import threading
 import time
 
 import numpy as np
+import scipy.sparse as sp
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -251,6 +252,67 @@ def run_profile(args):
     h.close()
 
 
+def run_serving(args, dev):
+    """Config-5 request stream through the solve server: a cold pass (each matrix
+    set up on its first request) and a warm pass over the same stream (all resident)."""
+    import torch
+    import slrgen
+    from paper_1505_04340_gb300 import serving
+    specs = slrgen.serving_specs(32, seed=3)
+    stream = slrgen.serving_requests(count=args.serving_requests, seed=3, nspecs=len(specs), rate=args.serving_rate)
+    used = sorted({d["spec"] for d in stream})
+    probs = {i: slrgen.serving_problem(specs[i]) for i in used}
+    mats = {i: serving.MatrixSpec(p.rowptr, p.colind, p.val, p.part, p.nparts, k=p.k) for i, p in probs.items()}
+
+    def requests():
+        out = []
+        for d in stream:
+            _, b = slrgen.request_rhs(probs[d["spec"]], d["nrhs"], d["rhs_seed"])
+            out.append(serving.Request(rid=d["rid"], matrix=d["spec"], b=b[:, 0] if d["nrhs"] == 1 else b,
+                                       arrival=d["arrival"]))
+        return out
+
+    srv = serving.SolveServer(mats, precision="mixed", nrhs_max=8, tol=1e-8, maxit=300,
+                              max_concurrent=args.serving_concurrency, log=sys.stderr)
+    res = {}
+    try:
+        for name in ("cold", "warm"):
+            reqs = requests()
+            l0 = pkg_launches()
+            torch.cuda.synchronize()
+            srv.run(reqs, realtime=True)
+            torch.cuda.synchronize()
+            st = serving.latency_stats(reqs)
+            worst = 0.0
+            failed = [r for r in reqs if r.x is None]
+            for r in failed:
+                print(f"[serving] request {r.rid} (matrix {r.matrix}) failed: status {r.status}: {r.error}",
+                      file=sys.stderr)
+            for r in reqs:
+                if r.x is None:
+                    continue
+                P = probs[r.matrix]
+                A = sp.csr_matrix((P.val, P.colind, P.rowptr))
+                B, X = r.b.reshape(P.n, -1), r.x.reshape(P.n, -1)
+                worst = max(worst, float(np.max(np.linalg.norm(B - A @ X, axis=0) / np.linalg.norm(B, axis=0))))
+            st.update(max_true_relres=worst, gpu_launches=pkg_launches() - l0,
+                      unconverged=sum(r.status != 0 for r in reqs), failed=len(failed),
+                      mean_batch_columns=float(np.mean([r.batch for r in reqs])))
+            res[name] = st
+        res.update(setups=srv.setups, evictions=srv.evictions, batches=srv.batches, matrices=len(mats),
+                   requests=len(stream), rate_per_s=args.serving_rate, concurrency=args.serving_concurrency,
+                   precision="f32 apply / f64 flexible CG", workload="fv-diffusion pool of %d specs, "
+                   "1-8 RHS, Poisson arrivals, seed 3" % len(specs))
+    finally:
+        srv.close()
+    return res
+
+
+def pkg_launches():
+    import paper_1505_04340_gb300 as pkg
+    return pkg.slr.kernel_launches()
+
+
 def run_ours(args):
     import torch
     import paper_1505_04340_gb300 as pkg
@@ -368,6 +430,12 @@ def run_ours(args):
                               "d2h_bytes_per_step": P.n * 8}
         h.close()
 
+    serving_res = None
+    if args.serving_requests > 0:
+        serving_res = run_serving(args, dev)
+        for key in ("cold", "warm"):
+            st = serving_res[key]
+            st["solves_per_s"], _, _ = aggregate(st["solves"], st["span_s"], device=dev)
     if rank != 0:
         if dist:
             dist.destroy_process_group()
@@ -419,6 +487,7 @@ def run_ours(args):
         "e2e": results["e2e"],
         "gpu_launches": r64["launches"],
         "clocks": r64["clocks"],
+        "serving": serving_res,
     }
     print(json.dumps(line), flush=True)
     if dist:
@@ -439,6 +508,9 @@ def main():
     ap.add_argument("--profile", action="store_true", help="solves inside an NVTX range only (for ncu)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--profile-kernel", default="pcg", choices=["pcg", "bsolve", "csolve", "apply"])
+    ap.add_argument("--serving-requests", type=int, default=256, help="config-5 request stream length (0: skip)")
+    ap.add_argument("--serving-rate", type=float, default=50.0, help="Poisson arrival rate, requests/s")
+    ap.add_argument("--serving-concurrency", type=int, default=4)
     ap.add_argument("--host-loop", action="store_true",
                     help="drive CG from the host (profilers do not see kernels inside conditional graph nodes)")
     args = ap.parse_args()

@@ -8,7 +8,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
+#include <shared_mutex>
 #include <string>
 #include <type_traits>
 #include <vector>
@@ -16,10 +18,6 @@
 #include "slr_device.h"
 
 using namespace slr;
-
-namespace slr {
-extern std::atomic<int64_t> g_kernel_launches;
-}
 
 namespace {
 
@@ -40,6 +38,13 @@ namespace {
 double now_s() {
     return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
+
+// Graph captures and device frees exclude each other.  A stream capture in one
+// thread fails if another thread meanwhile makes a call that must wait for the
+// capturing stream; a free may wait for the whole device.  Captures share the
+// lock, frees take it alone.  (Captures take milliseconds and happen once per
+// handle and right-hand-side count.)
+std::shared_mutex g_capture_mu;
 
 // Restores the caller's current device on scope exit.
 struct DeviceGuard {
@@ -75,7 +80,10 @@ void dfree(slr_handle h, T*& p, size_t count) {
     if (!p) return;
     auto it = std::find(h->allocs.begin(), h->allocs.end(), (void*)p);
     if (it != h->allocs.end()) h->allocs.erase(it);
-    cudaFree(p);
+    {
+        std::unique_lock<std::shared_mutex> lk(g_capture_mu);
+        cudaFree(p);
+    }
     h->device_bytes -= (int64_t)(count * sizeof(T));
     p = nullptr;
 }
@@ -84,11 +92,13 @@ template <typename TD, typename TS>
 slr_status upload(slr_handle h, TD** p, const std::vector<TS>& v) {
     CS(dalloc(h, p, v.size()));
     if (v.empty()) return SLR_OK;
+    // from pageable memory: the call returns once the data is staged, so the
+    // source may go away afterwards
     if constexpr (std::is_same<TD, TS>::value) {
-        CK(cudaMemcpy(*p, v.data(), v.size() * sizeof(TD), cudaMemcpyHostToDevice));
+        CK(cudaMemcpyAsync(*p, v.data(), v.size() * sizeof(TD), cudaMemcpyHostToDevice, h->stream));
     } else {
         std::vector<TD> tmp(v.begin(), v.end());
-        CK(cudaMemcpy(*p, tmp.data(), tmp.size() * sizeof(TD), cudaMemcpyHostToDevice));
+        CK(cudaMemcpyAsync(*p, tmp.data(), tmp.size() * sizeof(TD), cudaMemcpyHostToDevice, h->stream));
     }
     return SLR_OK;
 }
@@ -101,7 +111,7 @@ slr_status upload_operator(slr_handle h, DevOperator<T>& op, bool with_band) {
     if (with_band) CS(upload(h, &op.bfac, hs.bfac));
     op.band_G = hs.band_G;
     CS(dalloc(h, &op.err, 1));
-    CK(cudaMemset(op.err, 0, sizeof(int32_t)));
+    CK(cudaMemsetAsync(op.err, 0, sizeof(int32_t), h->stream));
     CS(upload(h, &op.e_rp, hs.e_rp));
     CS(upload(h, &op.e_ci, hs.e_ci));
     CS(upload(h, &op.e_v, hs.e_v));
@@ -136,9 +146,12 @@ slr_status upload_operator(slr_handle h, DevOperator<T>& op, bool with_band) {
         return SLR_ERR_UNSUPPORTED;
     }
     CS(dalloc(h, &d.tasks, c.tasks.size() / 4));
-    if (!c.tasks.empty()) CK(cudaMemcpy(d.tasks, c.tasks.data(), c.tasks.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    if (!c.tasks.empty())
+        CK(cudaMemcpyAsync(d.tasks, c.tasks.data(), c.tasks.size() * sizeof(int32_t), cudaMemcpyHostToDevice, h->stream));
     CS(dalloc(h, &d.ptasks, c.ptasks.size() / 4));
-    if (!c.ptasks.empty()) CK(cudaMemcpy(d.ptasks, c.ptasks.data(), c.ptasks.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    if (!c.ptasks.empty())
+        CK(cudaMemcpyAsync(d.ptasks, c.ptasks.data(), c.ptasks.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
+                           h->stream));
     CS(dalloc(h, &d.wbuf, (size_t)std::max<int64_t>(d.nrow, 1) * r));
     const int64_t n = hs.n, nI = hs.nI, s = hs.s;
     if constexpr (!std::is_same<T, double>::value) {
@@ -174,16 +187,17 @@ slr_status set_operator_lowrank(slr_handle h, DevOperator<T>& op, const double* 
     }
     if (k > 0) {
         if constexpr (std::is_same<T, double>::value) {
-            if ((void*)op.U != (void*)U64_dev) CK(cudaMemcpy(op.U, U64_dev, sizeof(double) * s * k, cudaMemcpyDeviceToDevice));
+            if ((void*)op.U != (void*)U64_dev)
+                CK(cudaMemcpyAsync(op.U, U64_dev, sizeof(double) * s * k, cudaMemcpyDeviceToDevice, h->stream));
         } else {
-            CK(launch_convert<double, float>(s, k, U64_dev, s, op.U, s, 0));
-            CK(cudaDeviceSynchronize());
+            CK(launch_convert<double, float>(s, k, U64_dev, s, op.U, s, h->stream));
         }
         // d_i = (1 - lambda_i)^{-1} - (1 - theta)^{-1}, formed in FP64 (cancellation near 1)
         std::vector<double> d(k);
         for (int32_t i = 0; i < k; ++i) d[i] = 1.0 / (1.0 - lam[i]) - 1.0 / (1.0 - theta);
         std::vector<T> dt(d.begin(), d.end());
-        CK(cudaMemcpy(op.dvec, dt.data(), sizeof(T) * k, cudaMemcpyHostToDevice));
+        CK(cudaMemcpyAsync(op.dvec, dt.data(), sizeof(T) * k, cudaMemcpyHostToDevice, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
     }
     op.cinv = (T)(1.0 / (1.0 - theta));
     return SLR_OK;
@@ -260,7 +274,7 @@ slr_status run_lanczos(slr_handle h, cudaStream_t st) {
     CS(dalloc(h, &sc, 4));
     std::vector<double> z(s);
     for (int32_t i = 0; i < s; ++i) z[i] = splitmix_pm1(h->opts.seed, (uint64_t)i);
-    CK(cudaMemcpy(w, z.data(), sizeof(double) * s, cudaMemcpyHostToDevice));
+    CK(cudaMemcpyAsync(w, z.data(), sizeof(double) * s, cudaMemcpyHostToDevice, st));
     CK(launch_csr_spmv(s, h->c_rp, h->c_ci, h->c_v, w, s, op.gp, s, 1, st));     // C z (DD order)
     CK(launch_c_forward<double>(op.cf, op.gp, s, op.tf, V, 1, st));              // L^{-1} C z
     slr_status err = SLR_OK;
@@ -301,7 +315,7 @@ slr_status run_lanczos(slr_handle h, cudaStream_t st) {
     h->theta = (h->opts.theta_mode == SLR_THETA_LAMBDA_K1 && m_eff > k) ? lam[k] : 0.0;
     h->lam.assign(lam.begin(), lam.begin() + k);
     CS(dalloc(h, &Yd, (size_t)m_eff * k));
-    CK(cudaMemcpy(Yd, Y.data(), sizeof(double) * m_eff * k, cudaMemcpyHostToDevice));
+    CK(cudaMemcpyAsync(Yd, Y.data(), sizeof(double) * m_eff * k, cudaMemcpyHostToDevice, st));
     CS(dalloc(h, &Ud, (size_t)s * k));
     CK(launch_gemm_nn(s, m_eff, k, V, Yd, Ud, st));
     CK(cudaStreamSynchronize(st));
@@ -403,7 +417,7 @@ slr_status setup_impl(slr_handle h, int32_t n, const int32_t* rowptr, const int3
     CS(dalloc(h, &h->scal, (size_t)8 * r));
     CS(dalloc(h, &h->iflags, (size_t)4 * r + 4));
     CS(dalloc(h, &h->dpart, (size_t)kRedBlocks * r));
-    CK(cudaDeviceSynchronize());
+    CK(cudaStreamSynchronize(st));
     double t4 = now_s();
     CS(run_lanczos(h, st));
     CK(cudaStreamSynchronize(st));
@@ -414,7 +428,7 @@ slr_status setup_impl(slr_handle h, int32_t n, const int32_t* rowptr, const int3
         // the FP64 band factor served the FP64 Lanczos only
         dfree(h, h->op64.bfac, hs.bfac.size());
     }
-    CK(cudaDeviceSynchronize());
+    CK(cudaStreamSynchronize(st));
     double t6 = now_s();
     h->setup_seconds[0] = t1 - t0;
     h->setup_seconds[1] = t2 - t1;
@@ -518,14 +532,27 @@ slr_status pcg_graph(slr_handle h, int32_t nrhs, slr_handle_s::PcgGraph** out) {
     cudaGraph_t ibody = ip.conditional.phGraph_out[0];
     slr_handle_s::PcgGraph gr;
     gr.nrhs = nrhs;
-    const int64_t l0 = g_kernel_launches.load();
+    std::shared_lock<std::shared_mutex> capture_lock(g_capture_mu);
+    const int64_t l0 = thread_launches();
+    // A capture that fails part-way leaves nodes in a conditional body of
+    // `graph`, and destroying such a graph has crashed inside the driver: on
+    // that error path the graph is left allocated (one graph per failure).
+    auto capture_failed = [&](slr_status st, cudaError_t ce) {
+        count_launches(-(thread_launches() - l0));
+        gg.g = nullptr;
+        cudaGetLastError();                       // the failure is reported by the status
+        if (st == SLR_OK) {
+            set_error(std::string("pcg graph capture: ") + cudaGetErrorString(ce));
+            st = SLR_ERR_CUDA;
+        }
+        return st;
+    };
     CK(cudaStreamBeginCaptureToGraph(cs, ibody, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
     slr_status s1 = pcg_update_part(h, nrhs, cs);
     cudaGraph_t tmp = nullptr;
     cudaError_t ce = cudaStreamEndCapture(cs, &tmp);
-    if (s1 != SLR_OK) return s1;
-    CK(ce);
-    const int64_t l1 = g_kernel_launches.load();
+    if (s1 != SLR_OK || ce != cudaSuccess) return capture_failed(s1, ce);
+    const int64_t l1 = thread_launches();
     CK(cudaStreamBeginCaptureToGraph(cs, body, &inode, nullptr, 1, cudaStreamCaptureModeRelaxed));
     s1 = pcg_test_part(h, nrhs, cs);
     if (s1 == SLR_OK) {
@@ -536,12 +563,12 @@ slr_status pcg_graph(slr_handle h, int32_t nrhs, slr_handle_s::PcgGraph** out) {
         }
     }
     ce = cudaStreamEndCapture(cs, &tmp);
-    if (s1 != SLR_OK) return s1;
-    CK(ce);
-    const int64_t l2 = g_kernel_launches.load();
+    if (s1 != SLR_OK || ce != cudaSuccess) return capture_failed(s1, ce);
+    capture_lock.unlock();
+    const int64_t l2 = thread_launches();
     gr.kB = l1 - l0;
     gr.kA = l2 - l1;
-    g_kernel_launches.fetch_sub(l2 - l0);     // captured, not run
+    count_launches(-(l2 - l0));               // captured, not run
     CK(cudaGraphInstantiate(&gr.exec, graph, 0));
     h->pcg_graphs.push_back(gr);
     *out = &h->pcg_graphs.back();
@@ -575,6 +602,7 @@ slr_status slr_setup(int32_t n, const int32_t* rowptr, const int32_t* colind, co
     if (h->opts.nrhs_max == 0) h->opts.nrhs_max = 1;
     slr_status s;
     try {
+        h->stream = (cudaStream_t)stream;
         s = setup_impl(h, n, rowptr, colind, val, nparts, part, (cudaStream_t)stream);
     } catch (const std::bad_alloc&) {
         set_error("host allocation failed");
@@ -672,11 +700,14 @@ slr_status slr_pcg_solve(slr_handle h, const double* b, double* x, int32_t nrhs,
     CK(launch_dots(nn, nrhs, h->pr, nn, h->pz, nn, h->dpart, h->scal + 0, 8, st));
     CK(cudaMemcpyAsync(h->pp, h->pz, sizeof(double) * nn * nrhs, cudaMemcpyDeviceToDevice, st));
     if (maxit > 0) {
-        if (h->opts.reserved[1] == 1) {
+        slr_handle_s::PcgGraph* gr = nullptr;
+        // the graph is captured on first use for this right-hand-side count; if
+        // the capture fails (another thread may have made a call that waits for
+        // the whole device meanwhile) this solve runs the same kernels from the
+        // host loop, and the next solve captures again
+        if (h->opts.reserved[1] == 1 || pcg_graph(h, nrhs, &gr) != SLR_OK) {
             CS(pcg_host_loop(h, nrhs, tol, maxit, st));
         } else {
-            slr_handle_s::PcgGraph* gr = nullptr;
-            CS(pcg_graph(h, nrhs, &gr));
             const double ctl[2] = {tol * tol, (double)maxit};
             CK(cudaMemcpyAsync(h->ctl, ctl, sizeof(ctl), cudaMemcpyHostToDevice, st));
             CK(cudaGraphLaunch(gr->exec, st));
@@ -684,7 +715,7 @@ slr_status slr_pcg_solve(slr_handle h, const double* b, double* x, int32_t nrhs,
             CK(cudaMemcpyAsync(&its, h->iflags + 4 * nrhs + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
             CK(cudaStreamSynchronize(st));
             // kernels the graph ran: the test part every iteration, the update part from the second on
-            g_kernel_launches.fetch_add(its * gr->kA + std::max(0, its - 1) * gr->kB);
+            count_launches(its * gr->kA + std::max(0, its - 1) * gr->kB);
         }
     }
     CK(launch_permute(n, nrhs, h->perm, h->px, nn, x, ld, false, st));                 // x = P^T x_dd
@@ -697,7 +728,8 @@ slr_status slr_pcg_solve(slr_handle h, const double* b, double* x, int32_t nrhs,
     {
         int32_t e = 0;
         const int32_t* ep = h->opts.precision == SLR_PREC_FP64 ? h->op64.err : h->op32.err;
-        CK(cudaMemcpy(&e, ep, sizeof(int32_t), cudaMemcpyDeviceToHost));
+        CK(cudaMemcpyAsync(&e, ep, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
         if (e) {
             set_error("a bounded device wait expired in the band solve");
             return SLR_ERR_TIMEOUT;
@@ -726,13 +758,14 @@ slr_status slr_set_lowrank(slr_handle h, int32_t k, const double* Z, const doubl
         if (!(lam[i] < 1.0)) { set_error("slr_set_lowrank: lambda must be < 1"); return SLR_ERR_INVALID_ARG; }
     DeviceGuard g(h->device);
     cudaStream_t st = (cudaStream_t)stream;
+    h->stream = st;
     double *Zd = nullptr, *CZ = nullptr, *U = nullptr, *T1 = nullptr;
     if (k > 0) {
         CS(dalloc(h, &Zd, (size_t)s * k));
         CS(dalloc(h, &CZ, (size_t)s * k));
         CS(dalloc(h, &U, (size_t)s * k));
         CS(dalloc(h, &T1, (size_t)s * k));
-        CK(cudaMemcpy(Zd, Z, sizeof(double) * s * k, cudaMemcpyHostToDevice));
+        CK(cudaMemcpyAsync(Zd, Z, sizeof(double) * s * k, cudaMemcpyHostToDevice, st));
         CK(launch_csr_spmv(s, h->c_rp, h->c_ci, h->c_v, Zd, s, CZ, s, k, st));       // C Z
         // U = L^{-1} C Z, at most nrhs_max columns at a time (the forward solve's
         // panel-product workspace holds nrhs_max columns)
@@ -746,7 +779,10 @@ slr_status slr_set_lowrank(slr_handle h, int32_t k, const double* Z, const doubl
     }
     std::vector<double> lv(lam, lam + k);
     const int32_t k_old = h->k;
-    drop_graphs(h);
+    {
+        std::unique_lock<std::shared_mutex> lk(g_capture_mu);
+        drop_graphs(h);
+    }
     CS(set_operator_lowrank<double>(h, h->op64, U, k_old, k, lv, theta));
     if (h->opts.precision == SLR_PREC_MIXED) CS(set_operator_lowrank<float>(h, h->op32, U, k_old, k, lv, theta));
     h->k = k;
@@ -838,8 +874,11 @@ void slr_destroy(slr_handle h) {
     int old = -1;
     cudaGetDevice(&old);
     if (old != h->device) cudaSetDevice(h->device);
-    drop_graphs(h);
-    for (void* p : h->allocs) cudaFree(p);
+    {
+        std::unique_lock<std::shared_mutex> lk(g_capture_mu);
+        drop_graphs(h);
+        for (void* p : h->allocs) cudaFree(p);
+    }
     if (old >= 0 && old != h->device) cudaSetDevice(old);
     delete h;
 }

@@ -24,14 +24,13 @@
 
 #include <atomic>
 #include <cstdint>
+#include <mutex>
 
 #include "slr_device.h"
 
 namespace cg = cooperative_groups;
 
 namespace slr {
-
-extern std::atomic<int64_t> g_kernel_launches;
 
 namespace {
 
@@ -401,8 +400,27 @@ cudaError_t band_launch(const DevOperator<T>& op, int32_t p, int32_t wmax, const
                         int64_t ldo, const T* base, int64_t ldb, cudaStream_t st) {
     const size_t smem = band_smem_bytes(wmax, G, NR, sizeof(T));
     auto kern = k_band_solve2<T, NR, G>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+    // The dynamic shared-memory limit of a kernel is process-wide state on its
+    // device.  It is raised once, to the device's opt-in maximum, so that
+    // threads launching this kernel for operators of different widths never
+    // race between one thread's setting and another's launch.
+    static std::mutex mu;
+    static uint64_t raised = 0;                     // bit d: done on device d
+    {
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+        std::lock_guard<std::mutex> lk(mu);
+        if (!(raised >> dev & 1)) {
+            int optin = 0;
+            e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+            if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+            if (e != cudaSuccess) return e;
+            raised |= 1ull << dev;
+        }
+    }
+    cudaError_t e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(p * G);
     cfg.blockDim = dim3(kT);
@@ -416,7 +434,7 @@ cudaError_t band_launch(const DevOperator<T>& op, int32_t p, int32_t wmax, const
     cfg.attrs = attr;
     cfg.numAttrs = G > 1 ? 1 : 0;
     e = cudaLaunchKernelEx(&cfg, kern, op.band, op.bfac, in, ldi, out, ldo, base, ldb, op.err);
-    g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
+    count_launches(1);
     return e;
 }
 

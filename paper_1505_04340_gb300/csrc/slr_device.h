@@ -62,6 +62,7 @@ struct DevOperator {
 struct slr_handle_s {
     int device = 0;
     slr_opts opts;
+    cudaStream_t stream = nullptr;   // stream of the setup or set_lowrank call in progress
     slr::HostSetup hs;               // sizes, permutation, CSR blocks (host copies)
     int32_t k = 0, m_steps = 0, nritz = 0;
     double theta = 0.0;
@@ -91,6 +92,11 @@ struct slr_handle_s {
 };
 
 namespace slr {
+
+// Kernel launches of the library: a process-wide count, and the calling
+// thread's own count (a graph capture takes back what its thread captured).
+void count_launches(int64_t n);
+int64_t thread_launches();
 
 constexpr int kRedBlocks = 256;     // fixed grid of the deterministic reductions
 

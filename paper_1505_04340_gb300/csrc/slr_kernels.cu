@@ -17,6 +17,13 @@
 namespace slr {
 
 std::atomic<int64_t> g_kernel_launches{0};
+thread_local int64_t t_kernel_launches = 0;
+
+void count_launches(int64_t n) {
+    g_kernel_launches.fetch_add(n, std::memory_order_relaxed);
+    t_kernel_launches += n;
+}
+int64_t thread_launches() { return t_kernel_launches; }
 
 namespace {
 
@@ -585,7 +592,7 @@ __global__ void k_pcg_update_p(int32_t n, int32_t nrhs, double* p, const double*
 inline unsigned blocks_for(int64_t n, int t = kThreads) { return (unsigned)((n + t - 1) / t); }
 
 // every kernel launch of the library goes through this counter
-inline void counted(int n = 1) { g_kernel_launches.fetch_add(n, std::memory_order_relaxed); }
+inline void counted(int n = 1) { count_launches(n); }
 
 }  // namespace
 

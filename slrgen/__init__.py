@@ -265,3 +265,36 @@ def serving_specs(count=32, seed=3):
         k = (16, 32, 64)[int(u[i, 3] * 3)]
         specs.append(dict(dims=dims, boxes=boxes, k=k, matrix_seed=1000 + i))
     return specs
+
+
+def serving_problem(spec):
+    """The matrix of one serving spec: FV diffusion with coefficients log-uniform in [1e-2, 1e2]."""
+    d = spec["dims"]
+    name = ("3d" if len(d) == 3 else "2d") + f"-fv-{d[0]}^{len(d)}-p{int(np.prod(spec['boxes']))}-k{spec['k']}"
+    return make_problem(name, d, spec["boxes"], spec["k"], kind="fv", coef_range=(1e-2, 1e2),
+                        matrix_seed=spec["matrix_seed"])
+
+
+def serving_requests(count=256, seed=3, nspecs=32, rate=50.0):
+    """The request stream: ``count`` requests with Poisson arrivals at ``rate`` per second.
+
+    Request i asks for matrix ``spec`` (uniform over ``nspecs`` serving specs)
+    with ``nrhs`` in 1..8 right-hand sides; x* column j of request i is
+    uniform[-1,1) from stream ``rhs_seed + j``.  Inter-arrival gaps are
+    ``-log(1-u)/rate`` from stream ``seed + 1``; the first request arrives at 0.
+    Returns a list of dicts (rid, spec, nrhs, arrival, rhs_seed).
+    """
+    u = uniform01(seed + 1, 3 * count).reshape(count, 3)
+    gaps = -np.log1p(-u[:, 0]) / rate
+    arrival = np.concatenate([[0.0], np.cumsum(gaps[1:])])
+    out = []
+    for i in range(count):
+        out.append(dict(rid=i, spec=int(u[i, 1] * nspecs), nrhs=1 + int(u[i, 2] * 8),
+                        arrival=float(arrival[i]), rhs_seed=1_000_000 + 16 * i))
+    return out
+
+
+def request_rhs(prob, nrhs, rhs_seed):
+    """b = A x* for one request, x* columns uniform[-1,1) from ``rhs_seed + j``."""
+    xstar = np.stack([uniform_pm1(rhs_seed + j, prob.n) for j in range(nrhs)], axis=1)
+    return xstar, np.ascontiguousarray(csr_matvec(prob.rowptr, prob.colind, prob.val, xstar))
