@@ -74,7 +74,9 @@ typedef struct {
     int32_t reserved[6];    /* reserved[0]: CTAs per subdomain in the band solve (1, 2, 4;
                                0 = automatic).  reserved[1]: 1 = drive the CG loop from
                                the host (one synchronisation per iteration) instead of
-                               one CUDA graph per solve.  The rest must be 0.            */
+                               one CUDA graph per solve.  reserved[2]: shared-memory
+                               buffers the band solve streams its factor through (2..8;
+                               0 = automatic).  The rest must be 0.                      */
 } slr_opts;
 
 typedef struct {

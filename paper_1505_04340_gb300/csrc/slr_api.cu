@@ -110,6 +110,7 @@ slr_status upload_operator(slr_handle h, DevOperator<T>& op, bool with_band) {
     CS(upload(h, &op.band, hs.band));
     if (with_band) CS(upload(h, &op.bfac, hs.bfac));
     op.band_G = hs.band_G;
+    op.band_nbuf = h->opts.reserved[2];
     CS(dalloc(h, &op.err, 1));
     CK(cudaMemsetAsync(op.err, 0, sizeof(int32_t), h->stream));
     CS(upload(h, &op.e_rp, hs.e_rp));
@@ -383,9 +384,10 @@ slr_status setup_impl(slr_handle h, int32_t n, const int32_t* rowptr, const int3
         const int32_t req = h->opts.reserved[0];        // opts.band_split, 0 = automatic
         if (req == 1 || req == 2 || req == 4) {
             if ((wmx + req - 1) / req <= 256) G = req;
-        } else if (G == 1 && 2 * nparts <= nsm && wmx >= 32 && h->opts.precision == SLR_PREC_FP64) {
-            // the FP64 solve is bound by the SMs' FP64 units: use twice the SMs.
-            // The FP32 solve streams fast enough from one SM per subdomain.
+        } else if (G == 1 && 2 * nparts <= nsm && wmx >= 32) {
+            // a subdomain's planes are a dependent chain: with few subdomains two
+            // CTAs (a cluster) per subdomain put twice the SMs on it (measured
+            // faster in both precisions on 16^3 boxes; four CTAs need two waves)
             G = 2;
         }
         CS(host_band_factor(hs, G));
@@ -594,7 +596,8 @@ slr_status slr_setup(int32_t n, const int32_t* rowptr, const int32_t* colind, co
     if (opts) h->opts = *opts; else slr_default_opts(&h->opts);
     if (h->opts.k < 0 || h->opts.lanczos_steps < 0 || h->opts.nrhs_max < 0 || h->opts.nrhs_max > 64 ||
         (h->opts.precision != SLR_PREC_FP64 && h->opts.precision != SLR_PREC_MIXED) ||
-        (h->opts.theta_mode != SLR_THETA_LAMBDA_K1 && h->opts.theta_mode != SLR_THETA_ZERO)) {
+        (h->opts.theta_mode != SLR_THETA_LAMBDA_K1 && h->opts.theta_mode != SLR_THETA_ZERO) ||
+        h->opts.reserved[2] < 0 || h->opts.reserved[2] == 1 || h->opts.reserved[2] > 8) {
         set_error("invalid options");
         delete h;
         return SLR_ERR_INVALID_ARG;

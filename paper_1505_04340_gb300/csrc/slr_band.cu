@@ -9,16 +9,25 @@
 //   backward (L^T x = y):  t = y_J - O_{J+1}^T x_{J+1};    x_J = D_J^T t
 // All four products are "output row = sum over columns" of a triangular
 // matrix (O_J, D_J^T upper; D_J, O_J^T lower), each stored on its own.  Output
-// rows are dealt to the G CTAs of a cluster (r mod G = rank); each CTA's
-// slice of a block is packed column-major (column c: its rows r <= c for an
-// upper block, r >= c for a lower one), so a CTA streams exactly its bytes.
+// rows are dealt to the G CTAs of a cluster (r mod G = rank).  Each CTA's slice
+// of a block is tiled: row block rb (its slice rows 32 rb .. 32 rb + 31) keeps,
+// for every column that meets it, one segment of 32 values (zero outside the
+// triangle), row blocks one after the other, columns ascending.  A lane owns a
+// row and a segment is one coalesced 32-wide load, so the inner loop is a
+// shared load, a broadcast load and an FMA; the padding costs about 16 values
+// per column (14% of a 225-wide block).
 //
-// Each CTA streams its slices through a ring of kNBuf shared buffers with 1-D
-// bulk asynchronous copies completed on mbarriers (one thread issues,
-// everyone waits with a bounded spin that sets a device status word instead of
-// hanging).  Lanes own output rows, warps take columns round-robin, and the
-// per-warp partial sums are added once per phase.  The full input vector of a
-// phase is assembled in every CTA through distributed shared memory.
+// Each CTA streams its slices through a ring of `nbuf` shared buffers of `slot`
+// bytes (2 by default, filling the shared memory left over) with 1-D bulk
+// asynchronous copies of whole segments completed on "full" mbarriers.  Every
+// warp releases a buffer on its "empty" mbarrier when done with it; thread 0
+// refills a buffer once all warps have released it, so copies run ahead of the
+// slowest warp across planes and phases with no CTA-wide barrier per chunk.
+// Every wait is a bounded spin that sets a device status word instead of
+// hanging.  Warp w takes the columns c = w (mod 16) of every row block, so a
+// warp's partial sums (added once per phase) do not depend on the chunking.
+// The full input vector of a phase is assembled in every CTA through
+// distributed shared memory.
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
@@ -36,16 +45,21 @@ namespace {
 
 constexpr int kT = 512;            // threads per CTA (4 warps per SM sub-partition hide the load->FMA latency)
 constexpr int kW = kT / 32;        // warps per CTA
-constexpr int kNBuf = 3;           // ring slots
-constexpr int kChunk = 48 * 1024;  // bytes per ring slot
-constexpr int kMaxCh = 64;         // chunks per block
+constexpr int kMaxBuf = 8;         // ring slots at most
+constexpr int kMinBuf = 2;         // ring slots at least
+constexpr int kDefBuf = 2;         // ring slots unless the operator asks for another count
+                                   // (two large slots measured fastest: per-chunk latency dominates)
+constexpr int kMinSlot = 16 * 1024;   // bytes per ring slot at least
+constexpr size_t kSmemCap = 227 * 1024;   // opt-in shared memory per CTA on sm_100-class GPUs
 constexpr int kRB = 8;             // row blocks of 32: at most 256 rows per slice
 constexpr long long kSpin = 1ll << 24;   // bounded mbarrier wait (about a second)
 
 // ---- slice geometry (the host packer uses the same rules: band_* in slr_internal.h)
 __device__ __forceinline__ int slice_rows(int W, int G, int g) { return g < W ? (W - 1 - g) / G + 1 : 0; }
-__device__ __forceinline__ int cnt_O(int c, int G, int g) { return c >= g ? (c - g) / G + 1 : 0; }
-__device__ __forceinline__ int lr0_D(int q, int G, int g) { return q <= g ? 0 : (q - g + G - 1) / G; }
+__device__ __forceinline__ int seg_cU0(int W, int G, int g, int rb) { return min(W, G * 32 * rb + g); }
+__device__ __forceinline__ int seg_cL1(int W, int G, int g, int rb) {
+    return min(W, G * min(32 * rb + 31, slice_rows(W, G, g) - 1) + g + 1);
+}
 
 // ---- mbarrier / bulk copy PTX
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -91,6 +105,11 @@ __device__ __forceinline__ void cluster_barrier() {
     }
 }
 
+// Column c of every block goes to warp c mod kW whatever the chunk boundaries,
+// so each warp's partial sums, and the result, do not depend on the ring's
+// slot size (which varies with the right-hand sides per CTA).
+__device__ __forceinline__ int first_col(int lo, int warp) { return lo + ((warp - lo % kW) + kW) % kW; }
+
 struct Geom {
     int W, c, g, nrg;
     int nU, nL;
@@ -98,20 +117,16 @@ struct Geom {
 };
 
 // Block types: 0 O_J (upper, fwd), 1 D_J (lower, fwd), 2 O_J^T (lower, bwd), 3 D_J^T (upper, bwd).
-// Stream: forward D_0, (O_J, D_J) J = 1..c-1; backward D_{c-1}^T, (O_{J+1}^T, D_J^T) J = c-2..0.
-__device__ __forceinline__ void chunk_pos(const Geom& q, int k, int& type, int& plane, int& idx) {
-    const int per = q.nU + q.nL, half = q.nL + (q.c - 1) * per;
-    if (k < half) {
-        if (k < q.nL) { type = 1; plane = 0; idx = k; return; }
-        const int kk = k - q.nL, pr = kk / per, r = kk % per;
-        plane = 1 + pr;
-        if (r < q.nU) { type = 0; idx = r; } else { type = 1; idx = r - q.nU; }
-        return;
+// Stream order: forward D_0, (O_J, D_J) J = 1..c-1; backward D_{c-1}^T, then
+// (O_{J+1}^T, D_J^T) J = c-2..0 (O_{J+1}^T is stored with plane J+1).
+// next_block advances (type, plane) along that order; plane < 0 ends it.
+__device__ __forceinline__ void next_block(int c, int& type, int& plane) {
+    switch (type) {
+        case 1: if (plane + 1 < c) { type = 0; ++plane; } else { type = 3; plane = c - 1; } break;
+        case 0: type = 1; break;
+        case 3: if (plane > 0) type = 2; else plane = -1; break;
+        default: type = 3; --plane; break;
     }
-    const int k2 = k - half;
-    if (k2 < q.nU) { type = 3; plane = q.c - 1; idx = k2; return; }
-    const int kk = k2 - q.nU, pr = kk / per, r = kk % per;
-    if (r < q.nL) { type = 2; plane = q.c - 1 - pr; idx = r; } else { type = 3; plane = q.c - 2 - pr; idx = r - q.nL; }
 }
 
 __device__ __forceinline__ int64_t block_off(const Geom& q, int type) {
@@ -123,7 +138,7 @@ __device__ __forceinline__ int64_t block_off(const Geom& q, int type) {
 template <typename T, int NR, int G>
 __global__ void __launch_bounds__(kT, 1)
 k_band_solve2(const BandBlock* __restrict__ blocks, const T* __restrict__ fac, const T* in, int64_t ldi, T* out,
-              int64_t ldo, const T* base, int64_t ldb, int32_t* err) {
+              int64_t ldo, const T* base, int64_t ldb, int32_t* err, int nbuf, int slot) {
     extern __shared__ __align__(128) unsigned char smem[];
     const int sub = blockIdx.x / G;
     const int g = (G > 1) ? (int)cg::this_cluster().block_rank() : 0;
@@ -132,19 +147,19 @@ k_band_solve2(const BandBlock* __restrict__ blocks, const T* __restrict__ fac, c
     const int W = b.w, c = b.c, m = b.m;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
-    // ---- shared memory carve-up
-    unsigned char* ring = smem;                                     // kNBuf x kChunk
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem + kNBuf * kChunk);
-    int* colU = reinterpret_cast<int*>(full + kNBuf);              // [W+1]
-    int* colL = colU + (W + 1);                                    // [W+1]
-    int* chU = colL + (W + 1);                                     // [kMaxCh+1]
-    int* chL = chU + (kMaxCh + 1);                                 // [kMaxCh+1]
-    int* hdr = chL + (kMaxCh + 1);                                 // nU, nL
+    // ---- shared memory carve-up: barriers, tables and vectors, then the ring
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem);              // [kMaxBuf]
+    uint64_t* empty = full + kMaxBuf;                                 // [kMaxBuf]
+    int* segU = reinterpret_cast<int*>(empty + kMaxBuf);             // [kRB+1] first segment of row block rb
+    int* segL = segU + (kRB + 1);                                    // [kRB+1]
+    int* hdr = segL + (kRB + 1);                                     // nU, nL, segments per chunk
     uintptr_t vp = reinterpret_cast<uintptr_t>(hdr + 4);
     vp = (vp + 15) & ~uintptr_t(15);
     T* vst = reinterpret_cast<T*>(vp);              // [NR][W] y_{J-1} (fwd) / x_{J+1} (bwd), whole plane
     T* vt = vst + NR * W;                           // [NR][W] t, whole plane
     T* part = vt + NR * W;                          // [kW][NR][256] per-warp partial sums
+    uintptr_t rp = reinterpret_cast<uintptr_t>(part + kW * NR * 256);
+    unsigned char* ring = reinterpret_cast<unsigned char*>((rp + 127) & ~uintptr_t(127));   // nbuf x slot bytes
 
     Geom q;
     q.W = W;
@@ -156,65 +171,61 @@ k_band_solve2(const BandBlock* __restrict__ blocks, const T* __restrict__ fac, c
     q.PS = (int64_t)G * 2 * (b.SU + b.SL);
     q.base = b.foff + (int64_t)g * 2 * (b.SU + b.SL);
 
+    const int nrb = (q.nrg + 31) / 32;
     if (tid == 0) {
         int a = 0, d = 0;
-        for (int cc = 0; cc < W; ++cc) {
-            colU[cc] = a;
-            colL[cc] = d;
-            a += cnt_O(cc, G, g);
-            d += q.nrg - min(q.nrg, lr0_D(cc, G, g));
-        }
-        colU[W] = a;
-        colL[W] = d;
-        // greedy column chunks of at most kChunk - 32 bytes (room for 16-byte alignment)
-        const int budget = (kChunk - 32) / (int)sizeof(T);
-        for (int t = 0; t < 2; ++t) {
-            const int* col = t ? colL : colU;
-            int* ch = t ? chL : chU;
-            int n = 0, acc = 0;
-            ch[0] = 0;
-            for (int cc = 0; cc < W; ++cc) {
-                const int e = col[cc + 1] - col[cc];
-                if (acc > 0 && acc + e > budget) { ch[++n] = cc; acc = 0; }
-                acc += e;
+        for (int rb = 0; rb <= kRB; ++rb) {
+            segU[rb] = a;
+            segL[rb] = d;
+            if (rb < nrb) {
+                a += W - seg_cU0(W, G, g, rb);
+                d += seg_cL1(W, G, g, rb);
             }
-            ch[++n] = W;
-            hdr[t] = n;
         }
-        for (int i = 0; i < kNBuf; ++i) mbar_init(&full[i], 1);
+        const int per = max(1, slot / (32 * (int)sizeof(T)));   // whole segments per chunk
+        hdr[0] = (a + per - 1) / per;
+        hdr[1] = (d + per - 1) / per;
+        hdr[2] = per;
+        for (int i = 0; i < nbuf; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], kW);
+        }
         fence_mbar_init();
     }
     __syncthreads();
     q.nU = hdr[0];
     q.nL = hdr[1];
-    const int total = 2 * (q.nL + (c - 1) * (q.nU + q.nL));
+    const int per = hdr[2];
+    // forward: D_0 (lower), then (O_J upper, D_J lower); backward: D_{c-1}^T (upper), then (O^T lower, D^T upper)
+    const int total = q.nL + q.nU + 2 * (c - 1) * (q.nU + q.nL);
 
-    auto src_of = [&](int k, int& type, int& ix, int64_t& e0, int64_t& e1) {
-        int pl;
-        chunk_pos(q, k, type, pl, ix);
+    // first and one-past-last element of chunk ix of a block: segments [ix per, ...)
+    auto chunk_src = [&](int type, int plane, int ix, int64_t& e0, int64_t& e1) {
         const bool up = (type == 0 || type == 3);
-        const int* col = up ? colU : colL;
-        const int* ch = up ? chU : chL;
-        e0 = q.base + (int64_t)pl * q.PS + block_off(q, type) + col[ch[ix]];
-        e1 = e0 + (col[ch[ix + 1]] - col[ch[ix]]);
+        const int nseg = up ? segU[kRB] : segL[kRB];
+        e0 = q.base + (int64_t)plane * q.PS + block_off(q, type) + (int64_t)ix * per * 32;
+        e1 = e0 + (int64_t)(min(per, nseg - ix * per)) * 32;
     };
-    auto issue = [&](int k) {   // thread 0 only
-        int type, ix;
+    // thread 0 issues chunks in stream order; its cursor is the next chunk to issue
+    int cur_type = 1, cur_plane = 0, cur_ix = 0, issued = 0;
+    auto issue_next = [&]() {
+        if (cur_plane < 0) return;                 // past the end of the stream: nothing to copy
         int64_t e0, e1;
-        src_of(k, type, ix, e0, e1);
-        const uintptr_t a0 = reinterpret_cast<uintptr_t>(fac + e0), a1 = reinterpret_cast<uintptr_t>(fac + e1);
-        const uintptr_t al0 = a0 & ~uintptr_t(15), al1 = (a1 + 15) & ~uintptr_t(15);
-        uint64_t* bar = &full[k % kNBuf];
-        if (al1 > al0) {
-            mbar_arrive_expect_tx(bar, (uint32_t)(al1 - al0));
-            bulk_g2s(ring + (k % kNBuf) * kChunk, reinterpret_cast<const void*>(al0), (uint32_t)(al1 - al0), bar);
-        } else {
-            mbar_arrive(bar);
+        chunk_src(cur_type, cur_plane, cur_ix, e0, e1);
+        // whole segments of 32 values: start and size are multiples of 128 bytes
+        const uint32_t bytes = (uint32_t)((e1 - e0) * (int64_t)sizeof(T));
+        const int sl = issued % nbuf;
+        uint64_t* bar = &full[sl];
+        mbar_arrive_expect_tx(bar, bytes);
+        bulk_g2s(ring + (size_t)sl * slot, fac + e0, bytes, bar);
+        ++issued;
+        const int nch = (cur_type == 0 || cur_type == 3) ? q.nU : q.nL;
+        if (++cur_ix == nch) {
+            cur_ix = 0;
+            next_block(c, cur_type, cur_plane);
         }
     };
-    auto wait_full = [&](int k) {
-        uint64_t* bar = &full[k % kNBuf];
-        const uint32_t par = (uint32_t)((k / kNBuf) & 1);
+    auto wait_bar = [&](uint64_t* bar, uint32_t par) {
         long long it = 0;
         while (!mbar_try_wait(bar, par)) {
             if (++it > kSpin) {
@@ -223,11 +234,20 @@ k_band_solve2(const BandBlock* __restrict__ blocks, const T* __restrict__ fac, c
             }
         }
     };
-    auto release = [&](int k) {   // everyone is done with chunk k's slot: refill it
-        __syncthreads();
-        if (tid == 0 && k + kNBuf < total) {
+    // chunk k's data has landed (the (k / nbuf)-th fill of its slot)
+    auto wait_full = [&](int k) { wait_bar(&full[k % nbuf], (uint32_t)((k / nbuf) & 1)); };
+    // this warp is done with chunk k's slot
+    auto release = [&](int k) {
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[k % nbuf]);
+    };
+    // thread 0, before consuming chunk k: once every warp has released chunk
+    // k - 1, its slot takes the next chunk of the stream
+    auto refill = [&](int k) {
+        if (tid == 0 && k >= 1 && issued < total) {
+            wait_bar(&empty[(k - 1) % nbuf], (uint32_t)(((k - 1) / nbuf) & 1));
             fence_proxy_async();
-            issue(k + kNBuf);
+            issue_next();
         }
     };
     auto peer = [&](T* p, int r) -> T* {
@@ -236,77 +256,41 @@ k_band_solve2(const BandBlock* __restrict__ blocks, const T* __restrict__ fac, c
     };
 
     if (tid == 0)
-        for (int k = 0; k < kNBuf && k < total; ++k) issue(k);
+        while (issued < nbuf && issued < total) issue_next();
     // every CTA of the cluster is running before anyone stores into a peer's shared memory
     cluster_barrier<G>();
 
     int k = 0;
     T acc[kRB][NR];
     // acc[rb][j] += sum over the chunks of one block of M[lr][cc] * vin[j][cc], lanes = rows
-    auto run_block = [&](bool upper, const T* vin) {
+    // acc[rb][j] = sum over the block's segments of row block rb of seg[lane] * vin[j][column]
+    auto run_block = [&](int type, int plane, const T* vin) {
+        const bool upper = (type == 0 || type == 3);
 #pragma unroll
         for (int rb = 0; rb < kRB; ++rb)
 #pragma unroll
             for (int j = 0; j < NR; ++j) acc[rb][j] = T(0);
         const int nch = upper ? q.nU : q.nL;
-        const int* col = upper ? colU : colL;
-        const int* ch = upper ? chU : chL;
+        const int* seg = upper ? segU : segL;
         for (int ix = 0; ix < nch; ++ix, ++k) {
+            refill(k);
             wait_full(k);
-            int type, ixx;
-            int64_t e0, e1;
-            src_of(k, type, ixx, e0, e1);
-            const int shift = (int)((reinterpret_cast<uintptr_t>(fac + e0) & 15) / sizeof(T));
-            const T* P = reinterpret_cast<const T*>(ring + (k % kNBuf) * kChunk) + shift - col[ch[ix]];
-            const int ca = ch[ix], cb = ch[ix + 1];
-            if constexpr (sizeof(T) == 8) {
-                // FP64: row block outer.  Row block rb (own rows 32 rb .. 32 rb + 31)
-                // meets column cc of an upper block iff cc >= G (32 rb) + g; a lower
-                // block holds rows >= lr0(cc), so rb meets columns cc <= G (32 rb + 31) + g.
-                // Separate loops per rb keep every DFMA unpredicated (an if-converted
-                // rb loop would issue all kRB of them per column on the slow FP64 pipe,
-                // which serves each SM sub-partition at a fixed rate).
+            const int s0 = ix * per, s1 = min(s0 + per, seg[kRB]);
+            const T* P = reinterpret_cast<const T*>(ring + (size_t)(k % nbuf) * slot);
 #pragma unroll
-                for (int rb = 0; rb < kRB; ++rb) {
-                    if (rb * 32 >= q.nrg) break;
-                    const int lr = rb * 32 + lane;
-                    const int c0 = max(ca, upper ? G * (rb * 32) + g : ca);
-                    const int c1 = upper ? cb : min(cb, G * (rb * 32 + 31) + g + 1);
-                    int cc = ca + warp + ((c0 > ca + warp) ? ((c0 - ca - warp + kW - 1) / kW) * kW : 0);
-                    auto term = [&](int c) {
-                        const int lo = upper ? 0 : min(q.nrg, lr0_D(c, G, g));
-                        const int hi = upper ? cnt_O(c, G, g) : q.nrg;
-                        const T a = (lr >= lo && lr < hi) ? P[col[c] - lo + lr] : T(0);
+            for (int rb = 0; rb < kRB; ++rb) {
+                if (rb >= nrb) break;
+                const int sa = max(s0, seg[rb]), sb = min(s1, seg[rb + 1]);
+                if (sa >= sb) continue;
+                const int cb0 = upper ? seg_cU0(W, G, g, rb) : 0;       // column of segment seg[rb]
+                const int ca = cb0 + (sa - seg[rb]), ce = cb0 + (sb - seg[rb]);
+                int cc = first_col(ca, warp);
+                const T* Ps = P + (sa - s0 + (cc - ca)) * 32 + lane;
+#pragma unroll 2
+                for (; cc < ce; cc += kW, Ps += kW * 32) {
+                    const T a = *Ps;
 #pragma unroll
-                        for (int j = 0; j < NR; ++j) acc[rb][j] = fma(a, vin[j * W + c], acc[rb][j]);
-                    };
-                    for (; cc + kW < c1; cc += 2 * kW) {
-                        term(cc);
-                        term(cc + kW);
-                    }
-                    if (cc < c1) term(cc);
-                }
-            } else {
-                // FP32: column outer, row blocks inner (the FP32 pipe absorbs the
-                // predicated-off lanes; this order issues the fewest instructions)
-                for (int cc = ca + warp; cc < cb; cc += kW) {
-                    const int lo = upper ? 0 : min(q.nrg, lr0_D(cc, G, g));
-                    const int hi = upper ? cnt_O(cc, G, g) : q.nrg;
-                    const T* Pc = P + col[cc] - lo;
-                    T v[NR];
-#pragma unroll
-                    for (int j = 0; j < NR; ++j) v[j] = vin[j * W + cc];
-#pragma unroll
-                    for (int rb = 0; rb < kRB; ++rb) {
-                        if (rb * 32 + 32 > lo && rb * 32 < hi) {
-                            const int lr = rb * 32 + lane;
-                            if (lr >= lo && lr < hi) {
-                                const T a = Pc[lr];
-#pragma unroll
-                                for (int j = 0; j < NR; ++j) acc[rb][j] += a * v[j];
-                            }
-                        }
-                    }
+                    for (int j = 0; j < NR; ++j) acc[rb][j] = fma(a, vin[j * W + cc], acc[rb][j]);
                 }
             }
             release(k);
@@ -328,77 +312,102 @@ k_band_solve2(const BandBlock* __restrict__ blocks, const T* __restrict__ fac, c
         return s;
     };
 
+    // Each thread owns at most one output row per plane (a slice has at most
+    // 256 rows): its right-hand side (forward) or forward result (backward) is
+    // loaded before the block product so the load is off the plane-to-plane chain.
+    const bool owner = tid < q.nrg;
+    const int own_r = tid * G + g;
     // =================================================================== forward
     for (int J = 0; J < c; ++J) {
-        if (J > 0) run_block(true, vst); else zero_part();                 // O_J y_{J-1}
-        for (int lr = tid; lr < q.nrg; lr += kT) {
-            const int r = lr * G + g, row = J * W + r;
+        const int row = J * W + own_r;
+        T pre[NR];
+#pragma unroll
+        for (int j = 0; j < NR; ++j) pre[j] = (owner && row < m) ? in[b.row0 + row + j * ldi] : T(0);
+        if (J > 0) run_block(0, J, vst); else zero_part();                 // O_J y_{J-1}
+        if (owner) {
 #pragma unroll
             for (int j = 0; j < NR; ++j) {
-                const T f = row < m ? in[b.row0 + row + j * ldi] : T(0);
-                const T t = f - part_sum(lr, j);
+                const T t = pre[j] - part_sum(tid, j);
 #pragma unroll
-                for (int pr = 0; pr < G; ++pr) peer(vt, pr)[j * W + r] = t;
+                for (int pr = 0; pr < G; ++pr) peer(vt, pr)[j * W + own_r] = t;
             }
         }
         cluster_barrier<G>();
-        run_block(false, vt);                                              // D_J t
-        for (int lr = tid; lr < q.nrg; lr += kT) {
-            const int r = lr * G + g, row = J * W + r;
+        run_block(1, J, vt);                                               // D_J t
+        if (owner) {
 #pragma unroll
             for (int j = 0; j < NR; ++j) {
-                const T y = part_sum(lr, j);
+                const T y = part_sum(tid, j);
                 if (row < m) out[b.row0 + row + j * ldo] = y;
 #pragma unroll
-                for (int pr = 0; pr < G; ++pr) peer(vst, pr)[j * W + r] = y;
+                for (int pr = 0; pr < G; ++pr) peer(vst, pr)[j * W + own_r] = y;
             }
         }
         cluster_barrier<G>();
     }
     // =================================================================== backward
     for (int J = c - 1; J >= 0; --J) {
-        if (J < c - 1) run_block(false, vst); else zero_part();            // O_{J+1}^T x_{J+1}
-        for (int lr = tid; lr < q.nrg; lr += kT) {
-            const int r = lr * G + g, row = J * W + r;
+        const int row = J * W + own_r;
+        const int64_t gi = b.row0 + row;
+        T pre[NR], bs[NR];
+#pragma unroll
+        for (int j = 0; j < NR; ++j) {
+            pre[j] = (owner && row < m) ? out[gi + j * ldo] : T(0);
+            bs[j] = (owner && row < m && base) ? base[gi + j * ldb] : T(0);
+        }
+        if (J < c - 1) run_block(2, J + 1, vst); else zero_part();         // O_{J+1}^T x_{J+1}
+        if (owner) {
 #pragma unroll
             for (int j = 0; j < NR; ++j) {
-                const T y = row < m ? out[b.row0 + row + j * ldo] : T(0);
-                const T t = y - part_sum(lr, j);
+                const T t = pre[j] - part_sum(tid, j);
 #pragma unroll
-                for (int pr = 0; pr < G; ++pr) peer(vt, pr)[j * W + r] = t;
+                for (int pr = 0; pr < G; ++pr) peer(vt, pr)[j * W + own_r] = t;
             }
         }
         cluster_barrier<G>();
-        run_block(true, vt);                                               // D_J^T t
-        for (int lr = tid; lr < q.nrg; lr += kT) {
-            const int r = lr * G + g, row = J * W + r;
+        run_block(3, J, vt);                                               // D_J^T t
+        if (owner) {
 #pragma unroll
             for (int j = 0; j < NR; ++j) {
-                const T x = part_sum(lr, j);
-                if (row < m) {
-                    const int64_t gi = b.row0 + row;
-                    out[gi + j * ldo] = base ? base[gi + j * ldb] - x : x;
-                }
+                const T x = part_sum(tid, j);
+                if (row < m) out[gi + j * ldo] = base ? bs[j] - x : x;
 #pragma unroll
-                for (int pr = 0; pr < G; ++pr) peer(vst, pr)[j * W + r] = x;
+                for (int pr = 0; pr < G; ++pr) peer(vst, pr)[j * W + own_r] = x;
             }
         }
         cluster_barrier<G>();
     }
 }
 
-size_t band_smem_bytes(int32_t wmax, int32_t G, int32_t nr, size_t elem) {
-    (void)G;
-    size_t fixed = (size_t)kNBuf * kChunk + kNBuf * 8 + 2 * (wmax + 1) * 4 + 2 * (kMaxCh + 1) * 4 + 16 + 16;
-    size_t vec = (size_t)(2 * nr * wmax + kW * nr * 256) * elem;
-    return fixed + vec;
+// Shared memory besides the ring (barriers, column tables, vectors, partials,
+// the ring's alignment), for planes of at most wmax rows.
+static size_t band_fixed_bytes(int32_t wmax, int32_t nr, size_t elem) {
+    (void)wmax;
+    const size_t head = 2 * kMaxBuf * 8 + 2 * (kRB + 1) * 4 + 16 + 16;
+    const size_t vec = (size_t)(2 * nr * wmax + kW * nr * 256) * elem;
+    return head + vec + 128;
+}
+
+bool band_ring(int32_t wmax, int32_t nr, size_t elem, int32_t nbuf_req, int32_t* nbuf, int32_t* slot) {
+    const size_t fx = band_fixed_bytes(wmax, nr, elem);
+    if (fx + (size_t)kMinBuf * kMinSlot > kSmemCap) return false;
+    const size_t avail = kSmemCap - fx;
+    int32_t n = nbuf_req > 0 ? nbuf_req : kDefBuf;
+    n = std::max(kMinBuf, std::min<int32_t>(n, kMaxBuf));
+    while (n > kMinBuf && avail / n < (size_t)kMinSlot) --n;
+    *nbuf = n;
+    *slot = (int32_t)((avail / n) & ~size_t(127));
+    return true;
+}
+
+size_t band_smem_bytes(int32_t wmax, int32_t nr, size_t elem, int32_t nbuf, int32_t slot) {
+    return band_fixed_bytes(wmax, nr, elem) + (size_t)nbuf * slot;
 }
 
 namespace {
 template <typename T, int NR, int G>
 cudaError_t band_launch(const DevOperator<T>& op, int32_t p, int32_t wmax, const T* in, int64_t ldi, T* out,
                         int64_t ldo, const T* base, int64_t ldb, cudaStream_t st) {
-    const size_t smem = band_smem_bytes(wmax, G, NR, sizeof(T));
     auto kern = k_band_solve2<T, NR, G>;
     // The dynamic shared-memory limit of a kernel is process-wide state on its
     // device.  It is raised once, to the device's opt-in maximum, so that
@@ -420,6 +429,9 @@ cudaError_t band_launch(const DevOperator<T>& op, int32_t p, int32_t wmax, const
             raised |= 1ull << dev;
         }
     }
+    int32_t nbuf = 0, slot = 0;
+    if (!band_ring(wmax, NR, sizeof(T), op.band_nbuf, &nbuf, &slot)) return cudaErrorInvalidValue;
+    const size_t smem = band_smem_bytes(wmax, NR, sizeof(T), nbuf, slot);
     cudaError_t e;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(p * G);
@@ -433,7 +445,7 @@ cudaError_t band_launch(const DevOperator<T>& op, int32_t p, int32_t wmax, const
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = G > 1 ? 1 : 0;
-    e = cudaLaunchKernelEx(&cfg, kern, op.band, op.bfac, in, ldi, out, ldo, base, ldb, op.err);
+    e = cudaLaunchKernelEx(&cfg, kern, op.band, op.bfac, in, ldi, out, ldo, base, ldb, op.err, (int)nbuf, (int)slot);
     count_launches(1);
     return e;
 }
@@ -453,12 +465,12 @@ template <typename T>
 cudaError_t launch_band_solve(const DevOperator<T>& op, int32_t p, int32_t wmax, const T* in, int64_t ldi, T* out,
                               int64_t ldo, const T* base, int64_t ldb, int32_t nrhs, cudaStream_t st) {
     if (p == 0 || wmax == 0) return cudaSuccess;
-    const size_t cap = 227 * 1024;
     for (int32_t c = 0; c < nrhs;) {
         const int32_t left = nrhs - c;
         int nr = 1;
-        if (left >= 4 && band_smem_bytes(wmax, op.band_G, 4, sizeof(T)) <= cap) nr = 4;
-        else if (left >= 2 && band_smem_bytes(wmax, op.band_G, 2, sizeof(T)) <= cap) nr = 2;
+        int32_t nb, sl;
+        if (left >= 4 && band_ring(wmax, 4, sizeof(T), 0, &nb, &sl)) nr = 4;
+        else if (left >= 2 && band_ring(wmax, 2, sizeof(T), 0, &nb, &sl)) nr = 2;
         const T* bs = base ? base + c * ldb : nullptr;
         cudaError_t e;
         if (nr == 4) e = band_launch_g<T, 4>(op, p, wmax, in + c * ldi, ldi, out + c * ldo, ldo, bs, ldb, st);

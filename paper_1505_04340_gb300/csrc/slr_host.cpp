@@ -212,18 +212,18 @@ slr_status host_band_factor(HostSetup& hs, int32_t G) {
         b.row0 = r0;
         b.w = m ? std::max(w, 1) : 0;
         b.c = m ? (m + b.w - 1) / b.w : 0;
-        int so = 0, sd = 0;
+        int so = 0, sd = 0;   // segments of the widest slice
         for (int g = 0; g < G; ++g) {
-            int a = 0, d = 0, nrg = band_slice_rows(b.w, G, g);
-            for (int cc = 0; cc < b.w; ++cc) {
-                a += band_cnt_O(cc, G, g);
-                d += nrg - std::min(nrg, band_lr0_D(cc, G, g));
+            int a = 0, d = 0;
+            for (int rb = 0; rb < band_nrb(b.w, G, g); ++rb) {
+                a += b.w - band_cU0(b.w, G, g, rb);
+                d += band_cL1(b.w, G, g, rb);
             }
             so = std::max(so, a);
             sd = std::max(sd, d);
         }
-        b.SU = (so + 31) / 32 * 32;
-        b.SL = (sd + 31) / 32 * 32;
+        b.SU = 32 * so;
+        b.SL = 32 * sd;
         b.foff = off;
         off += (int64_t)b.c * G * 2 * (b.SU + b.SL);
         hs.wmax = std::max(hs.wmax, b.w);
@@ -284,18 +284,22 @@ slr_status host_band_factor(HostSetup& hs, int32_t G) {
                 double* Lb = Lf + b.SL;                                 // O_J^T    (lower)
                 double* Ub = Lb + b.SL;                                 // D_J^T    (upper)
                 const int nrg = band_slice_rows(W, G, g);
-                int64_t u = 0, d = 0;
-                for (int cc = 0; cc < W; ++cc) {
-                    for (int lr = 0; lr < band_cnt_O(cc, G, g); ++lr, ++u) {   // rows r <= cc
-                        const int r = lr * G + g, l = J * W + r;
-                        Uf[u] = (J > 0 && l < m) ? Lat(l, (J - 1) * W + cc) : 0.0;   // O_J[r][cc]
-                        Ub[u] = X[(size_t)cc * W + r];                                // D_J^{-1}[cc][r]
-                    }
-                    for (int lr = std::min(nrg, band_lr0_D(cc, G, g)); lr < nrg; ++lr, ++d) {   // rows r >= cc
-                        const int r = lr * G + g, lc = J * W + cc;
-                        Lf[d] = X[(size_t)r * W + cc];                                // D_J^{-1}[r][cc]
-                        Lb[d] = (J > 0 && lc < m) ? Lat(lc, (J - 1) * W + r) : 0.0;   // O_J[cc][r]
-                    }
+                int64_t su = 0, sl = 0;   // next upper / lower segment
+                for (int rb = 0; rb < band_nrb(W, G, g); ++rb) {
+                    for (int cc = band_cU0(W, G, g, rb); cc < W; ++cc, ++su)      // upper: rows r <= cc
+                        for (int e = 0; e < 32; ++e) {
+                            const int lr = 32 * rb + e, r = lr * G + g, l = J * W + r;
+                            if (lr >= nrg || r > cc) continue;
+                            Uf[su * 32 + e] = (J > 0 && l < m) ? Lat(l, (J - 1) * W + cc) : 0.0;   // O_J[r][cc]
+                            Ub[su * 32 + e] = X[(size_t)cc * W + r];                             // D_J^{-1}[cc][r]
+                        }
+                    for (int cc = 0; cc < band_cL1(W, G, g, rb); ++cc, ++sl)      // lower: rows r >= cc
+                        for (int e = 0; e < 32; ++e) {
+                            const int lr = 32 * rb + e, r = lr * G + g, lc = J * W + cc;
+                            if (lr >= nrg || r < cc) continue;
+                            Lf[sl * 32 + e] = X[(size_t)r * W + cc];                             // D_J^{-1}[r][cc]
+                            Lb[sl * 32 + e] = (J > 0 && lc < m) ? Lat(lc, (J - 1) * W + r) : 0.0;   // O_J[cc][r]
+                        }
                 }
             }
         }

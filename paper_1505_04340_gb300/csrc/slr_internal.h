@@ -2,6 +2,7 @@
 // device-resident handle.  Not part of the public ABI (see include/slr.h).
 #pragma once
 
+#include <algorithm>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -31,14 +32,25 @@ struct BandBlock {
     int32_t c = 0;        // planes, c * W >= m
     int32_t row0 = 0;     // first row of B_i inside u (DD interior order)
     int64_t foff = 0;     // offset of plane 0 in the factor array (elements)
-    int32_t SU = 0;       // elements of one upper slice block (padded to 32)
-    int32_t SL = 0;       // elements of one lower slice block (padded to 32)
+    int32_t SU = 0;       // elements of one upper slice block (32 per segment, widest slice)
+    int32_t SL = 0;       // elements of one lower slice block (32 per segment, widest slice)
 };
 
 // Slice geometry of the band layout (host packer and device kernel agree on it).
 inline int band_slice_rows(int W, int G, int g) { return g < W ? (W - 1 - g) / G + 1 : 0; }
 inline int band_cnt_O(int c, int G, int g) { return c >= g ? (c - g) / G + 1 : 0; }
 inline int band_lr0_D(int q, int G, int g) { return q <= g ? 0 : (q - g + G - 1) / G; }
+// Tiled slices.  Row block rb holds slice rows 32 rb .. 32 rb + 31.  In an
+// upper block (O_J, D_J^T) it meets columns [band_cU0, W); in a lower block
+// (D_J, O_J^T) columns [0, band_cL1).  Each (row block, column) pair is one
+// segment of 32 values (zero outside the triangle and past the slice), stored
+// row block by row block, columns ascending.
+inline int band_nrb(int W, int G, int g) { return (band_slice_rows(W, G, g) + 31) / 32; }
+inline int band_cU0(int W, int G, int g, int rb) { return std::min(W, G * 32 * rb + g); }
+inline int band_cL1(int W, int G, int g, int rb) {
+    const int L = std::min(32 * rb + 31, band_slice_rows(W, G, g) - 1);
+    return std::min(W, G * L + g + 1);
+}
 
 // Supernodal Cholesky factor of the interface matrix C (Eq. 3.1) in a
 // nested-dissection order.  Supernode J owns factor positions [c0[J], c0[J+1]).

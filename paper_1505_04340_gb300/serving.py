@@ -302,14 +302,21 @@ class SolveServer:
 
 
 def latency_stats(reqs):
-    """p50/p99 latency (all requests, and those whose matrix was already resident) and throughput."""
+    """Latency percentiles (all requests, and those whose matrix was already
+    resident), queueing and service time, CG iterations and throughput."""
     served = [r for r in reqs if r.status in (0, 5)]
-    lat = np.array([r.latency for r in served]) * 1e3
-    warm = np.array([r.latency for r in served if not r.cold]) * 1e3
+    ms = lambda v: np.array(v, dtype=np.float64) * 1e3
+    lat = ms([r.latency for r in served])
+    warm = ms([r.latency for r in served if not r.cold])
+    queue = ms([r.start - r.arrival for r in served])
+    service = ms([r.done - r.start for r in served])
+    its = np.concatenate([np.atleast_1d(r.iterations) for r in served]) if served else np.zeros(0)
     span = max(r.done for r in served) - min(r.arrival for r in served)
     cols = sum(r.ncols for r in served)
     pct = lambda a, q: float(np.percentile(a, q)) if len(a) else None
     return {"requests": len(reqs), "served": len(served), "solves": cols,
             "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99),
             "warm_p50_ms": pct(warm, 50), "warm_p99_ms": pct(warm, 99),
+            "queue_p50_ms": pct(queue, 50), "service_p50_ms": pct(service, 50), "service_p99_ms": pct(service, 99),
+            "iterations_mean": float(its.mean()) if len(its) else None, "iterations_max": int(its.max()) if len(its) else None,
             "solves_per_s": cols / span, "requests_per_s": len(served) / span, "span_s": span}

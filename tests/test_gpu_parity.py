@@ -47,8 +47,15 @@ PROBLEMS = {
 }
 
 
+# band-layout cases run only by the ring/split test: 14 x 14 planes split in 2 or
+# 4 slices, where the upper and lower blocks break into different chunk counts
+EXTRA = {
+    "3d-196": ((30, 30, 8), (2, 2, 1), 6, "laplacian", None),
+}
+
+
 def make(name, nrhs=1):
-    dims, boxes, k, kind, cr = PROBLEMS[name]
+    dims, boxes, k, kind, cr = PROBLEMS[name] if name in PROBLEMS else EXTRA[name]
     return slrgen.make_problem(name, dims, boxes, k, kind=kind, coef_range=cr, nrhs=nrhs)
 
 
@@ -81,6 +88,20 @@ def test_bsolve_parity(name, precision):
     t = g.bsolve(cu(f)).cpu().numpy()
     want = o.bsolve.solve(f)
     assert rel(t, want) <= (TOL64 if precision == "fp64" else TOL32)
+
+
+@pytest.mark.parametrize("name,split,slots", [("3d-196", 2, 5), ("3d-196", 4, 5), ("3d-196", 1, 2),
+                                               ("3d-196", 2, 8), ("3d-wide", 2, 8), ("3d-wide", 4, 3),
+                                               ("fv-ragged", 1, 8), ("fv-ragged", 2, 2)])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_bsolve_ring_and_split(name, split, slots, precision):
+    """B^{-1} with the factor streamed through 2..8 buffers and 1, 2 or 4 CTAs per subdomain."""
+    P = make(name)
+    o = oracle(name)
+    g = gpu_handle(P, precision, band_split=split, band_slots=slots)
+    f = np.random.default_rng(2).standard_normal((o.order.n_I, 4))
+    t = g.bsolve(cu(f)).cpu().numpy()
+    assert rel(t, o.bsolve.solve(f)) <= (TOL64 if precision == "fp64" else TOL32)
 
 
 @pytest.mark.parametrize("name", [n for n in PROBLEMS if n != "one-part"])
