@@ -378,7 +378,14 @@ def run_ours(args):
                                            np.linalg.norm(results["x64"]))
         # apply alone (apply GB/s) and the dominant kernel alone (K1 band solve)
         info = h.get_info()
-        r = torch.randn(P.n, dtype=torch.float64, device=dev)
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(7)
+        r = torch.randn(P.n, dtype=torch.float64, device=dev, generator=gen)
+        z1 = h.apply(r).cpu().numpy()
+        if prec == "fp64":
+            results["z64"] = z1
+        else:       # the FP32 apply against the FP64 apply on the same vector
+            results["apply_rel_diff"] = float(np.abs(z1 - results["z64"]).max() / np.abs(results["z64"]).max())
         na = max(10, args.steps)
         for _ in range(3):
             h.apply(r)
@@ -478,6 +485,7 @@ def run_ours(args):
         "apply": {"us": r64["apply_us"], "gbs": r64["apply_gbs"], "bytes": r64["bytes_per_apply"]},
         "mixed": {"value": rm["solves_per_s"], "ms_per_step": rm["ms_per_step"], "iterations": rm["iters"],
                   "p50_ms": rm["p50_ms"], "p99_ms": rm["p99_ms"], "x_rel_diff_vs_fp64": results["x_mixed_err"],
+                  "apply_rel_diff_vs_fp64": results["apply_rel_diff"],
                   "apply_us": rm["apply_us"], "apply_gbs": rm["apply_gbs"],
                   "band_solve_us": rm["band_us"], "band_gbs": mixed_band_gbs,
                   "band_frac_hbm": mixed_band_gbs / hbm, "dtype": "f32 apply / f64 outer"},

@@ -76,7 +76,10 @@ typedef struct {
                                the host (one synchronisation per iteration) instead of
                                one CUDA graph per solve.  reserved[2]: shared-memory
                                buffers the band solve streams its factor through (2..8;
-                               0 = automatic).  The rest must be 0.                      */
+                               0 = automatic).  reserved[3]: 1 = solve with C's factor
+                               in one cooperative launch per direction (grid barriers
+                               between level steps) instead of one launch per step.
+                               The rest must be 0.                                      */
 } slr_opts;
 
 typedef struct {

@@ -139,6 +139,30 @@ slr_status upload_operator(slr_handle h, DevOperator<T>& op, bool with_band) {
     d.lev_sn_ptr = c.lev_sn_ptr;
     d.lev_small = c.lev_small;
     CS(upload(h, &d.lev_sn, c.lev_sn));
+    // the persistent solves read the level tables on the device; they run
+    // nsteps dependent steps (a grid barrier between consecutive ones)
+    CS(upload(h, &d.d_lev_task_ptr, c.lev_task_ptr));
+    CS(upload(h, &d.d_lev_ptask_ptr, c.lev_ptask_ptr));
+    CS(upload(h, &d.d_lev_sn_ptr, c.lev_sn_ptr));
+    CS(upload(h, &d.d_lev_small, c.lev_small));
+    d.nsteps_fwd = d.nsteps_bwd = 0;
+    d.max_cta_tasks = 1;
+    for (int32_t l = 0; l < c.nlev; ++l) {
+        const int32_t nt = c.lev_task_ptr[l + 1] - c.lev_task_ptr[l], np = c.lev_ptask_ptr[l + 1] - c.lev_ptask_ptr[l];
+        const int32_t ns = c.lev_sn_ptr[l + 1] - c.lev_sn_ptr[l];
+        if (c.lev_small[l]) {
+            d.nsteps_fwd += ns > 0;
+            d.nsteps_bwd += ns > 0;
+            d.max_cta_tasks = std::max(d.max_cta_tasks, ns);
+            continue;
+        }
+        d.nsteps_fwd += (nt > 0 ? 2 : 0) + (np > 0 ? 1 : 0);
+        d.nsteps_bwd += nt > 0 ? 2 : 0;
+        d.max_cta_tasks = std::max({d.max_cta_tasks, nt, np});
+    }
+    CS(dalloc(h, &d.bar, 1));
+    d.err = op.err;
+    d.per_level = h->opts.reserved[3] != 1;   // per-level launches unless the persistent solve is asked for
     d.nrow = (int64_t)c.rows.size();
     d.max_n = 1;
     for (int32_t J = 0; J < c.ns; ++J) d.max_n = std::max(d.max_n, c.c0[J + 1] - c.c0[J]);
@@ -597,7 +621,8 @@ slr_status slr_setup(int32_t n, const int32_t* rowptr, const int32_t* colind, co
     if (h->opts.k < 0 || h->opts.lanczos_steps < 0 || h->opts.nrhs_max < 0 || h->opts.nrhs_max > 64 ||
         (h->opts.precision != SLR_PREC_FP64 && h->opts.precision != SLR_PREC_MIXED) ||
         (h->opts.theta_mode != SLR_THETA_LAMBDA_K1 && h->opts.theta_mode != SLR_THETA_ZERO) ||
-        h->opts.reserved[2] < 0 || h->opts.reserved[2] == 1 || h->opts.reserved[2] > 8) {
+        h->opts.reserved[2] < 0 || h->opts.reserved[2] == 1 || h->opts.reserved[2] > 8 ||
+        h->opts.reserved[3] < 0 || h->opts.reserved[3] > 1) {
         set_error("invalid options");
         delete h;
         return SLR_ERR_INVALID_ARG;
@@ -734,7 +759,8 @@ slr_status slr_pcg_solve(slr_handle h, const double* b, double* x, int32_t nrhs,
         CK(cudaMemcpyAsync(&e, ep, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         if (e) {
-            set_error("a bounded device wait expired in the band solve");
+            set_error(e == 2 ? "a bounded grid-barrier wait expired in the C solve"
+                             : "a bounded device wait expired in the band solve");
             return SLR_ERR_TIMEOUT;
         }
     }

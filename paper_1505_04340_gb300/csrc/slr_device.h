@@ -34,6 +34,14 @@ struct DevCFactor {
     std::vector<int32_t> lev_sn_ptr;
     std::vector<uint8_t> lev_small;
     int32_t* lev_sn = nullptr;            // device: supernodes level by level
+    // the persistent (one launch per direction) solves
+    int32_t *d_lev_task_ptr = nullptr, *d_lev_ptask_ptr = nullptr, *d_lev_sn_ptr = nullptr;   // device copies
+    uint8_t* d_lev_small = nullptr;
+    int32_t nsteps_fwd = 0, nsteps_bwd = 0;   // dependent steps (grid barriers + 1)
+    int32_t max_cta_tasks = 1;                // most CTA tasks of any step (caps the grid)
+    unsigned* bar = nullptr;                  // grid barrier counter, zeroed before each launch
+    int32_t* err = nullptr;                   // the operator's status word
+    bool per_level = true;                    // one launch per level step (else one cooperative launch)
 };
 
 // Everything one apply needs in precision T (double: FP64 path; float: mixed).

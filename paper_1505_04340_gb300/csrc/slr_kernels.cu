@@ -69,17 +69,22 @@ __global__ void k_spmv(int32_t rows, int32_t nrhs, const int32_t* __restrict__ r
 // its diagonal block is stored inverted (packed lower, column-major: column j
 // starts at cs(j) = j n_J - j (j-1) / 2).  Levels go leaves -> root.
 // A column task is (J, first, count <= 32); a panel task is (J, first row, count <= 32).
+//
+// Each step is a device function run by one warp or one CTA of NW warps; the
+// per-level kernels below wrap them one launch per step, and the persistent
+// kernels run every level in one cooperative launch with a grid barrier
+// between dependent steps.
 __device__ __forceinline__ int64_t packed_col(int j, int n) { return (int64_t)j * n - (int64_t)j * (j - 1) / 2; }
 
-// forward, phase 1: t_i = g[cperm[i]] - sum of the panel products w that hold row i
+// forward, gather (one warp): t_i = g[cperm[i]] - sum of the panel products w that hold row i
 template <typename T>
-__global__ void __launch_bounds__(32)
-k_cfwd_gather(const int4* __restrict__ tasks, const int32_t* __restrict__ c0, const int32_t* __restrict__ cperm,
-              const int64_t* __restrict__ seg_ptr, const int32_t* __restrict__ seg_row, const T* wbuf,
-              int64_t nrow, const T* g, int64_t ldg, T* tf, int32_t s, int32_t nrhs) {
-    const int4 tk = tasks[blockIdx.x];
-    if ((int)threadIdx.x >= tk.z) return;
-    const int32_t i = c0[tk.x] + tk.y + threadIdx.x;
+__device__ __forceinline__ void cfwd_gather_warp(const int4 tk, int lane, const int32_t* __restrict__ c0,
+                                                 const int32_t* __restrict__ cperm,
+                                                 const int64_t* __restrict__ seg_ptr,
+                                                 const int32_t* __restrict__ seg_row, const T* wbuf, int64_t nrow,
+                                                 const T* g, int64_t ldg, T* tf, int32_t s, int32_t nrhs) {
+    if (lane >= tk.z) return;
+    const int32_t i = c0[tk.x] + tk.y + lane;
     const int64_t e0 = seg_ptr[i], e1 = seg_ptr[i + 1];
     for (int j = 0; j < nrhs; ++j) {
         const T* w = wbuf + (int64_t)j * nrow;
@@ -89,23 +94,18 @@ k_cfwd_gather(const int4* __restrict__ tasks, const int32_t* __restrict__ c0, co
     }
 }
 
-constexpr int kDiagT = 1024;   // threads of the diagonal-block kernels (32 warps)
-constexpr int kPanT = 512;     // threads of the panel kernels (16 warps)
-
-// forward, phase 2: x_J = L_JJ^{-1} t_J for a block of <= 32 rows; 32 warps
-// split the reduction over columns (lane = row), 8 loads in flight per lane
-template <typename T>
-__global__ void __launch_bounds__(kDiagT)
-k_cfwd_diag(const int4* __restrict__ tasks, const int32_t* __restrict__ c0, const int64_t* __restrict__ dinv_off,
-            const T* __restrict__ dinv, const T* tf, T* xf, int32_t s, int32_t nrhs) {
-    constexpr int nw = kDiagT / 32;
-    __shared__ T red[nw][33];
-    const int4 tk = tasks[blockIdx.x];
+// forward, diagonal (one CTA of NW warps): x_J = L_JJ^{-1} t_J for a block of
+// <= 32 rows; the warps split the reduction over columns (lane = row), 8 loads
+// in flight per lane
+template <typename T, int NW>
+__device__ void cfwd_diag_cta(const int4 tk, T (*red)[33], const int32_t* __restrict__ c0,
+                              const int64_t* __restrict__ dinv_off, const T* __restrict__ dinv, const T* tf, T* xf,
+                              int32_t s, int32_t nrhs) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int32_t a0 = c0[tk.x], nJ = c0[tk.x + 1] - a0;
     const int il = tk.y + lane;
     const int ncol = tk.y + tk.z;                  // columns 0 .. ncol-1 reach these rows
-    const int chunk = (ncol + nw - 1) / nw;
+    const int chunk = (ncol + NW - 1) / NW;
     const int jb = warp * chunk, je = min(ncol, jb + chunk);
     const T* D = dinv + dinv_off[tk.x];
     for (int j = 0; j < nrhs; ++j) {
@@ -131,29 +131,26 @@ k_cfwd_diag(const int4* __restrict__ tasks, const int32_t* __restrict__ c0, cons
         if (warp == 0) {
             T v = T(0);
 #pragma unroll 8
-            for (int w = 0; w < nw; ++w) v += red[w][lane];
+            for (int w = 0; w < NW; ++w) v += red[w][lane];
             if (lane < tk.z) xf[a0 + il + (int64_t)j * s] = v;
         }
         __syncthreads();
     }
 }
 
-// forward, phase 3: w[r_off[J] + p] = L[R_J[p], J] . x_J (warp per panel row,
-// lanes over columns); x_J staged in shared memory
-template <typename T>
-__global__ void __launch_bounds__(kPanT)
-k_cfwd_panel(const int4* __restrict__ ptasks, const int32_t* __restrict__ c0, const int64_t* __restrict__ r_off,
-             const int64_t* __restrict__ pan_off, const T* __restrict__ panel, const T* xf, T* wbuf, int64_t nrow,
-             int32_t s, int32_t nrhs) {
-    extern __shared__ unsigned char csm[];
-    T* xs = reinterpret_cast<T*>(csm);
-    const int4 tk = ptasks[blockIdx.x];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = kPanT / 32;
+// forward, panel (one CTA): w[r_off[J] + p] = L[R_J[p], J] . x_J (warp per panel
+// row, lanes over columns); x_J staged in shared memory xs[n_J]
+template <typename T, int NW>
+__device__ void cfwd_panel_cta(const int4 tk, T* xs, const int32_t* __restrict__ c0,
+                               const int64_t* __restrict__ r_off, const int64_t* __restrict__ pan_off,
+                               const T* __restrict__ panel, const T* xf, T* wbuf, int64_t nrow, int32_t s,
+                               int32_t nrhs) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int32_t a0 = c0[tk.x], nJ = c0[tk.x + 1] - a0;
     for (int j = 0; j < nrhs; ++j) {
-        for (int c = threadIdx.x; c < nJ; c += kPanT) xs[c] = xf[a0 + c + (int64_t)j * s];
+        for (int c = threadIdx.x; c < nJ; c += NW * 32) xs[c] = xf[a0 + c + (int64_t)j * s];
         __syncthreads();
-        for (int pr = warp; pr < tk.z; pr += nw) {
+        for (int pr = warp; pr < tk.z; pr += NW) {
             const int64_t p = tk.y + pr;
             const T* P = panel + pan_off[tk.x] + p * nJ;
             T acc0 = T(0), acc1 = T(0);
@@ -170,22 +167,19 @@ k_cfwd_panel(const int4* __restrict__ ptasks, const int32_t* __restrict__ c0, co
     }
 }
 
-// backward, phase 1: t_j = y_j - sum_p L[R_J[p], j] x[R_J[p]] for <= 32 columns
-// (lane = column); 16 warps split the panel rows, 8 loads in flight per lane
-template <typename T>
-__global__ void __launch_bounds__(kPanT)
-k_cbwd_panel(const int4* __restrict__ tasks, const int32_t* __restrict__ c0, const int64_t* __restrict__ r_off,
-             const int32_t* __restrict__ rows, const int64_t* __restrict__ pan_off, const T* __restrict__ panel,
-             T* yf, const T* xf, int32_t s, int32_t nrhs) {
-    constexpr int nw = kPanT / 32;
-    __shared__ T red[nw][33];
-    const int4 tk = tasks[blockIdx.x];
+// backward, panel (one CTA): t_j = y_j - sum_p L[R_J[p], j] x[R_J[p]] for <= 32
+// columns (lane = column); the warps split the panel rows, 8 loads in flight
+template <typename T, int NW>
+__device__ void cbwd_panel_cta(const int4 tk, T (*red)[33], const int32_t* __restrict__ c0,
+                               const int64_t* __restrict__ r_off, const int32_t* __restrict__ rows,
+                               const int64_t* __restrict__ pan_off, const T* __restrict__ panel, T* yf,
+                               const T* xf, int32_t s, int32_t nrhs) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int32_t a0 = c0[tk.x], nJ = c0[tk.x + 1] - a0, jl = tk.y + lane;
     const int64_t nr = r_off[tk.x + 1] - r_off[tk.x];
     const int32_t* R = rows + r_off[tk.x];
     const T* Pn = panel + pan_off[tk.x] + jl;
-    const int64_t chunk = (nr + nw - 1) / nw, pb = warp * chunk, pe = min(nr, pb + chunk);
+    const int64_t chunk = (nr + NW - 1) / NW, pb = warp * chunk, pe = min(nr, pb + chunk);
     for (int j = 0; j < nrhs; ++j) {
         const T* x = xf + (int64_t)j * s;
         T acc = T(0);
@@ -207,26 +201,24 @@ k_cbwd_panel(const int4* __restrict__ tasks, const int32_t* __restrict__ c0, con
         __syncthreads();
         if (warp == 0 && lane < tk.z) {
             T v = T(0);
-#pragma unroll
-            for (int w = 0; w < nw; ++w) v += red[w][lane];
+#pragma unroll 8
+            for (int w = 0; w < NW; ++w) v += red[w][lane];
             yf[a0 + jl + (int64_t)j * s] -= v;
         }
         __syncthreads();
     }
 }
 
-// backward, phase 2: x_J = L_JJ^{-T} t_J (warp per column, lanes over the column,
-// 8 loads in flight per lane), optional scatter to DD order
-template <typename T>
-__global__ void __launch_bounds__(kDiagT)
-k_cbwd_diag(const int4* __restrict__ tasks, const int32_t* __restrict__ c0, const int64_t* __restrict__ dinv_off,
-            const T* __restrict__ dinv, const int32_t* __restrict__ cperm, const T* tf, T* xf, T* y_dd,
-            int64_t ldy, int32_t s, int32_t nrhs) {
-    const int4 tk = tasks[blockIdx.x];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+// backward, diagonal (one CTA): x_J = L_JJ^{-T} t_J (warp per column, lanes over
+// the column, 8 loads in flight per lane), optional scatter to DD order
+template <typename T, int NW>
+__device__ void cbwd_diag_cta(const int4 tk, const int32_t* __restrict__ c0, const int64_t* __restrict__ dinv_off,
+                              const T* __restrict__ dinv, const int32_t* __restrict__ cperm, const T* tf, T* xf,
+                              T* y_dd, int64_t ldy, int32_t s, int32_t nrhs) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int32_t a0 = c0[tk.x], nJ = c0[tk.x + 1] - a0;
     const T* D = dinv + dinv_off[tk.x];
-    for (int cc = warp; cc < tk.z; cc += nwarp) {
+    for (int cc = warp; cc < tk.z; cc += NW) {
         const int jl = tk.y + cc;
         const T* Dc = D + packed_col(jl, nJ) - jl;
         for (int j = 0; j < nrhs; ++j) {
@@ -253,33 +245,43 @@ k_cbwd_diag(const int4* __restrict__ tasks, const int32_t* __restrict__ c0, cons
     }
 }
 
-// Fused levels: one CTA per supernode J with n_J <= kSmallN and |R_J| <= kSmallR.
-static_assert(kThreads == 2 * kSmallN, "k_cbwd_small pairs two threads per column");
+// Synchronises the NT threads of a group: the whole CTA (GROUPS = 1) or group
+// g of GROUPS equal groups (named barrier 1 + g).
+template <int NT, int GROUPS>
+__device__ __forceinline__ void group_sync() {
+    if constexpr (GROUPS == 1) {
+        __syncthreads();
+    } else {
+        asm volatile("bar.sync %0, %1;" ::"r"(1 + (int)(threadIdx.x / NT)), "r"(NT) : "memory");
+    }
+}
+
+// Fused levels: one group of NT threads (a CTA, or a part of one) per supernode J
+// with n_J <= kSmallN and |R_J| <= kSmallR.
 // forward: t_J = g_J - (gathered panel products); x_J = L_JJ^{-1} t_J; w_J = L[R_J, J] x_J
-template <typename T>
-__global__ void __launch_bounds__(kThreads)
-k_cfwd_small(const int32_t* __restrict__ sns, const int32_t* __restrict__ c0, const int32_t* __restrict__ cperm,
-             const int64_t* __restrict__ seg_ptr, const int32_t* __restrict__ seg_row, const int64_t* __restrict__ r_off,
-             const int64_t* __restrict__ pan_off, const T* __restrict__ panel, const int64_t* __restrict__ dinv_off,
-             const T* __restrict__ dinv, T* wbuf, int64_t nrow, const T* g, int64_t ldg, T* xf, int32_t s,
-             int32_t nrhs) {
-    __shared__ T ts[kSmallN], xs[kSmallN];
-    const int J = sns[blockIdx.x];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = kThreads / 32;
+template <typename T, int NT, int GROUPS>
+__device__ void cfwd_small_cta(int J, T* ts, T* xs, const int32_t* __restrict__ c0,
+                               const int32_t* __restrict__ cperm, const int64_t* __restrict__ seg_ptr,
+                               const int32_t* __restrict__ seg_row, const int64_t* __restrict__ r_off,
+                               const int64_t* __restrict__ pan_off, const T* __restrict__ panel,
+                               const int64_t* __restrict__ dinv_off, const T* __restrict__ dinv, T* wbuf,
+                               int64_t nrow, const T* g, int64_t ldg, T* xf, int32_t s, int32_t nrhs) {
+    constexpr int nw = NT / 32;
+    const int gt = threadIdx.x % NT, lane = gt & 31, warp = gt >> 5;
     const int32_t a0 = c0[J], nJ = c0[J + 1] - a0;
     const int64_t nr = r_off[J + 1] - r_off[J];
     const T* D = dinv + dinv_off[J];
     const T* Pn = panel + pan_off[J];
     for (int j = 0; j < nrhs; ++j) {
         const T* w = wbuf + (int64_t)j * nrow;
-        for (int i = threadIdx.x; i < nJ; i += kThreads) {
+        for (int i = gt; i < nJ; i += NT) {
             const int32_t pos = a0 + i;
             T acc = T(0);
             for (int64_t e = seg_ptr[pos]; e < seg_ptr[pos + 1]; ++e) acc += w[seg_row[e]];
             ts[i] = g[cperm[pos] + j * ldg] - acc;
         }
-        __syncthreads();
-        for (int i = threadIdx.x; i < nJ; i += kThreads) {
+        group_sync<NT, GROUPS>();
+        for (int i = gt; i < nJ; i += NT) {
             T acc = T(0);
             int jj = 0;
             for (; jj + 7 <= i; jj += 8) {
@@ -293,7 +295,7 @@ k_cfwd_small(const int32_t* __restrict__ sns, const int32_t* __restrict__ c0, co
             xs[i] = acc;
             xf[a0 + i + (int64_t)j * s] = acc;
         }
-        __syncthreads();
+        group_sync<NT, GROUPS>();
         // four panel rows per warp at a time: their loads are in flight together
         for (int64_t p0 = 4 * warp; p0 < nr; p0 += 4 * nw) {
             T acc[4] = {T(0), T(0), T(0), T(0)};
@@ -309,21 +311,22 @@ k_cfwd_small(const int32_t* __restrict__ sns, const int32_t* __restrict__ c0, co
                 if (lane == 0 && p0 + u < nr) wbuf[r_off[J] + p0 + u + (int64_t)j * nrow] = v;
             }
         }
-        __syncthreads();
+        group_sync<NT, GROUPS>();
     }
 }
 
-// backward: t_J = y_J - L[R_J, J]^T x_{R_J};  x_J = L_JJ^{-T} t_J (and scatter to DD order)
-template <typename T>
-__global__ void __launch_bounds__(kThreads)
-k_cbwd_small(const int32_t* __restrict__ sns, const int32_t* __restrict__ c0, const int64_t* __restrict__ r_off,
-             const int32_t* __restrict__ rows, const int64_t* __restrict__ pan_off, const T* __restrict__ panel,
-             const int64_t* __restrict__ dinv_off, const T* __restrict__ dinv, const int32_t* __restrict__ cperm,
-             const T* yf, T* xf, T* y_dd, int64_t ldy, int32_t s, int32_t nrhs) {
-    __shared__ T xr[kSmallR], ts[kSmallN];
-    __shared__ T red[2][kSmallN];
-    const int J = sns[blockIdx.x];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = kThreads / 32;
+// backward: t_J = y_J - L[R_J, J]^T x_{R_J};  x_J = L_JJ^{-T} t_J (and scatter to DD order).
+// NT / kSmallN threads share each column, each over a part of the panel rows.
+template <typename T, int NT, int GROUPS>
+__device__ void cbwd_small_cta(int J, T* xr, T* ts, T* red, const int32_t* __restrict__ c0,
+                               const int64_t* __restrict__ r_off, const int32_t* __restrict__ rows,
+                               const int64_t* __restrict__ pan_off, const T* __restrict__ panel,
+                               const int64_t* __restrict__ dinv_off, const T* __restrict__ dinv,
+                               const int32_t* __restrict__ cperm, const T* yf, T* xf, T* y_dd, int64_t ldy,
+                               int32_t s, int32_t nrhs) {
+    static_assert(NT % kSmallN == 0, "whole threads per column");
+    constexpr int nw = NT / 32, parts = NT / kSmallN;
+    const int gt = threadIdx.x % NT, lane = gt & 31, warp = gt >> 5;
     const int32_t a0 = c0[J], nJ = c0[J + 1] - a0;
     const int64_t nr = r_off[J + 1] - r_off[J];
     const int32_t* R = rows + r_off[J];
@@ -331,14 +334,13 @@ k_cbwd_small(const int32_t* __restrict__ sns, const int32_t* __restrict__ c0, co
     const T* Pn = panel + pan_off[J];
     for (int j = 0; j < nrhs; ++j) {
         const T* x = xf + (int64_t)j * s;
-        for (int64_t p = threadIdx.x; p < nr; p += kThreads) xr[p] = x[R[p]];
-        __syncthreads();
-        // two halves of the panel rows per column, thread (half, column)
+        for (int64_t p = gt; p < nr; p += NT) xr[p] = x[R[p]];
+        group_sync<NT, GROUPS>();
         {
-            const int half = threadIdx.x / kSmallN, c = threadIdx.x % kSmallN;
+            const int part = gt / kSmallN, c = gt % kSmallN;
             T acc = T(0);
             if (c < nJ) {
-                const int64_t mid = (nr + 1) / 2, pb = half ? mid : 0, pe = half ? nr : mid;
+                const int64_t len = (nr + parts - 1) / parts, pb = part * len, pe = min(nr, pb + len);
                 int64_t p = pb;
                 for (; p + 7 < pe; p += 8) {
                     T pv[8];
@@ -349,12 +351,16 @@ k_cbwd_small(const int32_t* __restrict__ sns, const int32_t* __restrict__ c0, co
                 }
                 for (; p < pe; ++p) acc += Pn[p * nJ + c] * xr[p];
             }
-            red[half][c] = acc;
+            red[part * kSmallN + c] = acc;
         }
-        __syncthreads();
-        for (int c = threadIdx.x; c < nJ; c += kThreads)
-            ts[c] = yf[a0 + c + (int64_t)j * s] - (red[0][c] + red[1][c]);
-        __syncthreads();
+        group_sync<NT, GROUPS>();
+        for (int c = gt; c < nJ; c += NT) {
+            T v = T(0);
+#pragma unroll
+            for (int q = 0; q < parts; ++q) v += red[q * kSmallN + c];
+            ts[c] = yf[a0 + c + (int64_t)j * s] - v;
+        }
+        group_sync<NT, GROUPS>();
         for (int c = warp; c < nJ; c += nw) {
             const T* Dc = D + packed_col(c, nJ) - c;
             T acc = T(0);
@@ -365,7 +371,213 @@ k_cbwd_small(const int32_t* __restrict__ sns, const int32_t* __restrict__ c0, co
                 if (y_dd) y_dd[cperm[a0 + c] + j * ldy] = acc;
             }
         }
-        __syncthreads();
+        group_sync<NT, GROUPS>();
+    }
+}
+
+constexpr int kDiagT = 1024;   // threads of the per-level diagonal-block kernels (32 warps)
+constexpr int kPanT = 512;     // threads of the per-level panel kernels (16 warps)
+
+// ---- per-level kernels: one launch per step
+template <typename T>
+__global__ void __launch_bounds__(32)
+k_cfwd_gather(const int4* __restrict__ tasks, const int32_t* __restrict__ c0, const int32_t* __restrict__ cperm,
+              const int64_t* __restrict__ seg_ptr, const int32_t* __restrict__ seg_row, const T* wbuf,
+              int64_t nrow, const T* g, int64_t ldg, T* tf, int32_t s, int32_t nrhs) {
+    cfwd_gather_warp<T>(tasks[blockIdx.x], threadIdx.x, c0, cperm, seg_ptr, seg_row, wbuf, nrow, g, ldg, tf, s, nrhs);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kDiagT)
+k_cfwd_diag(const int4* __restrict__ tasks, const int32_t* __restrict__ c0, const int64_t* __restrict__ dinv_off,
+            const T* __restrict__ dinv, const T* tf, T* xf, int32_t s, int32_t nrhs) {
+    __shared__ T red[kDiagT / 32][33];
+    cfwd_diag_cta<T, kDiagT / 32>(tasks[blockIdx.x], red, c0, dinv_off, dinv, tf, xf, s, nrhs);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kPanT)
+k_cfwd_panel(const int4* __restrict__ ptasks, const int32_t* __restrict__ c0, const int64_t* __restrict__ r_off,
+             const int64_t* __restrict__ pan_off, const T* __restrict__ panel, const T* xf, T* wbuf, int64_t nrow,
+             int32_t s, int32_t nrhs) {
+    extern __shared__ unsigned char csm[];
+    cfwd_panel_cta<T, kPanT / 32>(ptasks[blockIdx.x], reinterpret_cast<T*>(csm), c0, r_off, pan_off, panel, xf,
+                                  wbuf, nrow, s, nrhs);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kPanT)
+k_cbwd_panel(const int4* __restrict__ tasks, const int32_t* __restrict__ c0, const int64_t* __restrict__ r_off,
+             const int32_t* __restrict__ rows, const int64_t* __restrict__ pan_off, const T* __restrict__ panel,
+             T* yf, const T* xf, int32_t s, int32_t nrhs) {
+    __shared__ T red[kPanT / 32][33];
+    cbwd_panel_cta<T, kPanT / 32>(tasks[blockIdx.x], red, c0, r_off, rows, pan_off, panel, yf, xf, s, nrhs);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kDiagT)
+k_cbwd_diag(const int4* __restrict__ tasks, const int32_t* __restrict__ c0, const int64_t* __restrict__ dinv_off,
+            const T* __restrict__ dinv, const int32_t* __restrict__ cperm, const T* tf, T* xf, T* y_dd,
+            int64_t ldy, int32_t s, int32_t nrhs) {
+    cbwd_diag_cta<T, kDiagT / 32>(tasks[blockIdx.x], c0, dinv_off, dinv, cperm, tf, xf, y_dd, ldy, s, nrhs);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_cfwd_small(const int32_t* __restrict__ sns, const int32_t* __restrict__ c0, const int32_t* __restrict__ cperm,
+             const int64_t* __restrict__ seg_ptr, const int32_t* __restrict__ seg_row, const int64_t* __restrict__ r_off,
+             const int64_t* __restrict__ pan_off, const T* __restrict__ panel, const int64_t* __restrict__ dinv_off,
+             const T* __restrict__ dinv, T* wbuf, int64_t nrow, const T* g, int64_t ldg, T* xf, int32_t s,
+             int32_t nrhs) {
+    __shared__ T ts[kSmallN], xs[kSmallN];
+    cfwd_small_cta<T, kThreads, 1>(sns[blockIdx.x], ts, xs, c0, cperm, seg_ptr, seg_row, r_off, pan_off, panel,
+                                dinv_off, dinv, wbuf, nrow, g, ldg, xf, s, nrhs);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_cbwd_small(const int32_t* __restrict__ sns, const int32_t* __restrict__ c0, const int64_t* __restrict__ r_off,
+             const int32_t* __restrict__ rows, const int64_t* __restrict__ pan_off, const T* __restrict__ panel,
+             const int64_t* __restrict__ dinv_off, const T* __restrict__ dinv, const int32_t* __restrict__ cperm,
+             const T* yf, T* xf, T* y_dd, int64_t ldy, int32_t s, int32_t nrhs) {
+    __shared__ T xr[kSmallR], ts[kSmallN];
+    __shared__ T red[(kThreads / kSmallN) * kSmallN];
+    cbwd_small_cta<T, kThreads, 1>(sns[blockIdx.x], xr, ts, red, c0, r_off, rows, pan_off, panel, dinv_off, dinv, cperm,
+                                yf, xf, y_dd, ldy, s, nrhs);
+}
+
+// ---- persistent kernels: every level in one cooperative launch
+// Plain view of a DevCFactor (device pointers and sizes) passed by value.
+template <typename T>
+struct CView {
+    int32_t s, nlev, nsteps;
+    int64_t nrow;
+    const int32_t *cperm, *c0, *rows, *seg_row, *lev_sn;
+    const int64_t *r_off, *pan_off, *dinv_off, *seg_ptr;
+    const T *panel, *dinv;
+    T* wbuf;
+    const int4 *tasks, *ptasks;
+    const int32_t *lev_task_ptr, *lev_ptask_ptr, *lev_sn_ptr;
+    const uint8_t* lev_small;
+    unsigned* bar;
+    int32_t* err;
+};
+
+constexpr int kPersT = 1024;                  // 32 warps, one CTA per SM
+constexpr int kPersW = kPersT / 32;
+constexpr int kSmallT = 256;                  // fused levels: 4 groups of 256 threads, a supernode each
+constexpr int kSmallG = kPersT / kSmallT;
+constexpr long long kGridSpin = 1ll << 22;    // bounded barrier wait (x 64 ns sleep: about a quarter second)
+
+// All CTAs arrive; the counter (zeroed before the launch) reaches target =
+// round x gridDim.x.  A wait that runs out sets the status word and goes on;
+// once the status word is set, later waits give up early too.
+__device__ __forceinline__ void grid_barrier(unsigned* bar, unsigned target, int32_t* err) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(bar, 1u);
+        long long it = 0;
+        while (*reinterpret_cast<volatile unsigned*>(bar) < target) {
+            if (++it > kGridSpin) {
+                atomicExch(err, 2);
+                break;
+            }
+            if ((it & 1023) == 0 && *reinterpret_cast<volatile int32_t*>(err)) break;   // already failed
+            __nanosleep(64);
+        }
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+// shared bytes of the persistent kernels: the larger of the forward panel's
+// x_J (max_n values), the fused levels' buffers and the reduction arrays
+inline size_t pers_smem_bytes(int32_t max_n, size_t elem) {
+    const size_t small_fwd = kSmallG * 2 * kSmallN,
+                 small_bwd = kSmallG * (kSmallR + kSmallN + (kSmallT / kSmallN) * kSmallN);
+    const size_t red = kPersW * 33;
+    return std::max({(size_t)max_n, small_fwd, small_bwd, red}) * elem;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kPersT, 1)
+k_cfwd_persistent(const CView<T> cf, const T* g, int64_t ldg, T* tf, T* xf, int32_t nrhs) {
+    extern __shared__ __align__(16) unsigned char psm[];
+    T* sm = reinterpret_cast<T*>(psm);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    unsigned round = 0;
+    int steps_left = cf.nsteps;
+    auto sync = [&]() {
+        if (--steps_left > 0) grid_barrier(cf.bar, ++round * gridDim.x, cf.err);
+    };
+    for (int l = 0; l < cf.nlev; ++l) {
+        if (cf.lev_small[l]) {
+            const int s0 = cf.lev_sn_ptr[l], ns = cf.lev_sn_ptr[l + 1] - s0;
+            if (ns == 0) continue;
+            const int grp = threadIdx.x / kSmallT;
+            T* gs = sm + grp * 2 * kSmallN;
+            for (int q = blockIdx.x * kSmallG + grp; q < ns; q += gridDim.x * kSmallG)
+                cfwd_small_cta<T, kSmallT, kSmallG>(cf.lev_sn[s0 + q], gs, gs + kSmallN, cf.c0, cf.cperm, cf.seg_ptr,
+                                          cf.seg_row, cf.r_off, cf.pan_off, cf.panel, cf.dinv_off, cf.dinv, cf.wbuf,
+                                          cf.nrow, g, ldg, xf, cf.s, nrhs);
+            sync();
+            continue;
+        }
+        const int t0 = cf.lev_task_ptr[l], nt = cf.lev_task_ptr[l + 1] - t0;
+        const int p0 = cf.lev_ptask_ptr[l], np = cf.lev_ptask_ptr[l + 1] - p0;
+        if (nt > 0) {
+            for (int q = blockIdx.x * kPersW + warp; q < nt; q += gridDim.x * kPersW)
+                cfwd_gather_warp<T>(cf.tasks[t0 + q], lane, cf.c0, cf.cperm, cf.seg_ptr, cf.seg_row, cf.wbuf,
+                                    cf.nrow, g, ldg, tf, cf.s, nrhs);
+            sync();
+            for (int q = blockIdx.x; q < nt; q += gridDim.x)
+                cfwd_diag_cta<T, kPersW>(cf.tasks[t0 + q], reinterpret_cast<T(*)[33]>(sm), cf.c0, cf.dinv_off,
+                                         cf.dinv, tf, xf, cf.s, nrhs);
+            sync();
+        }
+        if (np > 0) {
+            for (int q = blockIdx.x; q < np; q += gridDim.x)
+                cfwd_panel_cta<T, kPersW>(cf.ptasks[p0 + q], sm, cf.c0, cf.r_off, cf.pan_off, cf.panel, xf, cf.wbuf,
+                                          cf.nrow, cf.s, nrhs);
+            sync();
+        }
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kPersT, 1)
+k_cbwd_persistent(const CView<T> cf, T* yf, T* xf, T* y_dd, int64_t ldy, int32_t nrhs) {
+    extern __shared__ __align__(16) unsigned char psm[];
+    T* sm = reinterpret_cast<T*>(psm);
+    unsigned round = 0;
+    int steps_left = cf.nsteps;
+    auto sync = [&]() {
+        if (--steps_left > 0) grid_barrier(cf.bar, ++round * gridDim.x, cf.err);
+    };
+    for (int l = cf.nlev - 1; l >= 0; --l) {
+        if (cf.lev_small[l]) {
+            const int s0 = cf.lev_sn_ptr[l], ns = cf.lev_sn_ptr[l + 1] - s0;
+            if (ns == 0) continue;
+            const int grp = threadIdx.x / kSmallT;
+            T* gs = sm + grp * (kSmallR + kSmallN + (kSmallT / kSmallN) * kSmallN);
+            for (int q = blockIdx.x * kSmallG + grp; q < ns; q += gridDim.x * kSmallG)
+                cbwd_small_cta<T, kSmallT, kSmallG>(cf.lev_sn[s0 + q], gs, gs + kSmallR, gs + kSmallR + kSmallN, cf.c0,
+                                          cf.r_off, cf.rows, cf.pan_off, cf.panel, cf.dinv_off, cf.dinv, cf.cperm,
+                                          yf, xf, y_dd, ldy, cf.s, nrhs);
+            sync();
+            continue;
+        }
+        const int t0 = cf.lev_task_ptr[l], nt = cf.lev_task_ptr[l + 1] - t0;
+        if (nt == 0) continue;
+        for (int q = blockIdx.x; q < nt; q += gridDim.x)
+            cbwd_panel_cta<T, kPersW>(cf.tasks[t0 + q], reinterpret_cast<T(*)[33]>(sm), cf.c0, cf.r_off, cf.rows,
+                                      cf.pan_off, cf.panel, yf, xf, cf.s, nrhs);
+        sync();
+        for (int q = blockIdx.x; q < nt; q += gridDim.x)
+            cbwd_diag_cta<T, kPersW>(cf.tasks[t0 + q], cf.c0, cf.dinv_off, cf.dinv, cf.cperm, yf, xf, y_dd, ldy,
+                                     cf.s, nrhs);
+        sync();
     }
 }
 
@@ -618,9 +830,81 @@ cudaError_t launch_spmv_e(const DevOperator<T>& op, int32_t nI, const T* y, int6
     return cudaGetLastError();
 }
 
+// Grid of a persistent solve on the current device: one CTA per SM (fewer if
+// no step has that many CTA tasks), 0 if the kernel cannot be co-resident.
+template <typename K>
+int pers_grid(K kern, size_t smem, int32_t max_cta_tasks) {
+    int dev = 0, nsm = 0, occ = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kPersT, smem) != cudaSuccess || occ < 1) {
+        cudaGetLastError();
+        return 0;
+    }
+    return std::max(1, std::min(nsm, max_cta_tasks));
+}
+
+template <typename T>
+CView<T> make_view(const DevCFactor<T>& cf, int32_t nsteps) {
+    CView<T> v;
+    v.s = cf.s;
+    v.nlev = cf.nlev;
+    v.nsteps = nsteps;
+    v.nrow = cf.nrow;
+    v.cperm = cf.cperm;
+    v.c0 = cf.c0;
+    v.rows = cf.rows;
+    v.seg_row = cf.seg_row;
+    v.lev_sn = cf.lev_sn;
+    v.r_off = cf.r_off;
+    v.pan_off = cf.pan_off;
+    v.dinv_off = cf.dinv_off;
+    v.seg_ptr = cf.seg_ptr;
+    v.panel = cf.panel;
+    v.dinv = cf.dinv;
+    v.wbuf = cf.wbuf;
+    v.tasks = cf.tasks;
+    v.ptasks = cf.ptasks;
+    v.lev_task_ptr = cf.d_lev_task_ptr;
+    v.lev_ptask_ptr = cf.d_lev_ptask_ptr;
+    v.lev_sn_ptr = cf.d_lev_sn_ptr;
+    v.lev_small = cf.d_lev_small;
+    v.bar = cf.bar;
+    v.err = cf.err;
+    return v;
+}
+
+// one cooperative launch; the barrier counter is zeroed first on the same stream
+template <typename K, typename... A>
+cudaError_t launch_persistent(K kern, int grid, size_t smem, unsigned* bar, cudaStream_t st, A... args) {
+    cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(unsigned), st);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kPersT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = cudaLaunchKernelEx(&cfg, kern, args...);
+    counted();
+    return e;
+}
+
 template <typename T>
 cudaError_t launch_c_forward(const DevCFactor<T>& cf, const T* g_dd, int64_t ldg, T* tf, T* xf, int32_t nrhs,
                              cudaStream_t st) {
+    if (cf.nsteps_fwd == 0) return cudaSuccess;
+    if (!cf.per_level) {
+        const size_t smem = pers_smem_bytes(cf.max_n, sizeof(T));
+        const int grid = pers_grid(k_cfwd_persistent<T>, smem, cf.max_cta_tasks);
+        if (grid > 0)
+            return launch_persistent(k_cfwd_persistent<T>, grid, smem, cf.bar, st, make_view(cf, cf.nsteps_fwd), g_dd,
+                                     ldg, tf, xf, nrhs);
+    }
     for (int l = 0; l < cf.nlev; ++l) {
         if (cf.lev_small[l]) {
             const int s0 = cf.lev_sn_ptr[l], ns = cf.lev_sn_ptr[l + 1] - s0;
@@ -652,6 +936,14 @@ cudaError_t launch_c_forward(const DevCFactor<T>& cf, const T* g_dd, int64_t ldg
 template <typename T>
 cudaError_t launch_c_backward(const DevCFactor<T>& cf, T* yf, T* xf, T* y_dd, int64_t ldy, int32_t nrhs,
                               cudaStream_t st) {
+    if (cf.nsteps_bwd == 0) return cudaSuccess;
+    if (!cf.per_level) {
+        const size_t smem = pers_smem_bytes(cf.max_n, sizeof(T));
+        const int grid = pers_grid(k_cbwd_persistent<T>, smem, cf.max_cta_tasks);
+        if (grid > 0)
+            return launch_persistent(k_cbwd_persistent<T>, grid, smem, cf.bar, st, make_view(cf, cf.nsteps_bwd), yf, xf,
+                                     y_dd, ldy, nrhs);
+    }
     for (int l = cf.nlev - 1; l >= 0; --l) {
         if (cf.lev_small[l]) {
             const int s0 = cf.lev_sn_ptr[l], ns = cf.lev_sn_ptr[l + 1] - s0;

@@ -77,6 +77,7 @@ size_t carve(slr_handle h, DevOperator<T>& op, int32_t nrhs, unsigned char* base
     op.tf = c.take<T>(s * nrhs);
     op.xf = c.take<T>(s * nrhs);
     op.cf.wbuf = c.take<T>(std::max<int64_t>(op.cf.nrow, 1) * nrhs);
+    op.cf.bar = c.take<unsigned>(1);          // the persistent C solves' grid barrier counter
     op.vk = c.take<T>(k * nrhs);
     op.part = c.take<T>(k * nrhs * kRedBlocks);
     if constexpr (!std::is_same<T, double>::value) {

@@ -158,7 +158,7 @@ class SLR:
 
     def __init__(self, rowptr, colind, val, part, nparts, k=16, lanczos_steps=0, theta="lambda_k1",
                  precision="fp64", nrhs_max=1, flexible_cg=False, seed=1, c_leaf=64, verbose=False,
-                 band_split=0, host_loop=False, band_slots=0, stream=None):
+                 band_split=0, host_loop=False, band_slots=0, c_persistent=False, stream=None):
         lib = load()
         self._lib = lib
         self._h = None
@@ -171,6 +171,7 @@ class SLR:
         o.reserved[0] = int(band_split)        # CTAs per subdomain in the band solve, 0 = automatic
         o.reserved[1] = int(bool(host_loop))   # CG loop driven from the host instead of a CUDA graph
         o.reserved[2] = int(band_slots)        # band-solve stream buffers, 0 = automatic
+        o.reserved[3] = int(bool(c_persistent))  # C solves in one cooperative launch per direction
         self.rowptr, self.colind = _i32(rowptr), _i32(colind)
         self.val = np.ascontiguousarray(val, dtype=np.float64)
         self.part = _i32(part)

@@ -106,13 +106,45 @@ def test_bsolve_ring_and_split(name, split, slots, precision):
 
 @pytest.mark.parametrize("name", [n for n in PROBLEMS if n != "one-part"])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_csolve_parity(name, precision):
+@pytest.mark.parametrize("persistent", [False, True])
+def test_csolve_parity(name, precision, persistent):
+    """C^{-1} by the per-level kernels and the persistent one (one cooperative launch per direction)."""
     P = make(name)
     o = oracle(name)
-    g = gpu_handle(P, precision)
-    gg = np.random.default_rng(2).standard_normal((o.order.s, 2))
+    g = gpu_handle(P, precision, c_persistent=persistent)
+    gg = np.random.default_rng(2).standard_normal((o.order.s, 3))
     y = g.csolve(cu(gg)).cpu().numpy()
     assert rel(y, o.cfac.solve(gg)) <= (TOL64 if precision == "fp64" else TOL32)
+    # a column alone gives the same numbers as in the block
+    assert np.array_equal(g.csolve(cu(gg[:, 1])).cpu().numpy(), y[:, 1])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_csolve_medium_with_fused_levels(precision):
+    """C^{-1} on a 40^3 Laplacian with 4^3 boxes (s = 24,696): its two lowest levels
+    hold more than 152 small supernodes each and run as fused one-CTA-per-supernode
+    steps; both the per-level and the persistent path against the oracle's factor."""
+    from oracle.slr_oracle import dd_order, split_blocks, CFactor
+    P = slrgen.make_problem("m40", (40, 40, 40), (4, 4, 4), 4)
+    order = dd_order(P.rowptr, P.colind, P.part, P.nparts)
+    C = split_blocks(P.rowptr, P.colind, P.val, order)[2]
+    want_fn = CFactor(C, route="sparse").solve
+    gg = np.random.default_rng(6).standard_normal((order.s, 2))
+    want = want_fn(gg)
+    for persistent in (False, True):
+        g = SLR(P.rowptr, P.colind, P.val, P.part, P.nparts, k=2, lanczos_steps=4, precision=precision,
+                nrhs_max=2, c_persistent=persistent)
+        y = g.csolve(cu(gg)).cpu().numpy()
+        assert rel(y, want) <= (TOL64 if precision == "fp64" else TOL32), persistent
+
+
+def test_pcg_with_persistent_c_solve_matches_per_level():
+    P = make("3d-lap")
+    b = cu(P.b[:, 0])
+    x1, it1, _, s1 = gpu_handle(P).pcg(b)
+    x2, it2, _, s2 = gpu_handle(P, c_persistent=True).pcg(b)
+    assert s1 == s2 == 0 and abs(int(it1[0]) - int(it2[0])) <= 1
+    assert rel(x2.cpu().numpy(), x1.cpu().numpy()) <= 1e-9
 
 
 @pytest.mark.parametrize("name", [n for n in PROBLEMS if n != "one-part"])
