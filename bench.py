@@ -332,7 +332,8 @@ def run_ours(args):
 
     def make(precision):
         return SLR(P.rowptr, P.colind, P.val, P.part, P.nparts, k=P.k, lanczos_steps=P.lanczos_steps,
-                   precision=precision, nrhs_max=1, flexible_cg=(precision == "mixed"))
+                   precision=precision, nrhs_max=1, flexible_cg=(precision == "mixed"),
+                   autotune=not args.no_autotune)
 
     results = {}
     for prec in ("fp64", "mixed"):
@@ -419,6 +420,9 @@ def run_ours(args):
             setup_s=setup_s, launches=launches, clocks=clocks, relres=float(rel[0]), true_relres=A_err,
             apply_us=apply_us, apply_gbs=info["bytes_per_apply"] / apply_us / 1e3,
             bytes_per_apply=info["bytes_per_apply"], band_us=band_us, band_bytes=band_bytes,
+            tuning={"band_split": info["band_split"], "band_slots": info["band_slots"],
+                    "c_persistent": info["c_persistent"], "tuned": info["tuned"],
+                    "tune_seconds": info["tune_seconds"]},
             band_flops=band_flops, device_bytes=info["device_bytes"], setup_parts=info["setup_seconds"])
         # end to end through host buffers: pinned b -> device, solve, x -> pinned host
         if prec == "fp64":
@@ -479,7 +483,7 @@ def run_ours(args):
         "config": {"workload": wname, "n": P.n, "nparts": P.nparts, "k": P.k, "lanczos_steps": P.lanczos_steps,
                    "tol": 1e-8, "precision": "fp64", "nrhs": 1,
                    "l2": "working set larger than L2 (band factor %.0f MB > 129 MB)" % (r64["band_bytes"] / 2e6),
-                   "parallelism": f"replicas x{ws}"},
+                   "parallelism": f"replicas x{ws}", "tuning": r64["tuning"]},
         "iterations": its_full, "p50_ms": r64["p50_ms"], "p99_ms": r64["p99_ms"],
         "true_relres": r64["true_relres"], "setup_s": r64["setup_s"],
         "apply": {"us": r64["apply_us"], "gbs": r64["apply_gbs"], "bytes": r64["bytes_per_apply"]},
@@ -488,7 +492,8 @@ def run_ours(args):
                   "apply_rel_diff_vs_fp64": results["apply_rel_diff"],
                   "apply_us": rm["apply_us"], "apply_gbs": rm["apply_gbs"],
                   "band_solve_us": rm["band_us"], "band_gbs": mixed_band_gbs,
-                  "band_frac_hbm": mixed_band_gbs / hbm, "dtype": "f32 apply / f64 outer"},
+                  "band_frac_hbm": mixed_band_gbs / hbm, "dtype": "f32 apply / f64 outer",
+                  "tuning": rm["tuning"]},
         "roofline": roof,
         "band_solve_us": r64["band_us"],
         "cpu_baseline": cpu,
@@ -516,6 +521,7 @@ def main():
     ap.add_argument("--profile", action="store_true", help="solves inside an NVTX range only (for ncu)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--profile-kernel", default="pcg", choices=["pcg", "bsolve", "csolve", "apply"])
+    ap.add_argument("--no-autotune", action="store_true", help="keep the built-in launch choices")
     ap.add_argument("--serving-requests", type=int, default=256, help="config-5 request stream length (0: skip)")
     ap.add_argument("--serving-rate", type=float, default=50.0, help="Poisson arrival rate, requests/s")
     ap.add_argument("--serving-concurrency", type=int, default=4)

@@ -79,6 +79,11 @@ typedef struct {
                                0 = automatic).  reserved[3]: 1 = solve with C's factor
                                in one cooperative launch per direction (grid barriers
                                between level steps) instead of one launch per step.
+                               reserved[4]: 1 = autotune: setup times the band solve
+                               for each split (1, 2, 4 CTAs) and buffer count (2, 3, 4)
+                               that fit, and both C-solve paths, on this operator, and
+                               keeps the fastest; the choice is cached per device,
+                               precision and problem shape for the process's life.
                                The rest must be 0.                                      */
 } slr_opts;
 
@@ -95,6 +100,11 @@ typedef struct {
     double theta;                /* theta used in S~^{-1}                                  */
     double setup_seconds[5];     /* analysis, B factor, C factor, upload, Lanczos          */
     int32_t precision, theta_mode;
+    int32_t band_split;          /* CTAs per subdomain in the band solve                    */
+    int32_t band_slots;          /* band-solve stream buffers (0: the default)              */
+    int32_t c_persistent;        /* 1: C solves in one cooperative launch per direction     */
+    int32_t tuned;               /* 1: the three above were chosen by timing (reserved[4]) */
+    double tune_seconds;         /* time the tuning took (0 when taken from the cache)      */
 } slr_info;
 
 /* Fill *opts with defaults: k = 16, m = 5k, theta = lambda_{k+1}, FP64, 1 RHS, seed 1. */

@@ -8,11 +8,13 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
 #include <shared_mutex>
 #include <string>
 #include <type_traits>
+#include <tuple>
 #include <vector>
 
 #include "slr_device.h"
@@ -373,6 +375,169 @@ void account(slr_handle h) {
     h->flops_per_apply = 2 * (4 * band + 2 * nnzE + 2 * cvals + 2 * s * k);
 }
 
+// ------------------------------------------------------------------ autotuning
+// Choices of the band solve (CTAs per subdomain, stream buffers) and of the C
+// solve (per-level or persistent), timed on the handle's own apply operator and
+// cached per device, precision and problem shape.
+struct TuneKey {
+    int32_t dev, prec, p, wmax, cmax, nI, s, ns, nlev, nrhs;
+    bool operator<(const TuneKey& o) const {
+        return std::tie(dev, prec, p, wmax, cmax, nI, s, ns, nlev, nrhs) <
+               std::tie(o.dev, o.prec, o.p, o.wmax, o.cmax, o.nI, o.s, o.ns, o.nlev, o.nrhs);
+    }
+};
+struct TuneChoice {
+    int32_t G = 1, slots = 0;
+    bool persistent = false;
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneChoice> g_tune_cache;
+
+// Average time of `reps` calls of f on stream st after two untimed ones (us).
+template <typename F>
+slr_status time_us(F f, cudaStream_t st, int reps, double* us) {
+    for (int i = 0; i < 2; ++i) CS(f());
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    CK(cudaEventRecord(e0, st));
+    slr_status r = SLR_OK;
+    for (int i = 0; i < reps && r == SLR_OK; ++i) r = f();
+    CK(cudaEventRecord(e1, st));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    *us = 1e3 * ms / reps;
+    return r;
+}
+
+// Capture what f launches (on a capture stream) into an executable graph.
+template <typename F>
+slr_status capture_graph(slr_handle h, F f, cudaGraphExec_t* out) {
+    (void)h;
+    cudaStream_t cs = nullptr;
+    CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    slr_status r;
+    {
+        std::shared_lock<std::shared_mutex> lk(g_capture_mu);
+        const int64_t l0 = thread_launches();
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
+        if (e != cudaSuccess) {
+            cudaStreamDestroy(cs);
+            set_error(std::string("capture: ") + cudaGetErrorString(e));
+            return SLR_ERR_CUDA;
+        }
+        r = f(cs);
+        e = cudaStreamEndCapture(cs, &g);
+        count_launches(-(thread_launches() - l0));   // captured, not run
+        if (r == SLR_OK && e != cudaSuccess) {
+            set_error(std::string("capture: ") + cudaGetErrorString(e));
+            r = SLR_ERR_CUDA;
+        }
+    }
+    if (r == SLR_OK) {
+        const cudaError_t e = cudaGraphInstantiate(out, g, 0);
+        if (e != cudaSuccess) {
+            set_error(std::string("instantiate: ") + cudaGetErrorString(e));
+            r = SLR_ERR_CUDA;
+        }
+    }
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    cudaGetLastError();
+    return r;
+}
+
+// Repack the band factor for G CTAs per subdomain and reload it into the apply operator.
+template <typename T>
+slr_status repack_band(slr_handle h, DevOperator<T>& op, int32_t G) {
+    HostSetup& hs = h->hs;
+    const size_t old_band = hs.band.size(), old_fac = hs.bfac.size();
+    CS(host_band_factor(hs, G));
+    CK(cudaStreamSynchronize(h->stream));
+    dfree(h, op.band, old_band);
+    dfree(h, op.bfac, old_fac);
+    CS(upload(h, &op.band, hs.band));
+    CS(upload(h, &op.bfac, hs.bfac));
+    CK(cudaStreamSynchronize(h->stream));
+    op.band_G = hs.band_G;
+    return SLR_OK;
+}
+
+template <typename T>
+slr_status autotune(slr_handle h, DevOperator<T>& op, cudaStream_t st) {
+    HostSetup& hs = h->hs;
+    const auto t0 = std::chrono::steady_clock::now();
+    int dev = 0, nsm = 152;
+    CK(cudaGetDevice(&dev));
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    int32_t cmax = 0;
+    for (const BandBlock& b : hs.band) cmax = std::max(cmax, b.c);
+    const TuneKey key{dev, h->opts.precision, hs.p, hs.wmax, cmax, hs.nI, hs.s, hs.cf.ns, hs.cf.nlev,
+                      h->opts.nrhs_max};
+    TuneChoice best;
+    bool cached = false;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            best = it->second;
+            cached = true;
+        }
+    }
+    if (!cached && hs.p > 0 && hs.wmax > 0) {
+        CK(cudaMemsetAsync(op.eb, 0, sizeof(T) * std::max(hs.nI, 1), st));
+        CK(cudaMemsetAsync(op.gp, 0, sizeof(T) * std::max(hs.s, 1), st));
+        double best_us = 1e30;
+        for (int32_t G : {1, 2, 4}) {
+            if ((hs.wmax + G - 1) / G > 256 || (G > 1 && hs.wmax < 16 * G) || hs.p * G > 2 * nsm) continue;
+            if (G != hs.band_G) CS(repack_band<T>(h, op, G));
+            for (int32_t slots : {2, 3, 4}) {
+                op.band_nbuf = slots;
+                double us = 0;
+                CS(time_us([&]() -> slr_status {
+                    CK(launch_band_solve<T>(op, hs.p, hs.wmax, op.eb, hs.nI, op.tB, hs.nI, nullptr, 0, 1, st));
+                    return SLR_OK;
+                }, st, 5, &us));
+                if (us < best_us) {
+                    best_us = us;
+                    best.G = G;
+                    best.slots = slots;
+                }
+            }
+        }
+        // the C solves run inside the PCG graph: time them as a replayed graph
+        double c_us[2] = {0, 0};
+        for (int v = 0; v < 2; ++v) {
+            op.cf.per_level = (v == 0);
+            cudaGraphExec_t ex = nullptr;
+            CS(capture_graph(h, [&](cudaStream_t cs) -> slr_status {
+                CK(launch_c_forward<T>(op.cf, op.gp, hs.s, op.tf, op.wf, 1, cs));
+                CK(launch_c_backward<T>(op.cf, op.wf, op.xf, op.gp, hs.s, 1, cs));
+                return SLR_OK;
+            }, &ex));
+            const slr_status r = time_us([&]() -> slr_status {
+                CK(cudaGraphLaunch(ex, st));
+                return SLR_OK;
+            }, st, 5, &c_us[v]);
+            cudaGraphExecDestroy(ex);
+            CS(r);
+        }
+        best.persistent = c_us[1] < c_us[0];
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[key] = best;
+    }
+    if (best.G != hs.band_G) CS(repack_band<T>(h, op, best.G));
+    op.band_nbuf = best.slots;
+    op.cf.per_level = !best.persistent;
+    h->tuned = true;
+    h->tune_seconds = cached ? 0.0 : std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return SLR_OK;
+}
+
 slr_status setup_impl(slr_handle h, int32_t n, const int32_t* rowptr, const int32_t* colind, const double* val,
                       int32_t nparts, const int32_t* part, cudaStream_t st) {
     HostSetup& hs = h->hs;
@@ -453,6 +618,10 @@ slr_status setup_impl(slr_handle h, int32_t n, const int32_t* rowptr, const int3
         CS(set_operator_lowrank<float>(h, h->op32, h->op64.U, 0, h->k, h->lam, h->theta));
         // the FP64 band factor served the FP64 Lanczos only
         dfree(h, h->op64.bfac, hs.bfac.size());
+    }
+    if (h->opts.reserved[4] == 1) {
+        if (h->opts.precision == SLR_PREC_FP64) CS(autotune<double>(h, h->op64, st));
+        else CS(autotune<float>(h, h->op32, st));
     }
     CK(cudaStreamSynchronize(st));
     double t6 = now_s();
@@ -621,8 +790,12 @@ slr_status slr_setup(int32_t n, const int32_t* rowptr, const int32_t* colind, co
     if (h->opts.k < 0 || h->opts.lanczos_steps < 0 || h->opts.nrhs_max < 0 || h->opts.nrhs_max > 64 ||
         (h->opts.precision != SLR_PREC_FP64 && h->opts.precision != SLR_PREC_MIXED) ||
         (h->opts.theta_mode != SLR_THETA_LAMBDA_K1 && h->opts.theta_mode != SLR_THETA_ZERO) ||
+        (h->opts.reserved[0] != 0 && h->opts.reserved[0] != 1 && h->opts.reserved[0] != 2 &&
+         h->opts.reserved[0] != 4) ||
+        h->opts.reserved[1] < 0 || h->opts.reserved[1] > 1 ||
         h->opts.reserved[2] < 0 || h->opts.reserved[2] == 1 || h->opts.reserved[2] > 8 ||
-        h->opts.reserved[3] < 0 || h->opts.reserved[3] > 1) {
+        h->opts.reserved[3] < 0 || h->opts.reserved[3] > 1 || h->opts.reserved[4] < 0 || h->opts.reserved[4] > 1 ||
+        h->opts.reserved[5] != 0) {
         set_error("invalid options");
         delete h;
         return SLR_ERR_INVALID_ARG;
@@ -895,6 +1068,12 @@ slr_status slr_get_info(slr_handle h, slr_info* info) {
     for (int i = 0; i < 5; ++i) info->setup_seconds[i] = h->setup_seconds[i];
     info->precision = h->opts.precision;
     info->theta_mode = h->opts.theta_mode;
+    info->band_split = hs.band_G;
+    const bool f64 = h->opts.precision == SLR_PREC_FP64;
+    info->band_slots = f64 ? h->op64.band_nbuf : h->op32.band_nbuf;
+    info->c_persistent = (f64 ? h->op64.cf.per_level : h->op32.cf.per_level) ? 0 : 1;
+    info->tuned = h->tuned ? 1 : 0;
+    info->tune_seconds = h->tune_seconds;
     return SLR_OK;
 }
 

@@ -98,6 +98,8 @@ struct slr_handle_s {
     int64_t device_bytes = 0;
     double setup_seconds[5] = {0, 0, 0, 0, 0};
     int64_t bytes_per_apply = 0, flops_per_apply = 0;
+    bool tuned = false;
+    double tune_seconds = 0.0;
 };
 
 namespace slr {

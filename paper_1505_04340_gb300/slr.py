@@ -46,7 +46,8 @@ class Info(C.Structure):
         "band_entries", "c_diag_entries", "c_panel_entries", "c_supernodes", "c_levels",
         "bytes_per_apply", "flops_per_apply", "device_bytes")] + [
         ("theta", C.c_double), ("setup_seconds", C.c_double * 5), ("precision", C.c_int32),
-        ("theta_mode", C.c_int32)]
+        ("theta_mode", C.c_int32), ("band_split", C.c_int32), ("band_slots", C.c_int32),
+        ("c_persistent", C.c_int32), ("tuned", C.c_int32), ("tune_seconds", C.c_double)]
 
 
 class SLRError(RuntimeError):
@@ -158,7 +159,7 @@ class SLR:
 
     def __init__(self, rowptr, colind, val, part, nparts, k=16, lanczos_steps=0, theta="lambda_k1",
                  precision="fp64", nrhs_max=1, flexible_cg=False, seed=1, c_leaf=64, verbose=False,
-                 band_split=0, host_loop=False, band_slots=0, c_persistent=False, stream=None):
+                 band_split=0, host_loop=False, band_slots=0, c_persistent=False, autotune=False, stream=None):
         lib = load()
         self._lib = lib
         self._h = None
@@ -172,6 +173,7 @@ class SLR:
         o.reserved[1] = int(bool(host_loop))   # CG loop driven from the host instead of a CUDA graph
         o.reserved[2] = int(band_slots)        # band-solve stream buffers, 0 = automatic
         o.reserved[3] = int(bool(c_persistent))  # C solves in one cooperative launch per direction
+        o.reserved[4] = int(bool(autotune))      # time the candidates at setup and keep the fastest
         self.rowptr, self.colind = _i32(rowptr), _i32(colind)
         self.val = np.ascontiguousarray(val, dtype=np.float64)
         self.part = _i32(part)

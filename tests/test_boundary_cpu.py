@@ -61,10 +61,12 @@ def test_dd_order_random_partition(lib):
     assert np.array_equal(perm, o.perm) and s == o.s
 
 
-def _setup_status(lib, rp, ci, v, part, p):
+def _setup_status(lib, rp, ci, v, part, p, reserved=None):
     from paper_1505_04340_gb300 import slr
     o = slr.Opts()
     lib.slr_default_opts(C.byref(o))
+    for i, r in (reserved or {}).items():
+        o.reserved[i] = r
     h = C.c_void_p()
     rp, ci, part = (np.ascontiguousarray(a, dtype=np.int32) for a in (rp, ci, part))
     v = np.ascontiguousarray(v, dtype=np.float64)
@@ -85,6 +87,16 @@ def test_setup_rejects_bad_input_before_any_device_work(lib):
     assert _setup_status(lib, rp, ci, asym, part, 2) == 1
     assert _setup_status(lib, rp, ci, v, part + 5, 2) == 1   # part out of range
     assert "range" in lib.slr_last_error_message().decode()
+
+
+@pytest.mark.parametrize("reserved", [{0: 3}, {1: 2}, {2: 1}, {2: 9}, {3: 2}, {4: -1}, {4: 2}, {5: 1}])
+def test_setup_rejects_bad_tuning_options(lib, reserved):
+    """Band split, host loop, band buffers, C-solve path, autotune: out-of-range values
+    are refused before any device work."""
+    rp, ci, v = slrgen.laplacian((6, 5))
+    part = slrgen.box_partition((6, 5), (2, 1))
+    assert _setup_status(lib, rp, ci, v, part, 2, reserved) == 1
+    assert "invalid options" in lib.slr_last_error_message().decode()
 
 
 def test_setup_detects_non_spd_block(lib):

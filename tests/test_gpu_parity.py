@@ -326,3 +326,29 @@ def test_full_size_3d_laplace_64_properties():
     x, its, relres, st = g.pcg(cu(P.b[:, 0]))
     A = sp.csr_matrix((P.val, P.colind, P.rowptr))
     assert st == 0 and np.linalg.norm(P.b[:, 0] - A @ x.cpu().numpy()) <= 2e-8 * np.linalg.norm(P.b[:, 0])
+
+
+@pytest.mark.parametrize("name", ["3d-lap", "3d-196"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_autotuned_handle(name, precision):
+    """Setup with autotune: the choice is reported, cached for the next handle of the
+    same shape, and the tuned operator keeps parity with the oracle."""
+    P = make(name)
+    o = oracle(name)
+    fl = precision == "mixed"
+    g = gpu_handle(P, precision, autotune=True, flexible_cg=fl)
+    inf = g.get_info()
+    assert inf["tuned"] == 1 and inf["band_split"] in (1, 2, 4) and inf["band_slots"] in (2, 3, 4)
+    g2 = gpu_handle(P, precision, autotune=True, flexible_cg=fl)
+    inf2 = g2.get_info()
+    assert inf2["tune_seconds"] == 0.0                 # taken from the cache
+    assert (inf2["band_split"], inf2["band_slots"], inf2["c_persistent"]) == \
+           (inf["band_split"], inf["band_slots"], inf["c_persistent"])
+    f = np.random.default_rng(8).standard_normal((o.order.n_I, 2))
+    assert rel(g.bsolve(cu(f)).cpu().numpy(), o.bsolve.solve(f)) <= (TOL64 if precision == "fp64" else TOL32)
+    gg = np.random.default_rng(9).standard_normal((o.order.s, 2))
+    assert rel(g.csolve(cu(gg)).cpu().numpy(), o.cfac.solve(gg)) <= (TOL64 if precision == "fp64" else TOL32)
+    b = cu(P.b[:, 0])
+    _, it1, _, s1 = g.pcg(b)
+    _, it2, _, s2 = gpu_handle(P, precision, flexible_cg=fl).pcg(b)
+    assert s1 == 0 and s2 == 0 and abs(int(it1[0]) - int(it2[0])) <= 1
