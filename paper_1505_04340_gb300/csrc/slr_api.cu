@@ -493,7 +493,7 @@ slr_status autotune(slr_handle h, DevOperator<T>& op, cudaStream_t st) {
         CK(cudaMemsetAsync(op.gp, 0, sizeof(T) * std::max(hs.s, 1), st));
         double best_us = 1e30;
         for (int32_t G : {1, 2, 4}) {
-            if ((hs.wmax + G - 1) / G > 256 || (G > 1 && hs.wmax < 16 * G) || hs.p * G > 2 * nsm) continue;
+            if (!band_split_ok(hs.wmax, G) || (G > 1 && hs.wmax < 32 * G) || hs.p * G > 2 * nsm) continue;
             if (G != hs.band_G) CS(repack_band<T>(h, op, G));
             for (int32_t slots : {2, 3, 4}) {
                 op.band_nbuf = slots;
@@ -565,15 +565,15 @@ slr_status setup_impl(slr_handle h, int32_t n, const int32_t* rowptr, const int3
                 }
             wmx = std::max(wmx, w);
         }
-        while ((wmx + G - 1) / G > 256 && G < 4) G *= 2;
-        if ((wmx + G - 1) / G > 256) {
+        while (!band_split_ok(wmx, G) && G < 4) G *= 2;
+        if (!band_split_ok(wmx, G)) {
             set_error("a B_i has plane width " + std::to_string(wmx) + " beyond the band kernel's limit (1024)");
             return SLR_ERR_UNSUPPORTED;
         }
         const int32_t req = h->opts.reserved[0];        // opts.band_split, 0 = automatic
         if (req == 1 || req == 2 || req == 4) {
-            if ((wmx + req - 1) / req <= 256) G = req;
-        } else if (G == 1 && 2 * nparts <= nsm && wmx >= 32) {
+            if (band_split_ok(wmx, req)) G = req;
+        } else if (G == 1 && 2 * nparts <= nsm && wmx >= 64) {
             // a subdomain's planes are a dependent chain: with few subdomains two
             // CTAs (a cluster) per subdomain put twice the SMs on it (measured
             // faster in both precisions on 16^3 boxes; four CTAs need two waves)

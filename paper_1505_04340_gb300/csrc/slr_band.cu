@@ -55,11 +55,10 @@ constexpr int kRB = 8;             // row blocks of 32: at most 256 rows per sli
 constexpr long long kSpin = 1ll << 24;   // bounded mbarrier wait (about a second)
 
 // ---- slice geometry (the host packer uses the same rules: band_* in slr_internal.h)
-__device__ __forceinline__ int slice_rows(int W, int G, int g) { return g < W ? (W - 1 - g) / G + 1 : 0; }
-__device__ __forceinline__ int seg_cU0(int W, int G, int g, int rb) { return min(W, G * 32 * rb + g); }
-__device__ __forceinline__ int seg_cL1(int W, int G, int g, int rb) {
-    return min(W, G * min(32 * rb + 31, slice_rows(W, G, g) - 1) + g + 1);
-}
+// local row block with first plane row R0: columns it meets in an upper block
+// start at seg_cU0, in a lower block end before seg_cL1
+__device__ __forceinline__ int seg_cU0(int W, int R0) { return min(W, R0); }
+__device__ __forceinline__ int seg_cL1(int W, int R0) { return min(W, min(R0 + 31, W - 1) + 1); }
 
 // ---- mbarrier / bulk copy PTX
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -111,7 +110,7 @@ __device__ __forceinline__ void cluster_barrier() {
 __device__ __forceinline__ int first_col(int lo, int warp) { return lo + ((warp - lo % kW) + kW) % kW; }
 
 struct Geom {
-    int W, c, g, nrg;
+    int W, c, g;
     int nU, nL;
     int64_t base, PS, SU, SL;
 };
@@ -165,21 +164,24 @@ k_band_solve2(const BandBlock* __restrict__ blocks, const T* __restrict__ fac, c
     q.W = W;
     q.c = c;
     q.g = g;
-    q.nrg = slice_rows(W, G, g);
     q.SU = b.SU;
     q.SL = b.SL;
     q.PS = (int64_t)G * 2 * (b.SU + b.SL);
     q.base = b.foff + (int64_t)g * 2 * (b.SU + b.SL);
 
-    const int nrb = (q.nrg + 31) / 32;
+    // this slice's row blocks: first plane row of each (past W: none)
+    const int nrb = b.nrb[g];
+    int R0[kRB];
+#pragma unroll
+    for (int rb = 0; rb < kRB; ++rb) R0[rb] = rb < nrb ? 32 * b.rbmap[g][rb] : W;
     if (tid == 0) {
         int a = 0, d = 0;
         for (int rb = 0; rb <= kRB; ++rb) {
             segU[rb] = a;
             segL[rb] = d;
             if (rb < nrb) {
-                a += W - seg_cU0(W, G, g, rb);
-                d += seg_cL1(W, G, g, rb);
+                a += W - seg_cU0(W, R0[rb]);
+                d += seg_cL1(W, R0[rb]);
             }
         }
         const int per = max(1, slot / (32 * (int)sizeof(T)));   // whole segments per chunk
@@ -282,7 +284,7 @@ k_band_solve2(const BandBlock* __restrict__ blocks, const T* __restrict__ fac, c
                 if (rb >= nrb) break;
                 const int sa = max(s0, seg[rb]), sb = min(s1, seg[rb + 1]);
                 if (sa >= sb) continue;
-                const int cb0 = upper ? seg_cU0(W, G, g, rb) : 0;       // column of segment seg[rb]
+                const int cb0 = upper ? seg_cU0(W, R0[rb]) : 0;         // column of segment seg[rb]
                 const int ca = cb0 + (sa - seg[rb]), ce = cb0 + (sb - seg[rb]);
                 int cc = first_col(ca, warp);
                 const T* Ps = P + (sa - s0 + (cc - ca)) * 32 + lane;
@@ -315,8 +317,11 @@ k_band_solve2(const BandBlock* __restrict__ blocks, const T* __restrict__ fac, c
     // Each thread owns at most one output row per plane (a slice has at most
     // 256 rows): its right-hand side (forward) or forward result (backward) is
     // loaded before the block product so the load is off the plane-to-plane chain.
-    const bool owner = tid < q.nrg;
-    const int own_r = tid * G + g;
+    int own_r = W;
+#pragma unroll
+    for (int rb = 0; rb < kRB; ++rb)
+        if ((tid >> 5) == rb) own_r = R0[rb] + (tid & 31);
+    const bool owner = tid < 32 * nrb && own_r < W;
     // =================================================================== forward
     for (int J = 0; J < c; ++J) {
         const int row = J * W + own_r;

@@ -16,6 +16,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -193,10 +194,71 @@ static void tri_inverse(int W, const double* D, double* X) {
     }
 }
 
+// Block k of a plane (rows 32 k .. min(32 k + 32, W) - 1) costs sum (W - r) in the
+// upper blocks and sum (r + 1) in the lower ones.  Each slice gets at most 8
+// blocks; the assignment minimises the larger of the two sums over the slices
+// (exhaustively for up to 2^18 assignments, else by dealing blocks from both ends
+// round-robin).  Inside a slice, blocks keep ascending order.
+void band_assign_blocks(BandBlock& b, int G) {
+    const int W = b.w, nb = (W + 31) / 32;
+    std::memset(b.nrb, 0, sizeof(b.nrb));
+    std::memset(b.rbmap, 0, sizeof(b.rbmap));
+    std::vector<int> owner(nb, 0);
+    if (G > 1 && nb > 0) {
+        std::vector<double> up(nb), lo(nb);
+        for (int k = 0; k < nb; ++k)
+            for (int r = 32 * k; r < std::min(W, 32 * k + 32); ++r) {
+                up[k] += W - r;
+                lo[k] += r + 1;
+            }
+        auto cost = [&](const std::vector<int>& own) {
+            double U[4] = {0, 0, 0, 0}, L[4] = {0, 0, 0, 0};
+            int cnt[4] = {0, 0, 0, 0};
+            for (int k = 0; k < nb; ++k) {
+                U[own[k]] += up[k];
+                L[own[k]] += lo[k];
+                ++cnt[own[k]];
+            }
+            double c = 0;
+            for (int g = 0; g < G; ++g) {
+                if (cnt[g] > 8) return 1e300;
+                c = std::max(c, std::max(U[g], L[g]));
+            }
+            return c;
+        };
+        double total = 1;
+        for (int k = 0; k < nb; ++k) total *= G;
+        if (total <= double(1 << 18)) {
+            std::vector<int> cur(nb, 0);
+            double best = 1e301;
+            for (long long code = 0; code < (long long)total; ++code) {
+                long long x = code;
+                for (int k = 0; k < nb; ++k, x /= G) cur[k] = (int)(x % G);
+                const double c = cost(cur);
+                if (c < best) {
+                    best = c;
+                    owner = cur;
+                }
+            }
+        } else {
+            int g = 0;
+            for (int lo_k = 0, hi_k = nb - 1; lo_k <= hi_k; ++lo_k, --hi_k, g = (g + 1) % G) {
+                owner[lo_k] = g;
+                owner[hi_k] = g;
+            }
+        }
+    }
+    for (int k = 0; k < nb; ++k) {
+        const int g = owner[k];
+        b.rbmap[g][b.nrb[g]++] = (uint8_t)k;
+    }
+}
+
 slr_status host_band_factor(HostSetup& hs, int32_t G) {
     const int32_t p = hs.p;
     hs.band.assign(p, BandBlock());
     std::vector<int32_t> bw(p, 0);
+    std::map<int32_t, BandBlock> assigned;   // block assignment per plane width
     int64_t off = 0;
     hs.wmax = 0;
     for (int32_t i = 0; i < p; ++i) {
@@ -212,12 +274,22 @@ slr_status host_band_factor(HostSetup& hs, int32_t G) {
         b.row0 = r0;
         b.w = m ? std::max(w, 1) : 0;
         b.c = m ? (m + b.w - 1) / b.w : 0;
+        if (m) {
+            auto it = assigned.find(b.w);
+            if (it == assigned.end()) {
+                band_assign_blocks(b, G);
+                assigned[b.w] = b;
+            } else {
+                std::memcpy(b.nrb, it->second.nrb, sizeof(b.nrb));
+                std::memcpy(b.rbmap, it->second.rbmap, sizeof(b.rbmap));
+            }
+        }
         int so = 0, sd = 0;   // segments of the widest slice
         for (int g = 0; g < G; ++g) {
             int a = 0, d = 0;
-            for (int rb = 0; rb < band_nrb(b.w, G, g); ++rb) {
-                a += b.w - band_cU0(b.w, G, g, rb);
-                d += band_cL1(b.w, G, g, rb);
+            for (int rb = 0; rb < b.nrb[g]; ++rb) {
+                a += b.w - band_cU0(b, g, rb);
+                d += band_cL1(b, g, rb);
             }
             so = std::max(so, a);
             sd = std::max(sd, d);
@@ -283,20 +355,20 @@ slr_status host_band_factor(HostSetup& hs, int32_t G) {
                 double* Lf = Uf + b.SU;                                 // D_J      (lower)
                 double* Lb = Lf + b.SL;                                 // O_J^T    (lower)
                 double* Ub = Lb + b.SL;                                 // D_J^T    (upper)
-                const int nrg = band_slice_rows(W, G, g);
                 int64_t su = 0, sl = 0;   // next upper / lower segment
-                for (int rb = 0; rb < band_nrb(W, G, g); ++rb) {
-                    for (int cc = band_cU0(W, G, g, rb); cc < W; ++cc, ++su)      // upper: rows r <= cc
+                for (int rb = 0; rb < b.nrb[g]; ++rb) {
+                    const int R0 = band_R0(b, g, rb);
+                    for (int cc = band_cU0(b, g, rb); cc < W; ++cc, ++su)      // upper: rows r <= cc
                         for (int e = 0; e < 32; ++e) {
-                            const int lr = 32 * rb + e, r = lr * G + g, l = J * W + r;
-                            if (lr >= nrg || r > cc) continue;
+                            const int r = R0 + e, l = J * W + r;
+                            if (r >= W || r > cc) continue;
                             Uf[su * 32 + e] = (J > 0 && l < m) ? Lat(l, (J - 1) * W + cc) : 0.0;   // O_J[r][cc]
                             Ub[su * 32 + e] = X[(size_t)cc * W + r];                             // D_J^{-1}[cc][r]
                         }
-                    for (int cc = 0; cc < band_cL1(W, G, g, rb); ++cc, ++sl)      // lower: rows r >= cc
+                    for (int cc = 0; cc < band_cL1(b, g, rb); ++cc, ++sl)      // lower: rows r >= cc
                         for (int e = 0; e < 32; ++e) {
-                            const int lr = 32 * rb + e, r = lr * G + g, lc = J * W + cc;
-                            if (lr >= nrg || r < cc) continue;
+                            const int r = R0 + e, lc = J * W + cc;
+                            if (r >= W || r < cc) continue;
                             Lf[sl * 32 + e] = X[(size_t)r * W + cc];                             // D_J^{-1}[r][cc]
                             Lb[sl * 32 + e] = (J > 0 && lc < m) ? Lat(lc, (J - 1) * W + r) : 0.0;   // O_J[cc][r]
                         }

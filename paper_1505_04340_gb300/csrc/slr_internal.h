@@ -13,19 +13,20 @@ namespace slr {
 
 // ---------------------------------------------------------------- host setup
 
-// One interior block B_i of the partition (Section 5.2).  Its Cholesky factor
-// L_i is banded with half-bandwidth w (natural, ascending-index order).  Rows
-// are grouped in planes of W = clamp(w, 1, m) rows; for plane J
-//   O_J = L_i[plane J, plane J-1]     upper triangular incl. diagonal,
-//   D_J = L_i[plane J, plane J]^{-1}  lower triangular incl. diagonal (inverted).
-// The forward solve applies O_J (upper) and D_J (lower); the backward solve
-// applies O_J^T (lower) and D_J^T (upper), stored separately so that both
-// passes compute "output row = sum over columns".  Output rows r of a plane are
-// dealt to G slices (r mod G).  A slice of an upper block is packed column-major
-// with column c holding the slice's rows r <= c; a slice of a lower block with
-// column q holding its rows r >= q.  Per plane and slice: [O_J | D_J | O_J^T |
-// D_J^T] = [SU | SL | SL | SU] elements; a plane occupies G * 2 (SU + SL).  The
-// last plane is padded with identity rows.  (Shared with slr_band.cu.)
+// Band factor layout (Section 5.2).  B_i = L_i L_i^T is banded with
+// half-bandwidth w; rows are grouped in planes of W = w rows.  For plane J:
+// O_J = L[J, J-1] (upper triangular), D_J = L[J, J]^{-1} (lower, inverted on the
+// host) and their transposes O_J^T (lower), D_J^T (upper): each of the four
+// products of a pass is "output row = sum over columns".  The W rows of a plane
+// form 32-row blocks; block k holds rows 32 k .. 32 k + 31.  The G CTAs of a
+// cluster (slices) each own whole blocks, assigned so that the slices' shares
+// of upper-block and lower-block work are even (band_assign_blocks); slice g's
+// local row block rb is block rbmap[g][rb].  A slice of a block is tiled: for
+// every (local row block, column) pair that meets the triangle, one segment of
+// 32 values (zero outside the triangle and past W), row blocks one after the
+// other, columns ascending.  Per plane and slice: [O_J | D_J | O_J^T | D_J^T] =
+// [SU | SL | SL | SU] elements; a plane occupies G * 2 (SU + SL).  The last plane
+// is padded with identity rows.  (Shared with slr_band.cu.)
 struct BandBlock {
     int32_t m = 0;        // rows of B_i
     int32_t w = 0;        // plane width W
@@ -34,23 +35,22 @@ struct BandBlock {
     int64_t foff = 0;     // offset of plane 0 in the factor array (elements)
     int32_t SU = 0;       // elements of one upper slice block (32 per segment, widest slice)
     int32_t SL = 0;       // elements of one lower slice block (32 per segment, widest slice)
+    uint8_t nrb[4] = {0, 0, 0, 0};   // row blocks of each slice (at most 8: 256 rows)
+    uint8_t rbmap[4][8] = {};        // block of slice g's local row block rb
 };
 
-// Slice geometry of the band layout (host packer and device kernel agree on it).
-inline int band_slice_rows(int W, int G, int g) { return g < W ? (W - 1 - g) / G + 1 : 0; }
-inline int band_cnt_O(int c, int G, int g) { return c >= g ? (c - g) / G + 1 : 0; }
-inline int band_lr0_D(int q, int G, int g) { return q <= g ? 0 : (q - g + G - 1) / G; }
-// Tiled slices.  Row block rb holds slice rows 32 rb .. 32 rb + 31.  In an
-// upper block (O_J, D_J^T) it meets columns [band_cU0, W); in a lower block
-// (D_J, O_J^T) columns [0, band_cL1).  Each (row block, column) pair is one
-// segment of 32 values (zero outside the triangle and past the slice), stored
-// row block by row block, columns ascending.
-inline int band_nrb(int W, int G, int g) { return (band_slice_rows(W, G, g) + 31) / 32; }
-inline int band_cU0(int W, int G, int g, int rb) { return std::min(W, G * 32 * rb + g); }
-inline int band_cL1(int W, int G, int g, int rb) {
-    const int L = std::min(32 * rb + 31, band_slice_rows(W, G, g) - 1);
-    return std::min(W, G * L + g + 1);
+// Slice geometry (the host packer and the device kernel agree on it).
+// Local row block rb of slice g starts at plane row band_R0; in an upper block
+// it meets columns [band_cU0, W), in a lower block columns [0, band_cL1).
+inline int band_R0(const BandBlock& b, int g, int rb) { return 32 * b.rbmap[g][rb]; }
+inline int band_cU0(const BandBlock& b, int g, int rb) { return std::min(b.w, band_R0(b, g, rb)); }
+inline int band_cL1(const BandBlock& b, int g, int rb) {
+    return std::min(b.w, std::min(band_R0(b, g, rb) + 31, b.w - 1) + 1);
 }
+// True if G slices can hold a plane of W rows (at most 8 blocks of 32 rows each).
+inline bool band_split_ok(int W, int G) { return (W + 31) / 32 <= 8 * G; }
+// Deal the 32-row blocks of a plane of b.w rows to G slices (fills nrb, rbmap).
+void band_assign_blocks(BandBlock& b, int G);
 
 // Supernodal Cholesky factor of the interface matrix C (Eq. 3.1) in a
 // nested-dissection order.  Supernode J owns factor positions [c0[J], c0[J+1]).
