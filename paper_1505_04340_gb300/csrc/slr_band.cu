@@ -23,6 +23,8 @@
 // warp releases a buffer on its "empty" mbarrier when done with it; thread 0
 // refills a buffer once all warps have released it, so copies run ahead of the
 // slowest warp across planes and phases with no CTA-wide barrier per chunk.
+// The cluster exchange between phases is a split barrier: arrive after the
+// stores into the peers, wait once the next block's first data has landed.
 // Every wait is a bounded spin that sets a device status word instead of
 // hanging.  Warp w takes the columns c = w (mod 16) of every row block, so a
 // warp's partial sums (added once per phase) do not depend on the chunking.
@@ -94,6 +96,21 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+// Split cluster barrier: arrive after a phase's stores into the peers, wait just
+// before the next phase reads them (with one CTA: a CTA barrier at the wait).
+template <int G>
+__device__ __forceinline__ void cluster_arrive() {
+    if constexpr (G > 1) asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+}
+template <int G>
+__device__ __forceinline__ void cluster_wait() {
+    if constexpr (G > 1) {
+        asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+    } else {
+        __syncthreads();
+    }
+}
 
 template <int G>
 __device__ __forceinline__ void cluster_barrier() {
@@ -263,6 +280,7 @@ k_band_solve2(const BandBlock* __restrict__ blocks, const T* __restrict__ fac, c
     cluster_barrier<G>();
 
     int k = 0;
+    bool pending = false;      // a cluster arrive waits for its wait (uniform in the cluster)
     T acc[kRB][NR];
     // acc[rb][j] += sum over the chunks of one block of M[lr][cc] * vin[j][cc], lanes = rows
     // acc[rb][j] = sum over the block's segments of row block rb of seg[lane] * vin[j][column]
@@ -277,6 +295,10 @@ k_band_solve2(const BandBlock* __restrict__ blocks, const T* __restrict__ fac, c
         for (int ix = 0; ix < nch; ++ix, ++k) {
             refill(k);
             wait_full(k);
+            if (pending) {                 // the input vector's last stores (peers included)
+                cluster_wait<G>();
+                pending = false;
+            }
             const int s0 = ix * per, s1 = min(s0 + per, seg[kRB]);
             const T* P = reinterpret_cast<const T*>(ring + (size_t)(k % nbuf) * slot);
 #pragma unroll
@@ -301,9 +323,17 @@ k_band_solve2(const BandBlock* __restrict__ blocks, const T* __restrict__ fac, c
         for (int rb = 0; rb < kRB; ++rb)
 #pragma unroll
             for (int j = 0; j < NR; ++j) part[(warp * NR + j) * 256 + rb * 32 + lane] = acc[rb][j];
+        if (pending) {                     // a block without chunks (a slice without rows)
+            cluster_wait<G>();
+            pending = false;
+        }
         __syncthreads();
     };
     auto zero_part = [&]() {
+        if (pending) {
+            cluster_wait<G>();
+            pending = false;
+        }
         for (int i = tid; i < kW * NR * 256; i += kT) part[i] = T(0);
         __syncthreads();
     };
@@ -337,7 +367,8 @@ k_band_solve2(const BandBlock* __restrict__ blocks, const T* __restrict__ fac, c
                 for (int pr = 0; pr < G; ++pr) peer(vt, pr)[j * W + own_r] = t;
             }
         }
-        cluster_barrier<G>();
+        cluster_arrive<G>();
+        pending = true;
         run_block(1, J, vt);                                               // D_J t
         if (owner) {
 #pragma unroll
@@ -348,7 +379,8 @@ k_band_solve2(const BandBlock* __restrict__ blocks, const T* __restrict__ fac, c
                 for (int pr = 0; pr < G; ++pr) peer(vst, pr)[j * W + own_r] = y;
             }
         }
-        cluster_barrier<G>();
+        cluster_arrive<G>();
+        pending = true;
     }
     // =================================================================== backward
     for (int J = c - 1; J >= 0; --J) {
@@ -369,7 +401,8 @@ k_band_solve2(const BandBlock* __restrict__ blocks, const T* __restrict__ fac, c
                 for (int pr = 0; pr < G; ++pr) peer(vt, pr)[j * W + own_r] = t;
             }
         }
-        cluster_barrier<G>();
+        cluster_arrive<G>();
+        pending = true;
         run_block(3, J, vt);                                               // D_J^T t
         if (owner) {
 #pragma unroll
@@ -380,8 +413,10 @@ k_band_solve2(const BandBlock* __restrict__ blocks, const T* __restrict__ fac, c
                 for (int pr = 0; pr < G; ++pr) peer(vst, pr)[j * W + own_r] = x;
             }
         }
-        cluster_barrier<G>();
+        cluster_arrive<G>();
+        pending = true;
     }
+    if (pending) cluster_wait<G>();    // no CTA leaves while a peer may still store into it
 }
 
 // Shared memory besides the ring (barriers, column tables, vectors, partials,
