@@ -76,6 +76,25 @@ __global__ void k_spmv(int32_t rows, int32_t nrhs, const int32_t* __restrict__ r
 // between dependent steps.
 __device__ __forceinline__ int64_t packed_col(int j, int n) { return (int64_t)j * n - (int64_t)j * (j - 1) / 2; }
 
+// sum of w[seg_row[e]] for e = e0 .. e1-1, in that order: indices and values are
+// loaded 8 at a time so that the two dependent loads are not paid per term
+template <typename T>
+__device__ __forceinline__ T gather_sum(const T* w, const int32_t* __restrict__ seg_row, int64_t e0, int64_t e1) {
+    T acc = T(0);
+    for (int64_t e = e0; e < e1; e += 8) {
+        int32_t idx[8];
+        T v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) idx[u] = e + u < e1 ? seg_row[e + u] : -1;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = idx[u] >= 0 ? w[idx[u]] : T(0);
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            if (e + u < e1) acc += v[u];
+    }
+    return acc;
+}
+
 // forward, gather (one warp): t_i = g[cperm[i]] - sum of the panel products w that hold row i
 template <typename T>
 __device__ __forceinline__ void cfwd_gather_warp(const int4 tk, int lane, const int32_t* __restrict__ c0,
@@ -88,9 +107,7 @@ __device__ __forceinline__ void cfwd_gather_warp(const int4 tk, int lane, const 
     const int64_t e0 = seg_ptr[i], e1 = seg_ptr[i + 1];
     for (int j = 0; j < nrhs; ++j) {
         const T* w = wbuf + (int64_t)j * nrow;
-        T acc = T(0);
-        for (int64_t e = e0; e < e1; ++e) acc += w[seg_row[e]];
-        tf[i + (int64_t)j * s] = g[cperm[i] + j * ldg] - acc;
+        tf[i + (int64_t)j * s] = g[cperm[i] + j * ldg] - gather_sum(w, seg_row, e0, e1);
     }
 }
 
@@ -153,14 +170,17 @@ __device__ void cfwd_panel_cta(const int4 tk, T* xs, const int32_t* __restrict__
         for (int pr = warp; pr < tk.z; pr += NW) {
             const int64_t p = tk.y + pr;
             const T* P = panel + pan_off[tk.x] + p * nJ;
-            T acc0 = T(0), acc1 = T(0);
+            T acc = T(0);
             int c = lane;
-            for (; c + 32 < nJ; c += 64) {
-                acc0 += P[c] * xs[c];
-                acc1 += P[c + 32] * xs[c + 32];
+            for (; c + 7 * 32 < nJ; c += 8 * 32) {
+                T pv[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) pv[u] = P[c + 32 * u];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) acc += pv[u] * xs[c + 32 * u];
             }
-            if (c < nJ) acc0 += P[c] * xs[c];
-            const T acc = warp_sum(acc0 + acc1);
+            for (; c < nJ; c += 32) acc += P[c] * xs[c];
+            acc = warp_sum(acc);
             if (lane == 0) wbuf[r_off[tk.x] + p + (int64_t)j * nrow] = acc;
         }
         __syncthreads();
@@ -169,7 +189,7 @@ __device__ void cfwd_panel_cta(const int4 tk, T* xs, const int32_t* __restrict__
 
 // backward, panel (one CTA): t_j = y_j - sum_p L[R_J[p], j] x[R_J[p]] for <= 32
 // columns (lane = column); the warps split the panel rows, 8 loads in flight
-template <typename T, int NW>
+template <typename T, int NW, int DEPTH = 8>
 __device__ void cbwd_panel_cta(const int4 tk, T (*red)[33], const int32_t* __restrict__ c0,
                                const int64_t* __restrict__ r_off, const int32_t* __restrict__ rows,
                                const int64_t* __restrict__ pan_off, const T* __restrict__ panel, T* yf,
@@ -185,15 +205,15 @@ __device__ void cbwd_panel_cta(const int4 tk, T (*red)[33], const int32_t* __res
         T acc = T(0);
         if (lane < tk.z) {
             int64_t p = pb;
-            for (; p + 7 < pe; p += 8) {
-                T pv[8], xv[8];
+            for (; p + DEPTH - 1 < pe; p += DEPTH) {
+                T pv[DEPTH], xv[DEPTH];
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
+                for (int u = 0; u < DEPTH; ++u) {
                     pv[u] = Pn[(p + u) * nJ];
                     xv[u] = x[R[p + u]];
                 }
 #pragma unroll
-                for (int u = 0; u < 8; ++u) acc += pv[u] * xv[u];
+                for (int u = 0; u < DEPTH; ++u) acc += pv[u] * xv[u];
             }
             for (; p < pe; ++p) acc += Pn[p * nJ] * x[R[p]];
         }
@@ -276,9 +296,7 @@ __device__ void cfwd_small_cta(int J, T* ts, T* xs, const int32_t* __restrict__ 
         const T* w = wbuf + (int64_t)j * nrow;
         for (int i = gt; i < nJ; i += NT) {
             const int32_t pos = a0 + i;
-            T acc = T(0);
-            for (int64_t e = seg_ptr[pos]; e < seg_ptr[pos + 1]; ++e) acc += w[seg_row[e]];
-            ts[i] = g[cperm[pos] + j * ldg] - acc;
+            ts[i] = g[cperm[pos] + j * ldg] - gather_sum(w, seg_row, seg_ptr[pos], seg_ptr[pos + 1]);
         }
         group_sync<NT, GROUPS>();
         for (int i = gt; i < nJ; i += NT) {
@@ -376,7 +394,8 @@ __device__ void cbwd_small_cta(int J, T* xr, T* ts, T* red, const int32_t* __res
 }
 
 constexpr int kDiagT = 1024;   // threads of the per-level diagonal-block kernels (32 warps)
-constexpr int kPanT = 512;     // threads of the per-level panel kernels (16 warps)
+constexpr int kPanT = 512;     // threads of the per-level forward panel kernels (16 warps)
+constexpr int kBPanT = 1024;   // threads of the per-level backward panel kernels (32 warps)
 
 // ---- per-level kernels: one launch per step
 template <typename T>
@@ -405,13 +424,15 @@ k_cfwd_panel(const int4* __restrict__ ptasks, const int32_t* __restrict__ c0, co
                                   wbuf, nrow, s, nrhs);
 }
 
+// one CTA of 32 warps per 32-column task, 16 (FP32) or 8 (FP64) panel loads in flight per lane
 template <typename T>
-__global__ void __launch_bounds__(kPanT)
+__global__ void __launch_bounds__(kBPanT)
 k_cbwd_panel(const int4* __restrict__ tasks, const int32_t* __restrict__ c0, const int64_t* __restrict__ r_off,
              const int32_t* __restrict__ rows, const int64_t* __restrict__ pan_off, const T* __restrict__ panel,
              T* yf, const T* xf, int32_t s, int32_t nrhs) {
-    __shared__ T red[kPanT / 32][33];
-    cbwd_panel_cta<T, kPanT / 32>(tasks[blockIdx.x], red, c0, r_off, rows, pan_off, panel, yf, xf, s, nrhs);
+    __shared__ T red[kBPanT / 32][33];
+    cbwd_panel_cta<T, kBPanT / 32, sizeof(T) == 4 ? 16 : 8>(tasks[blockIdx.x], red, c0, r_off, rows, pan_off, panel,
+                                                            yf, xf, s, nrhs);
 }
 
 template <typename T>
@@ -955,7 +976,7 @@ cudaError_t launch_c_backward(const DevCFactor<T>& cf, T* yf, T* xf, T* y_dd, in
         }
         const int t0 = cf.lev_task_ptr[l], nt = cf.lev_task_ptr[l + 1] - t0;
         if (nt == 0) continue;
-        k_cbwd_panel<T><<<nt, kPanT, 0, st>>>(cf.tasks + t0, cf.c0, cf.r_off, cf.rows, cf.pan_off, cf.panel,
+        k_cbwd_panel<T><<<nt, kBPanT, 0, st>>>(cf.tasks + t0, cf.c0, cf.r_off, cf.rows, cf.pan_off, cf.panel,
                                               yf, xf, cf.s, nrhs);
         counted();
         k_cbwd_diag<T><<<nt, kDiagT, 0, st>>>(cf.tasks + t0, cf.c0, cf.dinv_off, cf.dinv, cf.cperm, yf, xf,
