@@ -295,11 +295,13 @@ class SLR:
 
     ``eig='lanczos'`` follows Section 5.1 (m = lanczos_steps, default 5k);
     ``eig='dense'`` takes exact eigenpairs of a densely formed H (tiny
-    problems only; used for the rank-s identity checks).
+    problems only; used for the rank-s identity checks).  ``target_kappa``:
+    choose the rank by the rule of Section 4 (Eq. condk), k = the number of
+    eigenvalue estimates above 1 - 1/K, at most ``k``.
     """
 
     def __init__(self, rowptr, colind, val, part, nparts, k, lanczos_steps=None,
-                 theta_mode=THETA_LAMBDA_K1, seed=1, eig="lanczos", c_route="auto"):
+                 theta_mode=THETA_LAMBDA_K1, seed=1, eig="lanczos", c_route="auto", target_kappa=None):
         self.order = dd_order(rowptr, colind, part, nparts)
         Bi, E, C, App = split_blocks(rowptr, colind, val, self.order)
         self.E, self.C, self.App = E, C, App
@@ -322,6 +324,10 @@ class SLR:
             a, b, V = lanczos(lambda v: h_apply(v, E, self.bsolve, self.cfac), v1, m)
             lam, U = ritz(a, b, V)
         self.k = k = min(k, U.shape[1])
+        if target_kappa is not None and k > 0:
+            # rank rule of Section 4 (Eq. condk): the condition number of S S~^{-1} stays below K
+            # when lambda_{k+1} <= 1 - 1/K, i.e. k = number of eigenvalues above 1 - 1/K (capped)
+            self.k = k = min(k, int(np.sum(lam > 1.0 - 1.0 / target_kappa)))
         self.ritz_values = lam
         self.lam = lam[:k].copy()
         self.U = U[:, :k].copy()

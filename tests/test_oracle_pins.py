@@ -236,6 +236,41 @@ def test_prop_eigSS(theta_mode):
     assert kap == pytest.approx(float(brute.kappa(theta, lam[-1], lam[k])), rel=1e-8)
 
 
+@pytest.mark.parametrize("K", [1.5, 3.0, 10.0, 40.0])
+def test_rank_rule_bounds_condition_number(K):
+    """Rank rule of Section 4 (Eq. condk): with exact eigenpairs, k = #{lambda_i > 1 - 1/K}
+    (counted on an H formed densely from the blocks, not by the oracle) and, with
+    theta = lambda_{k+1}, the condition number of S S~^{-1} is at most K."""
+    P = small_fv()
+    slr = SLR(P.rowptr, P.colind, P.val, P.part, P.nparts, 10 ** 6, eig="dense", target_kappa=K)
+    B, E, C = brute.dense_blocks(slr)
+    lam = np.sort(np.linalg.eigvalsh(brute.h_from_blocks(B, E, C)))[::-1]
+    assert not np.any(np.abs(lam - (1 - 1 / K)) < 1e-9)          # no tie at the threshold
+    assert slr.k == int(np.sum(lam > 1 - 1 / K))
+    S = brute.schur(B, E, C)
+    sig = np.linalg.eigvals(S @ slr.stilde_inv(np.eye(S.shape[0]))).real
+    assert sig.max() / sig.min() <= K * (1 + 1e-9)
+    # the rule picks the smallest such rank: one vector fewer breaks the bound
+    if slr.k > 0:
+        fewer = SLR(P.rowptr, P.colind, P.val, P.part, P.nparts, slr.k - 1, eig="dense")
+        sig2 = np.linalg.eigvals(S @ fewer.stilde_inv(np.eye(S.shape[0]))).real
+        assert sig2.max() / sig2.min() > K
+
+
+def test_rank_rule_with_lanczos_caps_at_k():
+    """With Lanczos (Section 5.1) the rule counts Ritz values; the requested k is a cap."""
+    P = slrgen.config1()
+    full = SLR(P.rowptr, P.colind, P.val, P.part, P.nparts, 8, lanczos_steps=40)
+    lam = full.ritz_values
+    K = 4.0
+    want = min(8, int(np.sum(lam > 1 - 1 / K)))
+    got = SLR(P.rowptr, P.colind, P.val, P.part, P.nparts, 8, lanczos_steps=40, target_kappa=K)
+    assert got.k == want and np.allclose(got.lam, lam[:want])
+    assert got.theta == pytest.approx(lam[want])
+    capped = SLR(P.rowptr, P.colind, P.val, P.part, P.nparts, 2, lanczos_steps=40, target_kappa=1.05)
+    assert capped.k == 2
+
+
 def test_prop_kappa_piecewise_sweep():
     lam = np.sort(brute.two_domain_lambda(40, 19))[::-1]
     k = 6
