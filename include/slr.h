@@ -84,7 +84,11 @@ typedef struct {
                                that fit, and both C-solve paths, on this operator, and
                                keeps the fastest; the choice is cached per device,
                                precision and problem shape for the process's life.
-                               The rest must be 0.                                      */
+                               reserved[5]: a target condition number K >= 2 for S S~^{-1}
+                               (0 = off): the rank becomes the number of Ritz values
+                               above 1 - 1/K, at most k (Section 4, Eq. condk:
+                               lambda_{k+1} <= 1 - 1/K keeps the condition number of
+                               S S~^{-1} below K).  slr_get_info reports the rank used. */
 } slr_opts;
 
 typedef struct {

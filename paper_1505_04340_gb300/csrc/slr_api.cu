@@ -336,6 +336,14 @@ slr_status run_lanczos(slr_handle h, cudaStream_t st) {
     std::vector<double> lam(m_eff), Y((size_t)m_eff * m_eff);
     host_tridiag_eig(m_eff, alpha.data(), beta.data(), lam.data(), Y.data());
     k = std::min(k, m_eff);
+    if (h->opts.reserved[5] >= 2) {
+        // rank rule of Section 4 (Eq. condk): the condition number of S S~^{-1} stays
+        // below K when lambda_{k+1} <= 1 - 1/K; keep the Ritz values above 1 - 1/K
+        const double thr = 1.0 - 1.0 / (double)h->opts.reserved[5];
+        int32_t cnt = 0;
+        while (cnt < m_eff && lam[cnt] > thr) ++cnt;   // descending
+        k = std::min(k, cnt);
+    }
     h->ritz = lam;
     h->nritz = m_eff;
     h->m_steps = m_eff;
@@ -795,7 +803,7 @@ slr_status slr_setup(int32_t n, const int32_t* rowptr, const int32_t* colind, co
         h->opts.reserved[1] < 0 || h->opts.reserved[1] > 1 ||
         h->opts.reserved[2] < 0 || h->opts.reserved[2] == 1 || h->opts.reserved[2] > 8 ||
         h->opts.reserved[3] < 0 || h->opts.reserved[3] > 1 || h->opts.reserved[4] < 0 || h->opts.reserved[4] > 1 ||
-        h->opts.reserved[5] != 0) {
+        h->opts.reserved[5] < 0 || h->opts.reserved[5] == 1) {
         set_error("invalid options");
         delete h;
         return SLR_ERR_INVALID_ARG;

@@ -159,7 +159,8 @@ class SLR:
 
     def __init__(self, rowptr, colind, val, part, nparts, k=16, lanczos_steps=0, theta="lambda_k1",
                  precision="fp64", nrhs_max=1, flexible_cg=False, seed=1, c_leaf=64, verbose=False,
-                 band_split=0, host_loop=False, band_slots=0, c_persistent=False, autotune=False, stream=None):
+                 band_split=0, host_loop=False, band_slots=0, c_persistent=False, autotune=False, target_kappa=0,
+                 stream=None):
         lib = load()
         self._lib = lib
         self._h = None
@@ -174,6 +175,7 @@ class SLR:
         o.reserved[2] = int(band_slots)        # band-solve stream buffers, 0 = automatic
         o.reserved[3] = int(bool(c_persistent))  # C solves in one cooperative launch per direction
         o.reserved[4] = int(bool(autotune))      # time the candidates at setup and keep the fastest
+        o.reserved[5] = int(target_kappa)        # rank by the rule lambda_{k+1} <= 1 - 1/K (0 = off)
         self.rowptr, self.colind = _i32(rowptr), _i32(colind)
         self.val = np.ascontiguousarray(val, dtype=np.float64)
         self.part = _i32(part)

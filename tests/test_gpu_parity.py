@@ -352,3 +352,24 @@ def test_autotuned_handle(name, precision):
     _, it1, _, s1 = g.pcg(b)
     _, it2, _, s2 = gpu_handle(P, precision, flexible_cg=fl).pcg(b)
     assert s1 == 0 and s2 == 0 and abs(int(it1[0]) - int(it2[0])) <= 1
+
+
+@pytest.mark.parametrize("name,K", [("c1-lap32", 3), ("c1-lap32", 10), ("3d-lap", 4), ("fv-ragged", 20)])
+def test_target_condition_number_rank(name, K):
+    """Rank rule of Section 4 (Eq. condk): the GPU keeps the same number of Ritz values
+    above 1 - 1/K as the oracle, and a tighter K never needs more iterations."""
+    P = make(name)
+    cap = 40
+    o = OracleSLR(P.rowptr, P.colind, P.val, P.part, P.nparts, cap, P.lanczos_steps, target_kappa=K)
+    near = np.abs(o.ritz_values - (1 - 1 / K)).min()
+    if near < 1e-6:
+        pytest.skip("a Ritz value sits on the threshold")
+    g = SLR(P.rowptr, P.colind, P.val, P.part, P.nparts, k=cap, lanczos_steps=P.lanczos_steps, target_kappa=K)
+    assert g.get_info()["k"] == o.k
+    b = cu(P.b[:, 0])
+    _, it_k, _, st = g.pcg(b)
+    loose = SLR(P.rowptr, P.colind, P.val, P.part, P.nparts, k=cap, lanczos_steps=P.lanczos_steps,
+                target_kappa=4 * K)
+    _, it_loose, _, st2 = loose.pcg(b)
+    assert st == 0 and st2 == 0
+    assert loose.get_info()["k"] <= o.k and int(it_k[0]) <= int(it_loose[0]) + 1
