@@ -310,6 +310,8 @@ class SLR:
         s = self.order.s
         self.k = k = int(min(k, s))
         self.theta_mode = theta_mode
+        self.seed = seed
+        self.improvements = 0
         if k == 0 or s == 0:
             lam = np.zeros(1)
             U = np.zeros((s, 0))
@@ -335,6 +337,40 @@ class SLR:
             self.theta = float(lam[k])
         else:
             self.theta = 0.0
+
+    # -- Section 5.3: improve the preconditioner by adding vectors, keeping U_k
+    def improve(self, k_add, lanczos_steps=None):
+        """Append k_add eigenvector estimates of H without discarding U_k.
+
+        Deflation: Lanczos (Section 5.1, full reorthogonalisation) on
+        P H P with P = I - U_k U_k^T, started from L^{-1} C z (stream seed + 1 +
+        the number of earlier improvements) projected out of span(U_k).  Its
+        leading Ritz pairs approximate lambda_{k+1}, ...; they are appended to
+        (Lambda_k, U_k) and theta = lambda_{k+1} moves to the next Ritz value of
+        the deflated run (theta = 0 stays 0).
+        """
+        s = self.order.s
+        U = self.U
+        m = lanczos_steps if lanczos_steps is not None else 5 * k_add
+
+        def proj(x):
+            for _ in range(2):                       # two classical Gram-Schmidt passes
+                x = x - U @ (U.T @ x)
+            return x
+
+        self.improvements += 1
+        v1 = proj(lanczos_start(self.cfac, self.C, self.seed + self.improvements))
+        m = min(m, s - U.shape[1])
+        a, b, V = lanczos(lambda v: proj(h_apply(v, self.E, self.bsolve, self.cfac)), v1, m)
+        lam2, U2 = ritz(a, b, V)
+        j = min(k_add, U2.shape[1])
+        self.U = np.hstack([U, U2[:, :j]])
+        self.lam = np.concatenate([self.lam, lam2[:j]])
+        self.k += j
+        self.ritz_values = np.concatenate([self.lam, lam2[j:]])
+        if self.theta_mode == THETA_LAMBDA_K1:
+            self.theta = float(lam2[j]) if len(lam2) > j else 0.0
+        return j
 
     # H formed column by column (brute force aid for tiny problems)
     def h_dense(self):

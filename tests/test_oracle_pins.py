@@ -271,6 +271,41 @@ def test_rank_rule_with_lanczos_caps_at_k():
     assert capped.k == 2
 
 
+@pytest.mark.parametrize("theta_mode", [THETA_LAMBDA_K1, THETA_ZERO])
+def test_improve_by_deflation_adds_the_next_eigenpairs(theta_mode):
+    """Section 5.3: with exact U_k, a full deflated Lanczos run appends exactly the next
+    eigenpairs of H (a densely formed H, not the oracle's); the extended set keeps
+    U orthonormal and gives Proposition 4.1's spectrum of S S~^{-1} for rank k + j."""
+    P = small_fv()
+    k, j = 3, 4
+    slr = SLR(P.rowptr, P.colind, P.val, P.part, P.nparts, k, theta_mode=theta_mode, eig="dense")
+    B, E, C = brute.dense_blocks(slr)
+    lam = np.sort(np.linalg.eigvalsh(brute.h_from_blocks(B, E, C)))[::-1]
+    s = len(lam)
+    added = slr.improve(j, lanczos_steps=s - k)
+    assert added == j and slr.k == k + j
+    assert np.allclose(slr.lam, lam[:k + j], atol=1e-10)
+    assert np.allclose(slr.U.T @ slr.U, np.eye(k + j), atol=1e-10)
+    theta = lam[k + j] if theta_mode == THETA_LAMBDA_K1 else 0.0
+    assert slr.theta == pytest.approx(theta, abs=1e-10)
+    S = brute.schur(B, E, C)
+    sig = np.sort(np.linalg.eigvals(S @ slr.stilde_inv(np.eye(s))).real)
+    want = np.sort(np.concatenate([np.ones(k + j), (1 - lam[k + j:]) / (1 - theta)]))
+    assert np.allclose(sig, want, rtol=1e-8, atol=1e-9)
+
+
+def test_improve_with_lanczos_lowers_iterations():
+    """Adding vectors to a Lanczos-built preconditioner keeps the old ones and helps PCG."""
+    P = slrgen.config1()
+    slr = SLR(P.rowptr, P.colind, P.val, P.part, P.nparts, 2, lanczos_steps=20)
+    U0 = slr.U.copy()
+    its0 = slr_pcg(slr, P.b[:, 0])[1]
+    slr.improve(6, lanczos_steps=40)
+    assert slr.k == 8 and np.array_equal(slr.U[:, :2], U0)
+    assert np.abs(slr.U[:, :2].T @ slr.U[:, 2:]).max() < 1e-10
+    assert slr_pcg(slr, P.b[:, 0])[1] < its0
+
+
 def test_prop_kappa_piecewise_sweep():
     lam = np.sort(brute.two_domain_lambda(40, 19))[::-1]
     k = 6
