@@ -169,14 +169,27 @@ slr_status slr_stilde_solve(slr_handle h, const double* g_dev, double* y_dev, in
 slr_status slr_set_lowrank(slr_handle h, int32_t k, const double* Z_host, const double* lam_host,
                            double theta, void* stream);
 
+/* Improve the preconditioner by adding vectors (Section 5.3: its low-rank
+ * part grows without discarding the vectors it has).  Runs FP64 Lanczos with
+ * full reorthogonalisation on the deflated operator (I - U_k U_k^T) H (I - U_k U_k^T),
+ * lanczos_steps steps (0: 5 k_add, at most s - k), started from L^{-1} C z with z
+ * from SplitMix64 stream seed + (number of earlier calls) + 1, projected out of
+ * span(U_k); appends its leading min(k_add, steps) Ritz pairs to (Lambda_k, U_k);
+ * with theta = lambda_{k+1} (Eq. 4.11) theta becomes the next Ritz value of that
+ * run.  *added_out (may be NULL): vectors added.  The handle's CUDA graphs are
+ * rebuilt on the next solve.  Synchronises stream.  Errors: INVALID_ARG
+ * (k_add < 0), OOM, CUDA. */
+slr_status slr_add_vectors(slr_handle h, int32_t k_add, int32_t lanczos_steps, void* stream, int32_t* added_out);
+
 /* Export the low-rank part: Z_host (s x k column-major, DD interface order,
  * may be NULL), lam_host[k+1] (Ritz values lambda_1..lambda_{k+1} from Lanczos,
  * the last 0 when unavailable; may be NULL), *theta_out (may be NULL). */
 slr_status slr_get_lowrank(slr_handle h, double* Z_host, double* lam_host, double* theta_out,
                            void* stream);
 
-/* All Ritz values of the setup Lanczos run, descending; lam_host has room for
- * info.lanczos_steps values; *count_out gets how many were produced. */
+/* All Ritz values of the setup Lanczos run, descending (after slr_add_vectors:
+ * lambda_1..lambda_k, then the last deflated run's remaining Ritz values);
+ * lam_host has room for info.lanczos_steps values; *count_out gets how many. */
 slr_status slr_get_ritz(slr_handle h, double* lam_host, int32_t* count_out);
 
 /* perm_host[n]: DD position -> original index (new -> old), Eq. 2.2. */

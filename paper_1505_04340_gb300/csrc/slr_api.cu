@@ -366,6 +366,119 @@ slr_status run_lanczos(slr_handle h, cudaStream_t st) {
     return SLR_OK;
 }
 
+void drop_graphs(slr_handle h);
+
+// Section 5.3: append eigenvector estimates of H found by Lanczos on the
+// deflated operator P H P, P = I - U_k U_k^T (all FP64, as the setup Lanczos).
+slr_status run_lanczos_deflated(slr_handle h, int32_t k_add, int32_t steps, cudaStream_t st, int32_t* added) {
+    HostSetup& hs = h->hs;
+    const int32_t s = hs.s, k = h->k;
+    *added = 0;
+    if (k_add == 0 || s == 0) return SLR_OK;
+    const int32_t m = std::min(steps > 0 ? steps : 5 * k_add, s - k);
+    if (m <= 0) return SLR_OK;
+    DevOperator<double>& op = h->op64;
+    // the mixed path keeps only the FP32 band factor after setup: reload the FP64 one for the run
+    const bool reload = op.bfac == nullptr;
+    if (reload && hs.bfac.empty()) {                // never launch the band solve without its factor
+        set_error("slr_add_vectors: the FP64 band factor is not available on this handle");
+        return SLR_ERR_UNSUPPORTED;
+    }
+    if (reload) {
+        dfree(h, op.band, hs.band.size());
+        CS(upload(h, &op.band, hs.band));
+        CS(upload(h, &op.bfac, hs.bfac));
+        op.band_G = hs.band_G;
+    }
+    const int32_t mk = std::max(m, k);
+    double *V = nullptr, *w = nullptr, *hv = nullptr, *part = nullptr, *sc = nullptr, *Yd = nullptr, *Un = nullptr;
+    CS(dalloc(h, &V, (size_t)s * m));
+    CS(dalloc(h, &w, (size_t)s));
+    CS(dalloc(h, &hv, (size_t)mk));
+    CS(dalloc(h, &part, (size_t)mk * kRedBlocks));
+    CS(dalloc(h, &sc, 4));
+    auto project = [&](double* x) -> slr_status {       // x -= U (U^T x), two passes
+        for (int pass = 0; pass < 2 && k > 0; ++pass) {
+            CK(launch_gemv_t(s, k, op.U, x, part, hv, st));
+            CK(launch_gemv_n_sub(s, k, op.U, hv, x, st));
+        }
+        return SLR_OK;
+    };
+    h->improvements += 1;
+    std::vector<double> z(s);
+    for (int32_t i = 0; i < s; ++i) z[i] = splitmix_pm1(h->opts.seed + (uint64_t)h->improvements, (uint64_t)i);
+    CK(cudaMemcpyAsync(w, z.data(), sizeof(double) * s, cudaMemcpyHostToDevice, st));
+    CK(launch_csr_spmv(s, h->c_rp, h->c_ci, h->c_v, w, s, op.gp, s, 1, st));     // C z (DD order)
+    CK(launch_c_forward<double>(op.cf, op.gp, s, op.tf, V, 1, st));              // L^{-1} C z
+    CS(project(V));
+    slr_status err = SLR_OK;
+    CK(launch_dots(s, 1, V, s, V, s, part, sc, 1, st));
+    const double nrm = std::sqrt(read_scalar(sc, st, &err));
+    CS(err);
+    if (!(nrm > 0.0)) { set_error("deflated Lanczos start vector is zero"); return SLR_ERR_BREAKDOWN; }
+    CK(launch_axpby(s, 0.0, V, 1.0 / nrm, V, st));
+    std::vector<double> alpha(m), beta(m);
+    int32_t m_eff = m;
+    double amax = 0.0;
+    for (int32_t j = 0; j < m; ++j) {
+        double* vj = V + (int64_t)j * s;
+        CS(h_apply(h, vj, w, st));
+        CS(project(w));
+        if (j > 0) CK(launch_axpby(s, -beta[j - 1], V + (int64_t)(j - 1) * s, 1.0, w, st));
+        CK(launch_dots(s, 1, vj, s, w, s, part, sc, 1, st));
+        alpha[j] = read_scalar(sc, st, &err);
+        CS(err);
+        amax = std::max(amax, std::fabs(alpha[j]));
+        CK(launch_axpby(s, -alpha[j], vj, 1.0, w, st));
+        for (int pass = 0; pass < 2; ++pass) {                       // full reorthogonalisation
+            CK(launch_gemv_t(s, j + 1, V, w, part, hv, st));
+            CK(launch_gemv_n_sub(s, j + 1, V, hv, w, st));
+        }
+        CK(launch_dots(s, 1, w, s, w, s, part, sc, 1, st));
+        beta[j] = std::sqrt(read_scalar(sc, st, &err));
+        CS(err);
+        if (j + 1 == m) break;
+        if (beta[j] <= 1e-12 * amax) { m_eff = j + 1; break; }
+        CK(launch_axpby(s, 1.0 / beta[j], w, 0.0, V + (int64_t)(j + 1) * s, st));
+    }
+    std::vector<double> lam2(m_eff), Y((size_t)m_eff * m_eff);
+    host_tridiag_eig(m_eff, alpha.data(), beta.data(), lam2.data(), Y.data());
+    const int32_t ja = std::min(k_add, m_eff), kn = k + ja;
+    // U_new = [U_k | V Y_ja]
+    CS(dalloc(h, &Yd, (size_t)m_eff * ja));
+    CK(cudaMemcpyAsync(Yd, Y.data(), sizeof(double) * m_eff * ja, cudaMemcpyHostToDevice, st));
+    CS(dalloc(h, &Un, (size_t)s * kn));
+    if (k > 0) CK(cudaMemcpyAsync(Un, op.U, sizeof(double) * s * k, cudaMemcpyDeviceToDevice, st));
+    CK(launch_gemm_nn(s, m_eff, ja, V, Yd, Un + (int64_t)s * k, st));
+    CK(cudaStreamSynchronize(st));
+    std::vector<double> lam_new(h->lam);
+    lam_new.insert(lam_new.end(), lam2.begin(), lam2.begin() + ja);
+    const double theta = (h->opts.theta_mode == SLR_THETA_LAMBDA_K1 && m_eff > ja) ? lam2[ja] : 0.0;
+    {
+        std::unique_lock<std::shared_mutex> lk(g_capture_mu);
+        drop_graphs(h);
+    }
+    CS(set_operator_lowrank<double>(h, h->op64, Un, k, kn, lam_new, theta));
+    if (h->opts.precision == SLR_PREC_MIXED) CS(set_operator_lowrank<float>(h, h->op32, Un, k, kn, lam_new, theta));
+    h->k = kn;
+    h->lam = lam_new;
+    h->theta = theta;
+    h->ritz = lam_new;
+    h->ritz.insert(h->ritz.end(), lam2.begin() + ja, lam2.end());
+    h->nritz = (int32_t)h->ritz.size();
+    h->m_steps = std::max(h->m_steps, h->nritz);
+    dfree(h, Un, (size_t)s * kn);
+    dfree(h, Yd, (size_t)m_eff * ja);
+    dfree(h, V, (size_t)s * m);
+    dfree(h, w, (size_t)s);
+    dfree(h, hv, (size_t)mk);
+    dfree(h, part, (size_t)mk * kRedBlocks);
+    dfree(h, sc, 4);
+    if (reload) dfree(h, op.bfac, hs.bfac.size());
+    *added = ja;
+    return SLR_OK;
+}
+
 void account(slr_handle h) {
     const HostSetup& hs = h->hs;
     const bool fp64 = h->opts.precision == SLR_PREC_FP64;
@@ -642,8 +755,9 @@ slr_status setup_impl(slr_handle h, int32_t n, const int32_t* rowptr, const int3
     if (vb)
         fprintf(stderr, "[slr] upload %.3fs lanczos %.3fs (m=%d k=%d theta=%.6g) device %.1f MB\n", t4 - t3 + t6 - t5,
                 t5 - t4, h->m_steps, h->k, h->theta, h->device_bytes / 1e6);
-    // host copies of the big factors are no longer needed
-    std::vector<double>().swap(hs.bfac);
+    // host copies of the big factors are no longer needed, except the FP64 band
+    // factor of a mixed-precision handle: slr_add_vectors runs its FP64 Lanczos on it
+    if (h->opts.precision == SLR_PREC_FP64) std::vector<double>().swap(hs.bfac);
     std::vector<double>().swap(hs.cf.panel);
     std::vector<double>().swap(hs.cf.dinv);
     h->op64.ready = true;
@@ -1006,6 +1120,22 @@ slr_status slr_set_lowrank(slr_handle h, int32_t k, const double* Z, const doubl
     }
     account(h);
     return SLR_OK;
+}
+
+slr_status slr_add_vectors(slr_handle h, int32_t k_add, int32_t lanczos_steps, void* stream, int32_t* added_out) {
+    CS(check_handle(h));
+    if (k_add < 0 || lanczos_steps < 0) {
+        set_error("slr_add_vectors: k_add and lanczos_steps must be >= 0");
+        return SLR_ERR_INVALID_ARG;
+    }
+    DeviceGuard g(h->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    h->stream = st;
+    int32_t added = 0;
+    slr_status r = run_lanczos_deflated(h, k_add, lanczos_steps, st, &added);
+    if (added_out) *added_out = added;
+    if (r == SLR_OK) account(h);
+    return r;
 }
 
 slr_status slr_get_lowrank(slr_handle h, double* Z, double* lam, double* theta_out, void* stream) {

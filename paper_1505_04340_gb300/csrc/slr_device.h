@@ -74,6 +74,7 @@ struct slr_handle_s {
     cudaStream_t stream = nullptr;   // stream of the setup or set_lowrank call in progress
     slr::HostSetup hs;               // sizes, permutation, CSR blocks (host copies)
     int32_t k = 0, m_steps = 0, nritz = 0;
+    int32_t improvements = 0;        // slr_add_vectors calls so far (their start-vector streams)
     double theta = 0.0;
     std::vector<double> ritz;        // all Ritz values, descending
     std::vector<double> lam;         // lambda_1..lambda_k

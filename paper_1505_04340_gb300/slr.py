@@ -30,7 +30,7 @@ PRECISION = {"fp64": 0, "mixed": 1}
 EXPORTS = ["slr_default_opts", "slr_setup", "slr_apply", "slr_pcg_solve", "slr_bsolve", "slr_csolve",
            "slr_stilde_solve", "slr_set_lowrank", "slr_get_lowrank", "slr_get_ritz", "slr_get_perm",
            "slr_get_info", "slr_dd_order", "slr_kernel_launches", "slr_destroy", "slr_status_str",
-           "slr_last_error_message", "slr_apply_noalloc"]
+           "slr_last_error_message", "slr_apply_noalloc", "slr_add_vectors"]
 
 
 class Opts(C.Structure):
@@ -80,6 +80,7 @@ def load():
         "slr_csolve": (i32, [vp, vp, vp, i32, i32, vp]),
         "slr_stilde_solve": (i32, [vp, vp, vp, i32, i32, vp]),
         "slr_set_lowrank": (i32, [vp, i32, vp, vp, f64, vp]),
+        "slr_add_vectors": (i32, [vp, i32, i32, vp, vp]),
         "slr_get_lowrank": (i32, [vp, vp, vp, vp, vp]),
         "slr_get_ritz": (i32, [vp, vp, vp]),
         "slr_get_perm": (i32, [vp, vp]),
@@ -245,6 +246,15 @@ class SLR:
                                          _host_ptr(lam) if k else None, float(theta), _stream_ptr(stream)),
                "slr_set_lowrank")
         self.info = self.get_info()
+
+    def add_vectors(self, k_add, lanczos_steps=0, stream=None):
+        """Improve the preconditioner by k_add more eigenvector estimates of H, keeping
+        the ones it has (Section 5.3, deflated Lanczos).  Returns how many were added."""
+        added = C.c_int32(0)
+        _check(self._lib.slr_add_vectors(self._h, int(k_add), int(lanczos_steps), _stream_ptr(stream),
+                                         C.byref(added)), "slr_add_vectors")
+        self.info = self.get_info()
+        return added.value
 
     # -- the operator
     def _call(self, fn, x, rows, name, stream, out=None):

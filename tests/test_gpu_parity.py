@@ -373,3 +373,29 @@ def test_target_condition_number_rank(name, K):
     _, it_loose, _, st2 = loose.pcg(b)
     assert st == 0 and st2 == 0
     assert loose.get_info()["k"] <= o.k and int(it_k[0]) <= int(it_loose[0]) + 1
+
+
+@pytest.mark.parametrize("name", ["c1-lap32", "3d-lap"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_add_vectors_matches_oracle_improvement(name, precision):
+    """Section 5.3: vectors from a deflated Lanczos run are appended, the old ones kept;
+    the Ritz values match the oracle's improved preconditioner and PCG gets no slower."""
+    P = make(name)
+    k0, j = 2, 4
+    o = OracleSLR(P.rowptr, P.colind, P.val, P.part, P.nparts, k0, 20)
+    o.improve(j, lanczos_steps=24)
+    fl = precision == "mixed"
+    g = SLR(P.rowptr, P.colind, P.val, P.part, P.nparts, k=k0, lanczos_steps=20, precision=precision,
+            nrhs_max=1, flexible_cg=fl)
+    b = cu(P.b[:, 0])
+    _, it0, _, st0 = g.pcg(b)
+    Z0, _, _ = g.get_lowrank()
+    assert g.add_vectors(j, lanczos_steps=24) == j
+    assert g.get_info()["k"] == k0 + j
+    Z1, lam, th = g.get_lowrank()
+    assert np.abs(Z1[:, :k0] - Z0).max() <= 1e-12 * np.abs(Z0).max()     # old vectors kept
+    assert np.allclose(lam[:k0 + j], o.lam, rtol=1e-8, atol=1e-10), (lam[:k0 + j], o.lam)
+    assert th == pytest.approx(o.theta, rel=1e-8)
+    _, it1, _, st1 = g.pcg(b)
+    its_o = int(np.atleast_1d(slr_pcg(o, P.b[:, 0])[1])[0])
+    assert st0 == st1 == 0 and int(it1[0]) <= int(it0[0]) and abs(int(it1[0]) - its_o) <= 1
