@@ -509,10 +509,21 @@ cudaError_t launch_band_solve(const DevOperator<T>& op, int32_t p, int32_t wmax,
         const int32_t left = nrhs - c;
         int nr = 1;
         int32_t nb, sl;
-        if (left >= 4 && band_ring(wmax, 4, sizeof(T), 0, &nb, &sl)) nr = 4;
+        // FP32 takes up to 8 columns per CTA (FP64's partial sums would not fit): each
+        // group re-reads the factor, so wider groups save bytes on multi-RHS blocks
+        if (sizeof(T) == 4 && left >= 8 && band_ring(wmax, 8, sizeof(T), 0, &nb, &sl)) nr = 8;
+        else if (left >= 4 && band_ring(wmax, 4, sizeof(T), 0, &nb, &sl)) nr = 4;
         else if (left >= 2 && band_ring(wmax, 2, sizeof(T), 0, &nb, &sl)) nr = 2;
         const T* bs = base ? base + c * ldb : nullptr;
         cudaError_t e;
+        if constexpr (sizeof(T) == 4) {
+            if (nr == 8) {
+                e = band_launch_g<T, 8>(op, p, wmax, in + c * ldi, ldi, out + c * ldo, ldo, bs, ldb, st);
+                if (e != cudaSuccess) return e;
+                c += nr;
+                continue;
+            }
+        }
         if (nr == 4) e = band_launch_g<T, 4>(op, p, wmax, in + c * ldi, ldi, out + c * ldo, ldo, bs, ldb, st);
         else if (nr == 2) e = band_launch_g<T, 2>(op, p, wmax, in + c * ldi, ldi, out + c * ldo, ldo, bs, ldb, st);
         else e = band_launch_g<T, 1>(op, p, wmax, in + c * ldi, ldi, out + c * ldo, ldo, bs, ldb, st);

@@ -399,3 +399,17 @@ def test_add_vectors_matches_oracle_improvement(name, precision):
     _, it1, _, st1 = g.pcg(b)
     its_o = int(np.atleast_1d(slr_pcg(o, P.b[:, 0])[1])[0])
     assert st0 == st1 == 0 and int(it1[0]) <= int(it0[0]) and abs(int(it1[0]) - its_o) <= 1
+
+
+@pytest.mark.parametrize("name", ["3d-lap", "3d-wide", "fv-ragged"])
+def test_bsolve_wide_rhs_block_mixed(name):
+    """FP32 B^{-1} on 11 right-hand sides (column groups of 8, 2 and 1 per CTA): parity with
+    the oracle, and each column alone equals its column of the block bit for bit."""
+    P = make(name)
+    o = oracle(name)
+    g = gpu_handle(P, "mixed", nrhs_max=11)
+    f = np.random.default_rng(12).standard_normal((o.order.n_I, 11))
+    t = g.bsolve(cu(f)).cpu().numpy()
+    assert rel(t, o.bsolve.solve(f)) <= TOL32
+    for c in (0, 7, 8, 10):
+        assert np.array_equal(g.bsolve(cu(f[:, c])).cpu().numpy(), t[:, c]), c
