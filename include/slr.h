@@ -71,7 +71,7 @@ typedef struct {
                                order, u_i = (x_i >> 11) 2^-53, x_i output i of the stream */
     int32_t c_leaf;         /* nested-dissection leaf size for C's ordering; 0 => 64     */
     int32_t verbose;        /* 1: setup prints timings to stderr                          */
-    int32_t reserved[6];    /* reserved[0]: CTAs per subdomain in the band solve (1, 2, 4;
+    int32_t reserved[8];    /* reserved[0]: CTAs per subdomain in the band solve (1, 2, 4;
                                0 = automatic).  reserved[1]: 1 = drive the CG loop from
                                the host (one synchronisation per iteration) instead of
                                one CUDA graph per solve.  reserved[2]: shared-memory
@@ -80,15 +80,19 @@ typedef struct {
                                in one cooperative launch per direction (grid barriers
                                between level steps) instead of one launch per step.
                                reserved[4]: 1 = autotune: setup times the band solve
-                               for each split (1, 2, 4 CTAs) and buffer count (2, 3, 4)
-                               that fit, and both C-solve paths, on this operator, and
+                               for each split (1, 2, 4 CTAs), CTA size (512 or 256
+                               threads) and buffer count (2, 3, 4) that fit, and both
+                               C-solve paths, on this operator, and
                                keeps the fastest; the choice is cached per device,
                                precision and problem shape for the process's life.
                                reserved[5]: a target condition number K >= 2 for S S~^{-1}
                                (0 = off): the rank becomes the number of Ritz values
                                above 1 - 1/K, at most k (Section 4, Eq. condk:
                                lambda_{k+1} <= 1 - 1/K keeps the condition number of
-                               S S~^{-1} below K).  slr_get_info reports the rank used. */
+                               S S~^{-1} below K).  slr_get_info reports the rank used.
+                               reserved[6]: threads per band-solve CTA, 512 (one CTA per
+                               SM) or 256 (two per SM, for more CTAs than SMs); 0 =
+                               automatic.  reserved[7] must be 0.                      */
 } slr_opts;
 
 typedef struct {
@@ -109,6 +113,7 @@ typedef struct {
     int32_t c_persistent;        /* 1: C solves in one cooperative launch per direction     */
     int32_t tuned;               /* 1: the three above were chosen by timing (reserved[4]) */
     double tune_seconds;         /* time the tuning took (0 when taken from the cache)      */
+    int32_t band_threads;        /* threads per band-solve CTA (256: two subdomains per SM) */
 } slr_info;
 
 /* Fill *opts with defaults: k = 16, m = 5k, theta = lambda_{k+1}, FP64, 1 RHS, seed 1. */

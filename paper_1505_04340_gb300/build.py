@@ -21,7 +21,7 @@ BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "lib", "libslr.so")
 
 CXX_SOURCES = ["slr_host.cpp"]
-CU_SOURCES = ["slr_kernels.cu", "slr_band.cu", "slr_api.cu", "slr_noalloc.cu"]
+CU_SOURCES = ["slr_kernels.cu", "slr_band.cu", "slr_band_half.cu", "slr_api.cu", "slr_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -37,7 +37,7 @@ def _cuda_home() -> str:
 
 def _sources():
     files = [os.path.join(CSRC, f) for f in CXX_SOURCES + CU_SOURCES]
-    files += [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")]
+    files += [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h") or f.endswith(".cuh")]
     files += [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE) if f.endswith(".h")]
     return files
 

@@ -113,6 +113,7 @@ slr_status upload_operator(slr_handle h, DevOperator<T>& op, bool with_band) {
     if (with_band) CS(upload(h, &op.bfac, hs.bfac));
     op.band_G = hs.band_G;
     op.band_nbuf = h->opts.reserved[2];
+    op.band_nt = hs.band_nt;
     CS(dalloc(h, &op.err, 1));
     CK(cudaMemsetAsync(op.err, 0, sizeof(int32_t), h->stream));
     CS(upload(h, &op.e_rp, hs.e_rp));
@@ -508,7 +509,7 @@ struct TuneKey {
     }
 };
 struct TuneChoice {
-    int32_t G = 1, slots = 0;
+    int32_t G = 1, slots = 0, nt = 512;
     bool persistent = false;
 };
 std::mutex g_tune_mu;
@@ -616,19 +617,22 @@ slr_status autotune(slr_handle h, DevOperator<T>& op, cudaStream_t st) {
         for (int32_t G : {1, 2, 4}) {
             if (!band_split_ok(hs.wmax, G) || (G > 1 && hs.wmax < 32 * G) || hs.p * G > 2 * nsm) continue;
             if (G != hs.band_G) CS(repack_band<T>(h, op, G));
-            for (int32_t slots : {2, 3, 4}) {
-                op.band_nbuf = slots;
-                double us = 0;
-                CS(time_us([&]() -> slr_status {
-                    CK(launch_band_solve<T>(op, hs.p, hs.wmax, op.eb, hs.nI, op.tB, hs.nI, nullptr, 0, 1, st));
-                    return SLR_OK;
-                }, st, 5, &us));
-                if (us < best_us) {
-                    best_us = us;
-                    best.G = G;
-                    best.slots = slots;
+            for (int32_t nt : {512, 256})
+                for (int32_t slots : {2, 3, 4}) {
+                    op.band_nbuf = slots;
+                    op.band_nt = nt;
+                    double us = 0;
+                    CS(time_us([&]() -> slr_status {
+                        CK(launch_band_solve<T>(op, hs.p, hs.wmax, op.eb, hs.nI, op.tB, hs.nI, nullptr, 0, 1, st));
+                        return SLR_OK;
+                    }, st, 5, &us));
+                    if (us < best_us) {
+                        best_us = us;
+                        best.G = G;
+                        best.slots = slots;
+                        best.nt = nt;
+                    }
                 }
-            }
         }
         // the C solves run inside the PCG graph: time them as a replayed graph
         double c_us[2] = {0, 0};
@@ -653,6 +657,8 @@ slr_status autotune(slr_handle h, DevOperator<T>& op, cudaStream_t st) {
     }
     if (best.G != hs.band_G) CS(repack_band<T>(h, op, best.G));
     op.band_nbuf = best.slots;
+    op.band_nt = best.nt;
+    hs.band_nt = best.nt;
     op.cf.per_level = !best.persistent;
     h->tuned = true;
     h->tune_seconds = cached ? 0.0 : std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -701,6 +707,8 @@ slr_status setup_impl(slr_handle h, int32_t n, const int32_t* rowptr, const int3
             G = 2;
         }
         CS(host_band_factor(hs, G));
+        // more CTAs than SMs would run in two waves: 256-thread CTAs put two subdomains on an SM
+        hs.band_nt = h->opts.reserved[6] ? h->opts.reserved[6] : (nparts * G > nsm ? 256 : 512);
     }
     double t2 = now_s();
     CS(host_c_factor(hs, h->opts.c_leaf > 0 ? h->opts.c_leaf : 64, 32));
@@ -917,7 +925,9 @@ slr_status slr_setup(int32_t n, const int32_t* rowptr, const int32_t* colind, co
         h->opts.reserved[1] < 0 || h->opts.reserved[1] > 1 ||
         h->opts.reserved[2] < 0 || h->opts.reserved[2] == 1 || h->opts.reserved[2] > 8 ||
         h->opts.reserved[3] < 0 || h->opts.reserved[3] > 1 || h->opts.reserved[4] < 0 || h->opts.reserved[4] > 1 ||
-        h->opts.reserved[5] < 0 || h->opts.reserved[5] == 1) {
+        h->opts.reserved[5] < 0 || h->opts.reserved[5] == 1 ||
+        (h->opts.reserved[6] != 0 && h->opts.reserved[6] != 256 && h->opts.reserved[6] != 512) ||
+        h->opts.reserved[7] != 0) {
         set_error("invalid options");
         delete h;
         return SLR_ERR_INVALID_ARG;
@@ -1212,6 +1222,7 @@ slr_status slr_get_info(slr_handle h, slr_info* info) {
     info->c_persistent = (f64 ? h->op64.cf.per_level : h->op32.cf.per_level) ? 0 : 1;
     info->tuned = h->tuned ? 1 : 0;
     info->tune_seconds = h->tune_seconds;
+    info->band_threads = f64 ? h->op64.band_nt : h->op32.band_nt;
     return SLR_OK;
 }
 

@@ -30,476 +30,9 @@
 // warp's partial sums (added once per phase) do not depend on the chunking.
 // The full input vector of a phase is assembled in every CTA through
 // distributed shared memory.
-#include <cooperative_groups.h>
-#include <cuda_runtime.h>
-
-#include <atomic>
-#include <cstdint>
-#include <mutex>
-
-#include "slr_device.h"
-
-namespace cg = cooperative_groups;
+#include "slr_band_kernel.cuh"
 
 namespace slr {
-
-namespace {
-
-constexpr int kT = 512;            // threads per CTA (4 warps per SM sub-partition hide the load->FMA latency)
-constexpr int kW = kT / 32;        // warps per CTA
-constexpr int kMaxBuf = 8;         // ring slots at most
-constexpr int kMinBuf = 2;         // ring slots at least
-constexpr int kDefBuf = 2;         // ring slots unless the operator asks for another count
-                                   // (two large slots measured fastest: per-chunk latency dominates)
-constexpr int kMinSlot = 16 * 1024;   // bytes per ring slot at least
-constexpr size_t kSmemCap = 227 * 1024;   // opt-in shared memory per CTA on sm_100-class GPUs
-constexpr int kRB = 8;             // row blocks of 32: at most 256 rows per slice
-constexpr long long kSpin = 1ll << 24;   // bounded mbarrier wait (about a second)
-
-// ---- slice geometry (the host packer uses the same rules: band_* in slr_internal.h)
-// local row block with first plane row R0: columns it meets in an upper block
-// start at seg_cU0, in a lower block end before seg_cL1
-__device__ __forceinline__ int seg_cU0(int W, int R0) { return min(W, R0); }
-__device__ __forceinline__ int seg_cL1(int W, int R0) { return min(W, min(R0 + 31, W - 1) + 1); }
-
-// ---- mbarrier / bulk copy PTX
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar))
-        : "memory");
-}
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
-
-// Split cluster barrier: arrive after a phase's stores into the peers, wait just
-// before the next phase reads them (with one CTA: a CTA barrier at the wait).
-template <int G>
-__device__ __forceinline__ void cluster_arrive() {
-    if constexpr (G > 1) asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
-}
-template <int G>
-__device__ __forceinline__ void cluster_wait() {
-    if constexpr (G > 1) {
-        asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
-    } else {
-        __syncthreads();
-    }
-}
-
-template <int G>
-__device__ __forceinline__ void cluster_barrier() {
-    if constexpr (G > 1) {
-        cg::this_cluster().sync();
-    } else {
-        __syncthreads();
-    }
-}
-
-// Column c of every block goes to warp c mod kW whatever the chunk boundaries,
-// so each warp's partial sums, and the result, do not depend on the ring's
-// slot size (which varies with the right-hand sides per CTA).
-__device__ __forceinline__ int first_col(int lo, int warp) { return lo + ((warp - lo % kW) + kW) % kW; }
-
-struct Geom {
-    int W, c, g;
-    int nU, nL;
-    int64_t base, PS, SU, SL;
-};
-
-// Block types: 0 O_J (upper, fwd), 1 D_J (lower, fwd), 2 O_J^T (lower, bwd), 3 D_J^T (upper, bwd).
-// Stream order: forward D_0, (O_J, D_J) J = 1..c-1; backward D_{c-1}^T, then
-// (O_{J+1}^T, D_J^T) J = c-2..0 (O_{J+1}^T is stored with plane J+1).
-// next_block advances (type, plane) along that order; plane < 0 ends it.
-__device__ __forceinline__ void next_block(int c, int& type, int& plane) {
-    switch (type) {
-        case 1: if (plane + 1 < c) { type = 0; ++plane; } else { type = 3; plane = c - 1; } break;
-        case 0: type = 1; break;
-        case 3: if (plane > 0) type = 2; else plane = -1; break;
-        default: type = 3; --plane; break;
-    }
-}
-
-__device__ __forceinline__ int64_t block_off(const Geom& q, int type) {
-    return type == 0 ? 0 : type == 1 ? q.SU : type == 2 ? q.SU + q.SL : q.SU + 2 * q.SL;
-}
-
-}  // namespace
-
-template <typename T, int NR, int G>
-__global__ void __launch_bounds__(kT, 1)
-k_band_solve2(const BandBlock* __restrict__ blocks, const T* __restrict__ fac, const T* in, int64_t ldi, T* out,
-              int64_t ldo, const T* base, int64_t ldb, int32_t* err, int nbuf, int slot) {
-    extern __shared__ __align__(128) unsigned char smem[];
-    const int sub = blockIdx.x / G;
-    const int g = (G > 1) ? (int)cg::this_cluster().block_rank() : 0;
-    const BandBlock b = blocks[sub];
-    if (b.m == 0) return;                       // uniform across the cluster
-    const int W = b.w, c = b.c, m = b.m;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-
-    // ---- shared memory carve-up: barriers, tables and vectors, then the ring
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem);              // [kMaxBuf]
-    uint64_t* empty = full + kMaxBuf;                                 // [kMaxBuf]
-    int* segU = reinterpret_cast<int*>(empty + kMaxBuf);             // [kRB+1] first segment of row block rb
-    int* segL = segU + (kRB + 1);                                    // [kRB+1]
-    int* hdr = segL + (kRB + 1);                                     // nU, nL, segments per chunk
-    uintptr_t vp = reinterpret_cast<uintptr_t>(hdr + 4);
-    vp = (vp + 15) & ~uintptr_t(15);
-    T* vst = reinterpret_cast<T*>(vp);              // [NR][W] y_{J-1} (fwd) / x_{J+1} (bwd), whole plane
-    T* vt = vst + NR * W;                           // [NR][W] t, whole plane
-    T* part = vt + NR * W;                          // [kW][NR][256] per-warp partial sums
-    uintptr_t rp = reinterpret_cast<uintptr_t>(part + kW * NR * 256);
-    unsigned char* ring = reinterpret_cast<unsigned char*>((rp + 127) & ~uintptr_t(127));   // nbuf x slot bytes
-
-    Geom q;
-    q.W = W;
-    q.c = c;
-    q.g = g;
-    q.SU = b.SU;
-    q.SL = b.SL;
-    q.PS = (int64_t)G * 2 * (b.SU + b.SL);
-    q.base = b.foff + (int64_t)g * 2 * (b.SU + b.SL);
-
-    // this slice's row blocks: first plane row of each (past W: none)
-    const int nrb = b.nrb[g];
-    int R0[kRB];
-#pragma unroll
-    for (int rb = 0; rb < kRB; ++rb) R0[rb] = rb < nrb ? 32 * b.rbmap[g][rb] : W;
-    if (tid == 0) {
-        int a = 0, d = 0;
-        for (int rb = 0; rb <= kRB; ++rb) {
-            segU[rb] = a;
-            segL[rb] = d;
-            if (rb < nrb) {
-                a += W - seg_cU0(W, R0[rb]);
-                d += seg_cL1(W, R0[rb]);
-            }
-        }
-        const int per = max(1, slot / (32 * (int)sizeof(T)));   // whole segments per chunk
-        hdr[0] = (a + per - 1) / per;
-        hdr[1] = (d + per - 1) / per;
-        hdr[2] = per;
-        for (int i = 0; i < nbuf; ++i) {
-            mbar_init(&full[i], 1);
-            mbar_init(&empty[i], kW);
-        }
-        fence_mbar_init();
-    }
-    __syncthreads();
-    q.nU = hdr[0];
-    q.nL = hdr[1];
-    const int per = hdr[2];
-    // forward: D_0 (lower), then (O_J upper, D_J lower); backward: D_{c-1}^T (upper), then (O^T lower, D^T upper)
-    const int total = q.nL + q.nU + 2 * (c - 1) * (q.nU + q.nL);
-
-    // first and one-past-last element of chunk ix of a block: segments [ix per, ...)
-    auto chunk_src = [&](int type, int plane, int ix, int64_t& e0, int64_t& e1) {
-        const bool up = (type == 0 || type == 3);
-        const int nseg = up ? segU[kRB] : segL[kRB];
-        e0 = q.base + (int64_t)plane * q.PS + block_off(q, type) + (int64_t)ix * per * 32;
-        e1 = e0 + (int64_t)(min(per, nseg - ix * per)) * 32;
-    };
-    // thread 0 issues chunks in stream order; its cursor is the next chunk to issue
-    int cur_type = 1, cur_plane = 0, cur_ix = 0, issued = 0;
-    auto issue_next = [&]() {
-        if (cur_plane < 0) return;                 // past the end of the stream: nothing to copy
-        int64_t e0, e1;
-        chunk_src(cur_type, cur_plane, cur_ix, e0, e1);
-        // whole segments of 32 values: start and size are multiples of 128 bytes
-        const uint32_t bytes = (uint32_t)((e1 - e0) * (int64_t)sizeof(T));
-        const int sl = issued % nbuf;
-        uint64_t* bar = &full[sl];
-        mbar_arrive_expect_tx(bar, bytes);
-        bulk_g2s(ring + (size_t)sl * slot, fac + e0, bytes, bar);
-        ++issued;
-        const int nch = (cur_type == 0 || cur_type == 3) ? q.nU : q.nL;
-        if (++cur_ix == nch) {
-            cur_ix = 0;
-            next_block(c, cur_type, cur_plane);
-        }
-    };
-    auto wait_bar = [&](uint64_t* bar, uint32_t par) {
-        long long it = 0;
-        while (!mbar_try_wait(bar, par)) {
-            if (++it > kSpin) {
-                if (lane == 0) atomicExch(err, 1);
-                break;
-            }
-        }
-    };
-    // chunk k's data has landed (the (k / nbuf)-th fill of its slot)
-    auto wait_full = [&](int k) { wait_bar(&full[k % nbuf], (uint32_t)((k / nbuf) & 1)); };
-    // this warp is done with chunk k's slot
-    auto release = [&](int k) {
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&empty[k % nbuf]);
-    };
-    // thread 0, before consuming chunk k: once every warp has released chunk
-    // k - 1, its slot takes the next chunk of the stream
-    auto refill = [&](int k) {
-        if (tid == 0 && k >= 1 && issued < total) {
-            wait_bar(&empty[(k - 1) % nbuf], (uint32_t)(((k - 1) / nbuf) & 1));
-            fence_proxy_async();
-            issue_next();
-        }
-    };
-    auto peer = [&](T* p, int r) -> T* {
-        if constexpr (G > 1) return cg::this_cluster().map_shared_rank(p, r);
-        return p;
-    };
-
-    if (tid == 0)
-        while (issued < nbuf && issued < total) issue_next();
-    // every CTA of the cluster is running before anyone stores into a peer's shared memory
-    cluster_barrier<G>();
-
-    int k = 0;
-    bool pending = false;      // a cluster arrive waits for its wait (uniform in the cluster)
-    T acc[kRB][NR];
-    // acc[rb][j] += sum over the chunks of one block of M[lr][cc] * vin[j][cc], lanes = rows
-    // acc[rb][j] = sum over the block's segments of row block rb of seg[lane] * vin[j][column]
-    auto run_block = [&](int type, int plane, const T* vin) {
-        const bool upper = (type == 0 || type == 3);
-#pragma unroll
-        for (int rb = 0; rb < kRB; ++rb)
-#pragma unroll
-            for (int j = 0; j < NR; ++j) acc[rb][j] = T(0);
-        const int nch = upper ? q.nU : q.nL;
-        const int* seg = upper ? segU : segL;
-        for (int ix = 0; ix < nch; ++ix, ++k) {
-            refill(k);
-            wait_full(k);
-            if (pending) {                 // the input vector's last stores (peers included)
-                cluster_wait<G>();
-                pending = false;
-            }
-            const int s0 = ix * per, s1 = min(s0 + per, seg[kRB]);
-            const T* P = reinterpret_cast<const T*>(ring + (size_t)(k % nbuf) * slot);
-#pragma unroll
-            for (int rb = 0; rb < kRB; ++rb) {
-                if (rb >= nrb) break;
-                const int sa = max(s0, seg[rb]), sb = min(s1, seg[rb + 1]);
-                if (sa >= sb) continue;
-                const int cb0 = upper ? seg_cU0(W, R0[rb]) : 0;         // column of segment seg[rb]
-                const int ca = cb0 + (sa - seg[rb]), ce = cb0 + (sb - seg[rb]);
-                int cc = first_col(ca, warp);
-                const T* Ps = P + (sa - s0 + (cc - ca)) * 32 + lane;
-#pragma unroll 2
-                for (; cc < ce; cc += kW, Ps += kW * 32) {
-                    const T a = *Ps;
-#pragma unroll
-                    for (int j = 0; j < NR; ++j) acc[rb][j] = fma(a, vin[j * W + cc], acc[rb][j]);
-                }
-            }
-            release(k);
-        }
-#pragma unroll
-        for (int rb = 0; rb < kRB; ++rb)
-#pragma unroll
-            for (int j = 0; j < NR; ++j) part[(warp * NR + j) * 256 + rb * 32 + lane] = acc[rb][j];
-        if (pending) {                     // a block without chunks (a slice without rows)
-            cluster_wait<G>();
-            pending = false;
-        }
-        __syncthreads();
-    };
-    auto zero_part = [&]() {
-        if (pending) {
-            cluster_wait<G>();
-            pending = false;
-        }
-        for (int i = tid; i < kW * NR * 256; i += kT) part[i] = T(0);
-        __syncthreads();
-    };
-    auto part_sum = [&](int lr, int j) -> T {
-        T s = T(0);
-#pragma unroll
-        for (int w = 0; w < kW; ++w) s += part[(w * NR + j) * 256 + lr];
-        return s;
-    };
-
-    // Each thread owns at most one output row per plane (a slice has at most
-    // 256 rows): its right-hand side (forward) or forward result (backward) is
-    // loaded before the block product so the load is off the plane-to-plane chain.
-    int own_r = W;
-#pragma unroll
-    for (int rb = 0; rb < kRB; ++rb)
-        if ((tid >> 5) == rb) own_r = R0[rb] + (tid & 31);
-    const bool owner = tid < 32 * nrb && own_r < W;
-    // =================================================================== forward
-    for (int J = 0; J < c; ++J) {
-        const int row = J * W + own_r;
-        T pre[NR];
-#pragma unroll
-        for (int j = 0; j < NR; ++j) pre[j] = (owner && row < m) ? in[b.row0 + row + j * ldi] : T(0);
-        if (J > 0) run_block(0, J, vst); else zero_part();                 // O_J y_{J-1}
-        if (owner) {
-#pragma unroll
-            for (int j = 0; j < NR; ++j) {
-                const T t = pre[j] - part_sum(tid, j);
-#pragma unroll
-                for (int pr = 0; pr < G; ++pr) peer(vt, pr)[j * W + own_r] = t;
-            }
-        }
-        cluster_arrive<G>();
-        pending = true;
-        run_block(1, J, vt);                                               // D_J t
-        if (owner) {
-#pragma unroll
-            for (int j = 0; j < NR; ++j) {
-                const T y = part_sum(tid, j);
-                if (row < m) out[b.row0 + row + j * ldo] = y;
-#pragma unroll
-                for (int pr = 0; pr < G; ++pr) peer(vst, pr)[j * W + own_r] = y;
-            }
-        }
-        cluster_arrive<G>();
-        pending = true;
-    }
-    // =================================================================== backward
-    for (int J = c - 1; J >= 0; --J) {
-        const int row = J * W + own_r;
-        const int64_t gi = b.row0 + row;
-        T pre[NR], bs[NR];
-#pragma unroll
-        for (int j = 0; j < NR; ++j) {
-            pre[j] = (owner && row < m) ? out[gi + j * ldo] : T(0);
-            bs[j] = (owner && row < m && base) ? base[gi + j * ldb] : T(0);
-        }
-        if (J < c - 1) run_block(2, J + 1, vst); else zero_part();         // O_{J+1}^T x_{J+1}
-        if (owner) {
-#pragma unroll
-            for (int j = 0; j < NR; ++j) {
-                const T t = pre[j] - part_sum(tid, j);
-#pragma unroll
-                for (int pr = 0; pr < G; ++pr) peer(vt, pr)[j * W + own_r] = t;
-            }
-        }
-        cluster_arrive<G>();
-        pending = true;
-        run_block(3, J, vt);                                               // D_J^T t
-        if (owner) {
-#pragma unroll
-            for (int j = 0; j < NR; ++j) {
-                const T x = part_sum(tid, j);
-                if (row < m) out[gi + j * ldo] = base ? bs[j] - x : x;
-#pragma unroll
-                for (int pr = 0; pr < G; ++pr) peer(vst, pr)[j * W + own_r] = x;
-            }
-        }
-        cluster_arrive<G>();
-        pending = true;
-    }
-    if (pending) cluster_wait<G>();    // no CTA leaves while a peer may still store into it
-}
-
-// Shared memory besides the ring (barriers, column tables, vectors, partials,
-// the ring's alignment), for planes of at most wmax rows.
-static size_t band_fixed_bytes(int32_t wmax, int32_t nr, size_t elem) {
-    (void)wmax;
-    const size_t head = 2 * kMaxBuf * 8 + 2 * (kRB + 1) * 4 + 16 + 16;
-    const size_t vec = (size_t)(2 * nr * wmax + kW * nr * 256) * elem;
-    return head + vec + 128;
-}
-
-bool band_ring(int32_t wmax, int32_t nr, size_t elem, int32_t nbuf_req, int32_t* nbuf, int32_t* slot) {
-    const size_t fx = band_fixed_bytes(wmax, nr, elem);
-    if (fx + (size_t)kMinBuf * kMinSlot > kSmemCap) return false;
-    const size_t avail = kSmemCap - fx;
-    int32_t n = nbuf_req > 0 ? nbuf_req : kDefBuf;
-    n = std::max(kMinBuf, std::min<int32_t>(n, kMaxBuf));
-    while (n > kMinBuf && avail / n < (size_t)kMinSlot) --n;
-    *nbuf = n;
-    *slot = (int32_t)((avail / n) & ~size_t(127));
-    return true;
-}
-
-size_t band_smem_bytes(int32_t wmax, int32_t nr, size_t elem, int32_t nbuf, int32_t slot) {
-    return band_fixed_bytes(wmax, nr, elem) + (size_t)nbuf * slot;
-}
-
-namespace {
-template <typename T, int NR, int G>
-cudaError_t band_launch(const DevOperator<T>& op, int32_t p, int32_t wmax, const T* in, int64_t ldi, T* out,
-                        int64_t ldo, const T* base, int64_t ldb, cudaStream_t st) {
-    auto kern = k_band_solve2<T, NR, G>;
-    // The dynamic shared-memory limit of a kernel is process-wide state on its
-    // device.  It is raised once, to the device's opt-in maximum, so that
-    // threads launching this kernel for operators of different widths never
-    // race between one thread's setting and another's launch.
-    static std::mutex mu;
-    static uint64_t raised = 0;                     // bit d: done on device d
-    {
-        int dev = 0;
-        cudaError_t e = cudaGetDevice(&dev);
-        if (e != cudaSuccess) return e;
-        if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-        std::lock_guard<std::mutex> lk(mu);
-        if (!(raised >> dev & 1)) {
-            int optin = 0;
-            e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-            if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
-            if (e != cudaSuccess) return e;
-            raised |= 1ull << dev;
-        }
-    }
-    int32_t nbuf = 0, slot = 0;
-    if (!band_ring(wmax, NR, sizeof(T), op.band_nbuf, &nbuf, &slot)) return cudaErrorInvalidValue;
-    const size_t smem = band_smem_bytes(wmax, NR, sizeof(T), nbuf, slot);
-    cudaError_t e;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(p * G);
-    cfg.blockDim = dim3(kT);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = G;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = G > 1 ? 1 : 0;
-    e = cudaLaunchKernelEx(&cfg, kern, op.band, op.bfac, in, ldi, out, ldo, base, ldb, op.err, (int)nbuf, (int)slot);
-    count_launches(1);
-    return e;
-}
-
-template <typename T, int NR>
-cudaError_t band_launch_g(const DevOperator<T>& op, int32_t p, int32_t wmax, const T* in, int64_t ldi, T* out,
-                          int64_t ldo, const T* base, int64_t ldb, cudaStream_t st) {
-    switch (op.band_G) {
-        case 2: return band_launch<T, NR, 2>(op, p, wmax, in, ldi, out, ldo, base, ldb, st);
-        case 4: return band_launch<T, NR, 4>(op, p, wmax, in, ldi, out, ldo, base, ldb, st);
-        default: return band_launch<T, NR, 1>(op, p, wmax, in, ldi, out, ldo, base, ldb, st);
-    }
-}
-}  // namespace
 
 template <typename T>
 cudaError_t launch_band_solve(const DevOperator<T>& op, int32_t p, int32_t wmax, const T* in, int64_t ldi, T* out,
@@ -509,24 +42,31 @@ cudaError_t launch_band_solve(const DevOperator<T>& op, int32_t p, int32_t wmax,
         const int32_t left = nrhs - c;
         int nr = 1;
         int32_t nb, sl;
+        const int nt = op.band_nt;
         // FP32 takes up to 8 columns per CTA (FP64's partial sums would not fit): each
         // group re-reads the factor, so wider groups save bytes on multi-RHS blocks
-        if (sizeof(T) == 4 && left >= 8 && band_ring(wmax, 8, sizeof(T), 0, &nb, &sl)) nr = 8;
-        else if (left >= 4 && band_ring(wmax, 4, sizeof(T), 0, &nb, &sl)) nr = 4;
-        else if (left >= 2 && band_ring(wmax, 2, sizeof(T), 0, &nb, &sl)) nr = 2;
+        if (sizeof(T) == 4 && left >= 8 && band_ring(wmax, 8, sizeof(T), 0, nt, &nb, &sl)) nr = 8;
+        else if (left >= 4 && band_ring(wmax, 4, sizeof(T), 0, nt, &nb, &sl)) nr = 4;
+        else if (left >= 2 && band_ring(wmax, 2, sizeof(T), 0, nt, &nb, &sl)) nr = 2;
         const T* bs = base ? base + c * ldb : nullptr;
-        cudaError_t e;
-        if constexpr (sizeof(T) == 4) {
-            if (nr == 8) {
-                e = band_launch_g<T, 8>(op, p, wmax, in + c * ldi, ldi, out + c * ldo, ldo, bs, ldb, st);
-                if (e != cudaSuccess) return e;
-                c += nr;
-                continue;
+        cudaError_t e = cudaSuccess;
+        const T* ic = in + c * ldi;
+        T* oc = out + c * ldo;
+        if (nt == 256) {
+            if constexpr (sizeof(T) == 4) {
+                if (nr == 8) e = band_launch_half<T, 8>(op, p, wmax, ic, ldi, oc, ldo, bs, ldb, st);
             }
+            if (nr == 4) e = band_launch_half<T, 4>(op, p, wmax, ic, ldi, oc, ldo, bs, ldb, st);
+            else if (nr == 2) e = band_launch_half<T, 2>(op, p, wmax, ic, ldi, oc, ldo, bs, ldb, st);
+            else if (nr == 1) e = band_launch_half<T, 1>(op, p, wmax, ic, ldi, oc, ldo, bs, ldb, st);
+        } else {
+            if constexpr (sizeof(T) == 4) {
+                if (nr == 8) e = band_launch_g<T, 8, 512>(op, p, wmax, ic, ldi, oc, ldo, bs, ldb, st);
+            }
+            if (nr == 4) e = band_launch_g<T, 4, 512>(op, p, wmax, ic, ldi, oc, ldo, bs, ldb, st);
+            else if (nr == 2) e = band_launch_g<T, 2, 512>(op, p, wmax, ic, ldi, oc, ldo, bs, ldb, st);
+            else if (nr == 1) e = band_launch_g<T, 1, 512>(op, p, wmax, ic, ldi, oc, ldo, bs, ldb, st);
         }
-        if (nr == 4) e = band_launch_g<T, 4>(op, p, wmax, in + c * ldi, ldi, out + c * ldo, ldo, bs, ldb, st);
-        else if (nr == 2) e = band_launch_g<T, 2>(op, p, wmax, in + c * ldi, ldi, out + c * ldo, ldo, bs, ldb, st);
-        else e = band_launch_g<T, 1>(op, p, wmax, in + c * ldi, ldi, out + c * ldo, ldo, bs, ldb, st);
         if (e != cudaSuccess) return e;
         c += nr;
     }

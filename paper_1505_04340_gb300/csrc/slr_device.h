@@ -51,6 +51,7 @@ struct DevOperator {
     T* bfac = nullptr;
     int32_t band_G = 1;            // CTAs per subdomain (thread-block cluster size)
     int32_t band_nbuf = 0;         // ring slots of the band solve (0: the default count)
+    int32_t band_nt = 512;         // threads per band-solve CTA: 512 (one per SM) or 256 (two per SM)
     int32_t* err = nullptr;        // device status word: 1 = a bounded wait expired
     int32_t *e_rp = nullptr, *e_ci = nullptr;  T* e_v = nullptr;     // E   (nI x s)
     int32_t *et_rp = nullptr, *et_ci = nullptr; T* et_v = nullptr;   // E^T (s x nI)
@@ -118,11 +119,6 @@ cudaError_t launch_band_solve(const DevOperator<T>& op, int32_t p, int32_t wmax,
                               T* out, int64_t ldo, const T* base, int64_t ldb, int32_t nrhs,
                               cudaStream_t st);
 // shared memory one band-solve CTA needs for plane width wmax and nr columns per pass
-// Band solve ring: the slot count (nbuf_req, 0 for the default, clamped to
-// what fits) and the bytes per slot that fill the shared memory left beside
-// the tables and vectors; false if no ring fits.  And the CTA's shared bytes.
-bool band_ring(int32_t wmax, int32_t nr, size_t elem, int32_t nbuf_req, int32_t* nbuf, int32_t* slot);
-size_t band_smem_bytes(int32_t wmax, int32_t nr, size_t elem, int32_t nbuf, int32_t slot);
 // ---- K2: gp = g - E^T t (g == NULL: gp = E^T t) ;  eb = E y
 template <typename T>
 cudaError_t launch_gather_et(const DevOperator<T>& op, int32_t s, const T* g, int64_t ldg, const T* t,

@@ -98,6 +98,7 @@ struct HostSetup {
     std::vector<double> bfac;
     int32_t wmax = 0;
     int32_t band_G = 1;   // CTAs (slices) per subdomain in the band solve
+    int32_t band_nt = 512;   // threads per band-solve CTA (256: two CTAs per SM)
     CFactorHost cf;
 };
 

@@ -90,15 +90,19 @@ def test_bsolve_parity(name, precision):
     assert rel(t, want) <= (TOL64 if precision == "fp64" else TOL32)
 
 
-@pytest.mark.parametrize("name,split,slots", [("3d-196", 2, 5), ("3d-196", 4, 5), ("3d-196", 1, 2),
-                                               ("3d-196", 2, 8), ("3d-wide", 2, 8), ("3d-wide", 4, 3),
-                                               ("fv-ragged", 1, 8), ("fv-ragged", 2, 2)])
+@pytest.mark.parametrize("name,split,slots,nt", [("3d-196", 2, 5, 512), ("3d-196", 4, 5, 512), ("3d-196", 1, 2, 512),
+                                                  ("3d-196", 2, 8, 512), ("3d-wide", 2, 8, 512), ("3d-wide", 4, 3, 512),
+                                                  ("fv-ragged", 1, 8, 512), ("fv-ragged", 2, 2, 512),
+                                                  ("3d-196", 2, 2, 256), ("3d-196", 1, 3, 256),
+                                                  ("3d-wide", 2, 2, 256), ("fv-ragged", 1, 2, 256)])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_bsolve_ring_and_split(name, split, slots, precision):
-    """B^{-1} with the factor streamed through 2..8 buffers and 1, 2 or 4 CTAs per subdomain."""
+def test_bsolve_ring_and_split(name, split, slots, nt, precision):
+    """B^{-1} with the factor streamed through 2..8 buffers, 1, 2 or 4 CTAs per subdomain,
+    and CTAs of 512 or 256 threads."""
     P = make(name)
     o = oracle(name)
-    g = gpu_handle(P, precision, band_split=split, band_slots=slots)
+    g = gpu_handle(P, precision, band_split=split, band_slots=slots, band_threads=nt)
+    assert g.get_info()["band_threads"] == nt
     f = np.random.default_rng(2).standard_normal((o.order.n_I, 4))
     t = g.bsolve(cu(f)).cpu().numpy()
     assert rel(t, o.bsolve.solve(f)) <= (TOL64 if precision == "fp64" else TOL32)
@@ -402,12 +406,13 @@ def test_add_vectors_matches_oracle_improvement(name, precision):
 
 
 @pytest.mark.parametrize("name", ["3d-lap", "3d-wide", "fv-ragged"])
-def test_bsolve_wide_rhs_block_mixed(name):
-    """FP32 B^{-1} on 11 right-hand sides (column groups of 8, 2 and 1 per CTA): parity with
-    the oracle, and each column alone equals its column of the block bit for bit."""
+@pytest.mark.parametrize("nt", [512, 256])
+def test_bsolve_wide_rhs_block_mixed(name, nt):
+    """FP32 B^{-1} on 11 right-hand sides (column groups of 8, 2 and 1 per CTA, where they
+    fit): parity with the oracle, and each column alone equals its column of the block."""
     P = make(name)
     o = oracle(name)
-    g = gpu_handle(P, "mixed", nrhs_max=11)
+    g = gpu_handle(P, "mixed", nrhs_max=11, band_threads=nt)
     f = np.random.default_rng(12).standard_normal((o.order.n_I, 11))
     t = g.bsolve(cu(f)).cpu().numpy()
     assert rel(t, o.bsolve.solve(f)) <= TOL32
