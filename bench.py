@@ -100,18 +100,25 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def band_source_sha():
+    """SHA-256 over the band kernel's sources (kernel template and both instantiation units)."""
+    import hashlib
+    hsh = hashlib.sha256()
+    for f in ("slr_band_kernel.cuh", "slr_band.cu", "slr_band_half.cu"):
+        hsh.update(open(os.path.join(ROOT, "paper_1505_04340_gb300", "csrc", f), "rb").read())
+    return hsh.hexdigest()
+
+
 def captured_traffic(summary):
     """DRAM bytes per launch from a committed ncu summary, or None when the
     kernel source changed since the capture (its SHA-256 is recorded there)."""
-    import hashlib
     try:
         kv = {}
         for line in open(os.path.join(ROOT, "profiles", summary)):
             if ":" in line and not line.startswith("#"):
                 k, v = line.split(":", 1)
                 kv[k.strip()] = v.split("#")[0].strip()
-        src = os.path.join(ROOT, "paper_1505_04340_gb300", "csrc", "slr_band.cu")
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        sha = band_source_sha()
         return int(kv["traffic_bytes_per_launch"]) if kv.get("source_sha256") == sha else None
     except (OSError, KeyError, ValueError):
         return None
@@ -231,7 +238,7 @@ def run_profile(args):
     b = torch.tensor(P.b[:, 0], device="cuda")
     h = SLR(P.rowptr, P.colind, P.val, P.part, P.nparts, k=P.k, lanczos_steps=P.lanczos_steps,
             precision=args.precision, nrhs_max=1, flexible_cg=(args.precision == "mixed"),
-            host_loop=args.host_loop)
+            host_loop=args.host_loop, autotune=not args.no_autotune)   # the bench's kernel choices
     info = h.get_info()
     f = torch.randn(info["n_interior"], dtype=torch.float64, device="cuda")
     g = torch.randn(info["s"], dtype=torch.float64, device="cuda")
@@ -247,8 +254,11 @@ def run_profile(args):
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_pop()
     x, its, rel, st = h.pcg(b)
+    inf = h.get_info()
     print(json.dumps({"profile": args.precision, "kernel": args.profile_kernel, "iterations": int(its[0]),
-                      "relres": float(rel[0]), "launches_total": pkg.slr.kernel_launches()}))
+                      "relres": float(rel[0]), "launches_total": pkg.slr.kernel_launches(),
+                      "band_split": inf["band_split"], "band_threads": inf["band_threads"],
+                      "band_source_sha256": band_source_sha()}))
     h.close()
 
 
@@ -492,7 +502,9 @@ def run_ours(args):
                   "apply_rel_diff_vs_fp64": results["apply_rel_diff"],
                   "apply_us": rm["apply_us"], "apply_gbs": rm["apply_gbs"],
                   "band_solve_us": rm["band_us"], "band_gbs": mixed_band_gbs,
-                  "band_frac_hbm": mixed_band_gbs / hbm, "dtype": "f32 apply / f64 outer",
+                  "band_frac_hbm": mixed_band_gbs / hbm,
+                  "band_traffic": (captured_traffic("k_band_solve2_fp32_3d64.txt") if args.problem == "3d64" else None),
+                  "dtype": "f32 apply / f64 outer",
                   "tuning": rm["tuning"]},
         "roofline": roof,
         "band_solve_us": r64["band_us"],
