@@ -92,7 +92,11 @@ typedef struct {
                                S S~^{-1} below K).  slr_get_info reports the rank used.
                                reserved[6]: threads per band-solve CTA, 512 (one CTA per
                                SM) or 256 (two per SM, for more CTAs than SMs); 0 =
-                               automatic.  reserved[7] must be 0.                      */
+                               automatic.  reserved[7]: 1 = solve every level of C's
+                               factor level by level; 0 (default) = the top levels, as
+                               many as fit a fill and setup budget, are solved with an
+                               explicit inverse of their block of the factor (one step
+                               per direction instead of one per level).                */
 } slr_opts;
 
 typedef struct {
@@ -114,6 +118,9 @@ typedef struct {
     int32_t tuned;               /* 1: the three above were chosen by timing (reserved[4]) */
     double tune_seconds;         /* time the tuning took (0 when taken from the cache)      */
     int32_t band_threads;        /* threads per band-solve CTA (256: two subdomains per SM) */
+    int32_t c_top_levels;        /* levels of C's factor solved with the explicit inverse   */
+    int32_t c_top_positions;     /* interface positions in those levels                     */
+    int64_t c_top_entries;       /* stored entries of that inverse (each layout)            */
 } slr_info;
 
 /* Fill *opts with defaults: k = 16, m = 5k, theta = lambda_{k+1}, FP64, 1 RHS, seed 1. */

@@ -150,7 +150,7 @@ slr_status upload_operator(slr_handle h, DevOperator<T>& op, bool with_band) {
     CS(upload(h, &d.d_lev_small, c.lev_small));
     d.nsteps_fwd = d.nsteps_bwd = 0;
     d.max_cta_tasks = 1;
-    for (int32_t l = 0; l < c.nlev; ++l) {
+    for (int32_t l = 0; l < c.top_lev; ++l) {   // the top zone is not level-stepped
         const int32_t nt = c.lev_task_ptr[l + 1] - c.lev_task_ptr[l], np = c.lev_ptask_ptr[l + 1] - c.lev_ptask_ptr[l];
         const int32_t ns = c.lev_sn_ptr[l + 1] - c.lev_sn_ptr[l];
         if (c.lev_small[l]) {
@@ -159,18 +159,25 @@ slr_status upload_operator(slr_handle h, DevOperator<T>& op, bool with_band) {
             d.max_cta_tasks = std::max(d.max_cta_tasks, ns);
             continue;
         }
-        d.nsteps_fwd += (nt > 0 ? 2 : 0) + (np > 0 ? 1 : 0);
-        d.nsteps_bwd += nt > 0 ? 2 : 0;
-        d.max_cta_tasks = std::max({d.max_cta_tasks, nt, np});
+        d.nsteps_fwd += nt + np > 0;
+        d.nsteps_bwd += nt > 0;
+        d.max_cta_tasks = std::max(d.max_cta_tasks, nt + np);
     }
     CS(dalloc(h, &d.bar, 1));
     d.err = op.err;
     d.per_level = h->opts.reserved[3] != 1;   // per-level launches unless the persistent solve is asked for
+    {
+        int dev = 0, nsm = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && nsm > 0)
+            d.nsm = nsm;
+    }
     d.nrow = (int64_t)c.rows.size();
     d.max_n = 1;
     for (int32_t J = 0; J < c.ns; ++J) d.max_n = std::max(d.max_n, c.c0[J + 1] - c.c0[J]);
-    if ((size_t)d.max_n * sizeof(T) > 48 * 1024) {
-        set_error("a separator of C has " + std::to_string(d.max_n) + " nodes, beyond the panel kernel's limit");
+    // a forward task holds t_J (max_n values) and a 32 x 33 reduction array in shared memory
+    if (((size_t)d.max_n + 32 * 33) * sizeof(T) > 48 * 1024) {
+        set_error("a separator of C has " + std::to_string(d.max_n) + " nodes, beyond the C-solve kernels' limit");
         return SLR_ERR_UNSUPPORTED;
     }
     CS(dalloc(h, &d.tasks, c.tasks.size() / 4));
@@ -181,6 +188,43 @@ slr_status upload_operator(slr_handle h, DevOperator<T>& op, bool with_band) {
         CK(cudaMemcpyAsync(d.ptasks, c.ptasks.data(), c.ptasks.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
                            h->stream));
     CS(dalloc(h, &d.wbuf, (size_t)std::max<int64_t>(d.nrow, 1) * r));
+    d.ws_cols = r;
+    // top zone: explicit inverse in both layouts, task tables and workspaces
+    d.top_lev = c.top_lev;
+    d.nT = c.nT;
+    if (c.nT > 0) {
+        CS(upload(h, &d.tpos, c.tpos));
+        CS(upload(h, &d.tseg_ptr, c.tseg_ptr));
+        CS(upload(h, &d.tseg_row, c.tseg_row));
+        CS(upload(h, &d.tsk_off, c.tsk_off));
+        CS(upload(h, &d.tsk_lo, c.tsk_lo));
+        CS(upload(h, &d.tsk, c.tsk));
+        CS(upload(h, &d.tb_off, c.tb_off));
+        CS(upload(h, &d.tb, c.tb));
+        CS(upload(h, &d.tp_off, c.tp_off));
+        CS(upload(h, &d.tp_pos, c.tp_pos));
+        CS(upload(h, &d.tb_cb_part, c.tb_cb_part));
+        auto upload4 = [&](int4** p, const std::vector<int32_t>& v, int32_t* count) -> slr_status {
+            *count = (int32_t)(v.size() / 4);
+            CS(dalloc(h, p, v.size() / 4));
+            if (!v.empty())
+                CK(cudaMemcpyAsync(*p, v.data(), v.size() * sizeof(int32_t), cudaMemcpyHostToDevice, h->stream));
+            return SLR_OK;
+        };
+        CS(upload4(&d.tf_rb, c.tf_rb, &d.n_tf_rb));
+        CS(upload4(&d.tf_tasks, c.tf_tasks, &d.n_tf_tasks));
+        CS(upload4(&d.tb_cb, c.tb_cb, &d.n_tb_cb));
+        CS(upload4(&d.tb_tasks, c.tb_tasks, &d.n_tb_tasks));
+        d.tf_parts = c.tf_parts;
+        d.tb_parts = c.tb_parts;
+        CS(dalloc(h, &d.tT, (size_t)c.nT * r));
+        CS(dalloc(h, &d.tf_part, (size_t)c.tf_parts * r));
+        CS(dalloc(h, &d.tb_part, (size_t)c.tb_parts * r));
+        CS(dalloc(h, &d.tf_cnt, (size_t)d.n_tf_rb));
+        CS(dalloc(h, &d.tb_cnt, (size_t)d.n_tb_cb));
+        CK(cudaMemsetAsync(d.tf_cnt, 0, sizeof(int32_t) * d.n_tf_rb, h->stream));
+        CK(cudaMemsetAsync(d.tb_cnt, 0, sizeof(int32_t) * d.n_tb_cb, h->stream));
+    }
     const int64_t n = hs.n, nI = hs.nI, s = hs.s;
     if constexpr (!std::is_same<T, double>::value) {
         CS(dalloc(h, &op.wr, (size_t)n * r));
@@ -190,7 +234,6 @@ slr_status upload_operator(slr_handle h, DevOperator<T>& op, bool with_band) {
     CS(dalloc(h, &op.eb, (size_t)std::max<int64_t>(nI, 1) * r));
     CS(dalloc(h, &op.gp, (size_t)std::max<int64_t>(s, 1) * r));
     CS(dalloc(h, &op.wf, (size_t)std::max<int64_t>(s, 1) * r));
-    CS(dalloc(h, &op.tf, (size_t)std::max<int64_t>(s, 1) * r));
     CS(dalloc(h, &op.xf, (size_t)std::max<int64_t>(s, 1) * r));
     return SLR_OK;
 }
@@ -239,7 +282,7 @@ slr_status run_apply(slr_handle h, DevOperator<T>& op, const T* r, int64_t ldr, 
     const int32_t nI = hs.nI, s = hs.s;
     CK(launch_band_solve<T>(op, hs.p, hs.wmax, r, ldr, op.tB, nI, nullptr, 0, nrhs, st));   // t = B^{-1} f
     CK(launch_gather_et<T>(op, s, r + nI, ldr, op.tB, nI, op.gp, s, nrhs, st));              // g' = g - E^T t
-    CK(launch_c_forward<T>(op.cf, op.gp, s, op.tf, op.wf, nrhs, st));                        // w = L^{-1} g'
+    CK(launch_c_forward<T>(op.cf, op.gp, s, op.wf, nrhs, st));                               // w = L^{-1} g'
     CK(launch_lowrank<T>(op, s, h->k, op.wf, nrhs, st));                                     // w' (Eq. 4.7)
     CK(launch_c_backward<T>(op.cf, op.wf, op.xf, z + nI, ldz, nrhs, st));                    // y = L^{-T} w'
     CK(launch_spmv_e<T>(op, nI, z + nI, ldz, op.eb, nI, nrhs, st));                          // E y
@@ -262,12 +305,11 @@ slr_status apply_any(slr_handle h, const double* r, int64_t ldr, double* z, int6
 slr_status h_apply(slr_handle h, const double* v, double* w, cudaStream_t st) {
     DevOperator<double>& op = h->op64;
     const int32_t nI = h->hs.nI, s = h->hs.s;
-    CK(cudaMemcpyAsync(op.tf, v, sizeof(double) * s, cudaMemcpyDeviceToDevice, st));
-    CK(launch_c_backward<double>(op.cf, op.tf, op.xf, op.gp, s, 1, st));   // y = L^{-T} v (DD in gp)
+    CK(launch_c_backward<double>(op.cf, v, op.xf, op.gp, s, 1, st));       // y = L^{-T} v (DD in gp)
     CK(launch_spmv_e<double>(op, nI, op.gp, s, op.eb, nI, 1, st));         // E y
     CK(launch_band_solve<double>(op, h->hs.p, h->hs.wmax, op.eb, nI, op.tB, nI, nullptr, 0, 1, st));
     CK(launch_gather_et<double>(op, s, nullptr, 0, op.tB, nI, op.gp, s, 1, st));  // E^T B^{-1} E y
-    CK(launch_c_forward<double>(op.cf, op.gp, s, op.tf, w, 1, st));         // L^{-1} (...)
+    CK(launch_c_forward<double>(op.cf, op.gp, s, w, 1, st));         // L^{-1} (...)
     return SLR_OK;
 }
 
@@ -304,7 +346,7 @@ slr_status run_lanczos(slr_handle h, cudaStream_t st) {
     for (int32_t i = 0; i < s; ++i) z[i] = splitmix_pm1(h->opts.seed, (uint64_t)i);
     CK(cudaMemcpyAsync(w, z.data(), sizeof(double) * s, cudaMemcpyHostToDevice, st));
     CK(launch_csr_spmv(s, h->c_rp, h->c_ci, h->c_v, w, s, op.gp, s, 1, st));     // C z (DD order)
-    CK(launch_c_forward<double>(op.cf, op.gp, s, op.tf, V, 1, st));              // L^{-1} C z
+    CK(launch_c_forward<double>(op.cf, op.gp, s, V, 1, st));              // L^{-1} C z
     slr_status err = SLR_OK;
     CK(launch_dots(s, 1, V, s, V, s, part, sc, 1, st));
     double nrm = std::sqrt(read_scalar(sc, st, &err));
@@ -410,7 +452,7 @@ slr_status run_lanczos_deflated(slr_handle h, int32_t k_add, int32_t steps, cuda
     for (int32_t i = 0; i < s; ++i) z[i] = splitmix_pm1(h->opts.seed + (uint64_t)h->improvements, (uint64_t)i);
     CK(cudaMemcpyAsync(w, z.data(), sizeof(double) * s, cudaMemcpyHostToDevice, st));
     CK(launch_csr_spmv(s, h->c_rp, h->c_ci, h->c_v, w, s, op.gp, s, 1, st));     // C z (DD order)
-    CK(launch_c_forward<double>(op.cf, op.gp, s, op.tf, V, 1, st));              // L^{-1} C z
+    CK(launch_c_forward<double>(op.cf, op.gp, s, V, 1, st));              // L^{-1} C z
     CS(project(V));
     slr_status err = SLR_OK;
     CK(launch_dots(s, 1, V, s, V, s, part, sc, 1, st));
@@ -640,7 +682,7 @@ slr_status autotune(slr_handle h, DevOperator<T>& op, cudaStream_t st) {
             op.cf.per_level = (v == 0);
             cudaGraphExec_t ex = nullptr;
             CS(capture_graph(h, [&](cudaStream_t cs) -> slr_status {
-                CK(launch_c_forward<T>(op.cf, op.gp, hs.s, op.tf, op.wf, 1, cs));
+                CK(launch_c_forward<T>(op.cf, op.gp, hs.s, op.wf, 1, cs));
                 CK(launch_c_backward<T>(op.cf, op.wf, op.xf, op.gp, hs.s, 1, cs));
                 return SLR_OK;
             }, &ex));
@@ -712,6 +754,7 @@ slr_status setup_impl(slr_handle h, int32_t n, const int32_t* rowptr, const int3
     }
     double t2 = now_s();
     CS(host_c_factor(hs, h->opts.c_leaf > 0 ? h->opts.c_leaf : 64, 32));
+    host_c_top(hs.cf, h->opts.reserved[7] == 1 ? hs.cf.nlev : host_c_top_choose(hs.cf));
     double t3 = now_s();
     if (vb)
         fprintf(stderr, "[slr] n=%d nI=%d s=%d p=%d wmax=%d band=%zu cvals=%zu sn=%d lev=%d | analysis %.3fs B %.3fs C %.3fs\n",
@@ -768,6 +811,8 @@ slr_status setup_impl(slr_handle h, int32_t n, const int32_t* rowptr, const int3
     if (h->opts.precision == SLR_PREC_FP64) std::vector<double>().swap(hs.bfac);
     std::vector<double>().swap(hs.cf.panel);
     std::vector<double>().swap(hs.cf.dinv);
+    std::vector<double>().swap(hs.cf.tsk);
+    std::vector<double>().swap(hs.cf.tb);
     h->op64.ready = true;
     h->op32.ready = h->opts.precision == SLR_PREC_MIXED;
     return SLR_OK;
@@ -927,7 +972,7 @@ slr_status slr_setup(int32_t n, const int32_t* rowptr, const int32_t* colind, co
         h->opts.reserved[3] < 0 || h->opts.reserved[3] > 1 || h->opts.reserved[4] < 0 || h->opts.reserved[4] > 1 ||
         h->opts.reserved[5] < 0 || h->opts.reserved[5] == 1 ||
         (h->opts.reserved[6] != 0 && h->opts.reserved[6] != 256 && h->opts.reserved[6] != 512) ||
-        h->opts.reserved[7] != 0) {
+        h->opts.reserved[7] < 0 || h->opts.reserved[7] > 1) {
         set_error("invalid options");
         delete h;
         return SLR_ERR_INVALID_ARG;
@@ -991,14 +1036,14 @@ static slr_status interface_solve(slr_handle h, const double* g, double* y, int3
     DeviceGuard gd(h->device);
     if (h->opts.precision == SLR_PREC_FP64) {
         DevOperator<double>& op = h->op64;
-        CK(launch_c_forward<double>(op.cf, g, ld, op.tf, op.wf, nrhs, st));
+        CK(launch_c_forward<double>(op.cf, g, ld, op.wf, nrhs, st));
         if (lowrank) CK(launch_lowrank<double>(op, s, h->k, op.wf, nrhs, st));
         CK(launch_c_backward<double>(op.cf, op.wf, op.xf, y, ld, nrhs, st));
         return SLR_OK;
     }
     DevOperator<float>& op = h->op32;
     CK(launch_convert<double, float>(s, nrhs, g, ld, op.gp, s, st));
-    CK(launch_c_forward<float>(op.cf, op.gp, s, op.tf, op.wf, nrhs, st));
+    CK(launch_c_forward<float>(op.cf, op.gp, s, op.wf, nrhs, st));
     if (lowrank) CK(launch_lowrank<float>(op, s, h->k, op.wf, nrhs, st));
     CK(launch_c_backward<float>(op.cf, op.wf, op.xf, op.gp, s, nrhs, st));
     CK(launch_convert<float, double>(s, nrhs, op.gp, s, y, ld, st));
@@ -1093,12 +1138,11 @@ slr_status slr_set_lowrank(slr_handle h, int32_t k, const double* Z, const doubl
     DeviceGuard g(h->device);
     cudaStream_t st = (cudaStream_t)stream;
     h->stream = st;
-    double *Zd = nullptr, *CZ = nullptr, *U = nullptr, *T1 = nullptr;
+    double *Zd = nullptr, *CZ = nullptr, *U = nullptr;
     if (k > 0) {
         CS(dalloc(h, &Zd, (size_t)s * k));
         CS(dalloc(h, &CZ, (size_t)s * k));
         CS(dalloc(h, &U, (size_t)s * k));
-        CS(dalloc(h, &T1, (size_t)s * k));
         CK(cudaMemcpyAsync(Zd, Z, sizeof(double) * s * k, cudaMemcpyHostToDevice, st));
         CK(launch_csr_spmv(s, h->c_rp, h->c_ci, h->c_v, Zd, s, CZ, s, k, st));       // C Z
         // U = L^{-1} C Z, at most nrhs_max columns at a time (the forward solve's
@@ -1106,8 +1150,7 @@ slr_status slr_set_lowrank(slr_handle h, int32_t k, const double* Z, const doubl
         const int32_t r = std::max(1, h->opts.nrhs_max);
         for (int32_t c0 = 0; c0 < k; c0 += r) {
             const int32_t nc = std::min(r, k - c0);
-            CK(launch_c_forward<double>(h->op64.cf, CZ + (int64_t)c0 * s, s, T1 + (int64_t)c0 * s,
-                                        U + (int64_t)c0 * s, nc, st));
+            CK(launch_c_forward<double>(h->op64.cf, CZ + (int64_t)c0 * s, s, U + (int64_t)c0 * s, nc, st));
         }
         CK(cudaStreamSynchronize(st));
     }
@@ -1126,7 +1169,6 @@ slr_status slr_set_lowrank(slr_handle h, int32_t k, const double* Z, const doubl
         dfree(h, Zd, (size_t)s * k);
         dfree(h, CZ, (size_t)s * k);
         dfree(h, U, (size_t)s * k);
-        dfree(h, T1, (size_t)s * k);
     }
     account(h);
     return SLR_OK;
@@ -1154,15 +1196,17 @@ slr_status slr_get_lowrank(slr_handle h, double* Z, double* lam, double* theta_o
     cudaStream_t st = (cudaStream_t)stream;
     const int32_t s = h->hs.s, k = h->k;
     if (Z && k > 0) {
-        double *T1 = nullptr, *X1 = nullptr, *Y1 = nullptr;
-        CS(dalloc(h, &T1, (size_t)s * k));
+        double *X1 = nullptr, *Y1 = nullptr;
         CS(dalloc(h, &X1, (size_t)s * k));
         CS(dalloc(h, &Y1, (size_t)s * k));
-        CK(cudaMemcpyAsync(T1, h->op64.U, sizeof(double) * s * k, cudaMemcpyDeviceToDevice, st));
-        CK(launch_c_backward<double>(h->op64.cf, T1, X1, Y1, s, k, st));           // Z = L^{-T} U (DD order)
+        // Z = L^{-T} U (DD order), at most nrhs_max columns at a time (the top zone's
+        // partial-sum workspace holds nrhs_max columns)
+        const int32_t r = std::max(1, h->opts.nrhs_max);
+        for (int32_t c0 = 0; c0 < k; c0 += r)
+            CK(launch_c_backward<double>(h->op64.cf, h->op64.U + (int64_t)c0 * s, X1 + (int64_t)c0 * s,
+                                         Y1 + (int64_t)c0 * s, s, std::min(r, k - c0), st));
         CK(cudaMemcpyAsync(Z, Y1, sizeof(double) * s * k, cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
-        dfree(h, T1, (size_t)s * k);
         dfree(h, X1, (size_t)s * k);
         dfree(h, Y1, (size_t)s * k);
     }
@@ -1223,6 +1267,9 @@ slr_status slr_get_info(slr_handle h, slr_info* info) {
     info->tuned = h->tuned ? 1 : 0;
     info->tune_seconds = h->tune_seconds;
     info->band_threads = f64 ? h->op64.band_nt : h->op32.band_nt;
+    info->c_top_levels = hs.cf.nlev - hs.cf.top_lev;
+    info->c_top_positions = hs.cf.nT;
+    info->c_top_entries = hs.cf.tsk_off.empty() ? 0 : hs.cf.tsk_off.back();
     return SLR_OK;
 }
 

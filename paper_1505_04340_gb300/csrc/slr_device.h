@@ -19,14 +19,14 @@ struct DevCFactor {
     int64_t* r_off = nullptr;      // [ns+1]
     int32_t* rows = nullptr;       // R_J
     int64_t* pan_off = nullptr;    // [ns+1]
-    T* panel = nullptr;            // row-major |R_J| x n_J
+    T* panel = nullptr;            // M_J = L[R_J, J] L_JJ^{-1}, row-major |R_J| x n_J
     int64_t* dinv_off = nullptr;   // [ns+1]
     T* dinv = nullptr;             // packed lower, column-major
     int64_t* seg_ptr = nullptr;    // [s+1]
     int32_t* seg_row = nullptr;    // panel rows holding each position
     int64_t nrow = 0;              // panel rows in total
-    int32_t max_n = 0;             // widest supernode (shared memory of the forward panel kernel)
-    T* wbuf = nullptr;             // [nrow x nrhs_max] panel products of the forward solve
+    int32_t max_n = 0;             // widest supernode (shared memory of a forward task: t_J)
+    T* wbuf = nullptr;             // [nrow x nrhs_max] panel products M_J t_J of the forward solve
     int4* tasks = nullptr;         // (supernode, first column, count <= 32, 0)
     int4* ptasks = nullptr;        // (supernode, first panel row, count <= 32, 0)
     std::vector<int32_t> lev_task_ptr;    // host copies, [nlev+1]
@@ -41,7 +41,18 @@ struct DevCFactor {
     int32_t max_cta_tasks = 1;                // most CTA tasks of any step (caps the grid)
     unsigned* bar = nullptr;                  // grid barrier counter, zeroed before each launch
     int32_t* err = nullptr;                   // the operator's status word
+    // top zone (levels >= top_lev): explicit inverse of L_TT, one step per direction
+    int32_t top_lev = 0, nT = 0;
+    int32_t *tpos = nullptr, *tseg_row = nullptr, *tsk_lo = nullptr, *tp_pos = nullptr, *tb_cb_part = nullptr;
+    int64_t *tseg_ptr = nullptr, *tsk_off = nullptr, *tb_off = nullptr, *tp_off = nullptr;
+    T *tsk = nullptr, *tb = nullptr;          // forward row skyline, backward block columns
+    int4 *tf_rb = nullptr, *tf_tasks = nullptr, *tb_cb = nullptr, *tb_tasks = nullptr;
+    int32_t n_tf_rb = 0, n_tf_tasks = 0, n_tb_cb = 0, n_tb_tasks = 0, tf_parts = 0, tb_parts = 0;
+    T *tT = nullptr, *tf_part = nullptr, *tb_part = nullptr;   // workspaces of nrhs_max columns
+    int32_t *tf_cnt = nullptr, *tb_cnt = nullptr;              // arrival counters, zero between solves
+    int32_t ws_cols = 0;                      // right-hand sides the workspaces (wbuf and the zone's) hold
     bool per_level = true;                    // one launch per level step (else one cooperative launch)
+    int32_t nsm = 152;                        // SMs of the device (CTA size of the per-level kernels)
 };
 
 // Everything one apply needs in precision T (double: FP64 path; float: mixed).
@@ -62,7 +73,7 @@ struct DevOperator {
     // workspaces, nrhs_max columns each, leading dimension = rows
     T *wr = nullptr, *wz = nullptr;          // n: converted input / output (mixed only)
     T *tB = nullptr, *eb = nullptr;          // nI
-    T *gp = nullptr, *wf = nullptr, *tf = nullptr, *xf = nullptr;   // s
+    T *gp = nullptr, *wf = nullptr, *xf = nullptr;   // s
     T *vk = nullptr, *part = nullptr;        // k x r, partial sums
     bool ready = false;
 };
@@ -128,13 +139,15 @@ cudaError_t launch_spmv_e(const DevOperator<T>& op, int32_t nI, const T* y, int6
                           int64_t ldo, int32_t nrhs, cudaStream_t st);
 // ---- K3: C solves.  fwd: xf = L^{-1} P g (g in DD order, xf in factor order)
 //              bwd: xf = L^{-T} yf (factor order), optional scatter to DD order y_dd
-// tf, xf, yf: s x nrhs (leading dimension s).  The forward solve also writes
-// cf.wbuf, which holds nrhs_max columns: callers pass nrhs <= opts.nrhs_max.
+// xf, yf: s x nrhs (leading dimension s); yf is read only and must not overlap xf.
+// The forward solve also writes cf.wbuf and both use the top zone's workspaces,
+// which hold cf.ws_cols (= nrhs_max) columns: a wider call returns
+// cudaErrorInvalidValue without launching anything.
 template <typename T>
-cudaError_t launch_c_forward(const DevCFactor<T>& cf, const T* g_dd, int64_t ldg, T* tf, T* xf,
-                             int32_t nrhs, cudaStream_t st);
+cudaError_t launch_c_forward(const DevCFactor<T>& cf, const T* g_dd, int64_t ldg, T* xf, int32_t nrhs,
+                             cudaStream_t st);
 template <typename T>
-cudaError_t launch_c_backward(const DevCFactor<T>& cf, T* yf_inout, T* xf, T* y_dd, int64_t ldy,
+cudaError_t launch_c_backward(const DevCFactor<T>& cf, const T* yf, T* xf, T* y_dd, int64_t ldy,
                               int32_t nrhs, cudaStream_t st);
 // ---- K4: w' = cinv w + U (d o (U^T w)) in factor order (in place on w)
 template <typename T>

@@ -9,8 +9,11 @@
 //  * host_band_factor   - exact banded Cholesky of every B_i (Section 5.2),
 //                         repacked plane by plane with inverted diagonal blocks
 //  * host_c_factor      - exact Cholesky C = L L^T (Eq. 3.1) in a nested
-//                         dissection order, supernodal, with inverted diagonal
-//                         blocks and a level schedule for the device solves
+//                         dissection order, supernodal, kept as inverted diagonal
+//                         blocks L_JJ^{-1} and panels M_J = L[R_J, J] L_JJ^{-1},
+//                         with a level schedule for the device solves
+//  * host_c_top         - explicit inverse of the factor's top levels (partitioned
+//                         inverse) for one-step solves of that zone
 //  * host_tridiag_eig   - eigenpairs of the Lanczos tridiagonal (Section 5.1)
 #include <algorithm>
 #include <cmath>
@@ -640,7 +643,7 @@ slr_status host_c_factor(HostSetup& hs, int32_t leaf, int32_t task_rows) {
         set_error("C is not positive definite (Cholesky pivot <= 0 in supernode " + std::to_string(bad) + ")");
         return SLR_ERR_NOT_SPD;
     }
-    // inverted diagonal blocks (packed lower, column-major) and row-major panels
+    // inverted diagonal blocks (packed lower, column-major) and row-major panels M_J
     cf.dinv_off.assign(ns + 1, 0);
     cf.pan_off.assign(ns + 1, 0);
     for (int32_t J = 0; J < ns; ++J) {
@@ -662,7 +665,19 @@ slr_status host_c_factor(HostSetup& hs, int32_t leaf, int32_t task_rows) {
             int64_t cs = (int64_t)j * nJ - (int64_t)j * (j - 1) / 2;
             for (int32_t i = j; i < nJ; ++i) Dv[cs + (i - j)] = X[(size_t)i * nJ + j];
         }
-        std::memcpy(cf.panel.data() + cf.pan_off[J], Fj + (int64_t)nJ * nJ, sizeof(double) * nr * nJ);
+        // M_J = L[R_J, J] L_JJ^{-1}: the off-diagonal block of the unit block factor
+        // Lhat = L D^{-1}, D = diag(L_JJ), so C = Lhat D D^T Lhat^T (a block LDL^T form)
+        const double* Pj = Fj + (int64_t)nJ * nJ;
+        double* Mj = cf.panel.data() + cf.pan_off[J];
+        for (int64_t pr = 0; pr < nr; ++pr) {
+            const double* Lp = Pj + pr * nJ;
+            double* Mp = Mj + pr * nJ;
+            for (int32_t k = 0; k < nJ; ++k) {
+                const double a = Lp[k];
+                const double* Xk = X.data() + (size_t)k * nJ;
+                for (int32_t j = 0; j <= k; ++j) Mp[j] += a * Xk[j];
+            }
+        }
     }
     // forward gather lists: row i of L left of its diagonal block is the union of
     // the panel rows R_K[p] = i of its descendants K
@@ -717,6 +732,230 @@ slr_status host_c_factor(HostSetup& hs, int32_t leaf, int32_t task_rows) {
         cf.lev_sn_ptr[l + 1] = (int32_t)cf.lev_sn.size();
     }
     return SLR_OK;
+}
+
+// ------------------------------------------------------------------ top zone (partitioned inverse)
+
+// Entries of L_TT^{-1} (block columns over each supernode's path to the root)
+// and the multiply-adds that build it, for the zone of levels >= L.
+static void top_zone_cost(const CFactorHost& cf, int32_t L, double* entries, double* fmas) {
+    double e = 0.0, f = 0.0;
+    for (int32_t J = 0; J < cf.ns; ++J) {
+        if (cf.level[J] < L) continue;
+        const double nJ = cf.c0[J + 1] - cf.c0[J];
+        double below = nJ;
+        e += nJ * (nJ + 1) / 2;
+        f += nJ * nJ * nJ / 2;
+        for (int32_t A = cf.parent[J]; A >= 0; A = cf.parent[A]) {
+            const double nA = cf.c0[A + 1] - cf.c0[A];
+            e += nA * nJ;
+            f += nA * below * nJ + nA * nA / 2 * nJ;
+            below += nA;
+        }
+    }
+    *entries = e;
+    *fmas = f;
+}
+
+int32_t host_c_top_choose(const CFactorHost& cf) {
+    const double fac = (double)cf.panel.size() + (double)cf.dinv.size();
+    int32_t best = cf.nlev;
+    for (int32_t L = cf.nlev - 1; L >= 0; --L) {
+        double e = 0.0, f = 0.0;
+        top_zone_cost(cf, L, &e, &f);
+        if (e > kTopEntries * fac || f > kTopFmas) break;
+        best = L;
+    }
+    return cf.nlev - best >= 2 ? best : cf.nlev;   // a zone of one level saves no step
+}
+
+void host_c_top(CFactorHost& cf, int32_t top_lev) {
+    cf.top_lev = cf.nlev;
+    cf.nT = 0;
+    cf.tpos.clear(); cf.tseg_ptr.assign(1, 0); cf.tseg_row.clear();
+    cf.tsk_off.assign(1, 0); cf.tsk_lo.clear(); cf.tsk.clear();
+    cf.tf_rb.clear(); cf.tf_tasks.clear();
+    cf.tb_off.assign(cf.ns + 1, 0); cf.tb.clear(); cf.tp_off.assign(cf.ns + 1, 0); cf.tp_pos.clear();
+    cf.tb_cb.clear(); cf.tb_cb_part.clear(); cf.tb_tasks.clear();
+    cf.tf_parts = cf.tb_parts = 0;
+    if (top_lev >= cf.nlev) return;
+    const int32_t ns = cf.ns, s = cf.s;
+    std::vector<uint8_t> inT(ns, 0);
+    std::vector<int32_t> Tl;   // zone supernodes, ascending (children before parents)
+    for (int32_t J = 0; J < ns; ++J)
+        if (cf.level[J] >= top_lev) { inT[J] = 1; Tl.push_back(J); }
+    std::vector<int32_t> snof(s), loc(s, -1);
+    for (int32_t J = 0; J < ns; ++J)
+        for (int32_t t = cf.c0[J]; t < cf.c0[J + 1]; ++t) snof[t] = J;
+    std::vector<int32_t> tpos;
+    for (int32_t t = 0; t < s; ++t)
+        if (inT[snof[t]]) { loc[t] = (int32_t)tpos.size(); tpos.push_back(t); }
+    const int32_t nT = (int32_t)tpos.size();
+    // lo[A] = first local index of the zone within A's subtree; the subtree must
+    // fill lo[A] .. (A's last local index) exactly
+    std::vector<int32_t> lo(ns, 0);
+    std::vector<int64_t> sz(ns, 0);
+    for (int32_t J : Tl) { lo[J] = loc[cf.c0[J]]; sz[J] = cf.c0[J + 1] - cf.c0[J]; }
+    for (int32_t J : Tl) {
+        const int32_t A = cf.parent[J];
+        if (A < 0) continue;
+        if (!inT[A]) return;   // cannot happen: a parent's level is above its child's
+        lo[A] = std::min(lo[A], lo[J]);
+        sz[A] += sz[J];
+    }
+    for (int32_t A : Tl)
+        if ((int64_t)loc[cf.c0[A + 1] - 1] - lo[A] + 1 != sz[A]) return;   // not contiguous: no zone
+    // block columns X_J = L_TT^{-1}[path_J, J] with the unit block factor Lhat = L D^{-1}:
+    // Z = Lhat_TT^{-1}[path_J, J] (Z_J = I, Z_A = - sum_K M_K[rows in A] Z_K over the path
+    // below A), then X_A = L_AA^{-1} Z_A
+    std::vector<int64_t> plen(ns, 0);
+    for (int32_t J : Tl) {
+        for (int32_t A = J; A >= 0; A = cf.parent[A]) plen[J] += cf.c0[A + 1] - cf.c0[A];
+        const int64_t nJ = cf.c0[J + 1] - cf.c0[J];
+        cf.tb_off[J + 1] = nJ * plen[J];
+        cf.tp_off[J + 1] = plen[J];
+    }
+    for (int32_t J = 0; J < ns; ++J) {
+        cf.tb_off[J + 1] += cf.tb_off[J];
+        cf.tp_off[J + 1] += cf.tp_off[J];
+    }
+    cf.tb.assign(cf.tb_off[ns], 0.0);
+    cf.tp_pos.assign(cf.tp_off[ns], 0);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (size_t idx = 0; idx < Tl.size(); ++idx) {
+        const int32_t J = Tl[idx];   // children first: the long paths start early
+        const int32_t nJ = cf.c0[J + 1] - cf.c0[J];
+        std::vector<int32_t> path;
+        std::vector<int64_t> po;
+        int64_t rows = 0;
+        for (int32_t A = J; A >= 0; A = cf.parent[A]) {
+            path.push_back(A);
+            po.push_back(rows);
+            rows += cf.c0[A + 1] - cf.c0[A];
+        }
+        std::vector<double> Z((size_t)rows * nJ, 0.0);
+        for (int32_t q = 0; q < nJ; ++q) Z[(size_t)q * nJ + q] = 1.0;
+        for (size_t i = 1; i < path.size(); ++i) {
+            const int32_t A = path[i], a0 = cf.c0[A], nA = cf.c0[A + 1] - a0;
+            double* ZA = Z.data() + po[i] * nJ;
+            for (size_t k = 0; k < i; ++k) {
+                const int32_t K = path[k], nK = cf.c0[K + 1] - cf.c0[K];
+                const int32_t* Rk = cf.rows.data() + cf.r_off[K];
+                const int64_t nrK = cf.r_off[K + 1] - cf.r_off[K];
+                const int64_t pb = std::lower_bound(Rk, Rk + nrK, a0) - Rk;
+                const int64_t pe = std::lower_bound(Rk, Rk + nrK, a0 + nA) - Rk;
+                const double* MK = cf.panel.data() + cf.pan_off[K];
+                const double* ZK = Z.data() + po[k] * nJ;
+                for (int64_t p = pb; p < pe; ++p) {
+                    double* zr = ZA + (int64_t)(Rk[p] - a0) * nJ;
+                    const double* mrow = MK + p * nK;
+                    int32_t q = 0;
+                    for (; q + 3 < nK; q += 4) {   // four rows of Z_K per pass over zr
+                        const double m0 = mrow[q], m1 = mrow[q + 1], m2 = mrow[q + 2], m3 = mrow[q + 3];
+                        const double* z0 = ZK + (int64_t)q * nJ;
+                        const double *z1 = z0 + nJ, *z2 = z1 + nJ, *z3 = z2 + nJ;
+                        for (int32_t c = 0; c < nJ; ++c) zr[c] -= (m0 * z0[c] + m1 * z1[c]) + (m2 * z2[c] + m3 * z3[c]);
+                    }
+                    for (; q < nK; ++q) {
+                        const double m = mrow[q];
+                        const double* zk = ZK + (int64_t)q * nJ;
+                        for (int32_t c = 0; c < nJ; ++c) zr[c] -= m * zk[c];
+                    }
+                }
+            }
+        }
+        double* X = cf.tb.data() + cf.tb_off[J];
+        int32_t* pp = cf.tp_pos.data() + cf.tp_off[J];
+        for (size_t i = 0; i < path.size(); ++i) {
+            const int32_t A = path[i], nA = cf.c0[A + 1] - cf.c0[A];
+            const double* Dv = cf.dinv.data() + cf.dinv_off[A];
+            auto dv = [&](int32_t a, int32_t b) { return Dv[(int64_t)b * nA - (int64_t)b * (b - 1) / 2 + (a - b)]; };
+            for (int32_t a = 0; a < nA; ++a) {
+                double* xr = X + (po[i] + a) * nJ;
+                const double* zb = Z.data() + po[i] * nJ;
+                int32_t b = 0;
+                for (; b + 3 <= a; b += 4) {
+                    const double d0 = dv(a, b), d1 = dv(a, b + 1), d2 = dv(a, b + 2), d3 = dv(a, b + 3);
+                    const double* z0 = zb + (int64_t)b * nJ;
+                    const double *z1 = z0 + nJ, *z2 = z1 + nJ, *z3 = z2 + nJ;
+                    for (int32_t c = 0; c < nJ; ++c) xr[c] += (d0 * z0[c] + d1 * z1[c]) + (d2 * z2[c] + d3 * z3[c]);
+                }
+                for (; b <= a; ++b) {
+                    const double d = dv(a, b);
+                    const double* z = zb + (int64_t)b * nJ;
+                    for (int32_t c = 0; c < nJ; ++c) xr[c] += d * z[c];
+                }
+                pp[po[i] + a] = cf.c0[A] + a;
+            }
+        }
+    }
+    // forward row skyline of the same entries
+    cf.tsk_lo.assign(nT, 0);
+    cf.tsk_off.assign(nT + 1, 0);
+    for (int32_t la = 0; la < nT; ++la) {
+        cf.tsk_lo[la] = lo[snof[tpos[la]]];
+        cf.tsk_off[la + 1] = cf.tsk_off[la] + (la - cf.tsk_lo[la] + 1);
+    }
+    cf.tsk.assign(cf.tsk_off[nT], 0.0);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (size_t idx = 0; idx < Tl.size(); ++idx) {
+        const int32_t J = Tl[idx], nJ = cf.c0[J + 1] - cf.c0[J];
+        const double* X = cf.tb.data() + cf.tb_off[J];
+        const int32_t* pp = cf.tp_pos.data() + cf.tp_off[J];
+        const int64_t rows = cf.tp_off[J + 1] - cf.tp_off[J];
+        for (int64_t r = 0; r < rows; ++r) {
+            const int32_t la = loc[pp[r]];
+            for (int32_t q = 0; q < nJ; ++q) {
+                const int32_t lc = loc[cf.c0[J] + q];
+                if (lc <= la) cf.tsk[cf.tsk_off[la] + (lc - cf.tsk_lo[la])] = X[r * nJ + q];
+            }
+        }
+    }
+    // gather lists of the zone's rows: contributions of supernodes outside the zone
+    std::vector<int32_t> prow_sn(cf.rows.size());
+    for (int32_t K = 0; K < ns; ++K)
+        for (int64_t t = cf.r_off[K]; t < cf.r_off[K + 1]; ++t) prow_sn[t] = K;
+    cf.tseg_ptr.assign(nT + 1, 0);
+    for (int32_t la = 0; la < nT; ++la) {
+        const int32_t pos = tpos[la];
+        for (int64_t e = cf.seg_ptr[pos]; e < cf.seg_ptr[pos + 1]; ++e)
+            if (!inT[prow_sn[cf.seg_row[e]]]) cf.tseg_row.push_back(cf.seg_row[e]);
+        cf.tseg_ptr[la + 1] = (int64_t)cf.tseg_row.size();
+    }
+    // forward tasks: 32-row blocks within a supernode, their columns lo .. last row in chunks
+    for (int32_t A : Tl) {
+        const int32_t l0 = loc[cf.c0[A]], l1 = loc[cf.c0[A + 1] - 1] + 1;
+        for (int32_t r0 = l0; r0 < l1; r0 += 32) {
+            const int32_t cnt = std::min(32, l1 - r0), clo = lo[A], chi = r0 + cnt;
+            const int32_t nch = (chi - clo + kTopCW - 1) / kTopCW;
+            const int32_t rb = (int32_t)(cf.tf_rb.size() / 4);
+            cf.tf_rb.insert(cf.tf_rb.end(), {r0, cnt, nch, cf.tf_parts});
+            for (int32_t k = 0; k < nch; ++k)
+                cf.tf_tasks.insert(cf.tf_tasks.end(), {rb, clo + k * kTopCW, std::min(chi, clo + (k + 1) * kTopCW), k});
+            cf.tf_parts += 32 * nch;
+        }
+    }
+    // backward tasks: 32-column blocks of J, their path rows (from the block's first
+    // column down: the rows above it in J's diagonal block are zero) in chunks
+    for (int32_t J : Tl) {
+        const int32_t nJ = cf.c0[J + 1] - cf.c0[J];
+        const int64_t rows = cf.tp_off[J + 1] - cf.tp_off[J];
+        for (int32_t c0 = 0; c0 < nJ; c0 += 32) {
+            const int32_t cnt = std::min(32, nJ - c0);
+            const int32_t nch = (int32_t)((rows - c0 + kTopRCH - 1) / kTopRCH);
+            const int32_t cb = (int32_t)(cf.tb_cb.size() / 4);
+            cf.tb_cb.insert(cf.tb_cb.end(), {J, c0, cnt, nch});
+            cf.tb_cb_part.push_back(cf.tb_parts);
+            for (int32_t k = 0; k < nch; ++k)
+                cf.tb_tasks.insert(cf.tb_tasks.end(),
+                                   {cb, (int32_t)(c0 + (int64_t)k * kTopRCH),
+                                    (int32_t)std::min<int64_t>(rows, c0 + (int64_t)(k + 1) * kTopRCH), k});
+            cf.tb_parts += 32 * nch;
+        }
+    }
+    cf.tpos = std::move(tpos);
+    cf.nT = nT;
+    cf.top_lev = top_lev;
 }
 
 // ------------------------------------------------------------------ Section 5.1: T = Y diag(lam) Y^T

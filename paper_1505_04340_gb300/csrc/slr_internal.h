@@ -63,10 +63,15 @@ struct CFactorHost {
     std::vector<int64_t> r_off;        // [ns+1] offsets of R_J in rows
     std::vector<int32_t> rows;         // R_J: factor positions below the diagonal block
     std::vector<int64_t> pan_off;      // [ns+1] offsets of the row-major |R_J| x n_J panels
-    std::vector<double> panel;         // L[R_J, J]
+    std::vector<double> panel;         // M_J = L[R_J, J] L_JJ^{-1} (unit block factor, see below)
     std::vector<int64_t> dinv_off;     // [ns+1] offsets of the packed inverse blocks
     std::vector<double> dinv;          // L_JJ^{-1}: lower triangle, column-major, packed
-    // Forward solve: after level l, w[r_off[K] + p] = L[R_K[p], K] x_K for its supernodes K;
+    // With Lhat = L D^{-1} (D = diag(L_JJ), unit diagonal blocks, off-diagonal
+    // blocks M_J) the solves are L^{-1} = D^{-1} Lhat^{-1} and L^{-T} = Lhat^{-T} D^{-T}:
+    // forward  t_J = g_J - sum_K M_K[rows in J] t_K,  x_J = L_JJ^{-1} t_J
+    // backward x_J = L_JJ^{-T} y_J - M_J^T x_{R_J}
+    // so each level is one dependent step in either direction.
+    // Forward solve: after level l, w[r_off[K] + p] = M_K[p, :] t_K for its supernodes K;
     // position i then needs the sum of w over the panel rows that hold row i.
     std::vector<int64_t> seg_ptr;      // [s+1] panel rows of each position, CSR
     std::vector<int32_t> seg_row;      // global panel-row index r_off[K] + p
@@ -81,7 +86,37 @@ struct CFactorHost {
     std::vector<int32_t> lev_sn_ptr;   // [nlev+1] supernodes per level
     std::vector<int32_t> lev_sn;       // supernode ids, level by level
     std::vector<uint8_t> lev_small;    // [nlev]
+    // Top zone: the supernodes of levels >= top_lev (closed under parents) are
+    // solved with an explicit inverse of their diagonal block L_TT of L (a
+    // partitioned inverse): forward x_T = L_TT^{-1} t_T with t_T = g_T - L_TS x_S,
+    // backward y_T = L_TT^{-T} x_T, so the zone costs one step per direction
+    // (plus the gather of t_T) instead of one per level.  Local index la of the
+    // zone's positions follows the factor order; the zone of a supernode's
+    // subtree then covers one contiguous range of local indices.
+    int32_t top_lev = 0;               // = nlev when there is no zone
+    int32_t nT = 0;                    // positions in the zone
+    std::vector<int32_t> tpos;         // [nT] local index -> factor position
+    std::vector<int64_t> tseg_ptr;     // [nT+1] gather lists of the zone's rows, restricted to
+    std::vector<int32_t> tseg_row;     //   panel rows of supernodes outside the zone
+    std::vector<int64_t> tsk_off;      // [nT+1] forward, row skyline: row la of L_TT^{-1} holds
+    std::vector<int32_t> tsk_lo;       //   local columns tsk_lo[la] .. la, starting at tsk_off[la]
+    std::vector<double> tsk;
+    std::vector<int32_t> tf_rb;        // forward row blocks, 4 ints: first row, count (<= 32),
+                                       //   chunks, partial-sum offset
+    std::vector<int32_t> tf_tasks;     // 4 ints: row block, first column, end column, chunk
+    std::vector<int64_t> tb_off;       // [ns+1] backward: block column of J (zone only), row-major
+    std::vector<double> tb;            //   |path_J| x n_J, path_J = rows of J, then of its ancestors
+    std::vector<int64_t> tp_off;       // [ns+1] factor positions of the path rows
+    std::vector<int32_t> tp_pos;
+    std::vector<int32_t> tb_cb;        // backward column blocks, 4 ints: J, first column, count, chunks
+    std::vector<int32_t> tb_cb_part;   //   partial-sum offset of each column block
+    std::vector<int32_t> tb_tasks;     // 4 ints: column block, first path row, end path row, chunk
+    int32_t tf_parts = 0, tb_parts = 0;   // partial sums per right-hand side
 };
+constexpr int32_t kTopCW = 512;        // forward: columns per chunk of a 32-row block
+constexpr int32_t kTopRCH = 256;       // backward: path rows per chunk of a 32-column block
+constexpr double kTopEntries = 2.0;    // zone inverse at most this many times the factor's entries
+constexpr double kTopFmas = 1.5e10;    // and at most this many host multiply-adds to build
 constexpr int32_t kSmallN = 128;
 constexpr int32_t kSmallR = 1024;
 constexpr int32_t kSmallPanel = 16384;     // panel entries of one supernode
@@ -114,6 +149,11 @@ slr_status host_split_blocks(const int32_t* rowptr, const int32_t* colind, const
                              HostSetup& hs);
 slr_status host_band_factor(HostSetup& hs, int32_t G);
 slr_status host_c_factor(HostSetup& hs, int32_t leaf, int32_t task_rows);
+// Lowest level of the top zone within the entry and multiply-add budgets (nlev: no zone).
+int32_t host_c_top_choose(const CFactorHost& cf);
+// Builds the top zone from level top_lev up (no zone when top_lev >= nlev or
+// when the zone's subtrees are not contiguous in the factor order).
+void host_c_top(CFactorHost& cf, int32_t top_lev);
 // Symmetric eigen-decomposition of the m x m tridiagonal T (Jacobi rotations):
 // eigenvalues descending in lam[m], eigenvectors as columns of Y (column-major m x m).
 void host_tridiag_eig(int32_t m, const double* alpha, const double* beta, double* lam, double* Y);

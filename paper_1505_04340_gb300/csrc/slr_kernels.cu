@@ -4,6 +4,7 @@
 //  K1  band solve      t = B^{-1} f, p independent banded Cholesky solves
 //  K2  coupling SpMVs  g' = g - E^T t,  b = E y
 //  K3  C solves        L^{-1} and L^{-T} with a supernodal, level-scheduled factor
+//                      in unit block form (one dependent step per level)
 //  K4  low rank        w' = w/(1-theta) + U_k (d o U_k^T w)
 //  K5  PCG             A p, dots, axpys, scalar updates (FP64)
 #include <cuda_runtime.h>
@@ -64,17 +65,50 @@ __global__ void k_spmv(int32_t rows, int32_t nrhs, const int32_t* __restrict__ r
 }
 
 // ------------------------------------------------------------------ K3
-// Supernode J owns factor positions [c0[J], c0[J+1]) (n_J of them); its
-// off-diagonal rows R_J carry the row-major panel L[R_J, J] (|R_J| x n_J) and
-// its diagonal block is stored inverted (packed lower, column-major: column j
-// starts at cs(j) = j n_J - j (j-1) / 2).  Levels go leaves -> root.
-// A column task is (J, first, count <= 32); a panel task is (J, first row, count <= 32).
+// Supernode J owns factor positions [c0[J], c0[J+1]) (n_J of them).  Its
+// diagonal block is stored inverted (packed lower, column-major: column j
+// starts at cs(j) = j n_J - j (j-1) / 2) and its off-diagonal rows R_J carry
+// the row-major panel M_J = L[R_J, J] L_JJ^{-1} (|R_J| x n_J): the off-diagonal
+// block of the unit block factor Lhat = L D^{-1}, D = diag(L_JJ).  With
+// L^{-1} = D^{-1} Lhat^{-1} and L^{-T} = Lhat^{-T} D^{-T}:
+//   forward   t_J = g_J - sum of the panel products w that hold J's rows,
+//             then x_J = L_JJ^{-1} t_J and w_J = M_J t_J, both from t_J
+//   backward  x_J = L_JJ^{-T} y_J - M_J^T x_{R_J}
+// so every level (leaves -> root forward, root -> leaves backward) is one
+// dependent step.  A forward task is a block of <= 32 rows of L_JJ^{-1} or of
+// M_J (every task of J gathers all of t_J itself); a backward task is a block
+// of <= 32 columns of J.  Tasks are (J, first, count, 0).
 //
-// Each step is a device function run by one warp or one CTA of NW warps; the
-// per-level kernels below wrap them one launch per step, and the persistent
-// kernels run every level in one cooperative launch with a grid barrier
-// between dependent steps.
+// Levels whose supernodes are many and small run one group of threads per
+// supernode (all its tasks in one group).  The per-level kernels wrap one
+// level in one launch; the persistent kernels run every level in one
+// cooperative launch with a grid barrier between levels.
 __device__ __forceinline__ int64_t packed_col(int j, int n) { return (int64_t)j * n - (int64_t)j * (j - 1) / 2; }
+
+// Plain view of a DevCFactor (device pointers and sizes) passed by value.
+template <typename T>
+struct CView {
+    int32_t s, nlev, nsteps;
+    int64_t nrow;
+    const int32_t *cperm, *c0, *rows, *seg_row, *lev_sn;
+    const int64_t *r_off, *pan_off, *dinv_off, *seg_ptr;
+    const T *panel, *dinv;
+    T* wbuf;
+    const int4 *tasks, *ptasks;
+    const int32_t *lev_task_ptr, *lev_ptask_ptr, *lev_sn_ptr;
+    const uint8_t* lev_small;
+    int64_t red_off;   // persistent kernels: reduction array offset in shared memory (elements)
+    // top zone
+    int32_t nT, tf_parts, tb_parts;
+    const int32_t *tpos, *tseg_row, *tsk_lo, *tp_pos, *tb_cb_part;
+    const int64_t *tseg_ptr, *tsk_off, *tb_off, *tp_off;
+    const T *tsk, *tb;
+    const int4 *tf_rb, *tf_tasks, *tb_cb, *tb_tasks;
+    T *tT, *tf_part, *tb_part;
+    int32_t *tf_cnt, *tb_cnt;
+    unsigned* bar;
+    int32_t* err;
+};
 
 // sum of w[seg_row[e]] for e = e0 .. e1-1, in that order: indices and values are
 // loaded 8 at a time so that the two dependent loads are not paid per term
@@ -95,113 +129,117 @@ __device__ __forceinline__ T gather_sum(const T* w, const int32_t* __restrict__ 
     return acc;
 }
 
-// forward, gather (one warp): t_i = g[cperm[i]] - sum of the panel products w that hold row i
+// t_J = g_J - gathered panel products into ts[0 .. n_J) by NTH threads (thread gt)
 template <typename T>
-__device__ __forceinline__ void cfwd_gather_warp(const int4 tk, int lane, const int32_t* __restrict__ c0,
-                                                 const int32_t* __restrict__ cperm,
-                                                 const int64_t* __restrict__ seg_ptr,
-                                                 const int32_t* __restrict__ seg_row, const T* wbuf, int64_t nrow,
-                                                 const T* g, int64_t ldg, T* tf, int32_t s, int32_t nrhs) {
-    if (lane >= tk.z) return;
-    const int32_t i = c0[tk.x] + tk.y + lane;
-    const int64_t e0 = seg_ptr[i], e1 = seg_ptr[i + 1];
-    for (int j = 0; j < nrhs; ++j) {
-        const T* w = wbuf + (int64_t)j * nrow;
-        tf[i + (int64_t)j * s] = g[cperm[i] + j * ldg] - gather_sum(w, seg_row, e0, e1);
+__device__ __forceinline__ void gather_t(const CView<T>& cf, int J, int gt, int nth, T* ts, const T* g, int64_t ldg,
+                                         int j) {
+    const int32_t a0 = cf.c0[J], nJ = cf.c0[J + 1] - a0;
+    const T* w = cf.wbuf + (int64_t)j * cf.nrow;
+    for (int i = gt; i < nJ; i += nth) {
+        const int32_t pos = a0 + i;
+        ts[i] = g[cf.cperm[pos] + (int64_t)j * ldg] - gather_sum(w, cf.seg_row, cf.seg_ptr[pos], cf.seg_ptr[pos + 1]);
     }
 }
 
-// forward, diagonal (one CTA of NW warps): x_J = L_JJ^{-1} t_J for a block of
-// <= 32 rows; the warps split the reduction over columns (lane = row), 8 loads
-// in flight per lane
+// Forward task (one CTA of NW warps): t_J into ts, then rows tk.y .. tk.y + tk.z - 1
+// of w_J = M_J t_J (panel task: a warp per row, lanes over the columns, 8 loads in
+// flight) or of x_J = L_JJ^{-1} t_J (diagonal task: lane = row, the warps split
+// the columns, partial sums added in a fixed order).
 template <typename T, int NW>
-__device__ void cfwd_diag_cta(const int4 tk, T (*red)[33], const int32_t* __restrict__ c0,
-                              const int64_t* __restrict__ dinv_off, const T* __restrict__ dinv, const T* tf, T* xf,
-                              int32_t s, int32_t nrhs) {
+__device__ void cfwd_task_cta(const CView<T>& cf, const int4 tk, bool pan, T* ts, T (*red)[33], const T* g,
+                              int64_t ldg, T* xf, int32_t nrhs) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int32_t a0 = c0[tk.x], nJ = c0[tk.x + 1] - a0;
-    const int il = tk.y + lane;
-    const int ncol = tk.y + tk.z;                  // columns 0 .. ncol-1 reach these rows
-    const int chunk = (ncol + NW - 1) / NW;
-    const int jb = warp * chunk, je = min(ncol, jb + chunk);
-    const T* D = dinv + dinv_off[tk.x];
+    const int32_t J = tk.x, a0 = cf.c0[J], nJ = cf.c0[J + 1] - a0;
     for (int j = 0; j < nrhs; ++j) {
-        const T* t = tf + a0 + (int64_t)j * s;
-        T acc = T(0);
-        if (lane < tk.z) {
-            const int jend = min(je, il + 1);
-            int jj = jb;
-            for (; jj + 7 < jend; jj += 8) {
-                T d[8], tv[8];
+        gather_t(cf, J, threadIdx.x, NW * 32, ts, g, ldg, j);
+        __syncthreads();
+        if (pan) {
+            const T* P = cf.panel + cf.pan_off[J];
+            for (int pr = warp; pr < tk.z; pr += NW) {
+                const int64_t p = tk.y + pr;
+                const T* Pp = P + p * nJ;
+                T acc = T(0);
+                int c = lane;
+                for (; c + 7 * 32 < nJ; c += 8 * 32) {
+                    T pv[8];
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    d[u] = D[packed_col(jj + u, nJ) + (il - jj - u)];
-                    tv[u] = t[jj + u];
+                    for (int u = 0; u < 8; ++u) pv[u] = Pp[c + 32 * u];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) acc += pv[u] * ts[c + 32 * u];
                 }
-#pragma unroll
-                for (int u = 0; u < 8; ++u) acc += d[u] * tv[u];
+                for (; c < nJ; c += 32) acc += Pp[c] * ts[c];
+                acc = warp_sum(acc);
+                if (lane == 0) cf.wbuf[cf.r_off[J] + p + (int64_t)j * cf.nrow] = acc;
             }
-            for (; jj < jend; ++jj) acc += D[packed_col(jj, nJ) + (il - jj)] * t[jj];
-        }
-        red[warp][lane] = acc;
-        __syncthreads();
-        if (warp == 0) {
-            T v = T(0);
-#pragma unroll 8
-            for (int w = 0; w < NW; ++w) v += red[w][lane];
-            if (lane < tk.z) xf[a0 + il + (int64_t)j * s] = v;
-        }
-        __syncthreads();
-    }
-}
-
-// forward, panel (one CTA): w[r_off[J] + p] = L[R_J[p], J] . x_J (warp per panel
-// row, lanes over columns); x_J staged in shared memory xs[n_J]
-template <typename T, int NW>
-__device__ void cfwd_panel_cta(const int4 tk, T* xs, const int32_t* __restrict__ c0,
-                               const int64_t* __restrict__ r_off, const int64_t* __restrict__ pan_off,
-                               const T* __restrict__ panel, const T* xf, T* wbuf, int64_t nrow, int32_t s,
-                               int32_t nrhs) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int32_t a0 = c0[tk.x], nJ = c0[tk.x + 1] - a0;
-    for (int j = 0; j < nrhs; ++j) {
-        for (int c = threadIdx.x; c < nJ; c += NW * 32) xs[c] = xf[a0 + c + (int64_t)j * s];
-        __syncthreads();
-        for (int pr = warp; pr < tk.z; pr += NW) {
-            const int64_t p = tk.y + pr;
-            const T* P = panel + pan_off[tk.x] + p * nJ;
+        } else {
+            const T* D = cf.dinv + cf.dinv_off[J];
+            const int il = tk.y + lane;
+            const int ncol = tk.y + tk.z;   // columns 0 .. ncol-1 reach these rows
+            const int chunk = (ncol + NW - 1) / NW;
+            const int jb = warp * chunk, je = min(ncol, jb + chunk);
             T acc = T(0);
-            int c = lane;
-            for (; c + 7 * 32 < nJ; c += 8 * 32) {
-                T pv[8];
+            if (lane < tk.z) {
+                const int jend = min(je, il + 1);
+                int jj = jb;
+                for (; jj + 7 < jend; jj += 8) {
+                    T d[8];
 #pragma unroll
-                for (int u = 0; u < 8; ++u) pv[u] = P[c + 32 * u];
+                    for (int u = 0; u < 8; ++u) d[u] = D[packed_col(jj + u, nJ) + (il - jj - u)];
 #pragma unroll
-                for (int u = 0; u < 8; ++u) acc += pv[u] * xs[c + 32 * u];
+                    for (int u = 0; u < 8; ++u) acc += d[u] * ts[jj + u];
+                }
+                for (; jj < jend; ++jj) acc += D[packed_col(jj, nJ) + (il - jj)] * ts[jj];
             }
-            for (; c < nJ; c += 32) acc += P[c] * xs[c];
-            acc = warp_sum(acc);
-            if (lane == 0) wbuf[r_off[tk.x] + p + (int64_t)j * nrow] = acc;
+            red[warp][lane] = acc;
+            __syncthreads();
+            if (warp == 0) {
+                T v = T(0);
+#pragma unroll 8
+                for (int w = 0; w < NW; ++w) v += red[w][lane];
+                if (lane < tk.z) xf[a0 + il + (int64_t)j * cf.s] = v;
+            }
         }
         __syncthreads();
     }
 }
 
-// backward, panel (one CTA): t_j = y_j - sum_p L[R_J[p], j] x[R_J[p]] for <= 32
-// columns (lane = column); the warps split the panel rows, 8 loads in flight
-template <typename T, int NW, int DEPTH = 8>
-__device__ void cbwd_panel_cta(const int4 tk, T (*red)[33], const int32_t* __restrict__ c0,
-                               const int64_t* __restrict__ r_off, const int32_t* __restrict__ rows,
-                               const int64_t* __restrict__ pan_off, const T* __restrict__ panel, T* yf,
-                               const T* xf, int32_t s, int32_t nrhs) {
+// Backward task (one CTA of NW warps): columns c = tk.y .. tk.y + tk.z - 1 of
+// x_J = L_JJ^{-T} y_J - M_J^T x_{R_J}.  The diagonal part runs a warp per column
+// (lanes over column c of L_JJ^{-1}, contiguous in the packed layout); the panel
+// part has lanes over the columns and the warps splitting the panel rows, DEPTH
+// loads in flight per lane.  Optional scatter of the result to DD order.
+template <typename T, int NW, int DEPTH>
+__device__ void cbwd_task_cta(const CView<T>& cf, const int4 tk, T* us, T (*red)[33], const T* yf, T* xf, T* y_dd,
+                              int64_t ldy, int32_t nrhs) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int32_t a0 = c0[tk.x], nJ = c0[tk.x + 1] - a0, jl = tk.y + lane;
-    const int64_t nr = r_off[tk.x + 1] - r_off[tk.x];
-    const int32_t* R = rows + r_off[tk.x];
-    const T* Pn = panel + pan_off[tk.x] + jl;
+    const int32_t J = tk.x, a0 = cf.c0[J], nJ = cf.c0[J + 1] - a0, jl = tk.y + lane;
+    const int64_t nr = cf.r_off[J + 1] - cf.r_off[J];
+    const int32_t* R = cf.rows + cf.r_off[J];
+    const T* Pn = cf.panel + cf.pan_off[J] + jl;
+    const T* D = cf.dinv + cf.dinv_off[J];
     const int64_t chunk = (nr + NW - 1) / NW, pb = warp * chunk, pe = min(nr, pb + chunk);
     for (int j = 0; j < nrhs; ++j) {
-        const T* x = xf + (int64_t)j * s;
+        const T* y = yf + a0 + (int64_t)j * cf.s;
+        const T* x = xf + (int64_t)j * cf.s;
+        for (int cc = warp; cc < tk.z; cc += NW) {
+            const int c = tk.y + cc;
+            const T* Dc = D + packed_col(c, nJ) - c;   // Dc[i] = (L_JJ^{-1})[i, c], i >= c
+            T acc = T(0);
+            int i = c + lane;
+            for (; i + 7 * 32 < nJ; i += 8 * 32) {
+                T d[8], yv[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    d[u] = Dc[i + 32 * u];
+                    yv[u] = y[i + 32 * u];
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) acc += d[u] * yv[u];
+            }
+            for (; i < nJ; i += 32) acc += Dc[i] * y[i];
+            acc = warp_sum(acc);
+            if (lane == 0) us[cc] = acc;
+        }
         T acc = T(0);
         if (lane < tk.z) {
             int64_t p = pb;
@@ -223,45 +261,11 @@ __device__ void cbwd_panel_cta(const int4 tk, T (*red)[33], const int32_t* __res
             T v = T(0);
 #pragma unroll 8
             for (int w = 0; w < NW; ++w) v += red[w][lane];
-            yf[a0 + jl + (int64_t)j * s] -= v;
+            const T r = us[lane] - v;
+            xf[a0 + jl + (int64_t)j * cf.s] = r;
+            if (y_dd) y_dd[cf.cperm[a0 + jl] + (int64_t)j * ldy] = r;
         }
         __syncthreads();
-    }
-}
-
-// backward, diagonal (one CTA): x_J = L_JJ^{-T} t_J (warp per column, lanes over
-// the column, 8 loads in flight per lane), optional scatter to DD order
-template <typename T, int NW>
-__device__ void cbwd_diag_cta(const int4 tk, const int32_t* __restrict__ c0, const int64_t* __restrict__ dinv_off,
-                              const T* __restrict__ dinv, const int32_t* __restrict__ cperm, const T* tf, T* xf,
-                              T* y_dd, int64_t ldy, int32_t s, int32_t nrhs) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int32_t a0 = c0[tk.x], nJ = c0[tk.x + 1] - a0;
-    const T* D = dinv + dinv_off[tk.x];
-    for (int cc = warp; cc < tk.z; cc += NW) {
-        const int jl = tk.y + cc;
-        const T* Dc = D + packed_col(jl, nJ) - jl;
-        for (int j = 0; j < nrhs; ++j) {
-            const T* t = tf + a0 + (int64_t)j * s;
-            T acc = T(0);
-            int i = jl + lane;
-            for (; i + 7 * 32 < nJ; i += 8 * 32) {
-                T d[8], tv[8];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    d[u] = Dc[i + 32 * u];
-                    tv[u] = t[i + 32 * u];
-                }
-#pragma unroll
-                for (int u = 0; u < 8; ++u) acc += d[u] * tv[u];
-            }
-            for (; i < nJ; i += 32) acc += Dc[i] * t[i];
-            acc = warp_sum(acc);
-            if (lane == 0) {
-                xf[a0 + jl + (int64_t)j * s] = acc;
-                if (y_dd) y_dd[cperm[a0 + jl] + j * ldy] = acc;
-            }
-        }
     }
 }
 
@@ -277,217 +281,303 @@ __device__ __forceinline__ void group_sync() {
 }
 
 // Fused levels: one group of NT threads (a CTA, or a part of one) per supernode J
-// with n_J <= kSmallN and |R_J| <= kSmallR.
-// forward: t_J = g_J - (gathered panel products); x_J = L_JJ^{-1} t_J; w_J = L[R_J, J] x_J
+// with n_J <= kSmallN and |R_J| <= kSmallR.  Both directions use the stacked
+// matrix A_J = [L_JJ^{-1}; M_J] ((n_J + |R_J|) x n_J; row r < n_J of the
+// diagonal block is read from the packed column-major layout).
+// forward: t_J gathered into ts; [x_J; w_J] = A_J t_J with a warp per row of A_J
+// (lanes over the columns, four rows in flight per warp)
 template <typename T, int NT, int GROUPS>
-__device__ void cfwd_small_cta(int J, T* ts, T* xs, const int32_t* __restrict__ c0,
-                               const int32_t* __restrict__ cperm, const int64_t* __restrict__ seg_ptr,
-                               const int32_t* __restrict__ seg_row, const int64_t* __restrict__ r_off,
-                               const int64_t* __restrict__ pan_off, const T* __restrict__ panel,
-                               const int64_t* __restrict__ dinv_off, const T* __restrict__ dinv, T* wbuf,
-                               int64_t nrow, const T* g, int64_t ldg, T* xf, int32_t s, int32_t nrhs) {
+__device__ void cfwd_small_cta(const CView<T>& cf, int J, T* ts, const T* g, int64_t ldg, T* xf, int32_t nrhs) {
     constexpr int nw = NT / 32;
     const int gt = threadIdx.x % NT, lane = gt & 31, warp = gt >> 5;
-    const int32_t a0 = c0[J], nJ = c0[J + 1] - a0;
-    const int64_t nr = r_off[J + 1] - r_off[J];
-    const T* D = dinv + dinv_off[J];
-    const T* Pn = panel + pan_off[J];
+    const int32_t a0 = cf.c0[J], nJ = cf.c0[J + 1] - a0;
+    const int64_t nr = cf.r_off[J + 1] - cf.r_off[J], rtot = nJ + nr;
+    const T* D = cf.dinv + cf.dinv_off[J];
+    const T* Pn = cf.panel + cf.pan_off[J];
     for (int j = 0; j < nrhs; ++j) {
-        const T* w = wbuf + (int64_t)j * nrow;
-        for (int i = gt; i < nJ; i += NT) {
-            const int32_t pos = a0 + i;
-            ts[i] = g[cperm[pos] + j * ldg] - gather_sum(w, seg_row, seg_ptr[pos], seg_ptr[pos + 1]);
-        }
+        gather_t(cf, J, gt, NT, ts, g, ldg, j);
         group_sync<NT, GROUPS>();
-        for (int i = gt; i < nJ; i += NT) {
-            T acc = T(0);
-            int jj = 0;
-            for (; jj + 7 <= i; jj += 8) {
-                T d[8];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) d[u] = D[packed_col(jj + u, nJ) + (i - jj - u)];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) acc += d[u] * ts[jj + u];
-            }
-            for (; jj <= i; ++jj) acc += D[packed_col(jj, nJ) + (i - jj)] * ts[jj];
-            xs[i] = acc;
-            xf[a0 + i + (int64_t)j * s] = acc;
-        }
-        group_sync<NT, GROUPS>();
-        // four panel rows per warp at a time: their loads are in flight together
-        for (int64_t p0 = 4 * warp; p0 < nr; p0 += 4 * nw) {
+        for (int64_t r0 = 4 * warp; r0 < rtot; r0 += 4 * nw) {
             T acc[4] = {T(0), T(0), T(0), T(0)};
             for (int c = lane; c < nJ; c += 32) {
-                const T xv = xs[c];
+                const T tv = ts[c];
 #pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    if (p0 + u < nr) acc[u] += Pn[(p0 + u) * nJ + c] * xv;
+                for (int u = 0; u < 4; ++u) {
+                    const int64_t r = r0 + u;
+                    T a = T(0);
+                    if (r < nJ) {
+                        if (c <= r) a = D[packed_col(c, nJ) + (r - c)];
+                    } else if (r < rtot) {
+                        a = Pn[(r - nJ) * nJ + c];
+                    }
+                    acc[u] += a * tv;
+                }
             }
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
                 const T v = warp_sum(acc[u]);
-                if (lane == 0 && p0 + u < nr) wbuf[r_off[J] + p0 + u + (int64_t)j * nrow] = v;
+                const int64_t r = r0 + u;
+                if (lane == 0 && r < rtot) {
+                    if (r < nJ) xf[a0 + r + (int64_t)j * cf.s] = v;
+                    else cf.wbuf[cf.r_off[J] + (r - nJ) + (int64_t)j * cf.nrow] = v;
+                }
             }
         }
         group_sync<NT, GROUPS>();
     }
 }
 
-// backward: t_J = y_J - L[R_J, J]^T x_{R_J};  x_J = L_JJ^{-T} t_J (and scatter to DD order).
-// NT / kSmallN threads share each column, each over a part of the panel rows.
+// backward: x_J = A_J^T [y_J; -x_{R_J}] (and scatter to DD order).  The vector is
+// staged in vs; the columns, padded to a power of two P >= n_J, take P threads
+// each of the NT / P parts, and part q sums its share of the rows of A_J; the
+// parts' partial sums (in red) are added in a fixed order.
 template <typename T, int NT, int GROUPS>
-__device__ void cbwd_small_cta(int J, T* xr, T* ts, T* red, const int32_t* __restrict__ c0,
-                               const int64_t* __restrict__ r_off, const int32_t* __restrict__ rows,
-                               const int64_t* __restrict__ pan_off, const T* __restrict__ panel,
-                               const int64_t* __restrict__ dinv_off, const T* __restrict__ dinv,
-                               const int32_t* __restrict__ cperm, const T* yf, T* xf, T* y_dd, int64_t ldy,
-                               int32_t s, int32_t nrhs) {
-    static_assert(NT % kSmallN == 0, "whole threads per column");
-    constexpr int nw = NT / 32, parts = NT / kSmallN;
-    const int gt = threadIdx.x % NT, lane = gt & 31, warp = gt >> 5;
-    const int32_t a0 = c0[J], nJ = c0[J + 1] - a0;
-    const int64_t nr = r_off[J + 1] - r_off[J];
-    const int32_t* R = rows + r_off[J];
-    const T* D = dinv + dinv_off[J];
-    const T* Pn = panel + pan_off[J];
+__device__ void cbwd_small_cta(const CView<T>& cf, int J, T* vs, T* red, const T* yf, T* xf, T* y_dd, int64_t ldy,
+                               int32_t nrhs) {
+    static_assert(NT % kSmallN == 0 && NT <= 1024, "whole parts per column");
+    const int gt = threadIdx.x % NT;
+    const int32_t a0 = cf.c0[J], nJ = cf.c0[J + 1] - a0;
+    const int64_t nr = cf.r_off[J + 1] - cf.r_off[J], rtot = nJ + nr;
+    const int32_t* R = cf.rows + cf.r_off[J];
+    const T* D = cf.dinv + cf.dinv_off[J];
+    const T* Pn = cf.panel + cf.pan_off[J];
+    int P = 32;
+    while (P < nJ) P *= 2;
+    const int parts = NT / P, part = gt / P, c = gt % P;
+    const int64_t len = (rtot + parts - 1) / parts, rb = part * len, re = min(rtot, rb + len);
     for (int j = 0; j < nrhs; ++j) {
-        const T* x = xf + (int64_t)j * s;
-        for (int64_t p = gt; p < nr; p += NT) xr[p] = x[R[p]];
+        const T* x = xf + (int64_t)j * cf.s;
+        const T* y = yf + a0 + (int64_t)j * cf.s;
+        for (int64_t r = gt; r < rtot; r += NT) vs[r] = r < nJ ? y[r] : -x[R[r - nJ]];
         group_sync<NT, GROUPS>();
-        {
-            const int part = gt / kSmallN, c = gt % kSmallN;
-            T acc = T(0);
-            if (c < nJ) {
-                const int64_t len = (nr + parts - 1) / parts, pb = part * len, pe = min(nr, pb + len);
-                int64_t p = pb;
-                for (; p + 7 < pe; p += 8) {
-                    T pv[8];
+        T acc = T(0);
+        if (c < nJ) {
+            // rows of the diagonal block: (L_JJ^{-1})[r, c] for r >= c
+            const T* Dc = D + packed_col(c, nJ) - c;
+            const int64_t de = min(re, (int64_t)nJ);
+            int64_t r = max(rb, (int64_t)c);
+            for (; r + 7 < de; r += 8) {
+                T a[8];
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) pv[u] = Pn[(p + u) * nJ + c];
+                for (int u = 0; u < 8; ++u) a[u] = Dc[r + u];
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) acc += pv[u] * xr[p + u];
-                }
-                for (; p < pe; ++p) acc += Pn[p * nJ + c] * xr[p];
+                for (int u = 0; u < 8; ++u) acc += a[u] * vs[r + u];
             }
-            red[part * kSmallN + c] = acc;
+            for (; r < de; ++r) acc += Dc[r] * vs[r];
+            // rows of the panel: M_J[r - n_J, c]
+            r = max(rb, (int64_t)nJ);
+            for (; r + 7 < re; r += 8) {
+                T a[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) a[u] = Pn[(r + u - nJ) * nJ + c];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) acc += a[u] * vs[r + u];
+            }
+            for (; r < re; ++r) acc += Pn[(r - nJ) * nJ + c] * vs[r];
+        }
+        red[gt] = acc;
+        group_sync<NT, GROUPS>();
+        for (int cc = gt; cc < nJ; cc += NT) {
+            T v = T(0);
+            for (int q = 0; q < parts; ++q) v += red[q * P + cc];
+            xf[a0 + cc + (int64_t)j * cf.s] = v;
+            if (y_dd) y_dd[cf.cperm[a0 + cc] + (int64_t)j * ldy] = v;
         }
         group_sync<NT, GROUPS>();
-        for (int c = gt; c < nJ; c += NT) {
+    }
+}
+
+constexpr int kSmallT = 256;                  // threads per supernode group of the fused levels
+
+// ---- per-level kernels: one launch per level, NW warps per CTA (8 when the
+// level has more tasks than there are SMs, so that several CTAs share an SM;
+// 32 for the few wide tasks near the root)
+// forward: CTA q runs panel task q (q < np) or diagonal task q - np of the level
+template <typename T, int NW>
+__global__ void __launch_bounds__(NW * 32, NW == 8 ? 4 : 1)
+k_cfwd_level(const CView<T> cf, int32_t t0, int32_t p0, int32_t np, const T* g, int64_t ldg, T* xf, int32_t nrhs) {
+    extern __shared__ __align__(16) unsigned char csm[];
+    __shared__ T red[NW][33];
+    const int q = blockIdx.x;
+    const bool pan = q < np;
+    cfwd_task_cta<T, NW>(cf, pan ? cf.ptasks[p0 + q] : cf.tasks[t0 + q - np], pan, reinterpret_cast<T*>(csm), red, g,
+                         ldg, xf, nrhs);
+}
+
+// backward: one CTA per column task, 16 (FP32) or 8 (FP64) panel loads in flight per lane
+template <typename T, int NW>
+__global__ void __launch_bounds__(NW * 32, NW == 8 ? 4 : 1)
+k_cbwd_level(const CView<T> cf, int32_t t0, const T* yf, T* xf, T* y_dd, int64_t ldy, int32_t nrhs) {
+    __shared__ T red[NW][33];
+    __shared__ T us[32];
+    cbwd_task_cta<T, NW, sizeof(T) == 4 ? 16 : 8>(cf, cf.tasks[t0 + blockIdx.x], us, red, yf, xf, y_dd, ldy, nrhs);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_cfwd_small(const CView<T> cf, int32_t s0, const T* g, int64_t ldg, T* xf, int32_t nrhs) {
+    __shared__ T ts[kSmallN];
+    cfwd_small_cta<T, kThreads, 1>(cf, cf.lev_sn[s0 + blockIdx.x], ts, g, ldg, xf, nrhs);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_cbwd_small(const CView<T> cf, int32_t s0, const T* yf, T* xf, T* y_dd, int64_t ldy, int32_t nrhs) {
+    __shared__ T vs[kSmallN + kSmallR], red[kThreads];
+    cbwd_small_cta<T, kThreads, 1>(cf, cf.lev_sn[s0 + blockIdx.x], vs, red, yf, xf, y_dd, ldy, nrhs);
+}
+
+
+// ---- top zone: x_T = L_TT^{-1} t_T and y_T = L_TT^{-T} x_T with the explicit inverse
+// (local index la of the zone's positions; tpos maps it to the factor order)
+constexpr int kTopT = 256;   // threads of the zone kernels (8 warps)
+
+// t_T = g_T - (panel products of the supernodes below the zone), one thread per (la, j)
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_ctop_gather(const CView<T> cf, const T* g, int64_t ldg, int32_t nrhs) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)cf.nT * nrhs) return;
+    const int32_t la = (int32_t)(i % cf.nT), j = (int32_t)(i / cf.nT);
+    cf.tT[i] = g[cf.cperm[cf.tpos[la]] + (int64_t)j * ldg] -
+               gather_sum(cf.wbuf + (int64_t)j * cf.nrow, cf.tseg_row, cf.tseg_ptr[la], cf.tseg_ptr[la + 1]);
+}
+
+// Adds the chunks' partial sums of a block once all its tasks have stored theirs:
+// every task fences its stores and counts itself in; the last one to arrive reads
+// the partials (in chunk order, so the sum does not depend on the arrival order),
+// calls out(r, j, sum) and clears the counter for the next solve.
+template <typename T, typename Out>
+__device__ __forceinline__ void last_task_sum(int32_t* cnt, int nch, const T* part, int64_t pstride, int count,
+                                              int32_t nrhs, Out out) {
+    __shared__ int last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(cnt, 1) == nch - 1;
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (int i = threadIdx.x; i < count * nrhs; i += blockDim.x) {
+        const int r = i % count, j = i / count;
+        const T* pj = part + (int64_t)j * pstride + r;
+        T v = T(0);
+        for (int k = 0; k < nch; ++k) v += __ldcg(pj + (int64_t)k * 32);
+        out(r, j, v);
+    }
+    if (threadIdx.x == 0) *cnt = 0;
+}
+
+// forward task (row block rb, columns [cb, ce), chunk k): partial sums of rows
+// r0 .. r0 + count - 1 of L_TT^{-1} t_T over the chunk; a warp takes rows
+// w, w + 8, w + 16, w + 24 (four in flight), lanes over the columns
+template <typename T>
+__global__ void __launch_bounds__(kTopT)
+k_ctop_fwd(const CView<T> cf, T* xf, int32_t nrhs) {
+    __shared__ T ts[kTopCW];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int4 tk = cf.tf_tasks[blockIdx.x];
+    const int4 rb = cf.tf_rb[tk.x];
+    int64_t off[4];
+    int la[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int r = warp + 8 * u;
+        la[u] = r < rb.y ? rb.x + r : -1;
+        off[u] = r < rb.y ? cf.tsk_off[la[u]] - cf.tsk_lo[la[u]] : 0;
+    }
+    for (int j = 0; j < nrhs; ++j) {
+        const T* t = cf.tT + (int64_t)j * cf.nT;
+        for (int c = tk.y + threadIdx.x; c < tk.z; c += kTopT) ts[c - tk.y] = t[c];
+        __syncthreads();
+        T acc[4] = {T(0), T(0), T(0), T(0)};
+        int c = tk.y + lane;
+        // sixteen loads in flight per lane (four rows x four columns); entries right
+        // of a row's diagonal, and rows past the block, load nothing
+        for (; c + 96 < tk.z; c += 128) {
+            T a[4][4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) a[u][q] = c + 32 * q <= la[u] ? cf.tsk[off[u] + c + 32 * q] : T(0);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const T tv = ts[c + 32 * q - tk.y];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) acc[u] += a[u][q] * tv;
+            }
+        }
+        for (; c < tk.z; c += 32) {
+            const T tv = ts[c - tk.y];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (c <= la[u]) acc[u] += cf.tsk[off[u] + c] * tv;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const T v = warp_sum(acc[u]);
+            if (lane == 0 && la[u] >= 0)
+                cf.tf_part[(int64_t)j * cf.tf_parts + rb.w + tk.w * 32 + warp + 8 * u] = v;
+        }
+        __syncthreads();
+    }
+    last_task_sum(cf.tf_cnt + tk.x, rb.z, cf.tf_part + rb.w, cf.tf_parts, rb.y, nrhs,
+                  [&](int r, int j, T v) { xf[cf.tpos[rb.x + r] + (int64_t)j * cf.s] = v; });
+}
+
+// backward task (column block cb of J, path rows [r0, r1), chunk k): partial sums of
+// columns c0 .. c0 + count - 1 of X_J^T x over the chunk (lanes over the columns,
+// the warps split the rows, 16 (FP32) or 8 (FP64) loads in flight); the chunk's x
+// values are staged in shared memory
+template <typename T>
+__global__ void __launch_bounds__(kTopT)
+k_ctop_bwd(const CView<T> cf, const T* yf, T* xf, T* y_dd, int64_t ldy, int32_t nrhs) {
+    constexpr int NW = kTopT / 32, DEPTH = sizeof(T) == 4 ? 16 : 8;
+    __shared__ T xs[kTopRCH];
+    __shared__ T red[NW][33];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int4 tk = cf.tb_tasks[blockIdx.x];
+    const int4 cb = cf.tb_cb[tk.x];
+    const int32_t J = cb.x, nJ = cf.c0[J + 1] - cf.c0[J], pofs = cf.tb_cb_part[tk.x];
+    const T* X = cf.tb + cf.tb_off[J] + cb.y + lane;
+    const int32_t* pp = cf.tp_pos + cf.tp_off[J];
+    const int nrw = tk.z - tk.y, per = (nrw + NW - 1) / NW;
+    const int rb = tk.y + warp * per, re = min(tk.z, rb + per);
+    for (int j = 0; j < nrhs; ++j) {
+        for (int r = tk.y + threadIdx.x; r < tk.z; r += kTopT) xs[r - tk.y] = yf[pp[r] + (int64_t)j * cf.s];
+        __syncthreads();
+        T acc = T(0);
+        if (lane < cb.z) {
+            int r = rb;
+            for (; r + DEPTH - 1 < re; r += DEPTH) {
+                T a[DEPTH];
+#pragma unroll
+                for (int u = 0; u < DEPTH; ++u) a[u] = X[(int64_t)(r + u) * nJ];
+#pragma unroll
+                for (int u = 0; u < DEPTH; ++u) acc += a[u] * xs[r + u - tk.y];
+            }
+            for (; r < re; ++r) acc += X[(int64_t)r * nJ] * xs[r - tk.y];
+        }
+        red[warp][lane] = acc;
+        __syncthreads();
+        if (warp == 0 && lane < cb.z) {
             T v = T(0);
 #pragma unroll
-            for (int q = 0; q < parts; ++q) v += red[q * kSmallN + c];
-            ts[c] = yf[a0 + c + (int64_t)j * s] - v;
+            for (int w = 0; w < NW; ++w) v += red[w][lane];
+            cf.tb_part[(int64_t)j * cf.tb_parts + pofs + tk.w * 32 + lane] = v;
         }
-        group_sync<NT, GROUPS>();
-        for (int c = warp; c < nJ; c += nw) {
-            const T* Dc = D + packed_col(c, nJ) - c;
-            T acc = T(0);
-            for (int i = c + lane; i < nJ; i += 32) acc += Dc[i] * ts[i];
-            acc = warp_sum(acc);
-            if (lane == 0) {
-                xf[a0 + c + (int64_t)j * s] = acc;
-                if (y_dd) y_dd[cperm[a0 + c] + j * ldy] = acc;
-            }
-        }
-        group_sync<NT, GROUPS>();
+        __syncthreads();
     }
-}
-
-constexpr int kDiagT = 1024;   // threads of the per-level diagonal-block kernels (32 warps)
-constexpr int kPanT = 512;     // threads of the per-level forward panel kernels (16 warps)
-constexpr int kBPanT = 1024;   // threads of the per-level backward panel kernels (32 warps)
-
-// ---- per-level kernels: one launch per step
-template <typename T>
-__global__ void __launch_bounds__(32)
-k_cfwd_gather(const int4* __restrict__ tasks, const int32_t* __restrict__ c0, const int32_t* __restrict__ cperm,
-              const int64_t* __restrict__ seg_ptr, const int32_t* __restrict__ seg_row, const T* wbuf,
-              int64_t nrow, const T* g, int64_t ldg, T* tf, int32_t s, int32_t nrhs) {
-    cfwd_gather_warp<T>(tasks[blockIdx.x], threadIdx.x, c0, cperm, seg_ptr, seg_row, wbuf, nrow, g, ldg, tf, s, nrhs);
-}
-
-template <typename T>
-__global__ void __launch_bounds__(kDiagT)
-k_cfwd_diag(const int4* __restrict__ tasks, const int32_t* __restrict__ c0, const int64_t* __restrict__ dinv_off,
-            const T* __restrict__ dinv, const T* tf, T* xf, int32_t s, int32_t nrhs) {
-    __shared__ T red[kDiagT / 32][33];
-    cfwd_diag_cta<T, kDiagT / 32>(tasks[blockIdx.x], red, c0, dinv_off, dinv, tf, xf, s, nrhs);
-}
-
-template <typename T>
-__global__ void __launch_bounds__(kPanT)
-k_cfwd_panel(const int4* __restrict__ ptasks, const int32_t* __restrict__ c0, const int64_t* __restrict__ r_off,
-             const int64_t* __restrict__ pan_off, const T* __restrict__ panel, const T* xf, T* wbuf, int64_t nrow,
-             int32_t s, int32_t nrhs) {
-    extern __shared__ unsigned char csm[];
-    cfwd_panel_cta<T, kPanT / 32>(ptasks[blockIdx.x], reinterpret_cast<T*>(csm), c0, r_off, pan_off, panel, xf,
-                                  wbuf, nrow, s, nrhs);
-}
-
-// one CTA of 32 warps per 32-column task, 16 (FP32) or 8 (FP64) panel loads in flight per lane
-template <typename T>
-__global__ void __launch_bounds__(kBPanT)
-k_cbwd_panel(const int4* __restrict__ tasks, const int32_t* __restrict__ c0, const int64_t* __restrict__ r_off,
-             const int32_t* __restrict__ rows, const int64_t* __restrict__ pan_off, const T* __restrict__ panel,
-             T* yf, const T* xf, int32_t s, int32_t nrhs) {
-    __shared__ T red[kBPanT / 32][33];
-    cbwd_panel_cta<T, kBPanT / 32, sizeof(T) == 4 ? 16 : 8>(tasks[blockIdx.x], red, c0, r_off, rows, pan_off, panel,
-                                                            yf, xf, s, nrhs);
-}
-
-template <typename T>
-__global__ void __launch_bounds__(kDiagT)
-k_cbwd_diag(const int4* __restrict__ tasks, const int32_t* __restrict__ c0, const int64_t* __restrict__ dinv_off,
-            const T* __restrict__ dinv, const int32_t* __restrict__ cperm, const T* tf, T* xf, T* y_dd,
-            int64_t ldy, int32_t s, int32_t nrhs) {
-    cbwd_diag_cta<T, kDiagT / 32>(tasks[blockIdx.x], c0, dinv_off, dinv, cperm, tf, xf, y_dd, ldy, s, nrhs);
-}
-
-template <typename T>
-__global__ void __launch_bounds__(kThreads)
-k_cfwd_small(const int32_t* __restrict__ sns, const int32_t* __restrict__ c0, const int32_t* __restrict__ cperm,
-             const int64_t* __restrict__ seg_ptr, const int32_t* __restrict__ seg_row, const int64_t* __restrict__ r_off,
-             const int64_t* __restrict__ pan_off, const T* __restrict__ panel, const int64_t* __restrict__ dinv_off,
-             const T* __restrict__ dinv, T* wbuf, int64_t nrow, const T* g, int64_t ldg, T* xf, int32_t s,
-             int32_t nrhs) {
-    __shared__ T ts[kSmallN], xs[kSmallN];
-    cfwd_small_cta<T, kThreads, 1>(sns[blockIdx.x], ts, xs, c0, cperm, seg_ptr, seg_row, r_off, pan_off, panel,
-                                dinv_off, dinv, wbuf, nrow, g, ldg, xf, s, nrhs);
-}
-
-template <typename T>
-__global__ void __launch_bounds__(kThreads)
-k_cbwd_small(const int32_t* __restrict__ sns, const int32_t* __restrict__ c0, const int64_t* __restrict__ r_off,
-             const int32_t* __restrict__ rows, const int64_t* __restrict__ pan_off, const T* __restrict__ panel,
-             const int64_t* __restrict__ dinv_off, const T* __restrict__ dinv, const int32_t* __restrict__ cperm,
-             const T* yf, T* xf, T* y_dd, int64_t ldy, int32_t s, int32_t nrhs) {
-    __shared__ T xr[kSmallR], ts[kSmallN];
-    __shared__ T red[(kThreads / kSmallN) * kSmallN];
-    cbwd_small_cta<T, kThreads, 1>(sns[blockIdx.x], xr, ts, red, c0, r_off, rows, pan_off, panel, dinv_off, dinv, cperm,
-                                yf, xf, y_dd, ldy, s, nrhs);
+    const int32_t a0 = cf.c0[J] + cb.y;
+    last_task_sum(cf.tb_cnt + tk.x, cb.w, cf.tb_part + pofs, cf.tb_parts, cb.z, nrhs, [&](int c, int j, T v) {
+        xf[a0 + c + (int64_t)j * cf.s] = v;
+        if (y_dd) y_dd[cf.cperm[a0 + c] + (int64_t)j * ldy] = v;
+    });
 }
 
 // ---- persistent kernels: every level in one cooperative launch
-// Plain view of a DevCFactor (device pointers and sizes) passed by value.
-template <typename T>
-struct CView {
-    int32_t s, nlev, nsteps;
-    int64_t nrow;
-    const int32_t *cperm, *c0, *rows, *seg_row, *lev_sn;
-    const int64_t *r_off, *pan_off, *dinv_off, *seg_ptr;
-    const T *panel, *dinv;
-    T* wbuf;
-    const int4 *tasks, *ptasks;
-    const int32_t *lev_task_ptr, *lev_ptask_ptr, *lev_sn_ptr;
-    const uint8_t* lev_small;
-    unsigned* bar;
-    int32_t* err;
-};
-
 constexpr int kPersT = 1024;                  // 32 warps, one CTA per SM
 constexpr int kPersW = kPersT / 32;
-constexpr int kSmallT = 256;                  // fused levels: 4 groups of 256 threads, a supernode each
-constexpr int kSmallG = kPersT / kSmallT;
+constexpr int kSmallG = kPersT / kSmallT;     // fused levels: 4 groups of 256 threads, a supernode each
 constexpr long long kGridSpin = 1ll << 22;    // bounded barrier wait (x 64 ns sleep: about a quarter second)
 
 // All CTAs arrive; the counter (zeroed before the launch) reaches target =
@@ -512,93 +602,71 @@ __device__ __forceinline__ void grid_barrier(unsigned* bar, unsigned target, int
     __syncthreads();
 }
 
-// shared bytes of the persistent kernels: the larger of the forward panel's
-// x_J (max_n values), the fused levels' buffers and the reduction arrays
+// Shared memory of the persistent kernels (elements): t_J plus the reduction
+// array of a forward task, or the fused levels' buffers, whichever is larger.
+// The reduction array starts at a multiple of 32 elements.
+inline int64_t pers_red_off(int32_t max_n) { return ((int64_t)max_n + 31) / 32 * 32; }
 inline size_t pers_smem_bytes(int32_t max_n, size_t elem) {
-    const size_t small_fwd = kSmallG * 2 * kSmallN,
-                 small_bwd = kSmallG * (kSmallR + kSmallN + (kSmallT / kSmallN) * kSmallN);
-    const size_t red = kPersW * 33;
-    return std::max({(size_t)max_n, small_fwd, small_bwd, red}) * elem;
+    const int64_t task = pers_red_off(max_n) + kPersW * 33 + 32;
+    const int64_t small_fwd = kSmallG * kSmallN, small_bwd = kSmallG * (kSmallN + kSmallR + kSmallT);
+    return (size_t)std::max({task, small_fwd, small_bwd}) * elem;
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kPersT, 1)
-k_cfwd_persistent(const CView<T> cf, const T* g, int64_t ldg, T* tf, T* xf, int32_t nrhs) {
+k_cfwd_persistent(const CView<T> cf, const T* g, int64_t ldg, T* xf, int32_t nrhs) {
     extern __shared__ __align__(16) unsigned char psm[];
     T* sm = reinterpret_cast<T*>(psm);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    T(*red)[33] = reinterpret_cast<T(*)[33]>(sm + cf.red_off);
     unsigned round = 0;
     int steps_left = cf.nsteps;
-    auto sync = [&]() {
-        if (--steps_left > 0) grid_barrier(cf.bar, ++round * gridDim.x, cf.err);
-    };
     for (int l = 0; l < cf.nlev; ++l) {
+        bool any;
         if (cf.lev_small[l]) {
             const int s0 = cf.lev_sn_ptr[l], ns = cf.lev_sn_ptr[l + 1] - s0;
-            if (ns == 0) continue;
+            any = ns > 0;
             const int grp = threadIdx.x / kSmallT;
-            T* gs = sm + grp * 2 * kSmallN;
             for (int q = blockIdx.x * kSmallG + grp; q < ns; q += gridDim.x * kSmallG)
-                cfwd_small_cta<T, kSmallT, kSmallG>(cf.lev_sn[s0 + q], gs, gs + kSmallN, cf.c0, cf.cperm, cf.seg_ptr,
-                                          cf.seg_row, cf.r_off, cf.pan_off, cf.panel, cf.dinv_off, cf.dinv, cf.wbuf,
-                                          cf.nrow, g, ldg, xf, cf.s, nrhs);
-            sync();
-            continue;
+                cfwd_small_cta<T, kSmallT, kSmallG>(cf, cf.lev_sn[s0 + q], sm + grp * kSmallN, g, ldg, xf, nrhs);
+        } else {
+            const int t0 = cf.lev_task_ptr[l], nt = cf.lev_task_ptr[l + 1] - t0;
+            const int p0 = cf.lev_ptask_ptr[l], np = cf.lev_ptask_ptr[l + 1] - p0;
+            any = nt + np > 0;
+            for (int q = blockIdx.x; q < np + nt; q += gridDim.x) {
+                const bool pan = q < np;
+                cfwd_task_cta<T, kPersW>(cf, pan ? cf.ptasks[p0 + q] : cf.tasks[t0 + q - np], pan, sm, red, g, ldg,
+                                         xf, nrhs);
+            }
         }
-        const int t0 = cf.lev_task_ptr[l], nt = cf.lev_task_ptr[l + 1] - t0;
-        const int p0 = cf.lev_ptask_ptr[l], np = cf.lev_ptask_ptr[l + 1] - p0;
-        if (nt > 0) {
-            for (int q = blockIdx.x * kPersW + warp; q < nt; q += gridDim.x * kPersW)
-                cfwd_gather_warp<T>(cf.tasks[t0 + q], lane, cf.c0, cf.cperm, cf.seg_ptr, cf.seg_row, cf.wbuf,
-                                    cf.nrow, g, ldg, tf, cf.s, nrhs);
-            sync();
-            for (int q = blockIdx.x; q < nt; q += gridDim.x)
-                cfwd_diag_cta<T, kPersW>(cf.tasks[t0 + q], reinterpret_cast<T(*)[33]>(sm), cf.c0, cf.dinv_off,
-                                         cf.dinv, tf, xf, cf.s, nrhs);
-            sync();
-        }
-        if (np > 0) {
-            for (int q = blockIdx.x; q < np; q += gridDim.x)
-                cfwd_panel_cta<T, kPersW>(cf.ptasks[p0 + q], sm, cf.c0, cf.r_off, cf.pan_off, cf.panel, xf, cf.wbuf,
-                                          cf.nrow, cf.s, nrhs);
-            sync();
-        }
+        if (any && --steps_left > 0) grid_barrier(cf.bar, ++round * gridDim.x, cf.err);
     }
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kPersT, 1)
-k_cbwd_persistent(const CView<T> cf, T* yf, T* xf, T* y_dd, int64_t ldy, int32_t nrhs) {
+k_cbwd_persistent(const CView<T> cf, const T* yf, T* xf, T* y_dd, int64_t ldy, int32_t nrhs) {
     extern __shared__ __align__(16) unsigned char psm[];
     T* sm = reinterpret_cast<T*>(psm);
+    T(*red)[33] = reinterpret_cast<T(*)[33]>(sm + cf.red_off);
     unsigned round = 0;
     int steps_left = cf.nsteps;
-    auto sync = [&]() {
-        if (--steps_left > 0) grid_barrier(cf.bar, ++round * gridDim.x, cf.err);
-    };
     for (int l = cf.nlev - 1; l >= 0; --l) {
+        bool any;
         if (cf.lev_small[l]) {
             const int s0 = cf.lev_sn_ptr[l], ns = cf.lev_sn_ptr[l + 1] - s0;
-            if (ns == 0) continue;
+            any = ns > 0;
             const int grp = threadIdx.x / kSmallT;
-            T* gs = sm + grp * (kSmallR + kSmallN + (kSmallT / kSmallN) * kSmallN);
+            T* gs = sm + grp * (kSmallN + kSmallR + kSmallT);
             for (int q = blockIdx.x * kSmallG + grp; q < ns; q += gridDim.x * kSmallG)
-                cbwd_small_cta<T, kSmallT, kSmallG>(cf.lev_sn[s0 + q], gs, gs + kSmallR, gs + kSmallR + kSmallN, cf.c0,
-                                          cf.r_off, cf.rows, cf.pan_off, cf.panel, cf.dinv_off, cf.dinv, cf.cperm,
-                                          yf, xf, y_dd, ldy, cf.s, nrhs);
-            sync();
-            continue;
+                cbwd_small_cta<T, kSmallT, kSmallG>(cf, cf.lev_sn[s0 + q], gs, gs + kSmallN + kSmallR, yf, xf, y_dd,
+                                                    ldy, nrhs);
+        } else {
+            const int t0 = cf.lev_task_ptr[l], nt = cf.lev_task_ptr[l + 1] - t0;
+            any = nt > 0;
+            for (int q = blockIdx.x; q < nt; q += gridDim.x)
+                cbwd_task_cta<T, kPersW, 8>(cf, cf.tasks[t0 + q], sm, red, yf, xf, y_dd, ldy, nrhs);
         }
-        const int t0 = cf.lev_task_ptr[l], nt = cf.lev_task_ptr[l + 1] - t0;
-        if (nt == 0) continue;
-        for (int q = blockIdx.x; q < nt; q += gridDim.x)
-            cbwd_panel_cta<T, kPersW>(cf.tasks[t0 + q], reinterpret_cast<T(*)[33]>(sm), cf.c0, cf.r_off, cf.rows,
-                                      cf.pan_off, cf.panel, yf, xf, cf.s, nrhs);
-        sync();
-        for (int q = blockIdx.x; q < nt; q += gridDim.x)
-            cbwd_diag_cta<T, kPersW>(cf.tasks[t0 + q], cf.c0, cf.dinv_off, cf.dinv, cf.cperm, yf, xf, y_dd, ldy,
-                                     cf.s, nrhs);
-        sync();
+        if (any && --steps_left > 0) grid_barrier(cf.bar, ++round * gridDim.x, cf.err);
     }
 }
 
@@ -869,7 +937,7 @@ template <typename T>
 CView<T> make_view(const DevCFactor<T>& cf, int32_t nsteps) {
     CView<T> v;
     v.s = cf.s;
-    v.nlev = cf.nlev;
+    v.nlev = cf.top_lev;   // the level-scheduled part: levels below the top zone
     v.nsteps = nsteps;
     v.nrow = cf.nrow;
     v.cperm = cf.cperm;
@@ -890,6 +958,30 @@ CView<T> make_view(const DevCFactor<T>& cf, int32_t nsteps) {
     v.lev_ptask_ptr = cf.d_lev_ptask_ptr;
     v.lev_sn_ptr = cf.d_lev_sn_ptr;
     v.lev_small = cf.d_lev_small;
+    v.red_off = pers_red_off(cf.max_n);
+    v.nT = cf.nT;
+    v.tf_parts = cf.tf_parts;
+    v.tb_parts = cf.tb_parts;
+    v.tpos = cf.tpos;
+    v.tseg_row = cf.tseg_row;
+    v.tsk_lo = cf.tsk_lo;
+    v.tp_pos = cf.tp_pos;
+    v.tb_cb_part = cf.tb_cb_part;
+    v.tseg_ptr = cf.tseg_ptr;
+    v.tsk_off = cf.tsk_off;
+    v.tb_off = cf.tb_off;
+    v.tp_off = cf.tp_off;
+    v.tsk = cf.tsk;
+    v.tb = cf.tb;
+    v.tf_rb = cf.tf_rb;
+    v.tf_tasks = cf.tf_tasks;
+    v.tb_cb = cf.tb_cb;
+    v.tb_tasks = cf.tb_tasks;
+    v.tT = cf.tT;
+    v.tf_part = cf.tf_part;
+    v.tb_part = cf.tb_part;
+    v.tf_cnt = cf.tf_cnt;
+    v.tb_cnt = cf.tb_cnt;
     v.bar = cf.bar;
     v.err = cf.err;
     return v;
@@ -916,71 +1008,75 @@ cudaError_t launch_persistent(K kern, int grid, size_t smem, unsigned* bar, cuda
 }
 
 template <typename T>
-cudaError_t launch_c_forward(const DevCFactor<T>& cf, const T* g_dd, int64_t ldg, T* tf, T* xf, int32_t nrhs,
+cudaError_t launch_c_forward(const DevCFactor<T>& cf, const T* g_dd, int64_t ldg, T* xf, int32_t nrhs,
                              cudaStream_t st) {
-    if (cf.nsteps_fwd == 0) return cudaSuccess;
-    if (!cf.per_level) {
+    if (nrhs > cf.ws_cols) return cudaErrorInvalidValue;
+    const CView<T> v = make_view(cf, cf.nsteps_fwd);
+    bool levels_done = cf.nsteps_fwd == 0;
+    if (!levels_done && !cf.per_level) {
         const size_t smem = pers_smem_bytes(cf.max_n, sizeof(T));
         const int grid = pers_grid(k_cfwd_persistent<T>, smem, cf.max_cta_tasks);
-        if (grid > 0)
-            return launch_persistent(k_cfwd_persistent<T>, grid, smem, cf.bar, st, make_view(cf, cf.nsteps_fwd), g_dd,
-                                     ldg, tf, xf, nrhs);
+        if (grid > 0) {
+            const cudaError_t e = launch_persistent(k_cfwd_persistent<T>, grid, smem, cf.bar, st, v, g_dd, ldg, xf, nrhs);
+            if (e != cudaSuccess) return e;
+            levels_done = true;
+        }
     }
-    for (int l = 0; l < cf.nlev; ++l) {
+    for (int l = 0; !levels_done && l < cf.top_lev; ++l) {
         if (cf.lev_small[l]) {
             const int s0 = cf.lev_sn_ptr[l], ns = cf.lev_sn_ptr[l + 1] - s0;
             if (ns == 0) continue;
-            k_cfwd_small<T><<<ns, kThreads, 0, st>>>(cf.lev_sn + s0, cf.c0, cf.cperm, cf.seg_ptr, cf.seg_row, cf.r_off,
-                                                     cf.pan_off, cf.panel, cf.dinv_off, cf.dinv, cf.wbuf, cf.nrow,
-                                                     g_dd, ldg, xf, cf.s, nrhs);
+            k_cfwd_small<T><<<ns, kThreads, 0, st>>>(v, s0, g_dd, ldg, xf, nrhs);
             counted();
             continue;
         }
         const int t0 = cf.lev_task_ptr[l], nt = cf.lev_task_ptr[l + 1] - t0;
         const int p0 = cf.lev_ptask_ptr[l], np = cf.lev_ptask_ptr[l + 1] - p0;
-        if (nt > 0) {
-            k_cfwd_gather<T><<<nt, 32, 0, st>>>(cf.tasks + t0, cf.c0, cf.cperm, cf.seg_ptr, cf.seg_row, cf.wbuf,
-                                                cf.nrow, g_dd, ldg, tf, cf.s, nrhs);
-            counted();
-            k_cfwd_diag<T><<<nt, kDiagT, 0, st>>>(cf.tasks + t0, cf.c0, cf.dinv_off, cf.dinv, tf, xf, cf.s, nrhs);
-            counted();
-        }
-        if (np > 0) {
-            k_cfwd_panel<T><<<np, kPanT, cf.max_n * sizeof(T), st>>>(cf.ptasks + p0, cf.c0, cf.r_off, cf.pan_off,
-                                                                      cf.panel, xf, cf.wbuf, cf.nrow, cf.s, nrhs);
-            counted();
-        }
+        if (nt + np == 0) continue;
+        if (nt + np > cf.nsm)
+            k_cfwd_level<T, 8><<<nt + np, 256, cf.max_n * sizeof(T), st>>>(v, t0, p0, np, g_dd, ldg, xf, nrhs);
+        else
+            k_cfwd_level<T, 32><<<nt + np, 1024, cf.max_n * sizeof(T), st>>>(v, t0, p0, np, g_dd, ldg, xf, nrhs);
+        counted();
+    }
+    if (cf.nT > 0) {
+        k_ctop_gather<T><<<blocks_for((int64_t)cf.nT * nrhs), kThreads, 0, st>>>(v, g_dd, ldg, nrhs);
+        k_ctop_fwd<T><<<cf.n_tf_tasks, kTopT, 0, st>>>(v, xf, nrhs);
+        counted(2);
     }
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_c_backward(const DevCFactor<T>& cf, T* yf, T* xf, T* y_dd, int64_t ldy, int32_t nrhs,
+cudaError_t launch_c_backward(const DevCFactor<T>& cf, const T* yf, T* xf, T* y_dd, int64_t ldy, int32_t nrhs,
                               cudaStream_t st) {
-    if (cf.nsteps_bwd == 0) return cudaSuccess;
+    if (cf.nT > 0 && nrhs > cf.ws_cols) return cudaErrorInvalidValue;
+    const CView<T> v = make_view(cf, cf.nsteps_bwd);
+    if (cf.nT > 0) {
+        k_ctop_bwd<T><<<cf.n_tb_tasks, kTopT, 0, st>>>(v, yf, xf, y_dd, ldy, nrhs);
+        counted();
+    }
+    if (cf.nsteps_bwd == 0) return cudaGetLastError();
     if (!cf.per_level) {
         const size_t smem = pers_smem_bytes(cf.max_n, sizeof(T));
         const int grid = pers_grid(k_cbwd_persistent<T>, smem, cf.max_cta_tasks);
         if (grid > 0)
-            return launch_persistent(k_cbwd_persistent<T>, grid, smem, cf.bar, st, make_view(cf, cf.nsteps_bwd), yf, xf,
-                                     y_dd, ldy, nrhs);
+            return launch_persistent(k_cbwd_persistent<T>, grid, smem, cf.bar, st, v, yf, xf, y_dd, ldy, nrhs);
     }
-    for (int l = cf.nlev - 1; l >= 0; --l) {
+    for (int l = cf.top_lev - 1; l >= 0; --l) {
         if (cf.lev_small[l]) {
             const int s0 = cf.lev_sn_ptr[l], ns = cf.lev_sn_ptr[l + 1] - s0;
             if (ns == 0) continue;
-            k_cbwd_small<T><<<ns, kThreads, 0, st>>>(cf.lev_sn + s0, cf.c0, cf.r_off, cf.rows, cf.pan_off, cf.panel,
-                                                     cf.dinv_off, cf.dinv, cf.cperm, yf, xf, y_dd, ldy, cf.s, nrhs);
+            k_cbwd_small<T><<<ns, kThreads, 0, st>>>(v, s0, yf, xf, y_dd, ldy, nrhs);
             counted();
             continue;
         }
         const int t0 = cf.lev_task_ptr[l], nt = cf.lev_task_ptr[l + 1] - t0;
         if (nt == 0) continue;
-        k_cbwd_panel<T><<<nt, kBPanT, 0, st>>>(cf.tasks + t0, cf.c0, cf.r_off, cf.rows, cf.pan_off, cf.panel,
-                                              yf, xf, cf.s, nrhs);
-        counted();
-        k_cbwd_diag<T><<<nt, kDiagT, 0, st>>>(cf.tasks + t0, cf.c0, cf.dinv_off, cf.dinv, cf.cperm, yf, xf,
-                                              y_dd, ldy, cf.s, nrhs);
+        if (nt > cf.nsm)
+            k_cbwd_level<T, 8><<<nt, 256, 0, st>>>(v, t0, yf, xf, y_dd, ldy, nrhs);
+        else
+            k_cbwd_level<T, 32><<<nt, 1024, 0, st>>>(v, t0, yf, xf, y_dd, ldy, nrhs);
         counted();
     }
     return cudaGetLastError();
@@ -1108,9 +1204,9 @@ cudaError_t launch_pcg_update_p(int32_t n, int32_t nrhs, double* p, const double
                                              int64_t, T*, int64_t, int32_t, cudaStream_t);                      \
     template cudaError_t launch_spmv_e<T>(const DevOperator<T>&, int32_t, const T*, int64_t, T*, int64_t,       \
                                           int32_t, cudaStream_t);                                               \
-    template cudaError_t launch_c_forward<T>(const DevCFactor<T>&, const T*, int64_t, T*, T*, int32_t,          \
-                                             cudaStream_t);                                                     \
-    template cudaError_t launch_c_backward<T>(const DevCFactor<T>&, T*, T*, T*, int64_t, int32_t, cudaStream_t); \
+    template cudaError_t launch_c_forward<T>(const DevCFactor<T>&, const T*, int64_t, T*, int32_t, cudaStream_t); \
+    template cudaError_t launch_c_backward<T>(const DevCFactor<T>&, const T*, T*, T*, int64_t, int32_t,           \
+                                              cudaStream_t);                                                    \
     template cudaError_t launch_lowrank<T>(const DevOperator<T>&, int32_t, int32_t, T*, int32_t, cudaStream_t);
 SLR_INST(double)
 SLR_INST(float)

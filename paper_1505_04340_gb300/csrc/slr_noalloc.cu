@@ -74,9 +74,16 @@ size_t carve(slr_handle h, DevOperator<T>& op, int32_t nrhs, unsigned char* base
     op.eb = c.take<T>(nI * nrhs);
     op.gp = c.take<T>(s * nrhs);
     op.wf = c.take<T>(s * nrhs);
-    op.tf = c.take<T>(s * nrhs);
     op.xf = c.take<T>(s * nrhs);
     op.cf.wbuf = c.take<T>(std::max<int64_t>(op.cf.nrow, 1) * nrhs);
+    op.cf.ws_cols = nrhs;
+    if (op.cf.nT > 0) {   // the top zone's workspaces; its counters are cleared before each apply
+        op.cf.tT = c.take<T>((int64_t)op.cf.nT * nrhs);
+        op.cf.tf_part = c.take<T>((int64_t)op.cf.tf_parts * nrhs);
+        op.cf.tb_part = c.take<T>((int64_t)op.cf.tb_parts * nrhs);
+        op.cf.tf_cnt = c.take<int32_t>(op.cf.n_tf_rb);
+        op.cf.tb_cnt = c.take<int32_t>(op.cf.n_tb_cb);
+    }
     op.cf.bar = c.take<unsigned>(1);          // the persistent C solves' grid barrier counter
     op.vk = c.take<T>(k * nrhs);
     op.part = c.take<T>(k * nrhs * kRedBlocks);
@@ -104,7 +111,11 @@ slr_status apply_with(slr_handle h, DevOperator<T>& op, const T* r, int64_t ldr,
     const int32_t nI = hs.nI, s = hs.s;
     NA_CK(launch_band_solve<T>(op, hs.p, hs.wmax, r, ldr, op.tB, nI, nullptr, 0, nrhs, st));
     NA_CK(launch_gather_et<T>(op, s, r + nI, ldr, op.tB, nI, op.gp, s, nrhs, st));
-    NA_CK(launch_c_forward<T>(op.cf, op.gp, s, op.tf, op.wf, nrhs, st));
+    if (op.cf.nT > 0) {   // the array's bytes there may hold another call's data
+        NA_CK(cudaMemsetAsync(op.cf.tf_cnt, 0, sizeof(int32_t) * op.cf.n_tf_rb, st));
+        NA_CK(cudaMemsetAsync(op.cf.tb_cnt, 0, sizeof(int32_t) * op.cf.n_tb_cb, st));
+    }
+    NA_CK(launch_c_forward<T>(op.cf, op.gp, s, op.wf, nrhs, st));
     NA_CK(launch_lowrank<T>(op, s, h->k, op.wf, nrhs, st));
     NA_CK(launch_c_backward<T>(op.cf, op.wf, op.xf, z + nI, ldz, nrhs, st));
     NA_CK(launch_spmv_e<T>(op, nI, z + nI, ldz, op.eb, nI, nrhs, st));

@@ -48,7 +48,8 @@ class Info(C.Structure):
         ("theta", C.c_double), ("setup_seconds", C.c_double * 5), ("precision", C.c_int32),
         ("theta_mode", C.c_int32), ("band_split", C.c_int32), ("band_slots", C.c_int32),
         ("c_persistent", C.c_int32), ("tuned", C.c_int32), ("tune_seconds", C.c_double),
-        ("band_threads", C.c_int32)]
+        ("band_threads", C.c_int32), ("c_top_levels", C.c_int32), ("c_top_positions", C.c_int32),
+        ("c_top_entries", C.c_int64)]
 
 
 class SLRError(RuntimeError):
@@ -162,7 +163,7 @@ class SLR:
     def __init__(self, rowptr, colind, val, part, nparts, k=16, lanczos_steps=0, theta="lambda_k1",
                  precision="fp64", nrhs_max=1, flexible_cg=False, seed=1, c_leaf=64, verbose=False,
                  band_split=0, host_loop=False, band_slots=0, c_persistent=False, autotune=False, target_kappa=0,
-                 band_threads=0, stream=None):
+                 band_threads=0, c_top_zone=True, stream=None):
         lib = load()
         self._lib = lib
         self._h = None
@@ -179,6 +180,7 @@ class SLR:
         o.reserved[4] = int(bool(autotune))      # time the candidates at setup and keep the fastest
         o.reserved[5] = int(target_kappa)        # rank by the rule lambda_{k+1} <= 1 - 1/K (0 = off)
         o.reserved[6] = int(band_threads)        # threads per band-solve CTA: 512, 256 or 0 (automatic)
+        o.reserved[7] = 0 if c_top_zone else 1   # explicit inverse of the factor's top levels
         self.rowptr, self.colind = _i32(rowptr), _i32(colind)
         self.val = np.ascontiguousarray(val, dtype=np.float64)
         self.part = _i32(part)

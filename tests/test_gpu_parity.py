@@ -111,11 +111,15 @@ def test_bsolve_ring_and_split(name, split, slots, nt, precision):
 @pytest.mark.parametrize("name", [n for n in PROBLEMS if n != "one-part"])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 @pytest.mark.parametrize("persistent", [False, True])
-def test_csolve_parity(name, precision, persistent):
-    """C^{-1} by the per-level kernels and the persistent one (one cooperative launch per direction)."""
+@pytest.mark.parametrize("zone", [True, False])
+def test_csolve_parity(name, precision, persistent, zone):
+    """C^{-1} by the per-level kernels and the persistent one (one cooperative launch per
+    direction), with the factor's top levels solved by their explicit inverse or level by level."""
     P = make(name)
     o = oracle(name)
-    g = gpu_handle(P, precision, c_persistent=persistent)
+    g = gpu_handle(P, precision, c_persistent=persistent, c_top_zone=zone)
+    if not zone:
+        assert g.get_info()["c_top_levels"] == 0
     gg = np.random.default_rng(2).standard_normal((o.order.s, 3))
     y = g.csolve(cu(gg)).cpu().numpy()
     assert rel(y, o.cfac.solve(gg)) <= (TOL64 if precision == "fp64" else TOL32)
@@ -136,10 +140,14 @@ def test_csolve_medium_with_fused_levels(precision):
     gg = np.random.default_rng(6).standard_normal((order.s, 2))
     want = want_fn(gg)
     for persistent in (False, True):
-        g = SLR(P.rowptr, P.colind, P.val, P.part, P.nparts, k=2, lanczos_steps=4, precision=precision,
-                nrhs_max=2, c_persistent=persistent)
-        y = g.csolve(cu(gg)).cpu().numpy()
-        assert rel(y, want) <= (TOL64 if precision == "fp64" else TOL32), persistent
+        for zone in (True, False):
+            g = SLR(P.rowptr, P.colind, P.val, P.part, P.nparts, k=2, lanczos_steps=4, precision=precision,
+                    nrhs_max=2, c_persistent=persistent, c_top_zone=zone)
+            inf = g.get_info()
+            # the zone takes some top levels but leaves level steps below it
+            assert (0 < inf["c_top_levels"] < inf["c_levels"]) if zone else inf["c_top_levels"] == 0
+            y = g.csolve(cu(gg)).cpu().numpy()
+            assert rel(y, want) <= (TOL64 if precision == "fp64" else TOL32), (persistent, zone)
 
 
 def test_pcg_with_persistent_c_solve_matches_per_level():
