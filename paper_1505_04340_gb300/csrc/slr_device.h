@@ -53,6 +53,8 @@ struct DevCFactor {
     int32_t ws_cols = 0;                      // right-hand sides the workspaces (wbuf and the zone's) hold
     bool per_level = true;                    // one launch per level step (else one cooperative launch)
     int32_t nsm = 152;                        // SMs of the device (CTA size of the per-level kernels)
+    std::vector<int32_t> lev_stage;           // fused levels: shared stage buffer (elements) of a supernode's block
+    int32_t stage_cap = 0;                    // the largest of them (persistent kernels)
 };
 
 // Everything one apply needs in precision T (double: FP64 path; float: mixed).

@@ -12,6 +12,8 @@
 #include <algorithm>
 #include <atomic>
 #include <cstdint>
+#include <mutex>
+#include <vector>
 
 #include "slr_device.h"
 
@@ -98,6 +100,7 @@ struct CView {
     const int32_t *lev_task_ptr, *lev_ptask_ptr, *lev_sn_ptr;
     const uint8_t* lev_small;
     int64_t red_off;   // persistent kernels: reduction array offset in shared memory (elements)
+    int32_t stage_cap; // persistent kernels: stage buffer of each fused-level group (elements)
     // top zone
     int32_t nT, tf_parts, tb_parts;
     const int32_t *tpos, *tseg_row, *tsk_lo, *tp_pos, *tb_cb_part;
@@ -280,6 +283,40 @@ __device__ __forceinline__ void group_sync() {
     }
 }
 
+// Copies n elements from global src to shared dst with asynchronous copies, the NT
+// threads of a group each issuing several before any lands (one commit group).
+template <typename T, int NT>
+__device__ __forceinline__ void stage_async(T* dst, const T* src, int64_t n, int gt) {
+    static_assert(sizeof(T) == 4 || sizeof(T) == 8, "4- or 8-byte elements");
+    for (int64_t i = gt; i < n; i += NT) {
+        const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(dst + i));
+        if constexpr (sizeof(T) == 8)
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src + i) : "memory");
+        else
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src + i) : "memory");
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void stage_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Stages A_J = [L_JJ^{-1} (packed); M_J] of a small supernode in the group's shared
+// buffer stg (cap elements) when it fits; D and P then point there, else to HBM.
+// The arithmetic is the same either way.
+template <typename T, int NT>
+__device__ __forceinline__ bool stage_block(const CView<T>& cf, int J, T* stg, int cap, int gt, const T*& D,
+                                            const T*& P) {
+    const int64_t nJ = cf.c0[J + 1] - cf.c0[J], nr = cf.r_off[J + 1] - cf.r_off[J];
+    const int64_t nd = nJ * (nJ + 1) / 2;
+    D = cf.dinv + cf.dinv_off[J];
+    P = cf.panel + cf.pan_off[J];
+    if (nd + nr * nJ > cap) return false;
+    stage_async<T, NT>(stg, D, nd, gt);
+    stage_async<T, NT>(stg + nd, P, nr * nJ, gt);
+    D = stg;
+    P = stg + nd;
+    return true;
+}
+
 // Fused levels: one group of NT threads (a CTA, or a part of one) per supernode J
 // with n_J <= kSmallN and |R_J| <= kSmallR.  Both directions use the stacked
 // matrix A_J = [L_JJ^{-1}; M_J] ((n_J + |R_J|) x n_J; row r < n_J of the
@@ -287,15 +324,17 @@ __device__ __forceinline__ void group_sync() {
 // forward: t_J gathered into ts; [x_J; w_J] = A_J t_J with a warp per row of A_J
 // (lanes over the columns, four rows in flight per warp)
 template <typename T, int NT, int GROUPS>
-__device__ void cfwd_small_cta(const CView<T>& cf, int J, T* ts, const T* g, int64_t ldg, T* xf, int32_t nrhs) {
+__device__ void cfwd_small_cta(const CView<T>& cf, int J, T* ts, const T* g, int64_t ldg, T* xf, int32_t nrhs, T* stg,
+                               int cap) {
     constexpr int nw = NT / 32;
     const int gt = threadIdx.x % NT, lane = gt & 31, warp = gt >> 5;
     const int32_t a0 = cf.c0[J], nJ = cf.c0[J + 1] - a0;
     const int64_t nr = cf.r_off[J + 1] - cf.r_off[J], rtot = nJ + nr;
-    const T* D = cf.dinv + cf.dinv_off[J];
-    const T* Pn = cf.panel + cf.pan_off[J];
+    const T *D, *Pn;
+    const bool staged = stage_block<T, NT>(cf, J, stg, cap, gt, D, Pn);   // lands while t_J is gathered
     for (int j = 0; j < nrhs; ++j) {
         gather_t(cf, J, gt, NT, ts, g, ldg, j);
+        if (j == 0 && staged) stage_wait();
         group_sync<NT, GROUPS>();
         for (int64_t r0 = 4 * warp; r0 < rtot; r0 += 4 * nw) {
             T acc[4] = {T(0), T(0), T(0), T(0)};
@@ -333,14 +372,14 @@ __device__ void cfwd_small_cta(const CView<T>& cf, int J, T* ts, const T* g, int
 // parts' partial sums (in red) are added in a fixed order.
 template <typename T, int NT, int GROUPS>
 __device__ void cbwd_small_cta(const CView<T>& cf, int J, T* vs, T* red, const T* yf, T* xf, T* y_dd, int64_t ldy,
-                               int32_t nrhs) {
+                               int32_t nrhs, T* stg, int cap) {
     static_assert(NT % kSmallN == 0 && NT <= 1024, "whole parts per column");
     const int gt = threadIdx.x % NT;
     const int32_t a0 = cf.c0[J], nJ = cf.c0[J + 1] - a0;
     const int64_t nr = cf.r_off[J + 1] - cf.r_off[J], rtot = nJ + nr;
     const int32_t* R = cf.rows + cf.r_off[J];
-    const T* D = cf.dinv + cf.dinv_off[J];
-    const T* Pn = cf.panel + cf.pan_off[J];
+    const T *D, *Pn;
+    const bool staged = stage_block<T, NT>(cf, J, stg, cap, gt, D, Pn);   // lands while the vector is staged
     int P = 32;
     while (P < nJ) P *= 2;
     const int parts = NT / P, part = gt / P, c = gt % P;
@@ -349,6 +388,7 @@ __device__ void cbwd_small_cta(const CView<T>& cf, int J, T* vs, T* red, const T
         const T* x = xf + (int64_t)j * cf.s;
         const T* y = yf + a0 + (int64_t)j * cf.s;
         for (int64_t r = gt; r < rtot; r += NT) vs[r] = r < nJ ? y[r] : -x[R[r - nJ]];
+        if (j == 0 && staged) stage_wait();
         group_sync<NT, GROUPS>();
         T acc = T(0);
         if (c < nJ) {
@@ -413,18 +453,23 @@ k_cbwd_level(const CView<T> cf, int32_t t0, const T* yf, T* xf, T* y_dd, int64_t
     cbwd_task_cta<T, NW, sizeof(T) == 4 ? 16 : 8>(cf, cf.tasks[t0 + blockIdx.x], us, red, yf, xf, y_dd, ldy, nrhs);
 }
 
+// dynamic shared memory: the stage buffer of cap elements
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
-k_cfwd_small(const CView<T> cf, int32_t s0, const T* g, int64_t ldg, T* xf, int32_t nrhs) {
+k_cfwd_small(const CView<T> cf, int32_t s0, const T* g, int64_t ldg, T* xf, int32_t nrhs, int32_t cap) {
+    extern __shared__ __align__(16) unsigned char csm[];
     __shared__ T ts[kSmallN];
-    cfwd_small_cta<T, kThreads, 1>(cf, cf.lev_sn[s0 + blockIdx.x], ts, g, ldg, xf, nrhs);
+    cfwd_small_cta<T, kThreads, 1>(cf, cf.lev_sn[s0 + blockIdx.x], ts, g, ldg, xf, nrhs, reinterpret_cast<T*>(csm),
+                                   cap);
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
-k_cbwd_small(const CView<T> cf, int32_t s0, const T* yf, T* xf, T* y_dd, int64_t ldy, int32_t nrhs) {
+k_cbwd_small(const CView<T> cf, int32_t s0, const T* yf, T* xf, T* y_dd, int64_t ldy, int32_t nrhs, int32_t cap) {
+    extern __shared__ __align__(16) unsigned char csm[];
     __shared__ T vs[kSmallN + kSmallR], red[kThreads];
-    cbwd_small_cta<T, kThreads, 1>(cf, cf.lev_sn[s0 + blockIdx.x], vs, red, yf, xf, y_dd, ldy, nrhs);
+    cbwd_small_cta<T, kThreads, 1>(cf, cf.lev_sn[s0 + blockIdx.x], vs, red, yf, xf, y_dd, ldy, nrhs,
+                                   reinterpret_cast<T*>(csm), cap);
 }
 
 
@@ -606,9 +651,11 @@ __device__ __forceinline__ void grid_barrier(unsigned* bar, unsigned target, int
 // array of a forward task, or the fused levels' buffers, whichever is larger.
 // The reduction array starts at a multiple of 32 elements.
 inline int64_t pers_red_off(int32_t max_n) { return ((int64_t)max_n + 31) / 32 * 32; }
-inline size_t pers_smem_bytes(int32_t max_n, size_t elem) {
+// Each fused-level group also gets a stage buffer of stage_cap elements.
+inline size_t pers_smem_bytes(int32_t max_n, size_t elem, int32_t stage_cap) {
     const int64_t task = pers_red_off(max_n) + kPersW * 33 + 32;
-    const int64_t small_fwd = kSmallG * kSmallN, small_bwd = kSmallG * (kSmallN + kSmallR + kSmallT);
+    const int64_t small_fwd = kSmallG * ((int64_t)kSmallN + stage_cap),
+                  small_bwd = kSmallG * ((int64_t)kSmallN + kSmallR + kSmallT + stage_cap);
     return (size_t)std::max({task, small_fwd, small_bwd}) * elem;
 }
 
@@ -626,8 +673,10 @@ k_cfwd_persistent(const CView<T> cf, const T* g, int64_t ldg, T* xf, int32_t nrh
             const int s0 = cf.lev_sn_ptr[l], ns = cf.lev_sn_ptr[l + 1] - s0;
             any = ns > 0;
             const int grp = threadIdx.x / kSmallT;
+            T* gs = sm + grp * ((int64_t)kSmallN + cf.stage_cap);
             for (int q = blockIdx.x * kSmallG + grp; q < ns; q += gridDim.x * kSmallG)
-                cfwd_small_cta<T, kSmallT, kSmallG>(cf, cf.lev_sn[s0 + q], sm + grp * kSmallN, g, ldg, xf, nrhs);
+                cfwd_small_cta<T, kSmallT, kSmallG>(cf, cf.lev_sn[s0 + q], gs, g, ldg, xf, nrhs, gs + kSmallN,
+                                                    cf.stage_cap);
         } else {
             const int t0 = cf.lev_task_ptr[l], nt = cf.lev_task_ptr[l + 1] - t0;
             const int p0 = cf.lev_ptask_ptr[l], np = cf.lev_ptask_ptr[l + 1] - p0;
@@ -656,10 +705,10 @@ k_cbwd_persistent(const CView<T> cf, const T* yf, T* xf, T* y_dd, int64_t ldy, i
             const int s0 = cf.lev_sn_ptr[l], ns = cf.lev_sn_ptr[l + 1] - s0;
             any = ns > 0;
             const int grp = threadIdx.x / kSmallT;
-            T* gs = sm + grp * (kSmallN + kSmallR + kSmallT);
+            T* gs = sm + grp * ((int64_t)kSmallN + kSmallR + kSmallT + cf.stage_cap);
             for (int q = blockIdx.x * kSmallG + grp; q < ns; q += gridDim.x * kSmallG)
                 cbwd_small_cta<T, kSmallT, kSmallG>(cf, cf.lev_sn[s0 + q], gs, gs + kSmallN + kSmallR, yf, xf, y_dd,
-                                                    ldy, nrhs);
+                                                    ldy, nrhs, gs + kSmallN + kSmallR + kSmallT, cf.stage_cap);
         } else {
             const int t0 = cf.lev_task_ptr[l], nt = cf.lev_task_ptr[l + 1] - t0;
             any = nt > 0;
@@ -925,6 +974,19 @@ template <typename K>
 int pers_grid(K kern, size_t smem, int32_t max_cta_tasks) {
     int dev = 0, nsm = 0, occ = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (smem > 48 * 1024) {
+        // the limit is process-wide per kernel: raised once, to the opt-in maximum
+        static std::mutex mu;
+        static std::vector<const void*> raised;
+        std::lock_guard<std::mutex> lk(mu);
+        if (std::find(raised.begin(), raised.end(), (const void*)kern) == raised.end()) {
+            if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) != cudaSuccess) {
+                cudaGetLastError();
+                return 0;
+            }
+            raised.push_back((const void*)kern);
+        }
+    }
     if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kPersT, smem) != cudaSuccess || occ < 1) {
         cudaGetLastError();
@@ -959,6 +1021,7 @@ CView<T> make_view(const DevCFactor<T>& cf, int32_t nsteps) {
     v.lev_sn_ptr = cf.d_lev_sn_ptr;
     v.lev_small = cf.d_lev_small;
     v.red_off = pers_red_off(cf.max_n);
+    v.stage_cap = cf.stage_cap;
     v.nT = cf.nT;
     v.tf_parts = cf.tf_parts;
     v.tb_parts = cf.tb_parts;
@@ -1014,7 +1077,7 @@ cudaError_t launch_c_forward(const DevCFactor<T>& cf, const T* g_dd, int64_t ldg
     const CView<T> v = make_view(cf, cf.nsteps_fwd);
     bool levels_done = cf.nsteps_fwd == 0;
     if (!levels_done && !cf.per_level) {
-        const size_t smem = pers_smem_bytes(cf.max_n, sizeof(T));
+        const size_t smem = pers_smem_bytes(cf.max_n, sizeof(T), cf.stage_cap);
         const int grid = pers_grid(k_cfwd_persistent<T>, smem, cf.max_cta_tasks);
         if (grid > 0) {
             const cudaError_t e = launch_persistent(k_cfwd_persistent<T>, grid, smem, cf.bar, st, v, g_dd, ldg, xf, nrhs);
@@ -1026,7 +1089,8 @@ cudaError_t launch_c_forward(const DevCFactor<T>& cf, const T* g_dd, int64_t ldg
         if (cf.lev_small[l]) {
             const int s0 = cf.lev_sn_ptr[l], ns = cf.lev_sn_ptr[l + 1] - s0;
             if (ns == 0) continue;
-            k_cfwd_small<T><<<ns, kThreads, 0, st>>>(v, s0, g_dd, ldg, xf, nrhs);
+            const int32_t cap = cf.lev_stage[l];
+            k_cfwd_small<T><<<ns, kThreads, cap * sizeof(T), st>>>(v, s0, g_dd, ldg, xf, nrhs, cap);
             counted();
             continue;
         }
@@ -1058,7 +1122,7 @@ cudaError_t launch_c_backward(const DevCFactor<T>& cf, const T* yf, T* xf, T* y_
     }
     if (cf.nsteps_bwd == 0) return cudaGetLastError();
     if (!cf.per_level) {
-        const size_t smem = pers_smem_bytes(cf.max_n, sizeof(T));
+        const size_t smem = pers_smem_bytes(cf.max_n, sizeof(T), cf.stage_cap);
         const int grid = pers_grid(k_cbwd_persistent<T>, smem, cf.max_cta_tasks);
         if (grid > 0)
             return launch_persistent(k_cbwd_persistent<T>, grid, smem, cf.bar, st, v, yf, xf, y_dd, ldy, nrhs);
@@ -1067,7 +1131,8 @@ cudaError_t launch_c_backward(const DevCFactor<T>& cf, const T* yf, T* xf, T* y_
         if (cf.lev_small[l]) {
             const int s0 = cf.lev_sn_ptr[l], ns = cf.lev_sn_ptr[l + 1] - s0;
             if (ns == 0) continue;
-            k_cbwd_small<T><<<ns, kThreads, 0, st>>>(v, s0, yf, xf, y_dd, ldy, nrhs);
+            const int32_t cap = cf.lev_stage[l];
+            k_cbwd_small<T><<<ns, kThreads, cap * sizeof(T), st>>>(v, s0, yf, xf, y_dd, ldy, nrhs, cap);
             counted();
             continue;
         }
