@@ -433,7 +433,8 @@ def run_ours(args):
             tuning={"band_split": info["band_split"], "band_slots": info["band_slots"],
                     "c_persistent": info["c_persistent"], "tuned": info["tuned"],
                     "tune_seconds": info["tune_seconds"]},
-            band_flops=band_flops, device_bytes=info["device_bytes"], setup_parts=info["setup_seconds"])
+            band_flops=band_flops, device_bytes=info["device_bytes"], setup_parts=info["setup_seconds"],
+            lanczos_parts=info["lanczos_seconds"], band_on_device=info["band_on_device"])
         # end to end through host buffers: pinned b -> device, solve, x -> pinned host
         if prec == "fp64":
             bh = torch.tensor(P.b[:, 0]).pin_memory()
@@ -496,6 +497,12 @@ def run_ours(args):
                    "parallelism": f"replicas x{ws}", "tuning": r64["tuning"]},
         "iterations": its_full, "p50_ms": r64["p50_ms"], "p99_ms": r64["p99_ms"],
         "true_relres": r64["true_relres"], "setup_s": r64["setup_s"],
+        "setup_phases_s": dict(zip(["analysis", "band_factor", "c_factor", "upload", "lanczos"],
+                                   [round(x, 4) for x in r64["setup_parts"]]),
+                               lanczos_h_apply=round(r64["lanczos_parts"][0], 4),
+                               lanczos_reorth=round(r64["lanczos_parts"][1], 4),
+                               lanczos_eig=round(r64["lanczos_parts"][2], 4),
+                               band_on_device=r64["band_on_device"]),
         "apply": {"us": r64["apply_us"], "gbs": r64["apply_gbs"], "bytes": r64["bytes_per_apply"]},
         "mixed": {"value": rm["solves_per_s"], "ms_per_step": rm["ms_per_step"], "iterations": rm["iters"],
                   "p50_ms": rm["p50_ms"], "p99_ms": rm["p99_ms"], "x_rel_diff_vs_fp64": results["x_mixed_err"],

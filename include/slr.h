@@ -71,7 +71,7 @@ typedef struct {
                                order, u_i = (x_i >> 11) 2^-53, x_i output i of the stream */
     int32_t c_leaf;         /* nested-dissection leaf size for C's ordering; 0 => 64     */
     int32_t verbose;        /* 1: setup prints timings to stderr                          */
-    int32_t reserved[8];    /* reserved[0]: CTAs per subdomain in the band solve (1, 2, 4;
+    int32_t reserved[16];   /* reserved[0]: CTAs per subdomain in the band solve (1, 2, 4;
                                0 = automatic).  reserved[1]: 1 = drive the CG loop from
                                the host (one synchronisation per iteration) instead of
                                one CUDA graph per solve.  reserved[2]: shared-memory
@@ -96,7 +96,11 @@ typedef struct {
                                factor level by level; 0 (default) = the top levels, as
                                many as fit a fill and setup budget, are solved with an
                                explicit inverse of their block of the factor (one step
-                               per direction instead of one per level).                */
+                               per direction instead of one per level).
+                               reserved[8]: where the B_i are factored (Section 5.2):
+                               0 (default) = on the device when every plane is at most
+                               256 rows wide, else on the host; 1 = on the host.
+                               reserved[9..15] must be 0.                              */
 } slr_opts;
 
 typedef struct {
@@ -121,6 +125,10 @@ typedef struct {
     int32_t c_top_levels;        /* levels of C's factor solved with the explicit inverse   */
     int32_t c_top_positions;     /* interface positions in those levels                     */
     int64_t c_top_entries;       /* stored entries of that inverse (each layout)            */
+    int32_t band_on_device;      /* 1: the B_i were factored on the device (reserved[8])    */
+    double lanczos_seconds[3];   /* setup Lanczos (Section 5.1) split: H applies with the alpha
+                                    dot, full reorthogonalisation with the beta norm, the
+                                    tridiagonal eigensolve on the host and U_k = V Y_k      */
 } slr_info;
 
 /* Fill *opts with defaults: k = 16, m = 5k, theta = lambda_{k+1}, FP64, 1 RHS, seed 1. */

@@ -374,6 +374,9 @@ slr_status run_lanczos(slr_handle h, cudaStream_t st) {
     std::vector<double> alpha(m), beta(m);
     int32_t m_eff = m;
     double amax = 0.0;
+    // time split (both reads synchronise the stream): H applies with the alpha dot,
+    // reorthogonalisation with the beta norm, then the host eigensolve and U_k = V Y_k
+    double ta = 0.0, tr = 0.0, tcur = now_s();
     for (int32_t j = 0; j < m; ++j) {
         double* vj = V + (int64_t)j * s;
         CS(h_apply(h, vj, w, st));
@@ -381,6 +384,8 @@ slr_status run_lanczos(slr_handle h, cudaStream_t st) {
         CK(launch_dots(s, 1, vj, s, w, s, part, sc, 1, st));
         alpha[j] = read_scalar(sc, st, &err);
         CS(err);
+        ta += now_s() - tcur;
+        tcur = now_s();
         amax = std::max(amax, std::fabs(alpha[j]));
         CK(launch_axpby(s, -alpha[j], vj, 1.0, w, st));
         for (int pass = 0; pass < 2; ++pass) {                       // full reorthogonalisation
@@ -390,10 +395,13 @@ slr_status run_lanczos(slr_handle h, cudaStream_t st) {
         CK(launch_dots(s, 1, w, s, w, s, part, sc, 1, st));
         beta[j] = std::sqrt(read_scalar(sc, st, &err));
         CS(err);
+        tr += now_s() - tcur;
+        tcur = now_s();
         if (j + 1 == m) break;
         if (beta[j] <= 1e-12 * amax) { m_eff = j + 1; break; }
         CK(launch_axpby(s, 1.0 / beta[j], w, 0.0, V + (int64_t)(j + 1) * s, st));
     }
+    const double te0 = now_s();
     std::vector<double> lam(m_eff), Y((size_t)m_eff * m_eff);
     host_tridiag_eig(m_eff, alpha.data(), beta.data(), lam.data(), Y.data());
     k = std::min(k, m_eff);
@@ -415,6 +423,9 @@ slr_status run_lanczos(slr_handle h, cudaStream_t st) {
     CS(dalloc(h, &Ud, (size_t)s * k));
     CK(launch_gemm_nn(s, m_eff, k, V, Yd, Ud, st));
     CK(cudaStreamSynchronize(st));
+    h->lanczos_seconds[0] = ta;
+    h->lanczos_seconds[1] = tr;
+    h->lanczos_seconds[2] = now_s() - te0;
     CS(set_operator_lowrank<double>(h, op, Ud, 0, k, h->lam, h->theta));
     h->k = k;
     dfree(h, Ud, (size_t)s * k);
@@ -633,17 +644,64 @@ slr_status capture_graph(slr_handle h, F f, cudaGraphExec_t* out) {
     return r;
 }
 
-// Repack the band factor for G CTAs per subdomain and reload it into the apply operator.
+// Section 5.2 on the device: the plane blocks of every B_i into h->bf_scr; a
+// non-positive pivot returns SLR_ERR_NOT_SPD naming the subdomain.
+slr_status device_band_factor(slr_handle h, cudaStream_t st) {
+    HostSetup& hs = h->hs;
+    const int32_t p = hs.p;
+    std::vector<int64_t> soff(p + 1, 0);
+    for (int32_t i = 0; i < p; ++i) {
+        const BandBlock& b = hs.band[i];
+        soff[i + 1] = soff[i] + (b.m ? (int64_t)(1 + 2 * b.c) * b.w * b.w : 0);
+    }
+    h->bf_scr_len = std::max<int64_t>(soff[p], 1);
+    CS(dalloc(h, &h->bf_scr, (size_t)h->bf_scr_len));
+    CS(upload(h, &h->bf_soff, soff));
+    BandBlock* dband = nullptr;
+    int32_t* bad = nullptr;
+    CS(upload(h, &dband, hs.band));
+    CS(dalloc(h, &bad, 1));
+    CK(cudaMemsetAsync(bad, 0xff, sizeof(int32_t), st));   // -1: no failure
+    CK(launch_band_factor(dband, p, h->a_rp, h->a_ci, h->a_v, h->bf_scr, h->bf_soff, bad, st));
+    int32_t hb = -1;
+    CK(cudaMemcpyAsync(&hb, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    dfree(h, dband, hs.band.size());
+    dfree(h, bad, 1);
+    if (hb >= 0) {
+        set_error("B_" + std::to_string(hb) + " is not positive definite (Cholesky pivot <= 0)");
+        return SLR_ERR_NOT_SPD;
+    }
+    return SLR_OK;
+}
+
+// The operator's band factor, packed on the device for the current layout (op.band).
+template <typename T>
+slr_status device_band_pack(slr_handle h, DevOperator<T>& op, cudaStream_t st) {
+    HostSetup& hs = h->hs;
+    int32_t cmax = 0;
+    for (const BandBlock& b : hs.band) cmax = std::max(cmax, b.c);
+    CS(dalloc(h, &op.bfac, (size_t)hs.bfac_len));
+    CK(cudaMemsetAsync(op.bfac, 0, sizeof(T) * hs.bfac_len, st));
+    CK(launch_band_pack<T>(op.band, hs.p, cmax, hs.band_G, h->bf_scr, h->bf_soff, op.bfac, st));
+    return SLR_OK;
+}
+
+// Repack the band factor for G CTAs per subdomain and reload it into the apply
+// operator (from the device plane blocks when the B_i were factored there).
 template <typename T>
 slr_status repack_band(slr_handle h, DevOperator<T>& op, int32_t G) {
     HostSetup& hs = h->hs;
-    const size_t old_band = hs.band.size(), old_fac = hs.bfac.size();
-    CS(host_band_factor(hs, G));
+    const size_t old_band = hs.band.size();
+    const int64_t old_fac = hs.bfac_len;
+    if (h->bf_scr) host_band_layout(hs, G);
+    else CS(host_band_factor(hs, G));
     CK(cudaStreamSynchronize(h->stream));
     dfree(h, op.band, old_band);
-    dfree(h, op.bfac, old_fac);
+    dfree(h, op.bfac, (size_t)old_fac);
     CS(upload(h, &op.band, hs.band));
-    CS(upload(h, &op.bfac, hs.bfac));
+    if (h->bf_scr) CS(device_band_pack<T>(h, op, h->stream));
+    else CS(upload(h, &op.bfac, hs.bfac));
     CK(cudaStreamSynchronize(h->stream));
     op.band_G = hs.band_G;
     return SLR_OK;
@@ -734,13 +792,16 @@ slr_status setup_impl(slr_handle h, int32_t n, const int32_t* rowptr, const int3
     CS(host_dd_order(n, rowptr, colind, nparts, part, hs));
     CS(host_split_blocks(rowptr, colind, val, hs));
     double t1 = now_s();
+    bool dev_band = false;
     // CTAs per subdomain in the band solve: a slice holds at most 256 rows of a
     // plane; with few subdomains two CTAs (a cluster) share each one so that
     // more SMs stream the factor
     {
         int32_t G = 1;
         int dev = 0, nsm = 152;
-        if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        const bool have_dev = cudaGetDevice(&dev) == cudaSuccess;
+        if (have_dev) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        else cudaGetLastError();
         // the widest plane decides the minimum split
         int32_t wmx = 0;
         for (int32_t q = 0; q < nparts; ++q) {
@@ -766,7 +827,11 @@ slr_status setup_impl(slr_handle h, int32_t n, const int32_t* rowptr, const int3
             // faster in both precisions on 16^3 boxes; four CTAs need two waves)
             G = 2;
         }
-        CS(host_band_factor(hs, G));
+        // Section 5.2: factor the B_i on the device when every plane fits its kernel (at
+        // most 256 rows), else on the host
+        dev_band = have_dev && h->opts.reserved[8] == 0 && wmx > 0 && wmx <= 256;
+        if (dev_band) host_band_layout(hs, G);
+        else CS(host_band_factor(hs, G));
         // more CTAs than SMs would run in two waves: 256-thread CTAs put two subdomains on an SM
         hs.band_nt = h->opts.reserved[6] ? h->opts.reserved[6] : (nparts * G > nsm ? 256 : 512);
     }
@@ -786,7 +851,15 @@ slr_status setup_impl(slr_handle h, int32_t n, const int32_t* rowptr, const int3
     CS(upload(h, &h->c_rp, hs.c_rp));
     CS(upload(h, &h->c_ci, hs.c_ci));
     CS(upload(h, &h->c_v, hs.c_v));
-    CS(upload_operator<double>(h, h->op64, true));
+    double tb = 0.0;   // device band factorization time (part of the B-factor figure)
+    h->band_on_device = dev_band;
+    if (dev_band) {
+        const double tb0 = now_s();
+        CS(device_band_factor(h, st));
+        tb = now_s() - tb0;
+    }
+    CS(upload_operator<double>(h, h->op64, !dev_band));
+    if (dev_band) CS(device_band_pack<double>(h, h->op64, st));
     const int32_t r = std::max(1, h->opts.nrhs_max);
     const size_t nr = (size_t)std::max(1, n) * r;
     CS(dalloc(h, &h->px, nr));
@@ -804,21 +877,41 @@ slr_status setup_impl(slr_handle h, int32_t n, const int32_t* rowptr, const int3
     CK(cudaStreamSynchronize(st));
     double t5 = now_s();
     if (h->opts.precision == SLR_PREC_MIXED) {
-        CS(upload_operator<float>(h, h->op32, true));
+        CS(upload_operator<float>(h, h->op32, !dev_band));
+        if (dev_band) CS(device_band_pack<float>(h, h->op32, st));
         CS(set_operator_lowrank<float>(h, h->op32, h->op64.U, 0, h->k, h->lam, h->theta));
         // the FP64 band factor served the FP64 Lanczos only
-        dfree(h, h->op64.bfac, hs.bfac.size());
+        dfree(h, h->op64.bfac, (size_t)hs.bfac_len);
     }
     if (h->opts.reserved[4] == 1) {
         if (h->opts.precision == SLR_PREC_FP64) CS(autotune<double>(h, h->op64, st));
         else CS(autotune<float>(h, h->op32, st));
     }
+    if (dev_band) {
+        // a mixed-precision handle keeps an FP64 copy of the band factor on the host
+        // for slr_add_vectors (packed for the final layout); the plane blocks go
+        if (h->opts.precision == SLR_PREC_MIXED) {
+            double* tmp = nullptr;
+            CS(dalloc(h, &tmp, (size_t)hs.bfac_len));
+            CK(cudaMemsetAsync(tmp, 0, sizeof(double) * hs.bfac_len, st));
+            int32_t cmax = 0;
+            for (const BandBlock& b : hs.band) cmax = std::max(cmax, b.c);
+            CK(launch_band_pack<double>(h->op32.band, hs.p, cmax, hs.band_G, h->bf_scr, h->bf_soff, tmp, st));
+            hs.bfac.assign((size_t)hs.bfac_len, 0.0);
+            CK(cudaMemcpyAsync(hs.bfac.data(), tmp, sizeof(double) * hs.bfac_len, cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            dfree(h, tmp, (size_t)hs.bfac_len);
+        }
+        CK(cudaStreamSynchronize(st));
+        dfree(h, h->bf_scr, (size_t)h->bf_scr_len);
+        dfree(h, h->bf_soff, (size_t)hs.p + 1);
+    }
     CK(cudaStreamSynchronize(st));
     double t6 = now_s();
     h->setup_seconds[0] = t1 - t0;
-    h->setup_seconds[1] = t2 - t1;
+    h->setup_seconds[1] = t2 - t1 + tb;
     h->setup_seconds[2] = t3 - t2;
-    h->setup_seconds[3] = (t4 - t3) + (t6 - t5);
+    h->setup_seconds[3] = (t4 - t3 - tb) + (t6 - t5);
     h->setup_seconds[4] = t5 - t4;
     account(h);
     if (vb)
@@ -990,7 +1083,8 @@ slr_status slr_setup(int32_t n, const int32_t* rowptr, const int32_t* colind, co
         h->opts.reserved[3] < 0 || h->opts.reserved[3] > 1 || h->opts.reserved[4] < 0 || h->opts.reserved[4] > 1 ||
         h->opts.reserved[5] < 0 || h->opts.reserved[5] == 1 ||
         (h->opts.reserved[6] != 0 && h->opts.reserved[6] != 256 && h->opts.reserved[6] != 512) ||
-        h->opts.reserved[7] < 0 || h->opts.reserved[7] > 1) {
+        h->opts.reserved[7] < 0 || h->opts.reserved[7] > 1 || h->opts.reserved[8] < 0 || h->opts.reserved[8] > 1 ||
+        std::any_of(h->opts.reserved + 9, h->opts.reserved + 16, [](int32_t v) { return v != 0; })) {
         set_error("invalid options");
         delete h;
         return SLR_ERR_INVALID_ARG;
@@ -1288,6 +1382,8 @@ slr_status slr_get_info(slr_handle h, slr_info* info) {
     info->c_top_levels = hs.cf.nlev - hs.cf.top_lev;
     info->c_top_positions = hs.cf.nT;
     info->c_top_entries = hs.cf.tsk_off.empty() ? 0 : hs.cf.tsk_off.back();
+    info->band_on_device = h->band_on_device ? 1 : 0;
+    for (int i = 0; i < 3; ++i) info->lanczos_seconds[i] = h->lanczos_seconds[i];
     return SLR_OK;
 }
 

@@ -115,6 +115,13 @@ struct slr_handle_s {
     int64_t bytes_per_apply = 0, flops_per_apply = 0;
     bool tuned = false;
     double tune_seconds = 0.0;
+    // band factorization on the device: per-subdomain plane blocks D_J and O_J
+    // (kept through setup so that a repack for another split needs no refactoring)
+    double* bf_scr = nullptr;
+    int64_t bf_scr_len = 0;
+    int64_t* bf_soff = nullptr;
+    bool band_on_device = false;     // the B_i were factored on the device
+    double lanczos_seconds[3] = {0, 0, 0};   // setup Lanczos: H applies, reorthogonalisation, eigensolve + U_k
 };
 
 namespace slr {
@@ -139,6 +146,16 @@ cudaError_t launch_gather_et(const DevOperator<T>& op, int32_t s, const T* g, in
 template <typename T>
 cudaError_t launch_spmv_e(const DevOperator<T>& op, int32_t nI, const T* y, int64_t ldy, T* out,
                           int64_t ldo, int32_t nrhs, cudaStream_t st);
+// ---- band factorization on the device (slr_band_factor.cu): the plane blocks of
+// every B_i into scr (per subdomain at soff[i]: S, then D_J for every plane, then
+// O_J); *bad receives a subdomain whose pivot is not positive (it must hold -1)
+cudaError_t launch_band_factor(const BandBlock* band, int32_t p, const int32_t* a_rp, const int32_t* a_ci,
+                               const double* a_v, double* scr, const int64_t* soff, int32_t* bad, cudaStream_t st);
+// packs them into the tiled slice layout of `band` (split G) in precision T; bfac
+// must be zeroed first (slices shorter than the widest keep zeros)
+template <typename T>
+cudaError_t launch_band_pack(const BandBlock* band, int32_t p, int32_t cmax, int32_t G, const double* scr,
+                             const int64_t* soff, T* bfac, cudaStream_t st);
 // ---- K3: C solves.  fwd: xf = L^{-1} P g (g in DD order, xf in factor order)
 //              bwd: xf = L^{-T} yf (factor order), optional scatter to DD order y_dd
 // xf, yf: s x nrhs (leading dimension s); yf is read only and must not overlap xf.

@@ -257,10 +257,11 @@ void band_assign_blocks(BandBlock& b, int G) {
     }
 }
 
-slr_status host_band_factor(HostSetup& hs, int32_t G) {
+void host_band_layout(HostSetup& hs, int32_t G) {
     const int32_t p = hs.p;
     hs.band.assign(p, BandBlock());
-    std::vector<int32_t> bw(p, 0);
+    hs.band_w.assign(p, 0);
+    std::vector<int32_t>& bw = hs.band_w;
     std::map<int32_t, BandBlock> assigned;   // block assignment per plane width
     int64_t off = 0;
     hs.wmax = 0;
@@ -304,7 +305,14 @@ slr_status host_band_factor(HostSetup& hs, int32_t G) {
         hs.wmax = std::max(hs.wmax, b.w);
     }
     hs.band_G = G;
-    hs.bfac.assign(off + 64, 0.0);   // tail slack: bulk copies round up to 16 bytes
+    hs.bfac_len = off + 64;   // tail slack: bulk copies round up to 16 bytes
+}
+
+slr_status host_band_factor(HostSetup& hs, int32_t G) {
+    host_band_layout(hs, G);
+    const int32_t p = hs.p;
+    const std::vector<int32_t>& bw = hs.band_w;
+    hs.bfac.assign(hs.bfac_len, 0.0);
     int bad = -1;
 #pragma omp parallel for schedule(dynamic, 1)
     for (int32_t i = 0; i < p; ++i) {

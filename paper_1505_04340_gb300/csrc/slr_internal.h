@@ -130,6 +130,8 @@ struct HostSetup {
     std::vector<int32_t> et_rp, et_ci; std::vector<double> et_v;  // E^T (s x nI)
     std::vector<int32_t> c_rp, c_ci;  std::vector<double> c_v;    // C   (s x s)
     std::vector<BandBlock> band;
+    std::vector<int32_t> band_w;          // half-bandwidth of each B_i
+    int64_t bfac_len = 0;                 // elements of the packed band factor (one precision)
     std::vector<double> bfac;
     int32_t wmax = 0;
     int32_t band_G = 1;   // CTAs (slices) per subdomain in the band solve
@@ -147,6 +149,9 @@ slr_status host_validate_csr(int32_t n, const int32_t* rowptr, const int32_t* co
                              const double* val, int32_t nparts, const int32_t* part);
 slr_status host_split_blocks(const int32_t* rowptr, const int32_t* colind, const double* val,
                              HostSetup& hs);
+// Plane geometry and slice layout of every B_i for G CTAs per subdomain (band,
+// band_w, wmax, band_G, bfac_len); host_band_factor then factors and packs on the host.
+void host_band_layout(HostSetup& hs, int32_t G);
 slr_status host_band_factor(HostSetup& hs, int32_t G);
 slr_status host_c_factor(HostSetup& hs, int32_t leaf, int32_t task_rows);
 // Lowest level of the top zone within the entry and multiply-add budgets (nlev: no zone).

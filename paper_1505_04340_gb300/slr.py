@@ -37,7 +37,7 @@ class Opts(C.Structure):
     _fields_ = [("k", C.c_int32), ("lanczos_steps", C.c_int32), ("theta_mode", C.c_int32),
                 ("precision", C.c_int32), ("nrhs_max", C.c_int32), ("flexible_cg", C.c_int32),
                 ("seed", C.c_uint64), ("c_leaf", C.c_int32), ("verbose", C.c_int32),
-                ("reserved", C.c_int32 * 8)]
+                ("reserved", C.c_int32 * 16)]
 
 
 class Info(C.Structure):
@@ -49,7 +49,7 @@ class Info(C.Structure):
         ("theta_mode", C.c_int32), ("band_split", C.c_int32), ("band_slots", C.c_int32),
         ("c_persistent", C.c_int32), ("tuned", C.c_int32), ("tune_seconds", C.c_double),
         ("band_threads", C.c_int32), ("c_top_levels", C.c_int32), ("c_top_positions", C.c_int32),
-        ("c_top_entries", C.c_int64)]
+        ("c_top_entries", C.c_int64), ("band_on_device", C.c_int32), ("lanczos_seconds", C.c_double * 3)]
 
 
 class SLRError(RuntimeError):
@@ -163,7 +163,7 @@ class SLR:
     def __init__(self, rowptr, colind, val, part, nparts, k=16, lanczos_steps=0, theta="lambda_k1",
                  precision="fp64", nrhs_max=1, flexible_cg=False, seed=1, c_leaf=64, verbose=False,
                  band_split=0, host_loop=False, band_slots=0, c_persistent=False, autotune=False, target_kappa=0,
-                 band_threads=0, c_top_zone=True, stream=None):
+                 band_threads=0, c_top_zone=True, band_factor="auto", stream=None):
         lib = load()
         self._lib = lib
         self._h = None
@@ -181,6 +181,7 @@ class SLR:
         o.reserved[5] = int(target_kappa)        # rank by the rule lambda_{k+1} <= 1 - 1/K (0 = off)
         o.reserved[6] = int(band_threads)        # threads per band-solve CTA: 512, 256 or 0 (automatic)
         o.reserved[7] = 0 if c_top_zone else 1   # explicit inverse of the factor's top levels
+        o.reserved[8] = {"auto": 0, "host": 1}[band_factor]   # B_i factored on the device or the host
         self.rowptr, self.colind = _i32(rowptr), _i32(colind)
         self.val = np.ascontiguousarray(val, dtype=np.float64)
         self.part = _i32(part)
@@ -219,6 +220,7 @@ class SLR:
         _check(self._lib.slr_get_info(self._h, C.byref(inf)), "slr_get_info")
         d = {f: getattr(inf, f) for f, _ in Info._fields_}
         d["setup_seconds"] = list(inf.setup_seconds)
+        d["lanczos_seconds"] = list(inf.lanczos_seconds)
         return d
 
     def perm(self):

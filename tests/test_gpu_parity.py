@@ -78,16 +78,57 @@ def gpu_handle(P, precision="fp64", nrhs_max=4, theta="lambda_k1", **kw):
 
 @pytest.mark.parametrize("name", list(PROBLEMS))
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_bsolve_parity(name, precision):
+@pytest.mark.parametrize("factor", ["auto", "host"])
+def test_bsolve_parity(name, precision, factor):
+    """B^{-1} with the B_i factored on the device (planes up to 256 wide; the 324-wide
+    3-D case falls back to the host) and on the host."""
     P = make(name)
     o = oracle(name)
-    g = gpu_handle(P, precision)
+    g = gpu_handle(P, precision, band_factor=factor)
+    inf = g.get_info()
+    W = max(b for b in slrgen_plane_widths(P))
+    assert inf["band_on_device"] == (1 if factor == "auto" and 0 < W <= 256 else 0)
     assert np.array_equal(g.perm(), o.order.perm)
     nI = o.order.n_I
     f = np.random.default_rng(1).standard_normal((nI, 3))
     t = g.bsolve(cu(f)).cpu().numpy()
     want = o.bsolve.solve(f)
     assert rel(t, want) <= (TOL64 if precision == "fp64" else TOL32)
+
+
+def slrgen_plane_widths(P):
+    """Half-bandwidth of each B_i in DD order (natural order inside each box)."""
+    A = sp.csr_matrix((P.val, P.colind, P.rowptr))
+    out = [0]
+    for q in range(P.nparts):
+        idx = np.flatnonzero(P.part == q)
+        inner = [i for i in idx if all(P.part[j] == q for j in A.indices[A.indptr[i]:A.indptr[i + 1]])]
+        if not inner:
+            continue
+        B = A[sorted(inner)][:, sorted(inner)].tocoo()
+        out.append(int(np.max(np.abs(B.row - B.col))) if B.nnz else 0)
+    return out
+
+
+def test_device_band_factor_matches_host_factor():
+    """The device factorization and the host's band Cholesky give the same B solves
+    to rounding (both exact Cholesky factors, different operation orders)."""
+    P = make("3d-lap")
+    f = cu(np.random.default_rng(5).standard_normal((gpu_handle(P).info["n_interior"], 2)))
+    td = gpu_handle(P, band_factor="auto").bsolve(f).cpu().numpy()
+    th = gpu_handle(P, band_factor="host").bsolve(f).cpu().numpy()
+    assert rel(td, th) <= 1e-12
+
+
+def test_device_band_factor_detects_non_spd_block():
+    from paper_1505_04340_gb300.slr import SLRError
+    rp, ci, v = slrgen.laplacian((6, 5))
+    v = v.copy()
+    diag = np.array([q for i in range(30) for q in range(rp[i], rp[i + 1]) if ci[q] == i])
+    v[diag[7]] = -4.0                                # an interior node of part 0 loses positivity
+    part = slrgen.box_partition((6, 5), (2, 1))
+    with pytest.raises(SLRError, match="SLR_ERR_NOT_SPD"):
+        SLR(rp, ci, v, part, 2, k=2, lanczos_steps=4)
 
 
 @pytest.mark.parametrize("name,split,slots,nt", [("3d-196", 2, 5, 512), ("3d-196", 4, 5, 512), ("3d-196", 1, 2, 512),
