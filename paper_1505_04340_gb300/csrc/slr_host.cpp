@@ -14,11 +14,12 @@
 //                         with a level schedule for the device solves
 //  * host_c_top         - explicit inverse of the factor's top levels (partitioned
 //                         inverse) for one-step solves of that zone
-//  * host_tridiag_eig   - eigenpairs of the Lanczos tridiagonal (Section 5.1)
+//  * host_tridiag_eig   - eigenpairs of the Lanczos tridiagonal (Section 5.1), implicit QL
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <limits>
 #include <map>
 #include <numeric>
 #include <string>
@@ -187,6 +188,8 @@ slr_status host_split_blocks(const int32_t* rowptr, const int32_t* colind, const
 // Lower-triangular inverse of the W x W matrix D (row-major), into X (row-major).
 static void tri_inverse(int W, const double* D, double* X) {
     for (int i = 0; i < W * W; ++i) X[i] = 0.0;
+    // columns are independent: threads share a large block (serial inside a parallel region)
+#pragma omp parallel for schedule(dynamic, 4) if (W >= 256)
     for (int c = 0; c < W; ++c) {
         X[c * W + c] = 1.0 / D[c * W + c];
         for (int r = c + 1; r < W; ++r) {
@@ -499,6 +502,48 @@ struct NestedDissection {
 
 }  // namespace
 
+// In-place Cholesky of the lower triangle of the n x n row-major block F (leading
+// dimension n); false on a non-positive pivot.  Right-looking in 64-column
+// panels: the panel below and the trailing update run in parallel over rows.
+static bool chol_blocked(double* F, int32_t n) {
+    const int32_t nb = 64;
+    for (int32_t k0 = 0; k0 < n; k0 += nb) {
+        const int32_t k1 = std::min(n, k0 + nb);
+        for (int32_t i = k0; i < k1; ++i) {   // diagonal block (earlier panels applied)
+            double* Fi = F + (int64_t)i * n;
+            for (int32_t j = k0; j <= i; ++j) {
+                const double* Fr = F + (int64_t)j * n;
+                double sum = Fi[j];
+                for (int32_t k = k0; k < j; ++k) sum -= Fi[k] * Fr[k];
+                if (j < i) Fi[j] = sum / Fr[j];
+                else if (sum > 0.0) Fi[i] = std::sqrt(sum);
+                else return false;
+            }
+        }
+#pragma omp parallel for schedule(static) if ((int64_t)(n - k1) * (k1 - k0) > 8192)
+        for (int32_t i = k1; i < n; ++i) {   // panel rows: L[i, k0:k1] = F[i, k0:k1] L_kk^{-T}
+            double* Fi = F + (int64_t)i * n;
+            for (int32_t j = k0; j < k1; ++j) {
+                const double* Fr = F + (int64_t)j * n;
+                double sum = Fi[j];
+                for (int32_t k = k0; k < j; ++k) sum -= Fi[k] * Fr[k];
+                Fi[j] = sum / Fr[j];
+            }
+        }
+#pragma omp parallel for schedule(dynamic, 8) if (n - k1 > 64)
+        for (int32_t i = k1; i < n; ++i) {   // trailing lower triangle
+            double* Fi = F + (int64_t)i * n;
+            for (int32_t j = k1; j <= i; ++j) {
+                const double* Fr = F + (int64_t)j * n;
+                double dot = 0.0;
+                for (int32_t k = k0; k < k1; ++k) dot += Fi[k] * Fr[k];
+                Fi[j] -= dot;
+            }
+        }
+    }
+    return true;
+}
+
 slr_status host_c_factor(HostSetup& hs, int32_t leaf, int32_t task_rows) {
     CFactorHost& cf = hs.cf;
     const int32_t s = hs.s;
@@ -601,7 +646,10 @@ slr_status host_c_factor(HostSetup& hs, int32_t leaf, int32_t task_rows) {
         const int32_t a0 = cf.c0[J], nJ = cf.c0[J + 1] - a0;
         const int64_t nr = cf.r_off[J + 1] - cf.r_off[J];
         double* Fj = F.data() + fo[J];
-        for (int32_t i = 0; i < nJ && bad < 0; ++i) {
+        if (nJ >= 128) {   // large diagonal block: blocked, with parallel panels and updates
+            if (!chol_blocked(Fj, nJ)) bad = J;
+        }
+        for (int32_t i = 0; i < nJ && bad < 0 && nJ < 128; ++i) {
             double* Fi = Fj + (int64_t)i * nJ;
             for (int32_t j = 0; j <= i; ++j) {
                 const double* Fr = Fj + (int64_t)j * nJ;
@@ -661,8 +709,9 @@ slr_status host_c_factor(HostSetup& hs, int32_t leaf, int32_t task_rows) {
     }
     cf.dinv.assign(cf.dinv_off[ns], 0.0);
     cf.panel.assign(cf.pan_off[ns], 0.0);
-#pragma omp parallel for schedule(dynamic, 1)
-    for (int32_t J = 0; J < ns; ++J) {
+    // small supernodes in parallel, large ones (nJ >= 256) one at a time with
+    // parallel loops inside (tri_inverse's columns, M_J's rows)
+    auto inv_and_m = [&](int32_t J) {
         const int32_t nJ = cf.c0[J + 1] - cf.c0[J];
         const int64_t nr = cf.r_off[J + 1] - cf.r_off[J];
         const double* Fj = F.data() + fo[J];
@@ -677,6 +726,7 @@ slr_status host_c_factor(HostSetup& hs, int32_t leaf, int32_t task_rows) {
         // Lhat = L D^{-1}, D = diag(L_JJ), so C = Lhat D D^T Lhat^T (a block LDL^T form)
         const double* Pj = Fj + (int64_t)nJ * nJ;
         double* Mj = cf.panel.data() + cf.pan_off[J];
+#pragma omp parallel for schedule(static) if (nJ >= 256 && nr >= 16)
         for (int64_t pr = 0; pr < nr; ++pr) {
             const double* Lp = Pj + pr * nJ;
             double* Mp = Mj + pr * nJ;
@@ -686,7 +736,12 @@ slr_status host_c_factor(HostSetup& hs, int32_t leaf, int32_t task_rows) {
                 for (int32_t j = 0; j <= k; ++j) Mp[j] += a * Xk[j];
             }
         }
-    }
+    };
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int32_t J = 0; J < ns; ++J)
+        if (cf.c0[J + 1] - cf.c0[J] < 256) inv_and_m(J);
+    for (int32_t J = 0; J < ns; ++J)
+        if (cf.c0[J + 1] - cf.c0[J] >= 256) inv_and_m(J);
     // forward gather lists: row i of L left of its diagonal block is the union of
     // the panel rows R_K[p] = i of its descendants K
     cf.seg_ptr.assign(s + 1, 0);
@@ -968,55 +1023,67 @@ void host_c_top(CFactorHost& cf, int32_t top_lev) {
 
 // ------------------------------------------------------------------ Section 5.1: T = Y diag(lam) Y^T
 
+// Implicit QL iteration with Wilkinson shifts on the symmetric tridiagonal T
+// (Bowdler, Martin, Reinsch & Wilkinson, 1968): each sweep chases a bulge up from
+// the bottom of the unreduced block with Givens rotations, which are accumulated
+// into the eigenvector rows; a sub-diagonal entry below eps (|d_i| + |d_{i+1}|)
+// splits the matrix.  O(m^2) work per eigenvalue with its vector.
 void host_tridiag_eig(int32_t m, const double* alpha, const double* beta, double* lam, double* Y) {
-    // cyclic Jacobi on the dense symmetric T; A row-major, V accumulates rotations
-    std::vector<double> A((size_t)m * m, 0.0), V((size_t)m * m, 0.0);
-    for (int32_t i = 0; i < m; ++i) {
-        A[(size_t)i * m + i] = alpha[i];
-        V[(size_t)i * m + i] = 1.0;
-        if (i + 1 < m) A[(size_t)i * m + i + 1] = A[(size_t)(i + 1) * m + i] = beta[i];
-    }
-    double scale = 0.0;
-    for (int32_t i = 0; i < m * m; ++i) scale += A[i] * A[i];
-    for (int sweep = 0; sweep < 100; ++sweep) {
-        double off = 0.0;
-        for (int32_t i = 0; i < m; ++i)
-            for (int32_t j = i + 1; j < m; ++j) off += A[(size_t)i * m + j] * A[(size_t)i * m + j];
-        if (off <= 1e-32 * scale) break;
-        for (int32_t p = 0; p < m; ++p)
-            for (int32_t q = p + 1; q < m; ++q) {
-                double apq = A[(size_t)p * m + q];
-                if (std::fabs(apq) < 1e-300) continue;
-                double app = A[(size_t)p * m + p], aqq = A[(size_t)q * m + q];
-                // rotation angle phi with tan(2 phi) = 2 a_pq / (a_qq - a_pp); t = tan(phi)
-                double tau = (aqq - app) / (2.0 * apq);
-                double t = (tau >= 0 ? 1.0 : -1.0) / (std::fabs(tau) + std::sqrt(1.0 + tau * tau));
-                double c = 1.0 / std::sqrt(1.0 + t * t), sn = t * c;
-                for (int32_t k = 0; k < m; ++k) {   // A <- A G (columns p, q)
-                    double akp = A[(size_t)k * m + p], akq = A[(size_t)k * m + q];
-                    A[(size_t)k * m + p] = c * akp - sn * akq;
-                    A[(size_t)k * m + q] = sn * akp + c * akq;
+    if (m <= 0) return;
+    std::vector<double> d(alpha, alpha + m), e(m, 0.0);
+    for (int32_t i = 0; i + 1 < m; ++i) e[i] = beta[i];   // e[i] couples d[i] and d[i+1]
+    std::vector<double> Z((size_t)m * m, 0.0);             // row i: eigenvector of d[i]
+    for (int32_t i = 0; i < m; ++i) Z[(size_t)i * m + i] = 1.0;
+    const double eps = std::numeric_limits<double>::epsilon();
+    for (int32_t l = 0; l < m; ++l) {
+        for (int iter = 0; iter < 60; ++iter) {
+            int32_t q = l;   // end of the unreduced block that starts at l
+            while (q + 1 < m && std::fabs(e[q]) > eps * (std::fabs(d[q]) + std::fabs(d[q + 1]))) ++q;
+            if (q == l) break;
+            // shift: the eigenvalue of the leading 2 x 2 block nearer d[l]
+            double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
+            double r = std::hypot(g, 1.0);
+            g = d[q] - d[l] + e[l] / (g + (g >= 0.0 ? r : -r));
+            double sn = 1.0, cs = 1.0, p = 0.0;
+            int32_t i = q - 1;
+            bool split = false;
+            for (; i >= l; --i) {
+                const double f = sn * e[i], bb = cs * e[i];
+                r = std::hypot(f, g);
+                e[i + 1] = r;
+                if (r == 0.0) {   // the rotation vanished: the block splits at i + 1
+                    d[i + 1] -= p;
+                    e[q] = 0.0;
+                    split = true;
+                    break;
                 }
-                for (int32_t k = 0; k < m; ++k) {   // A <- G^T A (rows p, q)
-                    double apk = A[(size_t)p * m + k], aqk = A[(size_t)q * m + k];
-                    A[(size_t)p * m + k] = c * apk - sn * aqk;
-                    A[(size_t)q * m + k] = sn * apk + c * aqk;
-                }
-                for (int32_t k = 0; k < m; ++k) {   // V <- V G
-                    double vkp = V[(size_t)k * m + p], vkq = V[(size_t)k * m + q];
-                    V[(size_t)k * m + p] = c * vkp - sn * vkq;
-                    V[(size_t)k * m + q] = sn * vkp + c * vkq;
+                sn = f / r;
+                cs = g / r;
+                g = d[i + 1] - p;
+                r = (d[i] - g) * sn + 2.0 * cs * bb;
+                p = sn * r;
+                d[i + 1] = g + p;
+                g = cs * r - bb;
+                double* zi = Z.data() + (size_t)i * m;
+                double* zj = zi + m;
+                for (int32_t k = 0; k < m; ++k) {
+                    const double zk = zj[k];
+                    zj[k] = sn * zi[k] + cs * zk;
+                    zi[k] = cs * zi[k] - sn * zk;
                 }
             }
+            if (split) continue;
+            d[l] -= p;
+            e[l] = g;
+            e[q] = 0.0;
+        }
     }
     std::vector<int32_t> idx(m);
     std::iota(idx.begin(), idx.end(), 0);
-    std::stable_sort(idx.begin(), idx.end(), [&](int32_t a, int32_t b) {
-        return A[(size_t)a * m + a] > A[(size_t)b * m + b];
-    });
+    std::stable_sort(idx.begin(), idx.end(), [&](int32_t a, int32_t b) { return d[a] > d[b]; });
     for (int32_t j = 0; j < m; ++j) {
-        lam[j] = A[(size_t)idx[j] * m + idx[j]];
-        for (int32_t i = 0; i < m; ++i) Y[(size_t)j * m + i] = V[(size_t)i * m + idx[j]];
+        lam[j] = d[idx[j]];
+        std::memcpy(Y + (size_t)j * m, Z.data() + (size_t)idx[j] * m, sizeof(double) * m);
     }
 }
 

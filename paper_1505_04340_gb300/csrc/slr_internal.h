@@ -159,7 +159,7 @@ int32_t host_c_top_choose(const CFactorHost& cf);
 // Builds the top zone from level top_lev up (no zone when top_lev >= nlev or
 // when the zone's subtrees are not contiguous in the factor order).
 void host_c_top(CFactorHost& cf, int32_t top_lev);
-// Symmetric eigen-decomposition of the m x m tridiagonal T (Jacobi rotations):
+// Symmetric eigen-decomposition of the m x m tridiagonal T (implicit QL):
 // eigenvalues descending in lam[m], eigenvectors as columns of Y (column-major m x m).
 void host_tridiag_eig(int32_t m, const double* alpha, const double* beta, double* lam, double* Y);
 // SplitMix64 output i (0-based) of stream seed, as a double in [-1, 1).
