@@ -21,6 +21,9 @@ Every step is written in the paper's order and notation, slow and direct:
 * ``SLR.stilde_inv_zform`` - the same S~^{-1} through Proposition 4.3 (Eq. 4.15)
 * ``pcg``           - preconditioned CG, stop at ||r|| <= 1e-8 ||b||, 300 its
                                                                (Section 6)
+* ``gmres``         - right-preconditioned GMRES(40) for the symmetric indefinite
+                      problems of Section 6 (B_i may be indefinite, C is SPD:
+                      the SPD-interface assumption of Section 1)
 
 Readings where the paper is silent (they are listed with reasons in the design
 notes):  the Lanczos start vector is v_1 = L^{-1} C z / ||L^{-1} C z|| (= L^T z
@@ -143,11 +146,34 @@ class BandCholesky:
         return sla.cho_solve_banded((self.cb, True), f)
 
 
-class BSolver:
-    """t = B^{-1} f as p independent solves (Section 5.2)."""
+class BandLU:
+    """Direct solver for one symmetric, possibly indefinite block B_i: LAPACK's
+    banded LU with partial pivoting (dgbsv) on the full band.  An independent
+    method from any symmetric factorisation; used when A is indefinite."""
 
-    def __init__(self, Bi, int_off):
-        self.blocks = [BandCholesky(b) for b in Bi]
+    def __init__(self, Bi):
+        m = Bi.shape[0]
+        self.m = m
+        if m == 0:
+            self.w = 0
+            return
+        coo = Bi.tocoo()
+        self.w = w = int(np.max(np.abs(coo.row - coo.col))) if coo.nnz else 0
+        self.ab = np.zeros((2 * w + 1, m))      # ab[w + i - j, j] = B[i, j]
+        self.ab[w + coo.row - coo.col, coo.col] = coo.data
+
+    def solve(self, f):
+        if self.m == 0:
+            return f.copy()
+        return sla.solve_banded((self.w, self.w), self.ab, f)
+
+
+class BSolver:
+    """t = B^{-1} f as p independent solves (Section 5.2); ``indefinite`` takes
+    banded LU instead of banded Cholesky."""
+
+    def __init__(self, Bi, int_off, indefinite=False):
+        self.blocks = [BandLU(b) if indefinite else BandCholesky(b) for b in Bi]
         self.off = int_off
 
     def solve(self, f):
@@ -301,11 +327,13 @@ class SLR:
     """
 
     def __init__(self, rowptr, colind, val, part, nparts, k, lanczos_steps=None,
-                 theta_mode=THETA_LAMBDA_K1, seed=1, eig="lanczos", c_route="auto", target_kappa=None):
+                 theta_mode=THETA_LAMBDA_K1, seed=1, eig="lanczos", c_route="auto", target_kappa=None,
+                 indefinite=False):
         self.order = dd_order(rowptr, colind, part, nparts)
         Bi, E, C, App = split_blocks(rowptr, colind, val, self.order)
         self.E, self.C, self.App = E, C, App
-        self.bsolve = BSolver(Bi, self.order.int_off)
+        self.indefinite = indefinite
+        self.bsolve = BSolver(Bi, self.order.int_off, indefinite)
         self.cfac = CFactor(C, c_route)
         s = self.order.s
         self.k = k = int(min(k, s))
@@ -333,9 +361,11 @@ class SLR:
         self.ritz_values = lam
         self.lam = lam[:k].copy()
         self.U = U[:, :k].copy()
-        if theta_mode == THETA_LAMBDA_K1 and len(lam) > k:
+        if theta_mode == THETA_LAMBDA_K1 and len(lam) > k and lam[k] < 1.0:
             self.theta = float(lam[k])
         else:
+            # theta = 0 (Eq. 4.10); with an indefinite B, H can have eigenvalues >= 1, and
+            # theta = lambda_{k+1} >= 1 would flip the sign of the C^{-1} term of Eq. 4.7
             self.theta = 0.0
 
     # -- Section 5.3: improve the preconditioner by adding vectors, keeping U_k
@@ -459,6 +489,72 @@ def pcg(A, b, minv, tol=1e-8, maxit=300):
         p = z + (rho_new / rho) * p
         rho = rho_new
     return x, maxit, np.linalg.norm(r) / bnorm, False
+
+
+def gmres(A, b, minv, tol=1e-8, maxit=300, restart=40):
+    """Right-preconditioned GMRES(restart) from x_0 = 0 for one right-hand side
+    (Saad & Schultz 1986): Arnoldi on A M^{-1} with modified Gram-Schmidt, the
+    least-squares problem by Givens rotations, x = M^{-1} (V y) at each restart
+    or at convergence.  Stops when the residual estimate ||r_j|| <= tol ||b||
+    (with right preconditioning it is the residual of A x = b); at most
+    ``maxit`` products with A.  Returns (x, iterations, ||b - A x||/||b||,
+    converged)."""
+    n = len(b)
+    x = np.zeros_like(b)
+    bnorm = np.linalg.norm(b)
+    if bnorm == 0.0:
+        return x, 0, 0.0, True
+    its = 0
+    while True:
+        r = b - A @ x
+        beta = np.linalg.norm(r)
+        if beta <= tol * bnorm or its >= maxit:
+            return x, its, beta / bnorm, beta <= tol * bnorm
+        m = restart
+        V = np.zeros((n, m + 1))
+        Hh = np.zeros((m + 1, m))
+        cs, sn = np.zeros(m), np.zeros(m)
+        g = np.zeros(m + 1)
+        g[0] = beta
+        V[:, 0] = r / beta
+        j_done = 0
+        for j in range(m):
+            w = A @ minv(V[:, j])
+            its += 1
+            for i in range(j + 1):                       # modified Gram-Schmidt
+                Hh[i, j] = V[:, i] @ w
+                w = w - Hh[i, j] * V[:, i]
+            Hh[j + 1, j] = np.linalg.norm(w)
+            if Hh[j + 1, j] > 0.0:
+                V[:, j + 1] = w / Hh[j + 1, j]
+            for i in range(j):                           # earlier rotations on the new column
+                t = cs[i] * Hh[i, j] + sn[i] * Hh[i + 1, j]
+                Hh[i + 1, j] = -sn[i] * Hh[i, j] + cs[i] * Hh[i + 1, j]
+                Hh[i, j] = t
+            d = np.hypot(Hh[j, j], Hh[j + 1, j])         # new rotation zeroes H[j+1, j]
+            cs[j], sn[j] = (Hh[j, j] / d, Hh[j + 1, j] / d) if d > 0.0 else (1.0, 0.0)
+            Hh[j, j] = d
+            Hh[j + 1, j] = 0.0
+            g[j + 1] = -sn[j] * g[j]
+            g[j] = cs[j] * g[j]
+            j_done = j + 1
+            if abs(g[j + 1]) <= tol * bnorm or its >= maxit:
+                break
+        y = sla.solve_triangular(Hh[:j_done, :j_done], g[:j_done])
+        x = x + minv(V[:, :j_done] @ y)
+
+
+def slr_gmres(slr: SLR, b, tol=1e-8, maxit=300, restart=40):
+    """Solve A x = b (original order) with SLR-preconditioned GMRES(restart) in DD order."""
+    xs, its, rels, oks = [], [], [], []
+    b2 = b.reshape(len(b), -1)
+    for j in range(b2.shape[1]):
+        x, it, rel, ok = gmres(slr.App, slr.to_dd(b2[:, j]), slr.apply, tol, maxit, restart)
+        xs.append(slr.from_dd(x))
+        its.append(it)
+        rels.append(rel)
+        oks.append(ok)
+    return np.stack(xs, axis=1).reshape(b.shape), its, rels, oks
 
 
 def slr_pcg(slr: SLR, b, tol=1e-8, maxit=300):

@@ -194,12 +194,13 @@ class Problem:
 
 
 def make_problem(name, dims, boxes, k, *, kind="laplacian", coef=None, coef_range=None,
-                 nrhs=1, matrix_seed=1, rhs_seed=2, lanczos_steps=None):
+                 nrhs=1, matrix_seed=1, rhs_seed=2, lanczos_steps=None, shift=0.0):
     """Build a Problem; ``kind`` is 'laplacian' (constant axis coefficients) or 'fv'.
 
     x* column j is uniform[-1,1) from stream ``rhs_seed + j``; b = A x*.
     For 'fv' the cell coefficients are log-uniform in ``coef_range`` from
-    stream ``matrix_seed``.
+    stream ``matrix_seed``.  ``shift`` s > 0 subtracts s I (the shifted,
+    symmetric indefinite problems of Section 6: -Laplacian u - c u = f).
     """
     dims = tuple(int(d) for d in dims)
     n = int(np.prod(dims))
@@ -210,6 +211,10 @@ def make_problem(name, dims, boxes, k, *, kind="laplacian", coef=None, coef_rang
         rowptr, colind, val = diffusion_fv(dims, loguniform(matrix_seed, n, lo, hi))
     else:
         raise ValueError(kind)
+    if shift:
+        val = val.copy()
+        rows = np.repeat(np.arange(n), np.diff(rowptr))
+        val[colind == rows] -= shift
     part = box_partition(dims, boxes)
     xstar = np.stack([uniform_pm1(rhs_seed + j, n) for j in range(nrhs)], axis=1)
     b = csr_matvec(rowptr, colind, val, xstar)
@@ -217,7 +222,7 @@ def make_problem(name, dims, boxes, k, *, kind="laplacian", coef=None, coef_rang
                    nparts=int(np.prod(boxes)), k=int(k),
                    lanczos_steps=int(lanczos_steps if lanczos_steps is not None else 5 * k),
                    xstar=xstar, b=np.ascontiguousarray(b),
-                   meta=dict(boxes=tuple(boxes), kind=kind, coef=coef, coef_range=coef_range))
+                   meta=dict(boxes=tuple(boxes), kind=kind, coef=coef, coef_range=coef_range, shift=shift))
 
 
 # The five workloads (grid, partition, rank, right-hand sides).

@@ -13,8 +13,8 @@ import scipy.sparse as sp
 
 import slrgen
 from oracle import brute
-from oracle.slr_oracle import (SLR, THETA_LAMBDA_K1, THETA_ZERO, BandCholesky, BSolver, CFactor,
-                               dd_order, h_apply, lanczos, pcg, ritz, slr_pcg, split_blocks)
+from oracle.slr_oracle import (SLR, THETA_LAMBDA_K1, THETA_ZERO, BandCholesky, BandLU, BSolver, CFactor,
+                               dd_order, gmres, h_apply, lanczos, pcg, ritz, slr_gmres, slr_pcg, split_blocks)
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -424,3 +424,125 @@ def test_lanczos_three_term_recurrence_without_reorth():
     T = np.diag(a) + np.diag(b[:-1], 1) + np.diag(b[:-1], -1)
     assert np.allclose(V.T @ H @ V, T, atol=1e-12)
     assert np.allclose(V.T @ V, np.eye(6), atol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# Symmetric indefinite problems (Section 6, -Laplacian u - c u = f; SPD interface
+# assumed, Section 1) and the GMRES(40) accelerator
+# ---------------------------------------------------------------------------
+
+def _shifted(dims, boxes, shift, k=8):
+    return slrgen.make_problem("shifted", dims, boxes, k, shift=shift)
+
+
+def test_shifted_problem_is_indefinite_with_spd_interface():
+    """The test workload: A has negative eigenvalues, C (interface) is SPD and some B_i
+    are indefinite, so the B solves need a symmetric indefinite factorisation."""
+    P = _shifted((32, 32), (2, 2), 0.2)
+    slr = SLR(P.rowptr, P.colind, P.val, P.part, P.nparts, 4, indefinite=True)
+    B, E, C = brute.dense_blocks(slr)
+    assert np.linalg.eigvalsh(slr.App.toarray()).min() < 0
+    assert np.linalg.eigvalsh(C).min() > 0
+    assert np.linalg.eigvalsh(B).min() < 0
+
+
+@pytest.mark.parametrize("m,w", [(40, 3), (64, 8)])
+def test_band_lu_solve_vs_dense_indefinite(m, w):
+    rng = np.random.default_rng(m)
+    D = np.zeros((m, m))
+    for d in range(1, w + 1):
+        v = rng.standard_normal(m - d)
+        D += np.diag(v, d) + np.diag(v, -d)
+    D += np.diag(rng.uniform(-2, 2, m))                      # symmetric, indefinite
+    f = rng.standard_normal((m, 3))
+    got = BandLU(sp.csr_matrix(D)).solve(f)
+    assert np.allclose(got, np.linalg.solve(D, f), rtol=1e-10, atol=1e-10)
+
+
+def test_gmres_solves_nonsymmetric_system_and_restarts():
+    rng = np.random.default_rng(3)
+    n = 60
+    A = np.eye(n) * 4 + rng.standard_normal((n, n)) * 0.4
+    b = rng.standard_normal(n)
+    want = np.linalg.solve(A, b)
+    for restart in (60, 7):                                    # full and restarted
+        x, its, rel, ok = gmres(sp.csr_matrix(A), b, lambda v: v, tol=1e-10, maxit=2000, restart=restart)
+        assert ok and rel <= 1e-10
+        assert np.linalg.norm(A @ x - b) / np.linalg.norm(b) == pytest.approx(rel, rel=1e-6)
+        assert np.allclose(x, want, rtol=1e-8, atol=1e-9)
+    # without restarts GMRES terminates in at most n steps (exact arithmetic: the Krylov space is full)
+    _, its, _, ok = gmres(sp.csr_matrix(A), b, lambda v: v, tol=1e-10, maxit=2000, restart=n)
+    assert ok and its <= n
+    # an exact preconditioner: one step
+    Ainv = np.linalg.inv(A)
+    _, its, rel, ok = gmres(sp.csr_matrix(A), b, lambda v: Ainv @ v, tol=1e-10)
+    assert ok and its == 1
+
+
+def test_gmres_minimises_residual_over_krylov_space():
+    """At step j the GMRES iterate minimises ||b - A x|| over x in K_j (checked by a
+    dense least-squares problem on the Krylov basis)."""
+    rng = np.random.default_rng(4)
+    n = 30
+    A = np.diag(np.linspace(-1, 3, n)) + 0.1 * rng.standard_normal((n, n))
+    b = rng.standard_normal(n)
+    for j in (3, 8):
+        x, its, rel, _ = gmres(sp.csr_matrix(A), b, lambda v: v, tol=1e-14, maxit=j, restart=40)
+        K = np.stack([np.linalg.matrix_power(A, i) @ b for i in range(j)], axis=1)
+        y, *_ = np.linalg.lstsq(A @ K, b, rcond=None)
+        best = np.linalg.norm(b - A @ K @ y) / np.linalg.norm(b)
+        assert its == j and rel == pytest.approx(best, rel=1e-6)
+
+
+@pytest.mark.parametrize("theta_mode", [THETA_LAMBDA_K1, THETA_ZERO])
+def test_prop_eigSS_indefinite(theta_mode):
+    """Proposition 4.1 is algebraic (S = L(I - H)L^T for any symmetric H): with an
+    indefinite B, eig(S S~^{-1}) is still 1 (i <= k) and (1 - lambda_i)/(1 - theta)."""
+    P = _shifted((24, 24), (2, 2), 0.3)
+    k = 5
+    slr = SLR(P.rowptr, P.colind, P.val, P.part, P.nparts, k, theta_mode=theta_mode, eig="dense", indefinite=True)
+    B, E, C = brute.dense_blocks(slr)
+    lam = np.sort(np.linalg.eigvalsh(brute.h_from_blocks(B, E, C)))[::-1]
+    assert lam[0] > 1.0                                        # H has eigenvalues above 1
+    S = brute.schur(B, E, C)
+    sig = np.sort(np.linalg.eigvals(S @ slr.stilde_inv(np.eye(S.shape[0]))).real)
+    theta = slr.theta
+    assert theta == pytest.approx(lam[k] if (theta_mode == THETA_LAMBDA_K1 and lam[k] < 1) else 0.0)
+    want = np.sort(np.concatenate([np.ones(k), (1 - lam[k:]) / (1 - theta)]))
+    assert np.allclose(sig, want, rtol=1e-8, atol=1e-9)
+
+
+def test_theta_falls_back_to_zero_when_lambda_k1_reaches_one():
+    """Reading for the indefinite case: theta = lambda_{k+1} only while it is below 1."""
+    P = _shifted((24, 24), (2, 2), 0.3)
+    slr = SLR(P.rowptr, P.colind, P.val, P.part, P.nparts, 0, eig="dense", indefinite=True)
+    B, E, C = brute.dense_blocks(slr)
+    lam = np.sort(np.linalg.eigvalsh(brute.h_from_blocks(B, E, C)))[::-1]
+    assert lam[0] >= 1.0 and slr.theta == 0.0                  # k = 0: lambda_1 >= 1
+    k = int(np.sum(lam >= 1.0))
+    slr2 = SLR(P.rowptr, P.colind, P.val, P.part, P.nparts, k, eig="dense", indefinite=True)
+    assert slr2.theta == pytest.approx(lam[k])
+
+
+def test_full_rank_indefinite_gives_exact_inverse_and_one_gmres_step():
+    P = _shifted((16, 16), (2, 2), 0.5)
+    slr0 = SLR(P.rowptr, P.colind, P.val, P.part, P.nparts, 0, indefinite=True)
+    s = slr0.order.s
+    slr = SLR(P.rowptr, P.colind, P.val, P.part, P.nparts, s, eig="dense", indefinite=True)
+    A = slr.App.toarray()
+    M = np.stack([slr.apply(e) for e in np.eye(A.shape[0])], axis=1)
+    assert np.allclose(M @ A, np.eye(A.shape[0]), atol=1e-9)
+    x, its, rel, oks = slr_gmres(slr, P.b[:, 0])
+    assert its[0] == 1 and oks[0]
+
+
+def test_slr_gmres_converges_on_shifted_problem_and_rank_helps():
+    P = _shifted((32, 32), (2, 2), 0.2)
+    res = {}
+    for k in (0, 8):
+        slr = SLR(P.rowptr, P.colind, P.val, P.part, P.nparts, k, indefinite=True)
+        x, its, rels, oks = slr_gmres(slr, P.b[:, 0])
+        assert oks[0] and rels[0] <= 1e-8
+        assert np.linalg.norm(x - P.xstar[:, 0]) / np.linalg.norm(P.xstar[:, 0]) < 1e-5
+        res[k] = its[0]
+    assert res[8] < res[0]
