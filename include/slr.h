@@ -100,7 +100,13 @@ typedef struct {
                                reserved[8]: where the B_i are factored (Section 5.2):
                                0 (default) = on the device when every plane is at most
                                256 rows wide, else on the host; 1 = on the host.
-                               reserved[9..15] must be 0.                              */
+                               reserved[9]: 1 = A is symmetric indefinite with an SPD
+                               interface matrix C (Section 1; the shifted problems of
+                               Section 6): each B_i is factored as L S L^T with S the
+                               pivot signs (no pivoting; a zero pivot returns
+                               SLR_ERR_BREAKDOWN), H may have eigenvalues >= 1, and the
+                               accelerator is slr_gmres_solve.  0 = SPD.
+                               reserved[10..15] must be 0.                             */
 } slr_opts;
 
 typedef struct {
@@ -164,6 +170,23 @@ slr_status slr_apply(slr_handle h, const double* r_dev, double* z_dev, int32_t n
 slr_status slr_pcg_solve(slr_handle h, const double* b_dev, double* x_dev, int32_t nrhs, int32_t ld,
                          double tol, int32_t maxit, void* stream, int32_t* iters_out,
                          double* relres_out);
+
+/* Solve A x = b with SLR-preconditioned GMRES(restart) (Section 6: GMRES(40) for
+ * the symmetric indefinite problems, slr_opts.reserved[9] = 1; it works for SPD A
+ * too).  Flexible right preconditioning: z_j = M^{-1} v_j are kept and
+ * x = x_0 + Z_j y, so an FP32 apply (varying by rounding) does not spoil the
+ * minimal-residual property.  Arnoldi orthogonalises by two classical
+ * Gram-Schmidt passes; the Hessenberg least-squares problem is solved on the
+ * host by Givens rotations.  x_0 = 0; a column stops when the residual estimate
+ * satisfies ||r|| <= tol ||b|| or after maxit products with A; relres_out[j] is
+ * the true ||b - A x|| / ||b|| at exit.  Columns run one after another.
+ * b_dev, x_dev: n x nrhs FP64 in ORIGINAL order, leading dimension ld; nrhs <=
+ * nrhs_max; 1 <= restart <= 1000.  iters_out[nrhs], relres_out[nrhs]: host arrays
+ * (may be NULL).  Allocates its Krylov basis (2 restart + 1 vectors of n) per call.
+ * Synchronises stream.  Returns NOT_CONVERGED if a column reached maxit. */
+slr_status slr_gmres_solve(slr_handle h, const double* b_dev, double* x_dev, int32_t nrhs, int32_t ld,
+                           double tol, int32_t maxit, int32_t restart, void* stream, int32_t* iters_out,
+                           double* relres_out);
 
 /* t = B^{-1} f for the interior block (Section 5.2), DD interior order,
  * f_dev/t_dev: n_interior x nrhs FP64, leading dimension ld.  May alias. */

@@ -416,7 +416,9 @@ slr_status run_lanczos(slr_handle h, cudaStream_t st) {
     h->ritz = lam;
     h->nritz = m_eff;
     h->m_steps = m_eff;
-    h->theta = (h->opts.theta_mode == SLR_THETA_LAMBDA_K1 && m_eff > k) ? lam[k] : 0.0;
+    // theta = lambda_{k+1} (Eq. 4.11) while it is below 1; an indefinite B can give H
+    // eigenvalues >= 1, where it would flip the sign of the C^{-1} term: then theta = 0
+    h->theta = (h->opts.theta_mode == SLR_THETA_LAMBDA_K1 && m_eff > k && lam[k] < 1.0) ? lam[k] : 0.0;
     h->lam.assign(lam.begin(), lam.begin() + k);
     CS(dalloc(h, &Yd, (size_t)m_eff * k));
     CK(cudaMemcpyAsync(Yd, Y.data(), sizeof(double) * m_eff * k, cudaMemcpyHostToDevice, st));
@@ -525,7 +527,8 @@ slr_status run_lanczos_deflated(slr_handle h, int32_t k_add, int32_t steps, cuda
     CK(cudaStreamSynchronize(st));
     std::vector<double> lam_new(h->lam);
     lam_new.insert(lam_new.end(), lam2.begin(), lam2.begin() + ja);
-    const double theta = (h->opts.theta_mode == SLR_THETA_LAMBDA_K1 && m_eff > ja) ? lam2[ja] : 0.0;
+    const double theta =
+        (h->opts.theta_mode == SLR_THETA_LAMBDA_K1 && m_eff > ja && lam2[ja] < 1.0) ? lam2[ja] : 0.0;
     {
         std::unique_lock<std::shared_mutex> lk(g_capture_mu);
         drop_graphs(h);
@@ -652,7 +655,7 @@ slr_status device_band_factor(slr_handle h, cudaStream_t st) {
     std::vector<int64_t> soff(p + 1, 0);
     for (int32_t i = 0; i < p; ++i) {
         const BandBlock& b = hs.band[i];
-        soff[i + 1] = soff[i] + (b.m ? (int64_t)(1 + 2 * b.c) * b.w * b.w : 0);
+        soff[i + 1] = soff[i] + (b.m ? (int64_t)(1 + 2 * b.c) * b.w * b.w + (int64_t)b.c * b.w : 0);
     }
     h->bf_scr_len = std::max<int64_t>(soff[p], 1);
     CS(dalloc(h, &h->bf_scr, (size_t)h->bf_scr_len));
@@ -662,13 +665,17 @@ slr_status device_band_factor(slr_handle h, cudaStream_t st) {
     CS(upload(h, &dband, hs.band));
     CS(dalloc(h, &bad, 1));
     CK(cudaMemsetAsync(bad, 0xff, sizeof(int32_t), st));   // -1: no failure
-    CK(launch_band_factor(dband, p, h->a_rp, h->a_ci, h->a_v, h->bf_scr, h->bf_soff, bad, st));
+    CK(launch_band_factor(dband, p, h->a_rp, h->a_ci, h->a_v, h->bf_scr, h->bf_soff, bad, hs.indefinite, st));
     int32_t hb = -1;
     CK(cudaMemcpyAsync(&hb, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     dfree(h, dband, hs.band.size());
     dfree(h, bad, 1);
     if (hb >= 0) {
+        if (hs.indefinite) {
+            set_error("B_" + std::to_string(hb) + " has a zero pivot in its symmetric factorisation");
+            return SLR_ERR_BREAKDOWN;
+        }
         set_error("B_" + std::to_string(hb) + " is not positive definite (Cholesky pivot <= 0)");
         return SLR_ERR_NOT_SPD;
     }
@@ -683,7 +690,7 @@ slr_status device_band_pack(slr_handle h, DevOperator<T>& op, cudaStream_t st) {
     for (const BandBlock& b : hs.band) cmax = std::max(cmax, b.c);
     CS(dalloc(h, &op.bfac, (size_t)hs.bfac_len));
     CK(cudaMemsetAsync(op.bfac, 0, sizeof(T) * hs.bfac_len, st));
-    CK(launch_band_pack<T>(op.band, hs.p, cmax, hs.band_G, h->bf_scr, h->bf_soff, op.bfac, st));
+    CK(launch_band_pack<T>(op.band, hs.p, cmax, hs.band_G, h->bf_scr, h->bf_soff, op.bfac, hs.indefinite, st));
     return SLR_OK;
 }
 
@@ -787,6 +794,7 @@ slr_status setup_impl(slr_handle h, int32_t n, const int32_t* rowptr, const int3
                       int32_t nparts, const int32_t* part, cudaStream_t st) {
     HostSetup& hs = h->hs;
     const bool vb = h->opts.verbose != 0;
+    hs.indefinite = h->opts.reserved[9] == 1;
     double t0 = now_s();
     CS(host_validate_csr(n, rowptr, colind, val, nparts, part));
     CS(host_dd_order(n, rowptr, colind, nparts, part, hs));
@@ -896,7 +904,8 @@ slr_status setup_impl(slr_handle h, int32_t n, const int32_t* rowptr, const int3
             CK(cudaMemsetAsync(tmp, 0, sizeof(double) * hs.bfac_len, st));
             int32_t cmax = 0;
             for (const BandBlock& b : hs.band) cmax = std::max(cmax, b.c);
-            CK(launch_band_pack<double>(h->op32.band, hs.p, cmax, hs.band_G, h->bf_scr, h->bf_soff, tmp, st));
+            CK(launch_band_pack<double>(h->op32.band, hs.p, cmax, hs.band_G, h->bf_scr, h->bf_soff, tmp,
+                                        hs.indefinite, st));
             hs.bfac.assign((size_t)hs.bfac_len, 0.0);
             CK(cudaMemcpyAsync(hs.bfac.data(), tmp, sizeof(double) * hs.bfac_len, cudaMemcpyDeviceToHost, st));
             CK(cudaStreamSynchronize(st));
@@ -1062,6 +1071,115 @@ void drop_graphs(slr_handle h) {
     h->pcg_graphs.clear();
 }
 
+// Section 6 accelerator for the indefinite problems: flexible GMRES(m) on one
+// DD-order column b (device, length n) into x (device), x_0 = 0.  Device work:
+// applies of M^{-1} (kept as Z), products with A, two classical Gram-Schmidt passes
+// and the norm per step (one host read per step); host: the Hessenberg column's
+// Givens rotations and the triangular solve at each restart.
+slr_status gmres_column(slr_handle h, const double* b, double* x, double tol, int32_t maxit, int32_t m,
+                        cudaStream_t st, int32_t* its_out, double* rel_out) {
+    const int32_t n = h->hs.n;
+    const int64_t nn = n;
+    double *V = nullptr, *Z = nullptr, *w = nullptr, *hcol = nullptr, *part = nullptr, *sc = nullptr;
+    CS(dalloc(h, &V, (size_t)nn * (m + 1)));
+    CS(dalloc(h, &Z, (size_t)nn * m));
+    CS(dalloc(h, &w, (size_t)nn));
+    CS(dalloc(h, &hcol, (size_t)2 * (m + 1) + 2));
+    CS(dalloc(h, &part, (size_t)(m + 1) * kRedBlocks));
+    CS(dalloc(h, &sc, 2));
+    auto release = [&]() {
+        dfree(h, V, (size_t)nn * (m + 1));
+        dfree(h, Z, (size_t)nn * m);
+        dfree(h, w, (size_t)nn);
+        dfree(h, hcol, (size_t)2 * (m + 1) + 2);
+        dfree(h, part, (size_t)(m + 1) * kRedBlocks);
+        dfree(h, sc, 2);
+    };
+    slr_status err = SLR_OK;
+    auto norm2 = [&](const double* v) -> double {   // ||v||, synchronising
+        if (launch_dots(nn, 1, v, nn, v, nn, part, sc, 1, st) != cudaSuccess) err = SLR_ERR_CUDA;
+        return std::sqrt(std::max(read_scalar(sc, st, &err), 0.0));
+    };
+    // r = b - A x into w (x = 0: r = b)
+    auto residual = [&](bool zero_x) -> cudaError_t {
+        if (zero_x) return cudaMemcpyAsync(w, b, sizeof(double) * nn, cudaMemcpyDeviceToDevice, st);
+        cudaError_t e = launch_csr_spmv(n, h->a_rp, h->a_ci, h->a_v, x, nn, w, nn, 1, st);
+        if (e != cudaSuccess) return e;
+        return launch_axpby(nn, 1.0, b, -1.0, w, st);
+    };
+    CK(cudaMemsetAsync(x, 0, sizeof(double) * nn, st));
+    const double bnorm = norm2(b);
+    if (err != SLR_OK) { release(); return err; }
+    int32_t its = 0;
+    bool first = true;
+    std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), hv(2 * (m + 1) + 2), y(m);
+    while (bnorm > 0.0) {
+        CK(residual(first));
+        first = false;
+        const double beta = norm2(w);
+        if (err != SLR_OK) break;
+        if (beta <= tol * bnorm || its >= maxit) break;
+        CK(launch_axpby(nn, 1.0 / beta, w, 0.0, V, st));            // v_0 = r / beta
+        std::fill(H.begin(), H.end(), 0.0);
+        std::fill(g.begin(), g.end(), 0.0);
+        g[0] = beta;
+        int32_t jd = 0;
+        for (int32_t j = 0; j < m; ++j) {
+            double* vj = V + (int64_t)j * nn;
+            double* zj = Z + (int64_t)j * nn;
+            CS(apply_any(h, vj, nn, zj, nn, 1, st));                // z_j = M^{-1} v_j
+            CK(launch_csr_spmv(n, h->a_rp, h->a_ci, h->a_v, zj, nn, w, nn, 1, st));   // w = A z_j
+            ++its;
+            // two classical Gram-Schmidt passes: h = V^T w, w -= V h (twice), then ||w||
+            CK(launch_gemv_t(n, j + 1, V, w, part, hcol, st));
+            CK(launch_gemv_n_sub(n, j + 1, V, hcol, w, st));
+            CK(launch_gemv_t(n, j + 1, V, w, part, hcol + (m + 1), st));
+            CK(launch_gemv_n_sub(n, j + 1, V, hcol + (m + 1), w, st));
+            CK(launch_dots(nn, 1, w, nn, w, nn, part, hcol + 2 * (m + 1), 1, st));
+            CK(cudaMemcpyAsync(hv.data(), hcol, sizeof(double) * hv.size(), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            double* Hj = H.data() + (size_t)j * (m + 1);            // column j, rows 0 .. j+1
+            for (int32_t i = 0; i <= j; ++i) Hj[i] = hv[i] + hv[(m + 1) + i];
+            const double hn = std::sqrt(std::max(hv[2 * (m + 1)], 0.0));
+            Hj[j + 1] = hn;
+            if (hn > 0.0) CK(launch_axpby(nn, 1.0 / hn, w, 0.0, V + (int64_t)(j + 1) * nn, st));
+            for (int32_t i = 0; i < j; ++i) {                         // earlier rotations
+                const double t = cs[i] * Hj[i] + sn[i] * Hj[i + 1];
+                Hj[i + 1] = -sn[i] * Hj[i] + cs[i] * Hj[i + 1];
+                Hj[i] = t;
+            }
+            const double d = std::hypot(Hj[j], Hj[j + 1]);          // the rotation that zeroes H[j+1, j]
+            cs[j] = d > 0.0 ? Hj[j] / d : 1.0;
+            sn[j] = d > 0.0 ? Hj[j + 1] / d : 0.0;
+            Hj[j] = d;
+            Hj[j + 1] = 0.0;
+            g[j + 1] = -sn[j] * g[j];
+            g[j] = cs[j] * g[j];
+            jd = j + 1;
+            if (std::fabs(g[j + 1]) <= tol * bnorm || its >= maxit || hn == 0.0) break;
+        }
+        // y = R^{-1} g (R upper triangular, jd x jd), then x += Z y (as x -= Z (-y))
+        for (int32_t i = jd - 1; i >= 0; --i) {
+            double s = g[i];
+            for (int32_t q = i + 1; q < jd; ++q) s -= H[(size_t)q * (m + 1) + i] * y[q];
+            const double rii = H[(size_t)i * (m + 1) + i];
+            y[i] = rii != 0.0 ? s / rii : 0.0;
+        }
+        for (int32_t i = 0; i < jd; ++i) y[i] = -y[i];
+        CK(cudaMemcpyAsync(hcol, y.data(), sizeof(double) * jd, cudaMemcpyHostToDevice, st));
+        CK(launch_gemv_n_sub(n, jd, Z, hcol, x, st));
+    }
+    double rel = 0.0;
+    if (err == SLR_OK && bnorm > 0.0) {
+        CK(residual(false));
+        rel = norm2(w) / bnorm;
+    }
+    release();
+    *its_out = its;
+    *rel_out = rel;
+    return err;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1084,7 +1202,8 @@ slr_status slr_setup(int32_t n, const int32_t* rowptr, const int32_t* colind, co
         h->opts.reserved[5] < 0 || h->opts.reserved[5] == 1 ||
         (h->opts.reserved[6] != 0 && h->opts.reserved[6] != 256 && h->opts.reserved[6] != 512) ||
         h->opts.reserved[7] < 0 || h->opts.reserved[7] > 1 || h->opts.reserved[8] < 0 || h->opts.reserved[8] > 1 ||
-        std::any_of(h->opts.reserved + 9, h->opts.reserved + 16, [](int32_t v) { return v != 0; })) {
+        h->opts.reserved[9] < 0 || h->opts.reserved[9] > 1 ||
+        std::any_of(h->opts.reserved + 10, h->opts.reserved + 16, [](int32_t v) { return v != 0; })) {
         set_error("invalid options");
         delete h;
         return SLR_ERR_INVALID_ARG;
@@ -1238,15 +1357,57 @@ slr_status slr_pcg_solve(slr_handle h, const double* b, double* x, int32_t nrhs,
     return ret;
 }
 
+slr_status slr_gmres_solve(slr_handle h, const double* b, double* x, int32_t nrhs, int32_t ld, double tol,
+                           int32_t maxit, int32_t restart, void* stream, int32_t* iters_out, double* relres_out) {
+    CS(check_handle(h));
+    const int32_t n = h->hs.n;
+    if (nrhs < 1 || nrhs > h->opts.nrhs_max || ld < n || !b || !x || maxit < 0 || !(tol >= 0.0) || restart < 1 ||
+        restart > 1000) {
+        set_error("slr_gmres_solve: bad arguments");
+        return SLR_ERR_INVALID_ARG;
+    }
+    DeviceGuard g(h->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t nn = n;
+    CK(launch_permute(n, nrhs, h->perm, b, ld, h->pr, nn, true, st));   // b in DD order
+    slr_status ret = SLR_OK;
+    for (int32_t j = 0; j < nrhs; ++j) {
+        int32_t its = 0;
+        double rel = 0.0;
+        CS(gmres_column(h, h->pr + j * nn, h->px + j * nn, tol, maxit, restart, st, &its, &rel));
+        if (iters_out) iters_out[j] = its;
+        if (relres_out) relres_out[j] = rel;
+        if (!(rel <= tol * (1.0 + 1e-6)) && ret == SLR_OK) ret = SLR_ERR_NOT_CONVERGED;
+    }
+    CK(launch_permute(n, nrhs, h->perm, h->px, nn, x, ld, false, st));  // x = P^T x_dd
+    CK(cudaStreamSynchronize(st));
+    {
+        int32_t e = 0;
+        const int32_t* ep = h->opts.precision == SLR_PREC_FP64 ? h->op64.err : h->op32.err;
+        CK(cudaMemcpyAsync(&e, ep, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (e) {
+            set_error(e == 2 ? "a bounded grid-barrier wait expired in the C solve"
+                             : "a bounded device wait expired in the band solve");
+            return SLR_ERR_TIMEOUT;
+        }
+    }
+    if (ret == SLR_ERR_NOT_CONVERGED) set_error("GMRES reached maxit");
+    return ret;
+}
+
 slr_status slr_set_lowrank(slr_handle h, int32_t k, const double* Z, const double* lam, double theta, void* stream) {
     CS(check_handle(h));
     const int32_t s = h->hs.s;
-    if (k < 0 || k > s || (k > 0 && (!Z || !lam)) || !(theta >= 0.0 && theta < 1.0)) {
+    if (k < 0 || k > s || (k > 0 && (!Z || !lam)) || !(theta < 1.0 && (h->hs.indefinite || theta >= 0.0))) {
         set_error("slr_set_lowrank: bad arguments");
         return SLR_ERR_INVALID_ARG;
     }
     for (int32_t i = 0; i < k; ++i)
-        if (!(lam[i] < 1.0)) { set_error("slr_set_lowrank: lambda must be < 1"); return SLR_ERR_INVALID_ARG; }
+        if (h->hs.indefinite ? !(std::fabs(1.0 - lam[i]) > 0.0) : !(lam[i] < 1.0)) {
+            set_error("slr_set_lowrank: lambda must be < 1 (indefinite A: different from 1)");
+            return SLR_ERR_INVALID_ARG;
+        }
     DeviceGuard g(h->device);
     cudaStream_t st = (cudaStream_t)stream;
     h->stream = st;

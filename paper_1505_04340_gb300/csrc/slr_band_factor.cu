@@ -8,11 +8,15 @@
 //   L_JJ   = chol(S_J),   D_J = L_JJ^{-1}
 //   O_{J+1} = L[J+1, J] = A_{J+1,J} L_JJ^{-T} = A_{J+1,J} D_J^T
 // which is the same factor the host's column-oriented band Cholesky computes (up
-// to rounding).  One CTA of 512 threads per subdomain walks its planes; the dense
-// W x W blocks (W <= 256) live in a global scratch area, worked on in 32 x 32
-// tiles staged in shared memory.  Rows of the last plane past m are identity rows,
-// as in the host factor.  A pivot <= 0 records the subdomain in *bad and stops that
-// CTA.  A second kernel packs D_J and O_J into the tiled slice layout the band
+// to rounding).  For a symmetric indefinite A (SPD interface, Section 1) the
+// blocks are factored as L_JJ S_J L_JJ^T with S_J the pivot signs (no pivoting):
+// S_J = A_JJ - O_J S_{J-1} O_J^T and O_{J+1} = A_{J+1,J} D_J^T S_J; the pack
+// kernel folds the signs into the forward blocks (O_J S_{J-1}, S_J D_J).
+// One CTA of 512 threads per subdomain walks its planes; the dense W x W blocks
+// (W <= 256) live in a global scratch area, worked on in 32 x 32 tiles staged in
+// shared memory.  Rows of the last plane past m are identity rows, as in the host
+// factor.  A pivot <= 0 (zero when indefinite) records the subdomain in *bad and
+// stops that CTA.  A second kernel packs D_J and O_J into the tiled slice layout the band
 // solve streams (the same layout the host packer writes, for any split G), in the
 // operator's precision.
 #include <cuda_runtime.h>
@@ -39,10 +43,11 @@ __device__ __forceinline__ void load_tile(Tile& t, const double* M, int W, int r
     }
 }
 
-// S[ti, tj] -= A B^T summed over the 32-column chunks kc0 .. nt-1 (A: rows of tile ti
-// of X, B: rows of tile tj of Y, both row-major W x W), lower entries of S only.
+// S[ti, tj] -= A diag(sg) B^T summed over the 32-column chunks kc0 .. nt-1 (A: rows
+// of tile ti of X, B: rows of tile tj of Y, both row-major W x W; sg: signs of the
+// summed columns, or null for all +1), lower entries of S only.
 __device__ void tile_sub_abt(double* S, const double* X, const double* Y, int W, int ti, int tj, int kc0, int nt,
-                             Tile& ta, Tile& tb) {
+                             Tile& ta, Tile& tb, const double* sg = nullptr) {
     const int row = threadIdx.x >> 4, col = (threadIdx.x & 15) * 2;
     double acc0 = 0.0, acc1 = 0.0;
     for (int kc = kc0; kc < nt; ++kc) {
@@ -50,6 +55,13 @@ __device__ void tile_sub_abt(double* S, const double* X, const double* Y, int W,
         load_tile(ta, X, W, 32 * ti, 32 * kc);
         load_tile(tb, Y, W, 32 * tj, 32 * kc);
         __syncthreads();
+        if (sg) {
+            for (int i = threadIdx.x; i < 1024; i += kFT) {
+                const int c = 32 * kc + (i & 31);
+                if (c < W) ta.v[i >> 5][i & 31] *= sg[c];
+            }
+            __syncthreads();
+        }
 #pragma unroll 8
         for (int q = 0; q < 32; ++q) {
             const double a = ta.v[row][q];
@@ -64,9 +76,11 @@ __device__ void tile_sub_abt(double* S, const double* X, const double* Y, int W,
     }
 }
 
-// In-place Cholesky of the lower triangle of S (right-looking, 32-column panels).
-// Returns false (uniformly) if a pivot is not positive.
-__device__ bool chol_blocked(double* S, int W, int nt, Tile& ta, Tile& tb, int* flag) {
+// In-place Cholesky of the lower triangle of S (right-looking, 32-column panels):
+// S = L L^T, or with indef S = L diag(sg) L^T, the signs of the pivots into sg[W].
+// Returns false (uniformly) if a pivot is not positive (SPD) or is zero (indef).
+__device__ bool chol_blocked(double* S, int W, int nt, Tile& ta, Tile& tb, int* flag, double* sg, bool indef) {
+    __shared__ double tsg[32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int kb = 0; kb < nt; ++kb) {
         // diagonal tile: unblocked Cholesky by warp 0 (lane = row); rows past W get 1 on the diagonal
@@ -81,15 +95,22 @@ __device__ bool chol_blocked(double* S, int W, int nt, Tile& ta, Tile& tb, int* 
             for (int j = 0; j < 32; ++j) {
                 if (lane == j) {
                     const double d = ta.v[j][j];
-                    if (!(d > 0.0)) *flag = 1;
-                    ta.v[j][j] = sqrt(fmax(d, 0.0));
+                    double sj = 1.0;
+                    if (indef) {
+                        if (!(fabs(d) > 0.0)) *flag = 1;
+                        sj = d < 0.0 ? -1.0 : 1.0;
+                    } else if (!(d > 0.0)) {
+                        *flag = 1;
+                    }
+                    tsg[j] = sj;
+                    ta.v[j][j] = sqrt(fabs(d));
                 }
                 __syncwarp();
-                const double djj = ta.v[j][j];
-                if (lane > j) ta.v[lane][j] = djj > 0.0 ? ta.v[lane][j] / djj : 0.0;
+                const double djj = ta.v[j][j] * tsg[j];   // s_j l_jj
+                if (lane > j) ta.v[lane][j] = djj != 0.0 ? ta.v[lane][j] / djj : 0.0;
                 __syncwarp();
                 if (lane > j) {
-                    const double lj = ta.v[lane][j];
+                    const double lj = ta.v[lane][j] * tsg[j];
                     for (int k = j + 1; k <= lane; ++k) ta.v[lane][k] -= lj * ta.v[k][j];
                 }
                 __syncwarp();
@@ -101,7 +122,8 @@ __device__ bool chol_blocked(double* S, int W, int nt, Tile& ta, Tile& tb, int* 
             const int r = i >> 5, c = i & 31, gr = 32 * kb + r, gc = 32 * kb + c;
             if (gr < W && gc < W && c <= r) S[(int64_t)gr * W + gc] = ta.v[r][c];
         }
-        // panel below: row r of L[ib, kb] solves x L_kk^T = S[r, kb block] (forward substitution)
+        if (tid < 32 && 32 * kb + tid < W) sg[32 * kb + tid] = tsg[tid];
+        // panel below: row r of L[ib, kb] solves x diag(s) L_kk^T = S[r, kb block] (forward substitution)
         for (int r = 32 * (kb + 1) + tid; r < W; r += kFT) {
             double x[32];
             double* Sr = S + (int64_t)r * W + 32 * kb;
@@ -111,8 +133,8 @@ __device__ bool chol_blocked(double* S, int W, int nt, Tile& ta, Tile& tb, int* 
             for (int j = 0; j < 32; ++j) {
                 double s = x[j];
 #pragma unroll
-                for (int q = 0; q < j; ++q) s -= x[q] * ta.v[j][q];
-                x[j] = s / ta.v[j][j];
+                for (int q = 0; q < j; ++q) s -= x[q] * tsg[q] * ta.v[j][q];
+                x[j] = s / (tsg[j] * ta.v[j][j]);
             }
 #pragma unroll
             for (int j = 0; j < 32; ++j)
@@ -121,7 +143,7 @@ __device__ bool chol_blocked(double* S, int W, int nt, Tile& ta, Tile& tb, int* 
         __syncthreads();
         // trailing update of the lower tiles: S[ib, jb] -= L[ib, kb] L[jb, kb]^T, kb < jb <= ib
         for (int ib = kb + 1; ib < nt; ++ib)
-            for (int jb = kb + 1; jb <= ib; ++jb) tile_sub_abt(S, S, S, W, ib, jb, kb, kb + 1, ta, tb);
+            for (int jb = kb + 1; jb <= ib; ++jb) tile_sub_abt(S, S, S, W, ib, jb, kb, kb + 1, ta, tb, sg);
     }
     __syncthreads();
     return true;
@@ -192,7 +214,7 @@ __device__ void trtri_blocked(const double* S, double* X, int W, int nt, Tile& t
 
 __global__ void __launch_bounds__(kFT, 1)
 k_band_factor(const BandBlock* __restrict__ band, const int32_t* __restrict__ a_rp, const int32_t* __restrict__ a_ci,
-              const double* __restrict__ a_v, double* scr, const int64_t* __restrict__ soff, int32_t* bad) {
+              const double* __restrict__ a_v, double* scr, const int64_t* __restrict__ soff, int32_t* bad, int indef) {
     __shared__ Tile ta, tb;
     __shared__ int flag;
     const BandBlock b = band[blockIdx.x];
@@ -202,6 +224,7 @@ k_band_factor(const BandBlock* __restrict__ band, const int32_t* __restrict__ a_
     double* S = scr + soff[blockIdx.x];
     double* Dst = S + WW;               // D_J = L_JJ^{-1} at Dst + J W^2
     double* Ost = Dst + (int64_t)c * WW;   // O_J = L[J, J-1] at Ost + J W^2 (O_0 = 0)
+    double* Sg = Ost + (int64_t)c * WW;    // pivot signs of plane J at Sg + J W
     for (int J = 0; J < c; ++J) {
         // S = lower part of A_JJ (identity rows past m)
         for (int64_t i = tid; i < WW; i += kFT) S[i] = 0.0;
@@ -221,11 +244,12 @@ k_band_factor(const BandBlock* __restrict__ band, const int32_t* __restrict__ a_
         // S -= O_J O_J^T (O_J upper triangular: column chunks from the row tile on)
         if (J > 0) {
             const double* O = Ost + (int64_t)J * WW;
+            const double* sgp = indef ? Sg + (int64_t)(J - 1) * W : nullptr;
             for (int ti = 0; ti < nt; ++ti)
-                for (int tj = 0; tj <= ti; ++tj) tile_sub_abt(S, O, O, W, ti, tj, ti, nt, ta, tb);
+                for (int tj = 0; tj <= ti; ++tj) tile_sub_abt(S, O, O, W, ti, tj, ti, nt, ta, tb, sgp);
             __syncthreads();
         }
-        if (!chol_blocked(S, W, nt, ta, tb, &flag)) {
+        if (!chol_blocked(S, W, nt, ta, tb, &flag, Sg + (int64_t)J * W, indef != 0)) {
             if (tid == 0) atomicCAS(bad, -1, (int32_t)blockIdx.x);
             return;
         }
@@ -242,7 +266,7 @@ k_band_factor(const BandBlock* __restrict__ band, const int32_t* __restrict__ a_
                         const int qq = a_ci[q] - r0 - J * W;
                         if (qq >= 0 && qq < W && qq <= k) s += a_v[q] * D[(int64_t)k * W + qq];
                     }
-                On[i] = s;
+                On[i] = indef ? s * Sg[(int64_t)J * W + k] : s;
             }
             __syncthreads();
         }
@@ -254,7 +278,7 @@ k_band_factor(const BandBlock* __restrict__ band, const int32_t* __restrict__ a_
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_band_pack(const BandBlock* __restrict__ band, int32_t cmax, int32_t G, const double* __restrict__ scr,
-            const int64_t* __restrict__ soff, T* bfac) {
+            const int64_t* __restrict__ soff, T* bfac, int indef) {
     const int i = blockIdx.x / (cmax * G), J = (blockIdx.x / G) % cmax, g = blockIdx.x % G;
     const BandBlock b = band[i];
     if (b.m == 0 || J >= b.c) return;
@@ -262,6 +286,8 @@ k_band_pack(const BandBlock* __restrict__ band, int32_t cmax, int32_t G, const d
     const int64_t WW = (int64_t)W * W;
     const double* X = scr + soff[i] + WW + (int64_t)J * WW;        // D_J
     const double* O = scr + soff[i] + WW + (int64_t)(b.c + J) * WW;   // O_J
+    const double* Sg = scr + soff[i] + WW + 2 * (int64_t)b.c * WW;    // pivot signs, plane by plane
+    auto sgn = [&](int plane, int r) -> double { return indef ? Sg[(int64_t)plane * W + r] : 1.0; };
     T* plane = bfac + b.foff + (int64_t)J * G * 2 * (b.SU + b.SL) + (int64_t)g * 2 * (b.SU + b.SL);
     T* Uf = plane;          // O_J      (upper)
     T* Lf = Uf + b.SU;      // D_J      (lower)
@@ -275,13 +301,13 @@ k_band_pack(const BandBlock* __restrict__ band, int32_t cmax, int32_t G, const d
         for (int e = threadIdx.x; e < 32 * nu; e += blockDim.x) {   // upper: rows r <= cc
             const int cc = cu0 + e / 32, r = R0 + (e & 31), l = J * W + r;
             const bool in = r < W && r <= cc;
-            Uf[(su * 32) + e] = in && J > 0 && l < m ? (T)O[(int64_t)r * W + cc] : T(0);
+            Uf[(su * 32) + e] = in && J > 0 && l < m ? (T)(O[(int64_t)r * W + cc] * sgn(J - 1, cc)) : T(0);
             Ub[(su * 32) + e] = in ? (T)X[(int64_t)cc * W + r] : T(0);
         }
         for (int e = threadIdx.x; e < 32 * cl1; e += blockDim.x) {  // lower: rows r >= cc
             const int cc = e / 32, r = R0 + (e & 31), lc = J * W + cc;
             const bool in = r < W && r >= cc;
-            Lf[(sl * 32) + e] = in ? (T)X[(int64_t)r * W + cc] : T(0);
+            Lf[(sl * 32) + e] = in ? (T)(X[(int64_t)r * W + cc] * sgn(J, r)) : T(0);
             Lb[(sl * 32) + e] = in && J > 0 && lc < m ? (T)O[(int64_t)cc * W + r] : T(0);
         }
         su += nu;
@@ -292,25 +318,26 @@ k_band_pack(const BandBlock* __restrict__ band, int32_t cmax, int32_t G, const d
 }  // namespace
 
 cudaError_t launch_band_factor(const BandBlock* band, int32_t p, const int32_t* a_rp, const int32_t* a_ci,
-                               const double* a_v, double* scr, const int64_t* soff, int32_t* bad, cudaStream_t st) {
+                               const double* a_v, double* scr, const int64_t* soff, int32_t* bad, bool indef,
+                               cudaStream_t st) {
     if (p == 0) return cudaSuccess;
-    k_band_factor<<<p, kFT, 0, st>>>(band, a_rp, a_ci, a_v, scr, soff, bad);
+    k_band_factor<<<p, kFT, 0, st>>>(band, a_rp, a_ci, a_v, scr, soff, bad, indef ? 1 : 0);
     count_launches(1);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_band_pack(const BandBlock* band, int32_t p, int32_t cmax, int32_t G, const double* scr,
-                             const int64_t* soff, T* bfac, cudaStream_t st) {
+                             const int64_t* soff, T* bfac, bool indef, cudaStream_t st) {
     if (p == 0 || cmax == 0) return cudaSuccess;
-    k_band_pack<T><<<(unsigned)p * cmax * G, 256, 0, st>>>(band, cmax, G, scr, soff, bfac);
+    k_band_pack<T><<<(unsigned)p * cmax * G, 256, 0, st>>>(band, cmax, G, scr, soff, bfac, indef ? 1 : 0);
     count_launches(1);
     return cudaGetLastError();
 }
 
 template cudaError_t launch_band_pack<double>(const BandBlock*, int32_t, int32_t, int32_t, const double*,
-                                              const int64_t*, double*, cudaStream_t);
+                                              const int64_t*, double*, bool, cudaStream_t);
 template cudaError_t launch_band_pack<float>(const BandBlock*, int32_t, int32_t, int32_t, const double*,
-                                             const int64_t*, float*, cudaStream_t);
+                                             const int64_t*, float*, bool, cudaStream_t);
 
 }  // namespace slr

@@ -147,15 +147,18 @@ template <typename T>
 cudaError_t launch_spmv_e(const DevOperator<T>& op, int32_t nI, const T* y, int64_t ldy, T* out,
                           int64_t ldo, int32_t nrhs, cudaStream_t st);
 // ---- band factorization on the device (slr_band_factor.cu): the plane blocks of
-// every B_i into scr (per subdomain at soff[i]: S, then D_J for every plane, then
-// O_J); *bad receives a subdomain whose pivot is not positive (it must hold -1)
+// every B_i into scr (per subdomain at soff[i]: S (W^2), then D_J for every plane,
+// then O_J, then the pivot signs (c W)); *bad receives a subdomain whose pivot is
+// not positive, or zero when indef (it must hold -1)
 cudaError_t launch_band_factor(const BandBlock* band, int32_t p, const int32_t* a_rp, const int32_t* a_ci,
-                               const double* a_v, double* scr, const int64_t* soff, int32_t* bad, cudaStream_t st);
-// packs them into the tiled slice layout of `band` (split G) in precision T; bfac
-// must be zeroed first (slices shorter than the widest keep zeros)
+                               const double* a_v, double* scr, const int64_t* soff, int32_t* bad, bool indef,
+                               cudaStream_t st);
+// packs them into the tiled slice layout of `band` (split G) in precision T, the
+// pivot signs folded into the forward blocks when indef; bfac must be zeroed first
+// (slices shorter than the widest keep zeros)
 template <typename T>
 cudaError_t launch_band_pack(const BandBlock* band, int32_t p, int32_t cmax, int32_t G, const double* scr,
-                             const int64_t* soff, T* bfac, cudaStream_t st);
+                             const int64_t* soff, T* bfac, bool indef, cudaStream_t st);
 // ---- K3: C solves.  fwd: xf = L^{-1} P g (g in DD order, xf in factor order)
 //              bwd: xf = L^{-T} yf (factor order), optional scatter to DD order y_dd
 // xf, yf: s x nrhs (leading dimension s); yf is read only and must not overlap xf.

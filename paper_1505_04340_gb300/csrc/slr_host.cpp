@@ -329,6 +329,10 @@ slr_status host_band_factor(HostSetup& hs, int32_t G) {
                 int32_t k = hs.a_ci[q] - r0;
                 if (k >= 0 && k <= l) Lb[(size_t)l * lw + (k - l + w)] = hs.a_v[q];
             }
+        // SPD: B_i = L L^T.  Indefinite (hs.indefinite): B_i = L S L^T with S = diag(sg)
+        // the pivot signs (a symmetric factorisation without pivoting), L = Lt |D|^{1/2}.
+        std::vector<double> sg((size_t)b.c * W, 1.0);   // plane rows past m keep +1
+        const bool indef = hs.indefinite;
         bool ok = true;
         for (int32_t l = 0; l < m && ok; ++l) {
             double* Ll = &Lb[(size_t)l * lw + (w - l)];   // Ll[k] = L[l][k]
@@ -337,9 +341,16 @@ slr_status host_band_factor(HostSetup& hs, int32_t G) {
                 const double* Lj = &Lb[(size_t)j * lw + (w - j)];
                 int32_t klo = std::max(jlo, j - w);
                 double s = Ll[j];
-                for (int32_t k = klo; k < j; ++k) s -= Ll[k] * Lj[k];
+                if (indef)
+                    for (int32_t k = klo; k < j; ++k) s -= Ll[k] * sg[k] * Lj[k];
+                else
+                    for (int32_t k = klo; k < j; ++k) s -= Ll[k] * Lj[k];
                 if (j < l) {
-                    Ll[j] = s / Lj[j];
+                    Ll[j] = s / (sg[j] * Lj[j]);
+                } else if (indef) {
+                    if (!(std::fabs(s) > 0.0)) { ok = false; break; }
+                    sg[l] = s < 0.0 ? -1.0 : 1.0;
+                    Ll[l] = std::sqrt(std::fabs(s));
                 } else {
                     if (!(s > 0.0)) { ok = false; break; }
                     Ll[l] = std::sqrt(s);
@@ -376,14 +387,16 @@ slr_status host_band_factor(HostSetup& hs, int32_t G) {
                         for (int e = 0; e < 32; ++e) {
                             const int r = R0 + e, l = J * W + r;
                             if (r >= W || r > cc) continue;
-                            Uf[su * 32 + e] = (J > 0 && l < m) ? Lat(l, (J - 1) * W + cc) : 0.0;   // O_J[r][cc]
+                            // forward blocks carry the pivot signs: O_J S_{J-1} and S_J D_J^{-1}
+                            Uf[su * 32 + e] = (J > 0 && l < m) ? Lat(l, (J - 1) * W + cc) * sg[(size_t)(J - 1) * W + cc]
+                                                               : 0.0;                            // O_J[r][cc]
                             Ub[su * 32 + e] = X[(size_t)cc * W + r];                             // D_J^{-1}[cc][r]
                         }
                     for (int cc = 0; cc < band_cL1(b, g, rb); ++cc, ++sl)      // lower: rows r >= cc
                         for (int e = 0; e < 32; ++e) {
                             const int r = R0 + e, lc = J * W + cc;
                             if (r >= W || r < cc) continue;
-                            Lf[sl * 32 + e] = X[(size_t)r * W + cc];                             // D_J^{-1}[r][cc]
+                            Lf[sl * 32 + e] = X[(size_t)r * W + cc] * sg[(size_t)J * W + r];     // D_J^{-1}[r][cc]
                             Lb[sl * 32 + e] = (J > 0 && lc < m) ? Lat(lc, (J - 1) * W + r) : 0.0;   // O_J[cc][r]
                         }
                 }
@@ -391,6 +404,10 @@ slr_status host_band_factor(HostSetup& hs, int32_t G) {
         }
     }
     if (bad >= 0) {
+        if (hs.indefinite) {
+            set_error("B_" + std::to_string(bad) + " has a zero pivot in its symmetric factorisation");
+            return SLR_ERR_BREAKDOWN;
+        }
         set_error("B_" + std::to_string(bad) + " is not positive definite (Cholesky pivot <= 0)");
         return SLR_ERR_NOT_SPD;
     }

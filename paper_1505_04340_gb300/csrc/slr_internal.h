@@ -132,6 +132,9 @@ struct HostSetup {
     std::vector<BandBlock> band;
     std::vector<int32_t> band_w;          // half-bandwidth of each B_i
     int64_t bfac_len = 0;                 // elements of the packed band factor (one precision)
+    bool indefinite = false;              // A symmetric indefinite with an SPD interface C:
+                                          // B_i = L S L^T, S the pivot signs, folded into the
+                                          // forward blocks (O_J S_{J-1} and S_J D_J^{-1})
     std::vector<double> bfac;
     int32_t wmax = 0;
     int32_t band_G = 1;   // CTAs (slices) per subdomain in the band solve

@@ -30,7 +30,7 @@ PRECISION = {"fp64": 0, "mixed": 1}
 EXPORTS = ["slr_default_opts", "slr_setup", "slr_apply", "slr_pcg_solve", "slr_bsolve", "slr_csolve",
            "slr_stilde_solve", "slr_set_lowrank", "slr_get_lowrank", "slr_get_ritz", "slr_get_perm",
            "slr_get_info", "slr_dd_order", "slr_kernel_launches", "slr_destroy", "slr_status_str",
-           "slr_last_error_message", "slr_apply_noalloc", "slr_add_vectors"]
+           "slr_last_error_message", "slr_apply_noalloc", "slr_add_vectors", "slr_gmres_solve"]
 
 
 class Opts(C.Structure):
@@ -78,6 +78,7 @@ def load():
         "slr_apply": (i32, [vp, vp, vp, i32, i32, vp]),
         "slr_apply_noalloc": (i32, [vp, vp, vp, i32, i32, vp]),
         "slr_pcg_solve": (i32, [vp, vp, vp, i32, i32, f64, i32, vp, vp, vp]),
+        "slr_gmres_solve": (i32, [vp, vp, vp, i32, i32, f64, i32, i32, vp, vp, vp]),
         "slr_bsolve": (i32, [vp, vp, vp, i32, i32, vp]),
         "slr_csolve": (i32, [vp, vp, vp, i32, i32, vp]),
         "slr_stilde_solve": (i32, [vp, vp, vp, i32, i32, vp]),
@@ -163,7 +164,7 @@ class SLR:
     def __init__(self, rowptr, colind, val, part, nparts, k=16, lanczos_steps=0, theta="lambda_k1",
                  precision="fp64", nrhs_max=1, flexible_cg=False, seed=1, c_leaf=64, verbose=False,
                  band_split=0, host_loop=False, band_slots=0, c_persistent=False, autotune=False, target_kappa=0,
-                 band_threads=0, c_top_zone=True, band_factor="auto", stream=None):
+                 band_threads=0, c_top_zone=True, band_factor="auto", indefinite=False, stream=None):
         lib = load()
         self._lib = lib
         self._h = None
@@ -182,6 +183,7 @@ class SLR:
         o.reserved[6] = int(band_threads)        # threads per band-solve CTA: 512, 256 or 0 (automatic)
         o.reserved[7] = 0 if c_top_zone else 1   # explicit inverse of the factor's top levels
         o.reserved[8] = {"auto": 0, "host": 1}[band_factor]   # B_i factored on the device or the host
+        o.reserved[9] = int(bool(indefinite))    # symmetric indefinite A with an SPD interface
         self.rowptr, self.colind = _i32(rowptr), _i32(colind)
         self.val = np.ascontiguousarray(val, dtype=np.float64)
         self.part = _i32(part)
@@ -292,6 +294,23 @@ class SLR:
     def stilde_solve(self, g, stream=None):
         """y = S~^{-1} g (Eq. 4.7) on the interface unknowns (DD order)."""
         return self._call(self._lib.slr_stilde_solve, g, self.s, "g", stream)
+
+    def gmres(self, b, tol=1e-8, maxit=300, restart=40, stream=None, check=True):
+        """Solve A x = b (original order) by SLR-preconditioned flexible GMRES(restart)
+        (Section 6, the symmetric indefinite problems).
+
+        Returns (x, iterations[nrhs], relres[nrhs], status)."""
+        import torch
+        buf, r, one = _as_colmajor(b, self.n, "b")
+        x = torch.empty_like(buf)
+        its = np.zeros(r, np.int32)
+        rel = np.zeros(r, np.float64)
+        st = self._lib.slr_gmres_solve(self._h, C.c_void_p(buf.data_ptr()), C.c_void_p(x.data_ptr()), r,
+                                       self.n, float(tol), int(maxit), int(restart), _stream_ptr(stream),
+                                       _host_ptr(its), _host_ptr(rel))
+        if check and st not in (OK, 5):
+            _check(st, "slr_gmres_solve")
+        return _back(x, one), its, rel, st
 
     def pcg(self, b, tol=1e-8, maxit=300, stream=None, check=True):
         """Solve A x = b (original order) by SLR-preconditioned CG.
