@@ -143,7 +143,11 @@ void slr_default_opts(slr_opts* opts);
 /* Build the SLR preconditioner of A (Sections 2-5).
  * n, rowptr[n+1], colind[nnz], val[nnz]: host CSR of the FULL symmetric matrix
  *   (both triangles, sorted or unsorted columns, no duplicates), 0-based, n < 2^31.
- * nparts, part[n]: host partition, part[i] in [0, nparts) (vertex-based, Section 2.1).
+ * nparts, part[n]: host partition, part[i] in [0, nparts) (vertex-based, Section 2.1),
+ * or -1 for a vertex-separator node (a partition with vertex separators, which
+ * Section 2.1 notes the method also covers): separator nodes are interface
+ * nodes listed after y_p, and a part's node coupled only to its own part and to
+ * separators is interior.
  * opts: NULL => defaults.  stream: where the setup's device work runs.
  * *out: new handle on success, NULL on failure.  Errors: INVALID_ARG (sizes,
  * structure, part out of range), NOT_SPD (a pivot <= 0 in B_i or C), OOM, CUDA. */

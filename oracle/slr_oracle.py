@@ -68,20 +68,32 @@ def dd_order(rowptr, colind, part, nparts) -> DDOrder:
     The new order lists u_1, ..., u_p (interiors of part 0..p-1) and then
     y_1, ..., y_p (interfaces of part 0..p-1); inside each group nodes keep
     ascending original index.
+
+    Vertex separators (Section 2.1 notes the method applies to them too): part
+    id -1 marks a separator vertex; separator vertices are interface nodes listed
+    after y_p (beyond ifc_off[p]), and a node of a part is interface only if it
+    is coupled to another part's node (coupling to a separator keeps it interior).
     """
     n = len(rowptr) - 1
     part = np.asarray(part, dtype=np.int64)
     is_iface = np.zeros(n, dtype=bool)
     for i in range(n):
+        if part[i] < 0:
+            is_iface[i] = True
+            continue
         for q in range(rowptr[i], rowptr[i + 1]):
             j = colind[q]
-            if j != i and part[j] != part[i]:
+            if j != i and part[j] >= 0 and part[j] != part[i]:
                 is_iface[i] = True
                 break
     interior = [[] for _ in range(nparts)]
     iface = [[] for _ in range(nparts)]
+    separator = []
     for i in range(n):
-        (iface if is_iface[i] else interior)[part[i]].append(i)
+        if part[i] < 0:
+            separator.append(i)
+        else:
+            (iface if is_iface[i] else interior)[part[i]].append(i)
     perm = []
     int_off = [0]
     for q in range(nparts):
@@ -92,6 +104,7 @@ def dd_order(rowptr, colind, part, nparts) -> DDOrder:
     for q in range(nparts):
         perm += iface[q]
         ifc_off.append(len(perm) - n_I)
+    perm += separator
     perm = np.array(perm, dtype=np.int64)
     iperm = np.empty(n, dtype=np.int64)
     iperm[perm] = np.arange(n)

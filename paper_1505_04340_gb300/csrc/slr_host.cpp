@@ -61,7 +61,7 @@ slr_status host_validate_csr(int32_t n, const int32_t* rowptr, const int32_t* co
     int64_t nnz = rowptr[n];
     if (nnz > 0 && (!colind || !val)) { set_error("NULL colind/val"); return SLR_ERR_INVALID_ARG; }
     for (int32_t i = 0; i < n; ++i)
-        if (part[i] < 0 || part[i] >= nparts) {
+        if (part[i] < -1 || part[i] >= nparts) {   // -1: a vertex-separator node
             set_error("part[" + std::to_string(i) + "] out of range");
             return SLR_ERR_INVALID_ARG;
         }
@@ -116,15 +116,23 @@ slr_status host_dd_order(int32_t n, const int32_t* rowptr, const int32_t* colind
                          const int32_t* part, HostSetup& hs) {
     hs.n = n;
     hs.p = nparts;
+    // interface: coupled to another part's node; part -1 (a vertex separator) is
+    // always interface, and coupling to it keeps a part's node interior
     std::vector<char> iface(n, 0);
-    for (int32_t i = 0; i < n; ++i)
+    for (int32_t i = 0; i < n; ++i) {
+        if (part[i] < 0) { iface[i] = 1; continue; }
         for (int32_t q = rowptr[i]; q < rowptr[i + 1]; ++q) {
             int32_t j = colind[q];
-            if (j != i && part[j] != part[i]) { iface[i] = 1; break; }
+            if (j != i && part[j] >= 0 && part[j] != part[i]) { iface[i] = 1; break; }
         }
-    // counting sort by (is_interface, part), stable in the original index
-    std::vector<int64_t> cnt(2 * (int64_t)nparts + 1, 0);
-    for (int32_t i = 0; i < n; ++i) cnt[1 + (int64_t)iface[i] * nparts + part[i]]++;
+    }
+    // counting sort by (is_interface, part), stable in the original index; the
+    // separator nodes form a last group after the parts' interfaces
+    auto bucket = [&](int32_t i) -> int64_t {
+        return part[i] < 0 ? 2 * (int64_t)nparts : (int64_t)iface[i] * nparts + part[i];
+    };
+    std::vector<int64_t> cnt(2 * (int64_t)nparts + 2, 0);
+    for (int32_t i = 0; i < n; ++i) cnt[1 + bucket(i)]++;
     for (size_t t = 1; t < cnt.size(); ++t) cnt[t] += cnt[t - 1];
     hs.int_off.assign(nparts + 1, 0);
     hs.ifc_off.assign(nparts + 1, 0);
@@ -136,8 +144,7 @@ slr_status host_dd_order(int32_t n, const int32_t* rowptr, const int32_t* colind
     hs.iperm.assign(n, 0);
     std::vector<int64_t> pos(cnt.begin(), cnt.end() - 1);
     for (int32_t i = 0; i < n; ++i) {
-        int64_t key = (int64_t)iface[i] * nparts + part[i];
-        int32_t d = (int32_t)pos[key]++;
+        int32_t d = (int32_t)pos[bucket(i)]++;
         hs.perm[d] = i;
         hs.iperm[i] = d;
     }
@@ -1148,7 +1155,7 @@ slr_status slr_dd_order(int32_t n, const int32_t* rowptr, const int32_t* colind,
         return SLR_ERR_INVALID_ARG;
     }
     for (int32_t i = 0; i < n; ++i)
-        if (part[i] < 0 || part[i] >= nparts) { slr::set_error("part out of range"); return SLR_ERR_INVALID_ARG; }
+        if (part[i] < -1 || part[i] >= nparts) { slr::set_error("part out of range"); return SLR_ERR_INVALID_ARG; }
     for (int32_t i = 0; i < n; ++i)
         for (int32_t q = rowptr[i]; q < rowptr[i + 1]; ++q)
             if (colind[q] < 0 || colind[q] >= n) { slr::set_error("column out of range"); return SLR_ERR_INVALID_ARG; }

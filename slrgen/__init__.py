@@ -159,6 +159,25 @@ def box_partition(dims, boxes):
     return part.ravel().astype(np.int32)
 
 
+def box_partition_vsep(dims, boxes):
+    """Box partition with vertex separators: the first grid plane of every box but
+    the first along each axis (where ``floor(coord * B_ax / N_ax)`` steps up) is a
+    separator (part id -1); the other vertices keep their box id.  With 5/7-point
+    stencils the separator planes disconnect the boxes."""
+    dims = tuple(int(d) for d in dims)
+    boxes = tuple(int(b) for b in boxes)
+    part = box_partition(dims, boxes).astype(np.int64)
+    coords = np.meshgrid(*[np.arange(d) for d in reversed(dims)], indexing="ij")
+    coords = list(reversed(coords))
+    sep = np.zeros(coords[0].shape, dtype=bool)
+    for ax in range(len(dims)):
+        c = coords[ax]
+        sep |= (c > 0) & ((c * boxes[ax]) // dims[ax] > ((c - 1) * boxes[ax]) // dims[ax])
+    part = part.reshape(coords[0].shape)
+    part[sep] = -1
+    return part.ravel().astype(np.int32)
+
+
 def csr_matvec(rowptr, colind, val, x):
     A = sp.csr_matrix((val, colind, rowptr), shape=(len(rowptr) - 1,) * 2)
     return A @ x
@@ -194,13 +213,15 @@ class Problem:
 
 
 def make_problem(name, dims, boxes, k, *, kind="laplacian", coef=None, coef_range=None,
-                 nrhs=1, matrix_seed=1, rhs_seed=2, lanczos_steps=None, shift=0.0):
+                 nrhs=1, matrix_seed=1, rhs_seed=2, lanczos_steps=None, shift=0.0, separators=False):
     """Build a Problem; ``kind`` is 'laplacian' (constant axis coefficients) or 'fv'.
 
     x* column j is uniform[-1,1) from stream ``rhs_seed + j``; b = A x*.
     For 'fv' the cell coefficients are log-uniform in ``coef_range`` from
     stream ``matrix_seed``.  ``shift`` s > 0 subtracts s I (the shifted,
     symmetric indefinite problems of Section 6: -Laplacian u - c u = f).
+    ``separators``: a vertex-separator partition (``box_partition_vsep``) instead
+    of the edge-based one.
     """
     dims = tuple(int(d) for d in dims)
     n = int(np.prod(dims))
@@ -215,14 +236,15 @@ def make_problem(name, dims, boxes, k, *, kind="laplacian", coef=None, coef_rang
         val = val.copy()
         rows = np.repeat(np.arange(n), np.diff(rowptr))
         val[colind == rows] -= shift
-    part = box_partition(dims, boxes)
+    part = box_partition_vsep(dims, boxes) if separators else box_partition(dims, boxes)
     xstar = np.stack([uniform_pm1(rhs_seed + j, n) for j in range(nrhs)], axis=1)
     b = csr_matvec(rowptr, colind, val, xstar)
     return Problem(name=name, dims=dims, rowptr=rowptr, colind=colind, val=val, part=part,
                    nparts=int(np.prod(boxes)), k=int(k),
                    lanczos_steps=int(lanczos_steps if lanczos_steps is not None else 5 * k),
                    xstar=xstar, b=np.ascontiguousarray(b),
-                   meta=dict(boxes=tuple(boxes), kind=kind, coef=coef, coef_range=coef_range, shift=shift))
+                   meta=dict(boxes=tuple(boxes), kind=kind, coef=coef, coef_range=coef_range, shift=shift,
+                             separators=separators))
 
 
 # The five workloads (grid, partition, rank, right-hand sides).

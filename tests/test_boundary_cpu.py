@@ -52,6 +52,23 @@ def test_dd_order_bit_exact_vs_oracle(lib, dims, boxes):
     assert np.array_equal(io, o.int_off) and np.array_equal(fo, o.ifc_off)
 
 
+@pytest.mark.parametrize("dims,boxes", [((32, 32), (2, 2)), ((30, 17), (3, 2)), ((12, 11, 10), (2, 3, 2))])
+def test_dd_order_with_vertex_separators_vs_oracle(lib, dims, boxes):
+    """part = -1 marks separator vertices: the library's order equals the oracle's, the
+    separators come last, and every part's interface group is empty (the separators
+    disconnect the boxes)."""
+    from paper_1505_04340_gb300 import dd_order
+    rp, ci, v = slrgen.laplacian(dims)
+    part = slrgen.box_partition_vsep(dims, boxes)
+    p = int(np.prod(boxes))
+    perm, io, fo, s = dd_order(rp, ci, part, p)
+    o = oracle_dd_order(rp, ci, part, p)
+    assert s == o.s == int(np.sum(part < 0))
+    assert np.array_equal(perm, o.perm)
+    assert np.array_equal(io, o.int_off) and np.array_equal(fo, o.ifc_off) and fo[-1] == 0
+    assert np.all(part[perm[len(perm) - s:]] == -1)
+
+
 def test_dd_order_random_partition(lib):
     from paper_1505_04340_gb300 import dd_order
     rp, ci, v = slrgen.laplacian((15, 14))
@@ -86,6 +103,7 @@ def test_setup_rejects_bad_input_before_any_device_work(lib):
     asym[1] += 0.5                                   # values no longer symmetric
     assert _setup_status(lib, rp, ci, asym, part, 2) == 1
     assert _setup_status(lib, rp, ci, v, part + 5, 2) == 1   # part out of range
+    assert _setup_status(lib, rp, ci, v, part - 2, 2) == 1   # below -1 (the separator mark)
     assert "range" in lib.slr_last_error_message().decode()
 
 

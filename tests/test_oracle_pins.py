@@ -546,3 +546,36 @@ def test_slr_gmres_converges_on_shifted_problem_and_rank_helps():
         assert np.linalg.norm(x - P.xstar[:, 0]) / np.linalg.norm(P.xstar[:, 0]) < 1e-5
         res[k] = its[0]
     assert res[8] < res[0]
+
+
+# ---------------------------------------------------------------------------
+# Vertex-separator partitions (Section 2.1: the method also applies to them)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dims,boxes,want", [((32, 32), (2, 2), 2 * 32 - 1), ((17, 17), (3, 3), 2 * 2 * 17 - 4),
+                                             ((12, 12, 12), (2, 2, 2), 3 * 12 * 12 - 3 * 12 + 1)])
+def test_vertex_separator_interface_counts_and_block_diagonal_B(dims, boxes, want):
+    """The interface is exactly the separator planes (closed-form counts by
+    inclusion-exclusion) and B has no coupling between different parts' interiors."""
+    rp, ci, v = slrgen.laplacian(dims)
+    part = slrgen.box_partition_vsep(dims, boxes)
+    p = int(np.prod(boxes))
+    o = dd_order(rp, ci, part, p)
+    assert o.s == want == int(np.sum(part < 0))
+    Bi, E, C, App = split_blocks(rp, ci, v, o)
+    B = App[:o.n_I, :o.n_I].tocoo()
+    owner = np.repeat(np.arange(p), np.diff(o.int_off))
+    assert np.all(owner[B.row] == owner[B.col])
+    assert E.nnz > 0
+
+
+def test_vertex_separator_slr_full_rank_is_exact_and_pcg_converges():
+    P = slrgen.make_problem("vsep", (20, 20), (2, 2), 4, separators=True)
+    s = dd_order(P.rowptr, P.colind, P.part, P.nparts).s
+    full = SLR(P.rowptr, P.colind, P.val, P.part, P.nparts, s, eig="dense")
+    A = full.App.toarray()
+    M = np.stack([full.apply(e) for e in np.eye(A.shape[0])], axis=1)
+    assert np.allclose(M @ A, np.eye(A.shape[0]), atol=1e-9)
+    slr = SLR(P.rowptr, P.colind, P.val, P.part, P.nparts, 4)
+    x, its, rels, oks = slr_pcg(slr, P.b[:, 0])
+    assert oks[0] and np.linalg.norm(x - P.xstar[:, 0]) / np.linalg.norm(P.xstar[:, 0]) < 1e-6
