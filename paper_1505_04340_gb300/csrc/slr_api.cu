@@ -90,6 +90,25 @@ void dfree(slr_handle h, T*& p, size_t count) {
     p = nullptr;
 }
 
+// A device buffer of the handle freed when it goes out of scope (also on an early
+// error return).
+template <typename T>
+struct ScopedBuf {
+    slr_handle h;
+    T* p = nullptr;
+    size_t n = 0;
+    explicit ScopedBuf(slr_handle hh) : h(hh) {}
+    ScopedBuf(const ScopedBuf&) = delete;
+    ScopedBuf& operator=(const ScopedBuf&) = delete;
+    ~ScopedBuf() {
+        if (p) dfree(h, p, n);
+    }
+    slr_status alloc(size_t count) {
+        n = count;
+        return dalloc(h, &p, count);
+    }
+};
+
 template <typename TD, typename TS>
 slr_status upload(slr_handle h, TD** p, const std::vector<TS>& v) {
     CS(dalloc(h, p, v.size()));
@@ -660,17 +679,16 @@ slr_status device_band_factor(slr_handle h, cudaStream_t st) {
     h->bf_scr_len = std::max<int64_t>(soff[p], 1);
     CS(dalloc(h, &h->bf_scr, (size_t)h->bf_scr_len));
     CS(upload(h, &h->bf_soff, soff));
-    BandBlock* dband = nullptr;
-    int32_t* bad = nullptr;
-    CS(upload(h, &dband, hs.band));
-    CS(dalloc(h, &bad, 1));
-    CK(cudaMemsetAsync(bad, 0xff, sizeof(int32_t), st));   // -1: no failure
-    CK(launch_band_factor(dband, p, h->a_rp, h->a_ci, h->a_v, h->bf_scr, h->bf_soff, bad, hs.indefinite, st));
+    ScopedBuf<BandBlock> dband(h);
+    ScopedBuf<int32_t> bad(h);
+    CS(dband.alloc(hs.band.size()));
+    CK(cudaMemcpyAsync(dband.p, hs.band.data(), sizeof(BandBlock) * hs.band.size(), cudaMemcpyHostToDevice, st));
+    CS(bad.alloc(1));
+    CK(cudaMemsetAsync(bad.p, 0xff, sizeof(int32_t), st));   // -1: no failure
+    CK(launch_band_factor(dband.p, p, h->a_rp, h->a_ci, h->a_v, h->bf_scr, h->bf_soff, bad.p, hs.indefinite, st));
     int32_t hb = -1;
-    CK(cudaMemcpyAsync(&hb, bad, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(&hb, bad.p, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    dfree(h, dband, hs.band.size());
-    dfree(h, bad, 1);
     if (hb >= 0) {
         if (hs.indefinite) {
             set_error("B_" + std::to_string(hb) + " has a zero pivot in its symmetric factorisation");
@@ -1082,21 +1100,14 @@ slr_status gmres_column(slr_handle h, const double* b, double* x, double tol, in
                         cudaStream_t st, int32_t* its_out, double* rel_out) {
     const int32_t n = h->hs.n;
     const int64_t nn = n;
-    double *V = nullptr, *Z = nullptr, *w = nullptr, *hcol = nullptr, *part = nullptr, *sc = nullptr;
-    CS(dalloc(h, &V, (size_t)nn * (m + 1)));
-    CS(dalloc(h, &Z, (size_t)nn * m));
-    CS(dalloc(h, &w, (size_t)nn));
-    CS(dalloc(h, &hcol, (size_t)2 * (m + 1) + 2));
-    CS(dalloc(h, &part, (size_t)(m + 1) * kRedBlocks));
-    CS(dalloc(h, &sc, 2));
-    auto release = [&]() {
-        dfree(h, V, (size_t)nn * (m + 1));
-        dfree(h, Z, (size_t)nn * m);
-        dfree(h, w, (size_t)nn);
-        dfree(h, hcol, (size_t)2 * (m + 1) + 2);
-        dfree(h, part, (size_t)(m + 1) * kRedBlocks);
-        dfree(h, sc, 2);
-    };
+    ScopedBuf<double> bV(h), bZ(h), bw(h), bh(h), bp(h), bs(h);
+    CS(bV.alloc((size_t)nn * (m + 1)));
+    CS(bZ.alloc((size_t)nn * m));
+    CS(bw.alloc((size_t)nn));
+    CS(bh.alloc((size_t)2 * (m + 1) + 2));
+    CS(bp.alloc((size_t)(m + 1) * kRedBlocks));
+    CS(bs.alloc(2));
+    double *V = bV.p, *Z = bZ.p, *w = bw.p, *hcol = bh.p, *part = bp.p, *sc = bs.p;
     slr_status err = SLR_OK;
     auto norm2 = [&](const double* v) -> double {   // ||v||, synchronising
         if (launch_dots(nn, 1, v, nn, v, nn, part, sc, 1, st) != cudaSuccess) err = SLR_ERR_CUDA;
@@ -1111,7 +1122,7 @@ slr_status gmres_column(slr_handle h, const double* b, double* x, double tol, in
     };
     CK(cudaMemsetAsync(x, 0, sizeof(double) * nn, st));
     const double bnorm = norm2(b);
-    if (err != SLR_OK) { release(); return err; }
+    if (err != SLR_OK) return err;
     int32_t its = 0;
     bool first = true;
     std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), g(m + 1), hv(2 * (m + 1) + 2), y(m);
@@ -1176,7 +1187,6 @@ slr_status gmres_column(slr_handle h, const double* b, double* x, double tol, in
         CK(residual(false));
         rel = norm2(w) / bnorm;
     }
-    release();
     *its_out = its;
     *rel_out = rel;
     return err;

@@ -27,10 +27,16 @@ from paper_1505_04340_gb300 import SLR  # noqa: E402
 
 
 def _solve(P, precision, nrhs, maxit):
+    import time
     h = SLR(P.rowptr, P.colind, P.val, P.part, P.nparts, k=P.k, lanczos_steps=P.lanczos_steps,
             precision=precision, nrhs_max=nrhs, flexible_cg=(precision == "mixed"))
     B = torch.tensor(np.ascontiguousarray(P.b[:, :nrhs]), device="cuda")
+    h.pcg(B if nrhs > 1 else B[:, 0], maxit=maxit)           # builds the CG graph for this width
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
     x, its, rel, st = h.pcg(B if nrhs > 1 else B[:, 0], maxit=maxit)
+    torch.cuda.synchronize()
+    print(f"{P.name} {precision}: setup {h.get_info()['setup_seconds']} s, solve {time.perf_counter() - t0:.3f} s")
     X = x.cpu().numpy().reshape(P.n, -1)
     return h, X, its, rel, st
 
