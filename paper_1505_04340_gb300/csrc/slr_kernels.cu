@@ -144,76 +144,113 @@ __device__ __forceinline__ void gather_t(const CView<T>& cf, int J, int gt, int 
     }
 }
 
-// Forward task (one CTA of NW warps): t_J into ts, then rows tk.y .. tk.y + tk.z - 1
-// of w_J = M_J t_J (panel task: a warp per row, lanes over the columns, 8 loads in
-// flight) or of x_J = L_JJ^{-1} t_J (diagonal task: lane = row, the warps split
-// the columns, partial sums added in a fixed order).
-template <typename T, int NW>
-__device__ void cfwd_task_cta(const CView<T>& cf, const int4 tk, bool pan, T* ts, T (*red)[33], const T* g,
-                              int64_t ldg, T* xf, int32_t nrhs) {
+// Forward task (one CTA of NW warps) on RB right-hand sides j0 .. j0 + RB - 1: t_J of
+// each into ts (column b at ts + b * tstride), then rows tk.y .. tk.y + tk.z - 1 of
+// w_J = M_J t_J (panel task: a warp per row, lanes over the columns, 8 loads in
+// flight) or of x_J = L_JJ^{-1} t_J (diagonal task: lane = row, the warps split the
+// columns, partial sums added in a fixed order).  Each matrix entry is loaded once
+// for the RB columns; every column sees the same sequence of multiply-adds for any
+// RB, so a column gives the same bits alone and in a block.
+template <typename T, int NW, int RB>
+__device__ void cfwd_task_rb(const CView<T>& cf, const int4 tk, bool pan, T* ts, int tstride, T (*red)[33],
+                             const T* g, int64_t ldg, T* xf, int j0) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int32_t J = tk.x, a0 = cf.c0[J], nJ = cf.c0[J + 1] - a0;
-    for (int j = 0; j < nrhs; ++j) {
-        gather_t(cf, J, threadIdx.x, NW * 32, ts, g, ldg, j);
-        __syncthreads();
-        if (pan) {
-            const T* P = cf.panel + cf.pan_off[J];
-            for (int pr = warp; pr < tk.z; pr += NW) {
-                const int64_t p = tk.y + pr;
-                const T* Pp = P + p * nJ;
-                T acc = T(0);
-                int c = lane;
-                for (; c + 7 * 32 < nJ; c += 8 * 32) {
-                    T pv[8];
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) pv[u] = Pp[c + 32 * u];
+    for (int b = 0; b < RB; ++b) gather_t(cf, J, threadIdx.x, NW * 32, ts + b * tstride, g, ldg, j0 + b);
+    __syncthreads();
+    if (pan) {
+        const T* P = cf.panel + cf.pan_off[J];
+        for (int pr = warp; pr < tk.z; pr += NW) {
+            const int64_t p = tk.y + pr;
+            const T* Pp = P + p * nJ;
+            T acc[RB];
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) acc += pv[u] * ts[c + 32 * u];
-                }
-                for (; c < nJ; c += 32) acc += Pp[c] * ts[c];
-                acc = warp_sum(acc);
-                if (lane == 0) cf.wbuf[cf.r_off[J] + p + (int64_t)j * cf.nrow] = acc;
+            for (int b = 0; b < RB; ++b) acc[b] = T(0);
+            int c = lane;
+            for (; c + 7 * 32 < nJ; c += 8 * 32) {
+                T pv[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) pv[u] = Pp[c + 32 * u];
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+#pragma unroll
+                    for (int b = 0; b < RB; ++b) acc[b] += pv[u] * ts[b * tstride + c + 32 * u];
             }
-        } else {
-            const T* D = cf.dinv + cf.dinv_off[J];
-            const int il = tk.y + lane;
-            const int ncol = tk.y + tk.z;   // columns 0 .. ncol-1 reach these rows
-            const int chunk = (ncol + NW - 1) / NW;
-            const int jb = warp * chunk, je = min(ncol, jb + chunk);
-            T acc = T(0);
-            if (lane < tk.z) {
-                const int jend = min(je, il + 1);
-                int jj = jb;
-                for (; jj + 7 < jend; jj += 8) {
-                    T d[8];
+            for (; c < nJ; c += 32) {
+                const T pv = Pp[c];
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) d[u] = D[packed_col(jj + u, nJ) + (il - jj - u)];
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) acc += d[u] * ts[jj + u];
-                }
-                for (; jj < jend; ++jj) acc += D[packed_col(jj, nJ) + (il - jj)] * ts[jj];
+                for (int b = 0; b < RB; ++b) acc[b] += pv * ts[b * tstride + c];
             }
-            red[warp][lane] = acc;
+#pragma unroll
+            for (int b = 0; b < RB; ++b) {
+                const T v = warp_sum(acc[b]);
+                if (lane == 0) cf.wbuf[cf.r_off[J] + p + (int64_t)(j0 + b) * cf.nrow] = v;
+            }
+        }
+    } else {
+        const T* D = cf.dinv + cf.dinv_off[J];
+        const int il = tk.y + lane;
+        const int ncol = tk.y + tk.z;   // columns 0 .. ncol-1 reach these rows
+        const int chunk = (ncol + NW - 1) / NW;
+        const int jb = warp * chunk, je = min(ncol, jb + chunk);
+        T acc[RB];
+#pragma unroll
+        for (int b = 0; b < RB; ++b) acc[b] = T(0);
+        if (lane < tk.z) {
+            const int jend = min(je, il + 1);
+            int jj = jb;
+            for (; jj + 7 < jend; jj += 8) {
+                T d[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) d[u] = D[packed_col(jj + u, nJ) + (il - jj - u)];
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+#pragma unroll
+                    for (int b = 0; b < RB; ++b) acc[b] += d[u] * ts[b * tstride + jj + u];
+            }
+            for (; jj < jend; ++jj) {
+                const T d = D[packed_col(jj, nJ) + (il - jj)];
+#pragma unroll
+                for (int b = 0; b < RB; ++b) acc[b] += d * ts[b * tstride + jj];
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < RB; ++b) {
+            red[warp][lane] = acc[b];
             __syncthreads();
             if (warp == 0) {
                 T v = T(0);
 #pragma unroll 8
                 for (int w = 0; w < NW; ++w) v += red[w][lane];
-                if (lane < tk.z) xf[a0 + il + (int64_t)j * cf.s] = v;
+                if (lane < tk.z) xf[a0 + il + (int64_t)(j0 + b) * cf.s] = v;
             }
+            __syncthreads();
         }
-        __syncthreads();
     }
+    __syncthreads();
 }
 
-// Backward task (one CTA of NW warps): columns c = tk.y .. tk.y + tk.z - 1 of
-// x_J = L_JJ^{-T} y_J - M_J^T x_{R_J}.  The diagonal part runs a warp per column
-// (lanes over column c of L_JJ^{-1}, contiguous in the packed layout); the panel
-// part has lanes over the columns and the warps splitting the panel rows, DEPTH
-// loads in flight per lane.  Optional scatter of the result to DD order.
-template <typename T, int NW, int DEPTH>
-__device__ void cbwd_task_cta(const CView<T>& cf, const int4 tk, T* us, T (*red)[33], const T* yf, T* xf, T* y_dd,
-                              int64_t ldy, int32_t nrhs) {
+// All nrhs columns: blocks of 4 while ts holds 4 columns (rbmax = 4), then one at a time.
+template <typename T, int NW>
+__device__ void cfwd_task_cta(const CView<T>& cf, const int4 tk, bool pan, T* ts, int tstride, int rbmax,
+                              T (*red)[33], const T* g, int64_t ldg, T* xf, int32_t nrhs) {
+    int j0 = 0;
+    if (rbmax >= 4)
+        for (; j0 + 4 <= nrhs; j0 += 4) cfwd_task_rb<T, NW, 4>(cf, tk, pan, ts, tstride, red, g, ldg, xf, j0);
+    for (; j0 < nrhs; ++j0) cfwd_task_rb<T, NW, 1>(cf, tk, pan, ts, tstride, red, g, ldg, xf, j0);
+}
+
+// Backward task (one CTA of NW warps) on RB right-hand sides: columns
+// c = tk.y .. tk.y + tk.z - 1 of x_J = L_JJ^{-T} y_J - M_J^T x_{R_J}.  The diagonal
+// part runs a warp per column (lanes over column c of L_JJ^{-1}, contiguous in the
+// packed layout); the panel part has lanes over the columns and the warps splitting
+// the panel rows, DEPTH loads in flight per lane.  Each matrix entry is loaded once
+// for the RB columns, with the same per-column sequence of multiply-adds for any RB.
+// Optional scatter of the result to DD order.  us: RB x 32.
+template <typename T, int NW, int DEPTH, int RB>
+__device__ void cbwd_task_rb(const CView<T>& cf, const int4 tk, T* us, T (*red)[33], const T* yf, T* xf, T* y_dd,
+                             int64_t ldy, int j0) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int32_t J = tk.x, a0 = cf.c0[J], nJ = cf.c0[J + 1] - a0, jl = tk.y + lane;
     const int64_t nr = cf.r_off[J + 1] - cf.r_off[J];
@@ -221,55 +258,85 @@ __device__ void cbwd_task_cta(const CView<T>& cf, const int4 tk, T* us, T (*red)
     const T* Pn = cf.panel + cf.pan_off[J] + jl;
     const T* D = cf.dinv + cf.dinv_off[J];
     const int64_t chunk = (nr + NW - 1) / NW, pb = warp * chunk, pe = min(nr, pb + chunk);
-    for (int j = 0; j < nrhs; ++j) {
-        const T* y = yf + a0 + (int64_t)j * cf.s;
-        const T* x = xf + (int64_t)j * cf.s;
-        for (int cc = warp; cc < tk.z; cc += NW) {
-            const int c = tk.y + cc;
-            const T* Dc = D + packed_col(c, nJ) - c;   // Dc[i] = (L_JJ^{-1})[i, c], i >= c
-            T acc = T(0);
-            int i = c + lane;
-            for (; i + 7 * 32 < nJ; i += 8 * 32) {
-                T d[8], yv[8];
+    const T* y = yf + a0 + (int64_t)j0 * cf.s;
+    const T* x = xf + (int64_t)j0 * cf.s;
+    for (int cc = warp; cc < tk.z; cc += NW) {
+        const int c = tk.y + cc;
+        const T* Dc = D + packed_col(c, nJ) - c;   // Dc[i] = (L_JJ^{-1})[i, c], i >= c
+        T acc[RB];
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    d[u] = Dc[i + 32 * u];
-                    yv[u] = y[i + 32 * u];
-                }
+        for (int b = 0; b < RB; ++b) acc[b] = T(0);
+        int i = c + lane;
+        for (; i + 7 * 32 < nJ; i += 8 * 32) {
+            T d[8];
 #pragma unroll
-                for (int u = 0; u < 8; ++u) acc += d[u] * yv[u];
-            }
-            for (; i < nJ; i += 32) acc += Dc[i] * y[i];
-            acc = warp_sum(acc);
-            if (lane == 0) us[cc] = acc;
+            for (int u = 0; u < 8; ++u) d[u] = Dc[i + 32 * u];
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+#pragma unroll
+                for (int b = 0; b < RB; ++b) acc[b] += d[u] * y[(int64_t)b * cf.s + i + 32 * u];
         }
-        T acc = T(0);
-        if (lane < tk.z) {
-            int64_t p = pb;
-            for (; p + DEPTH - 1 < pe; p += DEPTH) {
-                T pv[DEPTH], xv[DEPTH];
+        for (; i < nJ; i += 32) {
+            const T d = Dc[i];
 #pragma unroll
-                for (int u = 0; u < DEPTH; ++u) {
-                    pv[u] = Pn[(p + u) * nJ];
-                    xv[u] = x[R[p + u]];
-                }
-#pragma unroll
-                for (int u = 0; u < DEPTH; ++u) acc += pv[u] * xv[u];
-            }
-            for (; p < pe; ++p) acc += Pn[p * nJ] * x[R[p]];
+            for (int b = 0; b < RB; ++b) acc[b] += d * y[(int64_t)b * cf.s + i];
         }
-        red[warp][lane] = acc;
+#pragma unroll
+        for (int b = 0; b < RB; ++b) {
+            const T v = warp_sum(acc[b]);
+            if (lane == 0) us[b * 32 + cc] = v;
+        }
+    }
+    T acc[RB];
+#pragma unroll
+    for (int b = 0; b < RB; ++b) acc[b] = T(0);
+    if (lane < tk.z) {
+        int64_t p = pb;
+        for (; p + DEPTH - 1 < pe; p += DEPTH) {
+            T pv[DEPTH];
+            int32_t rr[DEPTH];
+#pragma unroll
+            for (int u = 0; u < DEPTH; ++u) {
+                pv[u] = Pn[(p + u) * nJ];
+                rr[u] = R[p + u];
+            }
+#pragma unroll
+            for (int u = 0; u < DEPTH; ++u)
+#pragma unroll
+                for (int b = 0; b < RB; ++b) acc[b] += pv[u] * x[(int64_t)b * cf.s + rr[u]];
+        }
+        for (; p < pe; ++p) {
+            const T pv = Pn[p * nJ];
+            const int32_t r = R[p];
+#pragma unroll
+            for (int b = 0; b < RB; ++b) acc[b] += pv * x[(int64_t)b * cf.s + r];
+        }
+    }
+#pragma unroll
+    for (int b = 0; b < RB; ++b) {
+        red[warp][lane] = acc[b];
         __syncthreads();
         if (warp == 0 && lane < tk.z) {
             T v = T(0);
 #pragma unroll 8
             for (int w = 0; w < NW; ++w) v += red[w][lane];
-            const T r = us[lane] - v;
-            xf[a0 + jl + (int64_t)j * cf.s] = r;
-            if (y_dd) y_dd[cf.cperm[a0 + jl] + (int64_t)j * ldy] = r;
+            const T r = us[b * 32 + lane] - v;
+            xf[a0 + jl + (int64_t)(j0 + b) * cf.s] = r;
+            if (y_dd) y_dd[cf.cperm[a0 + jl] + (int64_t)(j0 + b) * ldy] = r;
         }
         __syncthreads();
     }
+}
+
+// All nrhs columns: blocks of 4 while us holds 4 columns (rb4), then one at a time
+// (DEPTH4: loads in flight per lane in a block of 4).
+template <typename T, int NW, int DEPTH, int DEPTH4>
+__device__ void cbwd_task_cta(const CView<T>& cf, const int4 tk, T* us, bool rb4, T (*red)[33], const T* yf, T* xf,
+                              T* y_dd, int64_t ldy, int32_t nrhs) {
+    int j0 = 0;
+    if (rb4)
+        for (; j0 + 4 <= nrhs; j0 += 4) cbwd_task_rb<T, NW, DEPTH4, 4>(cf, tk, us, red, yf, xf, y_dd, ldy, j0);
+    for (; j0 < nrhs; ++j0) cbwd_task_rb<T, NW, DEPTH, 1>(cf, tk, us, red, yf, xf, y_dd, ldy, j0);
 }
 
 // Synchronises the NT threads of a group: the whole CTA (GROUPS = 1) or group
@@ -433,24 +500,28 @@ constexpr int kSmallT = 256;                  // threads per supernode group of 
 // level has more tasks than there are SMs, so that several CTAs share an SM;
 // 32 for the few wide tasks near the root)
 // forward: CTA q runs panel task q (q < np) or diagonal task q - np of the level
+// dynamic shared memory: t_J of rbmax right-hand sides, tstride elements apart
 template <typename T, int NW>
 __global__ void __launch_bounds__(NW * 32, NW == 8 ? 4 : 1)
-k_cfwd_level(const CView<T> cf, int32_t t0, int32_t p0, int32_t np, const T* g, int64_t ldg, T* xf, int32_t nrhs) {
+k_cfwd_level(const CView<T> cf, int32_t t0, int32_t p0, int32_t np, const T* g, int64_t ldg, T* xf, int32_t nrhs,
+             int32_t tstride, int32_t rbmax) {
     extern __shared__ __align__(16) unsigned char csm[];
     __shared__ T red[NW][33];
     const int q = blockIdx.x;
     const bool pan = q < np;
-    cfwd_task_cta<T, NW>(cf, pan ? cf.ptasks[p0 + q] : cf.tasks[t0 + q - np], pan, reinterpret_cast<T*>(csm), red, g,
-                         ldg, xf, nrhs);
+    cfwd_task_cta<T, NW>(cf, pan ? cf.ptasks[p0 + q] : cf.tasks[t0 + q - np], pan, reinterpret_cast<T*>(csm), tstride,
+                         rbmax, red, g, ldg, xf, nrhs);
 }
 
-// backward: one CTA per column task, 16 (FP32) or 8 (FP64) panel loads in flight per lane
+// backward: one CTA per column task, 16 (FP32) or 8 (FP64) panel loads in flight per
+// lane for one right-hand side, 4 for a block of four
 template <typename T, int NW>
 __global__ void __launch_bounds__(NW * 32, NW == 8 ? 4 : 1)
 k_cbwd_level(const CView<T> cf, int32_t t0, const T* yf, T* xf, T* y_dd, int64_t ldy, int32_t nrhs) {
     __shared__ T red[NW][33];
-    __shared__ T us[32];
-    cbwd_task_cta<T, NW, sizeof(T) == 4 ? 16 : 8>(cf, cf.tasks[t0 + blockIdx.x], us, red, yf, xf, y_dd, ldy, nrhs);
+    __shared__ T us[4 * 32];
+    cbwd_task_cta<T, NW, sizeof(T) == 4 ? 16 : 8, 4>(cf, cf.tasks[t0 + blockIdx.x], us, true, red, yf, xf, y_dd, ldy,
+                                                      nrhs);
 }
 
 // dynamic shared memory: the stage buffer of cap elements
@@ -683,7 +754,7 @@ k_cfwd_persistent(const CView<T> cf, const T* g, int64_t ldg, T* xf, int32_t nrh
             any = nt + np > 0;
             for (int q = blockIdx.x; q < np + nt; q += gridDim.x) {
                 const bool pan = q < np;
-                cfwd_task_cta<T, kPersW>(cf, pan ? cf.ptasks[p0 + q] : cf.tasks[t0 + q - np], pan, sm, red, g, ldg,
+                cfwd_task_cta<T, kPersW>(cf, pan ? cf.ptasks[p0 + q] : cf.tasks[t0 + q - np], pan, sm, 0, 1, red, g, ldg,
                                          xf, nrhs);
             }
         }
@@ -713,7 +784,7 @@ k_cbwd_persistent(const CView<T> cf, const T* yf, T* xf, T* y_dd, int64_t ldy, i
             const int t0 = cf.lev_task_ptr[l], nt = cf.lev_task_ptr[l + 1] - t0;
             any = nt > 0;
             for (int q = blockIdx.x; q < nt; q += gridDim.x)
-                cbwd_task_cta<T, kPersW, 8>(cf, cf.tasks[t0 + q], sm, red, yf, xf, y_dd, ldy, nrhs);
+                cbwd_task_cta<T, kPersW, 8, 4>(cf, cf.tasks[t0 + q], sm, false, red, yf, xf, y_dd, ldy, nrhs);
         }
         if (any && --steps_left > 0) grid_barrier(cf.bar, ++round * gridDim.x, cf.err);
     }
@@ -970,23 +1041,34 @@ cudaError_t launch_spmv_e(const DevOperator<T>& op, int32_t nI, const T* y, int6
 
 // Grid of a persistent solve on the current device: one CTA per SM (fewer if
 // no step has that many CTA tasks), 0 if the kernel cannot be co-resident.
+// Raises a kernel's dynamic shared-memory limit to the opt-in maximum less its
+// static shared memory, once per kernel (the limit is process-wide per kernel, so
+// it is never set per launch).  False if the device refuses.
+bool raise_smem_once(const void* kern) {
+    static std::mutex mu;
+    static std::vector<const void*> raised;
+    std::lock_guard<std::mutex> lk(mu);
+    if (std::find(raised.begin(), raised.end(), kern) != raised.end()) return true;
+    int dev = 0, optin = 0;
+    cudaFuncAttributes fa;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+        cudaFuncGetAttributes(&fa, kern) != cudaSuccess ||
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             optin - (int)fa.sharedSizeBytes) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    raised.push_back(kern);
+    return true;
+}
+constexpr size_t kLevSmem = 200 * 1024;   // dynamic shared memory a per-level forward kernel may take
+
 template <typename K>
 int pers_grid(K kern, size_t smem, int32_t max_cta_tasks) {
     int dev = 0, nsm = 0, occ = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
-    if (smem > 48 * 1024) {
-        // the limit is process-wide per kernel: raised once, to the opt-in maximum
-        static std::mutex mu;
-        static std::vector<const void*> raised;
-        std::lock_guard<std::mutex> lk(mu);
-        if (std::find(raised.begin(), raised.end(), (const void*)kern) == raised.end()) {
-            if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) != cudaSuccess) {
-                cudaGetLastError();
-                return 0;
-            }
-            raised.push_back((const void*)kern);
-        }
-    }
+    if (smem > 48 * 1024 && !raise_smem_once((const void*)kern)) return 0;
     if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kPersT, smem) != cudaSuccess || occ < 1) {
         cudaGetLastError();
@@ -1097,10 +1179,16 @@ cudaError_t launch_c_forward(const DevCFactor<T>& cf, const T* g_dd, int64_t ldg
         const int t0 = cf.lev_task_ptr[l], nt = cf.lev_task_ptr[l + 1] - t0;
         const int p0 = cf.lev_ptask_ptr[l], np = cf.lev_ptask_ptr[l + 1] - p0;
         if (nt + np == 0) continue;
-        if (nt + np > cf.nsm)
-            k_cfwd_level<T, 8><<<nt + np, 256, cf.max_n * sizeof(T), st>>>(v, t0, p0, np, g_dd, ldg, xf, nrhs);
+        // blocks of four right-hand sides share each matrix load when t_J of four fits
+        const bool wide = nt + np <= cf.nsm;
+        const void* kern = wide ? (const void*)k_cfwd_level<T, 32> : (const void*)k_cfwd_level<T, 8>;
+        int32_t rbmax = (nrhs >= 4 && 4 * (size_t)cf.max_n * sizeof(T) <= kLevSmem) ? 4 : 1;
+        if (rbmax == 4 && 4 * (size_t)cf.max_n * sizeof(T) > 40 * 1024 && !raise_smem_once(kern)) rbmax = 1;
+        const size_t smem = (size_t)rbmax * cf.max_n * sizeof(T);
+        if (!wide)
+            k_cfwd_level<T, 8><<<nt + np, 256, smem, st>>>(v, t0, p0, np, g_dd, ldg, xf, nrhs, cf.max_n, rbmax);
         else
-            k_cfwd_level<T, 32><<<nt + np, 1024, cf.max_n * sizeof(T), st>>>(v, t0, p0, np, g_dd, ldg, xf, nrhs);
+            k_cfwd_level<T, 32><<<nt + np, 1024, smem, st>>>(v, t0, p0, np, g_dd, ldg, xf, nrhs, cf.max_n, rbmax);
         counted();
     }
     if (cf.nT > 0) {
