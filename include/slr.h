@@ -106,7 +106,13 @@ typedef struct {
                                pivot signs (no pivoting; a zero pivot returns
                                SLR_ERR_BREAKDOWN), H may have eigenvalues >= 1, and the
                                accelerator is slr_gmres_solve.  0 = SPD.
-                               reserved[10..15] must be 0.                             */
+                               reserved[10]: the order in which the band solve's
+                               subdomain clusters are launched (it sets which
+                               subdomains share SMs; every order gives the same
+                               result, bit for bit): 1 = subdomain order, 2 = most
+                               work first, 3 = most and least work alternating;
+                               0 (default) = automatic (3).
+                               reserved[11..15] must be 0.                             */
 } slr_opts;
 
 typedef struct {

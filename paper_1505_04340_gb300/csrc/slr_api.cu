@@ -124,11 +124,17 @@ slr_status upload(slr_handle h, TD** p, const std::vector<TS>& v) {
     return SLR_OK;
 }
 
+// The band blocks on the device, in the order their clusters are launched
+// (opts.reserved[10]; every order gives the same result, bit for bit).
+slr_status upload_band(slr_handle h, BandBlock** p) {
+    return upload(h, p, band_run_order(h->hs.band, h->opts.reserved[10] ? h->opts.reserved[10] : kBandOrderAuto));
+}
+
 template <typename T>
 slr_status upload_operator(slr_handle h, DevOperator<T>& op, bool with_band) {
     const HostSetup& hs = h->hs;
     const int32_t r = std::max(1, h->opts.nrhs_max);
-    CS(upload(h, &op.band, hs.band));
+    CS(upload_band(h, &op.band));
     if (with_band) CS(upload(h, &op.bfac, hs.bfac));
     op.band_G = hs.band_G;
     op.band_nbuf = h->opts.reserved[2];
@@ -479,7 +485,7 @@ slr_status run_lanczos_deflated(slr_handle h, int32_t k_add, int32_t steps, cuda
     }
     if (reload) {
         dfree(h, op.band, hs.band.size());
-        CS(upload(h, &op.band, hs.band));
+        CS(upload_band(h, &op.band));
         CS(upload(h, &op.bfac, hs.bfac));
         op.band_G = hs.band_G;
     }
@@ -724,7 +730,7 @@ slr_status repack_band(slr_handle h, DevOperator<T>& op, int32_t G) {
     CK(cudaStreamSynchronize(h->stream));
     dfree(h, op.band, old_band);
     dfree(h, op.bfac, (size_t)old_fac);
-    CS(upload(h, &op.band, hs.band));
+    CS(upload_band(h, &op.band));
     if (h->bf_scr) CS(device_band_pack<T>(h, op, h->stream));
     else CS(upload(h, &op.bfac, hs.bfac));
     CK(cudaStreamSynchronize(h->stream));
@@ -1214,8 +1220,8 @@ slr_status slr_setup(int32_t n, const int32_t* rowptr, const int32_t* colind, co
         h->opts.reserved[5] < 0 || h->opts.reserved[5] == 1 ||
         (h->opts.reserved[6] != 0 && h->opts.reserved[6] != 256 && h->opts.reserved[6] != 512) ||
         h->opts.reserved[7] < 0 || h->opts.reserved[7] > 1 || h->opts.reserved[8] < 0 || h->opts.reserved[8] > 1 ||
-        h->opts.reserved[9] < 0 || h->opts.reserved[9] > 1 ||
-        std::any_of(h->opts.reserved + 10, h->opts.reserved + 16, [](int32_t v) { return v != 0; })) {
+        h->opts.reserved[9] < 0 || h->opts.reserved[9] > 1 || h->opts.reserved[10] < 0 || h->opts.reserved[10] > 3 ||
+        std::any_of(h->opts.reserved + 11, h->opts.reserved + 16, [](int32_t v) { return v != 0; })) {
         set_error("invalid options");
         delete h;
         return SLR_ERR_INVALID_ARG;

@@ -221,7 +221,7 @@ k_band_factor(const BandBlock* __restrict__ band, const int32_t* __restrict__ a_
     if (b.m == 0) return;
     const int W = b.w, c = b.c, m = b.m, r0 = b.row0, nt = (W + 31) / 32, tid = threadIdx.x;
     const int64_t WW = (int64_t)W * W;
-    double* S = scr + soff[blockIdx.x];
+    double* S = scr + soff[b.id];
     double* Dst = S + WW;               // D_J = L_JJ^{-1} at Dst + J W^2
     double* Ost = Dst + (int64_t)c * WW;   // O_J = L[J, J-1] at Ost + J W^2 (O_0 = 0)
     double* Sg = Ost + (int64_t)c * WW;    // pivot signs of plane J at Sg + J W
@@ -284,9 +284,10 @@ k_band_pack(const BandBlock* __restrict__ band, int32_t cmax, int32_t G, const d
     if (b.m == 0 || J >= b.c) return;
     const int W = b.w, m = b.m;
     const int64_t WW = (int64_t)W * W;
-    const double* X = scr + soff[i] + WW + (int64_t)J * WW;        // D_J
-    const double* O = scr + soff[i] + WW + (int64_t)(b.c + J) * WW;   // O_J
-    const double* Sg = scr + soff[i] + WW + 2 * (int64_t)b.c * WW;    // pivot signs, plane by plane
+    const double* S0 = scr + soff[b.id];                            // the blocks of subdomain b.id
+    const double* X = S0 + WW + (int64_t)J * WW;                    // D_J
+    const double* O = S0 + WW + (int64_t)(b.c + J) * WW;            // O_J
+    const double* Sg = S0 + WW + 2 * (int64_t)b.c * WW;             // pivot signs, plane by plane
     auto sgn = [&](int plane, int r) -> double { return indef ? Sg[(int64_t)plane * W + r] : 1.0; };
     T* plane = bfac + b.foff + (int64_t)J * G * 2 * (b.SU + b.SL) + (int64_t)g * 2 * (b.SU + b.SL);
     T* Uf = plane;          // O_J      (upper)

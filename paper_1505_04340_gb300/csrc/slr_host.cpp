@@ -267,6 +267,22 @@ void band_assign_blocks(BandBlock& b, int G) {
     }
 }
 
+std::vector<BandBlock> band_run_order(const std::vector<BandBlock>& band, int mode) {
+    std::vector<BandBlock> run(band);
+    if (mode <= 1) return run;
+    auto work = [](const BandBlock& b) { return (int64_t)b.c * b.w * (b.w + 1); };
+    std::stable_sort(run.begin(), run.end(),
+                     [&](const BandBlock& a, const BandBlock& b) { return work(a) > work(b); });
+    if (mode == 2) return run;
+    std::vector<BandBlock> alt;
+    alt.reserve(run.size());
+    for (size_t lo = 0, hi = run.size(); lo < hi;) {
+        alt.push_back(run[lo++]);
+        if (lo < hi) alt.push_back(run[--hi]);
+    }
+    return alt;
+}
+
 void host_band_layout(HostSetup& hs, int32_t G) {
     const int32_t p = hs.p;
     hs.band.assign(p, BandBlock());
@@ -284,6 +300,7 @@ void host_band_layout(HostSetup& hs, int32_t G) {
             }
         bw[i] = w;
         BandBlock& b = hs.band[i];
+        b.id = i;
         b.m = m;
         b.row0 = r0;
         b.w = m ? std::max(w, 1) : 0;

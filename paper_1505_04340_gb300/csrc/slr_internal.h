@@ -35,6 +35,7 @@ struct BandBlock {
     int64_t foff = 0;     // offset of plane 0 in the factor array (elements)
     int32_t SU = 0;       // elements of one upper slice block (32 per segment, widest slice)
     int32_t SL = 0;       // elements of one lower slice block (32 per segment, widest slice)
+    int32_t id = 0;       // the subdomain i (blocks may be launched in another order)
     uint8_t nrb[4] = {0, 0, 0, 0};   // row blocks of each slice (at most 8: 256 rows)
     uint8_t rbmap[4][8] = {};        // block of slice g's local row block rb
 };
@@ -51,6 +52,13 @@ inline int band_cL1(const BandBlock& b, int g, int rb) {
 inline bool band_split_ok(int W, int G) { return (W + 31) / 32 <= 8 * G; }
 // Deal the 32-row blocks of a plane of b.w rows to G slices (fills nrb, rbmap).
 void band_assign_blocks(BandBlock& b, int G);
+// The blocks in the order their clusters are launched: 1 = subdomain order,
+// 2 = heaviest first, 3 = heaviest and lightest alternating (work c W (W+1)).
+std::vector<BandBlock> band_run_order(const std::vector<BandBlock>& band, int mode);
+// The order opts.reserved[10] = 0 selects: with two CTAs per SM the most and
+// least loaded subdomains tend to share SMs (FP64 3-D 64^3: 326 us per B-solve
+// instead of 370 in subdomain order; the HBM-bound FP32 solve does not change).
+constexpr int kBandOrderAuto = 3;
 
 // Supernodal Cholesky factor of the interface matrix C (Eq. 3.1) in a
 // nested-dissection order.  Supernode J owns factor positions [c0[J], c0[J+1]).

@@ -164,7 +164,8 @@ class SLR:
     def __init__(self, rowptr, colind, val, part, nparts, k=16, lanczos_steps=0, theta="lambda_k1",
                  precision="fp64", nrhs_max=1, flexible_cg=False, seed=1, c_leaf=64, verbose=False,
                  band_split=0, host_loop=False, band_slots=0, c_persistent=False, autotune=False, target_kappa=0,
-                 band_threads=0, c_top_zone=True, band_factor="auto", indefinite=False, stream=None):
+                 band_threads=0, c_top_zone=True, band_factor="auto", indefinite=False, band_order=0,
+                 stream=None):
         lib = load()
         self._lib = lib
         self._h = None
@@ -184,6 +185,7 @@ class SLR:
         o.reserved[7] = 0 if c_top_zone else 1   # explicit inverse of the factor's top levels
         o.reserved[8] = {"auto": 0, "host": 1}[band_factor]   # B_i factored on the device or the host
         o.reserved[9] = int(bool(indefinite))    # symmetric indefinite A with an SPD interface
+        o.reserved[10] = int(band_order)         # band-solve cluster launch order, 0 = automatic
         self.rowptr, self.colind = _i32(rowptr), _i32(colind)
         self.val = np.ascontiguousarray(val, dtype=np.float64)
         self.part = _i32(part)

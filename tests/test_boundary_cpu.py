@@ -107,7 +107,7 @@ def test_setup_rejects_bad_input_before_any_device_work(lib):
     assert "range" in lib.slr_last_error_message().decode()
 
 
-@pytest.mark.parametrize("reserved", [{0: 3}, {1: 2}, {2: 1}, {2: 9}, {3: 2}, {4: -1}, {4: 2}, {5: 1}, {5: -3}, {6: 128}, {6: 1024}, {7: 2}, {7: -1}, {8: 2}, {9: 2}, {10: 1}, {15: 1}])
+@pytest.mark.parametrize("reserved", [{0: 3}, {1: 2}, {2: 1}, {2: 9}, {3: 2}, {4: -1}, {4: 2}, {5: 1}, {5: -3}, {6: 128}, {6: 1024}, {7: 2}, {7: -1}, {8: 2}, {9: 2}, {10: 4}, {10: -1}, {11: 1}, {15: 1}])
 def test_setup_rejects_bad_tuning_options(lib, reserved):
     """Band split, host loop, band buffers, C-solve path, autotune, target condition
     number: out-of-range values are refused before any device work."""
