@@ -189,7 +189,8 @@ slr_status upload_operator(slr_handle h, DevOperator<T>& op, bool with_band) {
         d.max_cta_tasks = std::max(d.max_cta_tasks, nt + np);
     }
     // fused levels stage a supernode's [L_JJ^{-1}; M_J] in shared memory when it fits
-    // 36 KB (the rest of the 48 KB default holds the kernels' static arrays)
+    // 36 KB (the rest of the 48 KB default holds the kernels' static arrays); the
+    // forward stages the panel with an odd row stride (n_J | 1), so sizes count it
     {
         const int64_t capmax = 36 * 1024 / (int64_t)sizeof(T);
         d.lev_stage.assign(c.nlev, 0);
@@ -200,7 +201,7 @@ slr_status upload_operator(slr_handle h, DevOperator<T>& op, bool with_band) {
             for (int32_t q = c.lev_sn_ptr[l]; q < c.lev_sn_ptr[l + 1]; ++q) {
                 const int32_t J = c.lev_sn[q];
                 const int64_t nJ = c.c0[J + 1] - c.c0[J], nr = c.r_off[J + 1] - c.r_off[J];
-                mx = std::max(mx, nJ * (nJ + 1) / 2 + nr * nJ);
+                mx = std::max(mx, nJ * (nJ + 1) / 2 + nr * (nJ | 1));
             }
             d.lev_stage[l] = (int32_t)std::min(mx, capmax);
             d.stage_cap = std::max(d.stage_cap, d.lev_stage[l]);

@@ -384,12 +384,56 @@ __device__ __forceinline__ bool stage_block(const CView<T>& cf, int J, T* stg, i
     return true;
 }
 
+// Odd row stride of a staged panel: a warp reading one column across 32 panel
+// rows then meets every shared-memory bank equally often.
+__device__ __forceinline__ int32_t small_ldp(int32_t nJ) { return nJ | 1; }
+
+// Forward staging of A_J: L_JJ^{-1} packed as stored, then M_J with row stride
+// small_ldp(n_J); false (D and P in HBM, row stride n_J) when it does not fit cap.
+template <typename T, int NT>
+__device__ __forceinline__ bool stage_block_fwd(const CView<T>& cf, int J, T* stg, int cap, int gt, const T*& D,
+                                                const T*& P) {
+    const int32_t nJ = cf.c0[J + 1] - cf.c0[J], nr = (int32_t)(cf.r_off[J + 1] - cf.r_off[J]);
+    const int32_t nd = nJ * (nJ + 1) / 2, ldp = small_ldp(nJ);
+    D = cf.dinv + cf.dinv_off[J];
+    P = cf.panel + cf.pan_off[J];
+    if ((int64_t)nd + (int64_t)nr * ldp > cap) return false;
+    static_assert(sizeof(T) == 4 || sizeof(T) == 8, "4- or 8-byte elements");
+    for (int32_t i = gt; i < nd; i += NT) {
+        const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(stg + i));
+        if constexpr (sizeof(T) == 8)
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(D + i) : "memory");
+        else
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(D + i) : "memory");
+    }
+    // panel row q (n_J values, contiguous in HBM) to stg + nd + q * ldp, a warp per row
+    constexpr int nw = NT / 32;
+    const int lane = gt & 31;
+    for (int32_t q = gt >> 5; q < nr; q += nw)
+        for (int32_t c = lane; c < nJ; c += 32) {
+            const uint32_t d = static_cast<uint32_t>(__cvta_generic_to_shared(stg + nd + q * ldp + c));
+            const T* src = P + (int64_t)q * nJ + c;
+            if constexpr (sizeof(T) == 8)
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(src) : "memory");
+            else
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
+        }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+    D = stg;
+    P = stg + nd;
+    return true;
+}
+
 // Fused levels: one group of NT threads (a CTA, or a part of one) per supernode J
 // with n_J <= kSmallN and |R_J| <= kSmallR.  Both directions use the stacked
 // matrix A_J = [L_JJ^{-1}; M_J] ((n_J + |R_J|) x n_J; row r < n_J of the
 // diagonal block is read from the packed column-major layout).
-// forward: t_J gathered into ts; [x_J; w_J] = A_J t_J with a warp per row of A_J
-// (lanes over the columns, four rows in flight per warp)
+// forward: t_J gathered into ts, then [x_J; w_J] = A_J t_J.  Staged in shared
+// memory, a thread computes a row (columns in order: one multiply-add per column,
+// no cross-lane sums, which on this part's narrow FP64 unit cost more than the
+// products); from HBM, a warp per row keeps the loads coalesced (lanes over the
+// columns, four rows in flight per warp).  A supernode is staged or not whatever
+// the right-hand sides, so every column gets the same bits alone and in a block.
 template <typename T, int NT, int GROUPS>
 __device__ void cfwd_small_cta(const CView<T>& cf, int J, T* ts, const T* g, int64_t ldg, T* xf, int32_t nrhs, T* stg,
                                int cap) {
@@ -398,34 +442,56 @@ __device__ void cfwd_small_cta(const CView<T>& cf, int J, T* ts, const T* g, int
     const int32_t a0 = cf.c0[J], nJ = cf.c0[J + 1] - a0;
     const int64_t nr = cf.r_off[J + 1] - cf.r_off[J], rtot = nJ + nr;
     const T *D, *Pn;
-    const bool staged = stage_block<T, NT>(cf, J, stg, cap, gt, D, Pn);   // lands while t_J is gathered
+    const bool staged = stage_block_fwd<T, NT>(cf, J, stg, cap, gt, D, Pn);   // lands while t_J is gathered
     for (int j = 0; j < nrhs; ++j) {
         gather_t(cf, J, gt, NT, ts, g, ldg, j);
         if (j == 0 && staged) stage_wait();
         group_sync<NT, GROUPS>();
-        for (int64_t r0 = 4 * warp; r0 < rtot; r0 += 4 * nw) {
-            T acc[4] = {T(0), T(0), T(0), T(0)};
-            for (int c = lane; c < nJ; c += 32) {
-                const T tv = ts[c];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int64_t r = r0 + u;
-                    T a = T(0);
-                    if (r < nJ) {
-                        if (c <= r) a = D[packed_col(c, nJ) + (r - c)];
-                    } else if (r < rtot) {
-                        a = Pn[(r - nJ) * nJ + c];
+        if (staged) {
+            const int32_t ldp = small_ldp(nJ);
+            for (int32_t r = gt; r < rtot; r += NT) {
+                T acc = T(0);
+                if (r < nJ) {
+                    // (L_JJ^{-1})[r, c] = D[packed_col(c) + r - c]; the next column's entry is n_J - c - 1 further
+                    int32_t e = r;
+#pragma unroll 4
+                    for (int32_t c = 0; c <= r; ++c) {
+                        acc += D[e] * ts[c];
+                        e += nJ - c - 1;
                     }
-                    acc[u] += a * tv;
+                    xf[a0 + r + (int64_t)j * cf.s] = acc;
+                } else {
+                    const T* Mr = Pn + (r - nJ) * ldp;
+#pragma unroll 4
+                    for (int32_t c = 0; c < nJ; ++c) acc += Mr[c] * ts[c];
+                    cf.wbuf[cf.r_off[J] + (r - nJ) + (int64_t)j * cf.nrow] = acc;
                 }
             }
+        } else {
+            for (int64_t r0 = 4 * warp; r0 < rtot; r0 += 4 * nw) {
+                T acc[4] = {T(0), T(0), T(0), T(0)};
+                for (int c = lane; c < nJ; c += 32) {
+                    const T tv = ts[c];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const T v = warp_sum(acc[u]);
-                const int64_t r = r0 + u;
-                if (lane == 0 && r < rtot) {
-                    if (r < nJ) xf[a0 + r + (int64_t)j * cf.s] = v;
-                    else cf.wbuf[cf.r_off[J] + (r - nJ) + (int64_t)j * cf.nrow] = v;
+                    for (int u = 0; u < 4; ++u) {
+                        const int64_t r = r0 + u;
+                        T a = T(0);
+                        if (r < nJ) {
+                            if (c <= r) a = D[packed_col(c, nJ) + (r - c)];
+                        } else if (r < rtot) {
+                            a = Pn[(r - nJ) * nJ + c];
+                        }
+                        acc[u] += a * tv;
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const T v = warp_sum(acc[u]);
+                    const int64_t r = r0 + u;
+                    if (lane == 0 && r < rtot) {
+                        if (r < nJ) xf[a0 + r + (int64_t)j * cf.s] = v;
+                        else cf.wbuf[cf.r_off[J] + (r - nJ) + (int64_t)j * cf.nrow] = v;
+                    }
                 }
             }
         }
