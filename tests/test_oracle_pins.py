@@ -352,6 +352,31 @@ def test_rank_zero_is_block_lu_with_C():
     assert np.allclose(slr.apply(r), np.linalg.solve(L1 @ U1, r), rtol=1e-10, atol=1e-12)
 
 
+@pytest.mark.parametrize("theta_mode", [THETA_LAMBDA_K1, THETA_ZERO])
+def test_apply_is_inverse_of_dense_M(theta_mode):
+    """Eq. 4.1 formed densely from the blocks, M = [[B, E], [E^T, E^T B^{-1} E + S~]],
+    with S~^{-1} = L^{-T} ((1-theta)^{-1} I + U_k ((I-Lambda_k)^{-1} - (1-theta)^{-1} I) U_k^T) L^{-1}
+    (Eq. 4.7 with Eqs. 4.10-4.11) from a dense eigensolve of H (Eq. 3.2, dense Cholesky
+    of C in DD order): the apply is M^{-1}.  Random coefficients keep lambda_k and
+    lambda_{k+1} apart, so U_k is unique up to signs, which cancel."""
+    P = small_fv()
+    k = 5
+    slr = SLR(P.rowptr, P.colind, P.val, P.part, P.nparts, k, theta_mode=theta_mode, eig="dense")
+    B, E, C = brute.dense_blocks(slr)
+    H = brute.h_from_blocks(B, E, C)
+    w, V = np.linalg.eigh((H + H.T) / 2)
+    lam, U = w[::-1], V[:, ::-1][:, :k]
+    assert lam[k - 1] - lam[k] > 1e-6 * lam[0]
+    theta = lam[k] if theta_mode == THETA_LAMBDA_K1 else 0.0
+    Linv = np.linalg.inv(np.linalg.cholesky(C))
+    G = np.eye(C.shape[0]) / (1 - theta) + U @ np.diag(1 / (1 - lam[:k]) - 1 / (1 - theta)) @ U.T
+    St = np.linalg.inv(Linv.T @ G @ Linv)
+    M = np.block([[B, E], [E.T, E.T @ np.linalg.solve(B, E) + St]])
+    r = np.random.default_rng(8).standard_normal((P.n, 2))
+    want = np.linalg.solve(M, r)
+    assert np.allclose(slr.apply(r), want, rtol=1e-9, atol=1e-11 * np.abs(want).max())
+
+
 def test_apply_symmetric_positive():
     """M^{-1} is symmetric (M = [[B,E],[E^T, E^T B^{-1} E + S~]]) and here positive definite."""
     P = small_fv()
