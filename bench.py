@@ -572,7 +572,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--problem", default="3d64")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--ref-iters", type=int, default=23,
+    ap.add_argument("--ref-iters", type=int, default=22,
                     help="iterations of a full solve of the workload (measured by the GPU arm)")
     ap.add_argument("--ref-sample-its", type=int, default=2)
     ap.add_argument("--profile", action="store_true", help="solves inside an NVTX range only (for ncu)")
