@@ -702,14 +702,39 @@ slr_status host_c_factor(HostSetup& hs, int32_t leaf, int32_t task_rows) {
             }
         }
         if (bad >= 0) break;
+        // panel rows L[R_J, J] = F[R_J, J] L_JJ^{-T}, four rows per pass: four independent
+        // chains, each row's sum in the same order as alone
 #pragma omp parallel for schedule(static) if (nr * nJ > 4096)
-        for (int64_t pr = 0; pr < nr; ++pr) {
-            double* Fp = Fj + (nJ + pr) * nJ;
-            for (int32_t j = 0; j < nJ; ++j) {
-                const double* Fr = Fj + (int64_t)j * nJ;
-                double sum = Fp[j];
-                for (int32_t k = 0; k < j; ++k) sum -= Fp[k] * Fr[k];
-                Fp[j] = sum / Fr[j];
+        for (int64_t p4 = 0; p4 < (nr + 3) / 4; ++p4) {
+            const int64_t pr = 4 * p4;
+            if (pr + 4 <= nr) {
+                double* F0 = Fj + (nJ + pr) * nJ;
+                double *F1 = F0 + nJ, *F2 = F1 + nJ, *F3 = F2 + nJ;
+                for (int32_t j = 0; j < nJ; ++j) {
+                    const double* Fr = Fj + (int64_t)j * nJ;
+                    double s0 = F0[j], s1 = F1[j], s2 = F2[j], s3 = F3[j];
+                    for (int32_t k = 0; k < j; ++k) {
+                        const double r = Fr[k];
+                        s0 -= F0[k] * r;
+                        s1 -= F1[k] * r;
+                        s2 -= F2[k] * r;
+                        s3 -= F3[k] * r;
+                    }
+                    F0[j] = s0 / Fr[j];
+                    F1[j] = s1 / Fr[j];
+                    F2[j] = s2 / Fr[j];
+                    F3[j] = s3 / Fr[j];
+                }
+            } else {
+                for (int64_t q = pr; q < nr; ++q) {
+                    double* Fp = Fj + (nJ + q) * nJ;
+                    for (int32_t j = 0; j < nJ; ++j) {
+                        const double* Fr = Fj + (int64_t)j * nJ;
+                        double sum = Fp[j];
+                        for (int32_t k = 0; k < j; ++k) sum -= Fp[k] * Fr[k];
+                        Fp[j] = sum / Fr[j];
+                    }
+                }
             }
         }
         // update the ancestors: F_T[R_J[a], R_J[b]] -= L[R_J[a], J] . L[R_J[b], J]
@@ -724,13 +749,30 @@ slr_status host_c_factor(HostSetup& hs, int32_t leaf, int32_t task_rows) {
 #pragma omp parallel for schedule(dynamic, 16) if ((nr - b0) * (b1 - b0) * nJ > 100000)
             for (int64_t a = b0; a < nr; ++a) {
                 const double* La = Fj + (nJ + a) * nJ;
-                const int64_t tr = rowpos(T, RJ[a]);
+                const int64_t fb = rowpos(T, RJ[a]) * nT - cf.c0[T];   // F_T[row of R_J[a], col] at fb + col
                 const int64_t bend = std::min(a + 1, b1);
-                for (int64_t b = b0; b < bend; ++b) {
+                int64_t b = b0;
+                for (; b + 4 <= bend; b += 4) {   // four dots per pass over La, each in k order
+                    const double* L0 = Fj + (nJ + b) * nJ;
+                    const double *L1 = L0 + nJ, *L2 = L1 + nJ, *L3 = L2 + nJ;
+                    double d0 = 0.0, d1 = 0.0, d2 = 0.0, d3 = 0.0;
+                    for (int32_t k = 0; k < nJ; ++k) {
+                        const double x = La[k];
+                        d0 += x * L0[k];
+                        d1 += x * L1[k];
+                        d2 += x * L2[k];
+                        d3 += x * L3[k];
+                    }
+                    FT[fb + RJ[b]] -= d0;
+                    FT[fb + RJ[b + 1]] -= d1;
+                    FT[fb + RJ[b + 2]] -= d2;
+                    FT[fb + RJ[b + 3]] -= d3;
+                }
+                for (; b < bend; ++b) {
                     const double* Lbr = Fj + (nJ + b) * nJ;
                     double dot = 0.0;
                     for (int32_t k = 0; k < nJ; ++k) dot += La[k] * Lbr[k];
-                    FT[tr * nT + (RJ[b] - cf.c0[T])] -= dot;
+                    FT[fb + RJ[b]] -= dot;
                 }
             }
             b0 = b1;
