@@ -192,17 +192,31 @@ slr_status host_split_blocks(const int32_t* rowptr, const int32_t* colind, const
 
 // ------------------------------------------------------------------ Section 5.2: B_i
 
-// Lower-triangular inverse of the W x W matrix D (row-major), into X (row-major).
+// Lower-triangular inverse of the W x W matrix D (row-major), into X (row-major):
+// X[r][c] = -(sum over q = c .. r-1 of D[r][q] X[q][c]) / D[r][r], X[c][c] = 1 / D[c][c].
+// Columns are independent; a block of 16 columns walks the rows with the sums of
+// its columns side by side (contiguous in X's rows), each sum over q in ascending
+// order, so every entry is the same as computed column by column.
 static void tri_inverse(int W, const double* D, double* X) {
     for (int i = 0; i < W * W; ++i) X[i] = 0.0;
-    // columns are independent: threads share a large block (serial inside a parallel region)
-#pragma omp parallel for schedule(dynamic, 4) if (W >= 256)
-    for (int c = 0; c < W; ++c) {
-        X[c * W + c] = 1.0 / D[c * W + c];
-        for (int r = c + 1; r < W; ++r) {
-            double s = 0.0;
-            for (int q = c; q < r; ++q) s += D[r * W + q] * X[q * W + c];
-            X[r * W + c] = -s / D[r * W + r];
+    constexpr int CB = 16;
+    const int nblk = (W + CB - 1) / CB;
+    // threads share a large block (serial inside a parallel region)
+#pragma omp parallel for schedule(dynamic, 1) if (W >= 256)
+    for (int bk = 0; bk < nblk; ++bk) {
+        const int c0 = bk * CB, c1 = std::min(W, c0 + CB);
+        double acc[CB];
+        for (int r = c0; r < W; ++r) {
+            const int ce = std::min(r, c1);          // columns c0 .. ce-1 lie left of the diagonal
+            for (int c = c0; c < ce; ++c) acc[c - c0] = 0.0;
+            for (int q = c0; q < r; ++q) {           // column c takes the terms q >= c
+                const double d = D[r * W + q];
+                const double* xq = X + (int64_t)q * W;
+                const int qe = std::min(q + 1, ce);
+                for (int c = c0; c < qe; ++c) acc[c - c0] += d * xq[c];
+            }
+            for (int c = c0; c < ce; ++c) X[r * W + c] = -acc[c - c0] / D[r * W + r];
+            if (r < c1) X[r * W + r] = 1.0 / D[r * W + r];
         }
     }
 }
@@ -746,13 +760,13 @@ slr_status host_c_factor(HostSetup& hs, int32_t leaf, int32_t task_rows) {
             while (b1 < nr && RJ[b1] < cf.c0[T + 1]) ++b1;
             const int32_t nT = cf.c0[T + 1] - cf.c0[T];
             double* FT = F.data() + fo[T];
-#pragma omp parallel for schedule(dynamic, 16) if ((nr - b0) * (b1 - b0) * nJ > 100000)
-            for (int64_t a = b0; a < nr; ++a) {
+            // row a of F_T (position R_J[a]) -= L[R_J[a], J] . L[R_J[b], J] for b0 <= b <= a, b < b1;
+            // every dot runs over k in ascending order whatever the tiling
+            auto dots = [&](int64_t a, int64_t bs, int64_t be) {
                 const double* La = Fj + (nJ + a) * nJ;
                 const int64_t fb = rowpos(T, RJ[a]) * nT - cf.c0[T];   // F_T[row of R_J[a], col] at fb + col
-                const int64_t bend = std::min(a + 1, b1);
-                int64_t b = b0;
-                for (; b + 4 <= bend; b += 4) {   // four dots per pass over La, each in k order
+                int64_t b = bs;
+                for (; b + 4 <= be; b += 4) {   // four dots per pass over La
                     const double* L0 = Fj + (nJ + b) * nJ;
                     const double *L1 = L0 + nJ, *L2 = L1 + nJ, *L3 = L2 + nJ;
                     double d0 = 0.0, d1 = 0.0, d2 = 0.0, d3 = 0.0;
@@ -768,12 +782,43 @@ slr_status host_c_factor(HostSetup& hs, int32_t leaf, int32_t task_rows) {
                     FT[fb + RJ[b + 2]] -= d2;
                     FT[fb + RJ[b + 3]] -= d3;
                 }
-                for (; b < bend; ++b) {
+                for (; b < be; ++b) {
                     const double* Lbr = Fj + (nJ + b) * nJ;
                     double dot = 0.0;
                     for (int32_t k = 0; k < nJ; ++k) dot += La[k] * Lbr[k];
                     FT[fb + RJ[b]] -= dot;
                 }
+            };
+            // four rows a at a time: 4 x 4 tiles of dots over the b they all take (each
+            // row of the panel is then read once per four dots), the rest row by row
+            const int64_t ngrp = (nr - b0 + 3) / 4;
+#pragma omp parallel for schedule(dynamic, 4) if ((nr - b0) * (b1 - b0) * nJ > 100000)
+            for (int64_t gi = 0; gi < ngrp; ++gi) {
+                const int64_t a0 = b0 + 4 * gi, a1 = std::min(nr, a0 + 4);
+                int64_t bt = b0;   // tiles cover b0 .. bt-1 for every row of the group
+                if (a1 - a0 == 4) {
+                    const int64_t btile = std::min(a0 + 1, b1);   // every row of the group takes b < btile
+                    const double* A0 = Fj + (nJ + a0) * nJ;
+                    const double *A1 = A0 + nJ, *A2 = A1 + nJ, *A3 = A2 + nJ;
+                    int64_t fa[4];
+                    for (int u = 0; u < 4; ++u) fa[u] = rowpos(T, RJ[a0 + u]) * nT - cf.c0[T];
+                    for (; bt + 4 <= btile; bt += 4) {
+                        const double* B0 = Fj + (nJ + bt) * nJ;
+                        const double *B1 = B0 + nJ, *B2 = B1 + nJ, *B3 = B2 + nJ;
+                        double d[4][4] = {};
+                        for (int32_t k = 0; k < nJ; ++k) {
+                            const double x0 = A0[k], x1 = A1[k], x2 = A2[k], x3 = A3[k];
+                            const double y0 = B0[k], y1 = B1[k], y2 = B2[k], y3 = B3[k];
+                            d[0][0] += x0 * y0; d[0][1] += x0 * y1; d[0][2] += x0 * y2; d[0][3] += x0 * y3;
+                            d[1][0] += x1 * y0; d[1][1] += x1 * y1; d[1][2] += x1 * y2; d[1][3] += x1 * y3;
+                            d[2][0] += x2 * y0; d[2][1] += x2 * y1; d[2][2] += x2 * y2; d[2][3] += x2 * y3;
+                            d[3][0] += x3 * y0; d[3][1] += x3 * y1; d[3][2] += x3 * y2; d[3][3] += x3 * y3;
+                        }
+                        for (int u = 0; u < 4; ++u)
+                            for (int v = 0; v < 4; ++v) FT[fa[u] + RJ[bt + v]] -= d[u][v];
+                    }
+                }
+                for (int64_t a = a0; a < a1; ++a) dots(a, bt, std::min(a + 1, b1));
             }
             b0 = b1;
         }
@@ -809,14 +854,19 @@ slr_status host_c_factor(HostSetup& hs, int32_t leaf, int32_t task_rows) {
         // Lhat = L D^{-1}, D = diag(L_JJ), so C = Lhat D D^T Lhat^T (a block LDL^T form)
         const double* Pj = Fj + (int64_t)nJ * nJ;
         double* Mj = cf.panel.data() + cf.pan_off[J];
+        // eight panel rows per pass over each row of X (X is read once per eight rows
+        // instead of once per row); every M_J entry still sums k in ascending order
+        constexpr int64_t RB = 8;
 #pragma omp parallel for schedule(static) if (nJ >= 256 && nr >= 16)
-        for (int64_t pr = 0; pr < nr; ++pr) {
-            const double* Lp = Pj + pr * nJ;
-            double* Mp = Mj + pr * nJ;
+        for (int64_t pb = 0; pb < (nr + RB - 1) / RB; ++pb) {
+            const int64_t p0 = pb * RB, p1 = std::min(nr, p0 + RB);
             for (int32_t k = 0; k < nJ; ++k) {
-                const double a = Lp[k];
                 const double* Xk = X.data() + (size_t)k * nJ;
-                for (int32_t j = 0; j <= k; ++j) Mp[j] += a * Xk[j];
+                for (int64_t pr = p0; pr < p1; ++pr) {
+                    const double a = Pj[pr * nJ + k];
+                    double* Mp = Mj + pr * nJ;
+                    for (int32_t j = 0; j <= k; ++j) Mp[j] += a * Xk[j];
+                }
             }
         }
     };
