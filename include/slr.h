@@ -5,7 +5,9 @@
  * Method: R. Li, Y. Xi, Y. Saad, "Schur complement based domain
  * decomposition preconditioners with low-rank corrections", arXiv 1505.04340.
  *
- *   A x = b, A sparse symmetric positive definite (Section 1, Eq. 1.1).
+ *   A x = b, A sparse symmetric positive definite (Section 1, Eq. 1.1), or
+ *   symmetric indefinite with an SPD interface matrix C (an option; solved by
+ *   slr_gmres_solve).
  *   A vertex-based partition (Section 2.1) splits the unknowns into interiors
  *   u_1..u_p and interfaces y; in that order P A P^T = [[B, E], [E^T, C]]
  *   with B = diag(B_i) (Eqs. 2.2-2.3).  C = L L^T, H = L^{-1} E^T B^{-1} E L^{-T}
@@ -17,9 +19,11 @@
  *
  * Conventions used by every entry point:
  *  - "DD order" is the order of Eq. 2.2: interiors of part 0, ..., part p-1,
- *    then interfaces of part 0, ..., part p-1; inside each group nodes keep
- *    ascending original index.  A node is an interface node iff A couples it
- *    to a node of another part.
+ *    then interfaces of part 0, ..., part p-1, then the separator vertices
+ *    (part = -1, if any); inside each group nodes keep ascending original
+ *    index.  A node of a part is an interface node iff A couples it to a node
+ *    of another part (a coupling to a separator vertex keeps it interior);
+ *    separator vertices are always interface nodes.
  *  - Multi-column vectors are column-major with leading dimension ld >= rows;
  *    *_dev pointers are caller-owned device memory (e.g. torch tensors) on
  *    the device that was current at slr_setup, *_host pointers are host memory.
