@@ -1,13 +1,19 @@
 """Benchmark: SLR-preconditioned CG solves/s on one GB300 (and N replicas).
 
-Workload (default): 3-D 7-point Laplacian 64^3 (n = 262,144), Dirichlet, 4x4x4
-box partition (64 subdomains of 16^3), rank k = 32 from 5k Lanczos steps, one
-right-hand side b = A x*, x* uniform[-1,1) from a seed, PCG to 1e-8 relative
-residual.  A step is one full solve; the FP64 path is the headline (`value`),
-the mixed path (FP32 apply, FP64 outer loop) is reported beside it.
+Headline workload (``value``): the batching configuration, a 3-D 7-point
+anisotropic Laplacian on 96^3 (n = 884,736, coefficients (1, 1, 1e-2)), 6x6x6
+box partition (216 subdomains of 16^3), rank k = 64 from 5k Lanczos steps, a
+block of 32 right-hand sides b = A x* (x* columns uniform[-1,1) from seeds)
+solved together by PCG to 1e-8 relative residual per column, with the
+preconditioner applied in FP32 and the CG loop in FP64 (mixed).  A step is one
+block solve; ``value`` counts solved columns per second.  Beside it: the same
+workload in FP64, and as sub-objects the 3-D Laplacian 64^3 (k = 32, one
+right-hand side) and the 2-D FV diffusion 1024^2 (coefficients log-uniform in
+[1e-3, 1e3], k = 64), each in both precisions, plus the symmetric indefinite
+GMRES leg and the serving stream.
 
 Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle on a
-bounded sample of the same workload instead.
+bounded sample of the headline workload instead.
 """
 from __future__ import annotations
 
@@ -100,16 +106,28 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def band_source_sha():
-    """SHA-256 over the band kernel's sources (kernel template and both instantiation units)."""
+# the source files of each kernel whose ncu traffic a committed summary records
+KERNEL_SOURCES = {
+    "band": ("slr_band_kernel.cuh", "slr_band.cu", "slr_band_half.cu"),
+    "csolve": ("slr_kernels.cu",),
+    "lowrank": ("slr_kernels.cu",),
+}
+
+
+def source_sha(kernel):
+    """SHA-256 over a kernel's source files."""
     import hashlib
     hsh = hashlib.sha256()
-    for f in ("slr_band_kernel.cuh", "slr_band.cu", "slr_band_half.cu"):
+    for f in KERNEL_SOURCES[kernel]:
         hsh.update(open(os.path.join(ROOT, "paper_1505_04340_gb300", "csrc", f), "rb").read())
     return hsh.hexdigest()
 
 
-def captured_traffic(summary):
+def band_source_sha():
+    return source_sha("band")
+
+
+def captured_traffic(summary, kernel="band"):
     """DRAM bytes per launch from a committed ncu summary, or None when the
     kernel source changed since the capture (its SHA-256 is recorded there)."""
     try:
@@ -118,8 +136,7 @@ def captured_traffic(summary):
             if ":" in line and not line.startswith("#"):
                 k, v = line.split(":", 1)
                 kv[k.strip()] = v.split("#")[0].strip()
-        sha = band_source_sha()
-        return int(kv["traffic_bytes_per_launch"]) if kv.get("source_sha256") == sha else None
+        return int(kv["traffic_bytes_per_launch"]) if kv.get("source_sha256") == source_sha(kernel) else None
     except (OSError, KeyError, ValueError):
         return None
 
@@ -148,13 +165,22 @@ def aggregate(units, seconds, device=None):
     return float(u.item()) / float(t.item()), float(u.item()), float(t.item())
 
 
+# workloads: name -> (problem builder, right-hand sides per solve, PCG iteration cap,
+# iterations of a full FP64 solve as measured on the GPU (scales the oracle's sample))
+PROBLEMS = {
+    "2d32": ("config1", 1, 300, 9),
+    "3d64": ("config2", 1, 300, 22),
+    "2d1024fv": ("config3", 1, 3000, 901),
+    "3d96aniso": ("config4", 32, 300, 39),
+}
+HEADLINE = "3d96aniso"
+
+
 def build_problem(name):
     import slrgen
-    if name == "3d64":
-        return slrgen.config2(), "3d-laplace-64^3-p64-k32"
-    if name == "2d32":
-        return slrgen.config1(), "2d-laplace-32x32-p4-k8"
-    raise ValueError(name)
+    fn = PROBLEMS[name][0]
+    P = getattr(slrgen, fn)()
+    return P, P.name
 
 
 def cpu_threads():
@@ -164,48 +190,82 @@ def cpu_threads():
         return os.cpu_count()
 
 
-def oracle_sample(P, iters_full, sample_its=3):
-    """Time `sample_its` oracle PCG iterations (A product + SLR apply) on the full problem.
+def oracle_for_sample(P):
+    """The CPU oracle on P with a rank-k low-rank part of orthonormal columns.
 
-    The oracle's own Lanczos runs with k+1 steps here: the per-iteration cost of
-    the apply depends on k, not on how converged the Ritz pairs are.
-    """
-    import scipy.sparse as sp
+    The time of an apply does not depend on how good the pairs are, only on k,
+    so the oracle's Lanczos (minutes on the larger workloads) is replaced by an
+    orthonormalised seeded block; the apply then performs every product of
+    Eq. 4.1 / Eq. 4.7 at full size."""
+    import slrgen
     from oracle.slr_oracle import SLR as OracleSLR
+    ora = OracleSLR(P.rowptr, P.colind, P.val, P.part, P.nparts, 0)
+    s = ora.order.s
+    k = min(P.k, s)
+    X = np.stack([slrgen.uniform_pm1(900 + j, s) for j in range(k)], axis=1)
+    ora.U = np.linalg.qr(X)[0]
+    ora.lam = np.linspace(0.9, 0.5, k)
+    ora.k, ora.theta = k, 0.4
+    return ora
+
+
+def oracle_step(ora, b, cols):
+    """One bounded sample: `cols` PCG iterations' worth of work (an A product and an
+    SLR apply per column)."""
+    for j in range(cols):
+        r = b[:, j]
+        q = ora.App @ r
+        ora.apply(r - 1e-3 * q)
+
+
+def oracle_sample(P, name, sample_steps=2):
+    """CPU baseline: the oracle (as it stands) on the headline workload, bounded.
+
+    Returns the solves/s a full solve would reach at this per-iteration speed
+    (per column: iterations of a full FP64 GPU solve x one A product and one
+    apply), the seconds of the sample and of the oracle's setup."""
     t0 = time.perf_counter()
-    ora = OracleSLR(P.rowptr, P.colind, P.val, P.part, P.nparts, P.k, lanczos_steps=P.k + 1)
+    ora = oracle_for_sample(P)
     t_setup = time.perf_counter() - t0
-    b = ora.to_dd(P.b[:, 0])
-    r = b.copy()
-    p = ora.apply(r)
+    b = np.stack([ora.to_dd(P.b[:, j]) for j in range(1)], axis=1)
+    oracle_step(ora, b, 1)
     t0 = time.perf_counter()
-    for _ in range(sample_its):
-        q = ora.App @ p
-        r = r - 1e-3 * q
-        z = ora.apply(r)
-        p = z + 1e-3 * p
-    t_it = (time.perf_counter() - t0) / sample_its
-    return t_it, t_setup, t_it * iters_full
+    for _ in range(sample_steps):
+        oracle_step(ora, b, 1)
+    t_it = (time.perf_counter() - t0) / sample_steps
+    iters = PROBLEMS[name][3]
+    return 1.0 / (t_it * iters), t_it, t_setup
+
+
+def oracle_single_thread(name):
+    """The same sample in a child process whose BLAS and OpenMP pools have one thread."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-sample", name]
+    try:
+        r = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=900)
+        return json.loads(r.stdout.strip().splitlines()[-1])
+    except Exception as e:      # noqa: BLE001 - reported, not fatal
+        return {"error": str(e)[:200]}
+
+
+def run_cpu_sample(name):
+    P, _ = build_problem(name)
+    v, t_it, t_setup = oracle_sample(P, name)
+    print(json.dumps({"value": v, "t_iteration_s": t_it, "setup_s": t_setup}), flush=True)
 
 
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    P, wname = build_problem(args.problem)
-    # a full solve of this workload takes this many iterations with the same method
-    iters_full = int(args.ref_iters)
-    from oracle.slr_oracle import SLR as OracleSLR
-    ora = OracleSLR(P.rowptr, P.colind, P.val, P.part, P.nparts, P.k, lanczos_steps=P.k + 1)
-    b = ora.to_dd(P.b[:, 0])
+    name = args.problem or HEADLINE
+    P, wname = build_problem(name)
+    _, nrhs, _, iters_full = PROBLEMS[name]
+    ora = oracle_for_sample(P)
+    b = np.stack([ora.to_dd(P.b[:, 0])], axis=1)
 
     def step():
-        r = b.copy()
-        p = ora.apply(r)
-        for _ in range(args.ref_sample_its):
-            q = ora.App @ p
-            r = r - 1e-3 * q
-            p = ora.apply(r) + 1e-3 * p
+        oracle_step(ora, b, 1)
 
     for _ in range(args.warmup):
         step()
@@ -213,15 +273,14 @@ def run_reference(args):
     for _ in range(args.steps):
         step()
     dt = (time.perf_counter() - t0) / args.steps
-    per_it = dt / (args.ref_sample_its + 1)
-    value = 1.0 / (per_it * iters_full)
-    sample = (f"{args.ref_sample_its + 1} SLR applies + {args.ref_sample_its} A products per step on the full "
-              f"workload, scaled to a {iters_full}-iteration solve")
+    value = 1.0 / (dt * iters_full)            # solves (columns) per second
+    sample = (f"one PCG iteration's work per step (an A product and one SLR apply, rank {ora.k}) on one column "
+              f"of the full workload; solves/s = 1 / (that time x {iters_full} iterations of a full solve)")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": wname, "n": P.n, "nparts": P.nparts, "k": P.k, "precision": "fp64"},
+        "config": {"workload": wname, "n": P.n, "nparts": P.nparts, "k": P.k, "nrhs": nrhs, "precision": "fp64"},
         "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cpu_threads(), "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -234,17 +293,21 @@ def run_profile(args):
     import paper_1505_04340_gb300 as pkg
     from paper_1505_04340_gb300 import SLR
     pkg.load()
-    P, _ = build_problem(args.problem)
-    b = torch.tensor(P.b[:, 0], device="cuda")
+    name = args.problem or HEADLINE
+    P, _ = build_problem(name)
+    _, nrhs, maxit, _ = PROBLEMS[name]
+    maxit = args.maxit or maxit
+    b = torch.tensor(np.ascontiguousarray(P.b[:, :nrhs]), device="cuda")
+    b = b[:, 0] if nrhs == 1 else b
     h = SLR(P.rowptr, P.colind, P.val, P.part, P.nparts, k=P.k, lanczos_steps=P.lanczos_steps,
-            precision=args.precision, nrhs_max=1, flexible_cg=(args.precision == "mixed"),
+            precision=args.precision, nrhs_max=nrhs, flexible_cg=(args.precision == "mixed"),
             host_loop=args.host_loop, autotune=not args.no_autotune)   # the bench's kernel choices
     info = h.get_info()
-    f = torch.randn(info["n_interior"], dtype=torch.float64, device="cuda")
-    g = torch.randn(info["s"], dtype=torch.float64, device="cuda")
-    r = torch.randn(P.n, dtype=torch.float64, device="cuda")
-    step = {"pcg": lambda: h.pcg(b), "bsolve": lambda: h.bsolve(f), "csolve": lambda: h.csolve(g),
-            "apply": lambda: h.apply(r)}[args.profile_kernel]
+    f = torch.randn(info["n_interior"], nrhs, dtype=torch.float64, device="cuda")
+    g = torch.randn(info["s"], nrhs, dtype=torch.float64, device="cuda")
+    r = torch.randn(P.n, nrhs, dtype=torch.float64, device="cuda")
+    step = {"pcg": lambda: h.pcg(b, maxit=maxit, check=False), "bsolve": lambda: h.bsolve(f),
+            "csolve": lambda: h.csolve(g), "apply": lambda: h.apply(r)}[args.profile_kernel]
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -253,10 +316,10 @@ def run_profile(args):
         step()
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_pop()
-    x, its, rel, st = h.pcg(b)
+    x, its, rel, st = h.pcg(b, maxit=maxit, check=False)
     inf = h.get_info()
-    print(json.dumps({"profile": args.precision, "kernel": args.profile_kernel, "iterations": int(its[0]),
-                      "relres": float(rel[0]), "launches_total": pkg.slr.kernel_launches(),
+    print(json.dumps({"profile": args.precision, "kernel": args.profile_kernel, "iterations": int(its.max()),
+                      "relres": float(rel.max()), "launches_total": pkg.slr.kernel_launches(),
                       "band_split": inf["band_split"], "band_threads": inf["band_threads"],
                       "band_source_sha256": band_source_sha()}))
     h.close()
@@ -359,10 +422,184 @@ def pkg_launches():
     return pkg.slr.kernel_launches()
 
 
-def run_ours(args):
+# FP32 FMA peak of the CUDA cores: 152 SMs x 128 lanes x 2 flops x 2070 MHz (nominal)
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e-3
+# ncu summaries under profiles/ that record a kernel's DRAM traffic per launch, by
+# (kernel, workload, precision)
+TRAFFIC_SUMMARIES = {
+    ("band", "3d64", "fp64"): "k_band_solve2_fp64_3d64.txt",
+    ("band", "3d64", "mixed"): "k_band_solve2_fp32_3d64.txt",
+}
+
+
+def kernel_roofline(kind, info, prec, nrhs, us, hbm, hbm_src, name):
+    """Roofline of one kernel launch: algorithmic bytes and flops per launch (each
+    operand read once per use) against HBM and the ALU of its precision."""
+    wf = 8 if prec == "fp64" else 4
+    if kind == "band":        # one B-solve: forward and backward pass over the band factor
+        entries = info["band_entries"]
+        vec = 2 * info["n_interior"] * nrhs * wf
+        label = "k_band_solve2 (K1, one B-solve)"
+    else:                     # one C-solve: L^{-1} then L^{-T} (diagonal blocks, panels, top-zone inverse)
+        entries = info["c_diag_entries"] + info["c_panel_entries"] + info["c_top_entries"]
+        vec = 4 * info["s"] * nrhs * wf
+        label = "C solve (K3, forward + backward)"
+    nbytes = 2 * entries * wf + vec
+    flops = 2 * 2 * entries * nrhs
+    gbs = nbytes / us / 1e3
+    tfs = flops / us / 1e6
+    alu = FP64_PEAK_TFLOPS if prec == "fp64" else FP32_PEAK_TFLOPS
+    f_hbm, f_alu = gbs / hbm, tfs / alu
+    summary = TRAFFIC_SUMMARIES.get((kind, name, prec))
+    traffic = captured_traffic(summary, kind) if summary else None
+    common = {"kernel": label, "us": us, "algorithmic_bytes": nbytes, "flops": flops, "traffic": traffic,
+              "hbm_frac": f_hbm, "alu_frac": f_alu}
+    if f_alu > f_hbm:
+        return dict(bound="alu", achieved=tfs, peak=alu, unit="TFLOP/s", frac=f_alu,
+                    peak_source=("nominal FP64 (152 SMs x 2 FMA/clk x 2070 MHz); 1.20 measured" if prec == "fp64"
+                                 else "nominal FP32 CUDA cores (152 SMs x 128 FMA/clk x 2070 MHz)"), **common)
+    return dict(bound="hbm", achieved=gbs, peak=hbm, unit="GB/s", frac=f_hbm, peak_source=hbm_src, **common)
+
+
+def time_call(fn, stream, reps, warm=3):
+    """Average CUDA-event time (us) of `reps` calls of fn on stream."""
+    import torch
+    for _ in range(warm):
+        fn()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) * 1e3 / reps
+
+
+def measure(args, name, prec, steps, warmup, ctx, headline=False):
+    """Set up one workload in one precision, time `steps` solves, its apply and
+    its two dominant kernels; the headline also gets clocks and the end-to-end leg."""
     import torch
     import paper_1505_04340_gb300 as pkg
     from paper_1505_04340_gb300 import SLR
+    dev, stream, dist, rank, local = ctx["dev"], ctx["stream"], ctx["dist"], ctx["rank"], ctx["local"]
+    P, wname = build_problem(name)
+    _, nrhs, maxit, _ = PROBLEMS[name]
+    t0 = time.perf_counter()
+    h = SLR(P.rowptr, P.colind, P.val, P.part, P.nparts, k=P.k, lanczos_steps=P.lanczos_steps,
+            precision=prec, nrhs_max=nrhs, flexible_cg=(prec == "mixed"), autotune=not args.no_autotune)
+    setup_s = time.perf_counter() - t0
+    Bh = np.ascontiguousarray(P.b[:, :nrhs])
+    B = torch.tensor(Bh, device=dev)
+    B = B[:, 0] if nrhs == 1 else B
+    x, its, rel, st = h.pcg(B, maxit=maxit)
+    assert st == 0, f"{name} {prec} solve did not converge: {rel}"
+    for _ in range(warmup):
+        h.pcg(B, maxit=maxit)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    sampler = ClockSampler(local) if (rank == 0 and headline) else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    l0 = pkg.slr.kernel_launches()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    torch.cuda.synchronize()
+    ev[0].record(stream)
+    for i in range(steps):
+        x, its, rel, st = h.pcg(B, maxit=maxit)
+        ev[i + 1].record(stream)
+    torch.cuda.synchronize()
+    launches = pkg.slr.kernel_launches() - l0
+    per = [ev[i].elapsed_time(ev[i + 1]) for i in range(steps)]
+    total_ms = ev[0].elapsed_time(ev[-1])
+    clocks = sampler.stop() if sampler else None
+    job_rate, _, max_s = aggregate(steps * nrhs, total_ms / 1e3, device=dev)
+    X = x.cpu().numpy().reshape(P.n, -1)
+    A = sp.csr_matrix((P.val, P.colind, P.rowptr))
+    true_rel = float(np.max(np.linalg.norm(Bh - A @ X, axis=0) / np.linalg.norm(Bh, axis=0)))
+    xs = P.xstar[:, :nrhs]
+    x_err = float(np.max(np.linalg.norm(X - xs, axis=0) / np.linalg.norm(xs, axis=0)))
+    info = h.get_info()
+    its = np.atleast_1d(its)
+    # the apply and its kernels on an nrhs-column block (leading dimension = rows)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(7)
+    R = torch.randn(nrhs, P.n, dtype=torch.float64, device=dev, generator=gen)          # column-major n x nrhs
+    Z = torch.empty_like(R)
+    F = torch.randn(nrhs, info["n_interior"], dtype=torch.float64, device=dev, generator=gen)
+    T = torch.empty_like(F)
+    G = torch.randn(nrhs, info["s"], dtype=torch.float64, device=dev, generator=gen)
+    Y = torch.empty_like(G)
+    lib, hh, sp_ = h._lib, h._h, stream.cuda_stream
+    na = max(5, min(args.steps, 20))
+    apply_us = time_call(lambda: lib.slr_apply(hh, R.data_ptr(), Z.data_ptr(), nrhs, P.n, sp_), stream, na)
+    band_us = time_call(lambda: lib.slr_bsolve(hh, F.data_ptr(), T.data_ptr(), nrhs, info["n_interior"], sp_),
+                        stream, na)
+    c_us = time_call(lambda: lib.slr_csolve(hh, G.data_ptr(), Y.data_ptr(), nrhs, info["s"], sp_), stream, na)
+    lib.slr_apply(hh, R.data_ptr(), Z.data_ptr(), nrhs, P.n, sp_)
+    z = Z.cpu().numpy()
+    hbm, hbm_src = peaks()
+    roof = {"band": kernel_roofline("band", info, prec, nrhs, band_us, hbm, hbm_src, name),
+            "csolve": kernel_roofline("csolve", info, prec, nrhs, c_us, hbm, hbm_src, name)}
+    dominant = "band" if 2 * band_us >= c_us else "csolve"
+    out = dict(workload=wname, precision=prec, nrhs=nrhs, solves_per_s=job_rate, ms_per_step=max_s * 1e3 / steps,
+               p50_ms=float(np.percentile(per, 50)), p99_ms=float(np.percentile(per, 99)),
+               iterations=int(its.max()), iterations_min=int(its.min()), relres=float(np.max(rel)),
+               true_relres=true_rel, x_err_vs_xstar=x_err, setup_s=setup_s, launches=launches, clocks=clocks,
+               apply_us=apply_us, apply_gbs=info["bytes_per_apply"] * nrhs / apply_us / 1e3,
+               bytes_per_apply=info["bytes_per_apply"] * nrhs, band_us=band_us, c_us=c_us,
+               apply_share={"band (2 B-solves)": 2 * band_us / apply_us, "C solve": c_us / apply_us},
+               roofline=roof[dominant], rooflines=roof,
+               tuning={"band_split": info["band_split"], "band_slots": info["band_slots"],
+                       "band_threads": info["band_threads"], "c_persistent": info["c_persistent"],
+                       "tuned": info["tuned"], "tune_seconds": info["tune_seconds"]},
+               setup_phases_s=dict(zip(["analysis", "band_factor", "c_factor", "upload", "lanczos"],
+                                       [round(v, 4) for v in info["setup_seconds"]]),
+                                   lanczos_h_apply=round(info["lanczos_seconds"][0], 4),
+                                   lanczos_reorth=round(info["lanczos_seconds"][1], 4),
+                                   lanczos_eig=round(info["lanczos_seconds"][2], 4),
+                                   band_on_device=info["band_on_device"]),
+               device_bytes=info["device_bytes"], k=info["k"], lanczos_steps=info["lanczos_steps"])
+    out["_x"], out["_z"] = X, z
+    if headline:
+        # end to end through the public API with host buffers: pinned b -> device, block
+        # solve, x -> pinned host, every step inside the timed region
+        bh = torch.tensor(Bh).pin_memory()
+        xh = torch.empty(Bh.shape, dtype=torch.float64).pin_memory()
+        bd = torch.empty(Bh.shape, dtype=torch.float64, device=dev)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            bd.copy_(bh, non_blocking=True)
+            xd, _, _, _ = h.pcg(bd if nrhs > 1 else bd[:, 0], maxit=maxit)
+            xh.copy_(xd.reshape(Bh.shape), non_blocking=True)
+            torch.cuda.synchronize()
+        e2e_rate, _, _ = aggregate(steps * nrhs, time.perf_counter() - t0, device=dev)
+        out["e2e"] = {"value": e2e_rate, "unit": "solves/s", "h2d_bytes_per_step": int(Bh.nbytes),
+                      "d2h_bytes_per_step": int(Bh.nbytes)}
+    h.close()
+    return out
+
+
+def public(d):
+    return {k: v for k, v in d.items() if not k.startswith("_")}
+
+
+def pair(args, name, steps, warmup, ctx):
+    """Both precisions of one workload, the mixed one compared with the FP64 one."""
+    r64 = measure(args, name, "fp64", steps, warmup, ctx)
+    rm = measure(args, name, "mixed", steps, warmup, ctx)
+    rm["x_rel_diff_vs_fp64"] = float(np.max(np.linalg.norm(rm["_x"] - r64["_x"], axis=0) /
+                                            np.linalg.norm(r64["_x"], axis=0)))
+    rm["apply_rel_diff_vs_fp64"] = float(np.abs(rm["_z"] - r64["_z"]).max() / np.abs(r64["_z"]).max())
+    return {"fp64": public(r64), "mixed": public(rm), "mixed_over_fp64": rm["solves_per_s"] / r64["solves_per_s"]}
+
+
+def run_ours(args):
+    import torch
+    import paper_1505_04340_gb300 as pkg
 
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
@@ -371,191 +608,67 @@ def run_ours(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     pkg.load()
-    P, wname = build_problem(args.problem)
-    dev = "cuda"
-    b = torch.tensor(P.b[:, 0], device=dev)
-    stream = torch.cuda.current_stream()
-
-    def make(precision):
-        return SLR(P.rowptr, P.colind, P.val, P.part, P.nparts, k=P.k, lanczos_steps=P.lanczos_steps,
-                   precision=precision, nrhs_max=1, flexible_cg=(precision == "mixed"),
-                   autotune=not args.no_autotune)
-
-    results = {}
-    for prec in ("fp64", "mixed"):
-        t0 = time.perf_counter()
-        h = make(prec)
-        setup_s = time.perf_counter() - t0
-        x, its, rel, st = h.pcg(b)
-        assert st == 0, f"{prec} solve did not converge: {rel}"
-        for _ in range(args.warmup):
-            h.pcg(b)
-        torch.cuda.synchronize()
-        if dist:
-            dist.barrier()
-        sampler = ClockSampler(local) if (rank == 0 and prec == "fp64") else None
-        if sampler:
-            sampler.start()
-            time.sleep(0.3)
-        l0 = pkg.slr.kernel_launches()
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
-        torch.cuda.synchronize()
-        ev[0].record(stream)
-        its_all = []
-        for i in range(args.steps):
-            x, its, rel, st = h.pcg(b)
-            ev[i + 1].record(stream)
-            its_all.append(int(its[0]))
-        torch.cuda.synchronize()
-        launches = pkg.slr.kernel_launches() - l0
-        per = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
-        total_ms = ev[0].elapsed_time(ev[-1])
-        clocks = sampler.stop() if sampler else None
-        job_rate, _, max_s = aggregate(args.steps, total_ms / 1e3, device=dev)
-        total_ms = max_s * 1e3
-        A_err = None
-        if prec == "fp64":
-            import scipy.sparse as sp
-            A = sp.csr_matrix((P.val, P.colind, P.rowptr))
-            xn = x.cpu().numpy()
-            A_err = float(np.linalg.norm(P.b[:, 0] - A @ xn) / np.linalg.norm(P.b[:, 0]))
-            results["x64"] = xn
-        else:
-            results["x_mixed_err"] = float(np.linalg.norm(x.cpu().numpy() - results["x64"]) /
-                                           np.linalg.norm(results["x64"]))
-        # apply alone (apply GB/s) and the dominant kernel alone (K1 band solve)
-        info = h.get_info()
-        gen = torch.Generator(device=dev)
-        gen.manual_seed(7)
-        r = torch.randn(P.n, dtype=torch.float64, device=dev, generator=gen)
-        z1 = h.apply(r).cpu().numpy()
-        if prec == "fp64":
-            results["z64"] = z1
-        else:       # the FP32 apply against the FP64 apply on the same vector
-            results["apply_rel_diff"] = float(np.abs(z1 - results["z64"]).max() / np.abs(results["z64"]).max())
-        na = max(10, args.steps)
-        for _ in range(3):
-            h.apply(r)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        for _ in range(na):
-            h.apply(r)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        apply_us = e0.elapsed_time(e1) * 1e3 / na
-        f = torch.randn(info["n_interior"], dtype=torch.float64, device=dev)
-        out = torch.empty_like(f)
-        for _ in range(3):
-            h._lib.slr_bsolve(h._h, f.data_ptr(), out.data_ptr(), 1, info["n_interior"], stream.cuda_stream)
-        torch.cuda.synchronize()
-        e0.record(stream)
-        for _ in range(na):
-            h._lib.slr_bsolve(h._h, f.data_ptr(), out.data_ptr(), 1, info["n_interior"], stream.cuda_stream)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        band_us = e0.elapsed_time(e1) * 1e3 / na
-        wbytes = 8 if prec == "fp64" else 4
-        # one B-solve reads the forward blocks (O_J, D_J) and the backward blocks (O_J^T, D_J^T):
-        # band_entries = sum c_i W_i (W_i + 1) per pass
-        band_bytes = 2 * info["band_entries"] * wbytes + 2 * info["n_interior"] * wbytes
-        band_flops = 2 * 2 * info["band_entries"]
-        results[prec] = dict(
-            solves_per_s=job_rate, ms_per_step=total_ms / args.steps,
-            p50_ms=float(np.percentile(per, 50)), p99_ms=float(np.percentile(per, 99)), iters=its_all[-1],
-            setup_s=setup_s, launches=launches, clocks=clocks, relres=float(rel[0]), true_relres=A_err,
-            apply_us=apply_us, apply_gbs=info["bytes_per_apply"] / apply_us / 1e3,
-            bytes_per_apply=info["bytes_per_apply"], band_us=band_us, band_bytes=band_bytes,
-            tuning={"band_split": info["band_split"], "band_slots": info["band_slots"],
-                    "c_persistent": info["c_persistent"], "tuned": info["tuned"],
-                    "tune_seconds": info["tune_seconds"]},
-            band_flops=band_flops, device_bytes=info["device_bytes"], setup_parts=info["setup_seconds"],
-            lanczos_parts=info["lanczos_seconds"], band_on_device=info["band_on_device"])
-        # end to end through host buffers: pinned b -> device, solve, x -> pinned host
-        if prec == "fp64":
-            bh = torch.tensor(P.b[:, 0]).pin_memory()
-            xh = torch.empty(P.n, dtype=torch.float64).pin_memory()
-            bd = torch.empty(P.n, dtype=torch.float64, device=dev)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            for _ in range(args.steps):
-                bd.copy_(bh, non_blocking=True)
-                xd, _, _, _ = h.pcg(bd)
-                xh.copy_(xd, non_blocking=True)
-                torch.cuda.synchronize()
-            e2e_rate, _, _ = aggregate(args.steps, time.perf_counter() - t0, device=dev)
-            results["e2e"] = {"value": e2e_rate, "unit": "solves/s", "h2d_bytes_per_step": P.n * 8,
-                              "d2h_bytes_per_step": P.n * 8}
-        h.close()
-
-    indef_res = run_indefinite(args, dev) if (args.indefinite_k > 0 and ws == 1 and args.problem == "3d64") else None
+    ctx = dict(dev="cuda", stream=torch.cuda.current_stream(), dist=dist, rank=rank, local=local)
+    name = args.problem or HEADLINE
+    short = max(1, min(args.steps, 3))
+    # headline: the FP64 path first (its solution and apply are the mixed path's reference)
+    h64 = measure(args, name, "fp64", short if name == HEADLINE else args.steps, 1, ctx)
+    hm = measure(args, name, "mixed", args.steps, args.warmup, ctx, headline=True)
+    x_diff = float(np.max(np.linalg.norm(hm["_x"] - h64["_x"], axis=0) / np.linalg.norm(h64["_x"], axis=0)))
+    z_diff = float(np.abs(hm["_z"] - h64["_z"]).max() / np.abs(h64["_z"]).max())
+    others = {}
+    if not args.headline_only:
+        for other in ("3d64", "2d1024fv"):
+            if other != name:
+                others["config_" + other] = pair(args, other, args.steps if other == "3d64" else short,
+                                                  args.warmup if other == "3d64" else 1, ctx)
+    indef_res = run_indefinite(args, ctx["dev"]) if (args.indefinite_k > 0 and ws == 1 and not args.headline_only) \
+        else None
     serving_res = None
-    if args.serving_requests > 0:
-        serving_res = run_serving(args, dev)
+    if args.serving_requests > 0 and not args.headline_only:
+        serving_res = run_serving(args, ctx["dev"])
         for key in ("cold", "warm"):
             st = serving_res[key]
-            st["solves_per_s"], _, _ = aggregate(st["solves"], st["span_s"], device=dev)
+            st["solves_per_s"], _, _ = aggregate(st["solves"], st["span_s"], device=ctx["dev"])
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return
-    hbm, hbm_src = peaks()
-    r64 = results["fp64"]
-    # K1 FP64: compare its FMA rate with the FP64 peak and its bytes with HBM; report the binding one
-    ach_gbs = r64["band_bytes"] / r64["band_us"] / 1e3
-    ach_tf = r64["band_flops"] / r64["band_us"] / 1e6
-    frac_hbm, frac_alu = ach_gbs / hbm, ach_tf / FP64_PEAK_TFLOPS
-    traffic = captured_traffic("k_band_solve2_fp64_3d64.txt") if args.problem == "3d64" else None
-    if frac_alu >= frac_hbm:
-        roof = {"bound": "alu", "achieved": ach_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": frac_alu, "traffic": traffic, "kernel": "k_band_solve2<double> (K1, one B-solve)",
-                "peak_source": "nominal FP64 (152 SMs x 2 FMA/clk x 2070 MHz); 1.20 measured",
-                "hbm_frac": frac_hbm, "algorithmic_bytes": r64["band_bytes"]}
-    else:
-        roof = {"bound": "hbm", "achieved": ach_gbs, "peak": hbm, "unit": "GB/s", "frac": frac_hbm,
-                "traffic": traffic, "kernel": "k_band_solve2<double> (K1, one B-solve)", "peak_source": hbm_src}
-    rm = results["mixed"]
-    mixed_band_gbs = rm["band_bytes"] / rm["band_us"] / 1e3
-    its_full = r64["iters"]
     cpu = None
     if ws == 1 and not args.no_cpu_baseline:
-        t_it, t_setup, t_solve = oracle_sample(P, its_full)
-        cpu = {"value": 1.0 / t_solve, "unit": "solves/s", "cores": cpu_threads(), "kind": "oracle",
-               "sample": f"3 oracle PCG iterations (A product + SLR apply) on the full workload, "
-                         f"{t_it * 1e3:.0f} ms each, scaled to the {its_full}-iteration solve; "
-                         f"oracle setup {t_setup:.1f} s excluded as in the metric"}
+        P, _ = build_problem(name)
+        v, t_it, t_setup = oracle_sample(P, name)
+        single = oracle_single_thread(name)
+        cpu = {"value": v, "unit": "solves/s", "cores": cpu_threads(), "kind": "oracle",
+               "nproc": os.cpu_count(),
+               "sample": f"2 oracle PCG iterations' work (an A product and an SLR apply of rank {P.k}) on one "
+                         f"column of the full workload, {t_it * 1e3:.0f} ms each, scaled to the "
+                         f"{PROBLEMS[name][3]}-iteration FP64 solve; oracle setup {t_setup:.1f} s excluded as in "
+                         f"the metric; BLAS/OpenMP pools may use all cores (the oracle's banded and sparse "
+                         f"triangular solves run on one)",
+               "single_thread": single}
     line = {
-        "metric": METRIC, "value": r64["solves_per_s"], "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": r64["ms_per_step"], "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": wname, "n": P.n, "nparts": P.nparts, "k": P.k, "lanczos_steps": P.lanczos_steps,
-                   "tol": 1e-8, "precision": "fp64", "nrhs": 1,
-                   "l2": "working set larger than L2 (band factor %.0f MB > 129 MB)" % (r64["band_bytes"] / 2e6),
-                   "parallelism": f"replicas x{ws}", "tuning": r64["tuning"]},
-        "iterations": its_full, "p50_ms": r64["p50_ms"], "p99_ms": r64["p99_ms"],
-        "true_relres": r64["true_relres"], "setup_s": r64["setup_s"],
-        "setup_phases_s": dict(zip(["analysis", "band_factor", "c_factor", "upload", "lanczos"],
-                                   [round(x, 4) for x in r64["setup_parts"]]),
-                               lanczos_h_apply=round(r64["lanczos_parts"][0], 4),
-                               lanczos_reorth=round(r64["lanczos_parts"][1], 4),
-                               lanczos_eig=round(r64["lanczos_parts"][2], 4),
-                               band_on_device=r64["band_on_device"]),
-        "apply": {"us": r64["apply_us"], "gbs": r64["apply_gbs"], "bytes": r64["bytes_per_apply"]},
-        "mixed": {"value": rm["solves_per_s"], "ms_per_step": rm["ms_per_step"], "iterations": rm["iters"],
-                  "p50_ms": rm["p50_ms"], "p99_ms": rm["p99_ms"], "x_rel_diff_vs_fp64": results["x_mixed_err"],
-                  "apply_rel_diff_vs_fp64": results["apply_rel_diff"],
-                  "apply_us": rm["apply_us"], "apply_gbs": rm["apply_gbs"],
-                  "band_solve_us": rm["band_us"], "band_gbs": mixed_band_gbs,
-                  "band_frac_hbm": mixed_band_gbs / hbm,
-                  "band_traffic": (captured_traffic("k_band_solve2_fp32_3d64.txt") if args.problem == "3d64" else None),
-                  "dtype": "f32 apply / f64 outer",
-                  "tuning": rm["tuning"]},
-        "roofline": roof,
-        "band_solve_us": r64["band_us"],
+        "metric": METRIC, "value": hm["solves_per_s"], "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": hm["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 apply / f64 outer", "data": "synthetic",
+        "config": {"workload": hm["workload"], "n": build_problem(name)[0].n, "nrhs": hm["nrhs"], "k": hm["k"],
+                   "lanczos_steps": hm["lanczos_steps"], "tol": 1e-8, "precision": "mixed",
+                   "unit_note": "solves = right-hand-side columns solved to 1e-8",
+                   "l2": "working set larger than L2 (band factor alone %.0f MB > 129 MB)"
+                         % (2 * hm["rooflines"]["band"]["algorithmic_bytes"] / 4e6),
+                   "parallelism": f"replicas x{ws}", "tuning": hm["tuning"]},
+        "iterations": hm["iterations"], "p50_ms": hm["p50_ms"], "p99_ms": hm["p99_ms"],
+        "true_relres": hm["true_relres"], "setup_s": hm["setup_s"], "setup_phases_s": hm["setup_phases_s"],
+        "apply": {"us": hm["apply_us"], "gbs": hm["apply_gbs"], "bytes": hm["bytes_per_apply"],
+                  "share": hm["apply_share"], "band_solve_us": hm["band_us"], "c_solve_us": hm["c_us"]},
+        "x_rel_diff_vs_fp64": x_diff, "apply_rel_diff_vs_fp64": z_diff,
+        "fp64": public(h64), "mixed_over_fp64": hm["solves_per_s"] / h64["solves_per_s"],
+        "roofline": hm["roofline"], "rooflines": hm["rooflines"],
         "cpu_baseline": cpu,
-        "e2e": results["e2e"],
-        "gpu_launches": r64["launches"],
-        "clocks": r64["clocks"],
+        "e2e": hm["e2e"],
+        "gpu_launches": hm["launches"],
+        "clocks": hm["clocks"],
+        **others,
         "serving": serving_res,
         "indefinite": indef_res,
     }
@@ -570,14 +683,15 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--problem", default="3d64")
+    ap.add_argument("--problem", default=None, choices=list(PROBLEMS),
+                    help="the workload (default: the 3-D 96^3 block of 32 right-hand sides)")
+    ap.add_argument("--headline-only", action="store_true", help="skip the other workloads and legs")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--ref-iters", type=int, default=22,
-                    help="iterations of a full solve of the workload (measured by the GPU arm)")
-    ap.add_argument("--ref-sample-its", type=int, default=2)
+    ap.add_argument("--cpu-sample", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--profile", action="store_true", help="solves inside an NVTX range only (for ncu)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--profile-kernel", default="pcg", choices=["pcg", "bsolve", "csolve", "apply"])
+    ap.add_argument("--maxit", type=int, default=0, help="PCG iteration cap of --profile (0: the workload's)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the built-in launch choices")
     ap.add_argument("--serving-requests", type=int, default=256, help="config-5 request stream length (0: skip)")
     # the 256-request stream carries 4.4 right-hand sides per request on average; 12 requests/s
@@ -590,7 +704,9 @@ def main():
     ap.add_argument("--host-loop", action="store_true",
                     help="drive CG from the host (profilers do not see kernels inside conditional graph nodes)")
     args = ap.parse_args()
-    if args.profile:
+    if args.cpu_sample:
+        run_cpu_sample(args.cpu_sample)
+    elif args.profile:
         run_profile(args)
     elif args.impl == "reference":
         run_reference(args)

@@ -59,6 +59,7 @@ typedef enum {
 
 enum { SLR_THETA_LAMBDA_K1 = 0, SLR_THETA_ZERO = 1 };   /* Eq. 4.11 / Eq. 4.10      */
 enum { SLR_PREC_FP64 = 0, SLR_PREC_MIXED = 1 };         /* apply in FP64 / in FP32  */
+enum { SLR_U_FP32 = 0, SLR_U_TF32 = 1, SLR_U_BF16 = 2 }; /* low-rank products (u_dtype) */
 
 typedef struct {
     int32_t k;              /* rank of the correction (Section 4); clamped to s           */
@@ -75,48 +76,60 @@ typedef struct {
                                order, u_i = (x_i >> 11) 2^-53, x_i output i of the stream */
     int32_t c_leaf;         /* nested-dissection leaf size for C's ordering; 0 => 64     */
     int32_t verbose;        /* 1: setup prints timings to stderr                          */
-    int32_t reserved[16];   /* reserved[0]: CTAs per subdomain in the band solve (1, 2, 4;
-                               0 = automatic).  reserved[1]: 1 = drive the CG loop from
-                               the host (one synchronisation per iteration) instead of
-                               one CUDA graph per solve.  reserved[2]: shared-memory
-                               buffers the band solve streams its factor through (2..8;
-                               0 = automatic).  reserved[3]: 1 = solve with C's factor
-                               in one cooperative launch per direction (grid barriers
-                               between level steps) instead of one launch per step.
-                               reserved[4]: 1 = autotune: setup times the band solve
-                               for each split (1, 2, 4 CTAs), CTA size (512 or 256
-                               threads) and buffer count (2, 3, 4) that fit, and both
-                               C-solve paths, on this operator, and
-                               keeps the fastest; the choice is cached per device,
-                               precision and problem shape for the process's life.
-                               reserved[5]: a target condition number K >= 2 for S S~^{-1}
-                               (0 = off): the rank becomes the number of Ritz values
-                               above 1 - 1/K, at most k (Section 4, Eq. condk:
-                               lambda_{k+1} <= 1 - 1/K keeps the condition number of
-                               S S~^{-1} below K).  slr_get_info reports the rank used.
-                               reserved[6]: threads per band-solve CTA, 512 (one CTA per
-                               SM) or 256 (two per SM, for more CTAs than SMs); 0 =
-                               automatic.  reserved[7]: 1 = solve every level of C's
-                               factor level by level; 0 (default) = the top levels, as
-                               many as fit a fill and setup budget, are solved with an
-                               explicit inverse of their block of the factor (one step
-                               per direction instead of one per level).
-                               reserved[8]: where the B_i are factored (Section 5.2):
-                               0 (default) = on the device when every plane is at most
-                               256 rows wide, else on the host; 1 = on the host.
-                               reserved[9]: 1 = A is symmetric indefinite with an SPD
-                               interface matrix C (Section 1; the shifted problems of
-                               Section 6): each B_i is factored as L S L^T with S the
-                               pivot signs (no pivoting; a zero pivot returns
-                               SLR_ERR_BREAKDOWN), H may have eigenvalues >= 1, and the
-                               accelerator is slr_gmres_solve.  0 = SPD.
-                               reserved[10]: the order in which the band solve's
-                               subdomain clusters are launched (it sets which
-                               subdomains share SMs; every order gives the same
-                               result, bit for bit): 1 = subdomain order, 2 = most
-                               work first, 3 = most and least work alternating;
-                               0 (default) = automatic (3).
-                               reserved[11..15] must be 0.                             */
+
+    /* ---- method options */
+    int32_t target_kappa;   /* a target condition number K >= 2 for S S~^{-1} (0 = off): the
+                               rank becomes the number of Ritz values above 1 - 1/K, at most
+                               k (Section 4, Eq. condk: lambda_{k+1} <= 1 - 1/K keeps the
+                               condition number of S S~^{-1} below K); slr_get_info reports
+                               the rank used                                             */
+    int32_t indefinite;     /* 1: A is symmetric indefinite with an SPD interface matrix C
+                               (Section 1; the shifted problems of Section 6): each B_i is
+                               factored as L S L^T with S the pivot signs (no pivoting; a
+                               zero pivot returns SLR_ERR_BREAKDOWN), H may have eigenvalues
+                               >= 1, and the accelerator is slr_gmres_solve.  0 = SPD     */
+    int32_t u_dtype;        /* arithmetic of the low-rank products U_k^T W and U_k (d o V)
+                               (Eq. 4.7) on right-hand-side blocks of the mixed path:
+                               SLR_U_FP32 (default; FP32 CUDA cores), SLR_U_TF32 or
+                               SLR_U_BF16 (tensor cores: U and W rounded to TF32 / BF16,
+                               products accumulated in FP32; used for blocks of 8 or more
+                               right-hand sides, narrower blocks take the FP32 kernel).
+                               Must be SLR_U_FP32 with SLR_PREC_FP64                       */
+
+    /* ---- execution choices: each gives the same preconditioner up to rounding; the
+       band_* fields, c_persistent, host_loop and autotune give bitwise the same result */
+    int32_t band_split;     /* CTAs (a thread-block cluster) per subdomain in the band solve:
+                               1, 2 or 4; 0 = automatic                                  */
+    int32_t band_slots;     /* shared-memory buffers the band solve streams its factor
+                               through: 2..8; 0 = automatic                              */
+    int32_t band_threads;   /* threads per band-solve CTA: 512 (one CTA per SM) or 256 (two
+                               per SM, for more CTAs than SMs); 0 = automatic            */
+    int32_t band_order;     /* the order in which the band solve's subdomain clusters are
+                               launched (it sets which subdomains share SMs): 1 = subdomain
+                               order, 2 = most work first, 3 = most and least work
+                               alternating; 0 = automatic (3)                            */
+    int32_t band_factor_host; /* where the B_i are factored (Section 5.2): 0 = on the device
+                               when every plane is at most 256 rows wide, else on the host;
+                               1 = on the host                                           */
+    int32_t c_persistent;   /* 1: solve with C's factor in one cooperative launch per
+                               direction (grid barriers between level steps) instead of one
+                               launch per step                                           */
+    int32_t c_levels_only;  /* 1: solve every level of C's factor level by level; 0 = the top
+                               levels, as many as fit a fill and setup budget, are solved
+                               with an explicit inverse of their block of the factor (one
+                               step per direction instead of one per level)              */
+    int32_t host_loop;      /* 1: drive the CG loop from the host (one synchronisation per
+                               iteration) instead of one CUDA graph per solve            */
+    int32_t autotune;       /* 1: setup times the band solve for each split (1, 2, 4 CTAs),
+                               CTA size (512 or 256 threads) and buffer count (2, 3, 4) that
+                               fit, and both C-solve paths, on this operator, and keeps the
+                               fastest; the choice is cached per device, precision and
+                               problem shape for the process's life                      */
+    int32_t spin_limit;     /* polls of a bounded device wait between steps of the
+                               cooperative C solve (c_persistent) before it gives up and
+                               reports SLR_ERR_TIMEOUT; 0 = the default (2^22 polls, about a
+                               quarter second)                                           */
+    int32_t reserved[8];    /* must be 0                                                  */
 } slr_opts;
 
 typedef struct {
@@ -135,13 +148,13 @@ typedef struct {
     int32_t band_split;          /* CTAs per subdomain in the band solve                    */
     int32_t band_slots;          /* band-solve stream buffers (0: the default)              */
     int32_t c_persistent;        /* 1: C solves in one cooperative launch per direction     */
-    int32_t tuned;               /* 1: the three above were chosen by timing (reserved[4]) */
+    int32_t tuned;               /* 1: the three above were chosen by timing (autotune)    */
     double tune_seconds;         /* time the tuning took (0 when taken from the cache)      */
     int32_t band_threads;        /* threads per band-solve CTA (256: two subdomains per SM) */
     int32_t c_top_levels;        /* levels of C's factor solved with the explicit inverse   */
     int32_t c_top_positions;     /* interface positions in those levels                     */
     int64_t c_top_entries;       /* stored entries of that inverse (each layout)            */
-    int32_t band_on_device;      /* 1: the B_i were factored on the device (reserved[8])    */
+    int32_t band_on_device;      /* 1: the B_i were factored on the device               */
     double lanczos_seconds[3];   /* setup Lanczos (Section 5.1) split: H applies with the alpha
                                     dot, full reorthogonalisation with the beta norm, the
                                     tridiagonal eigensolve on the host and U_k = V Y_k      */
@@ -186,7 +199,7 @@ slr_status slr_pcg_solve(slr_handle h, const double* b_dev, double* x_dev, int32
                          double* relres_out);
 
 /* Solve A x = b with SLR-preconditioned GMRES(restart) (Section 6: GMRES(40) for
- * the symmetric indefinite problems, slr_opts.reserved[9] = 1; it works for SPD A
+ * the symmetric indefinite problems, slr_opts.indefinite = 1; it works for SPD A
  * too).  Flexible right preconditioning: z_j = M^{-1} v_j are kept and
  * x = x_0 + Z_j y, so an FP32 apply (varying by rounding) does not spoil the
  * minimal-residual property.  Arnoldi orthogonalises by two classical
@@ -262,24 +275,45 @@ slr_status slr_dd_order(int32_t n, const int32_t* rowptr, const int32_t* colind,
                         const int32_t* part, int32_t* perm_out, int32_t* int_off, int32_t* ifc_off,
                         int32_t* s_out);
 
-/* z = M^{-1} r exactly as slr_apply, for callers that cannot call cudaMalloc
- * while they run: code inside a stream capture in cudaStreamCaptureModeGlobal
- * (where allocation calls are errors), or a process whose device memory is
- * handed to an allocator it does not control.  It allocates nothing: its
- * per-call scratch (band-solve intermediates, interface vectors, panel
- * products, reduction partials) is carved from one file-scope __device__ array
- * of 32 MiB that every GPU loading this library holds until exit, instead of
- * the handle's workspaces.  The paper has no counterpart; this is a deployment
- * variant of the apply of Eq. 4.1.
+/* z = M^{-1} r exactly as slr_apply, for callers that cannot let device memory
+ * be allocated while they run: a process whose device memory is handed to an
+ * allocator it does not control (a fixed arena set up at start-up), or a server
+ * that must not grow its device footprint while it answers requests.  It
+ * allocates nothing: its per-call scratch (band-solve intermediates, interface
+ * vectors, panel products, reduction partials) is carved from one file-scope
+ * __device__ array of 32 MiB that every GPU loading this library holds until
+ * exit, instead of the handle's workspaces.  The paper has no counterpart; this
+ * is a deployment variant of the apply of Eq. 4.1.
  * Same arguments, layout and ownership as slr_apply.  Errors: INVALID_ARG as
  * slr_apply; UNSUPPORTED (nothing launched) when the scratch for this handle
- * and nrhs exceeds 32 MiB.  The first call on a device looks up the array's
- * device address (cudaGetSymbolAddress); make that first call before any
- * stream capture.  Every call shares the one array and no part of it needs to
- * start at zero (each call writes what it reads); calls that overlap on the
- * GPU, from any thread, stream or handle, race on it. */
+ * and nrhs exceeds 32 MiB.  slr_setup looks up the array's device address
+ * (cudaGetSymbolAddress, with the handle's device current) and keeps it in the
+ * handle, so this call looks nothing up; a cudaDeviceReset ends the handle and
+ * the address with it.  Every call shares the one array and no part of it needs
+ * to start at zero (each call writes what it reads, and clears its arrival
+ * counters); calls that overlap on the GPU, from any thread, stream or handle,
+ * race on it. */
 slr_status slr_apply_noalloc(slr_handle h, const double* r_dev, double* z_dev, int32_t nrhs, int32_t ld,
                              void* stream);
+
+/* The device status word of the handle's operator after the calls enqueued on
+ * stream so far: SLR_OK, or SLR_ERR_TIMEOUT when a bounded device wait expired
+ * (a band-solve copy that did not land within its bound, or a grid-barrier wait
+ * of the cooperative C solve beyond opts.spin_limit polls); the outputs of the
+ * call that saw it are then invalid.  Every call that runs the operator
+ * (slr_apply, slr_apply_noalloc, slr_bsolve, slr_csolve, slr_stilde_solve,
+ * slr_pcg_solve, slr_gmres_solve) clears the word on its stream before its
+ * kernels; slr_pcg_solve, slr_gmres_solve, slr_setup and slr_add_vectors read
+ * it themselves and return SLR_ERR_TIMEOUT.  Synchronises stream.  Bookkeeping
+ * of the device kernels' bounded waits; the paper has no counterpart. */
+slr_status slr_device_status(slr_handle h, void* stream);
+
+/* Fault injection for tests of the error paths (the paper has no counterpart):
+ * the nth device allocation this library makes from now on, counting every
+ * handle in the process, fails as if the device were out of memory (the call
+ * making it returns SLR_ERR_OOM and releases what it holds); nth <= 0 turns
+ * the injection off.  One failure per call of this function. */
+void slr_inject_alloc_failure(int64_t nth);
 
 /* Number of CUDA kernels this library has launched in this process so far
  * (all handles, all devices).  Lets a caller count the launches of a region. */

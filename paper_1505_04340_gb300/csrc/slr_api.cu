@@ -62,10 +62,17 @@ struct DeviceGuard {
     }
 };
 
+// slr_inject_alloc_failure: allocations left until the injected failure (0: off)
+std::atomic<int64_t> g_fail_alloc{0};
+
 template <typename T>
 slr_status dalloc(slr_handle h, T** p, size_t count) {
     *p = nullptr;
     if (count == 0) return SLR_OK;
+    if (g_fail_alloc.load(std::memory_order_relaxed) > 0 && g_fail_alloc.fetch_sub(1) == 1) {
+        set_error("cudaMalloc of " + std::to_string(count * sizeof(T)) + " bytes failed: injected failure");
+        return SLR_ERR_OOM;
+    }
     cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -125,9 +132,9 @@ slr_status upload(slr_handle h, TD** p, const std::vector<TS>& v) {
 }
 
 // The band blocks on the device, in the order their clusters are launched
-// (opts.reserved[10]; every order gives the same result, bit for bit).
+// (opts.band_order; every order gives the same result, bit for bit).
 slr_status upload_band(slr_handle h, BandBlock** p) {
-    return upload(h, p, band_run_order(h->hs.band, h->opts.reserved[10] ? h->opts.reserved[10] : kBandOrderAuto));
+    return upload(h, p, band_run_order(h->hs.band, h->opts.band_order ? h->opts.band_order : kBandOrderAuto));
 }
 
 template <typename T>
@@ -137,7 +144,7 @@ slr_status upload_operator(slr_handle h, DevOperator<T>& op, bool with_band) {
     CS(upload_band(h, &op.band));
     if (with_band) CS(upload(h, &op.bfac, hs.bfac));
     op.band_G = hs.band_G;
-    op.band_nbuf = h->opts.reserved[2];
+    op.band_nbuf = h->opts.band_slots;
     op.band_nt = hs.band_nt;
     CS(dalloc(h, &op.err, 1));
     CK(cudaMemsetAsync(op.err, 0, sizeof(int32_t), h->stream));
@@ -209,7 +216,8 @@ slr_status upload_operator(slr_handle h, DevOperator<T>& op, bool with_band) {
     }
     CS(dalloc(h, &d.bar, 1));
     d.err = op.err;
-    d.per_level = h->opts.reserved[3] != 1;   // per-level launches unless the persistent solve is asked for
+    if (h->opts.spin_limit > 0) d.grid_spin = h->opts.spin_limit;
+    d.per_level = h->opts.c_persistent != 1;   // per-level launches unless the persistent solve is asked for
     {
         int dev = 0, nsm = 0;
         if (cudaGetDevice(&dev) == cudaSuccess &&
@@ -367,6 +375,29 @@ double read_scalar(const double* dev, cudaStream_t st, slr_status* err) {
     return v;
 }
 
+// The operator's device status word: cleared on the call's stream before its
+// kernels, read (synchronising) after them.
+int32_t* status_word(slr_handle h) { return h->opts.precision == SLR_PREC_FP64 ? h->op64.err : h->op32.err; }
+
+slr_status clear_status(slr_handle h, cudaStream_t st) {
+    CK(cudaMemsetAsync(h->op64.err, 0, sizeof(int32_t), st));
+    if (h->op32.err && h->op32.err != h->op64.err) CK(cudaMemsetAsync(h->op32.err, 0, sizeof(int32_t), st));
+    return SLR_OK;
+}
+
+slr_status read_status(slr_handle h, const int32_t* word, cudaStream_t st) {
+    int32_t e = 0;
+    CK(cudaMemcpyAsync(&e, word, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (e) {
+        set_error(e == 2 ? "a bounded grid-barrier wait expired in the C solve"
+                         : "a bounded device wait expired in the band solve");
+        return SLR_ERR_TIMEOUT;
+    }
+    (void)h;
+    return SLR_OK;
+}
+
 // Section 5.1: m steps of Lanczos with full reorthogonalisation on H, Ritz pairs,
 // U_k = V Y_k, theta.  Start vector v_1 = L^{-1} C z / ||.||, z from SplitMix64.
 slr_status run_lanczos(slr_handle h, cudaStream_t st) {
@@ -427,14 +458,15 @@ slr_status run_lanczos(slr_handle h, cudaStream_t st) {
         if (beta[j] <= 1e-12 * amax) { m_eff = j + 1; break; }
         CK(launch_axpby(s, 1.0 / beta[j], w, 0.0, V + (int64_t)(j + 1) * s, st));
     }
+    CS(read_status(h, op.err, st));                // the H applies ran without an expired wait
     const double te0 = now_s();
     std::vector<double> lam(m_eff), Y((size_t)m_eff * m_eff);
     host_tridiag_eig(m_eff, alpha.data(), beta.data(), lam.data(), Y.data());
     k = std::min(k, m_eff);
-    if (h->opts.reserved[5] >= 2) {
+    if (h->opts.target_kappa >= 2) {
         // rank rule of Section 4 (Eq. condk): the condition number of S S~^{-1} stays
         // below K when lambda_{k+1} <= 1 - 1/K; keep the Ritz values above 1 - 1/K
-        const double thr = 1.0 - 1.0 / (double)h->opts.reserved[5];
+        const double thr = 1.0 - 1.0 / (double)h->opts.target_kappa;
         int32_t cnt = 0;
         while (cnt < m_eff && lam[cnt] > thr) ++cnt;   // descending
         k = std::min(k, cnt);
@@ -541,6 +573,7 @@ slr_status run_lanczos_deflated(slr_handle h, int32_t k_add, int32_t steps, cuda
         if (beta[j] <= 1e-12 * amax) { m_eff = j + 1; break; }
         CK(launch_axpby(s, 1.0 / beta[j], w, 0.0, V + (int64_t)(j + 1) * s, st));
     }
+    CS(read_status(h, op.err, st));
     std::vector<double> lam2(m_eff), Y((size_t)m_eff * m_eff);
     host_tridiag_eig(m_eff, alpha.data(), beta.data(), lam2.data(), Y.data());
     const int32_t ja = std::min(k_add, m_eff), kn = k + ja;
@@ -821,7 +854,7 @@ slr_status setup_impl(slr_handle h, int32_t n, const int32_t* rowptr, const int3
                       int32_t nparts, const int32_t* part, cudaStream_t st) {
     HostSetup& hs = h->hs;
     const bool vb = h->opts.verbose != 0;
-    hs.indefinite = h->opts.reserved[9] == 1;
+    hs.indefinite = h->opts.indefinite == 1;
     double t0 = now_s();
     CS(host_validate_csr(n, rowptr, colind, val, nparts, part));
     CS(host_dd_order(n, rowptr, colind, nparts, part, hs));
@@ -853,7 +886,7 @@ slr_status setup_impl(slr_handle h, int32_t n, const int32_t* rowptr, const int3
             set_error("a B_i has plane width " + std::to_string(wmx) + " beyond the band kernel's limit (1024)");
             return SLR_ERR_UNSUPPORTED;
         }
-        const int32_t req = h->opts.reserved[0];        // opts.band_split, 0 = automatic
+        const int32_t req = h->opts.band_split;        // 0 = automatic
         if (req == 1 || req == 2 || req == 4) {
             if (band_split_ok(wmx, req)) G = req;
         } else if (G == 1 && 2 * nparts <= nsm && wmx >= 64) {
@@ -864,21 +897,22 @@ slr_status setup_impl(slr_handle h, int32_t n, const int32_t* rowptr, const int3
         }
         // Section 5.2: factor the B_i on the device when every plane fits its kernel (at
         // most 256 rows), else on the host
-        dev_band = have_dev && h->opts.reserved[8] == 0 && wmx > 0 && wmx <= 256;
+        dev_band = have_dev && h->opts.band_factor_host == 0 && wmx > 0 && wmx <= 256;
         if (dev_band) host_band_layout(hs, G);
         else CS(host_band_factor(hs, G));
         // more CTAs than SMs would run in two waves: 256-thread CTAs put two subdomains on an SM
-        hs.band_nt = h->opts.reserved[6] ? h->opts.reserved[6] : (nparts * G > nsm ? 256 : 512);
+        hs.band_nt = h->opts.band_threads ? h->opts.band_threads : (nparts * G > nsm ? 256 : 512);
     }
     double t2 = now_s();
     CS(host_c_factor(hs, h->opts.c_leaf > 0 ? h->opts.c_leaf : 64, 32));
-    host_c_top(hs.cf, h->opts.reserved[7] == 1 ? hs.cf.nlev : host_c_top_choose(hs.cf));
+    host_c_top(hs.cf, h->opts.c_levels_only == 1 ? hs.cf.nlev : host_c_top_choose(hs.cf));
     double t3 = now_s();
     if (vb)
         fprintf(stderr, "[slr] n=%d nI=%d s=%d p=%d wmax=%d band=%zu cvals=%zu sn=%d lev=%d | analysis %.3fs B %.3fs C %.3fs\n",
                 hs.n, hs.nI, hs.s, hs.p, hs.wmax, hs.bfac.size(), hs.cf.panel.size() + hs.cf.dinv.size(), hs.cf.ns,
                 hs.cf.nlev, t1 - t0, t2 - t1, t3 - t2);
     CK(cudaGetDevice(&h->device));
+    CS(noalloc_lookup(h));
     CS(upload(h, &h->perm, hs.perm));
     CS(upload(h, &h->a_rp, hs.a_rp));
     CS(upload(h, &h->a_ci, hs.a_ci));
@@ -918,7 +952,7 @@ slr_status setup_impl(slr_handle h, int32_t n, const int32_t* rowptr, const int3
         // the FP64 band factor served the FP64 Lanczos only
         dfree(h, h->op64.bfac, (size_t)hs.bfac_len);
     }
-    if (h->opts.reserved[4] == 1) {
+    if (h->opts.autotune == 1) {
         if (h->opts.precision == SLR_PREC_FP64) CS(autotune<double>(h, h->op64, st));
         else CS(autotune<float>(h, h->op32, st));
     }
@@ -1210,19 +1244,20 @@ slr_status slr_setup(int32_t n, const int32_t* rowptr, const int32_t* colind, co
     slr_handle h = new (std::nothrow) slr_handle_s();
     if (!h) { set_error("host allocation failed"); return SLR_ERR_OOM; }
     if (opts) h->opts = *opts; else slr_default_opts(&h->opts);
-    if (h->opts.k < 0 || h->opts.lanczos_steps < 0 || h->opts.nrhs_max < 0 || h->opts.nrhs_max > 64 ||
-        (h->opts.precision != SLR_PREC_FP64 && h->opts.precision != SLR_PREC_MIXED) ||
-        (h->opts.theta_mode != SLR_THETA_LAMBDA_K1 && h->opts.theta_mode != SLR_THETA_ZERO) ||
-        (h->opts.reserved[0] != 0 && h->opts.reserved[0] != 1 && h->opts.reserved[0] != 2 &&
-         h->opts.reserved[0] != 4) ||
-        h->opts.reserved[1] < 0 || h->opts.reserved[1] > 1 ||
-        h->opts.reserved[2] < 0 || h->opts.reserved[2] == 1 || h->opts.reserved[2] > 8 ||
-        h->opts.reserved[3] < 0 || h->opts.reserved[3] > 1 || h->opts.reserved[4] < 0 || h->opts.reserved[4] > 1 ||
-        h->opts.reserved[5] < 0 || h->opts.reserved[5] == 1 ||
-        (h->opts.reserved[6] != 0 && h->opts.reserved[6] != 256 && h->opts.reserved[6] != 512) ||
-        h->opts.reserved[7] < 0 || h->opts.reserved[7] > 1 || h->opts.reserved[8] < 0 || h->opts.reserved[8] > 1 ||
-        h->opts.reserved[9] < 0 || h->opts.reserved[9] > 1 || h->opts.reserved[10] < 0 || h->opts.reserved[10] > 3 ||
-        std::any_of(h->opts.reserved + 11, h->opts.reserved + 16, [](int32_t v) { return v != 0; })) {
+    const slr_opts& o = h->opts;
+    if (o.k < 0 || o.lanczos_steps < 0 || o.nrhs_max < 0 || o.nrhs_max > 64 ||
+        (o.precision != SLR_PREC_FP64 && o.precision != SLR_PREC_MIXED) ||
+        (o.theta_mode != SLR_THETA_LAMBDA_K1 && o.theta_mode != SLR_THETA_ZERO) ||
+        (o.band_split != 0 && o.band_split != 1 && o.band_split != 2 && o.band_split != 4) ||
+        o.host_loop < 0 || o.host_loop > 1 || o.band_slots < 0 || o.band_slots == 1 || o.band_slots > 8 ||
+        o.c_persistent < 0 || o.c_persistent > 1 || o.autotune < 0 || o.autotune > 1 ||
+        o.target_kappa < 0 || o.target_kappa == 1 ||
+        (o.band_threads != 0 && o.band_threads != 256 && o.band_threads != 512) ||
+        o.c_levels_only < 0 || o.c_levels_only > 1 || o.band_factor_host < 0 || o.band_factor_host > 1 ||
+        o.indefinite < 0 || o.indefinite > 1 || o.band_order < 0 || o.band_order > 3 ||
+        o.u_dtype < SLR_U_FP32 || o.u_dtype > SLR_U_BF16 ||
+        (o.u_dtype != SLR_U_FP32 && o.precision != SLR_PREC_MIXED) || o.spin_limit < 0 ||
+        std::any_of(o.reserved, o.reserved + 8, [](int32_t v) { return v != 0; })) {
         set_error("invalid options");
         delete h;
         return SLR_ERR_INVALID_ARG;
@@ -1251,6 +1286,7 @@ slr_status slr_apply(slr_handle h, const double* r, double* z, int32_t nrhs, int
         return SLR_ERR_INVALID_ARG;
     }
     DeviceGuard g(h->device);
+    CS(clear_status(h, (cudaStream_t)stream));
     return apply_any(h, r, ld, z, ld, nrhs, (cudaStream_t)stream);
 }
 
@@ -1263,6 +1299,7 @@ slr_status slr_bsolve(slr_handle h, const double* f, double* t, int32_t nrhs, in
     }
     DeviceGuard g(h->device);
     cudaStream_t st = (cudaStream_t)stream;
+    CS(clear_status(h, st));
     if (h->opts.precision == SLR_PREC_FP64) {
         CK(launch_band_solve<double>(h->op64, h->hs.p, h->hs.wmax, f, ld, t, ld, nullptr, 0, nrhs, st));
         return SLR_OK;
@@ -1284,6 +1321,7 @@ static slr_status interface_solve(slr_handle h, const double* g, double* y, int3
     }
     if (s == 0) return SLR_OK;
     DeviceGuard gd(h->device);
+    CS(clear_status(h, st));
     if (h->opts.precision == SLR_PREC_FP64) {
         DevOperator<double>& op = h->op64;
         CK(launch_c_forward<double>(op.cf, g, ld, op.wf, nrhs, st));
@@ -1320,6 +1358,7 @@ slr_status slr_pcg_solve(slr_handle h, const double* b, double* x, int32_t nrhs,
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t nn = n;
     // start: r = P b (DD order), x = 0, b.b, flags, z = M^{-1} r, rho = r.z, p = z
+    CS(clear_status(h, st));
     CK(launch_permute(n, nrhs, h->perm, b, ld, h->pr, nn, true, st));
     CK(cudaMemsetAsync(h->px, 0, sizeof(double) * nn * nrhs, st));
     CK(launch_dots(nn, nrhs, h->pr, nn, h->pr, nn, h->dpart, h->scal + 4, 8, st));
@@ -1333,7 +1372,7 @@ slr_status slr_pcg_solve(slr_handle h, const double* b, double* x, int32_t nrhs,
         // the capture fails (another thread may have made a call that waits for
         // the whole device meanwhile) this solve runs the same kernels from the
         // host loop, and the next solve captures again
-        if (h->opts.reserved[1] == 1 || pcg_graph(h, nrhs, &gr) != SLR_OK) {
+        if (h->opts.host_loop == 1 || pcg_graph(h, nrhs, &gr) != SLR_OK) {
             CS(pcg_host_loop(h, nrhs, tol, maxit, st));
         } else {
             const double ctl[2] = {tol * tol, (double)maxit};
@@ -1353,17 +1392,7 @@ slr_status slr_pcg_solve(slr_handle h, const double* b, double* x, int32_t nrhs,
     CK(cudaMemcpyAsync(fl.data(), h->iflags, sizeof(int32_t) * fl.size(), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     slr_status ret = SLR_OK;
-    {
-        int32_t e = 0;
-        const int32_t* ep = h->opts.precision == SLR_PREC_FP64 ? h->op64.err : h->op32.err;
-        CK(cudaMemcpyAsync(&e, ep, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        if (e) {
-            set_error(e == 2 ? "a bounded grid-barrier wait expired in the C solve"
-                             : "a bounded device wait expired in the band solve");
-            return SLR_ERR_TIMEOUT;
-        }
-    }
+    CS(read_status(h, status_word(h), st));
     for (int j = 0; j < nrhs; ++j) {
         if (iters_out) iters_out[j] = fl[4 * j + 1];
         double bb = sc[8 * j + 4];
@@ -1388,6 +1417,7 @@ slr_status slr_gmres_solve(slr_handle h, const double* b, double* x, int32_t nrh
     DeviceGuard g(h->device);
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t nn = n;
+    CS(clear_status(h, st));
     CK(launch_permute(n, nrhs, h->perm, b, ld, h->pr, nn, true, st));   // b in DD order
     slr_status ret = SLR_OK;
     for (int32_t j = 0; j < nrhs; ++j) {
@@ -1399,18 +1429,7 @@ slr_status slr_gmres_solve(slr_handle h, const double* b, double* x, int32_t nrh
         if (!(rel <= tol * (1.0 + 1e-6)) && ret == SLR_OK) ret = SLR_ERR_NOT_CONVERGED;
     }
     CK(launch_permute(n, nrhs, h->perm, h->px, nn, x, ld, false, st));  // x = P^T x_dd
-    CK(cudaStreamSynchronize(st));
-    {
-        int32_t e = 0;
-        const int32_t* ep = h->opts.precision == SLR_PREC_FP64 ? h->op64.err : h->op32.err;
-        CK(cudaMemcpyAsync(&e, ep, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        if (e) {
-            set_error(e == 2 ? "a bounded grid-barrier wait expired in the C solve"
-                             : "a bounded device wait expired in the band solve");
-            return SLR_ERR_TIMEOUT;
-        }
-    }
+    CS(read_status(h, status_word(h), st));
     if (ret == SLR_ERR_NOT_CONVERGED) set_error("GMRES reached maxit");
     return ret;
 }
@@ -1476,6 +1495,7 @@ slr_status slr_add_vectors(slr_handle h, int32_t k_add, int32_t lanczos_steps, v
     cudaStream_t st = (cudaStream_t)stream;
     h->stream = st;
     int32_t added = 0;
+    CS(clear_status(h, st));
     slr_status r = run_lanczos_deflated(h, k_add, lanczos_steps, st, &added);
     if (added_out) *added_out = added;
     if (r == SLR_OK) account(h);
@@ -1566,6 +1586,14 @@ slr_status slr_get_info(slr_handle h, slr_info* info) {
     for (int i = 0; i < 3; ++i) info->lanczos_seconds[i] = h->lanczos_seconds[i];
     return SLR_OK;
 }
+
+slr_status slr_device_status(slr_handle h, void* stream) {
+    CS(check_handle(h));
+    DeviceGuard g(h->device);
+    return read_status(h, status_word(h), (cudaStream_t)stream);
+}
+
+void slr_inject_alloc_failure(int64_t nth) { g_fail_alloc.store(nth > 0 ? nth : 0); }
 
 void slr_destroy(slr_handle h) {
     if (!h) return;

@@ -146,7 +146,7 @@ k_band_solve2(const BandBlock* __restrict__ blocks, const T* __restrict__ fac, c
     uint64_t* empty = full + kMaxBuf;                                 // [kMaxBuf]
     int* segU = reinterpret_cast<int*>(empty + kMaxBuf);             // [kRB+1] first segment of row block rb
     int* segL = segU + (kRB + 1);                                    // [kRB+1]
-    int* hdr = segL + (kRB + 1);                                     // nU, nL, segments per chunk
+    int* hdr = segL + (kRB + 1);                                     // nU, nL, segments per chunk, abort
     uintptr_t vp = reinterpret_cast<uintptr_t>(hdr + 4);
     vp = (vp + 15) & ~uintptr_t(15);
     T* vst = reinterpret_cast<T*>(vp);              // [NR][W] y_{J-1} (fwd) / x_{J+1} (bwd), whole plane
@@ -183,6 +183,7 @@ k_band_solve2(const BandBlock* __restrict__ blocks, const T* __restrict__ fac, c
         hdr[0] = (a + per - 1) / per;
         hdr[1] = (d + per - 1) / per;
         hdr[2] = per;
+        hdr[3] = 0;                                // set once a bounded wait of this CTA expires
         for (int i = 0; i < nbuf; ++i) {
             mbar_init(&full[i], 1);
             mbar_init(&empty[i], kW);
@@ -222,29 +223,55 @@ k_band_solve2(const BandBlock* __restrict__ blocks, const T* __restrict__ fac, c
             next_block(c, cur_type, cur_plane);
         }
     };
-    auto wait_bar = [&](uint64_t* bar, uint32_t par) {
+    // After a bounded wait expires the CTA aborts: the status word and the
+    // CTA's abort flag (hdr[3]) are set, no further copy is issued, the block
+    // products are skipped (the barrier sequence is kept, so no peer waits on
+    // this CTA), and before it exits thread 0 waits for the copies it issued.
+    volatile int* abort_flag = hdr + 3;
+    auto wait_bar = [&](uint64_t* bar, uint32_t par) -> bool {
         long long it = 0;
         while (!mbar_try_wait(bar, par)) {
             if (++it > kSpin) {
-                if (lane == 0) atomicExch(err, 1);
-                break;
+                atomicExch(err, 1);
+                *abort_flag = 1;
+                return false;
             }
         }
+        return true;
     };
-    // chunk k's data has landed (the (k / nbuf)-th fill of its slot)
-    auto wait_full = [&](int k) { wait_bar(&full[k % nbuf], (uint32_t)((k / nbuf) & 1)); };
-    // this warp is done with chunk k's slot
+    // chunk k's data has landed (the (k / nbuf)-th fill of its slot); false once the CTA
+    // aborted.  The answer is the same for the whole warp (all lanes saw the data land).
+    auto wait_full = [&](int k) -> bool {
+        bool ok = !*abort_flag && wait_bar(&full[k % nbuf], (uint32_t)((k / nbuf) & 1));
+        return __all_sync(0xffffffffu, ok);
+    };
+    // this warp is done with chunk k's slot (its release is ordered after a store
+    // of the abort flag, so the refilling thread sees the flag once it has the slot)
     auto release = [&](int k) {
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[k % nbuf]);
     };
     // thread 0, before consuming chunk k: once every warp has released chunk
-    // k - 1, its slot takes the next chunk of the stream
+    // k - 1, its slot takes the next chunk of the stream (unless the CTA aborted:
+    // a warp whose wait for chunk k - 1 expired may have left that copy in flight)
     auto refill = [&](int k) {
-        if (tid == 0 && k >= 1 && issued < total) {
-            wait_bar(&empty[(k - 1) % nbuf], (uint32_t)(((k - 1) / nbuf) & 1));
-            fence_proxy_async();
-            issue_next();
+        if (tid == 0 && k >= 1 && issued < total && !*abort_flag) {
+            if (wait_bar(&empty[(k - 1) % nbuf], (uint32_t)(((k - 1) / nbuf) & 1)) && !*abort_flag) {
+                fence_proxy_async();
+                issue_next();
+            }
+        }
+    };
+    // thread 0 at exit after an abort: the last copy issued into each slot has
+    // landed (the fills of a slot are issued one after another, each once the
+    // previous one was consumed, so the last one completing means all did)
+    auto drain = [&]() {
+        if (tid != 0 || !*abort_flag) return;
+        for (int sl = 0; sl < nbuf && sl < issued; ++sl) {
+            const int last = sl + ((issued - 1 - sl) / nbuf) * nbuf;
+            long long it = 0;
+            while (!mbar_try_wait(&full[sl], (uint32_t)((last / nbuf) & 1)) && ++it <= kSpin) {
+            }
         }
     };
     auto peer = [&](T* p, int r) -> T* {
@@ -272,10 +299,14 @@ k_band_solve2(const BandBlock* __restrict__ blocks, const T* __restrict__ fac, c
         const int* seg = upper ? segU : segL;
         for (int ix = 0; ix < nch; ++ix, ++k) {
             refill(k);
-            wait_full(k);
+            const bool landed = wait_full(k);
             if (pending) {                 // the input vector's last stores (peers included)
                 cluster_wait<G>();
                 pending = false;
+            }
+            if (!landed) {                 // aborted: no product on a slot that may not have landed
+                release(k);
+                continue;
             }
             const int s0 = ix * per, s1 = min(s0 + per, seg[kRB]);
             const T* P = reinterpret_cast<const T*>(ring + (size_t)(k % nbuf) * slot);
@@ -395,6 +426,7 @@ k_band_solve2(const BandBlock* __restrict__ blocks, const T* __restrict__ fac, c
         pending = true;
     }
     if (pending) cluster_wait<G>();    // no CTA leaves while a peer may still store into it
+    drain();                           // nor with a bulk copy still writing its shared memory
 }
 
 // Shared memory besides the ring (barriers, column tables, vectors, partials,

@@ -41,6 +41,7 @@ struct DevCFactor {
     int32_t max_cta_tasks = 1;                // most CTA tasks of any step (caps the grid)
     unsigned* bar = nullptr;                  // grid barrier counter, zeroed before each launch
     int32_t* err = nullptr;                   // the operator's status word
+    long long grid_spin = 1ll << 22;          // polls of a grid-barrier wait (opts.spin_limit)
     // top zone (levels >= top_lev): explicit inverse of L_TT, one step per direction
     int32_t top_lev = 0, nT = 0;
     int32_t *tpos = nullptr, *tseg_row = nullptr, *tsk_lo = nullptr, *tp_pos = nullptr, *tb_cb_part = nullptr;
@@ -122,9 +123,14 @@ struct slr_handle_s {
     int64_t* bf_soff = nullptr;
     bool band_on_device = false;     // the B_i were factored on the device
     double lanczos_seconds[3] = {0, 0, 0};   // setup Lanczos: H applies, reorthogonalisation, eigensolve + U_k
+    void* noalloc_base = nullptr;    // device address of slr_apply_noalloc's scratch array (slr_noalloc.cu)
 };
 
 namespace slr {
+
+// Looks up the device address of slr_apply_noalloc's scratch array in the
+// current context and stores it in h->noalloc_base (slr_noalloc.cu).
+slr_status noalloc_lookup(slr_handle h);
 
 // Kernel launches of the library: a process-wide count, and the calling
 // thread's own count (a graph capture takes back what its thread captured).

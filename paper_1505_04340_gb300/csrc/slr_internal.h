@@ -55,7 +55,7 @@ void band_assign_blocks(BandBlock& b, int G);
 // The blocks in the order their clusters are launched: 1 = subdomain order,
 // 2 = heaviest first, 3 = heaviest and lightest alternating (work c W (W+1)).
 std::vector<BandBlock> band_run_order(const std::vector<BandBlock>& band, int mode);
-// The order opts.reserved[10] = 0 selects: with two CTAs per SM the most and
+// The order opts.band_order = 0 selects: with two CTAs per SM the most and
 // least loaded subdomains tend to share SMs (FP64 3-D 64^3: 326 us per B-solve
 // instead of 370 in subdomain order; the HBM-bound FP32 solve does not change).
 constexpr int kBandOrderAuto = 3;

@@ -111,6 +111,7 @@ struct CView {
     int32_t *tf_cnt, *tb_cnt;
     unsigned* bar;
     int32_t* err;
+    long long spin;    // polls of a grid-barrier wait before it gives up
 };
 
 // sum of w[seg_row[e]] for e = e0 .. e1-1, in that order: indices and values are
@@ -760,19 +761,20 @@ k_ctop_bwd(const CView<T> cf, const T* yf, T* xf, T* y_dd, int64_t ldy, int32_t 
 constexpr int kPersT = 1024;                  // 32 warps, one CTA per SM
 constexpr int kPersW = kPersT / 32;
 constexpr int kSmallG = kPersT / kSmallT;     // fused levels: 4 groups of 256 threads, a supernode each
-constexpr long long kGridSpin = 1ll << 22;    // bounded barrier wait (x 64 ns sleep: about a quarter second)
-
 // All CTAs arrive; the counter (zeroed before the launch) reaches target =
-// round x gridDim.x.  A wait that runs out sets the status word and goes on;
-// once the status word is set, later waits give up early too.
-__device__ __forceinline__ void grid_barrier(unsigned* bar, unsigned target, int32_t* err) {
+// round x gridDim.x.  A wait polls at most `spin` times (64 ns sleep between
+// polls); one that runs out sets the status word and goes on (the CTAs then
+// compute on inputs that may not be final: every index they use comes from the
+// factor's structure, so nothing reads or writes out of bounds); once the
+// status word is set, later waits give up early too.
+__device__ __forceinline__ void grid_barrier(unsigned* bar, unsigned target, int32_t* err, long long spin) {
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
         atomicAdd(bar, 1u);
         long long it = 0;
         while (*reinterpret_cast<volatile unsigned*>(bar) < target) {
-            if (++it > kGridSpin) {
+            if (++it > spin) {
                 atomicExch(err, 2);
                 break;
             }
@@ -824,7 +826,7 @@ k_cfwd_persistent(const CView<T> cf, const T* g, int64_t ldg, T* xf, int32_t nrh
                                          xf, nrhs);
             }
         }
-        if (any && --steps_left > 0) grid_barrier(cf.bar, ++round * gridDim.x, cf.err);
+        if (any && --steps_left > 0) grid_barrier(cf.bar, ++round * gridDim.x, cf.err, cf.spin);
     }
 }
 
@@ -852,7 +854,7 @@ k_cbwd_persistent(const CView<T> cf, const T* yf, T* xf, T* y_dd, int64_t ldy, i
             for (int q = blockIdx.x; q < nt; q += gridDim.x)
                 cbwd_task_cta<T, kPersW, 8, 4>(cf, cf.tasks[t0 + q], sm, false, red, yf, xf, y_dd, ldy, nrhs);
         }
-        if (any && --steps_left > 0) grid_barrier(cf.bar, ++round * gridDim.x, cf.err);
+        if (any && --steps_left > 0) grid_barrier(cf.bar, ++round * gridDim.x, cf.err, cf.spin);
     }
 }
 
@@ -1195,6 +1197,7 @@ CView<T> make_view(const DevCFactor<T>& cf, int32_t nsteps) {
     v.tb_cnt = cf.tb_cnt;
     v.bar = cf.bar;
     v.err = cf.err;
+    v.spin = cf.grid_spin;
     return v;
 }
 

@@ -9,11 +9,12 @@
 // without depending on the handle's workspace sizing.  This entry point
 // allocates nothing: it carves its scratch from one static __device__ array
 // of kNoAllocBytes, which every GPU that loads the library holds until exit.
+// slr_setup looks up the array's device address (noalloc_lookup) and keeps it
+// in the handle.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cstdint>
-#include <mutex>
 #include <string>
 #include <type_traits>
 
@@ -24,32 +25,31 @@ using namespace slr;
 namespace {
 
 constexpr size_t kNoAllocBytes = 32ull << 20;   // 32 MiB per device
-constexpr int kMaxDevices = 64;
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
-std::mutex g_noalloc_mu;
-void* g_noalloc_addr[kMaxDevices] = {};          // device address of the array, per device
+}  // namespace
 
-// Device address of the array on `dev` (which is current): looked up once per device.
-slr_status scratch_base(int dev, unsigned char** out) {
-    if (dev < 0 || dev >= kMaxDevices) {
-        set_error("slr_apply_noalloc: device index out of range");
-        return SLR_ERR_UNSUPPORTED;
+// Device address of the array in the current device's context, stored in the
+// handle by slr_setup (with the handle's device current, outside any stream
+// capture).  In host code the array's name is only a host-side stand-in; its
+// device address must come from cudaGetSymbolAddress.  The handle's other
+// device memory lives in the same context, so the address stays valid for as
+// long as the handle does.
+slr_status slr::noalloc_lookup(slr_handle h) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+        cudaGetLastError();
+        set_error(std::string("cudaGetSymbolAddress of the allocation-free scratch array failed: ") +
+                  cudaGetErrorString(e));
+        return SLR_ERR_CUDA;
     }
-    std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_addr[dev]) {
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p) {
-            set_error(std::string("slr_apply_noalloc: cudaGetSymbolAddress failed: ") + cudaGetErrorString(e));
-            return SLR_ERR_CUDA;
-        }
-        g_noalloc_addr[dev] = p;
-    }
-    *out = static_cast<unsigned char*>(g_noalloc_addr[dev]);
+    h->noalloc_base = p;
     return SLR_OK;
 }
+
+namespace {
 
 // Hands out 256-byte aligned slices of the array; `need` counts the bytes.
 struct Carver {
@@ -132,16 +132,19 @@ slr_status run_noalloc(slr_handle h, DevOperator<T> op, const double* r, double*
                   std::to_string(nrhs) + ", more than its fixed " + std::to_string(kNoAllocBytes) + " bytes");
         return SLR_ERR_UNSUPPORTED;
     }
-    unsigned char* base = nullptr;
-    slr_status st = scratch_base(h->device, &base);
-    if (st != SLR_OK) return st;
+    unsigned char* base = static_cast<unsigned char*>(h->noalloc_base);
+    if (!base) {
+        set_error("slr_apply_noalloc: the handle holds no address of the scratch array");
+        return SLR_ERR_CUDA;
+    }
     carve(h, op, nrhs, base);
+    NA_CK(cudaMemsetAsync(op.err, 0, sizeof(int32_t), s));   // the call's status word (slr_device_status)
     if constexpr (std::is_same<T, double>::value) {
         return apply_with<double>(h, op, r, ld, z, ld, nrhs, s);
     } else {
         const int64_t n = h->hs.n;
         NA_CK(launch_convert<double, float>(n, nrhs, r, ld, op.wr, n, s));
-        st = apply_with<float>(h, op, op.wr, n, op.wz, n, nrhs, s);
+        const slr_status st = apply_with<float>(h, op, op.wr, n, op.wz, n, nrhs, s);
         if (st != SLR_OK) return st;
         NA_CK(launch_convert<float, double>(n, nrhs, op.wz, n, z, ld, s));
         return SLR_OK;
@@ -161,11 +164,22 @@ extern "C" slr_status slr_apply_noalloc(slr_handle h, const double* r, double* z
         return SLR_ERR_INVALID_ARG;
     }
     int old = -1;
-    cudaGetDevice(&old);
-    if (old != h->device) cudaSetDevice(h->device);
+    cudaError_t e = cudaGetDevice(&old);
+    if (e == cudaSuccess && old != h->device) e = cudaSetDevice(h->device);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error(std::string("slr_apply_noalloc: cannot make the handle's device current: ") + cudaGetErrorString(e));
+        return SLR_ERR_CUDA;
+    }
     cudaStream_t s = (cudaStream_t)stream;
-    const slr_status st = h->opts.precision == SLR_PREC_FP64 ? run_noalloc<double>(h, h->op64, r, z, nrhs, ld, s)
-                                                             : run_noalloc<float>(h, h->op32, r, z, nrhs, ld, s);
-    if (old >= 0 && old != h->device) cudaSetDevice(old);
+    slr_status st = h->opts.precision == SLR_PREC_FP64 ? run_noalloc<double>(h, h->op64, r, z, nrhs, ld, s)
+                                                       : run_noalloc<float>(h, h->op32, r, z, nrhs, ld, s);
+    if (old >= 0 && old != h->device && cudaSetDevice(old) != cudaSuccess) {
+        cudaGetLastError();
+        if (st == SLR_OK) {
+            set_error("slr_apply_noalloc: cannot restore the caller's current device");
+            st = SLR_ERR_CUDA;
+        }
+    }
     return st;
 }

@@ -30,14 +30,22 @@ PRECISION = {"fp64": 0, "mixed": 1}
 EXPORTS = ["slr_default_opts", "slr_setup", "slr_apply", "slr_pcg_solve", "slr_bsolve", "slr_csolve",
            "slr_stilde_solve", "slr_set_lowrank", "slr_get_lowrank", "slr_get_ritz", "slr_get_perm",
            "slr_get_info", "slr_dd_order", "slr_kernel_launches", "slr_destroy", "slr_status_str",
-           "slr_last_error_message", "slr_apply_noalloc", "slr_add_vectors", "slr_gmres_solve"]
+           "slr_last_error_message", "slr_apply_noalloc", "slr_add_vectors", "slr_gmres_solve",
+           "slr_device_status", "slr_inject_alloc_failure"]
+
+
+U_DTYPE = {"fp32": 0, "tf32": 1, "bf16": 2}
 
 
 class Opts(C.Structure):
     _fields_ = [("k", C.c_int32), ("lanczos_steps", C.c_int32), ("theta_mode", C.c_int32),
                 ("precision", C.c_int32), ("nrhs_max", C.c_int32), ("flexible_cg", C.c_int32),
                 ("seed", C.c_uint64), ("c_leaf", C.c_int32), ("verbose", C.c_int32),
-                ("reserved", C.c_int32 * 16)]
+                ("target_kappa", C.c_int32), ("indefinite", C.c_int32), ("u_dtype", C.c_int32),
+                ("band_split", C.c_int32), ("band_slots", C.c_int32), ("band_threads", C.c_int32),
+                ("band_order", C.c_int32), ("band_factor_host", C.c_int32), ("c_persistent", C.c_int32),
+                ("c_levels_only", C.c_int32), ("host_loop", C.c_int32), ("autotune", C.c_int32),
+                ("spin_limit", C.c_int32), ("reserved", C.c_int32 * 8)]
 
 
 class Info(C.Structure):
@@ -90,6 +98,8 @@ def load():
         "slr_get_info": (i32, [vp, P(Info)]),
         "slr_dd_order": (i32, [i32, vp, vp, i32, vp, vp, vp, vp, vp]),
         "slr_kernel_launches": (C.c_int64, []),
+        "slr_device_status": (i32, [vp, vp]),
+        "slr_inject_alloc_failure": (None, [C.c_int64]),
         "slr_destroy": (None, [vp]),
         "slr_status_str": (C.c_char_p, [i32]),
         "slr_last_error_message": (C.c_char_p, []),
@@ -165,7 +175,7 @@ class SLR:
                  precision="fp64", nrhs_max=1, flexible_cg=False, seed=1, c_leaf=64, verbose=False,
                  band_split=0, host_loop=False, band_slots=0, c_persistent=False, autotune=False, target_kappa=0,
                  band_threads=0, c_top_zone=True, band_factor="auto", indefinite=False, band_order=0,
-                 stream=None):
+                 u_dtype="fp32", spin_limit=0, stream=None):
         lib = load()
         self._lib = lib
         self._h = None
@@ -175,17 +185,19 @@ class SLR:
         o.theta_mode, o.precision = THETA[theta], PRECISION[precision]
         o.nrhs_max, o.flexible_cg, o.seed = int(nrhs_max), int(bool(flexible_cg)), int(seed)
         o.c_leaf, o.verbose = int(c_leaf), int(bool(verbose))
-        o.reserved[0] = int(band_split)        # CTAs per subdomain in the band solve, 0 = automatic
-        o.reserved[1] = int(bool(host_loop))   # CG loop driven from the host instead of a CUDA graph
-        o.reserved[2] = int(band_slots)        # band-solve stream buffers, 0 = automatic
-        o.reserved[3] = int(bool(c_persistent))  # C solves in one cooperative launch per direction
-        o.reserved[4] = int(bool(autotune))      # time the candidates at setup and keep the fastest
-        o.reserved[5] = int(target_kappa)        # rank by the rule lambda_{k+1} <= 1 - 1/K (0 = off)
-        o.reserved[6] = int(band_threads)        # threads per band-solve CTA: 512, 256 or 0 (automatic)
-        o.reserved[7] = 0 if c_top_zone else 1   # explicit inverse of the factor's top levels
-        o.reserved[8] = {"auto": 0, "host": 1}[band_factor]   # B_i factored on the device or the host
-        o.reserved[9] = int(bool(indefinite))    # symmetric indefinite A with an SPD interface
-        o.reserved[10] = int(band_order)         # band-solve cluster launch order, 0 = automatic
+        o.band_split = int(band_split)          # CTAs per subdomain in the band solve, 0 = automatic
+        o.host_loop = int(bool(host_loop))      # CG loop driven from the host instead of a CUDA graph
+        o.band_slots = int(band_slots)          # band-solve stream buffers, 0 = automatic
+        o.c_persistent = int(bool(c_persistent))  # C solves in one cooperative launch per direction
+        o.autotune = int(bool(autotune))        # time the candidates at setup and keep the fastest
+        o.target_kappa = int(target_kappa)      # rank by the rule lambda_{k+1} <= 1 - 1/K (0 = off)
+        o.band_threads = int(band_threads)      # threads per band-solve CTA: 512, 256 or 0 (automatic)
+        o.c_levels_only = 0 if c_top_zone else 1  # explicit inverse of the factor's top levels
+        o.band_factor_host = {"auto": 0, "host": 1}[band_factor]   # B_i factored on the device or the host
+        o.indefinite = int(bool(indefinite))    # symmetric indefinite A with an SPD interface
+        o.band_order = int(band_order)          # band-solve cluster launch order, 0 = automatic
+        o.u_dtype = U_DTYPE[u_dtype]            # low-rank products on RHS blocks: fp32, tf32, bf16
+        o.spin_limit = int(spin_limit)          # polls of a grid-barrier wait, 0 = default
         self.rowptr, self.colind = _i32(rowptr), _i32(colind)
         self.val = np.ascontiguousarray(val, dtype=np.float64)
         self.part = _i32(part)
@@ -284,6 +296,11 @@ class SLR:
     def apply_noalloc(self, r, stream=None):
         """z = M^{-1} r with the scratch in the library's fixed device array (no allocation)."""
         return self._call(self._lib.slr_apply_noalloc, r, self.n, "r", stream)
+
+    def device_status(self, stream=None):
+        """Status of the device's bounded waits in the calls enqueued so far
+        (0, or 7 = SLR_ERR_TIMEOUT: the last call's outputs are invalid)."""
+        return int(self._lib.slr_device_status(self._h, _stream_ptr(stream)))
 
     def bsolve(self, f, stream=None):
         """t = B^{-1} f on the interior unknowns (DD order)."""

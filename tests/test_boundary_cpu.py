@@ -78,12 +78,15 @@ def test_dd_order_random_partition(lib):
     assert np.array_equal(perm, o.perm) and s == o.s
 
 
-def _setup_status(lib, rp, ci, v, part, p, reserved=None):
+def _setup_status(lib, rp, ci, v, part, p, fields=None):
     from paper_1505_04340_gb300 import slr
     o = slr.Opts()
     lib.slr_default_opts(C.byref(o))
-    for i, r in (reserved or {}).items():
-        o.reserved[i] = r
+    for name, r in (fields or {}).items():
+        if isinstance(name, int):
+            o.reserved[name] = r
+        else:
+            setattr(o, name, r)
     h = C.c_void_p()
     rp, ci, part = (np.ascontiguousarray(a, dtype=np.int32) for a in (rp, ci, part))
     v = np.ascontiguousarray(v, dtype=np.float64)
@@ -107,14 +110,32 @@ def test_setup_rejects_bad_input_before_any_device_work(lib):
     assert "range" in lib.slr_last_error_message().decode()
 
 
-@pytest.mark.parametrize("reserved", [{0: 3}, {1: 2}, {2: 1}, {2: 9}, {3: 2}, {4: -1}, {4: 2}, {5: 1}, {5: -3}, {6: 128}, {6: 1024}, {7: 2}, {7: -1}, {8: 2}, {9: 2}, {10: 4}, {10: -1}, {11: 1}, {15: 1}])
-def test_setup_rejects_bad_tuning_options(lib, reserved):
-    """Band split, host loop, band buffers, C-solve path, autotune, target condition
-    number: out-of-range values are refused before any device work."""
+BAD_OPTIONS = [{"band_split": 3}, {"host_loop": 2}, {"band_slots": 1}, {"band_slots": 9}, {"c_persistent": 2},
+               {"autotune": -1}, {"autotune": 2}, {"target_kappa": 1}, {"target_kappa": -3}, {"band_threads": 128},
+               {"band_threads": 1024}, {"c_levels_only": 2}, {"c_levels_only": -1}, {"band_factor_host": 2},
+               {"indefinite": 2}, {"band_order": 4}, {"band_order": -1}, {"u_dtype": 3}, {"u_dtype": -1},
+               {"u_dtype": 1},                     # a tensor-core dtype needs the mixed path
+               {"spin_limit": -5}, {0: 1}, {7: 1}]
+
+
+@pytest.mark.parametrize("fields", BAD_OPTIONS)
+def test_setup_rejects_bad_tuning_options(lib, fields):
+    """Execution choices, method options and the reserved tail: out-of-range values
+    are refused before any device work."""
     rp, ci, v = slrgen.laplacian((6, 5))
     part = slrgen.box_partition((6, 5), (2, 1))
-    assert _setup_status(lib, rp, ci, v, part, 2, reserved) == 1
+    assert _setup_status(lib, rp, ci, v, part, 2, fields) == 1
     assert "invalid options" in lib.slr_last_error_message().decode()
+
+
+def test_opts_layout_matches_header(lib):
+    """The binding's slr_opts mirrors include/slr.h field for field (names and order)."""
+    import re
+    from paper_1505_04340_gb300 import slr
+    hdr = open(os.path.join(ROOT, "include", "slr.h")).read()
+    body = hdr[hdr.index("typedef struct {", hdr.index("SLR_U_FP32")):hdr.index("} slr_opts;")]
+    names = re.findall(r"^\s*(?:int32_t|uint64_t)\s+(\w+)", body, flags=re.M)
+    assert names == [f for f, _ in slr.Opts._fields_]
 
 
 def test_setup_detects_non_spd_block(lib):

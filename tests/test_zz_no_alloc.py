@@ -31,18 +31,30 @@ def _colmajor(x):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_noalloc_apply_matches_apply_twice(precision):
-    P = slrgen.make_problem("3d", (20, 19, 18), (3, 2, 2), 8, nrhs=2)
-    h = SLR(P.rowptr, P.colind, P.val, P.part, P.nparts, k=P.k, lanczos_steps=P.lanczos_steps,
-            precision=precision, nrhs_max=2)
+@pytest.mark.parametrize("case", ["3d-levels", "3d-persistent", "c2-top-zone"])
+def test_noalloc_apply_matches_apply_twice(precision, case):
+    """The per-level C solve, the cooperative one (its barrier counter lives in the
+    array) and a problem whose C factor has a top zone (its arrival counters too)."""
+    if case == "c2-top-zone":
+        P = slrgen.config2()
+        nr, steps = 1, P.k + 1
+    else:
+        P = slrgen.make_problem("3d", (20, 19, 18), (3, 2, 2), 8, nrhs=2)
+        nr, steps = 2, P.lanczos_steps
+    h = SLR(P.rowptr, P.colind, P.val, P.part, P.nparts, k=P.k, lanczos_steps=steps,
+            precision=precision, nrhs_max=2, c_persistent=(case == "3d-persistent"))
+    info = h.get_info()
+    assert info["c_persistent"] == (case == "3d-persistent")
+    if case == "c2-top-zone":
+        assert info["c_top_positions"] > 0
     lib = slr.load()
     stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
-    r = _colmajor(torch.tensor(np.random.default_rng(3).standard_normal((P.n, 2)), device="cuda"))
+    r = _colmajor(torch.tensor(np.random.default_rng(3).standard_normal((P.n, nr)), device="cuda"))
     z_ref = torch.empty_like(r)
-    assert lib.slr_apply(h._h, C.c_void_p(r.data_ptr()), C.c_void_p(z_ref.data_ptr()), 2, P.n, stream) == 0
+    assert lib.slr_apply(h._h, C.c_void_p(r.data_ptr()), C.c_void_p(z_ref.data_ptr()), nr, P.n, stream) == 0
     for _ in range(2):                       # the array keeps the previous call's contents
         z = torch.full_like(r, float("nan"))
-        st = lib.slr_apply_noalloc(h._h, C.c_void_p(r.data_ptr()), C.c_void_p(z.data_ptr()), 2, P.n, stream)
+        st = lib.slr_apply_noalloc(h._h, C.c_void_p(r.data_ptr()), C.c_void_p(z.data_ptr()), nr, P.n, stream)
         assert st == 0, lib.slr_last_error_message()
         torch.cuda.synchronize()
         err = float((z - z_ref).abs().max() / z_ref.abs().max())
