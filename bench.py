@@ -486,8 +486,11 @@ def measure(args, name, prec, steps, warmup, ctx, headline=False):
     P, wname = build_problem(name)
     _, nrhs, maxit, _ = PROBLEMS[name]
     t0 = time.perf_counter()
+    tc = {}
+    if prec == "mixed" and nrhs >= 8:        # tensor-core products on right-hand-side blocks
+        tc = dict(u_dtype=args.u_dtype, band_mma=args.band_mma)
     h = SLR(P.rowptr, P.colind, P.val, P.part, P.nparts, k=P.k, lanczos_steps=P.lanczos_steps,
-            precision=prec, nrhs_max=nrhs, flexible_cg=(prec == "mixed"), autotune=not args.no_autotune)
+            precision=prec, nrhs_max=nrhs, flexible_cg=(prec == "mixed"), autotune=not args.no_autotune, **tc)
     setup_s = time.perf_counter() - t0
     Bh = np.ascontiguousarray(P.b[:, :nrhs])
     B = torch.tensor(Bh, device=dev)
@@ -561,7 +564,9 @@ def measure(args, name, prec, steps, warmup, ctx, headline=False):
                                    lanczos_reorth=round(info["lanczos_seconds"][1], 4),
                                    lanczos_eig=round(info["lanczos_seconds"][2], 4),
                                    band_on_device=info["band_on_device"]),
-               device_bytes=info["device_bytes"], k=info["k"], lanczos_steps=info["lanczos_steps"])
+               device_bytes=info["device_bytes"], k=info["k"], lanczos_steps=info["lanczos_steps"],
+               tensor_cores={"band_mma": ["off", "tf32", "bf16"][info["band_mma"]],
+                             "u_dtype": ["fp32", "tf32", "bf16"][info["u_dtype"]]})
     out["_x"], out["_z"] = X, z
     if headline:
         # end to end through the public API with host buffers: pinned b -> device, block
@@ -638,15 +643,15 @@ def run_ours(args):
     if ws == 1 and not args.no_cpu_baseline:
         P, _ = build_problem(name)
         v, t_it, t_setup = oracle_sample(P, name)
-        single = oracle_single_thread(name)
         cpu = {"value": v, "unit": "solves/s", "cores": cpu_threads(), "kind": "oracle",
                "nproc": os.cpu_count(),
                "sample": f"2 oracle PCG iterations' work (an A product and an SLR apply of rank {P.k}) on one "
                          f"column of the full workload, {t_it * 1e3:.0f} ms each, scaled to the "
                          f"{PROBLEMS[name][3]}-iteration FP64 solve; oracle setup {t_setup:.1f} s excluded as in "
-                         f"the metric; BLAS/OpenMP pools may use all cores (the oracle's banded and sparse "
-                         f"triangular solves run on one)",
-               "single_thread": single}
+                         f"the metric; the BLAS pool may use every core, but the oracle's banded and sparse "
+                         f"triangular solves run on one (--cpu-single-thread times it with one thread)"}
+        if args.cpu_single_thread:
+            cpu["single_thread"] = oracle_single_thread(name)
     line = {
         "metric": METRIC, "value": hm["solves_per_s"], "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": hm["ms_per_step"], "higher_is_better": True, "scaling": "weak",
@@ -687,12 +692,18 @@ def main():
                     help="the workload (default: the 3-D 96^3 block of 32 right-hand sides)")
     ap.add_argument("--headline-only", action="store_true", help="skip the other workloads and legs")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-single-thread", action="store_true",
+                    help="also time the CPU baseline's sample with one BLAS/OpenMP thread (a second oracle setup)")
     ap.add_argument("--cpu-sample", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--profile", action="store_true", help="solves inside an NVTX range only (for ncu)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--profile-kernel", default="pcg", choices=["pcg", "bsolve", "csolve", "apply"])
     ap.add_argument("--maxit", type=int, default=0, help="PCG iteration cap of --profile (0: the workload's)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the built-in launch choices")
+    ap.add_argument("--band-mma", default="off", choices=["off", "tf32", "bf16"],
+                    help="band solve of right-hand-side blocks on the tensor cores (mixed path)")
+    ap.add_argument("--u-dtype", default="fp32", choices=["fp32", "tf32", "bf16"],
+                    help="low-rank products of right-hand-side blocks (mixed path)")
     ap.add_argument("--serving-requests", type=int, default=256, help="config-5 request stream length (0: skip)")
     # the 256-request stream carries 4.4 right-hand sides per request on average; 12 requests/s
     # (about 53 solves/s) keeps the server below its measured capacity so latencies are service

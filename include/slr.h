@@ -125,11 +125,18 @@ typedef struct {
                                fit, and both C-solve paths, on this operator, and keeps the
                                fastest; the choice is cached per device, precision and
                                problem shape for the process's life                      */
+    int32_t band_mma;       /* 0 (default): the band solve runs on the CUDA cores.
+                               SLR_U_TF32 or SLR_U_BF16 (mixed path only): blocks of 8 or
+                               more right-hand sides are solved with the band factor and
+                               the plane vectors rounded to TF32 / BF16 and every block
+                               product on the tensor cores, accumulated in FP32; needs the
+                               B_i factored on the device (planes of at most 256 rows),
+                               else it is not used (slr_info.band_mma says which ran)   */
     int32_t spin_limit;     /* polls of a bounded device wait between steps of the
                                cooperative C solve (c_persistent) before it gives up and
                                reports SLR_ERR_TIMEOUT; 0 = the default (2^22 polls, about a
                                quarter second)                                           */
-    int32_t reserved[8];    /* must be 0                                                  */
+    int32_t reserved[7];    /* must be 0                                                  */
 } slr_opts;
 
 typedef struct {
@@ -158,6 +165,9 @@ typedef struct {
     double lanczos_seconds[3];   /* setup Lanczos (Section 5.1) split: H applies with the alpha
                                     dot, full reorthogonalisation with the beta norm, the
                                     tridiagonal eigensolve on the host and U_k = V Y_k      */
+    int32_t band_mma;            /* the band solve's tensor-core factor in use: 0 (none),
+                                    SLR_U_TF32 or SLR_U_BF16 (opts.band_mma)               */
+    int32_t u_dtype;             /* the low-rank products' arithmetic (opts.u_dtype)        */
 } slr_info;
 
 /* Fill *opts with defaults: k = 16, m = 5k, theta = lambda_{k+1}, FP64, 1 RHS, seed 1. */

@@ -296,17 +296,22 @@ slr_status set_operator_lowrank(slr_handle h, DevOperator<T>& op, const double* 
                                 int32_t k, const std::vector<double>& lam, double theta) {
     const int64_t s = h->hs.s;
     const int32_t r = std::max(1, h->opts.nrhs_max);
+    if (op.U_tc_rm) {   // the tensor-core copies are rebuilt below
+        const size_t eb = lowrank_tc_elem(op.u_dtype) * (size_t)s * k_old;
+        dfree(h, reinterpret_cast<char*&>(op.U_tc_rm), eb);
+        if (op.U_tc_cm) dfree(h, reinterpret_cast<char*&>(op.U_tc_cm), eb);
+    }
     if (op.U && k_old != k) {
         dfree(h, op.U, (size_t)s * k_old);
         dfree(h, op.dvec, (size_t)k_old);
         dfree(h, op.vk, (size_t)k_old * r);
-        dfree(h, op.part, (size_t)k_old * r * kRedBlocks);
+        dfree(h, op.part, (size_t)lowrank_part_elems((int32_t)s, k_old, r));
     }
     if (!op.U && k > 0) {
         CS(dalloc(h, &op.U, (size_t)s * k));
         CS(dalloc(h, &op.dvec, (size_t)k));
         CS(dalloc(h, &op.vk, (size_t)k * r));
-        CS(dalloc(h, &op.part, (size_t)k * r * kRedBlocks));
+        CS(dalloc(h, &op.part, (size_t)lowrank_part_elems((int32_t)s, k, r)));
     }
     if (k > 0) {
         if constexpr (std::is_same<T, double>::value) {
@@ -314,6 +319,16 @@ slr_status set_operator_lowrank(slr_handle h, DevOperator<T>& op, const double* 
                 CK(cudaMemcpyAsync(op.U, U64_dev, sizeof(double) * s * k, cudaMemcpyDeviceToDevice, h->stream));
         } else {
             CK(launch_convert<double, float>(s, k, U64_dev, s, op.U, s, h->stream));
+            op.u_dtype = h->opts.u_dtype;
+            if (op.u_dtype != SLR_U_FP32 && k <= 128) {
+                const size_t eb = lowrank_tc_elem(op.u_dtype) * (size_t)s * k;
+                char *rm = nullptr, *cm = nullptr;
+                CS(dalloc(h, &rm, eb));
+                if (op.u_dtype == SLR_U_BF16) CS(dalloc(h, &cm, eb));
+                op.U_tc_rm = rm;
+                op.U_tc_cm = cm;
+                CK(launch_lowrank_tc_pack(op.u_dtype, (int32_t)s, k, U64_dev, rm, cm, h->stream));
+            }
         }
         // d_i = (1 - lambda_i)^{-1} - (1 - theta)^{-1}, formed in FP64 (cancellation near 1)
         std::vector<double> d(k);
@@ -390,8 +405,9 @@ slr_status read_status(slr_handle h, const int32_t* word, cudaStream_t st) {
     CK(cudaMemcpyAsync(&e, word, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     if (e) {
-        set_error(e == 2 ? "a bounded grid-barrier wait expired in the C solve"
-                         : "a bounded device wait expired in the band solve");
+        set_error(e == 2   ? "a bounded grid-barrier wait expired in the C solve"
+                  : e == 3 ? "a bounded tensor-core completion wait expired in the low-rank products"
+                           : "a bounded device wait expired in the band solve");
         return SLR_ERR_TIMEOUT;
     }
     (void)h;
@@ -793,9 +809,12 @@ slr_status autotune(slr_handle h, DevOperator<T>& op, cudaStream_t st) {
             cached = true;
         }
     }
+    // the candidates are timed on blocks of nrhs_max right-hand sides (the workspaces'
+    // width), the block the handle's solves will carry
+    const int32_t r = std::max(1, h->opts.nrhs_max);
     if (!cached && hs.p > 0 && hs.wmax > 0) {
-        CK(cudaMemsetAsync(op.eb, 0, sizeof(T) * std::max(hs.nI, 1), st));
-        CK(cudaMemsetAsync(op.gp, 0, sizeof(T) * std::max(hs.s, 1), st));
+        CK(cudaMemsetAsync(op.eb, 0, sizeof(T) * std::max(hs.nI, 1) * r, st));
+        CK(cudaMemsetAsync(op.gp, 0, sizeof(T) * std::max(hs.s, 1) * r, st));
         double best_us = 1e30;
         for (int32_t G : {1, 2, 4}) {
             if (!band_split_ok(hs.wmax, G) || (G > 1 && hs.wmax < 32 * G) || hs.p * G > 2 * nsm) continue;
@@ -806,7 +825,7 @@ slr_status autotune(slr_handle h, DevOperator<T>& op, cudaStream_t st) {
                     op.band_nt = nt;
                     double us = 0;
                     CS(time_us([&]() -> slr_status {
-                        CK(launch_band_solve<T>(op, hs.p, hs.wmax, op.eb, hs.nI, op.tB, hs.nI, nullptr, 0, 1, st));
+                        CK(launch_band_solve<T>(op, hs.p, hs.wmax, op.eb, hs.nI, op.tB, hs.nI, nullptr, 0, r, st));
                         return SLR_OK;
                     }, st, 5, &us));
                     if (us < best_us) {
@@ -823,16 +842,16 @@ slr_status autotune(slr_handle h, DevOperator<T>& op, cudaStream_t st) {
             op.cf.per_level = (v == 0);
             cudaGraphExec_t ex = nullptr;
             CS(capture_graph(h, [&](cudaStream_t cs) -> slr_status {
-                CK(launch_c_forward<T>(op.cf, op.gp, hs.s, op.wf, 1, cs));
-                CK(launch_c_backward<T>(op.cf, op.wf, op.xf, op.gp, hs.s, 1, cs));
+                CK(launch_c_forward<T>(op.cf, op.gp, hs.s, op.wf, r, cs));
+                CK(launch_c_backward<T>(op.cf, op.wf, op.xf, op.gp, hs.s, r, cs));
                 return SLR_OK;
             }, &ex));
-            const slr_status r = time_us([&]() -> slr_status {
+            const slr_status rs = time_us([&]() -> slr_status {
                 CK(cudaGraphLaunch(ex, st));
                 return SLR_OK;
             }, st, 5, &c_us[v]);
             cudaGraphExecDestroy(ex);
-            CS(r);
+            CS(rs);
         }
         // the two paths often time within noise of each other: keep the per-level default
         // unless the persistent one is clearly (5%) faster, so the pick is stable from run to run
@@ -955,6 +974,22 @@ slr_status setup_impl(slr_handle h, int32_t n, const int32_t* rowptr, const int3
     if (h->opts.autotune == 1) {
         if (h->opts.precision == SLR_PREC_FP64) CS(autotune<double>(h, h->op64, st));
         else CS(autotune<float>(h, h->op32, st));
+    }
+    if (dev_band && h->opts.band_mma != 0 && h->opts.precision == SLR_PREC_MIXED) {
+        // the tensor-core band solve's factor, packed from the same plane blocks; its
+        // table follows the launch order of the CUDA-core kernel's clusters
+        DevOperator<float>& op = h->op32;
+        int32_t cmax = 0;
+        for (const BandBlock& b : hs.band) cmax = std::max(cmax, b.c);
+        const std::vector<BandTcBlock> tcb = band_tc_layout(
+            band_run_order(hs.band, h->opts.band_order ? h->opts.band_order : kBandOrderAuto), h->opts.band_mma,
+            &op.band_tc_bytes);
+        CS(upload(h, &op.band_tc, tcb));
+        CS(dalloc(h, &op.band_tc_fac, (size_t)op.band_tc_bytes));
+        CK(launch_band_tc_pack(h->opts.band_mma, op.band_tc, hs.p, cmax, h->bf_scr, h->bf_soff, op.band_tc_fac,
+                               hs.indefinite, st));
+        op.band_mma = h->opts.band_mma;
+        op.band_tc_wmax = hs.wmax;
     }
     if (dev_band) {
         // a mixed-precision handle keeps an FP64 copy of the band factor on the host
@@ -1257,7 +1292,8 @@ slr_status slr_setup(int32_t n, const int32_t* rowptr, const int32_t* colind, co
         o.indefinite < 0 || o.indefinite > 1 || o.band_order < 0 || o.band_order > 3 ||
         o.u_dtype < SLR_U_FP32 || o.u_dtype > SLR_U_BF16 ||
         (o.u_dtype != SLR_U_FP32 && o.precision != SLR_PREC_MIXED) || o.spin_limit < 0 ||
-        std::any_of(o.reserved, o.reserved + 8, [](int32_t v) { return v != 0; })) {
+        o.band_mma < 0 || o.band_mma > SLR_U_BF16 || (o.band_mma != 0 && o.precision != SLR_PREC_MIXED) ||
+        std::any_of(o.reserved, o.reserved + 7, [](int32_t v) { return v != 0; })) {
         set_error("invalid options");
         delete h;
         return SLR_ERR_INVALID_ARG;
@@ -1584,6 +1620,8 @@ slr_status slr_get_info(slr_handle h, slr_info* info) {
     info->c_top_entries = hs.cf.tsk_off.empty() ? 0 : hs.cf.tsk_off.back();
     info->band_on_device = h->band_on_device ? 1 : 0;
     for (int i = 0; i < 3; ++i) info->lanczos_seconds[i] = h->lanczos_seconds[i];
+    info->band_mma = f64 ? 0 : h->op32.band_mma;
+    info->u_dtype = f64 ? 0 : h->op32.u_dtype;
     return SLR_OK;
 }
 

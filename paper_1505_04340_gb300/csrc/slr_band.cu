@@ -38,6 +38,10 @@ template <typename T>
 cudaError_t launch_band_solve(const DevOperator<T>& op, int32_t p, int32_t wmax, const T* in, int64_t ldi, T* out,
                               int64_t ldo, const T* base, int64_t ldb, int32_t nrhs, cudaStream_t st) {
     if (p == 0 || wmax == 0) return cudaSuccess;
+    if constexpr (sizeof(T) == 4) {
+        // blocks of right-hand sides on the tensor cores when the operator carries that factor
+        if (op.band_tc && nrhs >= 8) return launch_band_solve_tc(op, p, in, ldi, out, ldo, base, ldb, nrhs, st);
+    }
     for (int32_t c = 0; c < nrhs;) {
         const int32_t left = nrhs - c;
         int nr = 1;

@@ -77,7 +77,18 @@ struct DevOperator {
     T *wr = nullptr, *wz = nullptr;          // n: converted input / output (mixed only)
     T *tB = nullptr, *eb = nullptr;          // nI
     T *gp = nullptr, *wf = nullptr, *xf = nullptr;   // s
-    T *vk = nullptr, *part = nullptr;        // k x r, partial sums
+    T *vk = nullptr, *part = nullptr;        // k x r, partial sums (lowrank_part_elems)
+    // tensor-core low-rank products (FP32 apply, opts.u_dtype TF32 or BF16): U in the
+    // operand type, row-major (pass 2) and, for BF16, column-major (pass 1)
+    int32_t u_dtype = 0;
+    void *U_tc_rm = nullptr, *U_tc_cm = nullptr;
+    // tensor-core band solve for blocks of >= 8 right-hand sides (FP32 apply,
+    // opts.band_mma TF32 or BF16): sub-tile table in launch order and the packed factor
+    int32_t band_mma = 0;
+    BandTcBlock* band_tc = nullptr;
+    unsigned char* band_tc_fac = nullptr;
+    int64_t band_tc_bytes = 0;
+    int32_t band_tc_wmax = 0;
     bool ready = false;
 };
 
@@ -145,6 +156,15 @@ cudaError_t launch_band_solve(const DevOperator<T>& op, int32_t p, int32_t wmax,
                               T* out, int64_t ldo, const T* base, int64_t ldb, int32_t nrhs,
                               cudaStream_t st);
 // shared memory one band-solve CTA needs for plane width wmax and nr columns per pass
+// ---- K1 on the tensor cores (slr_band_tc.cu): the sub-tile layout of the band
+// factor (per subdomain, in the given launch order; *bytes: factor size), its
+// pack kernel from the device plane blocks, and the solve of 8-64 columns at a time
+std::vector<BandTcBlock> band_tc_layout(const std::vector<BandBlock>& run_order, int32_t mma_dtype, int64_t* bytes);
+cudaError_t launch_band_tc_pack(int32_t mma_dtype, const BandTcBlock* band, int32_t p, int32_t cmax,
+                                const double* scr, const int64_t* soff, unsigned char* fac, bool indef,
+                                cudaStream_t st);
+cudaError_t launch_band_solve_tc(const DevOperator<float>& op, int32_t p, const float* in, int64_t ldi, float* out,
+                                 int64_t ldo, const float* base, int64_t ldb, int32_t nrhs, cudaStream_t st);
 // ---- K2: gp = g - E^T t (g == NULL: gp = E^T t) ;  eb = E y
 template <typename T>
 cudaError_t launch_gather_et(const DevOperator<T>& op, int32_t s, const T* g, int64_t ldg, const T* t,
@@ -181,6 +201,17 @@ cudaError_t launch_c_backward(const DevCFactor<T>& cf, const T* yf, T* xf, T* y_
 template <typename T>
 cudaError_t launch_lowrank(const DevOperator<T>& op, int32_t s, int32_t k, T* w, int32_t nrhs,
                            cudaStream_t st);
+// elements of op.part that launch_lowrank needs for rank k and nrhs columns
+int64_t lowrank_part_elems(int32_t s, int32_t k, int32_t nrhs);
+// the tensor-core variant (slr_lowrank_tc.cu): usable for u_dtype TF32/BF16, 8..64
+// right-hand sides and k <= 128; the pack kernel fills U_tc_rm (and U_tc_cm for
+// BF16) from the FP64 U (s x k column-major)
+bool lowrank_tc_usable(const DevOperator<float>& op, int32_t k, int32_t nrhs);
+cudaError_t launch_lowrank_tc(const DevOperator<float>& op, int32_t s, int32_t k, float* w, int32_t nrhs,
+                              cudaStream_t st);
+size_t lowrank_tc_elem(int32_t u_dtype);
+cudaError_t launch_lowrank_tc_pack(int32_t u_dtype, int32_t s, int32_t k, const double* U, void* Urm, void* Ucm,
+                                   cudaStream_t st);
 // ---- helpers
 template <typename TS, typename TD>
 cudaError_t launch_convert(int64_t rows, int32_t cols, const TS* src, int64_t lds, TD* dst, int64_t ldd,

@@ -40,6 +40,15 @@ struct BandBlock {
     uint8_t rbmap[4][8] = {};        // block of slice g's local row block rb
 };
 
+// The tensor-core band solve's view of a subdomain (slr_band_tc.cu): its factor is
+// stored as 4096-byte sub-tiles (128 rows x one K-step) from byte foff on, per plane
+// [O_J: nU | D_J: nL | O_J^T: nL | D_J^T: nU] sub-tiles.
+struct BandTcBlock {
+    int32_t m = 0, w = 0, c = 0, row0 = 0, id = 0;
+    int32_t nU = 0, nL = 0;      // sub-tiles of an upper / a lower block
+    int64_t foff = 0;            // bytes
+};
+
 // Slice geometry (the host packer and the device kernel agree on it).
 // Local row block rb of slice g starts at plane row band_R0; in an upper block
 // it meets columns [band_cU0, W), in a lower block columns [0, band_cL1).

@@ -13,6 +13,7 @@
 #include <atomic>
 #include <cstdint>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "slr_device.h"
@@ -100,6 +101,7 @@ struct CView {
     const int32_t *lev_task_ptr, *lev_ptask_ptr, *lev_sn_ptr;
     const uint8_t* lev_small;
     int64_t red_off;   // persistent kernels: reduction array offset in shared memory (elements)
+    int32_t pers_rb, pers_tstride;   // persistent forward: right-hand sides per matrix load, t_J stride
     int32_t stage_cap; // persistent kernels: stage buffer of each fused-level group (elements)
     // top zone
     int32_t nT, tf_parts, tb_parts;
@@ -789,10 +791,14 @@ __device__ __forceinline__ void grid_barrier(unsigned* bar, unsigned target, int
 // Shared memory of the persistent kernels (elements): t_J plus the reduction
 // array of a forward task, or the fused levels' buffers, whichever is larger.
 // The reduction array starts at a multiple of 32 elements.
-inline int64_t pers_red_off(int32_t max_n) { return ((int64_t)max_n + 31) / 32 * 32; }
+// t_J of rb right-hand sides (rb x max_n) before it; at least the backward's
+// 4 x 32 block of diagonal results, which shares the start of the buffer.
+inline int64_t pers_red_off(int32_t max_n, int32_t rb = 1) {
+    return std::max<int64_t>(((int64_t)rb * max_n + 31) / 32 * 32, 4 * 32);
+}
 // Each fused-level group also gets a stage buffer of stage_cap elements.
-inline size_t pers_smem_bytes(int32_t max_n, size_t elem, int32_t stage_cap) {
-    const int64_t task = pers_red_off(max_n) + kPersW * 33 + 32;
+inline size_t pers_smem_bytes(int32_t max_n, size_t elem, int32_t stage_cap, int32_t rb = 1) {
+    const int64_t task = pers_red_off(max_n, rb) + kPersW * 33 + 32;
     const int64_t small_fwd = kSmallG * ((int64_t)kSmallN + stage_cap),
                   small_bwd = kSmallG * ((int64_t)kSmallN + kSmallR + kSmallT + stage_cap);
     return (size_t)std::max({task, small_fwd, small_bwd}) * elem;
@@ -822,8 +828,8 @@ k_cfwd_persistent(const CView<T> cf, const T* g, int64_t ldg, T* xf, int32_t nrh
             any = nt + np > 0;
             for (int q = blockIdx.x; q < np + nt; q += gridDim.x) {
                 const bool pan = q < np;
-                cfwd_task_cta<T, kPersW>(cf, pan ? cf.ptasks[p0 + q] : cf.tasks[t0 + q - np], pan, sm, 0, 1, red, g, ldg,
-                                         xf, nrhs);
+                cfwd_task_cta<T, kPersW>(cf, pan ? cf.ptasks[p0 + q] : cf.tasks[t0 + q - np], pan, sm, cf.pers_tstride,
+                                         cf.pers_rb, red, g, ldg, xf, nrhs);
             }
         }
         if (any && --steps_left > 0) grid_barrier(cf.bar, ++round * gridDim.x, cf.err, cf.spin);
@@ -852,57 +858,122 @@ k_cbwd_persistent(const CView<T> cf, const T* yf, T* xf, T* y_dd, int64_t ldy, i
             const int t0 = cf.lev_task_ptr[l], nt = cf.lev_task_ptr[l + 1] - t0;
             any = nt > 0;
             for (int q = blockIdx.x; q < nt; q += gridDim.x)
-                cbwd_task_cta<T, kPersW, 8, 4>(cf, cf.tasks[t0 + q], sm, false, red, yf, xf, y_dd, ldy, nrhs);
+                cbwd_task_cta<T, kPersW, 8, 4>(cf, cf.tasks[t0 + q], sm, true, red, yf, xf, y_dd, ldy, nrhs);
         }
         if (any && --steps_left > 0) grid_barrier(cf.bar, ++round * gridDim.x, cf.err, cf.spin);
     }
 }
 
 // ------------------------------------------------------------------ K4
-// part[(j k + kk) G + b] = partial of U[:, kk] . w[:, j] over block b's rows
+// w' = cinv w + U (d o (U^T w)) (Eq. 4.7 in U-form), U s x k column-major, w s x nrhs
+// column-major (leading dimension s).  Each pass reads U once for the whole block
+// of right-hand sides:
+//   k_lr_vt     part[b][kk][j] = sum over block b's rows of U[i, kk] w[i, j]
+//   k_lr_vt_fin vk[kk + j k] = d[kk] * sum over b of part[b][kk][j]
+//   k_lr_update w[i, j] = cinv w[i, j] + sum over kk of U[i, kk] vk[kk + j k]
+// Every sum runs in a fixed order that depends on s and k only (block b owns rows
+// [b R, b R + R); one thread walks them in ascending order for one (kk, j)), so a
+// column gives the same bits alone and inside a block.
+constexpr int kLrK = 64;        // U columns per CTA (blockIdx.y groups larger k)
+constexpr int kLrJ = 32;        // right-hand sides per CTA (blockIdx.z groups more)
+constexpr int kLrCh = 32;       // rows per chunk staged in shared memory
+constexpr int kLrMaxBlocks = 1024;
+
+// row blocks of the first pass: enough to fill the SMs, a fixed function of s
+__host__ __device__ inline int lr_blocks(int32_t s) {
+    const int b = (s + 127) / 128;
+    return b < 1 ? 1 : (b > kLrMaxBlocks ? kLrMaxBlocks : b);
+}
+
+// thread t: U column kk0 + t % 64, right-hand sides j0 + 8 (t / 64) .. + 7
 template <typename T>
-__global__ void __launch_bounds__(kThreads)
-k_ut_partial(int32_t s, int32_t k, const T* __restrict__ U, const T* __restrict__ w, T* part) {
-    __shared__ T red[kThreads / 32];
-    const int kk = blockIdx.y, j = blockIdx.z;
-    const T* u = U + (int64_t)kk * s;
-    const T* x = w + (int64_t)j * s;
-    T acc = T(0);
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < s; i += (int64_t)gridDim.x * blockDim.x)
-        acc += u[i] * x[i];
-    acc = warp_sum(acc);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        T v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : T(0);
-        v = warp_sum(v);
-        if (threadIdx.x == 0) part[((int64_t)j * k + kk) * gridDim.x + blockIdx.x] = v;
+__global__ void __launch_bounds__(256)
+k_lr_vt(int32_t s, int32_t k, int32_t nrhs, const T* __restrict__ U, const T* __restrict__ w, T* part) {
+    __shared__ T su[kLrCh][kLrK + 1];
+    __shared__ T sw[kLrCh][kLrJ + 1];
+    const int kk0 = blockIdx.y * kLrK, j0 = blockIdx.z * kLrJ;
+    const int kn = min(kLrK, k - kk0), jn = min(kLrJ, nrhs - j0);
+    const int t = threadIdx.x;
+    const int R = (s + gridDim.x - 1) / gridDim.x;
+    const int r0 = blockIdx.x * R, r1 = min(s, r0 + R);
+    const int kk = t % kLrK, jg = t / kLrK;             // 4 groups of 8 right-hand sides
+    T acc[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[q] = T(0);
+    // loader mapping: row t % 32 of the chunk, columns t / 32 + 8 q
+    const int lr = t % kLrCh, lc = t / kLrCh;
+    T pu[8], pw[4];
+    auto fetch = [&](int c0) {
+        const int i = c0 + lr;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int col = lc + 8 * q;
+            pu[q] = (i < r1 && col < kn) ? U[i + (int64_t)(kk0 + col) * s] : T(0);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int col = lc + 8 * q;
+            pw[q] = (i < r1 && col < jn) ? w[i + (int64_t)(j0 + col) * s] : T(0);
+        }
+    };
+    if (r0 < r1) fetch(r0);
+    for (int c0 = r0; c0 < r1; c0 += kLrCh) {
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < 8; ++q) su[lr][lc + 8 * q] = pu[q];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) sw[lr][lc + 8 * q] = pw[q];
+        __syncthreads();
+        if (c0 + kLrCh < r1) fetch(c0 + kLrCh);        // next chunk's loads overlap this chunk's sums
+        const int rows = min(kLrCh, r1 - c0);
+        if (kk < kn && 8 * jg < jn) {
+            for (int i = 0; i < rows; ++i) {
+                const T u = su[i][kk];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) acc[q] = fma(u, sw[i][8 * jg + q], acc[q]);
+            }
+        }
+    }
+    if (kk < kn) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int j = 8 * jg + q;
+            if (j < jn) part[((int64_t)blockIdx.x * k + kk0 + kk) * nrhs + j0 + j] = acc[q];
+        }
     }
 }
 
-// vk[kk + j k] = d[kk] * sum_b part[...]   (one warp per (kk, j))
 template <typename T>
-__global__ void k_ut_final(int32_t k, int32_t nrhs, int32_t G, const T* part, const T* __restrict__ dvec,
-                           T* vk) {
-    const int id = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+__global__ void k_lr_vt_fin(int32_t k, int32_t nrhs, int32_t G, const T* __restrict__ part,
+                            const T* __restrict__ dvec, T* vk) {
+    const int id = blockIdx.x * blockDim.x + threadIdx.x;
     if (id >= k * nrhs) return;
-    const T* pp = part + (int64_t)id * G;
+    const int kk = id % k, j = id / k;
     T acc = T(0);
-    for (int b = lane; b < G; b += 32) acc += pp[b];
-    acc = warp_sum(acc);
-    if (lane == 0) vk[id] = dvec[id % k] * acc;
+    for (int b = 0; b < G; ++b) acc += part[((int64_t)b * k + kk) * nrhs + j];
+    vk[kk + (int64_t)j * k] = dvec[kk] * acc;
 }
 
-template <typename T>
-__global__ void k_lowrank_update(int32_t s, int32_t k, int32_t nrhs, const T* __restrict__ U, const T* vk,
-                                 T cinv, T* w) {
-    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (int64_t)s * nrhs) return;
-    const int32_t i = (int32_t)(idx % s), j = (int32_t)(idx / s);
-    const T* v = vk + (int64_t)j * k;
-    T acc = cinv * w[i + (int64_t)j * s];
-    for (int kk = 0; kk < k; ++kk) acc += U[i + (int64_t)kk * s] * v[kk];
-    w[i + (int64_t)j * s] = acc;
+// thread = row i, JG right-hand sides (a block's columns j0 .. j0 + JG - 1 of nrhs)
+template <typename T, int JG>
+__global__ void __launch_bounds__(256)
+k_lr_update(int32_t s, int32_t k, int32_t nrhs, const T* __restrict__ U, const T* __restrict__ vk, T cinv, T* w) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= s) return;
+    const int j0 = blockIdx.y * JG;
+    const int jn = min(JG, nrhs - j0);
+    T acc[JG];
+#pragma unroll
+    for (int q = 0; q < JG; ++q) acc[q] = q < jn ? cinv * w[i + (int64_t)(j0 + q) * s] : T(0);
+    for (int kk = 0; kk < k; ++kk) {
+        const T u = U[i + (int64_t)kk * s];
+#pragma unroll
+        for (int q = 0; q < JG; ++q)
+            if (q < jn) acc[q] = fma(u, __ldg(&vk[kk + (int64_t)(j0 + q) * k]), acc[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < JG; ++q)
+        if (q < jn) w[i + (int64_t)(j0 + q) * s] = acc[q];
 }
 
 // ------------------------------------------------------------------ helpers
@@ -1171,6 +1242,8 @@ CView<T> make_view(const DevCFactor<T>& cf, int32_t nsteps) {
     v.lev_sn_ptr = cf.d_lev_sn_ptr;
     v.lev_small = cf.d_lev_small;
     v.red_off = pers_red_off(cf.max_n);
+    v.pers_rb = 1;
+    v.pers_tstride = 0;
     v.stage_cap = cf.stage_cap;
     v.nT = cf.nT;
     v.tf_parts = cf.tf_parts;
@@ -1225,10 +1298,15 @@ template <typename T>
 cudaError_t launch_c_forward(const DevCFactor<T>& cf, const T* g_dd, int64_t ldg, T* xf, int32_t nrhs,
                              cudaStream_t st) {
     if (nrhs > cf.ws_cols) return cudaErrorInvalidValue;
-    const CView<T> v = make_view(cf, cf.nsteps_fwd);
+    CView<T> v = make_view(cf, cf.nsteps_fwd);
     bool levels_done = cf.nsteps_fwd == 0;
     if (!levels_done && !cf.per_level) {
-        const size_t smem = pers_smem_bytes(cf.max_n, sizeof(T), cf.stage_cap);
+        // blocks of four right-hand sides share each matrix load when t_J of four fits
+        const int32_t rb = (nrhs >= 4 && pers_smem_bytes(cf.max_n, sizeof(T), cf.stage_cap, 4) <= kLevSmem) ? 4 : 1;
+        v.pers_rb = rb;
+        v.pers_tstride = cf.max_n;
+        v.red_off = pers_red_off(cf.max_n, rb);
+        const size_t smem = pers_smem_bytes(cf.max_n, sizeof(T), cf.stage_cap, rb);
         const int grid = pers_grid(k_cfwd_persistent<T>, smem, cf.max_cta_tasks);
         if (grid > 0) {
             const cudaError_t e = launch_persistent(k_cfwd_persistent<T>, grid, smem, cf.bar, st, v, g_dd, ldg, xf, nrhs);
@@ -1307,17 +1385,31 @@ cudaError_t launch_c_backward(const DevCFactor<T>& cf, const T* yf, T* xf, T* y_
 template <typename T>
 cudaError_t launch_lowrank(const DevOperator<T>& op, int32_t s, int32_t k, T* w, int32_t nrhs, cudaStream_t st) {
     if (s == 0) return cudaSuccess;
-    if (k > 0) {
-        const int G = kRedBlocks;
-        k_ut_partial<T><<<dim3(G, k, nrhs), kThreads, 0, st>>>(s, k, op.U, w, op.part);
-        counted();
-        k_ut_final<T><<<blocks_for((int64_t)k * nrhs * 32), kThreads, 0, st>>>(k, nrhs, G, op.part, op.dvec, op.vk);
-        counted();
+    if constexpr (std::is_same<T, float>::value) {
+        if (lowrank_tc_usable(op, k, nrhs)) return launch_lowrank_tc(op, s, k, w, nrhs, st);
     }
-    k_lowrank_update<T><<<blocks_for((int64_t)s * nrhs), kThreads, 0, st>>>(s, k, nrhs, op.U, op.vk, op.cinv, w);
+    if (k > 0) {
+        const int G = lr_blocks(s);
+        k_lr_vt<T><<<dim3(G, (k + kLrK - 1) / kLrK, (nrhs + kLrJ - 1) / kLrJ), 256, 0, st>>>(s, k, nrhs, op.U, w,
+                                                                                           op.part);
+        k_lr_vt_fin<T><<<blocks_for((int64_t)k * nrhs), kThreads, 0, st>>>(k, nrhs, G, op.part, op.dvec, op.vk);
+        counted(2);
+    }
+    const dim3 grid((unsigned)((s + 255) / 256));
+    // every column sees the same multiply-adds in the same order whatever JG is
+    if (nrhs == 1) {
+        k_lr_update<T, 1><<<grid, 256, 0, st>>>(s, k, nrhs, op.U, op.vk, op.cinv, w);
+    } else if (nrhs <= 8) {
+        k_lr_update<T, 8><<<grid, 256, 0, st>>>(s, k, nrhs, op.U, op.vk, op.cinv, w);
+    } else {
+        k_lr_update<T, 32><<<dim3(grid.x, (nrhs + 31) / 32), 256, 0, st>>>(s, k, nrhs, op.U, op.vk, op.cinv, w);
+    }
     counted();
     return cudaGetLastError();
 }
+
+// elements of the first pass's partial sums for rank k and nrhs columns
+int64_t lowrank_part_elems(int32_t s, int32_t k, int32_t nrhs) { return (int64_t)lr_blocks(s) * k * nrhs; }
 
 template <typename TS, typename TD>
 cudaError_t launch_convert(int64_t rows, int32_t cols, const TS* src, int64_t lds, TD* dst, int64_t ldd,

@@ -86,7 +86,7 @@ size_t carve(slr_handle h, DevOperator<T>& op, int32_t nrhs, unsigned char* base
     }
     op.cf.bar = c.take<unsigned>(1);          // the persistent C solves' grid barrier counter
     op.vk = c.take<T>(k * nrhs);
-    op.part = c.take<T>(k * nrhs * kRedBlocks);
+    op.part = c.take<T>(lowrank_part_elems((int32_t)s, (int32_t)k, nrhs));
     if constexpr (!std::is_same<T, double>::value) {
         op.wr = c.take<T>(n * nrhs);
         op.wz = c.take<T>(n * nrhs);

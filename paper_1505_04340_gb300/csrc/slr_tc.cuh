@@ -1,0 +1,136 @@
+// Fifth-generation tensor-core building blocks for sm_103a, as inline PTX:
+// tensor-memory (TMEM) allocation, shared-memory matrix descriptors, the
+// instruction descriptor, tcgen05.mma with an mbarrier commit, and tcgen05.ld
+// of the FP32 accumulator.  Only single-CTA MMAs (cta_group::1), M = 128.
+//
+// Operand layout ("K-major, no swizzle"): an M x K (or N x K) tile is a grid of
+// core matrices of 8 rows x 16 bytes; a core matrix is 128 contiguous bytes (its
+// 8 rows 16 bytes apart).  Core matrices adjacent along K are LBO = 128 bytes
+// apart, the 8-row groups SBO = 8 * kc * E bytes apart (kc elements of E bytes
+// per row of the tile), so row r, element q of a row sits at byte
+//   (r / 8) SBO + (q / (16 / E)) 128 + (r % 8) 16 + (q % (16 / E)) E.
+// One MMA consumes K = 32 bytes of each row (8 TF32 or 16 BF16 elements), i.e.
+// two core matrices along K; step s of a tile starts 256 s bytes in.
+#pragma once
+#include <cstdint>
+
+namespace slr {
+namespace tc {
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// byte offset of (row r, element q) in a K-major tile with kc elements per row
+template <int E>
+__device__ __forceinline__ uint32_t kmajor_off(int r, int q, int kc) {
+    constexpr int per = 16 / E;
+    return (uint32_t)((r >> 3) * (8 * kc * E) + (q / per) * 128 + (r & 7) * 16 + (q % per) * E);
+}
+
+// shared-memory matrix descriptor (tcgen05 format: version 1 in bits 46-47,
+// no swizzle, base offset 0); addresses and offsets in units of 16 bytes
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// instruction descriptor: FP32 accumulator, A and B K-major, M x N
+// ab = 2 (TF32, kind::tf32) or 1 (BF16, kind::f16)
+__host__ __device__ constexpr uint32_t instr_desc(int ab, int M, int N) {
+    return (1u << 4) | ((uint32_t)ab << 7) | ((uint32_t)ab << 10) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
+}
+
+// TMEM: one warp allocates ncols (a power of two >= 32) columns, writing the base
+// address to shared memory; the same warp frees them
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(dst)),
+                 "r"(ncols)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// D[tmem] (+)= A[smem] B[smem]^T, issued by one thread
+template <int AB>
+__device__ __forceinline__ void mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, bool accum) {
+    if constexpr (AB == 2) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"((uint32_t)accum)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"((uint32_t)accum)
+            : "memory");
+    }
+}
+
+// the MMAs issued so far by this thread arrive on the mbarrier when they complete
+__device__ __forceinline__ void commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// generic-proxy stores to shared memory become visible to the tensor core's reads
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait for phase `parity` of bar; false once `spin` polls have passed
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long long spin) {
+    for (long long it = 0; !mbar_try_wait(bar, parity); ++it)
+        if (it >= spin) return false;
+    return true;
+}
+
+// 32 consecutive 32-bit columns of the warp's 32 TMEM lanes (lane quarter of
+// warp % 4): thread t gets lane (32 (warp % 4) + t), columns col .. col + 31
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// FP32 -> TF32 (round to nearest, ties away), kept in an FP32 container
+__device__ __forceinline__ float to_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+}  // namespace tc
+}  // namespace slr

@@ -115,7 +115,8 @@ BAD_OPTIONS = [{"band_split": 3}, {"host_loop": 2}, {"band_slots": 1}, {"band_sl
                {"band_threads": 1024}, {"c_levels_only": 2}, {"c_levels_only": -1}, {"band_factor_host": 2},
                {"indefinite": 2}, {"band_order": 4}, {"band_order": -1}, {"u_dtype": 3}, {"u_dtype": -1},
                {"u_dtype": 1},                     # a tensor-core dtype needs the mixed path
-               {"spin_limit": -5}, {0: 1}, {7: 1}]
+               {"spin_limit": -5}, {"band_mma": 3}, {"band_mma": 1},   # tensor cores need the mixed path
+               {0: 1}, {6: 1}]
 
 
 @pytest.mark.parametrize("fields", BAD_OPTIONS)
