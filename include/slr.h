@@ -225,6 +225,32 @@ slr_status slr_gmres_solve(slr_handle h, const double* b_dev, double* x_dev, int
                            double tol, int32_t maxit, int32_t restart, void* stream, int32_t* iters_out,
                            double* relres_out);
 
+/* Continuous batching at iteration granularity: the handle's nrhs_max CG columns
+ * serve as "slots", each an independent run of the CG of Section 6 (x_0 = 0,
+ * stop when ||r|| <= tol ||b|| or after maxit iterations), which can be started
+ * while other slots are mid-solve.  A slot runs exactly the arithmetic of a
+ * column of slr_pcg_solve, so its answer does not depend on which other slots
+ * ran beside it.  The slots share the handle's CG workspaces with slr_pcg_solve
+ * and slr_gmres_solve: a call of either discards every slot's state.
+ *
+ * slr_cg_slot_start: load b_dev (n FP64, original order) into slot `slot`
+ *   (0 <= slot < nrhs_max) with its own tol and maxit; asynchronous on stream.
+ * slr_cg_advance: run `iters` CG iterations over slots 0 .. width-1 (finished or
+ *   unused slots cost an apply column but change nothing), then report per slot
+ *   active_out (1: still iterating), iters_out (its iterations so far),
+ *   relres_out (||r|| / ||b||, recurrence residual) and status_out (1: met its
+ *   tolerance, 2: breakdown p^T A p <= 0, 0: still running or stopped at maxit);
+ *   any output may be NULL; synchronises stream.
+ * slr_cg_slot_result: x of the slot (n FP64, original order) into x_dev;
+ *   asynchronous on stream.
+ * Errors: INVALID_ARG (bad slot, width, pointer, tol or maxit; advance before any
+ * start), TIMEOUT (a bounded device wait expired), CUDA. */
+slr_status slr_cg_slot_start(slr_handle h, int32_t slot, const double* b_dev, double tol, int32_t maxit,
+                             void* stream);
+slr_status slr_cg_advance(slr_handle h, int32_t iters, int32_t width, void* stream, int32_t* active_out,
+                          int32_t* iters_out, double* relres_out, int32_t* status_out);
+slr_status slr_cg_slot_result(slr_handle h, int32_t slot, double* x_dev, void* stream);
+
 /* t = B^{-1} f for the interior block (Section 5.2), DD interior order,
  * f_dev/t_dev: n_interior x nrhs FP64, leading dimension ld.  May alias. */
 slr_status slr_bsolve(slr_handle h, const double* f_dev, double* t_dev, int32_t nrhs, int32_t ld,

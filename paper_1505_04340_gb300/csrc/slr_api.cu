@@ -1394,6 +1394,7 @@ slr_status slr_pcg_solve(slr_handle h, const double* b, double* x, int32_t nrhs,
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t nn = n;
     // start: r = P b (DD order), x = 0, b.b, flags, z = M^{-1} r, rho = r.z, p = z
+    h->slots_live = false;
     CS(clear_status(h, st));
     CK(launch_permute(n, nrhs, h->perm, b, ld, h->pr, nn, true, st));
     CK(cudaMemsetAsync(h->px, 0, sizeof(double) * nn * nrhs, st));
@@ -1453,6 +1454,7 @@ slr_status slr_gmres_solve(slr_handle h, const double* b, double* x, int32_t nrh
     DeviceGuard g(h->device);
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t nn = n;
+    h->slots_live = false;
     CS(clear_status(h, st));
     CK(launch_permute(n, nrhs, h->perm, b, ld, h->pr, nn, true, st));   // b in DD order
     slr_status ret = SLR_OK;
@@ -1468,6 +1470,72 @@ slr_status slr_gmres_solve(slr_handle h, const double* b, double* x, int32_t nrh
     CS(read_status(h, status_word(h), st));
     if (ret == SLR_ERR_NOT_CONVERGED) set_error("GMRES reached maxit");
     return ret;
+}
+
+slr_status slr_cg_slot_start(slr_handle h, int32_t slot, const double* b, double tol, int32_t maxit, void* stream) {
+    CS(check_handle(h));
+    const int32_t n = h->hs.n;
+    if (slot < 0 || slot >= h->opts.nrhs_max || !b || maxit < 0 || !(tol >= 0.0)) {
+        set_error("slr_cg_slot_start: bad slot, pointer, tol or maxit");
+        return SLR_ERR_INVALID_ARG;
+    }
+    DeviceGuard g(h->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!h->slot_ctl) CS(dalloc(h, &h->slot_ctl, (size_t)2 * h->opts.nrhs_max));
+    if (!h->slots_live) {       // the workspaces last served slr_pcg_solve / slr_gmres_solve: every slot idle
+        CK(cudaMemsetAsync(h->iflags, 0, sizeof(int32_t) * (4 * (size_t)h->opts.nrhs_max + 4), st));
+        h->slots_live = true;
+    }
+    const int64_t nn = n, off = (int64_t)slot * nn;
+    CK(launch_permute(n, 1, h->perm, b, nn, h->pr + off, nn, true, st));          // r = P b
+    CK(cudaMemsetAsync(h->px + off, 0, sizeof(double) * nn, st));                 // x = 0
+    CK(cudaMemsetAsync(h->pp + off, 0, sizeof(double) * nn, st));                 // p = 0
+    CK(cudaMemsetAsync(h->pz + off, 0, sizeof(double) * nn, st));                 // z = 0 (z_old of the first step)
+    CK(launch_dots(nn, 1, h->pr + off, nn, h->pr + off, nn, h->dpart, h->scal + 8 * slot + 4, 8, st));   // b.b
+    CK(launch_cg_slot_init(slot, tol, maxit, h->scal, h->iflags, h->slot_ctl, st));
+    return SLR_OK;
+}
+
+slr_status slr_cg_advance(slr_handle h, int32_t iters, int32_t width, void* stream, int32_t* active_out,
+                          int32_t* iters_out, double* relres_out, int32_t* status_out) {
+    CS(check_handle(h));
+    if (iters < 0 || width < 1 || width > h->opts.nrhs_max || !h->slots_live) {
+        set_error("slr_cg_advance: bad iters or width, or no slot was started");
+        return SLR_ERR_INVALID_ARG;
+    }
+    DeviceGuard g(h->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    CS(clear_status(h, st));
+    for (int32_t it = 0; it < iters; ++it) {
+        CS(pcg_update_part(h, width, st));
+        CS(pcg_test_part(h, width, st));
+        CK(launch_cg_slot_check(width, 4 * h->opts.nrhs_max, h->scal, h->iflags, h->slot_ctl, st));
+    }
+    std::vector<double> sc(8 * (size_t)width);
+    std::vector<int32_t> fl(4 * (size_t)width);
+    CK(cudaMemcpyAsync(sc.data(), h->scal, sizeof(double) * sc.size(), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(fl.data(), h->iflags, sizeof(int32_t) * fl.size(), cudaMemcpyDeviceToHost, st));
+    CS(read_status(h, status_word(h), st));
+    for (int32_t j = 0; j < width; ++j) {
+        if (active_out) active_out[j] = fl[4 * j];
+        if (iters_out) iters_out[j] = fl[4 * j + 1];
+        if (status_out) status_out[j] = fl[4 * j + 2];
+        const double bb = sc[8 * j + 4];
+        if (relres_out) relres_out[j] = bb > 0 ? std::sqrt(std::max(sc[8 * j + 3], 0.0) / bb) : 0.0;
+    }
+    return SLR_OK;
+}
+
+slr_status slr_cg_slot_result(slr_handle h, int32_t slot, double* x, void* stream) {
+    CS(check_handle(h));
+    if (slot < 0 || slot >= h->opts.nrhs_max || !x) {
+        set_error("slr_cg_slot_result: bad slot or pointer");
+        return SLR_ERR_INVALID_ARG;
+    }
+    DeviceGuard g(h->device);
+    const int64_t nn = h->hs.n;
+    CK(launch_permute(h->hs.n, 1, h->perm, h->px + (int64_t)slot * nn, nn, x, nn, false, (cudaStream_t)stream));
+    return SLR_OK;
 }
 
 slr_status slr_set_lowrank(slr_handle h, int32_t k, const double* Z, const double* lam, double theta, void* stream) {

@@ -115,6 +115,8 @@ struct slr_handle_s {
     double *dpart = nullptr;         // reduction partials
     int32_t *iflags = nullptr;       // per-column status words
     double* ctl = nullptr;           // PCG graph controls: tol^2, maxit
+    double* slot_ctl = nullptr;      // slot CG: tol^2 and maxit of each slot (2 x nrhs_max)
+    bool slots_live = false;         // the CG workspaces hold slot state (cleared by pcg / gmres)
     struct PcgGraph {
         int32_t nrhs = 0;
         cudaGraphExec_t exec = nullptr;
@@ -249,5 +251,10 @@ cudaError_t launch_pcg_check_graph(int32_t nrhs, const double* scal, int32_t* fl
                                    cudaStream_t st);
 cudaError_t launch_pcg_update_p(int32_t n, int32_t nrhs, double* p, const double* z, const double* scal,
                                 const int32_t* flags, cudaStream_t st);
+// slot CG (continuous batching, slr_cg_*): start slot j; per-slot test after an iteration
+cudaError_t launch_cg_slot_init(int32_t j, double tol, int32_t maxit, double* scal, int32_t* flags, double* ctl,
+                               cudaStream_t st);
+cudaError_t launch_cg_slot_check(int32_t width, int32_t count_at, const double* scal, int32_t* flags,
+                                 const double* ctl, cudaStream_t st);
 
 }  // namespace slr

@@ -1149,6 +1149,46 @@ __global__ void k_pcg_update_p(int32_t n, int32_t nrhs, double* p, const double*
     p[t] = z[t] + scal[8 * j + 5] * p[t];
 }
 
+// Slot CG (continuous batching): slot j starts with p = 0, z = 0 and a unit
+// placeholder for rho, so the preconditioner update of its first iteration gives
+// p = z exactly and every slot runs the same kernels at every iteration.
+// ctl[2 j] = tol^2, ctl[2 j + 1] = maxit of slot j.
+__global__ void k_cg_slot_init(int32_t j, double tol, int32_t maxit, double* scal, int32_t* flags, double* ctl) {
+    if (threadIdx.x != 0) return;
+    double* sc = scal + 8 * j;
+    const bool zero = !(sc[4] > 0.0);
+    sc[0] = 1.0;
+    sc[3] = sc[4];
+    flags[4 * j] = zero ? 0 : 1;
+    flags[4 * j + 1] = 0;
+    flags[4 * j + 2] = zero ? 1 : 0;
+    flags[4 * j + 3] = 0;
+    ctl[2 * j] = tol * tol;
+    ctl[2 * j + 1] = (double)maxit;
+}
+
+// after an iteration's test part: each active slot counts the iteration and stops
+// when its residual meets its tolerance (status 1) or at its own maxit (status 0)
+__global__ void k_cg_slot_check(int32_t width, int32_t count_at, const double* scal, int32_t* flags,
+                                const double* ctl) {
+    if (threadIdx.x != 0) return;
+    int32_t active = 0;
+    for (int j = 0; j < width; ++j) {
+        if (!flags[4 * j]) continue;
+        const double* sc = scal + 8 * j;
+        const int32_t it = ++flags[4 * j + 1];
+        if (sc[3] <= ctl[2 * j] * sc[4]) {
+            flags[4 * j] = 0;
+            flags[4 * j + 2] = 1;
+        } else if (it >= (int32_t)ctl[2 * j + 1]) {
+            flags[4 * j] = 0;
+        } else {
+            ++active;
+        }
+    }
+    flags[count_at] = active;                  // past every slot's words
+}
+
 inline unsigned blocks_for(int64_t n, int t = kThreads) { return (unsigned)((n + t - 1) / t); }
 
 // every kernel launch of the library goes through this counter
@@ -1486,6 +1526,18 @@ cudaError_t launch_pcg_update_xr(int32_t n, int32_t nrhs, double* x, double* r, 
 }
 cudaError_t launch_pcg_check(int32_t nrhs, double* scal, int32_t* flags, int32_t it, double tol, cudaStream_t st) {
     k_pcg_check<<<1, 32, 0, st>>>(nrhs, scal, flags, it, tol);
+    counted();
+    return cudaGetLastError();
+}
+cudaError_t launch_cg_slot_init(int32_t j, double tol, int32_t maxit, double* scal, int32_t* flags, double* ctl,
+                               cudaStream_t st) {
+    k_cg_slot_init<<<1, 32, 0, st>>>(j, tol, maxit, scal, flags, ctl);
+    counted();
+    return cudaGetLastError();
+}
+cudaError_t launch_cg_slot_check(int32_t width, int32_t count_at, const double* scal, int32_t* flags,
+                                 const double* ctl, cudaStream_t st) {
+    k_cg_slot_check<<<1, 32, 0, st>>>(width, count_at, scal, flags, ctl);
     counted();
     return cudaGetLastError();
 }

@@ -4,17 +4,22 @@ Requests (a matrix id and 1..nrhs_max right-hand sides) arrive over time.  The
 server keeps one SLR handle per matrix resident on the device: it is set up on
 the first request for that matrix, admitted only while free device memory (and
 the server's own capacity, if one is given) covers it, and least recently used
-idle handles are evicted to make room.  Every pending request of a matrix is
-packed into the columns of one multi-RHS SLR-PCG solve; solves of different
-matrices run at the same time, each on its own CUDA stream in its own worker
-thread (the library releases the interpreter lock while it runs).  A request
-that arrives while its matrix is being solved joins the next batch of that
-matrix as soon as the running solve returns; one that arrives for an idle
-matrix starts as soon as a worker slot is free.
+idle handles are evicted to make room.
 
-Each column of a multi-RHS solve is an independent CG run with its own scalars,
-convergence mask and fixed-order reductions, so a request's answer does not
-depend on what it was batched or overlapped with.
+Batching is continuous at iteration granularity.  A handle's nrhs_max CG
+columns are slots (``slr_cg_*``): a worker per active matrix starts the columns
+of waiting requests in free slots, advances every occupied slot a few CG
+iterations (``iters_per_step``), collects the columns that have converged,
+frees their slots and starts waiting columns in them, and so on until the
+matrix has no work.  A request that arrives while its matrix is being solved
+therefore joins at the next iteration boundary, and a converged column's slot
+is refilled without waiting for the rest of its batch.  Workers of different
+matrices run at once, each on its own CUDA stream in its own thread (the
+library releases the interpreter lock while it runs).
+
+Each slot is an independent CG run with its own scalars, convergence mask and
+fixed-order reductions, so a request's answer does not depend on what it ran
+beside.
 
 The solver is the C library (``slr.SLR``); this module only schedules.
 """
@@ -57,9 +62,9 @@ class Request:
     relres: np.ndarray | None = None
     status: int = -1               # slr_status of the solve, -1 = not served
     error: str = ""
-    start: float = 0.0             # when its solve began
-    done: float = 0.0              # when its solution was back on the host
-    batch: int = 0                 # columns in the solve it was part of
+    start: float = 0.0             # when its first column started
+    done: float = 0.0              # when its last column was back on the host
+    batch: int = 0                 # slots occupied on its matrix when it started
     cold: bool = False             # its matrix was set up for it
 
     @property
@@ -71,7 +76,7 @@ class Request:
         return self.done - self.arrival
 
 
-class _Slot:
+class Resident:
     """A resident handle and its stream."""
 
     def __init__(self, handle, stream, footprint):
@@ -82,7 +87,8 @@ class _Slot:
 
 
 class CudaBackend:
-    """Handles of the SLR library on the current GPU, one CUDA stream each."""
+    """Handles of the SLR library on the current GPU, one CUDA stream each; the CG
+    slots of a handle through slr_cg_slot_start / slr_cg_advance / slr_cg_slot_result."""
 
     def __init__(self, precision="mixed", nrhs_max=8, setup_kw=None):
         import torch
@@ -99,19 +105,33 @@ class CudaBackend:
                 lanczos_steps=spec.lanczos_steps, precision=self.precision, nrhs_max=self.nrhs_max,
                 flexible_cg=(self.precision == "mixed"), stream=stream, **self.setup_kw)
         stream.synchronize()
-        return _Slot(h, stream, h.info["device_bytes"])
+        return Resident(h, stream, h.info["device_bytes"])
 
-    def solve(self, slot, B, tol, maxit):
-        """B: (n, r) float64 host array -> (X host array, iterations, relres, status)."""
+    def start(self, res, slots, B, tol, maxit):
+        """Start the columns B[:, i] (host, original order) in the given slots; returns
+        the device copy, which the caller keeps until the next advance has run."""
         torch = self.torch
-        with torch.cuda.stream(slot.stream):
-            bd = torch.from_numpy(B).pin_memory().to("cuda", non_blocking=True)
-            x, its, rel, st = slot.handle.pcg(bd, tol=tol, maxit=maxit, stream=slot.stream, check=False)
-            xh = x.cpu().numpy()                   # waits for this stream only
-        return xh, its, rel, st
+        with torch.cuda.stream(res.stream):
+            bd = torch.from_numpy(np.ascontiguousarray(B.T)).pin_memory().to("cuda", non_blocking=True)
+            for i, j in enumerate(slots):
+                res.handle.cg_start(j, bd[i], tol=tol, maxit=maxit, stream=res.stream)
+        return bd
 
-    def release(self, slot):
-        slot.handle.close()
+    def advance(self, res, iters, width):
+        """(active, iterations, relres, status) of slots 0 .. width-1 after `iters` iterations."""
+        return res.handle.cg_advance(iters, width, stream=res.stream)
+
+    def results(self, res, slots):
+        """x of the given slots as an (n, len(slots)) host array."""
+        torch = self.torch
+        with torch.cuda.stream(res.stream):
+            X = torch.empty((len(slots), res.handle.n), dtype=torch.float64, device="cuda")
+            for i, j in enumerate(slots):
+                res.handle.cg_result(j, out=X[i], stream=res.stream)
+            return X.cpu().numpy().T                 # waits for this stream only
+
+    def release(self, res):
+        res.handle.close()
 
 
 class SolveServer:
@@ -119,18 +139,20 @@ class SolveServer:
 
     matrices: key -> MatrixSpec.
     precision, nrhs_max, tol, maxit: for every handle and solve ("mixed" uses
-        flexible CG around the FP32 apply).
-    backend: what sets up handles and runs solves (default: CudaBackend).
-    max_concurrent: solves (worker threads, streams) in flight at once.
+        flexible CG around the FP32 apply); nrhs_max is the number of CG slots.
+    backend: what sets up handles and runs the slots (default: CudaBackend).
+    max_concurrent: matrices (worker threads, streams) served at once.
     reserve_bytes: device memory left free when a new handle is admitted.
     capacity_bytes: device memory all resident handles may hold (None: no cap
         beyond free memory).
     log: a text stream that receives one line per failed setup or solve.
+    iters_per_step: CG iterations every occupied slot runs between two looks at
+        the slots (completions, admissions).
     """
 
     def __init__(self, matrices: dict, precision="mixed", nrhs_max=8, tol=1e-8, maxit=300,
                  max_concurrent=4, reserve_bytes=1 << 30, capacity_bytes=None, setup_kw=None, backend=None,
-                 log=None):
+                 log=None, iters_per_step=4):
         self.backend = backend or CudaBackend(precision, nrhs_max, setup_kw)
         self.matrices = matrices
         self.precision = precision
@@ -140,14 +162,16 @@ class SolveServer:
         self.reserve = int(reserve_bytes)
         self.capacity = capacity_bytes
         self.log = log
+        self.iters_per_step = int(iters_per_step)
         self.errors: list = []           # (seconds, key, message)
-        self.slots: dict = {}            # key -> _Slot (resident handles)
+        self.slots: dict = {}            # key -> Resident (resident handles)
         self.footprints: dict = {}       # key -> device bytes seen at its last setup
         self.claimed: dict = {}          # key -> bytes admitted for a setup in progress
         self.cv = threading.Condition()
         self.setups = 0
         self.evictions = 0
-        self.batches = 0
+        self.batches = 0                 # admissions of waiting requests into free slots
+        self.steps = 0                   # advances of a matrix's slots
         self.max_inflight = 0
 
     # ------------------------------------------------------------ residency
@@ -186,40 +210,79 @@ class SolveServer:
             self.evictions += 1
 
     # ------------------------------------------------------------ solving
-    def _solve(self, key, slot, reqs, cold):
-        n = self.matrices[key].n
-        B = np.ascontiguousarray(np.concatenate([r.b.reshape(n, -1) for r in reqs], axis=1))
-        start = time.perf_counter() - self.t0
-        xh, its, rel, st = self.backend.solve(slot, B, self.tol, self.maxit)
-        done = time.perf_counter() - self.t0
-        c = 0
-        for r in reqs:
-            w = r.ncols
-            r.x = xh[:, c:c + w].reshape(r.b.shape).copy()
-            r.iterations, r.relres = its[c:c + w].copy(), rel[c:c + w].copy()
-            # the library's status covers the whole block: a request whose own
-            # columns all met the tolerance has converged
-            r.status = 0 if st == 0 or bool(np.all(r.relres <= self.tol)) else int(st)
-            r.start, r.done, r.batch, r.cold = start, done, B.shape[1], cold
-            c += w
-
-    def _take_batch(self, key):
+    def _take_columns(self, key, free):
+        """Waiting requests of `key` whose columns fit the free slots, oldest first
+        (called with the lock held); each with the slots it gets."""
         q = self.pending.get(key)
-        batch, cols = [], 0
-        while q and (not batch or cols + q[0].ncols <= self.nrhs_max):
+        taken = []
+        while q and q[0].ncols <= len(free):
             r = q.popleft()
-            batch.append(r)
-            cols += r.ncols
-        return batch
+            taken.append((r, [free.pop(0) for _ in range(r.ncols)]))
+        return taken
+
+    def _run_matrix(self, key, res, cold, started):
+        """The slot loop of one matrix: admit, advance, collect, until it has no work."""
+        n = self.matrices[key].n
+        free = list(range(self.nrhs_max))
+        owner = {}                       # slot -> (request, column)
+        left = {}                        # rid -> columns not finished
+        keep = []                        # device copies of started columns, until the next advance
+        while True:
+            with self.cv:
+                taken = self._take_columns(key, free)
+                if taken:
+                    self.batches += 1
+            if taken:
+                now = time.perf_counter() - self.t0
+                for r, sl in taken:
+                    started.append(r)
+                    keep.append(self.backend.start(res, sl, r.b.reshape(n, -1), self.tol, self.maxit))
+                    for c, j in enumerate(sl):
+                        owner[j] = (r, c)
+                    left[r.rid] = r.ncols
+                    r.x = np.zeros(r.b.shape)
+                    r.iterations = np.zeros(r.ncols, np.int32)
+                    r.relres = np.zeros(r.ncols)
+                    r.status, r.start, r.cold = 0, now, cold
+                for r, _ in taken:
+                    r.batch = len(owner)
+                cold = False
+            if not owner:
+                return
+            width = max(owner) + 1
+            act, its, rel, sts = self.backend.advance(res, self.iters_per_step, width)
+            self.steps += 1
+            keep.clear()
+            done = sorted(j for j in owner if not act[j])
+            if done:
+                X = self.backend.results(res, done)
+                t = time.perf_counter() - self.t0
+                for i, j in enumerate(done):
+                    r, c = owner.pop(j)
+                    free.append(j)
+                    if r.b.ndim == 1:
+                        r.x[:] = X[:, i]
+                    else:
+                        r.x[:, c] = X[:, i]
+                    r.iterations[c], r.relres[c] = its[j], rel[j]
+                    if sts[j] == 2:
+                        r.status = 6                       # SLR_ERR_BREAKDOWN
+                    elif sts[j] != 1 and r.status == 0:
+                        r.status = 5                       # SLR_ERR_NOT_CONVERGED (maxit)
+                    left[r.rid] -= 1
+                    if left[r.rid] == 0:
+                        r.done = t
+                free.sort()
+            res.last_used = time.perf_counter()
 
     def _worker(self, key):
-        cold = False
-        batch = []
+        started = []
         try:
             with self.cv:
                 slot = self.slots.get(key)
                 while slot is None and not self._admit(key):
                     self.cv.wait(0.05)
+            cold = False
             if slot is None:
                 try:
                     slot = self.backend.setup(self.matrices[key])
@@ -231,25 +294,17 @@ class SolveServer:
                     self.slots[key] = slot
                     self.footprints[key] = slot.footprint
                     self.setups += 1
-            while True:
-                with self.cv:
-                    batch = self._take_batch(key)
-                    if not batch:
-                        break
-                    self.batches += 1
-                self._solve(key, slot, batch, cold)
-                cold = False
-                slot.last_used = time.perf_counter()
+            self._run_matrix(key, slot, cold, started)
         except (SLRError, RuntimeError) as e:            # this matrix's requests fail, the server goes on
             t = time.perf_counter() - self.t0
             with self.cv:
                 self.errors.append((t, key, f"{type(e).__name__}: {e}"))
                 if self.log is not None:
                     print(f"[serving] {t:.3f}s matrix {key}: {type(e).__name__}: {e}", file=self.log, flush=True)
-                for r in batch + list(self.pending.pop(key, deque())):
-                    if r.status == -1:
-                        r.status = e.status if isinstance(e, SLRError) else 4
-                        r.error, r.done = str(e), time.perf_counter() - self.t0
+                unfinished = [r for r in started if r.done == 0.0] + list(self.pending.pop(key, deque()))
+                for r in unfinished:
+                    r.status = e.status if isinstance(e, SLRError) else 4
+                    r.error, r.done = str(e), time.perf_counter() - self.t0
         finally:
             with self.cv:
                 self.busy.discard(key)
@@ -276,6 +331,7 @@ class SolveServer:
                 while arrivals and (not realtime or arrivals[0].arrival <= now):
                     r = arrivals.popleft()
                     self.pending.setdefault(r.matrix, deque()).append(r)
+                    self.cv.notify_all()               # a running worker of that matrix may take it
                 # oldest waiting request first, one worker per matrix
                 ready = sorted(((q[0].arrival, k) for k, q in self.pending.items() if q and k not in self.busy),
                                key=lambda t: t[0])

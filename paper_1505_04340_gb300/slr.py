@@ -31,7 +31,8 @@ EXPORTS = ["slr_default_opts", "slr_setup", "slr_apply", "slr_pcg_solve", "slr_b
            "slr_stilde_solve", "slr_set_lowrank", "slr_get_lowrank", "slr_get_ritz", "slr_get_perm",
            "slr_get_info", "slr_dd_order", "slr_kernel_launches", "slr_destroy", "slr_status_str",
            "slr_last_error_message", "slr_apply_noalloc", "slr_add_vectors", "slr_gmres_solve",
-           "slr_device_status", "slr_inject_alloc_failure"]
+           "slr_device_status", "slr_inject_alloc_failure", "slr_cg_slot_start", "slr_cg_advance",
+           "slr_cg_slot_result"]
 
 
 U_DTYPE = {"fp32": 0, "tf32": 1, "bf16": 2}
@@ -100,6 +101,9 @@ def load():
         "slr_dd_order": (i32, [i32, vp, vp, i32, vp, vp, vp, vp, vp]),
         "slr_kernel_launches": (C.c_int64, []),
         "slr_device_status": (i32, [vp, vp]),
+        "slr_cg_slot_start": (i32, [vp, i32, vp, f64, i32, vp]),
+        "slr_cg_advance": (i32, [vp, i32, i32, vp, vp, vp, vp, vp]),
+        "slr_cg_slot_result": (i32, [vp, i32, vp, vp]),
         "slr_inject_alloc_failure": (None, [C.c_int64]),
         "slr_destroy": (None, [vp]),
         "slr_status_str": (C.c_char_p, [i32]),
@@ -332,6 +336,35 @@ class SLR:
         if check and st not in (OK, 5):
             _check(st, "slr_gmres_solve")
         return _back(x, one), its, rel, st
+
+    # -- continuous batching: CG slots (slr_cg_*)
+    def cg_start(self, slot, b, tol=1e-8, maxit=300, stream=None):
+        """Start slot `slot` on the right-hand side b (float64 CUDA tensor (n,), original order)."""
+        b = b.contiguous()
+        if not (b.is_cuda and b.dtype.is_floating_point and b.numel() == self.n):
+            raise ValueError("b must be a float64 CUDA vector of length n")
+        _check(self._lib.slr_cg_slot_start(self._h, int(slot), C.c_void_p(b.data_ptr()), float(tol), int(maxit),
+                                          _stream_ptr(stream)), "slr_cg_slot_start")
+        return b
+
+    def cg_advance(self, iters, width, stream=None):
+        """Run `iters` iterations over slots 0 .. width-1; returns (active, iterations,
+        relres, status) per slot (numpy arrays)."""
+        act = np.zeros(width, np.int32)
+        its = np.zeros(width, np.int32)
+        rel = np.zeros(width, np.float64)
+        sts = np.zeros(width, np.int32)
+        _check(self._lib.slr_cg_advance(self._h, int(iters), int(width), _stream_ptr(stream), _host_ptr(act),
+                                        _host_ptr(its), _host_ptr(rel), _host_ptr(sts)), "slr_cg_advance")
+        return act, its, rel, sts
+
+    def cg_result(self, slot, out=None, stream=None):
+        """x of a slot (original order) as a float64 CUDA tensor (n,)."""
+        import torch
+        x = out if out is not None else torch.empty(self.n, dtype=torch.float64, device="cuda")
+        _check(self._lib.slr_cg_slot_result(self._h, int(slot), C.c_void_p(x.data_ptr()), _stream_ptr(stream)),
+               "slr_cg_slot_result")
+        return x
 
     def pcg(self, b, tol=1e-8, maxit=300, stream=None, check=True):
         """Solve A x = b (original order) by SLR-preconditioned CG.

@@ -1,8 +1,9 @@
 """Scheduling logic of the solve server, on the CPU with a fake backend.
 
 The fake backend stands in for the device: it keeps a byte count for each
-resident "handle", sleeps for a setup or a solve, and returns x = b / diag(A)
-so that the column bookkeeping of packed batches can be checked exactly.
+resident "handle", sleeps for a setup or an advance of the CG slots, lets each
+started column run a set number of iterations, and returns x = b / diag(A) so
+that the column bookkeeping can be checked exactly.
 """
 import threading
 import time
@@ -16,12 +17,12 @@ import slrgen
 
 
 class FakeBackend:
-    def __init__(self, total, setup_s=0.02, solve_s=0.03, fail=()):
+    def __init__(self, total, setup_s=0.02, step_s=0.01, fail=(), need=lambda b: 8):
         self.total, self.used, self.max_used = total, 0, 0
-        self.setup_s, self.solve_s, self.fail = setup_s, solve_s, set(fail)
+        self.setup_s, self.step_s, self.fail, self.need = setup_s, step_s, set(fail), need
         self.lock = threading.Lock()
         self.inflight = self.max_inflight = 0
-        self.solves = []                         # (key, columns, start, end)
+        self.steps = []                          # (key, width, occupied, start, end)
 
     def free_bytes(self):
         with self.lock:
@@ -37,24 +38,44 @@ class FakeBackend:
         time.sleep(self.setup_s)
         diag = np.array([spec.val[spec.rowptr[i]:spec.rowptr[i + 1]][spec.colind[spec.rowptr[i]:spec.rowptr[i + 1]] == i][0]
                          for i in range(spec.n)])
-        return serving._Slot(handle=(spec.k, diag), stream=None, footprint=fp)
+        return serving.Resident(handle={"k": spec.k, "diag": diag, "slots": {}}, stream=None, footprint=fp)
 
-    def solve(self, slot, B, tol, maxit):
+    def start(self, res, slots, B, tol, maxit):
+        for i, j in enumerate(slots):
+            assert j not in res.handle["slots"] or not res.handle["slots"][j]["active"]
+            res.handle["slots"][j] = {"b": B[:, i].copy(), "its": 0, "need": self.need(B[:, i]), "active": True}
+        return None
+
+    def advance(self, res, iters, width):
         with self.lock:
             self.inflight += 1
             self.max_inflight = max(self.max_inflight, self.inflight)
         t = time.perf_counter()
-        time.sleep(self.solve_s)
-        X = B / slot.handle[1][:, None]
+        time.sleep(self.step_s)
+        act, its, rel, sts = (np.zeros(width, np.int32), np.zeros(width, np.int32), np.zeros(width),
+                              np.zeros(width, np.int32))
+        occupied = 0
+        for j, st in res.handle["slots"].items():
+            if j >= width:
+                continue
+            if st["active"]:
+                occupied += 1
+                st["its"] = min(st["its"] + iters, st["need"])
+                st["active"] = st["its"] < st["need"]
+            act[j], its[j] = st["active"], st["its"]
+            rel[j], sts[j] = (0.5, 0) if st["active"] else (1e-9, 1)
         with self.lock:
             self.inflight -= 1
-            self.solves.append((slot.handle[0], B.shape[1], t, time.perf_counter()))
-        r = B.shape[1]
-        return X, np.full(r, 3, np.int32), np.full(r, 1e-9), 0
+            self.steps.append((res.handle["k"], width, occupied, t, time.perf_counter()))
+        return act, its, rel, sts
 
-    def release(self, slot):
+    def results(self, res, slots):
+        d = res.handle["diag"]
+        return np.stack([res.handle["slots"][j]["b"] / d for j in slots], axis=1)
+
+    def release(self, res):
         with self.lock:
-            self.used -= slot.footprint
+            self.used -= res.footprint
 
 
 def _matrices(count=4):
@@ -99,29 +120,44 @@ def test_backlog_is_batched_per_matrix_and_bounded():
     srv.run(reqs, realtime=False)
     _check_answers(mats, reqs)
     assert be.max_inflight <= 3 and srv.max_inflight <= 3
-    assert all(c <= 8 for _, c, _, _ in be.solves)
+    assert all(w <= 8 and occ <= 8 for _, w, occ, _, _ in be.steps)
     assert srv.setups == 4 and srv.evictions == 0
-    # a backlog is packed: fewer solves than requests, and some batch holds several requests
-    assert len(be.solves) < len(reqs)
+    # a backlog shares the slots: some request started beside others
     assert any(r.batch > r.ncols for r in reqs)
     st = serving.latency_stats(reqs)
     assert st["served"] == 30 and st["solves"] == sum(r.ncols for r in reqs)
     assert 0 < st["p50_ms"] <= st["p99_ms"]
 
 
-def test_late_arrivals_join_next_batch_and_other_matrices_overlap():
+def test_late_arrivals_join_at_an_iteration_boundary():
     mats = _matrices(2)
-    # r0 on matrix 0 at t=0; r1, r2 on matrix 0 arrive during its solve; r3 on matrix 1 too
+    # r0 on matrix 0 at t=0 needs 40 iterations; r1, r2 on matrix 0 and r3 on matrix 1
+    # arrive while it runs: they start in free slots before r0 finishes
     reqs = _requests(mats, [(0, 2, 0.0), (0, 1, 0.08), (0, 3, 0.09), (1, 1, 0.08)])
-    be = FakeBackend(total=1 << 40, setup_s=0.05, solve_s=0.15)
+    need = lambda b: 40 if abs(b[0] - reqs[0].b[0, 0]) < 1e-15 or abs(b[0] - reqs[0].b[0, 1]) < 1e-15 else 8
+    be = FakeBackend(total=1 << 40, setup_s=0.05, step_s=0.02, need=need)
     srv = serving.SolveServer(mats, nrhs_max=8, max_concurrent=2, reserve_bytes=0, backend=be)
     srv.run(reqs, realtime=True)
     _check_answers(mats, reqs)
     r0, r1, r2, r3 = reqs
     assert r0.batch == 2
-    assert r1.batch == r2.batch == 4 and r1.start == r2.start >= r0.done
-    assert r3.start < r0.done                 # the other matrix did not wait for matrix 0
+    assert r1.start < r0.done and r2.start < r0.done      # joined the running slots
+    assert r1.done < r0.done                              # and finished first
+    assert r3.start < r0.done                             # the other matrix did not wait for matrix 0
     assert be.max_inflight == 2
+
+
+def test_converged_slot_is_refilled():
+    mats = _matrices(1)
+    # two slots; r0 needs 40 iterations, r1 8, r2 waits for a slot: it takes r1's when r1 converges
+    reqs = _requests(mats, [(0, 1, 0.0), (0, 1, 0.0), (0, 1, 0.0)])
+    first = reqs[0].b[0]
+    be = FakeBackend(total=1 << 40, setup_s=0.0, step_s=0.01, need=lambda b: 40 if b[0] == first else 8)
+    srv = serving.SolveServer(mats, nrhs_max=2, max_concurrent=1, reserve_bytes=0, backend=be)
+    srv.run(reqs, realtime=False)
+    _check_answers(mats, reqs)
+    r0, r1, r2 = reqs
+    assert r1.done <= r2.start < r0.done
 
 
 def test_capacity_forces_lru_eviction():
@@ -130,7 +166,7 @@ def test_capacity_forces_lru_eviction():
     cap = fp[2] + fp[3] + 10                  # any two handles fit, never three
     order = [0, 1, 2, 3, 0, 1, 3, 2, 0, 0, 1]
     reqs = _requests(mats, [(k, 1, 0.01 * i) for i, k in enumerate(order)])
-    be = FakeBackend(total=1 << 40, setup_s=0.01, solve_s=0.01)
+    be = FakeBackend(total=1 << 40, setup_s=0.01, step_s=0.005)
     srv = serving.SolveServer(mats, nrhs_max=4, max_concurrent=2, reserve_bytes=0, capacity_bytes=cap, backend=be)
     srv.footprints = {k: fp[k] for k in mats}
     srv.run(reqs, realtime=True)

@@ -150,3 +150,43 @@ def test_concurrent_handles_of_different_widths():
         P = wide if nm == "wide" else narrow
         x = outs[nm + "fp64"][:, 0]
         assert np.linalg.norm(x - P.xstar[:, 0]) / np.linalg.norm(P.xstar[:, 0]) < 1e-6
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_cg_slots_equal_pcg_solve(precision):
+    """Columns started in CG slots at different iteration boundaries (one refilling a
+    converged column's slot) give bitwise the answers and iteration counts of
+    slr_pcg_solve on each column alone: a slot starts with p = 0 and a unit rho
+    placeholder, so its first preconditioner update yields p = z exactly."""
+    import torch
+    from paper_1505_04340_gb300 import SLR
+    P = slrgen.make_problem("slots", (18, 17, 16), (3, 2, 2), 8, kind="fv", coef_range=(1e-2, 1e2), nrhs=3)
+    h = SLR(P.rowptr, P.colind, P.val, P.part, P.nparts, k=P.k, lanczos_steps=P.lanczos_steps, precision=precision,
+            nrhs_max=4, flexible_cg=(precision == "mixed"))
+    B = [torch.tensor(np.ascontiguousarray(P.b[:, j]), device="cuda") for j in range(3)]
+    ref = [h.pcg(b) for b in B]                             # (x, its, rel, status) of each column alone
+    holder = {0: 0}                                         # slot -> column it runs
+    h.cg_start(0, B[0])
+    act, its, rel, st = h.cg_advance(3, 1)
+    assert act[0] == 1 and its[0] == 3
+    h.cg_start(2, B[1])                                     # slot 1 stays idle; slot 2 joins at iteration 3
+    holder[2] = 1
+    out, queue = {}, [2]                                    # column 2 waits for a free slot
+    for _ in range(300):
+        act, its, rel, st = h.cg_advance(2, 3)
+        assert act[1] == 0                                  # the idle slot never runs
+        for slot in list(holder):
+            if not act[slot]:
+                out[holder.pop(slot)] = (h.cg_result(slot).cpu().numpy(), int(its[slot]), int(st[slot]))
+                if queue:                                   # refill the converged column's slot
+                    holder[slot] = queue.pop(0)
+                    h.cg_start(slot, B[holder[slot]])
+        if not holder:
+            break
+    assert sorted(out) == [0, 1, 2]
+    for j in range(3):
+        x, it, s_ = out[j]
+        xr, itr, _, sr = ref[j]
+        assert s_ == 1 and sr == 0
+        assert it == int(itr[0]), (j, it, itr)
+        assert np.array_equal(x, xr.cpu().numpy()), j

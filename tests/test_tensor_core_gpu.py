@@ -131,9 +131,13 @@ def _kappa_L(name, o):
 @pytest.mark.parametrize("mma", ["tf32", "bf16"])
 @pytest.mark.parametrize("nrhs", [8, 32, 40])
 def test_band_solve_on_tensor_cores_matches_oracle(name, mma, nrhs):
-    """t = B^{-1} F with the factor and the plane vectors rounded to TF32 / BF16: a
-    solve with a factor perturbed by u relative is off by about kappa(L) u, for the
-    forward and the backward pass; the bound is 8 kappa(L) u."""
+    """t = B^{-1} F with the factor and the plane vectors rounded to TF32 / BF16.
+    Rounding an input moves each product term by at most u relative (factor and
+    vector: 2u per term, FP32 accumulation adds far less); these diagonally
+    dominant blocks keep the plane sums well conditioned and the chain contractive,
+    so the solve stays within a few u of the exact one, while a block left out or
+    misplaced moves it by O(1).  Bound 16 u; kappa(L) u, the worst-case bound, is
+    printed beside it (it runs to 0.3 for TF32 on the FV blocks)."""
     P = _band_problem(name)
     o = OracleSLR(P.rowptr, P.colind, P.val, P.part, P.nparts, 0)
     h = SLR(P.rowptr, P.colind, P.val, P.part, P.nparts, k=0, precision="mixed", nrhs_max=nrhs, band_mma=mma)
@@ -142,8 +146,9 @@ def test_band_solve_on_tensor_cores_matches_oracle(name, mma, nrhs):
     T = h.bsolve(cu(F)).cpu().numpy()
     To = np.stack([o.bsolve.solve(F[:, j]) for j in range(nrhs)], axis=1)
     err = float((np.abs(T - To).max(axis=0) / np.abs(To).max(axis=0)).max())
-    tol = 8 * _kappa_L(name, o) * U_TC[mma]
-    print(f"{name} {mma} nrhs {nrhs}: band solve error {err:.2e} (bound {tol:.2e})")
+    tol = 16 * U_TC[mma]
+    print(f"{name} {mma} nrhs {nrhs}: band solve error {err:.2e} (bound {tol:.2e}; kappa(L) u = "
+          f"{_kappa_L(name, o) * U_TC[mma]:.2e})")
     assert err <= tol
 
 
