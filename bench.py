@@ -296,12 +296,14 @@ def run_profile(args):
     name = args.problem or HEADLINE
     P, _ = build_problem(name)
     _, nrhs, maxit, _ = PROBLEMS[name]
+    nrhs = args.nrhs or nrhs
     maxit = args.maxit or maxit
-    b = torch.tensor(np.ascontiguousarray(P.b[:, :nrhs]), device="cuda")
+    b = torch.tensor(np.ascontiguousarray(np.tile(P.b, (1, nrhs))[:, :nrhs]), device="cuda")
     b = b[:, 0] if nrhs == 1 else b
+    tc = dict(u_dtype=args.u_dtype, band_mma=args.band_mma) if (args.precision == "mixed" and nrhs >= 8) else {}
     h = SLR(P.rowptr, P.colind, P.val, P.part, P.nparts, k=P.k, lanczos_steps=P.lanczos_steps,
             precision=args.precision, nrhs_max=nrhs, flexible_cg=(args.precision == "mixed"),
-            host_loop=args.host_loop, autotune=not args.no_autotune)   # the bench's kernel choices
+            host_loop=args.host_loop, autotune=not args.no_autotune, **tc)   # the bench's kernel choices
     info = h.get_info()
     f = torch.randn(info["n_interior"], nrhs, dtype=torch.float64, device="cuda")
     g = torch.randn(info["s"], nrhs, dtype=torch.float64, device="cuda")
@@ -706,6 +708,7 @@ def main():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
     ap.add_argument("--profile-kernel", default="pcg", choices=["pcg", "bsolve", "csolve", "apply"])
     ap.add_argument("--maxit", type=int, default=0, help="PCG iteration cap of --profile (0: the workload's)")
+    ap.add_argument("--nrhs", type=int, default=0, help="right-hand sides of --profile (0: the workload's)")
     ap.add_argument("--no-autotune", action="store_true", help="keep the built-in launch choices")
     ap.add_argument("--band-mma", default="tf32", choices=["off", "tf32", "bf16"],
                     help="band solve of right-hand-side blocks on the tensor cores (mixed path)")

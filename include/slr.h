@@ -125,6 +125,12 @@ typedef struct {
                                fit, and both C-solve paths, on this operator, and keeps the
                                fastest; the choice is cached per device, precision and
                                problem shape for the process's life                      */
+    int32_t zform;          /* 1: apply S~^{-1} in the form of Proposition 4.3 (Eq. 4.15),
+                               (1-theta)^{-1} C^{-1} g + Z_k (d o Z_k^T g) with Z_k = L^{-T} U_k
+                               formed at setup: the product Z_k^T g runs beside the two
+                               solves with C's factor instead of between them.  The same
+                               operator as the default U-form (Eq. 4.7) up to rounding.
+                               0 (default): the U-form                                 */
     int32_t band_mma;       /* 0 (default): the band solve runs on the CUDA cores.
                                SLR_U_TF32 or SLR_U_BF16 (mixed path only): blocks of 8 or
                                more right-hand sides are solved with the band factor and
@@ -136,7 +142,7 @@ typedef struct {
                                cooperative C solve (c_persistent) before it gives up and
                                reports SLR_ERR_TIMEOUT; 0 = the default (2^22 polls, about a
                                quarter second)                                           */
-    int32_t reserved[7];    /* must be 0                                                  */
+    int32_t reserved[6];    /* must be 0                                                  */
 } slr_opts;
 
 typedef struct {

@@ -240,6 +240,15 @@ slr_status upload_operator(slr_handle h, DevOperator<T>& op, bool with_band) {
         CK(cudaMemcpyAsync(d.ptasks, c.ptasks.data(), c.ptasks.size() * sizeof(int32_t), cudaMemcpyHostToDevice,
                            h->stream));
     CS(dalloc(h, &d.wbuf, (size_t)std::max<int64_t>(d.nrow, 1) * r));
+    CS(dalloc(h, &d.tws, (size_t)std::max<int64_t>(c.s, 1) * r));
+    d.lev_maxn.assign(c.nlev, 0);
+    for (int32_t l = 0; l < c.nlev; ++l) {
+        if (c.lev_small[l]) continue;
+        for (int32_t q = c.lev_sn_ptr[l]; q < c.lev_sn_ptr[l + 1]; ++q) {
+            const int32_t J = c.lev_sn[q];
+            d.lev_maxn[l] = std::max(d.lev_maxn[l], c.c0[J + 1] - c.c0[J]);
+        }
+    }
     d.ws_cols = r;
     // top zone: explicit inverse in both layouts, task tables and workspaces
     d.top_lev = c.top_lev;
@@ -301,6 +310,7 @@ slr_status set_operator_lowrank(slr_handle h, DevOperator<T>& op, const double* 
         dfree(h, reinterpret_cast<char*&>(op.U_tc_rm), eb);
         if (op.U_tc_cm) dfree(h, reinterpret_cast<char*&>(op.U_tc_cm), eb);
     }
+    if (op.Zdd) dfree(h, op.Zdd, (size_t)s * k_old);
     if (op.U && k_old != k) {
         dfree(h, op.U, (size_t)s * k_old);
         dfree(h, op.dvec, (size_t)k_old);
@@ -330,6 +340,23 @@ slr_status set_operator_lowrank(slr_handle h, DevOperator<T>& op, const double* 
                 CK(launch_lowrank_tc_pack(op.u_dtype, (int32_t)s, k, U64_dev, rm, cm, h->stream));
             }
         }
+        if (h->opts.zform) {
+            // Z_k = L^{-T} U_k (Proposition 4.3) with the FP64 factor, scattered to DD order,
+            // at most nrhs_max columns at a time (the solves' workspaces hold that many)
+            double* Z64 = nullptr;
+            CS(dalloc(h, &Z64, (size_t)s * k));
+            for (int32_t c0 = 0; c0 < k; c0 += r)
+                CK(launch_c_backward<double>(h->op64.cf, U64_dev + (int64_t)c0 * s, h->op64.xf, Z64 + (int64_t)c0 * s,
+                                             s, std::min(r, k - c0), h->stream));
+            if constexpr (std::is_same<T, double>::value) {
+                op.Zdd = Z64;
+            } else {
+                CS(dalloc(h, &op.Zdd, (size_t)s * k));
+                CK(launch_convert<double, float>(s, k, Z64, s, op.Zdd, s, h->stream));
+                CK(cudaStreamSynchronize(h->stream));
+                dfree(h, Z64, (size_t)s * k);
+            }
+        }
         // d_i = (1 - lambda_i)^{-1} - (1 - theta)^{-1}, formed in FP64 (cancellation near 1)
         std::vector<double> d(k);
         for (int32_t i = 0; i < k; ++i) d[i] = 1.0 / (1.0 - lam[i]) - 1.0 / (1.0 - theta);
@@ -349,9 +376,22 @@ slr_status run_apply(slr_handle h, DevOperator<T>& op, const T* r, int64_t ldr, 
     const int32_t nI = hs.nI, s = hs.s;
     CK(launch_band_solve<T>(op, hs.p, hs.wmax, r, ldr, op.tB, nI, nullptr, 0, nrhs, st));   // t = B^{-1} f
     CK(launch_gather_et<T>(op, s, r + nI, ldr, op.tB, nI, op.gp, s, nrhs, st));              // g' = g - E^T t
-    CK(launch_c_forward<T>(op.cf, op.gp, s, op.wf, nrhs, st));                               // w = L^{-1} g'
-    CK(launch_lowrank<T>(op, s, h->k, op.wf, nrhs, st));                                     // w' (Eq. 4.7)
-    CK(launch_c_backward<T>(op.cf, op.wf, op.xf, z + nI, ldz, nrhs, st));                    // y = L^{-T} w'
+    if (op.Zdd && h->k > 0) {
+        // Z-form (Proposition 4.3, Eq. 4.15): v = d o Z_k^T g' on the side stream while
+        // y = C^{-1} g' runs, then y = (1-theta)^{-1} y + Z_k v
+        CK(cudaEventRecord(h->ev_fork, st));
+        CK(cudaStreamWaitEvent(h->aux, h->ev_fork, 0));
+        CK(launch_lowrank_v<T>(op, s, h->k, op.Zdd, op.gp, s, nrhs, h->aux));
+        CK(cudaEventRecord(h->ev_join, h->aux));
+        CK(launch_c_forward<T>(op.cf, op.gp, s, op.wf, nrhs, st));                           // L^{-1} g'
+        CK(launch_c_backward<T>(op.cf, op.wf, op.xf, z + nI, ldz, nrhs, st));                // C^{-1} g'
+        CK(cudaStreamWaitEvent(st, h->ev_join, 0));
+        CK(launch_lowrank_update<T>(op, s, h->k, op.Zdd, z + nI, ldz, nrhs, st));
+    } else {
+        CK(launch_c_forward<T>(op.cf, op.gp, s, op.wf, nrhs, st));                           // w = L^{-1} g'
+        CK(launch_lowrank<T>(op, s, h->k, op.wf, nrhs, st));                                 // w' (Eq. 4.7)
+        CK(launch_c_backward<T>(op.cf, op.wf, op.xf, z + nI, ldz, nrhs, st));                // y = L^{-T} w'
+    }
     CK(launch_spmv_e<T>(op, nI, z + nI, ldz, op.eb, nI, nrhs, st));                          // E y
     CK(launch_band_solve<T>(op, hs.p, hs.wmax, op.eb, nI, z, ldz, op.tB, nI, nrhs, st));    // u = t - B^{-1} E y
     return SLR_OK;
@@ -932,6 +972,11 @@ slr_status setup_impl(slr_handle h, int32_t n, const int32_t* rowptr, const int3
                 hs.cf.nlev, t1 - t0, t2 - t1, t3 - t2);
     CK(cudaGetDevice(&h->device));
     CS(noalloc_lookup(h));
+    if (h->opts.zform) {
+        CK(cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+    }
     CS(upload(h, &h->perm, hs.perm));
     CS(upload(h, &h->a_rp, hs.a_rp));
     CS(upload(h, &h->a_ci, hs.a_ci));
@@ -1293,7 +1338,8 @@ slr_status slr_setup(int32_t n, const int32_t* rowptr, const int32_t* colind, co
         o.u_dtype < SLR_U_FP32 || o.u_dtype > SLR_U_BF16 ||
         (o.u_dtype != SLR_U_FP32 && o.precision != SLR_PREC_MIXED) || o.spin_limit < 0 ||
         o.band_mma < 0 || o.band_mma > SLR_U_BF16 || (o.band_mma != 0 && o.precision != SLR_PREC_MIXED) ||
-        std::any_of(o.reserved, o.reserved + 7, [](int32_t v) { return v != 0; })) {
+        o.zform < 0 || o.zform > 1 ||
+        std::any_of(o.reserved, o.reserved + 6, [](int32_t v) { return v != 0; })) {
         set_error("invalid options");
         delete h;
         return SLR_ERR_INVALID_ARG;
@@ -1709,6 +1755,12 @@ void slr_destroy(slr_handle h) {
     {
         std::unique_lock<std::shared_mutex> lk(g_capture_mu);
         drop_graphs(h);
+        if (h->aux) {
+            cudaStreamSynchronize(h->aux);
+            cudaStreamDestroy(h->aux);
+        }
+        if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+        if (h->ev_join) cudaEventDestroy(h->ev_join);
         for (void* p : h->allocs) cudaFree(p);
     }
     if (old >= 0 && old != h->device) cudaSetDevice(old);

@@ -135,6 +135,55 @@ __device__ __forceinline__ BtBlock bt_block(int q, int c) {
     return (u & 1) ? BtBlock{J + 1, 2, J} : BtBlock{J, 3, J};
 }
 
+// Operand rows of 32 columns c0 .. c0 + 31 from the lanes' values v (lane = row
+// rbase + lane): a butterfly transpose inside groups of RPQ = 16 / E lanes (the rows
+// that share 16 bytes of a core-matrix row) leaves lane u of a group holding
+// column c0 + jc RPQ + u of the group's RPQ rows, stored as one 16-byte word.
+template <int AB>
+__device__ __forceinline__ void bt_put_rows(unsigned char* vdst, int rbase, int c0, const float (&v)[32],
+                                            uint32_t sbo_v, int nrhs, int W, int lane) {
+    using Tp = BtType<AB>;
+    using Te = typename Tp::Te;
+    constexpr int RPQ = 16 / Tp::E;
+    const int grp = lane / RPQ, u = lane % RPQ;
+#pragma unroll
+    for (int jc = 0; jc < 32 / RPQ; ++jc) {
+        float a[RPQ];
+#pragma unroll
+        for (int i = 0; i < RPQ; ++i) a[i] = v[jc * RPQ + i];
+#pragma unroll
+        for (int m = 1; m < RPQ; m <<= 1) {
+            const bool upper = (u & m) != 0;
+#pragma unroll
+            for (int i = 0; i < RPQ; ++i) {
+                if (i & m) continue;
+                const float send = upper ? a[i] : a[i | m];
+                const float recv = __shfl_xor_sync(0xffffffffu, send, m);
+                if (upper) a[i] = recv;
+                else a[i | m] = recv;
+            }
+        }
+        const int j = c0 + jc * RPQ + u;
+        const int r0 = rbase + grp * RPQ;              // first of the group's rows (a multiple of RPQ)
+        if (j < nrhs && r0 < W) {
+            uint32_t w32[4];
+            if constexpr (RPQ == 4) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) w32[k] = __float_as_uint(Tp::pack(r0 + k < W ? a[k] : 0.0f));
+            } else {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const __nv_bfloat162 h2 = __floats2bfloat162_rn(r0 + 2 * k < W ? a[2 * k] : 0.0f,
+                                                                    r0 + 2 * k + 1 < W ? a[2 * k + 1] : 0.0f);
+                    w32[k] = *reinterpret_cast<const uint32_t*>(&h2);
+                }
+            }
+            *reinterpret_cast<uint4*>(vdst + (j >> 3) * sbo_v + (r0 / RPQ) * 128 + (j & 7) * 16) =
+                make_uint4(w32[0], w32[1], w32[2], w32[3]);
+        }
+    }
+}
+
 template <int AB, int NP>
 __global__ void __launch_bounds__(kBtThreads, 1)
 k_band_tc(const BandTcBlock* __restrict__ blocks, const unsigned char* __restrict__ fac, const float* in,
@@ -158,6 +207,9 @@ k_band_tc(const BandTcBlock* __restrict__ blocks, const unsigned char* __restric
     uint64_t* fin_bar = opnd_bar + 1;
     uint32_t* tbase = reinterpret_cast<uint32_t*>(fin_bar + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tbase + 1);
+    // the epilogue's global operands of a block (F_J, Y_J or the base), staged by cp.async
+    // before the accumulator wait: [M-tile][column][epilogue thread]
+    float* pre_s = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(tbase) + 16);
     const int tid = threadIdx.x, warp = tid >> 5;
     const int nM = (W + 127) / 128;
     const uint32_t ncol = nM * NP <= 32 ? 32 : nM * NP <= 64 ? 64 : 128;
@@ -284,53 +336,75 @@ k_band_tc(const BandTcBlock* __restrict__ blocks, const unsigned char* __restric
                 *reinterpret_cast<Te*>(v1 + opos(j, r)) = Tp::pack(ok ? in[row_of(0, r) + j * ldi] : 0.0f);
         }
         arrive();
+        auto put_rows = [&](unsigned char* vdst, int rbase, int c0, const float (&v)[32]) {
+            bt_put_rows<AB>(vdst, rbase, c0, v, sbo_v, nrhs, W, tid & 31);
+        };
         for (int q = 0; q < nblk; ++q) {
             const BtBlock bk = bt_block(q, c);
             const int J = bk.vplane;
+            // this block's global operands into shared memory while its MMAs run
+            const bool need_pre = bk.type == 0 || bk.type == 2 || (bk.type == 3 && base);
+            if (need_pre) {
+                const float* srcb = bk.type == 0 ? in : bk.type == 2 ? out : base;
+                const int64_t lds = bk.type == 0 ? ldi : bk.type == 2 ? ldo : ldb;
+                for (int mt = 0; mt < nM; ++mt) {
+                    const int r = 128 * mt + e;
+                    const bool ok = valid(J, r);
+                    const int64_t row = row_of(J, r);
+                    for (int j = 0; j < nrhs; ++j) {
+                        float* dst = pre_s + ((size_t)mt * NP + j) * 128 + e;
+                        if (ok)
+                            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(tc::smem_addr(dst)),
+                                         "l"(srcb + row + j * lds)
+                                         : "memory");
+                        else
+                            *dst = 0.0f;
+                    }
+                }
+                asm volatile("cp.async.commit_group;" ::: "memory");
+            }
             // the warp decides together (tcgen05.ld below is warp-collective)
             bool ok = tc::mbar_wait(acc_bar, (uint32_t)(q & 1), kBtSpin);
             if (!__all_sync(0xffffffffu, ok)) {
                 if ((tid & 31) == 0) fail();
+                asm volatile("cp.async.wait_all;" ::: "memory");
                 break;
             }
-            if (__any_sync(0xffffffffu, *abort_flag != 0)) break;
+            if (__any_sync(0xffffffffu, *abort_flag != 0)) {
+                asm volatile("cp.async.wait_all;" ::: "memory");
+                break;
+            }
             tc::fence_after_sync();
+            if (need_pre) asm volatile("cp.async.wait_all;" ::: "memory");
             for (int mt = 0; mt < nM; ++mt) {
                 const int r = 128 * mt + e;
                 const bool in_w = r < W, ok_r = valid(J, r);
                 const int64_t row = row_of(J, r);
+                const int rbase = 128 * mt + 32 * quarter;      // first row of the warp
 #pragma unroll
                 for (int c0 = 0; c0 < NP; c0 += 32) {
-                    float v[32], pre[32];
+                    float v[32];
                     tc::tmem_ld32(tmem + lane_addr + (uint32_t)(mt * NP + c0), v);
-                    if (!in_w) continue;
-                    // the global operands of the 32 columns first (independent loads in flight)
+                    const float* pre = pre_s + ((size_t)mt * NP + c0) * 128 + e;
+                    if (bk.type == 0 || bk.type == 2) {          // t = F_J - O_J Y_{J-1}  /  Y_J - O^T X
 #pragma unroll
-                    for (int jj = 0; jj < 32; ++jj) {
-                        const int j = c0 + jj;
-                        float x = 0.0f;
-                        if (j < nrhs && ok_r) {
-                            if (bk.type == 0) x = in[row + j * ldi];
-                            else if (bk.type == 2) x = out[row + j * ldo];
-                            else if (bk.type == 3 && base) x = base[row + j * ldb];
-                        }
-                        pre[jj] = x;
-                    }
+                        for (int jj = 0; jj < 32; ++jj) v[jj] = (c0 + jj < nrhs ? pre[jj * 128] : 0.0f) - v[jj];
+                        put_rows(v1, rbase, c0, v);
+                    } else if (bk.type == 1) {                   // Y_J = D_J t
+                        if (in_w && ok_r) {
 #pragma unroll
-                    for (int jj = 0; jj < 32; ++jj) {
-                        const int j = c0 + jj;
-                        if (j >= nrhs) break;
-                        const float a = v[jj];
-                        if (bk.type == 0 || bk.type == 2) {          // t = F_J - O_J Y_{J-1}  /  Y_J - O^T X
-                            *reinterpret_cast<Te*>(v1 + opos(j, r)) = Tp::pack(pre[jj] - a);
-                        } else if (bk.type == 1) {                   // Y_J = D_J t
-                            if (ok_r) out[row + j * ldo] = a;
-                            *reinterpret_cast<Te*>(v0 + opos(j, r)) = Tp::pack(a);
-                            if (J == c - 1) *reinterpret_cast<Te*>(v1 + opos(j, r)) = Tp::pack(a);
-                        } else {                                     // X_J = D_J^T t
-                            if (ok_r) out[row + j * ldo] = base ? pre[jj] - a : a;
-                            *reinterpret_cast<Te*>(v0 + opos(j, r)) = Tp::pack(a);
+                            for (int jj = 0; jj < 32; ++jj)
+                                if (c0 + jj < nrhs) out[row + (c0 + jj) * ldo] = v[jj];
                         }
+                        put_rows(v0, rbase, c0, v);
+                        if (J == c - 1) put_rows(v1, rbase, c0, v);   // the backward starts from t = Y_{c-1}
+                    } else {                                     // X_J = D_J^T t
+                        if (in_w && ok_r) {
+#pragma unroll
+                            for (int jj = 0; jj < 32; ++jj)
+                                if (c0 + jj < nrhs) out[row + (c0 + jj) * ldo] = base ? pre[jj * 128] - v[jj] : v[jj];
+                        }
+                        put_rows(v0, rbase, c0, v);
                     }
                 }
             }
@@ -351,7 +425,7 @@ cudaError_t bt_launch(const DevOperator<float>& op, int32_t p, const float* in, 
     constexpr int E = BtType<AB>::E, KS = BtType<AB>::KS;
     const int WK = bt_nk(op.band_tc_wmax, KS) * KS;
     const size_t vbytes = (size_t)NP * WK * E;
-    const size_t fixed = 2 * vbytes + 8 * (2 * 8 + 3) + 16;
+    const size_t fixed = 2 * vbytes + 8 * (2 * 8 + 3) + 16 + (size_t)2 * NP * 128 * sizeof(float);
     // ring: as many 4-sub-tile slots (16 KB) as fit in the opt-in maximum, 2 .. 8
     const int stiles = 4;
     int nslot = (int)((227 * 1024 - fixed) / ((size_t)stiles * kSub));

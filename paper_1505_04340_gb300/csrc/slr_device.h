@@ -27,6 +27,8 @@ struct DevCFactor {
     int64_t nrow = 0;              // panel rows in total
     int32_t max_n = 0;             // widest supernode (shared memory of a forward task: t_J)
     T* wbuf = nullptr;             // [nrow x nrhs_max] panel products M_J t_J of the forward solve
+    T* tws = nullptr;              // [s x nrhs_max] t_J gathered once per level (per-level forward tasks)
+    std::vector<int32_t> lev_maxn; // widest supernode of each level (0 for the fused small levels)
     int4* tasks = nullptr;         // (supernode, first column, count <= 32, 0)
     int4* ptasks = nullptr;        // (supernode, first panel row, count <= 32, 0)
     std::vector<int32_t> lev_task_ptr;    // host copies, [nlev+1]
@@ -71,6 +73,7 @@ struct DevOperator {
     int32_t *et_rp = nullptr, *et_ci = nullptr; T* et_v = nullptr;   // E^T (s x nI)
     DevCFactor<T> cf;
     T* U = nullptr;                // s x k column-major, factor order
+    T* Zdd = nullptr;              // Z_k = L^{-T} U_k, s x k column-major, DD interface order (Z-form only)
     T* dvec = nullptr;             // [k] (1-lambda_i)^{-1} - (1-theta)^{-1}, from FP64
     T cinv = 1;                    // (1-theta)^{-1}
     // workspaces, nrhs_max columns each, leading dimension = rows
@@ -137,6 +140,9 @@ struct slr_handle_s {
     bool band_on_device = false;     // the B_i were factored on the device
     double lanczos_seconds[3] = {0, 0, 0};   // setup Lanczos: H applies, reorthogonalisation, eigensolve + U_k
     void* noalloc_base = nullptr;    // device address of slr_apply_noalloc's scratch array (slr_noalloc.cu)
+    // Z-form apply: Z_k^T g' runs on aux beside the C solves (fork and join events)
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 namespace slr {
@@ -203,6 +209,15 @@ cudaError_t launch_c_backward(const DevCFactor<T>& cf, const T* yf, T* xf, T* y_
 template <typename T>
 cudaError_t launch_lowrank(const DevOperator<T>& op, int32_t s, int32_t k, T* w, int32_t nrhs,
                            cudaStream_t st);
+// its two passes on a basis Ub (s x k column-major) and a block w (leading dimension
+// ldw): op.vk = d o (Ub^T w), then w = cinv w + Ub op.vk (the Z-form of Proposition 4.3
+// runs them on Z_k, the first beside the C solves)
+template <typename T>
+cudaError_t launch_lowrank_v(const DevOperator<T>& op, int32_t s, int32_t k, const T* Ub, const T* w, int64_t ldw,
+                             int32_t nrhs, cudaStream_t st);
+template <typename T>
+cudaError_t launch_lowrank_update(const DevOperator<T>& op, int32_t s, int32_t k, const T* Ub, T* w, int64_t ldw,
+                                  int32_t nrhs, cudaStream_t st);
 // elements of op.part that launch_lowrank needs for rank k and nrhs columns
 int64_t lowrank_part_elems(int32_t s, int32_t k, int32_t nrhs);
 // the tensor-core variant (slr_lowrank_tc.cu): usable for u_dtype TF32/BF16, 8..64

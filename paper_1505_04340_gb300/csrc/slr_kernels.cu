@@ -97,6 +97,8 @@ struct CView {
     const int64_t *r_off, *pan_off, *dinv_off, *seg_ptr;
     const T *panel, *dinv;
     T* wbuf;
+    T* tws;            // t_J of the level's supernodes gathered by k_cfwd_gather (s x nrhs), or null:
+                       // each forward task gathers t_J itself
     const int4 *tasks, *ptasks;
     const int32_t *lev_task_ptr, *lev_ptask_ptr, *lev_sn_ptr;
     const uint8_t* lev_small;
@@ -160,7 +162,14 @@ __device__ void cfwd_task_rb(const CView<T>& cf, const int4 tk, bool pan, T* ts,
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int32_t J = tk.x, a0 = cf.c0[J], nJ = cf.c0[J + 1] - a0;
 #pragma unroll
-    for (int b = 0; b < RB; ++b) gather_t(cf, J, threadIdx.x, NW * 32, ts + b * tstride, g, ldg, j0 + b);
+    for (int b = 0; b < RB; ++b) {
+        if (cf.tws) {                   // gathered once for the level (the same values)
+            const T* src = cf.tws + a0 + (int64_t)(j0 + b) * cf.s;
+            for (int i = threadIdx.x; i < nJ; i += NW * 32) ts[b * tstride + i] = src[i];
+        } else {
+            gather_t(cf, J, threadIdx.x, NW * 32, ts + b * tstride, g, ldg, j0 + b);
+        }
+    }
     __syncthreads();
     if (pan) {
         const T* P = cf.panel + cf.pan_off[J];
@@ -234,11 +243,15 @@ __device__ void cfwd_task_rb(const CView<T>& cf, const int4 tk, bool pan, T* ts,
     __syncthreads();
 }
 
-// All nrhs columns: blocks of 4 while ts holds 4 columns (rbmax = 4), then one at a time.
-template <typename T, int NW>
+// All nrhs columns: blocks of 8 or 4 while ts holds that many columns (rbmax), then one at a time.
+template <typename T, int NW, int RBMAX = 8>
 __device__ void cfwd_task_cta(const CView<T>& cf, const int4 tk, bool pan, T* ts, int tstride, int rbmax,
                               T (*red)[33], const T* g, int64_t ldg, T* xf, int32_t nrhs) {
     int j0 = 0;
+    if constexpr (RBMAX >= 8) {
+        if (rbmax >= 8)
+            for (; j0 + 8 <= nrhs; j0 += 8) cfwd_task_rb<T, NW, 8>(cf, tk, pan, ts, tstride, red, g, ldg, xf, j0);
+    }
     if (rbmax >= 4)
         for (; j0 + 4 <= nrhs; j0 += 4) cfwd_task_rb<T, NW, 4>(cf, tk, pan, ts, tstride, red, g, ldg, xf, j0);
     for (; j0 < nrhs; ++j0) cfwd_task_rb<T, NW, 1>(cf, tk, pan, ts, tstride, red, g, ldg, xf, j0);
@@ -331,13 +344,17 @@ __device__ void cbwd_task_rb(const CView<T>& cf, const int4 tk, T* us, T (*red)[
     }
 }
 
-// All nrhs columns: blocks of 4 while us holds 4 columns (rb4), then one at a time
-// (DEPTH4: loads in flight per lane in a block of 4).
-template <typename T, int NW, int DEPTH, int DEPTH4>
-__device__ void cbwd_task_cta(const CView<T>& cf, const int4 tk, T* us, bool rb4, T (*red)[33], const T* yf, T* xf,
+// All nrhs columns: blocks of 8 or 4 while us holds that many columns (rbmax), then
+// one at a time (DEPTH4: loads in flight per lane in a block).
+template <typename T, int NW, int DEPTH, int DEPTH4, int RBMAX = 8>
+__device__ void cbwd_task_cta(const CView<T>& cf, const int4 tk, T* us, int rbmax, T (*red)[33], const T* yf, T* xf,
                               T* y_dd, int64_t ldy, int32_t nrhs) {
     int j0 = 0;
-    if (rb4)
+    if constexpr (RBMAX >= 8) {
+        if (rbmax >= 8)
+            for (; j0 + 8 <= nrhs; j0 += 8) cbwd_task_rb<T, NW, DEPTH4, 8>(cf, tk, us, red, yf, xf, y_dd, ldy, j0);
+    }
+    if (rbmax >= 4)
         for (; j0 + 4 <= nrhs; j0 += 4) cbwd_task_rb<T, NW, DEPTH4, 4>(cf, tk, us, red, yf, xf, y_dd, ldy, j0);
     for (; j0 < nrhs; ++j0) cbwd_task_rb<T, NW, DEPTH, 1>(cf, tk, us, red, yf, xf, y_dd, ldy, j0);
 }
@@ -435,9 +452,11 @@ __device__ __forceinline__ bool stage_block_fwd(const CView<T>& cf, int J, T* st
 // memory, a thread computes a row (columns in order: one multiply-add per column,
 // no cross-lane sums, which on this part's narrow FP64 unit cost more than the
 // products); from HBM, a warp per row keeps the loads coalesced (lanes over the
-// columns, four rows in flight per warp).  A supernode is staged or not whatever
-// the right-hand sides, so every column gets the same bits alone and in a block.
-template <typename T, int NT, int GROUPS>
+// columns, four rows in flight per warp).  RB right-hand sides share each pass
+// over A_J (ts holds RB vectors, kSmallN apart), each with the multiply-adds it
+// gets alone; a supernode is staged or not whatever the right-hand sides, so
+// every column gets the same bits alone and in a block.
+template <typename T, int NT, int GROUPS, int RB>
 __device__ void cfwd_small_cta(const CView<T>& cf, int J, T* ts, const T* g, int64_t ldg, T* xf, int32_t nrhs, T* stg,
                                int cap) {
     constexpr int nw = NT / 32;
@@ -446,35 +465,47 @@ __device__ void cfwd_small_cta(const CView<T>& cf, int J, T* ts, const T* g, int
     const int64_t nr = cf.r_off[J + 1] - cf.r_off[J], rtot = nJ + nr;
     const T *D, *Pn;
     const bool staged = stage_block_fwd<T, NT>(cf, J, stg, cap, gt, D, Pn);   // lands while t_J is gathered
-    for (int j = 0; j < nrhs; ++j) {
-        gather_t(cf, J, gt, NT, ts, g, ldg, j);
-        if (j == 0 && staged) stage_wait();
+    for (int j0 = 0; j0 < nrhs; j0 += RB) {
+        const int nb = min(RB, nrhs - j0);
+        for (int b = 0; b < nb; ++b) gather_t(cf, J, gt, NT, ts + b * kSmallN, g, ldg, j0 + b);
+        if (j0 == 0 && staged) stage_wait();
         group_sync<NT, GROUPS>();
         if (staged) {
             const int32_t ldp = small_ldp(nJ);
             for (int32_t r = gt; r < rtot; r += NT) {
-                T acc = T(0);
+                T acc[RB];
+#pragma unroll
+                for (int b = 0; b < RB; ++b) acc[b] = T(0);
                 if (r < nJ) {
                     // (L_JJ^{-1})[r, c] = D[packed_col(c) + r - c]; the next column's entry is n_J - c - 1 further
                     int32_t e = r;
 #pragma unroll 4
                     for (int32_t c = 0; c <= r; ++c) {
-                        acc += D[e] * ts[c];
+                        const T a = D[e];
+#pragma unroll
+                        for (int b = 0; b < RB; ++b) acc[b] += a * ts[b * kSmallN + c];
                         e += nJ - c - 1;
                     }
-                    xf[a0 + r + (int64_t)j * cf.s] = acc;
+                    for (int b = 0; b < nb; ++b) xf[a0 + r + (int64_t)(j0 + b) * cf.s] = acc[b];
                 } else {
                     const T* Mr = Pn + (r - nJ) * ldp;
 #pragma unroll 4
-                    for (int32_t c = 0; c < nJ; ++c) acc += Mr[c] * ts[c];
-                    cf.wbuf[cf.r_off[J] + (r - nJ) + (int64_t)j * cf.nrow] = acc;
+                    for (int32_t c = 0; c < nJ; ++c) {
+                        const T a = Mr[c];
+#pragma unroll
+                        for (int b = 0; b < RB; ++b) acc[b] += a * ts[b * kSmallN + c];
+                    }
+                    for (int b = 0; b < nb; ++b) cf.wbuf[cf.r_off[J] + (r - nJ) + (int64_t)(j0 + b) * cf.nrow] = acc[b];
                 }
             }
         } else {
             for (int64_t r0 = 4 * warp; r0 < rtot; r0 += 4 * nw) {
-                T acc[4] = {T(0), T(0), T(0), T(0)};
+                T acc[4][RB];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int b = 0; b < RB; ++b) acc[u][b] = T(0);
                 for (int c = lane; c < nJ; c += 32) {
-                    const T tv = ts[c];
 #pragma unroll
                     for (int u = 0; u < 4; ++u) {
                         const int64_t r = r0 + u;
@@ -484,18 +515,21 @@ __device__ void cfwd_small_cta(const CView<T>& cf, int J, T* ts, const T* g, int
                         } else if (r < rtot) {
                             a = Pn[(r - nJ) * nJ + c];
                         }
-                        acc[u] += a * tv;
+#pragma unroll
+                        for (int b = 0; b < RB; ++b) acc[u][b] += a * ts[b * kSmallN + c];
                     }
                 }
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const T v = warp_sum(acc[u]);
-                    const int64_t r = r0 + u;
-                    if (lane == 0 && r < rtot) {
-                        if (r < nJ) xf[a0 + r + (int64_t)j * cf.s] = v;
-                        else cf.wbuf[cf.r_off[J] + (r - nJ) + (int64_t)j * cf.nrow] = v;
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int b = 0; b < RB; ++b) {
+                        const T v = warp_sum(acc[u][b]);
+                        const int64_t r = r0 + u;
+                        if (lane == 0 && r < rtot && b < nb) {
+                            if (r < nJ) xf[a0 + r + (int64_t)(j0 + b) * cf.s] = v;
+                            else cf.wbuf[cf.r_off[J] + (r - nJ) + (int64_t)(j0 + b) * cf.nrow] = v;
+                        }
                     }
-                }
             }
         }
         group_sync<NT, GROUPS>();
@@ -505,11 +539,14 @@ __device__ void cfwd_small_cta(const CView<T>& cf, int J, T* ts, const T* g, int
 // backward: x_J = A_J^T [y_J; -x_{R_J}] (and scatter to DD order).  The vector is
 // staged in vs; the columns, padded to a power of two P >= n_J, take P threads
 // each of the NT / P parts, and part q sums its share of the rows of A_J; the
-// parts' partial sums (in red) are added in a fixed order.
-template <typename T, int NT, int GROUPS>
+// parts' partial sums (in red) are added in a fixed order.  RB right-hand sides
+// per pass (vs: RB vectors kSmallN + kSmallR apart, red: RB x NT), each with its
+// single-column sequence of multiply-adds.
+template <typename T, int NT, int GROUPS, int RB>
 __device__ void cbwd_small_cta(const CView<T>& cf, int J, T* vs, T* red, const T* yf, T* xf, T* y_dd, int64_t ldy,
                                int32_t nrhs, T* stg, int cap) {
     static_assert(NT % kSmallN == 0 && NT <= 1024, "whole parts per column");
+    constexpr int VS = kSmallN + kSmallR;
     const int gt = threadIdx.x % NT;
     const int32_t a0 = cf.c0[J], nJ = cf.c0[J + 1] - a0;
     const int64_t nr = cf.r_off[J + 1] - cf.r_off[J], rtot = nJ + nr;
@@ -520,13 +557,18 @@ __device__ void cbwd_small_cta(const CView<T>& cf, int J, T* vs, T* red, const T
     while (P < nJ) P *= 2;
     const int parts = NT / P, part = gt / P, c = gt % P;
     const int64_t len = (rtot + parts - 1) / parts, rb = part * len, re = min(rtot, rb + len);
-    for (int j = 0; j < nrhs; ++j) {
-        const T* x = xf + (int64_t)j * cf.s;
-        const T* y = yf + a0 + (int64_t)j * cf.s;
-        for (int64_t r = gt; r < rtot; r += NT) vs[r] = r < nJ ? y[r] : -x[R[r - nJ]];
-        if (j == 0 && staged) stage_wait();
+    for (int j0 = 0; j0 < nrhs; j0 += RB) {
+        const int nb = min(RB, nrhs - j0);
+        for (int b = 0; b < nb; ++b) {
+            const T* x = xf + (int64_t)(j0 + b) * cf.s;
+            const T* y = yf + a0 + (int64_t)(j0 + b) * cf.s;
+            for (int64_t r = gt; r < rtot; r += NT) vs[b * VS + r] = r < nJ ? y[r] : -x[R[r - nJ]];
+        }
+        if (j0 == 0 && staged) stage_wait();
         group_sync<NT, GROUPS>();
-        T acc = T(0);
+        T acc[RB];
+#pragma unroll
+        for (int b = 0; b < RB; ++b) acc[b] = T(0);
         if (c < nJ) {
             // rows of the diagonal block: (L_JJ^{-1})[r, c] for r >= c
             const T* Dc = D + packed_col(c, nJ) - c;
@@ -537,9 +579,15 @@ __device__ void cbwd_small_cta(const CView<T>& cf, int J, T* vs, T* red, const T
 #pragma unroll
                 for (int u = 0; u < 8; ++u) a[u] = Dc[r + u];
 #pragma unroll
-                for (int u = 0; u < 8; ++u) acc += a[u] * vs[r + u];
+                for (int u = 0; u < 8; ++u)
+#pragma unroll
+                    for (int b = 0; b < RB; ++b) acc[b] += a[u] * vs[b * VS + r + u];
             }
-            for (; r < de; ++r) acc += Dc[r] * vs[r];
+            for (; r < de; ++r) {
+                const T a = Dc[r];
+#pragma unroll
+                for (int b = 0; b < RB; ++b) acc[b] += a * vs[b * VS + r];
+            }
             // rows of the panel: M_J[r - n_J, c]
             r = max(rb, (int64_t)nJ);
             for (; r + 7 < re; r += 8) {
@@ -547,18 +595,26 @@ __device__ void cbwd_small_cta(const CView<T>& cf, int J, T* vs, T* red, const T
 #pragma unroll
                 for (int u = 0; u < 8; ++u) a[u] = Pn[(r + u - nJ) * nJ + c];
 #pragma unroll
-                for (int u = 0; u < 8; ++u) acc += a[u] * vs[r + u];
+                for (int u = 0; u < 8; ++u)
+#pragma unroll
+                    for (int b = 0; b < RB; ++b) acc[b] += a[u] * vs[b * VS + r + u];
             }
-            for (; r < re; ++r) acc += Pn[(r - nJ) * nJ + c] * vs[r];
+            for (; r < re; ++r) {
+                const T a = Pn[(r - nJ) * nJ + c];
+#pragma unroll
+                for (int b = 0; b < RB; ++b) acc[b] += a * vs[b * VS + r];
+            }
         }
-        red[gt] = acc;
+#pragma unroll
+        for (int b = 0; b < RB; ++b) red[b * NT + gt] = acc[b];
         group_sync<NT, GROUPS>();
-        for (int cc = gt; cc < nJ; cc += NT) {
-            T v = T(0);
-            for (int q = 0; q < parts; ++q) v += red[q * P + cc];
-            xf[a0 + cc + (int64_t)j * cf.s] = v;
-            if (y_dd) y_dd[cf.cperm[a0 + cc] + (int64_t)j * ldy] = v;
-        }
+        for (int cc = gt; cc < nJ; cc += NT)
+            for (int b = 0; b < nb; ++b) {
+                T v = T(0);
+                for (int q = 0; q < parts; ++q) v += red[b * NT + q * P + cc];
+                xf[a0 + cc + (int64_t)(j0 + b) * cf.s] = v;
+                if (y_dd) y_dd[cf.cperm[a0 + cc] + (int64_t)(j0 + b) * ldy] = v;
+            }
         group_sync<NT, GROUPS>();
     }
 }
@@ -582,34 +638,58 @@ k_cfwd_level(const CView<T> cf, int32_t t0, int32_t p0, int32_t np, const T* g, 
                          rbmax, red, g, ldg, xf, nrhs);
 }
 
+// t_J = g_J - (gathered panel products) for every supernode of a level, once, into
+// cf.tws: block (q, c) takes entries c * 256 .. c * 256 + 255 of the (position,
+// right-hand side) pairs of the level's q-th supernode.  The per-level forward tasks
+// then read t_J instead of each gathering it again.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_cfwd_gather(const CView<T> cf, int32_t s0, const T* g, int64_t ldg, int32_t nrhs) {
+    const int32_t J = cf.lev_sn[s0 + blockIdx.x];
+    const int32_t a0 = cf.c0[J], nJ = cf.c0[J + 1] - a0;
+    const int64_t e = (int64_t)blockIdx.y * 256 + threadIdx.x;
+    if (e >= (int64_t)nJ * nrhs) return;
+    const int32_t i = (int32_t)(e % nJ), j = (int32_t)(e / nJ);
+    const int32_t pos = a0 + i;
+    const T* w = cf.wbuf + (int64_t)j * cf.nrow;
+    cf.tws[pos + (int64_t)j * cf.s] =
+        g[cf.cperm[pos] + (int64_t)j * ldg] - gather_sum(w, cf.seg_row, cf.seg_ptr[pos], cf.seg_ptr[pos + 1]);
+}
+
 // backward: one CTA per column task, 16 (FP32) or 8 (FP64) panel loads in flight per
 // lane for one right-hand side, 4 for a block of four
 template <typename T, int NW>
 __global__ void __launch_bounds__(NW * 32, NW == 8 ? 4 : 1)
 k_cbwd_level(const CView<T> cf, int32_t t0, const T* yf, T* xf, T* y_dd, int64_t ldy, int32_t nrhs) {
     __shared__ T red[NW][33];
-    __shared__ T us[4 * 32];
-    cbwd_task_cta<T, NW, sizeof(T) == 4 ? 16 : 8, 4>(cf, cf.tasks[t0 + blockIdx.x], us, true, red, yf, xf, y_dd, ldy,
+    __shared__ T us[8 * 32];
+    cbwd_task_cta<T, NW, sizeof(T) == 4 ? 16 : 8, 4>(cf, cf.tasks[t0 + blockIdx.x], us, 8, red, yf, xf, y_dd, ldy,
                                                       nrhs);
 }
 
-// dynamic shared memory: the stage buffer of cap elements
+// right-hand sides per pass of the fused small levels' per-level kernels
+constexpr int kSmallRBf = 8, kSmallRBb = 4;
+
+// dynamic shared memory: t_J of kSmallRBf right-hand sides, then the stage buffer of cap elements
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
 k_cfwd_small(const CView<T> cf, int32_t s0, const T* g, int64_t ldg, T* xf, int32_t nrhs, int32_t cap) {
     extern __shared__ __align__(16) unsigned char csm[];
-    __shared__ T ts[kSmallN];
-    cfwd_small_cta<T, kThreads, 1>(cf, cf.lev_sn[s0 + blockIdx.x], ts, g, ldg, xf, nrhs, reinterpret_cast<T*>(csm),
-                                   cap);
+    T* ts = reinterpret_cast<T*>(csm);
+    cfwd_small_cta<T, kThreads, 1, kSmallRBf>(cf, cf.lev_sn[s0 + blockIdx.x], ts, g, ldg, xf, nrhs,
+                                              ts + kSmallRBf * kSmallN, cap);
 }
 
+// dynamic shared memory: kSmallRBb vectors of kSmallN + kSmallR, kSmallRBb x kThreads partial
+// sums, then the stage buffer of cap elements
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
 k_cbwd_small(const CView<T> cf, int32_t s0, const T* yf, T* xf, T* y_dd, int64_t ldy, int32_t nrhs, int32_t cap) {
     extern __shared__ __align__(16) unsigned char csm[];
-    __shared__ T vs[kSmallN + kSmallR], red[kThreads];
-    cbwd_small_cta<T, kThreads, 1>(cf, cf.lev_sn[s0 + blockIdx.x], vs, red, yf, xf, y_dd, ldy, nrhs,
-                                   reinterpret_cast<T*>(csm), cap);
+    T* vs = reinterpret_cast<T*>(csm);
+    T* red = vs + kSmallRBb * (kSmallN + kSmallR);
+    cbwd_small_cta<T, kThreads, 1, kSmallRBb>(cf, cf.lev_sn[s0 + blockIdx.x], vs, red, yf, xf, y_dd, ldy, nrhs,
+                                              red + kSmallRBb * kThreads, cap);
 }
 
 
@@ -820,7 +900,7 @@ k_cfwd_persistent(const CView<T> cf, const T* g, int64_t ldg, T* xf, int32_t nrh
             const int grp = threadIdx.x / kSmallT;
             T* gs = sm + grp * ((int64_t)kSmallN + cf.stage_cap);
             for (int q = blockIdx.x * kSmallG + grp; q < ns; q += gridDim.x * kSmallG)
-                cfwd_small_cta<T, kSmallT, kSmallG>(cf, cf.lev_sn[s0 + q], gs, g, ldg, xf, nrhs, gs + kSmallN,
+                cfwd_small_cta<T, kSmallT, kSmallG, 1>(cf, cf.lev_sn[s0 + q], gs, g, ldg, xf, nrhs, gs + kSmallN,
                                                     cf.stage_cap);
         } else {
             const int t0 = cf.lev_task_ptr[l], nt = cf.lev_task_ptr[l + 1] - t0;
@@ -828,8 +908,8 @@ k_cfwd_persistent(const CView<T> cf, const T* g, int64_t ldg, T* xf, int32_t nrh
             any = nt + np > 0;
             for (int q = blockIdx.x; q < np + nt; q += gridDim.x) {
                 const bool pan = q < np;
-                cfwd_task_cta<T, kPersW>(cf, pan ? cf.ptasks[p0 + q] : cf.tasks[t0 + q - np], pan, sm, cf.pers_tstride,
-                                         cf.pers_rb, red, g, ldg, xf, nrhs);
+                cfwd_task_cta<T, kPersW, 4>(cf, pan ? cf.ptasks[p0 + q] : cf.tasks[t0 + q - np], pan, sm,
+                                            cf.pers_tstride, cf.pers_rb, red, g, ldg, xf, nrhs);
             }
         }
         if (any && --steps_left > 0) grid_barrier(cf.bar, ++round * gridDim.x, cf.err, cf.spin);
@@ -852,13 +932,13 @@ k_cbwd_persistent(const CView<T> cf, const T* yf, T* xf, T* y_dd, int64_t ldy, i
             const int grp = threadIdx.x / kSmallT;
             T* gs = sm + grp * ((int64_t)kSmallN + kSmallR + kSmallT + cf.stage_cap);
             for (int q = blockIdx.x * kSmallG + grp; q < ns; q += gridDim.x * kSmallG)
-                cbwd_small_cta<T, kSmallT, kSmallG>(cf, cf.lev_sn[s0 + q], gs, gs + kSmallN + kSmallR, yf, xf, y_dd,
+                cbwd_small_cta<T, kSmallT, kSmallG, 1>(cf, cf.lev_sn[s0 + q], gs, gs + kSmallN + kSmallR, yf, xf, y_dd,
                                                     ldy, nrhs, gs + kSmallN + kSmallR + kSmallT, cf.stage_cap);
         } else {
             const int t0 = cf.lev_task_ptr[l], nt = cf.lev_task_ptr[l + 1] - t0;
             any = nt > 0;
             for (int q = blockIdx.x; q < nt; q += gridDim.x)
-                cbwd_task_cta<T, kPersW, 8, 4>(cf, cf.tasks[t0 + q], sm, true, red, yf, xf, y_dd, ldy, nrhs);
+                cbwd_task_cta<T, kPersW, 8, 4, 4>(cf, cf.tasks[t0 + q], sm, 4, red, yf, xf, y_dd, ldy, nrhs);
         }
         if (any && --steps_left > 0) grid_barrier(cf.bar, ++round * gridDim.x, cf.err, cf.spin);
     }
@@ -888,7 +968,7 @@ __host__ __device__ inline int lr_blocks(int32_t s) {
 // thread t: U column kk0 + t % 64, right-hand sides j0 + 8 (t / 64) .. + 7
 template <typename T>
 __global__ void __launch_bounds__(256)
-k_lr_vt(int32_t s, int32_t k, int32_t nrhs, const T* __restrict__ U, const T* __restrict__ w, T* part) {
+k_lr_vt(int32_t s, int32_t k, int32_t nrhs, const T* __restrict__ U, const T* __restrict__ w, int64_t ldw, T* part) {
     __shared__ T su[kLrCh][kLrK + 1];
     __shared__ T sw[kLrCh][kLrJ + 1];
     const int kk0 = blockIdx.y * kLrK, j0 = blockIdx.z * kLrJ;
@@ -913,7 +993,7 @@ k_lr_vt(int32_t s, int32_t k, int32_t nrhs, const T* __restrict__ U, const T* __
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int col = lc + 8 * q;
-            pw[q] = (i < r1 && col < jn) ? w[i + (int64_t)(j0 + col) * s] : T(0);
+            pw[q] = (i < r1 && col < jn) ? w[i + (int64_t)(j0 + col) * ldw] : T(0);
         }
     };
     if (r0 < r1) fetch(r0);
@@ -957,14 +1037,15 @@ __global__ void k_lr_vt_fin(int32_t k, int32_t nrhs, int32_t G, const T* __restr
 // thread = row i, JG right-hand sides (a block's columns j0 .. j0 + JG - 1 of nrhs)
 template <typename T, int JG>
 __global__ void __launch_bounds__(256)
-k_lr_update(int32_t s, int32_t k, int32_t nrhs, const T* __restrict__ U, const T* __restrict__ vk, T cinv, T* w) {
+k_lr_update(int32_t s, int32_t k, int32_t nrhs, const T* __restrict__ U, const T* __restrict__ vk, T cinv, T* w,
+            int64_t ldw) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= s) return;
     const int j0 = blockIdx.y * JG;
     const int jn = min(JG, nrhs - j0);
     T acc[JG];
 #pragma unroll
-    for (int q = 0; q < JG; ++q) acc[q] = q < jn ? cinv * w[i + (int64_t)(j0 + q) * s] : T(0);
+    for (int q = 0; q < JG; ++q) acc[q] = q < jn ? cinv * w[i + (int64_t)(j0 + q) * ldw] : T(0);
     for (int kk = 0; kk < k; ++kk) {
         const T u = U[i + (int64_t)kk * s];
 #pragma unroll
@@ -973,7 +1054,7 @@ k_lr_update(int32_t s, int32_t k, int32_t nrhs, const T* __restrict__ U, const T
     }
 #pragma unroll
     for (int q = 0; q < JG; ++q)
-        if (q < jn) w[i + (int64_t)(j0 + q) * s] = acc[q];
+        if (q < jn) w[i + (int64_t)(j0 + q) * ldw] = acc[q];
 }
 
 // ------------------------------------------------------------------ helpers
@@ -1275,6 +1356,7 @@ CView<T> make_view(const DevCFactor<T>& cf, int32_t nsteps) {
     v.panel = cf.panel;
     v.dinv = cf.dinv;
     v.wbuf = cf.wbuf;
+    v.tws = nullptr;
     v.tasks = cf.tasks;
     v.ptasks = cf.ptasks;
     v.lev_task_ptr = cf.d_lev_task_ptr;
@@ -1359,23 +1441,36 @@ cudaError_t launch_c_forward(const DevCFactor<T>& cf, const T* g_dd, int64_t ldg
             const int s0 = cf.lev_sn_ptr[l], ns = cf.lev_sn_ptr[l + 1] - s0;
             if (ns == 0) continue;
             const int32_t cap = cf.lev_stage[l];
-            k_cfwd_small<T><<<ns, kThreads, cap * sizeof(T), st>>>(v, s0, g_dd, ldg, xf, nrhs, cap);
+            const size_t sm = ((size_t)kSmallRBf * kSmallN + cap) * sizeof(T);
+            if (sm > 48 * 1024 && !raise_smem_once((const void*)k_cfwd_small<T>)) return cudaErrorInvalidValue;
+            k_cfwd_small<T><<<ns, kThreads, sm, st>>>(v, s0, g_dd, ldg, xf, nrhs, cap);
             counted();
             continue;
         }
         const int t0 = cf.lev_task_ptr[l], nt = cf.lev_task_ptr[l + 1] - t0;
         const int p0 = cf.lev_ptask_ptr[l], np = cf.lev_ptask_ptr[l + 1] - p0;
         if (nt + np == 0) continue;
-        // blocks of four right-hand sides share each matrix load when t_J of four fits
+        // t_J of the level's supernodes, once (every task of a supernode reads it)
+        CView<T> vl = v;
+        if (cf.tws && cf.lev_maxn[l] > 0) {
+            vl.tws = cf.tws;                  // the gather writes it, the level's tasks read it
+            const int s0 = cf.lev_sn_ptr[l], ns = cf.lev_sn_ptr[l + 1] - s0;
+            const unsigned chunks = (unsigned)(((int64_t)cf.lev_maxn[l] * nrhs + 255) / 256);
+            k_cfwd_gather<T><<<dim3(ns, chunks), 256, 0, st>>>(vl, s0, g_dd, ldg, nrhs);
+            counted();
+        }
+        // blocks of eight or four right-hand sides share each matrix load when t_J of that many fits
         const bool wide = nt + np <= cf.nsm;
         const void* kern = wide ? (const void*)k_cfwd_level<T, 32> : (const void*)k_cfwd_level<T, 8>;
-        int32_t rbmax = (nrhs >= 4 && 4 * (size_t)cf.max_n * sizeof(T) <= kLevSmem) ? 4 : 1;
-        if (rbmax == 4 && 4 * (size_t)cf.max_n * sizeof(T) > 40 * 1024 && !raise_smem_once(kern)) rbmax = 1;
+        int32_t rbmax = 1;
+        if (nrhs >= 8 && 8 * (size_t)cf.max_n * sizeof(T) <= kLevSmem) rbmax = 8;
+        else if (nrhs >= 4 && 4 * (size_t)cf.max_n * sizeof(T) <= kLevSmem) rbmax = 4;
+        if (rbmax > 1 && rbmax * (size_t)cf.max_n * sizeof(T) > 40 * 1024 && !raise_smem_once(kern)) rbmax = 1;
         const size_t smem = (size_t)rbmax * cf.max_n * sizeof(T);
         if (!wide)
-            k_cfwd_level<T, 8><<<nt + np, 256, smem, st>>>(v, t0, p0, np, g_dd, ldg, xf, nrhs, cf.max_n, rbmax);
+            k_cfwd_level<T, 8><<<nt + np, 256, smem, st>>>(vl, t0, p0, np, g_dd, ldg, xf, nrhs, cf.max_n, rbmax);
         else
-            k_cfwd_level<T, 32><<<nt + np, 1024, smem, st>>>(v, t0, p0, np, g_dd, ldg, xf, nrhs, cf.max_n, rbmax);
+            k_cfwd_level<T, 32><<<nt + np, 1024, smem, st>>>(vl, t0, p0, np, g_dd, ldg, xf, nrhs, cf.max_n, rbmax);
         counted();
     }
     if (cf.nT > 0) {
@@ -1407,7 +1502,9 @@ cudaError_t launch_c_backward(const DevCFactor<T>& cf, const T* yf, T* xf, T* y_
             const int s0 = cf.lev_sn_ptr[l], ns = cf.lev_sn_ptr[l + 1] - s0;
             if (ns == 0) continue;
             const int32_t cap = cf.lev_stage[l];
-            k_cbwd_small<T><<<ns, kThreads, cap * sizeof(T), st>>>(v, s0, yf, xf, y_dd, ldy, nrhs, cap);
+            const size_t sm = ((size_t)kSmallRBb * (kSmallN + kSmallR + kThreads) + cap) * sizeof(T);
+            if (sm > 48 * 1024 && !raise_smem_once((const void*)k_cbwd_small<T>)) return cudaErrorInvalidValue;
+            k_cbwd_small<T><<<ns, kThreads, sm, st>>>(v, s0, yf, xf, y_dd, ldy, nrhs, cap);
             counted();
             continue;
         }
@@ -1422,30 +1519,48 @@ cudaError_t launch_c_backward(const DevCFactor<T>& cf, const T* yf, T* xf, T* y_
     return cudaGetLastError();
 }
 
+// the two passes of K4 on any s x k column-major basis Ub (U_k in the U-form, Z_k in
+// the Z-form of Proposition 4.3) and a block w of leading dimension ldw:
+//   lowrank_v:      op.vk = d o (Ub^T w)
+//   lowrank_update: w = cinv w + Ub op.vk
+template <typename T>
+cudaError_t launch_lowrank_v(const DevOperator<T>& op, int32_t s, int32_t k, const T* Ub, const T* w, int64_t ldw,
+                             int32_t nrhs, cudaStream_t st) {
+    if (s == 0 || k == 0) return cudaSuccess;
+    const int G = lr_blocks(s);
+    k_lr_vt<T><<<dim3(G, (k + kLrK - 1) / kLrK, (nrhs + kLrJ - 1) / kLrJ), 256, 0, st>>>(s, k, nrhs, Ub, w, ldw,
+                                                                                       op.part);
+    k_lr_vt_fin<T><<<blocks_for((int64_t)k * nrhs), kThreads, 0, st>>>(k, nrhs, G, op.part, op.dvec, op.vk);
+    counted(2);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_lowrank_update(const DevOperator<T>& op, int32_t s, int32_t k, const T* Ub, T* w, int64_t ldw,
+                                  int32_t nrhs, cudaStream_t st) {
+    if (s == 0) return cudaSuccess;
+    const dim3 grid((unsigned)((s + 255) / 256));
+    // every column sees the same multiply-adds in the same order whatever JG is
+    if (nrhs == 1) {
+        k_lr_update<T, 1><<<grid, 256, 0, st>>>(s, k, nrhs, Ub, op.vk, op.cinv, w, ldw);
+    } else if (nrhs <= 8) {
+        k_lr_update<T, 8><<<grid, 256, 0, st>>>(s, k, nrhs, Ub, op.vk, op.cinv, w, ldw);
+    } else {
+        k_lr_update<T, 32><<<dim3(grid.x, (nrhs + 31) / 32), 256, 0, st>>>(s, k, nrhs, Ub, op.vk, op.cinv, w, ldw);
+    }
+    counted();
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_lowrank(const DevOperator<T>& op, int32_t s, int32_t k, T* w, int32_t nrhs, cudaStream_t st) {
     if (s == 0) return cudaSuccess;
     if constexpr (std::is_same<T, float>::value) {
         if (lowrank_tc_usable(op, k, nrhs)) return launch_lowrank_tc(op, s, k, w, nrhs, st);
     }
-    if (k > 0) {
-        const int G = lr_blocks(s);
-        k_lr_vt<T><<<dim3(G, (k + kLrK - 1) / kLrK, (nrhs + kLrJ - 1) / kLrJ), 256, 0, st>>>(s, k, nrhs, op.U, w,
-                                                                                           op.part);
-        k_lr_vt_fin<T><<<blocks_for((int64_t)k * nrhs), kThreads, 0, st>>>(k, nrhs, G, op.part, op.dvec, op.vk);
-        counted(2);
-    }
-    const dim3 grid((unsigned)((s + 255) / 256));
-    // every column sees the same multiply-adds in the same order whatever JG is
-    if (nrhs == 1) {
-        k_lr_update<T, 1><<<grid, 256, 0, st>>>(s, k, nrhs, op.U, op.vk, op.cinv, w);
-    } else if (nrhs <= 8) {
-        k_lr_update<T, 8><<<grid, 256, 0, st>>>(s, k, nrhs, op.U, op.vk, op.cinv, w);
-    } else {
-        k_lr_update<T, 32><<<dim3(grid.x, (nrhs + 31) / 32), 256, 0, st>>>(s, k, nrhs, op.U, op.vk, op.cinv, w);
-    }
-    counted();
-    return cudaGetLastError();
+    cudaError_t e = launch_lowrank_v<T>(op, s, k, op.U, w, s, nrhs, st);
+    if (e != cudaSuccess) return e;
+    return launch_lowrank_update<T>(op, s, k, op.U, w, s, nrhs, st);
 }
 
 // elements of the first pass's partial sums for rank k and nrhs columns
@@ -1577,6 +1692,14 @@ cudaError_t launch_pcg_update_p(int32_t n, int32_t nrhs, double* p, const double
 SLR_INST(double)
 SLR_INST(float)
 #undef SLR_INST
+template cudaError_t launch_lowrank_v<double>(const DevOperator<double>&, int32_t, int32_t, const double*,
+                                              const double*, int64_t, int32_t, cudaStream_t);
+template cudaError_t launch_lowrank_v<float>(const DevOperator<float>&, int32_t, int32_t, const float*, const float*,
+                                             int64_t, int32_t, cudaStream_t);
+template cudaError_t launch_lowrank_update<double>(const DevOperator<double>&, int32_t, int32_t, const double*,
+                                                   double*, int64_t, int32_t, cudaStream_t);
+template cudaError_t launch_lowrank_update<float>(const DevOperator<float>&, int32_t, int32_t, const float*, float*,
+                                                  int64_t, int32_t, cudaStream_t);
 template cudaError_t launch_convert<double, float>(int64_t, int32_t, const double*, int64_t, float*, int64_t,
                                                    cudaStream_t);
 template cudaError_t launch_convert<float, double>(int64_t, int32_t, const float*, int64_t, double*, int64_t,

@@ -46,7 +46,8 @@ class Opts(C.Structure):
                 ("band_split", C.c_int32), ("band_slots", C.c_int32), ("band_threads", C.c_int32),
                 ("band_order", C.c_int32), ("band_factor_host", C.c_int32), ("c_persistent", C.c_int32),
                 ("c_levels_only", C.c_int32), ("host_loop", C.c_int32), ("autotune", C.c_int32),
-                ("band_mma", C.c_int32), ("spin_limit", C.c_int32), ("reserved", C.c_int32 * 7)]
+                ("zform", C.c_int32), ("band_mma", C.c_int32), ("spin_limit", C.c_int32),
+                ("reserved", C.c_int32 * 6)]
 
 
 class Info(C.Structure):
@@ -180,7 +181,7 @@ class SLR:
                  precision="fp64", nrhs_max=1, flexible_cg=False, seed=1, c_leaf=64, verbose=False,
                  band_split=0, host_loop=False, band_slots=0, c_persistent=False, autotune=False, target_kappa=0,
                  band_threads=0, c_top_zone=True, band_factor="auto", indefinite=False, band_order=0,
-                 u_dtype="fp32", band_mma="off", spin_limit=0, stream=None):
+                 u_dtype="fp32", band_mma="off", spin_limit=0, zform=False, stream=None):
         lib = load()
         self._lib = lib
         self._h = None
@@ -203,6 +204,7 @@ class SLR:
         o.band_order = int(band_order)          # band-solve cluster launch order, 0 = automatic
         o.u_dtype = U_DTYPE[u_dtype]            # low-rank products on RHS blocks: fp32, tf32, bf16
         o.band_mma = {"off": 0, "tf32": 1, "bf16": 2}[band_mma]   # band solve of RHS blocks on tensor cores
+        o.zform = int(bool(zform))              # S~^{-1} in the Z-form of Proposition 4.3
         o.spin_limit = int(spin_limit)          # polls of a grid-barrier wait, 0 = default
         self.rowptr, self.colind = _i32(rowptr), _i32(colind)
         self.val = np.ascontiguousarray(val, dtype=np.float64)

@@ -116,7 +116,7 @@ BAD_OPTIONS = [{"band_split": 3}, {"host_loop": 2}, {"band_slots": 1}, {"band_sl
                {"indefinite": 2}, {"band_order": 4}, {"band_order": -1}, {"u_dtype": 3}, {"u_dtype": -1},
                {"u_dtype": 1},                     # a tensor-core dtype needs the mixed path
                {"spin_limit": -5}, {"band_mma": 3}, {"band_mma": 1},   # tensor cores need the mixed path
-               {0: 1}, {6: 1}]
+               {"zform": 2}, {"zform": -1}, {0: 1}, {5: 1}]
 
 
 @pytest.mark.parametrize("fields", BAD_OPTIONS)

@@ -24,6 +24,10 @@ from paper_1505_04340_gb300 import SLR  # noqa: E402
 from paper_1505_04340_gb300.slr import SLRError  # noqa: E402
 
 TOL64 = 1e-10
+# The blocks B_i = L S L^T are indefinite and factored without pivoting, so the
+# FP32 solves can carry element growth that the SPD bound of tests/tolerances.py
+# does not cover; the mixed path is held to 1e-4 here and its error is printed
+# beside that bound.
 TOL32 = 1e-4
 
 CASES = {
@@ -66,7 +70,9 @@ def test_indefinite_bsolve_parity(name, precision, factor):
     assert g.get_info()["band_on_device"] == (1 if factor == "auto" else 0)
     f = np.random.default_rng(1).standard_normal((o.order.n_I, 3))
     t = g.bsolve(cu(f)).cpu().numpy()
-    assert rel(t, o.bsolve.solve(f)) <= (TOL64 if precision == "fp64" else TOL32)
+    err = rel(t, o.bsolve.solve(f))
+    print(f"indefinite bsolve {precision}: {err:.2e}")
+    assert err <= (TOL64 if precision == "fp64" else TOL32)
 
 
 @pytest.mark.parametrize("name", list(CASES))
@@ -78,7 +84,9 @@ def test_indefinite_apply_parity_with_oracle_pairs(name, precision):
     g.set_lowrank(o.Z(), o.lam, o.theta)       # lambda_1 > 1 here: accepted in indefinite mode
     r = np.random.default_rng(3).standard_normal((o.App.shape[0], 2))
     z = g.apply(cu(r)).cpu().numpy()
-    assert rel(z, o.apply(r)) <= (TOL64 if precision == "fp64" else TOL32)
+    err = rel(z, o.apply(r))
+    print(f"indefinite apply {precision}: {err:.2e}")
+    assert err <= (TOL64 if precision == "fp64" else TOL32)
 
 
 @pytest.mark.parametrize("name", list(CASES))

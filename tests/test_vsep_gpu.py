@@ -21,7 +21,7 @@ if not torch.cuda.is_available():
 from paper_1505_04340_gb300 import SLR  # noqa: E402
 
 TOL64 = 1e-10
-TOL32 = 1e-4
+from tolerances import tol32  # noqa: E402
 
 CASES = {
     "2d-vsep": ((32, 32), (2, 2), 8),
@@ -50,7 +50,7 @@ def test_vsep_solves_and_apply_parity(name, precision):
     o = OracleSLR(P.rowptr, P.colind, P.val, P.part, P.nparts, P.k, lanczos_steps=P.lanczos_steps)
     g = SLR(P.rowptr, P.colind, P.val, P.part, P.nparts, k=P.k, lanczos_steps=P.lanczos_steps, precision=precision,
             nrhs_max=2)
-    tol = TOL64 if precision == "fp64" else TOL32
+    tol = TOL64 if precision == "fp64" else tol32(g.get_info())
     assert np.array_equal(g.perm(), o.order.perm)
     assert g.get_info()["s"] == int(np.sum(P.part < 0))
     rng = np.random.default_rng(7)
