@@ -23,13 +23,13 @@
 // warp releases a buffer on its "empty" mbarrier when done with it; thread 0
 // refills a buffer once all warps have released it, so copies run ahead of the
 // slowest warp across planes and phases with no CTA-wide barrier per chunk.
-// The cluster exchange between phases is a split barrier: arrive after the
-// stores into the peers, wait once the next block's first data has landed.
-// Every wait is a bounded spin that sets a device status word instead of
-// hanging.  Warp w takes the columns c = w (mod 16) of every row block, so a
-// warp's partial sums (added once per phase) do not depend on the chunking.
-// The full input vector of a phase is assembled in every CTA through
-// distributed shared memory.
+// Each phase's input vector (t, or y/x) reaches every CTA of the cluster by
+// st.async stores into distributed shared memory that complete bytes on the
+// receiver's mbarrier, so a CTA waits only for the vector it reads and no
+// cluster-wide barrier is taken per phase.  Every wait is a bounded spin that
+// sets a device status word instead of hanging.  Warp w takes the columns
+// c = w (mod warps) of every row block, so a warp's partial sums (added once
+// per phase) do not depend on the chunking.
 #include "slr_band_kernel.cuh"
 
 namespace slr {

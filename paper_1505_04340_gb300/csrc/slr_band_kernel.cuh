@@ -67,23 +67,39 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
         "l"(src), "r"(bytes), "r"(smem_u32(bar))
         : "memory");
 }
+// Wait with acquire at cluster scope: the bytes it waits for were stored by
+// peers with st.async, whose complete_tx releases at cluster scope.
+__device__ __forceinline__ bool mbar_try_wait_cluster(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Address of the same shared-memory location in cluster CTA `rank`.
+__device__ __forceinline__ uint32_t peer_addr(uint32_t a, int rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    return r;
+}
+// Store one value into a cluster CTA's shared memory; its bytes complete on
+// that CTA's mbarrier `bar` (both addresses in the shared::cluster window).
+__device__ __forceinline__ void st_async(uint32_t addr, float v, uint32_t bar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];" ::"r"(addr),
+                 "r"(__float_as_uint(v)), "r"(bar)
+                 : "memory");
+}
+__device__ __forceinline__ void st_async(uint32_t addr, double v, uint32_t bar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b64 [%0], %1, [%2];" ::"r"(addr),
+                 "l"(__double_as_longlong(v)), "r"(bar)
+                 : "memory");
+}
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
-
-// Split cluster barrier: arrive after a phase's stores into the peers, wait just
-// before the next phase reads them (with one CTA: a CTA barrier at the wait).
-template <int G>
-__device__ __forceinline__ void cluster_arrive() {
-    if constexpr (G > 1) asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
-}
-template <int G>
-__device__ __forceinline__ void cluster_wait() {
-    if constexpr (G > 1) {
-        asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
-    } else {
-        __syncthreads();
-    }
-}
 
 template <int G>
 __device__ __forceinline__ void cluster_barrier() {
@@ -144,16 +160,19 @@ k_band_solve2(const BandBlock* __restrict__ blocks, const T* __restrict__ fac, c
     // ---- shared memory carve-up: barriers, tables and vectors, then the ring
     uint64_t* full = reinterpret_cast<uint64_t*>(smem);              // [kMaxBuf]
     uint64_t* empty = full + kMaxBuf;                                 // [kMaxBuf]
-    int* segU = reinterpret_cast<int*>(empty + kMaxBuf);             // [kRB+1] first segment of row block rb
+    uint64_t* vbar = empty + kMaxBuf;                                 // [3] t (two buffers), y/x
+    int* segU = reinterpret_cast<int*>(vbar + 4);                    // [kRB+1] first segment of row block rb
     int* segL = segU + (kRB + 1);                                    // [kRB+1]
     int* hdr = segL + (kRB + 1);                                     // nU, nL, segments per chunk, abort
     uintptr_t vp = reinterpret_cast<uintptr_t>(hdr + 4);
     vp = (vp + 15) & ~uintptr_t(15);
     T* vst = reinterpret_cast<T*>(vp);              // [NR][W] y_{J-1} (fwd) / x_{J+1} (bwd), whole plane
-    T* vt = vst + NR * W;                           // [NR][W] t, whole plane
-    T* part = vt + NR * W;                          // [kW][NR][256] per-warp partial sums
+    T* vt = vst + NR * W;                           // [2][NR][W] t, whole plane, by phase parity
+    T* part = vt + 2 * NR * W;                      // [kW][NR][256] per-warp partial sums
     uintptr_t rp = reinterpret_cast<uintptr_t>(part + kW * NR * 256);
     unsigned char* ring = reinterpret_cast<unsigned char*>((rp + 127) & ~uintptr_t(127));   // nbuf x slot bytes
+    // bytes of one plane vector: every row of the plane has one owner in the cluster
+    const uint32_t vbytes = (uint32_t)(W * NR * (int)sizeof(T));
 
     Geom q;
     q.W = W;
@@ -187,6 +206,12 @@ k_band_solve2(const BandBlock* __restrict__ blocks, const T* __restrict__ fac, c
         for (int i = 0; i < nbuf; ++i) {
             mbar_init(&full[i], 1);
             mbar_init(&empty[i], kW);
+        }
+        // one arrival (this thread, arming the phase with the vector's bytes) and
+        // the peers' st.async bytes complete each phase of a vector barrier
+        for (int i = 0; i < 3; ++i) {
+            mbar_init(&vbar[i], 1);
+            mbar_arrive_expect_tx(&vbar[i], vbytes);
         }
         fence_mbar_init();
     }
@@ -225,8 +250,8 @@ k_band_solve2(const BandBlock* __restrict__ blocks, const T* __restrict__ fac, c
     };
     // After a bounded wait expires the CTA aborts: the status word and the
     // CTA's abort flag (hdr[3]) are set, no further copy is issued, the block
-    // products are skipped (the barrier sequence is kept, so no peer waits on
-    // this CTA), and before it exits thread 0 waits for the copies it issued.
+    // products and the vector waits are skipped, and before it exits thread 0
+    // waits for the copies it issued.
     volatile int* abort_flag = hdr + 3;
     auto wait_bar = [&](uint64_t* bar, uint32_t par) -> bool {
         long long it = 0;
@@ -274,22 +299,61 @@ k_band_solve2(const BandBlock* __restrict__ blocks, const T* __restrict__ fac, c
             }
         }
     };
-    auto peer = [&](T* p, int r) -> T* {
-        if constexpr (G > 1) return cg::this_cluster().map_shared_rank(p, r);
-        return p;
+    // The plane vector of a phase reaches every CTA of the cluster by st.async:
+    // each owner stores its rows into every CTA's copy, and the bytes complete
+    // on that CTA's vector barrier, armed by its thread 0 with the vector's size.
+    // No cluster-wide barrier is taken per phase.  A CTA re-arms a barrier for
+    // its next phase as soon as it has seen the current one complete: the next
+    // phase's stores into it come only after the peers have received this CTA's
+    // own next rows, which it sends after consuming the current phase.  For the
+    // same reason the t vector has two buffers (by phase parity): the forward
+    // pass's last t and the backward pass's first t have no exchange of y
+    // between them, so a fast peer can send the second before a slow CTA has
+    // read the first.  y/x needs one buffer (an exchange of t always lies between
+    // two of its phases).  A wait that expires sets the abort flag; the barrier
+    // is then left un-armed (thread 0 never arrives twice in one phase).
+    auto wait_vec = [&](uint64_t* bar, uint32_t par) -> bool {
+        bool ok = false;
+        if (!*abort_flag) {
+            long long it = 0;
+            ok = true;
+            while (!mbar_try_wait_cluster(bar, par)) {
+                if (++it > kSpin) {
+                    atomicExch(err, 1);
+                    *abort_flag = 1;
+                    ok = false;
+                    break;
+                }
+            }
+            if (ok && tid == 0) mbar_arrive_expect_tx(bar, vbytes);
+        }
+        return __all_sync(0xffffffffu, ok);
+    };
+    // owner rows of a phase into vector vec (element j W + own_r) of every CTA.
+    // An aborted CTA sends nothing more: its peers' waits for its rows then
+    // expire and they abort in turn, so at most a phase or two of bytes reach a
+    // barrier this CTA no longer arms.
+    auto send = [&](T* vec, uint64_t* bar, int j, int r, T v) {
+        if (*abort_flag) return;
+        const uint32_t a = smem_u32(vec + j * W + r), mb = smem_u32(bar);
+        if constexpr (G > 1) {
+#pragma unroll
+            for (int pr = 0; pr < G; ++pr) st_async(peer_addr(a, pr), v, peer_addr(mb, pr));
+        } else {
+            st_async(a, v, mb);
+        }
     };
 
     if (tid == 0)
         while (issued < nbuf && issued < total) issue_next();
-    // every CTA of the cluster is running before anyone stores into a peer's shared memory
+    // every CTA of the cluster has armed its barriers before any st.async reaches it
     cluster_barrier<G>();
 
     int k = 0;
-    bool pending = false;      // a cluster arrive waits for its wait (uniform in the cluster)
     T acc[kRB][NR];
-    // acc[rb][j] += sum over the chunks of one block of M[lr][cc] * vin[j][cc], lanes = rows
-    // acc[rb][j] = sum over the block's segments of row block rb of seg[lane] * vin[j][column]
-    auto run_block = [&](int type, int plane, const T* vin) {
+    // acc[rb][j] = sum over the block's segments of row block rb of seg[lane] * vin[j][column];
+    // vin is complete once phase `par` of vector barrier `vb` has
+    auto run_block = [&](int type, int plane, const T* vin, uint64_t* vb, uint32_t par) {
         const bool upper = (type == 0 || type == 3);
 #pragma unroll
         for (int rb = 0; rb < kRB; ++rb)
@@ -297,14 +361,15 @@ k_band_solve2(const BandBlock* __restrict__ blocks, const T* __restrict__ fac, c
             for (int j = 0; j < NR; ++j) acc[rb][j] = T(0);
         const int nch = upper ? q.nU : q.nL;
         const int* seg = upper ? segU : segL;
+        bool vok = true, waited = false;
         for (int ix = 0; ix < nch; ++ix, ++k) {
             refill(k);
             const bool landed = wait_full(k);
-            if (pending) {                 // the input vector's last stores (peers included)
-                cluster_wait<G>();
-                pending = false;
+            if (!waited) {                 // the input vector (after the block's first data)
+                vok = wait_vec(vb, par);
+                waited = true;
             }
-            if (!landed) {                 // aborted: no product on a slot that may not have landed
+            if (!landed || !vok) {         // aborted: no product
                 release(k);
                 continue;
             }
@@ -328,21 +393,16 @@ k_band_solve2(const BandBlock* __restrict__ blocks, const T* __restrict__ fac, c
             }
             release(k);
         }
+        if (!waited) wait_vec(vb, par);    // a block without chunks (a slice without rows)
 #pragma unroll
         for (int rb = 0; rb < kRB; ++rb)
 #pragma unroll
             for (int j = 0; j < NR; ++j) part[(warp * NR + j) * 256 + rb * 32 + lane] = acc[rb][j];
-        if (pending) {                     // a block without chunks (a slice without rows)
-            cluster_wait<G>();
-            pending = false;
-        }
         __syncthreads();
     };
+    // (the barrier first: owners may still be reading the previous phase's sums)
     auto zero_part = [&]() {
-        if (pending) {
-            cluster_wait<G>();
-            pending = false;
-        }
+        __syncthreads();
         for (int i = tid; i < kW * NR * 256; i += kT) part[i] = T(0);
         __syncthreads();
     };
@@ -361,35 +421,30 @@ k_band_solve2(const BandBlock* __restrict__ blocks, const T* __restrict__ fac, c
     for (int rb = 0; rb < kRB; ++rb)
         if ((tid >> 5) == rb) own_r = R0[rb] + (tid & 31);
     const bool owner = tid < 32 * nrb && own_r < W;
+    int ut = 0, uy = 0;        // phases of the t vector and of the y/x vector so far
     // =================================================================== forward
     for (int J = 0; J < c; ++J) {
         const int row = J * W + own_r;
         T pre[NR];
 #pragma unroll
         for (int j = 0; j < NR; ++j) pre[j] = (owner && row < m) ? in[b.row0 + row + j * ldi] : T(0);
-        if (J > 0) run_block(0, J, vst); else zero_part();                 // O_J y_{J-1}
+        if (J > 0) run_block(0, J, vst, &vbar[2], (uint32_t)(uy++ & 1));        // O_J y_{J-1}
+        else zero_part();
+        T* vtb = vt + (ut & 1) * NR * W;
         if (owner) {
 #pragma unroll
-            for (int j = 0; j < NR; ++j) {
-                const T t = pre[j] - part_sum(tid, j);
-#pragma unroll
-                for (int pr = 0; pr < G; ++pr) peer(vt, pr)[j * W + own_r] = t;
-            }
+            for (int j = 0; j < NR; ++j) send(vtb, &vbar[ut & 1], j, own_r, pre[j] - part_sum(tid, j));
         }
-        cluster_arrive<G>();
-        pending = true;
-        run_block(1, J, vt);                                               // D_J t
+        run_block(1, J, vtb, &vbar[ut & 1], (uint32_t)((ut >> 1) & 1));        // D_J t
+        ++ut;
         if (owner) {
 #pragma unroll
             for (int j = 0; j < NR; ++j) {
                 const T y = part_sum(tid, j);
                 if (row < m) out[b.row0 + row + j * ldo] = y;
-#pragma unroll
-                for (int pr = 0; pr < G; ++pr) peer(vst, pr)[j * W + own_r] = y;
+                if (J + 1 < c) send(vst, &vbar[2], j, own_r, y);                 // read by O_{J+1}
             }
         }
-        cluster_arrive<G>();
-        pending = true;
     }
     // =================================================================== backward
     for (int J = c - 1; J >= 0; --J) {
@@ -401,39 +456,33 @@ k_band_solve2(const BandBlock* __restrict__ blocks, const T* __restrict__ fac, c
             pre[j] = (owner && row < m) ? out[gi + j * ldo] : T(0);
             bs[j] = (owner && row < m && base) ? base[gi + j * ldb] : T(0);
         }
-        if (J < c - 1) run_block(2, J + 1, vst); else zero_part();         // O_{J+1}^T x_{J+1}
+        if (J < c - 1) run_block(2, J + 1, vst, &vbar[2], (uint32_t)(uy++ & 1));   // O_{J+1}^T x_{J+1}
+        else zero_part();
+        T* vtb = vt + (ut & 1) * NR * W;
         if (owner) {
 #pragma unroll
-            for (int j = 0; j < NR; ++j) {
-                const T t = pre[j] - part_sum(tid, j);
-#pragma unroll
-                for (int pr = 0; pr < G; ++pr) peer(vt, pr)[j * W + own_r] = t;
-            }
+            for (int j = 0; j < NR; ++j) send(vtb, &vbar[ut & 1], j, own_r, pre[j] - part_sum(tid, j));
         }
-        cluster_arrive<G>();
-        pending = true;
-        run_block(3, J, vt);                                               // D_J^T t
+        run_block(3, J, vtb, &vbar[ut & 1], (uint32_t)((ut >> 1) & 1));           // D_J^T t
+        ++ut;
         if (owner) {
 #pragma unroll
             for (int j = 0; j < NR; ++j) {
                 const T x = part_sum(tid, j);
                 if (row < m) out[gi + j * ldo] = base ? bs[j] - x : x;
-#pragma unroll
-                for (int pr = 0; pr < G; ++pr) peer(vst, pr)[j * W + own_r] = x;
+                if (J > 0) send(vst, &vbar[2], j, own_r, x);                      // read by O_J^T
             }
         }
-        cluster_arrive<G>();
-        pending = true;
     }
-    if (pending) cluster_wait<G>();    // no CTA leaves while a peer may still store into it
-    drain();                           // nor with a bulk copy still writing its shared memory
+    cluster_barrier<G>();    // no CTA leaves while a peer may still store into it
+    drain();                 // nor with a bulk copy still writing its shared memory
 }
 
 // Shared memory besides the ring (barriers, column tables, vectors, partials,
 // the ring's alignment), for planes of at most wmax rows.
 inline size_t band_fixed_bytes(int32_t wmax, int32_t nr, size_t elem, int nt) {
-    const size_t head = 2 * kMaxBuf * 8 + 2 * (kRB + 1) * 4 + 16 + 16;
-    const size_t vec = (size_t)(2 * nr * wmax + (nt / 32) * nr * 256) * elem;
+    const size_t head = 2 * kMaxBuf * 8 + 4 * 8 + 2 * (kRB + 1) * 4 + 16 + 16;
+    const size_t vec = (size_t)(3 * nr * wmax + (nt / 32) * nr * 256) * elem;
     return head + vec + 128;
 }
 
