@@ -86,8 +86,9 @@ __device__ __forceinline__ uint32_t peer_addr(uint32_t a, int rank) {
     asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
     return r;
 }
-// Store one value into a cluster CTA's shared memory; its bytes complete on
-// that CTA's mbarrier `bar` (both addresses in the shared::cluster window).
+// Store one value into another cluster CTA's shared memory; its bytes complete
+// on that CTA's mbarrier `bar` (both addresses in the shared::cluster window, in
+// the same CTA, which must not be the executing one).
 __device__ __forceinline__ void st_async(uint32_t addr, float v, uint32_t bar) {
     asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.b32 [%0], %1, [%2];" ::"r"(addr),
                  "r"(__float_as_uint(v)), "r"(bar)
@@ -171,8 +172,6 @@ k_band_solve2(const BandBlock* __restrict__ blocks, const T* __restrict__ fac, c
     T* part = vt + 2 * NR * W;                      // [kW][NR][256] per-warp partial sums
     uintptr_t rp = reinterpret_cast<uintptr_t>(part + kW * NR * 256);
     unsigned char* ring = reinterpret_cast<unsigned char*>((rp + 127) & ~uintptr_t(127));   // nbuf x slot bytes
-    // bytes of one plane vector: every row of the plane has one owner in the cluster
-    const uint32_t vbytes = (uint32_t)(W * NR * (int)sizeof(T));
 
     Geom q;
     q.W = W;
@@ -188,6 +187,15 @@ k_band_solve2(const BandBlock* __restrict__ blocks, const T* __restrict__ fac, c
     int R0[kRB];
 #pragma unroll
     for (int rb = 0; rb < kRB; ++rb) R0[rb] = rb < nrb ? 32 * b.rbmap[g][rb] : W;
+    // Every row of a plane has one owner in the cluster.  A phase of a vector
+    // barrier completes with 1 + nrb arrivals (thread 0 arming it, and each of
+    // this slice's owner warps once its rows are stored here) and the bytes of
+    // the other slices' rows, stored by their owners with st.async.
+    int my_rows = 0;
+#pragma unroll
+    for (int rb = 0; rb < kRB; ++rb)
+        if (rb < nrb) my_rows += min(32, W - R0[rb]);
+    const uint32_t rbytes = (uint32_t)((W - my_rows) * NR * (int)sizeof(T));
     if (tid == 0) {
         int a = 0, d = 0;
         for (int rb = 0; rb <= kRB; ++rb) {
@@ -207,11 +215,10 @@ k_band_solve2(const BandBlock* __restrict__ blocks, const T* __restrict__ fac, c
             mbar_init(&full[i], 1);
             mbar_init(&empty[i], kW);
         }
-        // one arrival (this thread, arming the phase with the vector's bytes) and
-        // the peers' st.async bytes complete each phase of a vector barrier
+        for (int i = 0; i < 3; ++i) mbar_init(&vbar[i], 1 + nrb);
         for (int i = 0; i < 3; ++i) {
-            mbar_init(&vbar[i], 1);
-            mbar_arrive_expect_tx(&vbar[i], vbytes);
+            if (rbytes) mbar_arrive_expect_tx(&vbar[i], rbytes);
+            else mbar_arrive(&vbar[i]);
         }
         fence_mbar_init();
     }
@@ -299,10 +306,11 @@ k_band_solve2(const BandBlock* __restrict__ blocks, const T* __restrict__ fac, c
             }
         }
     };
-    // The plane vector of a phase reaches every CTA of the cluster by st.async:
-    // each owner stores its rows into every CTA's copy, and the bytes complete
-    // on that CTA's vector barrier, armed by its thread 0 with the vector's size.
-    // No cluster-wide barrier is taken per phase.  A CTA re-arms a barrier for
+    // The plane vector of a phase reaches every CTA of the cluster: each owner
+    // stores its rows into this CTA's copy (then its warp arrives on the local
+    // vector barrier) and, by st.async, into every peer's copy, where the bytes
+    // complete on the peer's vector barrier, armed by the peer's thread 0 with
+    // the bytes it receives.  No cluster-wide barrier is taken per phase.  A CTA re-arms a barrier for
     // its next phase as soon as it has seen the current one complete: the next
     // phase's stores into it come only after the peers have received this CTA's
     // own next rows, which it sends after consuming the current phase.  For the
@@ -325,7 +333,10 @@ k_band_solve2(const BandBlock* __restrict__ blocks, const T* __restrict__ fac, c
                     break;
                 }
             }
-            if (ok && tid == 0) mbar_arrive_expect_tx(bar, vbytes);
+            if (ok && tid == 0) {
+                if (rbytes) mbar_arrive_expect_tx(bar, rbytes);
+                else mbar_arrive(bar);
+            }
         }
         return __all_sync(0xffffffffu, ok);
     };
@@ -335,12 +346,19 @@ k_band_solve2(const BandBlock* __restrict__ blocks, const T* __restrict__ fac, c
     // barrier this CTA no longer arms.
     auto send = [&](T* vec, uint64_t* bar, int j, int r, T v) {
         if (*abort_flag) return;
-        const uint32_t a = smem_u32(vec + j * W + r), mb = smem_u32(bar);
+        vec[j * W + r] = v;
         if constexpr (G > 1) {
+            const uint32_t a = smem_u32(vec + j * W + r), mb = smem_u32(bar);
 #pragma unroll
-            for (int pr = 0; pr < G; ++pr) st_async(peer_addr(a, pr), v, peer_addr(mb, pr));
-        } else {
-            st_async(a, v, mb);
+            for (int pr = 0; pr < G; ++pr)
+                if (pr != g) st_async(peer_addr(a, pr), v, peer_addr(mb, pr));
+        }
+    };
+    // an owner warp, once all its rows of a phase are stored here (all of its lanes)
+    auto arrive_local = [&](uint64_t* bar) {
+        if (warp < nrb) {
+            __syncwarp();
+            if (lane == 0 && !*abort_flag) mbar_arrive(bar);
         }
     };
 
@@ -435,6 +453,7 @@ k_band_solve2(const BandBlock* __restrict__ blocks, const T* __restrict__ fac, c
 #pragma unroll
             for (int j = 0; j < NR; ++j) send(vtb, &vbar[ut & 1], j, own_r, pre[j] - part_sum(tid, j));
         }
+        arrive_local(&vbar[ut & 1]);
         run_block(1, J, vtb, &vbar[ut & 1], (uint32_t)((ut >> 1) & 1));        // D_J t
         ++ut;
         if (owner) {
@@ -445,6 +464,7 @@ k_band_solve2(const BandBlock* __restrict__ blocks, const T* __restrict__ fac, c
                 if (J + 1 < c) send(vst, &vbar[2], j, own_r, y);                 // read by O_{J+1}
             }
         }
+        if (J + 1 < c) arrive_local(&vbar[2]);
     }
     // =================================================================== backward
     for (int J = c - 1; J >= 0; --J) {
@@ -463,6 +483,7 @@ k_band_solve2(const BandBlock* __restrict__ blocks, const T* __restrict__ fac, c
 #pragma unroll
             for (int j = 0; j < NR; ++j) send(vtb, &vbar[ut & 1], j, own_r, pre[j] - part_sum(tid, j));
         }
+        arrive_local(&vbar[ut & 1]);
         run_block(3, J, vtb, &vbar[ut & 1], (uint32_t)((ut >> 1) & 1));           // D_J^T t
         ++ut;
         if (owner) {
@@ -473,6 +494,7 @@ k_band_solve2(const BandBlock* __restrict__ blocks, const T* __restrict__ fac, c
                 if (J > 0) send(vst, &vbar[2], j, own_r, x);                      // read by O_J^T
             }
         }
+        if (J > 0) arrive_local(&vbar[2]);
     }
     cluster_barrier<G>();    // no CTA leaves while a peer may still store into it
     drain();                 // nor with a bulk copy still writing its shared memory
