@@ -137,17 +137,40 @@ __device__ __forceinline__ T gather_sum(const T* w, const int32_t* __restrict__ 
     return acc;
 }
 
+// entry pos of t = g - gathered panel products, right-hand side j
+template <typename T>
+__device__ __forceinline__ T t_entry(const CView<T>& cf, int32_t pos, const T* g, int64_t ldg, int j) {
+    const T* w = cf.wbuf + (int64_t)j * cf.nrow;
+    return g[cf.cperm[pos] + (int64_t)j * ldg] - gather_sum(w, cf.seg_row, cf.seg_ptr[pos], cf.seg_ptr[pos + 1]);
+}
+
 // t_J = g_J - gathered panel products into ts[0 .. n_J) by NTH threads (thread gt)
 template <typename T>
 __device__ __forceinline__ void gather_t(const CView<T>& cf, int J, int gt, int nth, T* ts, const T* g, int64_t ldg,
                                          int j) {
     const int32_t a0 = cf.c0[J], nJ = cf.c0[J + 1] - a0;
-    const T* w = cf.wbuf + (int64_t)j * cf.nrow;
-    for (int i = gt; i < nJ; i += nth) {
-        const int32_t pos = a0 + i;
-        ts[i] = g[cf.cperm[pos] + (int64_t)j * ldg] - gather_sum(w, cf.seg_row, cf.seg_ptr[pos], cf.seg_ptr[pos + 1]);
+    for (int i = gt; i < nJ; i += nth) ts[i] = t_entry(cf, a0 + i, g, ldg, j);
+}
+
+// eight consecutive values from shared memory (p 16-byte aligned)
+template <typename T>
+__device__ __forceinline__ void ld8(const T* p, T (&v)[8]) {
+    if constexpr (sizeof(T) == 4) {
+        const float4 a = reinterpret_cast<const float4*>(p)[0], b = reinterpret_cast<const float4*>(p)[1];
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+        v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const double2 a = reinterpret_cast<const double2*>(p)[q];
+            v[2 * q] = a.x;
+            v[2 * q + 1] = a.y;
+        }
     }
 }
+// right-hand sides per pass of the tiled small-supernode paths
+template <typename T>
+__host__ __device__ constexpr int tile_rp() { return sizeof(T) == 4 ? 32 : 16; }
 
 // Forward task (one CTA of NW warps) on RB right-hand sides j0 .. j0 + RB - 1: t_J of
 // each into ts (column b at ts + b * tstride), then rows tk.y .. tk.y + tk.z - 1 of
@@ -456,15 +479,93 @@ __device__ __forceinline__ bool stage_block_fwd(const CView<T>& cf, int J, T* st
 // over A_J (ts holds RB vectors, kSmallN apart), each with the multiply-adds it
 // gets alone; a supernode is staged or not whatever the right-hand sides, so
 // every column gets the same bits alone and in a block.
+// Blocks of right-hand sides on a staged supernode (tiled): the n_J rows of
+// L_JJ^{-1}, padded to whole groups of 32, then the |R_J| panel rows form the
+// virtual rows; a warp takes 128 of them (lane + 32 u, u < 4) for 8 right-hand
+// sides, so that each thread holds 4 x 8 sums and a column costs four matrix loads
+// and two 16-byte loads of t_J (stored right-hand sides contiguous, RP per pass)
+// for 32 multiply-adds.  Each (row, right-hand side) still takes its multiply-adds
+// over the columns in order from zero; a diagonal row adds exact zeros past its
+// last column, so the bits are those of the row-per-thread path.
+template <typename T, int NT, int GROUPS>
+__device__ void cfwd_small_tiled(const CView<T>& cf, int J, T* ts, const T* g, int64_t ldg, T* xf, int32_t nrhs,
+                                 const T* D, const T* Pn) {
+    constexpr int nw = NT / 32, RPM = tile_rp<T>();
+    const int gt = threadIdx.x % NT, lane = gt & 31, warp = gt >> 5;
+    const int32_t a0 = cf.c0[J], nJ = cf.c0[J + 1] - a0;
+    const int32_t nr = (int32_t)(cf.r_off[J + 1] - cf.r_off[J]);
+    const int32_t ND = (nJ + 31) & ~31, RV = ND + nr, ldp = small_ldp(nJ);
+    T* wb = cf.wbuf + cf.r_off[J];
+    for (int j0 = 0; j0 < nrhs; j0 += RPM) {
+        const int nb = min(RPM, nrhs - j0), RP = (nb + 7) & ~7, ngrp = RP / 8;
+        for (int idx = gt; idx < nJ * RP; idx += NT) {
+            const int i = idx / RP, b = idx - i * RP;
+            ts[idx] = b < nb ? t_entry(cf, a0 + i, g, ldg, j0 + b) : T(0);
+        }
+        if (j0 == 0) stage_wait();
+        group_sync<NT, GROUPS>();
+        const int items = ((RV + 127) >> 7) * ngrp;
+        for (int it = warp; it < items; it += nw) {
+            const int tile = it / ngrp, h = it - tile * ngrp, rbase = tile * 128;
+            int kind[4], r[4], cend = 0;       // kind (warp-uniform): 0 none, 1 diagonal, 2 panel
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int v0 = rbase + 32 * u;
+                kind[u] = v0 < ND ? 1 : (v0 < RV ? 2 : 0);
+                r[u] = v0 + lane;
+                if (kind[u] == 1) cend = max(cend, min(nJ, v0 + 32));
+                if (kind[u] == 2) cend = nJ;
+            }
+            T acc[4][8];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int b = 0; b < 8; ++b) acc[u][b] = T(0);
+            int32_t pcm = 0;                   // packed_col(c) - c
+            for (int c = 0; c < cend; ++c) {
+                T tv[8];
+                ld8(ts + c * RP + 8 * h, tv);
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (kind[u] == 0) continue;
+                    T a = T(0);
+                    if (kind[u] == 1) {
+                        if (r[u] >= c && r[u] < nJ) a = D[pcm + r[u]];
+                    } else if (r[u] < RV) {
+                        a = Pn[(r[u] - ND) * ldp + c];
+                    }
+#pragma unroll
+                    for (int b = 0; b < 8; ++b) acc[u][b] = fma(a, tv[b], acc[u][b]);
+                }
+                pcm += nJ - c - 1;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int b = 0; b < 8; ++b) {
+                    const int j = 8 * h + b;
+                    if (j >= nb) continue;
+                    if (kind[u] == 1 && r[u] < nJ) xf[a0 + r[u] + (int64_t)(j0 + j) * cf.s] = acc[u][b];
+                    else if (kind[u] == 2 && r[u] < RV) wb[(r[u] - ND) + (int64_t)(j0 + j) * cf.nrow] = acc[u][b];
+                }
+        }
+        group_sync<NT, GROUPS>();
+    }
+}
+
 template <typename T, int NT, int GROUPS, int RB>
 __device__ void cfwd_small_cta(const CView<T>& cf, int J, T* ts, const T* g, int64_t ldg, T* xf, int32_t nrhs, T* stg,
-                               int cap) {
+                               int cap, bool tiled = false) {
     constexpr int nw = NT / 32;
     const int gt = threadIdx.x % NT, lane = gt & 31, warp = gt >> 5;
     const int32_t a0 = cf.c0[J], nJ = cf.c0[J + 1] - a0;
     const int64_t nr = cf.r_off[J + 1] - cf.r_off[J], rtot = nJ + nr;
     const T *D, *Pn;
     const bool staged = stage_block_fwd<T, NT>(cf, J, stg, cap, gt, D, Pn);   // lands while t_J is gathered
+    if (tiled && staged) {
+        cfwd_small_tiled<T, NT, GROUPS>(cf, J, ts, g, ldg, xf, nrhs, D, Pn);
+        return;
+    }
     for (int j0 = 0; j0 < nrhs; j0 += RB) {
         const int nb = min(RB, nrhs - j0);
         for (int b = 0; b < nb; ++b) gather_t(cf, J, gt, NT, ts + b * kSmallN, g, ldg, j0 + b);
@@ -542,9 +643,97 @@ __device__ void cfwd_small_cta(const CView<T>& cf, int J, T* ts, const T* g, int
 // parts' partial sums (in red) are added in a fixed order.  RB right-hand sides
 // per pass (vs: RB vectors kSmallN + kSmallR apart, red: RB x NT), each with its
 // single-column sequence of multiply-adds.
+// shared-memory elements of the tiled backward's vector (and partial-sum) buffer
+template <typename T>
+__host__ __device__ constexpr int tile_vs() { return sizeof(T) == 4 ? 8192 : 4096; }
+
+// Blocks of right-hand sides (tiled backward): the rows of A_J split into the same
+// parts as the column-per-thread path below, and a thread takes 4 columns x 8
+// right-hand sides of one part (a row costs four matrix loads and two 16-byte loads
+// of the stacked vector, stored right-hand sides contiguous, for 32 multiply-adds).
+// Each (column, part) sums its rows in order from zero (diagonal rows above the
+// column add exact zeros) and the parts are added in order, as there: the same bits.
+// The vector buffer (rows x RP) then holds the parts' sums (at most NT x RP).
+template <typename T, int NT, int GROUPS>
+__device__ void cbwd_small_tiled(const CView<T>& cf, int J, T* vs, const T* yf, T* xf, T* y_dd, int64_t ldy,
+                                 int32_t nrhs, const T* D, const T* Pn, int rpm) {
+    const int gt = threadIdx.x % NT;
+    const int32_t a0 = cf.c0[J], nJ = cf.c0[J + 1] - a0;
+    const int64_t nr = cf.r_off[J + 1] - cf.r_off[J], rtot = nJ + nr;
+    const int32_t* R = cf.rows + cf.r_off[J];
+    int P = 32;
+    while (P < nJ) P *= 2;
+    const int parts = NT / P, ncg = (nJ + 3) / 4;
+    const int64_t len = (rtot + parts - 1) / parts;
+    int32_t pcm[4];                                      // packed_col(c) - c of the thread's columns
+    for (int j0 = 0; j0 < nrhs; j0 += rpm) {
+        const int nb = min(rpm, nrhs - j0), RP = (nb + 7) & ~7, ngrp = RP / 8;
+        for (int64_t idx = gt; idx < rtot * RP; idx += NT) {
+            const int64_t r = idx / RP;
+            const int b = (int)(idx - r * RP);
+            T v = T(0);
+            if (b < nb) v = r < nJ ? yf[a0 + r + (int64_t)(j0 + b) * cf.s] : -xf[R[r - nJ] + (int64_t)(j0 + b) * cf.s];
+            vs[idx] = v;
+        }
+        if (j0 == 0) stage_wait();
+        group_sync<NT, GROUPS>();
+        const int items = parts * ngrp * ncg;          // at most NT: one per thread
+        const bool act = gt < items;
+        const int cg = act ? gt % ncg : 0, h = act ? (gt / ncg) % ngrp : 0, q = act ? gt / (ncg * ngrp) : 0;
+        T acc[4][8];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+#pragma unroll
+            for (int b = 0; b < 8; ++b) acc[i][b] = T(0);
+            const int c = 4 * cg + i;
+            pcm[i] = (int32_t)(packed_col(c, nJ) - c);
+        }
+        if (act) {
+            const int64_t rb = q * len, re = min(rtot, rb + len);
+            for (int64_t r = rb; r < re; ++r) {
+                T tv[8];
+                ld8(vs + r * RP + 8 * h, tv);
+                T a[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int c = 4 * cg + i;
+                    a[i] = T(0);
+                    if (c < nJ) {
+                        if (r >= nJ) a[i] = Pn[(r - nJ) * nJ + c];
+                        else if (r >= c) a[i] = D[pcm[i] + r];
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int b = 0; b < 8; ++b) acc[i][b] = fma(a[i], tv[b], acc[i][b]);
+            }
+        }
+        group_sync<NT, GROUPS>();                      // the vector is read: its buffer takes the sums
+        if (act) {
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int b = 0; b < 8; ++b) {
+                    const int c = 4 * cg + i, j = 8 * h + b;
+                    if (c < nJ && j < nb) vs[((int64_t)q * nJ + c) * RP + j] = acc[i][b];
+                }
+        }
+        group_sync<NT, GROUPS>();
+        for (int idx = gt; idx < nJ * nb; idx += NT) {
+            const int c = idx / nb, j = idx - c * nb;
+            T v = T(0);
+            for (int qq = 0; qq < parts; ++qq) v += vs[((int64_t)qq * nJ + c) * RP + j];
+            xf[a0 + c + (int64_t)(j0 + j) * cf.s] = v;
+            if (y_dd) y_dd[cf.cperm[a0 + c] + (int64_t)(j0 + j) * ldy] = v;
+        }
+        group_sync<NT, GROUPS>();
+    }
+}
+
 template <typename T, int NT, int GROUPS, int RB>
 __device__ void cbwd_small_cta(const CView<T>& cf, int J, T* vs, T* red, const T* yf, T* xf, T* y_dd, int64_t ldy,
-                               int32_t nrhs, T* stg, int cap) {
+                               int32_t nrhs, T* stg, int cap, bool tiled = false) {
     static_assert(NT % kSmallN == 0 && NT <= 1024, "whole parts per column");
     constexpr int VS = kSmallN + kSmallR;
     const int gt = threadIdx.x % NT;
@@ -553,6 +742,14 @@ __device__ void cbwd_small_cta(const CView<T>& cf, int J, T* vs, T* red, const T
     const int32_t* R = cf.rows + cf.r_off[J];
     const T *D, *Pn;
     const bool staged = stage_block<T, NT>(cf, J, stg, cap, gt, D, Pn);   // lands while the vector is staged
+    if (tiled) {
+        // right-hand sides per pass: the vector (rows x RP) and the sums (NT x RP) fit the buffer
+        const int rpm = min(tile_rp<T>(), (int)(tile_vs<T>() / max(rtot, (int64_t)NT)) & ~7);
+        if (rpm >= 8) {
+            cbwd_small_tiled<T, NT, GROUPS>(cf, J, vs, yf, xf, y_dd, ldy, nrhs, D, Pn, rpm);
+            return;
+        }
+    }
     int P = 32;
     while (P < nJ) P *= 2;
     const int parts = NT / P, part = gt / P, c = gt % P;
@@ -670,26 +867,36 @@ k_cbwd_level(const CView<T> cf, int32_t t0, const T* yf, T* xf, T* y_dd, int64_t
 // right-hand sides per pass of the fused small levels' per-level kernels
 constexpr int kSmallRBf = 8, kSmallRBb = 4;
 
-// dynamic shared memory: t_J of kSmallRBf right-hand sides, then the stage buffer of cap elements
+// dynamic shared memory: t_J (tsz elements: kSmallRBf right-hand sides, or tile_rp
+// contiguous ones for the tiled path of blocks of 8 or more), then the stage buffer
+// of cap elements
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
-k_cfwd_small(const CView<T> cf, int32_t s0, const T* g, int64_t ldg, T* xf, int32_t nrhs, int32_t cap) {
+k_cfwd_small(const CView<T> cf, int32_t s0, const T* g, int64_t ldg, T* xf, int32_t nrhs, int32_t cap, int32_t tsz) {
     extern __shared__ __align__(16) unsigned char csm[];
     T* ts = reinterpret_cast<T*>(csm);
-    cfwd_small_cta<T, kThreads, 1, kSmallRBf>(cf, cf.lev_sn[s0 + blockIdx.x], ts, g, ldg, xf, nrhs,
-                                              ts + kSmallRBf * kSmallN, cap);
+    cfwd_small_cta<T, kThreads, 1, kSmallRBf>(cf, cf.lev_sn[s0 + blockIdx.x], ts, g, ldg, xf, nrhs, ts + tsz, cap,
+                                              tsz == kSmallN * tile_rp<T>());
 }
 
-// dynamic shared memory: kSmallRBb vectors of kSmallN + kSmallR, kSmallRBb x kThreads partial
-// sums, then the stage buffer of cap elements
+// dynamic shared memory (vsz elements): kSmallRBb vectors of kSmallN + kSmallR and
+// kSmallRBb x kThreads partial sums, or for blocks of 8 or more the tiled path's
+// buffer, then the stage buffer of cap elements
+template <typename T>
+__host__ __device__ constexpr int small_bwd_vsz(bool tiled) {
+    return tiled ? (tile_vs<T>() > kSmallRBb * (kSmallN + kSmallR + kThreads) ? tile_vs<T>()
+                                                                              : kSmallRBb * (kSmallN + kSmallR + kThreads))
+                 : kSmallRBb * (kSmallN + kSmallR + kThreads);
+}
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
-k_cbwd_small(const CView<T> cf, int32_t s0, const T* yf, T* xf, T* y_dd, int64_t ldy, int32_t nrhs, int32_t cap) {
+k_cbwd_small(const CView<T> cf, int32_t s0, const T* yf, T* xf, T* y_dd, int64_t ldy, int32_t nrhs, int32_t cap,
+             bool tiled) {
     extern __shared__ __align__(16) unsigned char csm[];
     T* vs = reinterpret_cast<T*>(csm);
     T* red = vs + kSmallRBb * (kSmallN + kSmallR);
     cbwd_small_cta<T, kThreads, 1, kSmallRBb>(cf, cf.lev_sn[s0 + blockIdx.x], vs, red, yf, xf, y_dd, ldy, nrhs,
-                                              red + kSmallRBb * kThreads, cap);
+                                              vs + small_bwd_vsz<T>(tiled), cap, tiled);
 }
 
 
@@ -1441,9 +1648,10 @@ cudaError_t launch_c_forward(const DevCFactor<T>& cf, const T* g_dd, int64_t ldg
             const int s0 = cf.lev_sn_ptr[l], ns = cf.lev_sn_ptr[l + 1] - s0;
             if (ns == 0) continue;
             const int32_t cap = cf.lev_stage[l];
-            const size_t sm = ((size_t)kSmallRBf * kSmallN + cap) * sizeof(T);
+            const int32_t tsz = nrhs >= 8 ? kSmallN * tile_rp<T>() : kSmallRBf * kSmallN;
+            const size_t sm = ((size_t)tsz + cap) * sizeof(T);
             if (sm > 48 * 1024 && !raise_smem_once((const void*)k_cfwd_small<T>)) return cudaErrorInvalidValue;
-            k_cfwd_small<T><<<ns, kThreads, sm, st>>>(v, s0, g_dd, ldg, xf, nrhs, cap);
+            k_cfwd_small<T><<<ns, kThreads, sm, st>>>(v, s0, g_dd, ldg, xf, nrhs, cap, tsz);
             counted();
             continue;
         }
@@ -1502,9 +1710,10 @@ cudaError_t launch_c_backward(const DevCFactor<T>& cf, const T* yf, T* xf, T* y_
             const int s0 = cf.lev_sn_ptr[l], ns = cf.lev_sn_ptr[l + 1] - s0;
             if (ns == 0) continue;
             const int32_t cap = cf.lev_stage[l];
-            const size_t sm = ((size_t)kSmallRBb * (kSmallN + kSmallR + kThreads) + cap) * sizeof(T);
+            const bool tiled = nrhs >= 8;
+            const size_t sm = ((size_t)small_bwd_vsz<T>(tiled) + cap) * sizeof(T);
             if (sm > 48 * 1024 && !raise_smem_once((const void*)k_cbwd_small<T>)) return cudaErrorInvalidValue;
-            k_cbwd_small<T><<<ns, kThreads, sm, st>>>(v, s0, yf, xf, y_dd, ldy, nrhs, cap);
+            k_cbwd_small<T><<<ns, kThreads, sm, st>>>(v, s0, yf, xf, y_dd, ldy, nrhs, cap, tiled);
             counted();
             continue;
         }

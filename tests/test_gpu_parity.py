@@ -218,6 +218,28 @@ def test_csolve_medium_with_fused_levels(precision):
             assert rel(y, want) <= (TOL64 if precision == "fp64" else tol32(g.get_info())), (persistent, zone)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("persistent", [False, True])
+def test_csolve_wide_block_fused_levels(precision, persistent):
+    """C^{-1} of a block of 11 right-hand sides on the 40^3 problem: the fused small
+    levels take blocks of 8 or more through their tiled paths (a group of 8 and a
+    ragged group of 3, padded).  Parity with the oracle's factor, and a column solved
+    alone (by the row-per-thread paths) equals its column of the block bit for bit."""
+    from oracle.slr_oracle import dd_order, split_blocks, CFactor
+    P = slrgen.make_problem("m40", (40, 40, 40), (4, 4, 4), 4)
+    order = dd_order(P.rowptr, P.colind, P.part, P.nparts)
+    C = split_blocks(P.rowptr, P.colind, P.val, order)[2]
+    gg = np.random.default_rng(12).standard_normal((order.s, 11))
+    want = CFactor(C, route="sparse").solve(gg)
+    g = SLR(P.rowptr, P.colind, P.val, P.part, P.nparts, k=2, lanczos_steps=4, precision=precision,
+            nrhs_max=11, c_persistent=persistent, c_top_zone=False)
+    y = g.csolve(cu(gg)).cpu().numpy()
+    assert rel(y, want) <= (TOL64 if precision == "fp64" else tol32(g.get_info()))
+    for c in (0, 9, 10):
+        assert np.array_equal(g.csolve(cu(gg[:, c])).cpu().numpy(), y[:, c]), c
+    g.close()
+
+
 def test_pcg_with_persistent_c_solve_matches_per_level():
     P = make("3d-lap")
     b = cu(P.b[:, 0])
