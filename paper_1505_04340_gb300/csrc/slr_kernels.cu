@@ -40,6 +40,44 @@ __device__ __forceinline__ T warp_sum(T v) {
     return v;
 }
 
+// The warp sums of N values (N a power of two up to 32) at once: at each of the
+// first log2 N butterfly steps a lane keeps half of its values and adds its
+// partner's copies of them (own + partner, as warp_sum does), the remaining steps
+// add whole; every sum is formed by warp_sum's tree, bit for bit, with N - 1 +
+// 5 - log2 N shuffles instead of 5 N.  Lane l returns the sum of value
+// rs_index<N>(l); lanes that differ only in the low 5 - log2 N bits hold the same.
+template <typename T, int N>
+__device__ __forceinline__ T reduce_scatter(T (&v)[N], int lane) {
+    static_assert(N >= 1 && N <= 32 && (N & (N - 1)) == 0, "a power of two up to 32");
+    int o = 16;
+#pragma unroll
+    for (int h = N / 2; h >= 1; h /= 2, o >>= 1) {
+        const bool up = (lane & o) != 0;
+#pragma unroll
+        for (int i = 0; i < h; ++i) {
+            const T send = up ? v[i] : v[i + h];
+            const T keep = up ? v[i + h] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+    T r = v[0];
+    for (; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+    return r;
+}
+template <int N>
+__device__ __forceinline__ int rs_index(int lane) {
+    int k = 0, o = 16;
+#pragma unroll
+    for (int h = N / 2; h >= 1; h /= 2, o >>= 1)
+        if (lane & o) k += h;
+    return k;
+}
+// a lane that writes its reduce_scatter<N> sum (one per distinct sum)
+template <int N>
+__device__ __forceinline__ bool rs_writer(int lane) {
+    return (lane & (32 / N - 1)) == 0;
+}
+
 // K1 (the batched band solve) lives in slr_band.cu.
 
 // ------------------------------------------------------------------ K2
@@ -144,6 +182,38 @@ __device__ __forceinline__ T t_entry(const CView<T>& cf, int32_t pos, const T* g
     return g[cf.cperm[pos] + (int64_t)j * ldg] - gather_sum(w, cf.seg_row, cf.seg_ptr[pos], cf.seg_ptr[pos + 1]);
 }
 
+// t at position pos for right-hand sides j .. j + nb - 1 (nb <= 8) into out[0 .. 8)
+// (zeros past nb): the index chain is loaded once for the eight, each sum still
+// takes its contributions in order, as t_entry does
+template <typename T>
+__device__ __forceinline__ void t_entry8(const CView<T>& cf, int32_t pos, const T* g, int64_t ldg, int j, int nb,
+                                         T (&out)[8]) {
+    const int64_t e0 = cf.seg_ptr[pos], e1 = cf.seg_ptr[pos + 1];
+    const int32_t gp = cf.cperm[pos];
+    T acc[8];
+#pragma unroll
+    for (int b = 0; b < 8; ++b) acc[b] = T(0);
+    for (int64_t e = e0; e < e1; e += 4) {
+        int32_t idx[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) idx[u] = e + u < e1 ? cf.seg_row[e + u] : -1;
+        T v[4][8];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int b = 0; b < 8; ++b)
+                v[u][b] = (idx[u] >= 0 && b < nb) ? cf.wbuf[idx[u] + (int64_t)(j + b) * cf.nrow] : T(0);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (idx[u] >= 0) {
+#pragma unroll
+                for (int b = 0; b < 8; ++b) acc[b] += v[u][b];
+            }
+    }
+#pragma unroll
+    for (int b = 0; b < 8; ++b) out[b] = b < nb ? g[gp + (int64_t)(j + b) * ldg] - acc[b] : T(0);
+}
+
 // t_J = g_J - gathered panel products into ts[0 .. n_J) by NTH threads (thread gt)
 template <typename T>
 __device__ __forceinline__ void gather_t(const CView<T>& cf, int J, int gt, int nth, T* ts, const T* g, int64_t ldg,
@@ -181,7 +251,7 @@ __host__ __device__ constexpr int tile_rp() { return sizeof(T) == 4 ? 32 : 16; }
 // RB, so a column gives the same bits alone and in a block.
 template <typename T, int NW, int RB>
 __device__ void cfwd_task_rb(const CView<T>& cf, const int4 tk, bool pan, T* ts, int tstride, T (*red)[33],
-                             const T* g, int64_t ldg, T* xf, int j0) {
+                             const T* g, int64_t ldg, T* xf, int j0, T* red2) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int32_t J = tk.x, a0 = cf.c0[J], nJ = cf.c0[J + 1] - a0;
 #pragma unroll
@@ -217,11 +287,8 @@ __device__ void cfwd_task_rb(const CView<T>& cf, const int4 tk, bool pan, T* ts,
 #pragma unroll
                 for (int b = 0; b < RB; ++b) acc[b] += pv * ts[b * tstride + c];
             }
-#pragma unroll
-            for (int b = 0; b < RB; ++b) {
-                const T v = warp_sum(acc[b]);
-                if (lane == 0) cf.wbuf[cf.r_off[J] + p + (int64_t)(j0 + b) * cf.nrow] = v;
-            }
+            const T v = reduce_scatter<T, RB>(acc, lane);
+            if (rs_writer<RB>(lane)) cf.wbuf[cf.r_off[J] + p + (int64_t)(j0 + rs_index<RB>(lane)) * cf.nrow] = v;
         }
     } else {
         const T* D = cf.dinv + cf.dinv_off[J];
@@ -250,34 +317,50 @@ __device__ void cfwd_task_rb(const CView<T>& cf, const int4 tk, bool pan, T* ts,
                 for (int b = 0; b < RB; ++b) acc[b] += d * ts[b * tstride + jj];
             }
         }
+        if (red2) {
+            // the warps' partial sums of all RB columns at once (red2: NW x RB x 32),
+            // then each column's added over the warps in order, as below
 #pragma unroll
-        for (int b = 0; b < RB; ++b) {
-            red[warp][lane] = acc[b];
+            for (int b = 0; b < RB; ++b) red2[(warp * RB + b) * 32 + lane] = acc[b];
             __syncthreads();
-            if (warp == 0) {
+            for (int b = warp; b < RB; b += NW) {
                 T v = T(0);
 #pragma unroll 8
-                for (int w = 0; w < NW; ++w) v += red[w][lane];
+                for (int w = 0; w < NW; ++w) v += red2[(w * RB + b) * 32 + lane];
                 if (lane < tk.z) xf[a0 + il + (int64_t)(j0 + b) * cf.s] = v;
             }
-            __syncthreads();
+        } else {
+#pragma unroll
+            for (int b = 0; b < RB; ++b) {
+                red[warp][lane] = acc[b];
+                __syncthreads();
+                if (warp == 0) {
+                    T v = T(0);
+#pragma unroll 8
+                    for (int w = 0; w < NW; ++w) v += red[w][lane];
+                    if (lane < tk.z) xf[a0 + il + (int64_t)(j0 + b) * cf.s] = v;
+                }
+                __syncthreads();
+            }
         }
     }
     __syncthreads();
 }
 
 // All nrhs columns: blocks of 8 or 4 while ts holds that many columns (rbmax), then one at a time.
+// red2 (NW x rbmax x 32, or null): the diagonal tasks' partial sums of a block at once.
 template <typename T, int NW, int RBMAX = 8>
 __device__ void cfwd_task_cta(const CView<T>& cf, const int4 tk, bool pan, T* ts, int tstride, int rbmax,
-                              T (*red)[33], const T* g, int64_t ldg, T* xf, int32_t nrhs) {
+                              T (*red)[33], const T* g, int64_t ldg, T* xf, int32_t nrhs, T* red2 = nullptr) {
     int j0 = 0;
     if constexpr (RBMAX >= 8) {
         if (rbmax >= 8)
-            for (; j0 + 8 <= nrhs; j0 += 8) cfwd_task_rb<T, NW, 8>(cf, tk, pan, ts, tstride, red, g, ldg, xf, j0);
+            for (; j0 + 8 <= nrhs; j0 += 8)
+                cfwd_task_rb<T, NW, 8>(cf, tk, pan, ts, tstride, red, g, ldg, xf, j0, red2);
     }
     if (rbmax >= 4)
-        for (; j0 + 4 <= nrhs; j0 += 4) cfwd_task_rb<T, NW, 4>(cf, tk, pan, ts, tstride, red, g, ldg, xf, j0);
-    for (; j0 < nrhs; ++j0) cfwd_task_rb<T, NW, 1>(cf, tk, pan, ts, tstride, red, g, ldg, xf, j0);
+        for (; j0 + 4 <= nrhs; j0 += 4) cfwd_task_rb<T, NW, 4>(cf, tk, pan, ts, tstride, red, g, ldg, xf, j0, red2);
+    for (; j0 < nrhs; ++j0) cfwd_task_rb<T, NW, 1>(cf, tk, pan, ts, tstride, red, g, ldg, xf, j0, nullptr);
 }
 
 // Backward task (one CTA of NW warps) on RB right-hand sides: columns
@@ -289,7 +372,7 @@ __device__ void cfwd_task_cta(const CView<T>& cf, const int4 tk, bool pan, T* ts
 // Optional scatter of the result to DD order.  us: RB x 32.
 template <typename T, int NW, int DEPTH, int RB>
 __device__ void cbwd_task_rb(const CView<T>& cf, const int4 tk, T* us, T (*red)[33], const T* yf, T* xf, T* y_dd,
-                             int64_t ldy, int j0) {
+                             int64_t ldy, int j0, T* red2) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int32_t J = tk.x, a0 = cf.c0[J], nJ = cf.c0[J + 1] - a0, jl = tk.y + lane;
     const int64_t nr = cf.r_off[J + 1] - cf.r_off[J];
@@ -320,11 +403,8 @@ __device__ void cbwd_task_rb(const CView<T>& cf, const int4 tk, T* us, T (*red)[
 #pragma unroll
             for (int b = 0; b < RB; ++b) acc[b] += d * y[(int64_t)b * cf.s + i];
         }
-#pragma unroll
-        for (int b = 0; b < RB; ++b) {
-            const T v = warp_sum(acc[b]);
-            if (lane == 0) us[b * 32 + cc] = v;
-        }
+        const T v = reduce_scatter<T, RB>(acc, lane);
+        if (rs_writer<RB>(lane)) us[rs_index<RB>(lane) * 32 + cc] = v;
     }
     T acc[RB];
 #pragma unroll
@@ -351,6 +431,25 @@ __device__ void cbwd_task_rb(const CView<T>& cf, const int4 tk, T* us, T (*red)[
             for (int b = 0; b < RB; ++b) acc[b] += pv * x[(int64_t)b * cf.s + r];
         }
     }
+    if (red2) {
+        // all RB columns' partial sums at once (red2: NW x RB x 32), each column's then
+        // added over the warps in order, as below
+#pragma unroll
+        for (int b = 0; b < RB; ++b) red2[(warp * RB + b) * 32 + lane] = acc[b];
+        __syncthreads();
+        for (int b = warp; b < RB; b += NW) {
+            if (lane < tk.z) {
+                T v = T(0);
+#pragma unroll 8
+                for (int w = 0; w < NW; ++w) v += red2[(w * RB + b) * 32 + lane];
+                const T r = us[b * 32 + lane] - v;
+                xf[a0 + jl + (int64_t)(j0 + b) * cf.s] = r;
+                if (y_dd) y_dd[cf.cperm[a0 + jl] + (int64_t)(j0 + b) * ldy] = r;
+            }
+        }
+        __syncthreads();
+        return;
+    }
 #pragma unroll
     for (int b = 0; b < RB; ++b) {
         red[warp][lane] = acc[b];
@@ -369,17 +468,19 @@ __device__ void cbwd_task_rb(const CView<T>& cf, const int4 tk, T* us, T (*red)[
 
 // All nrhs columns: blocks of 8 or 4 while us holds that many columns (rbmax), then
 // one at a time (DEPTH4: loads in flight per lane in a block).
+// red2 (NW x rbmax x 32, or null): the panel part's partial sums of a block at once.
 template <typename T, int NW, int DEPTH, int DEPTH4, int RBMAX = 8>
 __device__ void cbwd_task_cta(const CView<T>& cf, const int4 tk, T* us, int rbmax, T (*red)[33], const T* yf, T* xf,
-                              T* y_dd, int64_t ldy, int32_t nrhs) {
+                              T* y_dd, int64_t ldy, int32_t nrhs, T* red2 = nullptr) {
     int j0 = 0;
     if constexpr (RBMAX >= 8) {
         if (rbmax >= 8)
-            for (; j0 + 8 <= nrhs; j0 += 8) cbwd_task_rb<T, NW, DEPTH4, 8>(cf, tk, us, red, yf, xf, y_dd, ldy, j0);
+            for (; j0 + 8 <= nrhs; j0 += 8)
+                cbwd_task_rb<T, NW, DEPTH4, 8>(cf, tk, us, red, yf, xf, y_dd, ldy, j0, red2);
     }
     if (rbmax >= 4)
-        for (; j0 + 4 <= nrhs; j0 += 4) cbwd_task_rb<T, NW, DEPTH4, 4>(cf, tk, us, red, yf, xf, y_dd, ldy, j0);
-    for (; j0 < nrhs; ++j0) cbwd_task_rb<T, NW, DEPTH, 1>(cf, tk, us, red, yf, xf, y_dd, ldy, j0);
+        for (; j0 + 4 <= nrhs; j0 += 4) cbwd_task_rb<T, NW, DEPTH4, 4>(cf, tk, us, red, yf, xf, y_dd, ldy, j0, red2);
+    for (; j0 < nrhs; ++j0) cbwd_task_rb<T, NW, DEPTH, 1>(cf, tk, us, red, yf, xf, y_dd, ldy, j0, nullptr);
 }
 
 // Synchronises the NT threads of a group: the whole CTA (GROUPS = 1) or group
@@ -498,9 +599,12 @@ __device__ void cfwd_small_tiled(const CView<T>& cf, int J, T* ts, const T* g, i
     T* wb = cf.wbuf + cf.r_off[J];
     for (int j0 = 0; j0 < nrhs; j0 += RPM) {
         const int nb = min(RPM, nrhs - j0), RP = (nb + 7) & ~7, ngrp = RP / 8;
-        for (int idx = gt; idx < nJ * RP; idx += NT) {
-            const int i = idx / RP, b = idx - i * RP;
-            ts[idx] = b < nb ? t_entry(cf, a0 + i, g, ldg, j0 + b) : T(0);
+        for (int it = gt; it < nJ * ngrp; it += NT) {
+            const int i = it / ngrp, h = it - i * ngrp;
+            T tv[8];
+            t_entry8(cf, a0 + i, g, ldg, j0 + 8 * h, nb - 8 * h, tv);
+#pragma unroll
+            for (int b = 0; b < 8; ++b) ts[i * RP + 8 * h + b] = tv[b];
         }
         if (j0 == 0) stage_wait();
         group_sync<NT, GROUPS>();
@@ -668,12 +772,20 @@ __device__ void cbwd_small_tiled(const CView<T>& cf, int J, T* vs, const T* yf, 
     int32_t pcm[4];                                      // packed_col(c) - c of the thread's columns
     for (int j0 = 0; j0 < nrhs; j0 += rpm) {
         const int nb = min(rpm, nrhs - j0), RP = (nb + 7) & ~7, ngrp = RP / 8;
-        for (int64_t idx = gt; idx < rtot * RP; idx += NT) {
-            const int64_t r = idx / RP;
-            const int b = (int)(idx - r * RP);
-            T v = T(0);
-            if (b < nb) v = r < nJ ? yf[a0 + r + (int64_t)(j0 + b) * cf.s] : -xf[R[r - nJ] + (int64_t)(j0 + b) * cf.s];
-            vs[idx] = v;
+        // rows of [y_J; -x_{R_J}], eight right-hand sides per item (one index load)
+        for (int64_t it = gt; it < rtot * ngrp; it += NT) {
+            const int64_t r = it / ngrp;
+            const int h = (int)(it - r * ngrp);
+            const int64_t src = r < nJ ? a0 + r : R[r - nJ];
+            T v[8];
+#pragma unroll
+            for (int b = 0; b < 8; ++b) {
+                const int j = 8 * h + b;
+                v[b] = T(0);
+                if (j < nb) v[b] = r < nJ ? yf[src + (int64_t)(j0 + j) * cf.s] : -xf[src + (int64_t)(j0 + j) * cf.s];
+            }
+#pragma unroll
+            for (int b = 0; b < 8; ++b) vs[r * RP + 8 * h + b] = v[b];
         }
         if (j0 == 0) stage_wait();
         group_sync<NT, GROUPS>();
@@ -831,8 +943,10 @@ k_cfwd_level(const CView<T> cf, int32_t t0, int32_t p0, int32_t np, const T* g, 
     __shared__ T red[NW][33];
     const int q = blockIdx.x;
     const bool pan = q < np;
-    cfwd_task_cta<T, NW>(cf, pan ? cf.ptasks[p0 + q] : cf.tasks[t0 + q - np], pan, reinterpret_cast<T*>(csm), tstride,
-                         rbmax, red, g, ldg, xf, nrhs);
+    T* ts = reinterpret_cast<T*>(csm);
+    T* red2 = rbmax > 1 ? ts + (size_t)rbmax * tstride : nullptr;     // NW x rbmax x 32 after t_J
+    cfwd_task_cta<T, NW>(cf, pan ? cf.ptasks[p0 + q] : cf.tasks[t0 + q - np], pan, ts, tstride, rbmax, red, g, ldg, xf,
+                         nrhs, red2);
 }
 
 // t_J = g_J - (gathered panel products) for every supernode of a level, once, into
@@ -858,10 +972,12 @@ k_cfwd_gather(const CView<T> cf, int32_t s0, const T* g, int64_t ldg, int32_t nr
 template <typename T, int NW>
 __global__ void __launch_bounds__(NW * 32, NW == 8 ? 4 : 1)
 k_cbwd_level(const CView<T> cf, int32_t t0, const T* yf, T* xf, T* y_dd, int64_t ldy, int32_t nrhs) {
+    extern __shared__ __align__(16) unsigned char csm[];
     __shared__ T red[NW][33];
     __shared__ T us[8 * 32];
+    T* red2 = nrhs >= 4 ? reinterpret_cast<T*>(csm) : nullptr;        // NW x 8 x 32
     cbwd_task_cta<T, NW, sizeof(T) == 4 ? 16 : 8, 4>(cf, cf.tasks[t0 + blockIdx.x], us, 8, red, yf, xf, y_dd, ldy,
-                                                      nrhs);
+                                                      nrhs, red2);
 }
 
 // right-hand sides per pass of the fused small levels' per-level kernels
@@ -1670,11 +1786,16 @@ cudaError_t launch_c_forward(const DevCFactor<T>& cf, const T* g_dd, int64_t ldg
         // blocks of eight or four right-hand sides share each matrix load when t_J of that many fits
         const bool wide = nt + np <= cf.nsm;
         const void* kern = wide ? (const void*)k_cfwd_level<T, 32> : (const void*)k_cfwd_level<T, 8>;
+        // t_J of rbmax columns, then (blocks) the diagonal tasks' partial sums, NW x rbmax x 32
+        auto need = [&](int32_t rb) {
+            return ((size_t)rb * cf.max_n + (rb > 1 ? (size_t)(wide ? 32 : 8) * rb * 32 : 0)) * sizeof(T);
+        };
         int32_t rbmax = 1;
-        if (nrhs >= 8 && 8 * (size_t)cf.max_n * sizeof(T) <= kLevSmem) rbmax = 8;
-        else if (nrhs >= 4 && 4 * (size_t)cf.max_n * sizeof(T) <= kLevSmem) rbmax = 4;
-        if (rbmax > 1 && rbmax * (size_t)cf.max_n * sizeof(T) > 40 * 1024 && !raise_smem_once(kern)) rbmax = 1;
-        const size_t smem = (size_t)rbmax * cf.max_n * sizeof(T);
+        if (nrhs >= 8 && need(8) <= kLevSmem) rbmax = 8;
+        else if (nrhs >= 4 && need(4) <= kLevSmem) rbmax = 4;
+        if (rbmax > 1 && need(rbmax) > 40 * 1024 && !raise_smem_once(kern)) rbmax = 1;
+        const size_t smem = need(rbmax);
+        if (smem > 48 * 1024 && !raise_smem_once(kern)) return cudaErrorInvalidValue;
         if (!wide)
             k_cfwd_level<T, 8><<<nt + np, 256, smem, st>>>(vl, t0, p0, np, g_dd, ldg, xf, nrhs, cf.max_n, rbmax);
         else
@@ -1719,10 +1840,15 @@ cudaError_t launch_c_backward(const DevCFactor<T>& cf, const T* yf, T* xf, T* y_
         }
         const int t0 = cf.lev_task_ptr[l], nt = cf.lev_task_ptr[l + 1] - t0;
         if (nt == 0) continue;
-        if (nt > cf.nsm)
-            k_cbwd_level<T, 8><<<nt, 256, 0, st>>>(v, t0, yf, xf, y_dd, ldy, nrhs);
-        else
-            k_cbwd_level<T, 32><<<nt, 1024, 0, st>>>(v, t0, yf, xf, y_dd, ldy, nrhs);
+        // blocks of four or more: the panel part's partial sums, NW x 8 x 32
+        if (nt > cf.nsm) {
+            const size_t sm = nrhs >= 4 ? (size_t)8 * 8 * 32 * sizeof(T) : 0;
+            k_cbwd_level<T, 8><<<nt, 256, sm, st>>>(v, t0, yf, xf, y_dd, ldy, nrhs);
+        } else {
+            const size_t sm = nrhs >= 4 ? (size_t)32 * 8 * 32 * sizeof(T) : 0;
+            if (sm > 48 * 1024 && !raise_smem_once((const void*)k_cbwd_level<T, 32>)) return cudaErrorInvalidValue;
+            k_cbwd_level<T, 32><<<nt, 1024, sm, st>>>(v, t0, yf, xf, y_dd, ldy, nrhs);
+        }
         counted();
     }
     return cudaGetLastError();
