@@ -185,7 +185,7 @@ __device__ __forceinline__ void bt_put_rows(unsigned char* vdst, int rbase, int 
 }
 
 template <int AB, int NP>
-__global__ void __launch_bounds__(kBtThreads, 1)
+__global__ void __launch_bounds__(kBtThreads, NP <= 32 ? 2 : 1)
 k_band_tc(const BandTcBlock* __restrict__ blocks, const unsigned char* __restrict__ fac, const float* in,
           int64_t ldi, float* out, int64_t ldo, const float* base, int64_t ldb, int32_t nrhs, int32_t nslot,
           int32_t stiles, int32_t* err) {
@@ -198,9 +198,12 @@ k_band_tc(const BandTcBlock* __restrict__ blocks, const unsigned char* __restric
     const int W = b.w, c = b.c, m = b.m;
     const int WK = bt_nk(W, KS) * KS;
     const uint32_t vbytes = (uint32_t)NP * WK * E, sbo_v = 8u * WK * E;
+    // One operand buffer: a block's MMAs all complete (acc_bar) before its epilogue
+    // overwrites the operand with the next block's, and the next block's MMAs wait
+    // for that epilogue (opnd_bar), so the two never overlap.
     unsigned char* ring = sm;                                      // nslot x stiles sub-tiles
-    unsigned char* vbuf = ring + (size_t)nslot * stiles * kSub;    // [2] vector operands
-    uint64_t* full = reinterpret_cast<uint64_t*>(vbuf + 2 * (size_t)vbytes);
+    unsigned char* vbuf = ring + (size_t)nslot * stiles * kSub;    // the vector operand
+    uint64_t* full = reinterpret_cast<uint64_t*>(vbuf + (size_t)vbytes);
     uint64_t* empty = full + nslot;
     uint64_t* acc_bar = empty + nslot;
     uint64_t* opnd_bar = acc_bar + 1;
@@ -228,7 +231,7 @@ k_band_tc(const BandTcBlock* __restrict__ blocks, const unsigned char* __restric
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    for (uint32_t e = tid; e < 2 * vbytes / 16; e += kBtThreads)            // K and N padding stay zero
+    for (uint32_t e = tid; e < vbytes / 16; e += kBtThreads)                // K and N padding stay zero
         reinterpret_cast<uint4*>(vbuf)[e] = make_uint4(0, 0, 0, 0);
     tc::fence_async_smem();
     tc::fence_before_sync();
@@ -286,8 +289,8 @@ k_band_tc(const BandTcBlock* __restrict__ blocks, const unsigned char* __restric
             tc::fence_after_sync();
             const BtBlock bk = bt_block(q, c);
             const bool upper = bk.type == 0 || bk.type == 3;
-            // the operand: t (D blocks) is in buffer 1, Y / X (O blocks) in buffer 0
-            const uint32_t vb = tc::smem_addr(vbuf + (size_t)((bk.type == 1 || bk.type == 3) ? 1 : 0) * vbytes);
+            // the operand: t (D blocks) or Y / X (O blocks), written by the last epilogue
+            const uint32_t vb = tc::smem_addr(vbuf);
             int t = 0;
             bool ok = true;
             for (int mt = 0; mt < nM && ok; ++mt)
@@ -315,7 +318,7 @@ k_band_tc(const BandTcBlock* __restrict__ blocks, const unsigned char* __restric
         const int e = tid - 128, quarter = warp - 4;
         const uint32_t lane_addr = (uint32_t)(32 * quarter) << 16;
         unsigned char* v0 = vbuf;                       // Y / X
-        unsigned char* v1 = vbuf + vbytes;              // t
+        unsigned char* v1 = vbuf;                       // t (the same buffer, in turn)
         // byte of (column j, row r) of an operand (K index r)
         auto opos = [&](int j, int r) -> uint32_t {
             return (uint32_t)((j >> 3) * sbo_v + (r / (16 / E)) * 128 + (j & 7) * 16 + (r % (16 / E)) * E);
@@ -396,8 +399,7 @@ k_band_tc(const BandTcBlock* __restrict__ blocks, const unsigned char* __restric
                             for (int jj = 0; jj < 32; ++jj)
                                 if (c0 + jj < nrhs) out[row + (c0 + jj) * ldo] = v[jj];
                         }
-                        put_rows(v0, rbase, c0, v);
-                        if (J == c - 1) put_rows(v1, rbase, c0, v);   // the backward starts from t = Y_{c-1}
+                        put_rows(v0, rbase, c0, v);             // also the backward's first t (J = c - 1)
                     } else {                                     // X_J = D_J^T t
                         if (in_w && ok_r) {
 #pragma unroll
@@ -425,10 +427,12 @@ cudaError_t bt_launch(const DevOperator<float>& op, int32_t p, const float* in, 
     constexpr int E = BtType<AB>::E, KS = BtType<AB>::KS;
     const int WK = bt_nk(op.band_tc_wmax, KS) * KS;
     const size_t vbytes = (size_t)NP * WK * E;
-    const size_t fixed = 2 * vbytes + 8 * (2 * 8 + 3) + 16 + (size_t)2 * NP * 128 * sizeof(float);
-    // ring: as many 4-sub-tile slots (16 KB) as fit in the opt-in maximum, 2 .. 8
+    const size_t fixed = vbytes + 8 * (2 * 8 + 3) + 16 + (size_t)2 * NP * 128 * sizeof(float);
+    // ring: as many 4-sub-tile slots (16 KB) as fit, 2 .. 8, in the opt-in maximum or,
+    // with more subdomains than SMs, in half an SM (113 KB: two CTAs per SM, one wave)
     const int stiles = 4;
-    int nslot = (int)((227 * 1024 - fixed) / ((size_t)stiles * kSub));
+    const size_t cap = (NP <= 32 && p > op.cf.nsm) ? 113 * 1024 : 227 * 1024;
+    int nslot = fixed < cap ? (int)((cap - fixed) / ((size_t)stiles * kSub)) : 0;
     nslot = nslot > 8 ? 8 : nslot;
     if (nslot < 2) return cudaErrorInvalidValue;
     const size_t smem = (size_t)nslot * stiles * kSub + fixed;

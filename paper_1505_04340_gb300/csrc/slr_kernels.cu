@@ -987,7 +987,7 @@ constexpr int kSmallRBf = 8, kSmallRBb = 4;
 // contiguous ones for the tiled path of blocks of 8 or more), then the stage buffer
 // of cap elements
 template <typename T>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2)
 k_cfwd_small(const CView<T> cf, int32_t s0, const T* g, int64_t ldg, T* xf, int32_t nrhs, int32_t cap, int32_t tsz) {
     extern __shared__ __align__(16) unsigned char csm[];
     T* ts = reinterpret_cast<T*>(csm);
@@ -1005,7 +1005,7 @@ __host__ __device__ constexpr int small_bwd_vsz(bool tiled) {
                  : kSmallRBb * (kSmallN + kSmallR + kThreads);
 }
 template <typename T>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 3 : 2)
 k_cbwd_small(const CView<T> cf, int32_t s0, const T* yf, T* xf, T* y_dd, int64_t ldy, int32_t nrhs, int32_t cap,
              bool tiled) {
     extern __shared__ __align__(16) unsigned char csm[];
