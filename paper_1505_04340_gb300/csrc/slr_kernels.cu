@@ -363,6 +363,110 @@ __device__ void cfwd_task_cta(const CView<T>& cf, const int4 tk, bool pan, T* ts
     for (; j0 < nrhs; ++j0) cfwd_task_rb<T, NW, 1>(cf, tk, pan, ts, tstride, red, g, ldg, xf, j0, nullptr);
 }
 
+// four consecutive values from shared memory (p 16-byte aligned)
+template <typename T>
+__device__ __forceinline__ void ld4(const T* p, T (&v)[4]) {
+    if constexpr (sizeof(T) == 4) {
+        const float4 a = *reinterpret_cast<const float4*>(p);
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    } else {
+        const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+        v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+    }
+}
+
+// Forward task on a block of RP right-hand sides j0 .. j0 + nb - 1 in one pass (RP 16
+// or 32; columns past nb are zeros): t_J from the level's gather, stored right-hand
+// sides contiguous with row stride RP + 4 (16-byte loads by the lanes of different
+// columns then meet distinct banks).  Panel rows: a warp per row, lanes over the
+// columns with RP sums each, then one reduce-scatter; diagonal rows: lane = row, the
+// warps split the columns and their partial sums are added in order.  Every (row,
+// right-hand side) gets the multiply-adds and additions of cfwd_task_rb, bit for bit.
+// red2: NW x RP x 32.
+template <typename T, int NW, int RP>
+__device__ void cfwd_task_blk(const CView<T>& cf, const int4 tk, bool pan, T* ts, T* red2, T* xf, int j0, int nb) {
+    constexpr int RS = RP + 4;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int32_t J = tk.x, a0 = cf.c0[J], nJ = cf.c0[J + 1] - a0;
+    const int ncl = pan ? nJ : tk.y + tk.z;        // columns the task reads
+    for (int idx = threadIdx.x; idx < ncl * RP; idx += NW * 32) {
+        const int b = idx / ncl, i = idx - b * ncl;   // i fastest: coalesced reads of the gather
+        ts[i * RS + b] = b < nb ? cf.tws[a0 + i + (int64_t)(j0 + b) * cf.s] : T(0);
+    }
+    __syncthreads();
+    if (pan) {
+        const T* P = cf.panel + cf.pan_off[J];
+        for (int pr = warp; pr < tk.z; pr += NW) {
+            const int64_t p = tk.y + pr;
+            const T* Pp = P + p * nJ;
+            T acc[RP];
+#pragma unroll
+            for (int b = 0; b < RP; ++b) acc[b] = T(0);
+            auto madd = [&](T a, int c) {
+#pragma unroll
+                for (int q = 0; q < RP; q += 4) {
+                    T t4[4];
+                    ld4(ts + c * RS + q, t4);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) acc[q + e] += a * t4[e];
+                }
+            };
+            int c = lane;
+            for (; c + 7 * 32 < nJ; c += 8 * 32) {
+                T pv[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) pv[u] = Pp[c + 32 * u];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) madd(pv[u], c + 32 * u);
+            }
+            for (; c < nJ; c += 32) madd(Pp[c], c);
+            const T v = reduce_scatter<T, RP>(acc, lane);
+            const int k = rs_index<RP>(lane);
+            if (rs_writer<RP>(lane) && k < nb) cf.wbuf[cf.r_off[J] + p + (int64_t)(j0 + k) * cf.nrow] = v;
+        }
+    } else {
+        const T* D = cf.dinv + cf.dinv_off[J];
+        const int il = tk.y + lane;
+        const int ncol = tk.y + tk.z;
+        const int chunk = (ncol + NW - 1) / NW;
+        const int jb = warp * chunk, je = min(ncol, jb + chunk);
+        T acc[RP];
+#pragma unroll
+        for (int b = 0; b < RP; ++b) acc[b] = T(0);
+        auto madd = [&](T a, int c) {
+#pragma unroll
+            for (int q = 0; q < RP; q += 4) {
+                T t4[4];
+                ld4(ts + c * RS + q, t4);
+#pragma unroll
+                for (int e = 0; e < 4; ++e) acc[q + e] += a * t4[e];
+            }
+        };
+        if (lane < tk.z) {
+            const int jend = min(je, il + 1);
+            int jj = jb;
+            for (; jj + 7 < jend; jj += 8) {
+                T d[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) d[u] = D[packed_col(jj + u, nJ) + (il - jj - u)];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) madd(d[u], jj + u);
+            }
+            for (; jj < jend; ++jj) madd(D[packed_col(jj, nJ) + (il - jj)], jj);
+        }
+#pragma unroll
+        for (int b = 0; b < RP; ++b) red2[(warp * RP + b) * 32 + lane] = acc[b];
+        __syncthreads();
+        for (int b = warp; b < nb; b += NW) {
+            T v = T(0);
+#pragma unroll 8
+            for (int w = 0; w < NW; ++w) v += red2[(w * RP + b) * 32 + lane];
+            if (lane < tk.z) xf[a0 + il + (int64_t)(j0 + b) * cf.s] = v;
+        }
+    }
+    __syncthreads();
+}
+
 // Backward task (one CTA of NW warps) on RB right-hand sides: columns
 // c = tk.y .. tk.y + tk.z - 1 of x_J = L_JJ^{-T} y_J - M_J^T x_{R_J}.  The diagonal
 // part runs a warp per column (lanes over column c of L_JJ^{-1}, contiguous in the
@@ -464,6 +568,104 @@ __device__ void cbwd_task_rb(const CView<T>& cf, const int4 tk, T* us, T (*red)[
         }
         __syncthreads();
     }
+}
+
+// Backward task on a block of RP right-hand sides j0 .. j0 + nb - 1 in one pass: the
+// diagonal part as in cbwd_task_rb (a warp per column, lanes over the rows) with RP
+// sums per lane and one reduce-scatter; the panel part with lanes over the columns
+// and the warps splitting the panel rows, each warp staging the gathered rows of
+// x_{R_J} (32 rows x RP, one right-hand side per lane, row stride RP + 4) in its own
+// part of xs and reading them back by 16-byte broadcasts; its
+// partial sums then go to xs (the same buffer) and are added over the warps in
+// order.  Every column gets cbwd_task_rb's multiply-adds and additions, bit for bit.
+// us: RP x 32; xs: NW x 32 x (RP + 4).
+template <typename T, int NW, int RP>
+__device__ void cbwd_task_blk(const CView<T>& cf, const int4 tk, T* us, T* xs, const T* yf, T* xf, T* y_dd,
+                              int64_t ldy, int j0, int nb) {
+    constexpr int RS = RP + 4;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int32_t J = tk.x, a0 = cf.c0[J], nJ = cf.c0[J + 1] - a0, jl = tk.y + lane;
+    const int64_t nr = cf.r_off[J + 1] - cf.r_off[J];
+    const int32_t* R = cf.rows + cf.r_off[J];
+    const T* Pn = cf.panel + cf.pan_off[J] + jl;
+    const T* D = cf.dinv + cf.dinv_off[J];
+    const int64_t chunk = (nr + NW - 1) / NW, pb = warp * chunk, pe = min(nr, pb + chunk);
+    const T* y = yf + a0 + (int64_t)j0 * cf.s;
+    const T* x = xf + (int64_t)j0 * cf.s;
+    // right-hand side b of the block (zero past nb)
+    auto yv = [&](int b, int64_t i) { return b < nb ? y[(int64_t)b * cf.s + i] : T(0); };
+    for (int cc = warp; cc < tk.z; cc += NW) {
+        const int c = tk.y + cc;
+        const T* Dc = D + packed_col(c, nJ) - c;   // Dc[i] = (L_JJ^{-1})[i, c], i >= c
+        T acc[RP];
+#pragma unroll
+        for (int b = 0; b < RP; ++b) acc[b] = T(0);
+        int i = c + lane;
+        for (; i + 7 * 32 < nJ; i += 8 * 32) {
+            T d[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) d[u] = Dc[i + 32 * u];
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+#pragma unroll
+                for (int b = 0; b < RP; ++b) acc[b] += d[u] * yv(b, i + 32 * u);
+        }
+        for (; i < nJ; i += 32) {
+            const T d = Dc[i];
+#pragma unroll
+            for (int b = 0; b < RP; ++b) acc[b] += d * yv(b, i);
+        }
+        const T v = reduce_scatter<T, RP>(acc, lane);
+        if (rs_writer<RP>(lane)) us[rs_index<RP>(lane) * 32 + cc] = v;
+    }
+    T acc[RP];
+#pragma unroll
+    for (int b = 0; b < RP; ++b) acc[b] = T(0);
+    T* xw = xs + (size_t)warp * 32 * RS;               // this warp's rows
+    for (int64_t q0 = pb; q0 < pe; q0 += 32) {
+        const int nq = (int)min((int64_t)32, pe - q0);
+        // x_{R_J} rows q0 .. q0 + nq - 1: lane b loads right-hand side b of each
+        if (lane < RP) {
+            T v[8];
+            for (int pp0 = 0; pp0 < nq; pp0 += 8) {
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    v[u] = (pp0 + u < nq && lane < nb) ? x[(int64_t)lane * cf.s + R[q0 + pp0 + u]] : T(0);
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (pp0 + u < nq) xw[(pp0 + u) * RS + lane] = v[u];
+            }
+        }
+        __syncwarp();
+        if (lane < tk.z) {
+            for (int pp = 0; pp < nq; ++pp) {
+                const T pv = Pn[(q0 + pp) * nJ];
+#pragma unroll
+                for (int q = 0; q < RP; q += 4) {
+                    T t4[4];
+                    ld4(xw + pp * RS + q, t4);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) acc[q + e] += pv * t4[e];
+                }
+            }
+        }
+        __syncwarp();
+    }
+    __syncthreads();                                    // every warp is done with its rows: xs takes the sums
+#pragma unroll
+    for (int b = 0; b < RP; ++b) xs[(warp * RP + b) * 32 + lane] = acc[b];
+    __syncthreads();
+    for (int b = warp; b < nb; b += NW) {
+        if (lane < tk.z) {
+            T v = T(0);
+#pragma unroll 8
+            for (int w = 0; w < NW; ++w) v += xs[(w * RP + b) * 32 + lane];
+            const T r = us[b * 32 + lane] - v;
+            xf[a0 + jl + (int64_t)(j0 + b) * cf.s] = r;
+            if (y_dd) y_dd[cf.cperm[a0 + jl] + (int64_t)(j0 + b) * ldy] = r;
+        }
+    }
+    __syncthreads();
 }
 
 // All nrhs columns: blocks of 8 or 4 while us holds that many columns (rbmax), then
@@ -949,6 +1151,20 @@ k_cfwd_level(const CView<T> cf, int32_t t0, int32_t p0, int32_t np, const T* g, 
                          nrhs, red2);
 }
 
+// forward level, blocks of right-hand sides in passes of RP (cfwd_task_blk); dynamic
+// shared memory: t_J (tstride x (RP + 4)), then NW x RP x 32 partial sums
+template <typename T, int NW, int RP>
+__global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 1)
+k_cfwd_level_blk(const CView<T> cf, int32_t t0, int32_t p0, int32_t np, T* xf, int32_t nrhs, int32_t tstride) {
+    extern __shared__ __align__(16) unsigned char csm[];
+    const int q = blockIdx.x;
+    const bool pan = q < np;
+    T* ts = reinterpret_cast<T*>(csm);
+    T* red2 = ts + (size_t)tstride * (RP + 4);
+    const int4 tk = pan ? cf.ptasks[p0 + q] : cf.tasks[t0 + q - np];
+    for (int j0 = 0; j0 < nrhs; j0 += RP) cfwd_task_blk<T, NW, RP>(cf, tk, pan, ts, red2, xf, j0, min(RP, nrhs - j0));
+}
+
 // t_J = g_J - (gathered panel products) for every supernode of a level, once, into
 // cf.tws: block (q, c) takes entries c * 256 .. c * 256 + 255 of the (position,
 // right-hand side) pairs of the level's q-th supernode.  The per-level forward tasks
@@ -978,6 +1194,19 @@ k_cbwd_level(const CView<T> cf, int32_t t0, const T* yf, T* xf, T* y_dd, int64_t
     T* red2 = nrhs >= 4 ? reinterpret_cast<T*>(csm) : nullptr;        // NW x 8 x 32
     cbwd_task_cta<T, NW, sizeof(T) == 4 ? 16 : 8, 4>(cf, cf.tasks[t0 + blockIdx.x], us, 8, red, yf, xf, y_dd, ldy,
                                                       nrhs, red2);
+}
+
+// backward level, blocks of right-hand sides in passes of RP (cbwd_task_blk); dynamic
+// shared memory: us (RP x 32), then xs (NW x 32 x (RP + 4))
+template <typename T, int NW, int RP>
+__global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 1)
+k_cbwd_level_blk(const CView<T> cf, int32_t t0, const T* yf, T* xf, T* y_dd, int64_t ldy, int32_t nrhs) {
+    extern __shared__ __align__(16) unsigned char csm[];
+    T* us = reinterpret_cast<T*>(csm);
+    T* xs = us + RP * 32;
+    const int4 tk = cf.tasks[t0 + blockIdx.x];
+    for (int j0 = 0; j0 < nrhs; j0 += RP)
+        cbwd_task_blk<T, NW, RP>(cf, tk, us, xs, yf, xf, y_dd, ldy, j0, min(RP, nrhs - j0));
 }
 
 // right-hand sides per pass of the fused small levels' per-level kernels
@@ -1783,8 +2012,24 @@ cudaError_t launch_c_forward(const DevCFactor<T>& cf, const T* g_dd, int64_t ldg
             k_cfwd_gather<T><<<dim3(ns, chunks), 256, 0, st>>>(vl, s0, g_dd, ldg, nrhs);
             counted();
         }
-        // blocks of eight or four right-hand sides share each matrix load when t_J of that many fits
         const bool wide = nt + np <= cf.nsm;
+        // blocks of 8 or more with the level's gather: one pass per 32 (16 in the wide
+        // variant) right-hand sides when t_J of the level's widest supernode fits
+        if (nrhs >= 8 && vl.tws) {
+            const int32_t ts_n = cf.lev_maxn[l] > 0 ? cf.lev_maxn[l] : cf.max_n;
+            const int rp = wide ? 16 : 32;
+            const size_t sm = ((size_t)ts_n * (rp + 4) + (size_t)(wide ? 32 : 8) * rp * 32) * sizeof(T);
+            const void* kb = wide ? (const void*)k_cfwd_level_blk<T, 32, 16> : (const void*)k_cfwd_level_blk<T, 8, 32>;
+            if (sm <= kLevSmem && (sm <= 48 * 1024 || raise_smem_once(kb))) {
+                if (wide)
+                    k_cfwd_level_blk<T, 32, 16><<<nt + np, 1024, sm, st>>>(vl, t0, p0, np, xf, nrhs, ts_n);
+                else
+                    k_cfwd_level_blk<T, 8, 32><<<nt + np, 256, sm, st>>>(vl, t0, p0, np, xf, nrhs, ts_n);
+                counted();
+                continue;
+            }
+        }
+        // blocks of eight or four right-hand sides share each matrix load when t_J of that many fits
         const void* kern = wide ? (const void*)k_cfwd_level<T, 32> : (const void*)k_cfwd_level<T, 8>;
         // t_J of rbmax columns, then (blocks) the diagonal tasks' partial sums, NW x rbmax x 32
         auto need = [&](int32_t rb) {
@@ -1840,6 +2085,24 @@ cudaError_t launch_c_backward(const DevCFactor<T>& cf, const T* yf, T* xf, T* y_
         }
         const int t0 = cf.lev_task_ptr[l], nt = cf.lev_task_ptr[l + 1] - t0;
         if (nt == 0) continue;
+        if (nrhs >= 8) {                               // blocks of 8 or more: one pass per 32 (16 wide)
+            const bool wide = nt <= cf.nsm;
+            if (!wide) {
+                const size_t sm = ((size_t)32 * 32 + (size_t)8 * 32 * 36) * sizeof(T);
+                if (sm <= 48 * 1024 || raise_smem_once((const void*)k_cbwd_level_blk<T, 8, 32>)) {
+                    k_cbwd_level_blk<T, 8, 32><<<nt, 256, sm, st>>>(v, t0, yf, xf, y_dd, ldy, nrhs);
+                    counted();
+                    continue;
+                }
+            } else {
+                const size_t sm = ((size_t)16 * 32 + (size_t)32 * 32 * 20) * sizeof(T);
+                if (sm <= 48 * 1024 || raise_smem_once((const void*)k_cbwd_level_blk<T, 32, 16>)) {
+                    k_cbwd_level_blk<T, 32, 16><<<nt, 1024, sm, st>>>(v, t0, yf, xf, y_dd, ldy, nrhs);
+                    counted();
+                    continue;
+                }
+            }
+        }
         // blocks of four or more: the panel part's partial sums, NW x 8 x 32
         if (nt > cf.nsm) {
             const size_t sm = nrhs >= 4 ? (size_t)8 * 8 * 32 * sizeof(T) : 0;
