@@ -305,9 +305,10 @@ def run_profile(args):
             precision=args.precision, nrhs_max=nrhs, flexible_cg=(args.precision == "mixed"),
             host_loop=args.host_loop, autotune=not args.no_autotune, **tc)   # the bench's kernel choices
     info = h.get_info()
-    f = torch.randn(info["n_interior"], nrhs, dtype=torch.float64, device="cuda")
-    g = torch.randn(info["s"], nrhs, dtype=torch.float64, device="cuda")
-    r = torch.randn(P.n, nrhs, dtype=torch.float64, device="cuda")
+    # column-major blocks, the layout the library takes: the binding passes them without a copy
+    f = torch.randn(nrhs, info["n_interior"], dtype=torch.float64, device="cuda").t()
+    g = torch.randn(nrhs, info["s"], dtype=torch.float64, device="cuda").t()
+    r = torch.randn(nrhs, P.n, dtype=torch.float64, device="cuda").t()
     step = {"pcg": lambda: h.pcg(b, maxit=maxit, check=False), "bsolve": lambda: h.bsolve(f),
             "csolve": lambda: h.csolve(g), "apply": lambda: h.apply(r)}[args.profile_kernel]
     for _ in range(args.warmup):
