@@ -58,7 +58,8 @@ __host__ __device__ inline int tc_blocks(int32_t s) {
     return b < 1 ? 1 : (b > 1024 ? 1024 : b);
 }
 
-template <int AB>
+// UK, WK: columns of U (k <= 4 UK) and of W (nrhs <= 4 WK) a thread holds per chunk
+template <int AB, int UK, int WK>
 __global__ void __launch_bounds__(kTcThreads, 1)
 k_lr_vt_tc(int32_t s, int32_t k, int32_t nrhs, int32_t np, const typename TcType<AB>::U* __restrict__ Ucm,
            const float* __restrict__ w, float* part, int32_t* err) {
@@ -96,23 +97,45 @@ k_lr_vt_tc(int32_t s, int32_t k, int32_t nrhs, int32_t np, const typename TcType
     const uint32_t idesc = tc::instr_desc(AB, M, np);
     bool ok = true;
     int nchunks = 0;
+    // a thread's share of a chunk: row q of s, columns m = m0 + 4 i of U (i < UK) and
+    // n = m0 + 4 i of W (i < WK); its values are loaded into registers one chunk ahead,
+    // so the loads of the next chunk are in flight while this one's MMAs run
+    constexpr int kStep = kTcThreads / kTcKc;
+    const int q = t % kTcKc, m0 = t / kTcKc;        // consecutive threads: consecutive rows (coalesced)
+    static_assert(kStep == 4, "four rows of U and W per thread step");
+    float ur[UK], wr[WK];
+    auto fetch = [&](int c0) {
+        const int rows = min(kTcKc, r1 - c0);
+#pragma unroll
+        for (int i = 0; i < UK; ++i) {
+            const int m = m0 + kStep * i;
+            ur[i] = (q < rows && m < k) ? load_u<AB>(Ucm + (c0 + q) + (int64_t)m * s) : 0.0f;
+        }
+#pragma unroll
+        for (int i = 0; i < WK; ++i) {
+            const int n = m0 + kStep * i;
+            wr[i] = (q < rows && n < nrhs) ? w[(c0 + q) + (int64_t)n * s] : 0.0f;
+        }
+    };
+    if (r0 < r1) fetch(r0);
     for (int c0 = r0; c0 < r1; c0 += kTcKc, ++nchunks) {
         const int st = nchunks & 1;
         if (nchunks >= 2 && ok) ok = tc::mbar_wait(&bar[st], (uint32_t)(((nchunks - 2) >> 1) & 1), kTcSpin);
         ok = __syncthreads_and(ok);
         if (!ok) break;
-        const int rows = min(kTcKc, r1 - c0);
         unsigned char* a = sA + st * kA;
         unsigned char* b = sB + st * kB;
-        const int q = t % kTcKc;                     // row of s in the chunk (consecutive threads: coalesced)
-        for (int m = t / kTcKc; m < k; m += kTcThreads / kTcKc) {
-            const float v = q < rows ? load_u<AB>(Ucm + (c0 + q) + (int64_t)m * s) : 0.0f;
-            *reinterpret_cast<Te*>(a + tc::kmajor_off<E>(m, q, kTcKc)) = Tp::pack(v);
+#pragma unroll
+        for (int i = 0; i < UK; ++i) {
+            const int m = m0 + kStep * i;
+            if (m < k) *reinterpret_cast<Te*>(a + tc::kmajor_off<E>(m, q, kTcKc)) = Tp::pack(ur[i]);
         }
-        for (int n = t / kTcKc; n < nrhs; n += kTcThreads / kTcKc) {
-            const float v = q < rows ? w[(c0 + q) + (int64_t)n * s] : 0.0f;
-            *reinterpret_cast<Te*>(b + tc::kmajor_off<E>(n, q, kTcKc)) = Tp::pack(v);
+#pragma unroll
+        for (int i = 0; i < WK; ++i) {
+            const int n = m0 + kStep * i;
+            if (n < nrhs) *reinterpret_cast<Te*>(b + tc::kmajor_off<E>(n, q, kTcKc)) = Tp::pack(wr[i]);
         }
+        if (c0 + kTcKc < r1) fetch(c0 + kTcKc);
         tc::fence_async_smem();
         __syncthreads();
         if (t == 0) {
@@ -179,10 +202,19 @@ k_lr_update_tc(int32_t s, int32_t k, int32_t kp, int32_t nrhs, int32_t np, const
     }
     const int64_t i0 = (int64_t)blockIdx.x * M;
     const int rows = (int)((s - i0) < M ? (s - i0) : M);
-    for (int e = t; e < M * kp; e += kTcThreads) {
-        const int r = e / kp, q = e % kp;
-        const float v = (r < rows && q < k) ? load_u<AB>(Urm + (i0 + r) * k + q) : 0.0f;
-        *reinterpret_cast<Te*>(sA + tc::kmajor_off<E>(r, q, kp)) = Tp::pack(v);
+    // rows of U: sixteen loads in flight per thread before any is stored
+    for (int e0 = t; e0 < M * kp; e0 += 16 * kTcThreads) {
+        float v[16];
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const int e = e0 + u * kTcThreads, r = e / kp, q = e % kp;
+            v[u] = (e < M * kp && r < rows && q < k) ? load_u<AB>(Urm + (i0 + r) * k + q) : 0.0f;
+        }
+#pragma unroll
+        for (int u = 0; u < 16; ++u) {
+            const int e = e0 + u * kTcThreads, r = e / kp, q = e % kp;
+            if (e < M * kp) *reinterpret_cast<Te*>(sA + tc::kmajor_off<E>(r, q, kp)) = Tp::pack(v[u]);
+        }
     }
     for (int e = t; e < np * kp; e += kTcThreads) {
         const int n = e / kp, q = e % kp;
@@ -212,12 +244,12 @@ k_lr_update_tc(int32_t s, int32_t k, int32_t kp, int32_t nrhs, int32_t np, const
             float v[32];
             tc::tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c, v);
             if (r < rows) {
+                float o[32];
+#pragma unroll
+                for (int j = 0; j < 32; ++j) o[j] = c + j < nrhs ? w[i0 + r + (int64_t)(c + j) * s] : 0.0f;
 #pragma unroll
                 for (int j = 0; j < 32; ++j)
-                    if (c + j < nrhs) {
-                        float* p = w + i0 + r + (int64_t)(c + j) * s;
-                        *p = cinv * *p + v[j];
-                    }
+                    if (c + j < nrhs) w[i0 + r + (int64_t)(c + j) * s] = cinv * o[j] + v[j];
             }
         }
     }
@@ -229,15 +261,36 @@ k_lr_update_tc(int32_t s, int32_t k, int32_t kp, int32_t nrhs, int32_t np, const
     }
 }
 
-// V^T of pass 1 needs d o (sum over blocks), the CUDA-core pass's final kernel
-__global__ void k_lr_fin_tc(int32_t k, int32_t nrhs, int32_t G, const float* __restrict__ part,
-                            const float* __restrict__ dvec, float* vk) {
-    const int id = blockIdx.x * blockDim.x + threadIdx.x;
-    if (id >= k * nrhs) return;
-    const int kk = id % k, j = id / k;
+// V = d o (sum over the pass-1 blocks of their partial products), in a fixed order:
+// block (kk, j-group) has kFinSeg segments of the G blocks, each summed in order by
+// its threads (the right-hand sides j fastest: coalesced), then the segment sums
+// added in order
+constexpr int kFinSeg = 16, kFinJ = 16;
+__global__ void __launch_bounds__(kFinSeg * kFinJ)
+k_lr_fin_tc(int32_t k, int32_t nrhs, int32_t G, const float* __restrict__ part, const float* __restrict__ dvec,
+            float* vk) {
+    __shared__ float seg[kFinSeg][kFinJ];
+    const int kk = blockIdx.x, j = blockIdx.y * kFinJ + (threadIdx.x % kFinJ), q = threadIdx.x / kFinJ;
+    const int len = (G + kFinSeg - 1) / kFinSeg, b0 = q * len, b1 = min(G, b0 + len);
     float acc = 0.0f;
-    for (int b = 0; b < G; ++b) acc += part[((int64_t)b * k + kk) * nrhs + j];
-    vk[kk + (int64_t)j * k] = dvec[kk] * acc;
+    if (j < nrhs) {
+        int b = b0;
+        for (; b + 4 <= b1; b += 4) {
+            float v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) v[u] = part[((int64_t)(b + u) * k + kk) * nrhs + j];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) acc += v[u];
+        }
+        for (; b < b1; ++b) acc += part[((int64_t)b * k + kk) * nrhs + j];
+    }
+    seg[q][threadIdx.x % kFinJ] = acc;
+    __syncthreads();
+    if (q == 0 && j < nrhs) {
+        float v = 0.0f;
+        for (int qq = 0; qq < kFinSeg; ++qq) v += seg[qq][threadIdx.x];
+        vk[kk + (int64_t)j * k] = dvec[kk] * v;
+    }
 }
 
 template <typename Te>
@@ -263,10 +316,13 @@ cudaError_t launch_tc(const DevOperator<float>& op, int32_t s, int32_t k, float*
     const int G = tc_blocks(s);
     const Te* Ucm = AB == 2 ? reinterpret_cast<const Te*>(op.U) : reinterpret_cast<const Te*>(op.U_tc_cm);
     const size_t sm1 = 2 * (128 + 64) * kTcKc * E + 64;
-    cudaError_t e = cudaFuncSetAttribute(k_lr_vt_tc<AB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
+    // registers per thread for the chunk prefetch: as many as k and nrhs need
+    auto vt = k <= 64 ? (np <= 32 ? k_lr_vt_tc<AB, 16, 8> : k_lr_vt_tc<AB, 16, 16>)
+                      : (np <= 32 ? k_lr_vt_tc<AB, 32, 8> : k_lr_vt_tc<AB, 32, 16>);
+    cudaError_t e = cudaFuncSetAttribute(vt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
     if (e != cudaSuccess) return e;
-    k_lr_vt_tc<AB><<<G, kTcThreads, sm1, st>>>(s, k, nrhs, np, Ucm, w, op.part, op.err);
-    k_lr_fin_tc<<<(k * nrhs + 255) / 256, 256, 0, st>>>(k, nrhs, G, op.part, op.dvec, op.vk);
+    vt<<<G, kTcThreads, sm1, st>>>(s, k, nrhs, np, Ucm, w, op.part, op.err);
+    k_lr_fin_tc<<<dim3(k, (nrhs + kFinJ - 1) / kFinJ), kFinSeg * kFinJ, 0, st>>>(k, nrhs, G, op.part, op.dvec, op.vk);
     const int kp = AB == 2 ? (k + 7) / 8 * 8 : (k + 15) / 16 * 16;
     const size_t sm2 = (size_t)(128 + 64) * kp * E + 64;
     // the limit is process-wide state of the kernel: always the same (largest) value,
