@@ -18,6 +18,7 @@ bounded sample of the headline workload instead.
 from __future__ import annotations
 
 import argparse
+import copy
 import json
 import os
 import statistics
@@ -109,6 +110,7 @@ class ClockSampler:
 # the source files of each kernel whose ncu traffic a committed summary records
 KERNEL_SOURCES = {
     "band": ("slr_band_kernel.cuh", "slr_band.cu", "slr_band_half.cu"),
+    "band_tc": ("slr_band_tc.cu", "slr_tc.cuh"),
     "csolve": ("slr_kernels.cu",),
     "lowrank": ("slr_kernels.cu",),
 }
@@ -439,13 +441,44 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e-3
 TRAFFIC_SUMMARIES = {
     ("band", "3d64", "fp64"): "k_band_solve2_fp64_3d64.txt",
     ("band", "3d64", "mixed"): "k_band_solve2_fp32_3d64.txt",
+    ("band_tc", "3d96aniso", "mixed"): "k_band_tc_tf32_3d96aniso_r32.txt",
 }
+
+
+def tensor_peak(dtype):
+    """Dense tensor peak (TFLOP/s) for a contraction's input type: the measured BF16
+    cuBLAS rate, times the nominal TF32 / BF16 ratio (1.1 / 2.25) for TF32."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            bf16 = float(json.load(f)["bf16_tflops"])
+        src = "measured bf16"
+    except Exception:
+        bf16, src = 1900.0, "fallback bf16"
+    return (bf16, src) if dtype == "bf16" else (bf16 * 1.1 / 2.25, src + " x 1.1/2.25 (nominal tf32/bf16)")
 
 
 def kernel_roofline(kind, info, prec, nrhs, us, hbm, hbm_src, name):
     """Roofline of one kernel launch: algorithmic bytes and flops per launch (each
     operand read once per use) against HBM and the ALU of its precision."""
     wf = 8 if prec == "fp64" else 4
+    tc_band = kind == "band" and prec == "mixed" and nrhs >= 8 and info.get("band_mma", 0) != 0
+    if tc_band:               # one B-solve on the tensor cores: the factor in TF32 (4 bytes) or BF16 (2)
+        dt = "tf32" if info["band_mma"] == 1 else "bf16"
+        entries = info["band_entries"]
+        ef = 4 if dt == "tf32" else 2
+        nbytes = 2 * entries * ef + 2 * info["n_interior"] * nrhs * wf
+        flops = 2 * 2 * entries * nrhs
+        gbs, tfs = nbytes / us / 1e3, flops / us / 1e6
+        tpk, tsrc = tensor_peak(dt)
+        f_hbm, f_t = gbs / hbm, tfs / tpk
+        summary = TRAFFIC_SUMMARIES.get(("band_tc", name, prec)) if dt == "tf32" else None
+        traffic = captured_traffic(summary, "band_tc") if summary else None
+        common = {"kernel": f"k_band_tc (K1 on the tensor cores, {dt}, one B-solve)", "us": us,
+                  "algorithmic_bytes": nbytes, "flops": flops, "traffic": traffic, "hbm_frac": f_hbm,
+                  "tensor_frac": f_t}
+        if f_t > f_hbm:
+            return dict(bound="tensor", achieved=tfs, peak=tpk, unit="TFLOP/s", frac=f_t, peak_source=tsrc, **common)
+        return dict(bound="hbm", achieved=gbs, peak=hbm, unit="GB/s", frac=f_hbm, peak_source=hbm_src, **common)
     if kind == "band":        # one B-solve: forward and backward pass over the band factor
         entries = info["band_entries"]
         vec = 2 * info["n_interior"] * nrhs * wf
@@ -631,6 +664,18 @@ def run_ours(args):
     hm = measure(args, name, "mixed", args.steps, args.warmup, ctx, headline=True)
     x_diff = float(np.max(np.linalg.norm(hm["_x"] - h64["_x"], axis=0) / np.linalg.norm(h64["_x"], axis=0)))
     z_diff = float(np.abs(hm["_z"] - h64["_z"]).max() / np.abs(h64["_z"]).max())
+    bf16 = None
+    if PROBLEMS[name][1] >= 8 and (args.band_mma != "bf16" or args.u_dtype != "bf16") and not args.no_bf16_leg:
+        # the same workload with BF16 tensor-core operands (band factor and U_k)
+        a16 = copy.copy(args)
+        a16.band_mma, a16.u_dtype = "bf16", "bf16"
+        hb = measure(a16, name, "mixed", short, 1, ctx)
+        bf16 = {k: hb[k] for k in ("solves_per_s", "ms_per_step", "iterations", "true_relres", "x_err_vs_xstar",
+                                   "band_us", "c_us", "apply_us")}
+        bf16["x_rel_diff_vs_fp64"] = float(np.max(np.linalg.norm(hb["_x"] - h64["_x"], axis=0) /
+                                                  np.linalg.norm(h64["_x"], axis=0)))
+        bf16["apply_rel_diff_vs_fp64"] = float(np.abs(hb["_z"] - h64["_z"]).max() / np.abs(h64["_z"]).max())
+        bf16["roofline_band"] = hb["rooflines"]["band"]
     others = {}
     if not args.headline_only:
         for other in ("3d64", "2d1024fv"):
@@ -678,6 +723,7 @@ def run_ours(args):
                   "share": hm["apply_share"], "band_solve_us": hm["band_us"], "c_solve_us": hm["c_us"]},
         "x_rel_diff_vs_fp64": x_diff, "apply_rel_diff_vs_fp64": z_diff,
         "fp64": public(h64), "mixed_over_fp64": hm["solves_per_s"] / h64["solves_per_s"],
+        "mixed_bf16": bf16,
         "roofline": hm["roofline"], "rooflines": hm["rooflines"],
         "cpu_baseline": cpu,
         "e2e": hm["e2e"],
@@ -701,6 +747,7 @@ def main():
     ap.add_argument("--problem", default=None, choices=list(PROBLEMS),
                     help="the workload (default: the 3-D 96^3 block of 32 right-hand sides)")
     ap.add_argument("--headline-only", action="store_true", help="skip the other workloads and legs")
+    ap.add_argument("--no-bf16-leg", action="store_true", help="skip the headline's BF16 tensor-core variant")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-single-thread", action="store_true",
                     help="also time the CPU baseline's sample with one BLAS/OpenMP thread (a second oracle setup)")
