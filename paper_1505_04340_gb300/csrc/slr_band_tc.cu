@@ -210,12 +210,12 @@ k_band_tc(const BandTcBlock* __restrict__ blocks, const unsigned char* __restric
     uint64_t* fin_bar = opnd_bar + 1;
     uint32_t* tbase = reinterpret_cast<uint32_t*>(fin_bar + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tbase + 1);
-    // the epilogue's global operands of a block (F_J, Y_J or the base), staged by cp.async
-    // before the accumulator wait: [M-tile][column][epilogue thread]
-    float* pre_s = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(tbase) + 16);
     const int tid = threadIdx.x, warp = tid >> 5;
     const int nM = (W + 127) / 128;
-    const uint32_t ncol = nM * NP <= 32 ? 32 : nM * NP <= 64 ? 64 : 128;
+    // tensor memory: the accumulators (M-tile mt at column mt NP), then as many columns
+    // holding the epilogue's global operand of a block (F_J, Y_J or the base), written
+    // by the epilogue threads while the block's MMAs run
+    const uint32_t acols = nM * NP <= 32 ? 32 : nM * NP <= 64 ? 64 : 128, ncol = 2 * acols;
     if (warp == 0) {
         tc::tmem_alloc(tbase, ncol);
         tc::tmem_relinquish();
@@ -345,7 +345,8 @@ k_band_tc(const BandTcBlock* __restrict__ blocks, const unsigned char* __restric
         for (int q = 0; q < nblk; ++q) {
             const BtBlock bk = bt_block(q, c);
             const int J = bk.vplane;
-            // this block's global operands into shared memory while its MMAs run
+            // this block's global operand into tensor memory while its MMAs run (the
+            // previous block's epilogue, by these threads, has read the columns)
             const bool need_pre = bk.type == 0 || bk.type == 2 || (bk.type == 3 && base);
             if (need_pre) {
                 const float* srcb = bk.type == 0 ? in : bk.type == 2 ? out : base;
@@ -354,31 +355,24 @@ k_band_tc(const BandTcBlock* __restrict__ blocks, const unsigned char* __restric
                     const int r = 128 * mt + e;
                     const bool ok = valid(J, r);
                     const int64_t row = row_of(J, r);
-                    for (int j = 0; j < nrhs; ++j) {
-                        float* dst = pre_s + ((size_t)mt * NP + j) * 128 + e;
-                        if (ok)
-                            asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(tc::smem_addr(dst)),
-                                         "l"(srcb + row + j * lds)
-                                         : "memory");
-                        else
-                            *dst = 0.0f;
+#pragma unroll
+                    for (int c0 = 0; c0 < NP; c0 += 32) {
+                        float pv[32];
+#pragma unroll
+                        for (int jj = 0; jj < 32; ++jj)
+                            pv[jj] = (ok && c0 + jj < nrhs) ? srcb[row + (c0 + jj) * lds] : 0.0f;
+                        tc::tmem_st32(tmem + lane_addr + acols + (uint32_t)(mt * NP + c0), pv);
                     }
                 }
-                asm volatile("cp.async.commit_group;" ::: "memory");
             }
             // the warp decides together (tcgen05.ld below is warp-collective)
             bool ok = tc::mbar_wait(acc_bar, (uint32_t)(q & 1), kBtSpin);
             if (!__all_sync(0xffffffffu, ok)) {
                 if ((tid & 31) == 0) fail();
-                asm volatile("cp.async.wait_all;" ::: "memory");
                 break;
             }
-            if (__any_sync(0xffffffffu, *abort_flag != 0)) {
-                asm volatile("cp.async.wait_all;" ::: "memory");
-                break;
-            }
+            if (__any_sync(0xffffffffu, *abort_flag != 0)) break;
             tc::fence_after_sync();
-            if (need_pre) asm volatile("cp.async.wait_all;" ::: "memory");
             for (int mt = 0; mt < nM; ++mt) {
                 const int r = 128 * mt + e;
                 const bool in_w = r < W, ok_r = valid(J, r);
@@ -388,10 +382,19 @@ k_band_tc(const BandTcBlock* __restrict__ blocks, const unsigned char* __restric
                 for (int c0 = 0; c0 < NP; c0 += 32) {
                     float v[32];
                     tc::tmem_ld32(tmem + lane_addr + (uint32_t)(mt * NP + c0), v);
-                    const float* pre = pre_s + ((size_t)mt * NP + c0) * 128 + e;
-                    if (bk.type == 0 || bk.type == 2) {          // t = F_J - O_J Y_{J-1}  /  Y_J - O^T X
+                    const uint32_t pre_col = tmem + lane_addr + acols + (uint32_t)(mt * NP + c0);
+                    // v := pre - v (the operand's columns past nrhs were stored as zeros)
+                    auto pre_minus = [&]() {
 #pragma unroll
-                        for (int jj = 0; jj < 32; ++jj) v[jj] = (c0 + jj < nrhs ? pre[jj * 128] : 0.0f) - v[jj];
+                        for (int h = 0; h < 2; ++h) {
+                            float p[16];
+                            tc::tmem_ld16(pre_col + 16 * h, p);
+#pragma unroll
+                            for (int i = 0; i < 16; ++i) v[16 * h + i] = p[i] - v[16 * h + i];
+                        }
+                    };
+                    if (bk.type == 0 || bk.type == 2) {          // t = F_J - O_J Y_{J-1}  /  Y_J - O^T X
+                        pre_minus();
                         put_rows(v1, rbase, c0, v);
                     } else if (bk.type == 1) {                   // Y_J = D_J t
                         if (in_w && ok_r) {
@@ -400,11 +403,22 @@ k_band_tc(const BandTcBlock* __restrict__ blocks, const unsigned char* __restric
                                 if (c0 + jj < nrhs) out[row + (c0 + jj) * ldo] = v[jj];
                         }
                         put_rows(v0, rbase, c0, v);             // also the backward's first t (J = c - 1)
-                    } else {                                     // X_J = D_J^T t
-                        if (in_w && ok_r) {
+                    } else {                                     // X_J = D_J^T t (out: base - X_J with a base)
+                        if (base) {
+#pragma unroll
+                            for (int h = 0; h < 2; ++h) {
+                                float p[16];
+                                tc::tmem_ld16(pre_col + 16 * h, p);    // warp-collective: every lane
+                                if (in_w && ok_r) {
+#pragma unroll
+                                    for (int i = 0; i < 16; ++i)
+                                        if (c0 + 16 * h + i < nrhs) out[row + (c0 + 16 * h + i) * ldo] = p[i] - v[16 * h + i];
+                                }
+                            }
+                        } else if (in_w && ok_r) {
 #pragma unroll
                             for (int jj = 0; jj < 32; ++jj)
-                                if (c0 + jj < nrhs) out[row + (c0 + jj) * ldo] = base ? pre[jj * 128] - v[jj] : v[jj];
+                                if (c0 + jj < nrhs) out[row + (c0 + jj) * ldo] = v[jj];
                         }
                         put_rows(v0, rbase, c0, v);
                     }
@@ -427,7 +441,7 @@ cudaError_t bt_launch(const DevOperator<float>& op, int32_t p, const float* in, 
     constexpr int E = BtType<AB>::E, KS = BtType<AB>::KS;
     const int WK = bt_nk(op.band_tc_wmax, KS) * KS;
     const size_t vbytes = (size_t)NP * WK * E;
-    const size_t fixed = vbytes + 8 * (2 * 8 + 3) + 16 + (size_t)2 * NP * 128 * sizeof(float);
+    const size_t fixed = vbytes + 8 * (2 * 8 + 3) + 16;
     // ring: as many 4-sub-tile slots (16 KB) as fit, 2 .. 8, in the opt-in maximum or,
     // with more subdomains than SMs, in half an SM (113 KB: two CTAs per SM, one wave)
     const int stiles = 4;

@@ -153,6 +153,25 @@ def test_band_solve_on_tensor_cores_matches_oracle(name, mma, nrhs):
 
 
 @pytest.mark.parametrize("mma", ["tf32", "bf16"])
+def test_apply_with_tensor_core_band_solve(mma):
+    """The whole apply (Eq. 4.1) with both B-solves on the tensor cores, the second
+    one subtracting from its base (u = t - B^{-1} E y), against the same operator's
+    CUDA-core FP32 apply on 16 columns: within 16 u of the operand type relative to
+    the largest entry, as each B-solve is (a base misapplied moves it by O(1))."""
+    P = _problem("3d-lap", nrhs=16)
+    kw = dict(k=P.k, lanczos_steps=P.lanczos_steps, precision="mixed", nrhs_max=16)
+    h0 = SLR(P.rowptr, P.colind, P.val, P.part, P.nparts, **kw)
+    h1 = SLR(P.rowptr, P.colind, P.val, P.part, P.nparts, band_mma=mma, **kw)
+    R = cu(np.random.default_rng(31).standard_normal((P.rowptr.size - 1, 16)))
+    z0, z1 = h0.apply(R).cpu().numpy(), h1.apply(R).cpu().numpy()
+    err = float((np.abs(z1 - z0).max(axis=0) / np.abs(z0).max(axis=0)).max())
+    print(f"apply with the {mma} band solve: {err:.2e} (bound {16 * U_TC[mma]:.2e})")
+    assert err <= 16 * U_TC[mma]
+    h0.close()
+    h1.close()
+
+
+@pytest.mark.parametrize("mma", ["tf32", "bf16"])
 def test_mixed_pcg_with_tensor_core_band_solve(mma):
     """Flexible CG absorbs the rounded factor: every column reaches 1e-8 and the
     solution matches the FP64 oracle's to 1e-7."""
