@@ -442,6 +442,7 @@ TRAFFIC_SUMMARIES = {
     ("band", "3d64", "fp64"): "k_band_solve2_fp64_3d64.txt",
     ("band", "3d64", "mixed"): "k_band_solve2_fp32_3d64.txt",
     ("band_tc", "3d96aniso", "mixed"): "k_band_tc_tf32_3d96aniso_r32.txt",
+    ("csolve", "3d96aniso", "mixed"): "c_solve_fp32_3d96aniso_r32.txt",
 }
 
 
