@@ -588,6 +588,8 @@ def measure(args, name, prec, steps, warmup, ctx, headline=False):
     lib.slr_apply(hh, R.data_ptr(), Z.data_ptr(), nrhs, P.n, sp_)
     z = Z.cpu().numpy()
     hbm, hbm_src = peaks()
+    # a block apply reads the factors, U_k and the index arrays once, the vectors once per column
+    block_bytes = info["bytes_per_apply"] + (nrhs - 1) * info["vector_bytes_per_column"]
     roof = {"band": kernel_roofline("band", info, prec, nrhs, band_us, hbm, hbm_src, name),
             "csolve": kernel_roofline("csolve", info, prec, nrhs, c_us, hbm, hbm_src, name)}
     dominant = "band" if 2 * band_us >= c_us else "csolve"
@@ -595,8 +597,8 @@ def measure(args, name, prec, steps, warmup, ctx, headline=False):
                p50_ms=float(np.percentile(per, 50)), p99_ms=float(np.percentile(per, 99)),
                iterations=int(its.max()), iterations_min=int(its.min()), relres=float(np.max(rel)),
                true_relres=true_rel, x_err_vs_xstar=x_err, setup_s=setup_s, launches=launches, clocks=clocks,
-               apply_us=apply_us, apply_gbs=info["bytes_per_apply"] * nrhs / apply_us / 1e3,
-               bytes_per_apply=info["bytes_per_apply"] * nrhs, band_us=band_us, c_us=c_us,
+               apply_us=apply_us, apply_gbs=block_bytes / apply_us / 1e3,
+               bytes_per_apply=block_bytes, band_us=band_us, c_us=c_us,
                apply_share={"band (2 B-solves)": 2 * band_us / apply_us, "C solve": c_us / apply_us},
                roofline=roof[dominant], rooflines=roof,
                tuning={"band_split": info["band_split"], "band_slots": info["band_slots"],

@@ -152,7 +152,7 @@ typedef struct {
     int64_t c_diag_entries;      /* stored entries of the inverted supernode diagonal blocks */
     int64_t c_panel_entries;     /* stored entries of the supernode off-diagonal panels      */
     int64_t c_supernodes, c_levels;
-    int64_t bytes_per_apply;     /* algorithmic bytes one apply reads/writes per RHS column */
+    int64_t bytes_per_apply;     /* algorithmic bytes one apply of one RHS column reads/writes */
     int64_t flops_per_apply;     /* multiply-adds x 2 of one apply per RHS column          */
     int64_t device_bytes;        /* device memory the handle holds                          */
     double theta;                /* theta used in S~^{-1}                                  */
@@ -174,6 +174,11 @@ typedef struct {
     int32_t band_mma;            /* the band solve's tensor-core factor in use: 0 (none),
                                     SLR_U_TF32 or SLR_U_BF16 (opts.band_mma)               */
     int32_t u_dtype;             /* the low-rank products' arithmetic (opts.u_dtype)        */
+    int64_t vector_bytes_per_column; /* the part of bytes_per_apply that every further column of
+                                    a block repeats (vectors, the w values written and
+                                    gathered); the factors, U_k and the index arrays are read
+                                    once per block: a block of r columns moves
+                                    bytes_per_apply + (r - 1) vector_bytes_per_column        */
 } slr_info;
 
 /* Fill *opts with defaults: k = 16, m = 5k, theta = lambda_{k+1}, FP64, 1 RHS, seed 1. */

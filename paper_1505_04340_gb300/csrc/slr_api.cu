@@ -684,6 +684,7 @@ void account(slr_handle h) {
     h->bytes_per_apply = 4 * band * wf + 2 * nnzE * (wf + 4) + 2 * cvals * wf + nseg * (4 + wf) + nrow * (4 + wf) +
                          2 * s * k * wf + (2 * (int64_t)hs.n + 2 * (int64_t)hs.nI) * wv;
     h->flops_per_apply = 2 * (4 * band + 2 * nnzE + 2 * cvals + 2 * s * k);
+    h->vector_bytes_per_column = nseg * wf + nrow * wf + (2 * (int64_t)hs.n + 2 * (int64_t)hs.nI) * wv;
 }
 
 // ------------------------------------------------------------------ autotuning
@@ -1716,6 +1717,7 @@ slr_status slr_get_info(slr_handle h, slr_info* info) {
     info->c_supernodes = hs.cf.ns;
     info->c_levels = hs.cf.nlev;
     info->bytes_per_apply = h->bytes_per_apply;
+    info->vector_bytes_per_column = h->vector_bytes_per_column;
     info->flops_per_apply = h->flops_per_apply;
     info->device_bytes = h->device_bytes;
     info->theta = h->theta;

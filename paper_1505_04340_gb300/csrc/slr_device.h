@@ -129,7 +129,7 @@ struct slr_handle_s {
     std::vector<void*> allocs;       // every device allocation, freed by slr_destroy
     int64_t device_bytes = 0;
     double setup_seconds[5] = {0, 0, 0, 0, 0};
-    int64_t bytes_per_apply = 0, flops_per_apply = 0;
+    int64_t bytes_per_apply = 0, flops_per_apply = 0, vector_bytes_per_column = 0;
     bool tuned = false;
     double tune_seconds = 0.0;
     // band factorization on the device: per-subdomain plane blocks D_J and O_J

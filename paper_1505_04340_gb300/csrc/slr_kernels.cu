@@ -872,6 +872,57 @@ __device__ void cfwd_small_cta(const CView<T>& cf, int J, T* ts, const T* g, int
         cfwd_small_tiled<T, NT, GROUPS>(cf, J, ts, g, ldg, xf, nrhs, D, Pn);
         return;
     }
+    if (tiled) {
+        // Blocks of 8 or more on a block left in HBM: t_J of up to tile_rp<T>() columns
+        // gathered at once (column-major, kSmallN apart: ts holds kSmallN x tile_rp), then
+        // the warp-per-four-rows products of the path below for each group of 8 columns,
+        // whose 32 warp sums per quad of rows are formed by one reduce-scatter (warp_sum's
+        // tree, bit for bit); the block is re-read from cache for each group.
+        constexpr int RPM = tile_rp<T>();
+        for (int j0 = 0; j0 < nrhs; j0 += RPM) {
+            const int nbp = min(RPM, nrhs - j0);
+            for (int it = gt; it < nJ * ((nbp + 7) / 8); it += NT) {
+                const int i = it % nJ, h = it / nJ;
+                T tv[8];
+                t_entry8(cf, a0 + i, g, ldg, j0 + 8 * h, nbp - 8 * h, tv);
+#pragma unroll
+                for (int b = 0; b < 8; ++b) ts[(8 * h + b) * kSmallN + i] = tv[b];
+            }
+            group_sync<NT, GROUPS>();
+            for (int h = 0; h < (nbp + 7) / 8; ++h) {
+                const T* th = ts + (size_t)(8 * h) * kSmallN;
+                const int nb = min(8, nbp - 8 * h);
+                for (int64_t r0 = 4 * warp; r0 < rtot; r0 += 4 * nw) {
+                    T acc[32];
+#pragma unroll
+                    for (int q = 0; q < 32; ++q) acc[q] = T(0);
+                    for (int c = lane; c < nJ; c += 32) {
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const int64_t r = r0 + u;
+                            T a = T(0);
+                            if (r < nJ) {
+                                if (c <= r) a = D[packed_col(c, nJ) + (r - c)];
+                            } else if (r < rtot) {
+                                a = Pn[(r - nJ) * nJ + c];
+                            }
+#pragma unroll
+                            for (int b = 0; b < 8; ++b) acc[8 * u + b] += a * th[b * kSmallN + c];
+                        }
+                    }
+                    const T v = reduce_scatter<T, 32>(acc, lane);
+                    const int64_t r = r0 + lane / 8;             // sum lane = 8 u + b
+                    const int b = lane % 8;
+                    if (r < rtot && b < nb) {
+                        if (r < nJ) xf[a0 + r + (int64_t)(j0 + 8 * h + b) * cf.s] = v;
+                        else cf.wbuf[cf.r_off[J] + (r - nJ) + (int64_t)(j0 + 8 * h + b) * cf.nrow] = v;
+                    }
+                }
+            }
+            group_sync<NT, GROUPS>();
+        }
+        return;
+    }
     for (int j0 = 0; j0 < nrhs; j0 += RB) {
         const int nb = min(RB, nrhs - j0);
         for (int b = 0; b < nb; ++b) gather_t(cf, J, gt, NT, ts + b * kSmallN, g, ldg, j0 + b);

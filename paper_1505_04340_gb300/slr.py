@@ -60,7 +60,7 @@ class Info(C.Structure):
         ("c_persistent", C.c_int32), ("tuned", C.c_int32), ("tune_seconds", C.c_double),
         ("band_threads", C.c_int32), ("c_top_levels", C.c_int32), ("c_top_positions", C.c_int32),
         ("c_top_entries", C.c_int64), ("band_on_device", C.c_int32), ("lanczos_seconds", C.c_double * 3),
-        ("band_mma", C.c_int32), ("u_dtype", C.c_int32)]
+        ("band_mma", C.c_int32), ("u_dtype", C.c_int32), ("vector_bytes_per_column", C.c_int64)]
 
 
 class SLRError(RuntimeError):

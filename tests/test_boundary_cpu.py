@@ -139,6 +139,29 @@ def test_opts_layout_matches_header(lib):
     assert names == [f for f, _ in slr.Opts._fields_]
 
 
+@pytest.mark.parametrize("struct", ["slr_opts", "slr_info"])
+def test_struct_offsets_match_header(struct, tmp_path):
+    """Every field of the binding's slr_opts / slr_info sits at the offset the C compiler
+    gives it in include/slr.h, and the sizes agree (a program built with gcc prints them)."""
+    import ctypes
+    import shutil
+    import subprocess
+    from paper_1505_04340_gb300 import slr
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    cls = slr.Opts if struct == "slr_opts" else slr.Info
+    names = [f for f, _ in cls._fields_]
+    src = tmp_path / "offsets.c"
+    src.write_text("#include <stddef.h>\n#include <stdio.h>\n#include \"slr.h\"\nint main(void) {\n" +
+                   "".join(f'  printf("%zu\\n", offsetof({struct}, {n}));\n' for n in names) +
+                   f'  printf("%zu\\n", sizeof({struct}));\n  return 0;\n}}\n')
+    exe = tmp_path / "offsets"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()]
+    want = [getattr(cls, n).offset for n in names] + [ctypes.sizeof(cls)]
+    assert got == want, dict(zip(names + ["sizeof"], zip(got, want)))
+
+
 def test_setup_detects_non_spd_block(lib):
     rp, ci, v = slrgen.laplacian((6, 5))
     v = v.copy()
