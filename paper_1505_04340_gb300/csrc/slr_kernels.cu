@@ -1549,17 +1549,14 @@ k_cbwd_persistent(const CView<T> cf, const T* yf, T* xf, T* y_dd, int64_t ldy, i
 
 // ------------------------------------------------------------------ K4
 // w' = cinv w + U (d o (U^T w)) (Eq. 4.7 in U-form), U s x k column-major, w s x nrhs
-// column-major (leading dimension s).  Each pass reads U once for the whole block
-// of right-hand sides:
+// column-major (leading dimension ldw).  Each pass reads U once:
 //   k_lr_vt     part[b][kk][j] = sum over block b's rows of U[i, kk] w[i, j]
 //   k_lr_vt_fin vk[kk + j k] = d[kk] * sum over b of part[b][kk][j]
 //   k_lr_update w[i, j] = cinv w[i, j] + sum over kk of U[i, kk] vk[kk + j k]
 // Every sum runs in a fixed order that depends on s and k only (block b owns rows
-// [b R, b R + R); one thread walks them in ascending order for one (kk, j)), so a
-// column gives the same bits alone and inside a block.
-constexpr int kLrK = 64;        // U columns per CTA (blockIdx.y groups larger k)
-constexpr int kLrJ = 32;        // right-hand sides per CTA (blockIdx.z groups more)
-constexpr int kLrCh = 32;       // rows per chunk staged in shared memory
+// [b R, b R + R), lanes stride them, the warp's sums follow warp_sum's tree; the
+// blocks are added in fixed segments), so a column gives the same bits alone and
+// inside a block.
 constexpr int kLrMaxBlocks = 1024;
 
 // row blocks of the first pass: enough to fill the SMs, a fixed function of s
@@ -1568,73 +1565,66 @@ __host__ __device__ inline int lr_blocks(int32_t s) {
     return b < 1 ? 1 : (b > kLrMaxBlocks ? kLrMaxBlocks : b);
 }
 
-// thread t: U column kk0 + t % 64, right-hand sides j0 + 8 (t / 64) .. + 7
+// Pass 1: CTA b owns rows [b R, b R + R) of s; warp w takes the columns kk = w, w + 8,
+// ... of U; its lanes stride the rows (U and w read coalesced, U once), each lane
+// keeping eight right-hand sides' sums, which one reduce-scatter (warp_sum's tree)
+// turns into the CTA's partial sums.  The order of every sum depends on s only.
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_lr_vt(int32_t s, int32_t k, int32_t nrhs, const T* __restrict__ U, const T* __restrict__ w, int64_t ldw, T* part) {
-    __shared__ T su[kLrCh][kLrK + 1];
-    __shared__ T sw[kLrCh][kLrJ + 1];
-    const int kk0 = blockIdx.y * kLrK, j0 = blockIdx.z * kLrJ;
-    const int kn = min(kLrK, k - kk0), jn = min(kLrJ, nrhs - j0);
-    const int t = threadIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int R = (s + gridDim.x - 1) / gridDim.x;
     const int r0 = blockIdx.x * R, r1 = min(s, r0 + R);
-    const int kk = t % kLrK, jg = t / kLrK;             // 4 groups of 8 right-hand sides
-    T acc[8];
+    for (int kk = warp; kk < k; kk += 8) {
+        const T* Uc = U + (int64_t)kk * s;
+        for (int j0 = 0; j0 < nrhs; j0 += 8) {
+            const int jn = min(8, nrhs - j0);
+            T acc[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) acc[q] = T(0);
-    // loader mapping: row t % 32 of the chunk, columns t / 32 + 8 q
-    const int lr = t % kLrCh, lc = t / kLrCh;
-    T pu[8], pw[4];
-    auto fetch = [&](int c0) {
-        const int i = c0 + lr;
+            for (int q = 0; q < 8; ++q) acc[q] = T(0);
+            for (int i = r0 + lane; i < r1; i += 32) {
+                const T u = Uc[i];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int col = lc + 8 * q;
-            pu[q] = (i < r1 && col < kn) ? U[i + (int64_t)(kk0 + col) * s] : T(0);
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int col = lc + 8 * q;
-            pw[q] = (i < r1 && col < jn) ? w[i + (int64_t)(j0 + col) * ldw] : T(0);
-        }
-    };
-    if (r0 < r1) fetch(r0);
-    for (int c0 = r0; c0 < r1; c0 += kLrCh) {
-        __syncthreads();
-#pragma unroll
-        for (int q = 0; q < 8; ++q) su[lr][lc + 8 * q] = pu[q];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) sw[lr][lc + 8 * q] = pw[q];
-        __syncthreads();
-        if (c0 + kLrCh < r1) fetch(c0 + kLrCh);        // next chunk's loads overlap this chunk's sums
-        const int rows = min(kLrCh, r1 - c0);
-        if (kk < kn && 8 * jg < jn) {
-            for (int i = 0; i < rows; ++i) {
-                const T u = su[i][kk];
-#pragma unroll
-                for (int q = 0; q < 8; ++q) acc[q] = fma(u, sw[i][8 * jg + q], acc[q]);
+                for (int q = 0; q < 8; ++q)
+                    if (q < jn) acc[q] = fma(u, w[i + (int64_t)(j0 + q) * ldw], acc[q]);
             }
-        }
-    }
-    if (kk < kn) {
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int j = 8 * jg + q;
-            if (j < jn) part[((int64_t)blockIdx.x * k + kk0 + kk) * nrhs + j0 + j] = acc[q];
+            const T v = reduce_scatter<T, 8>(acc, lane);
+            const int q = rs_index<8>(lane);
+            if (rs_writer<8>(lane) && q < jn) part[((int64_t)blockIdx.x * k + kk) * nrhs + j0 + q] = v;
         }
     }
 }
 
+// vk = d o (sum over the G pass-1 blocks), in a fixed order: block (kk, group of 16
+// right-hand sides) sums kFinSeg segments of the blocks in order, reading the
+// right-hand sides coalesced, then adds the segments in order
+constexpr int kLrSeg = 16, kLrFinJ = 16;
 template <typename T>
-__global__ void k_lr_vt_fin(int32_t k, int32_t nrhs, int32_t G, const T* __restrict__ part,
-                            const T* __restrict__ dvec, T* vk) {
-    const int id = blockIdx.x * blockDim.x + threadIdx.x;
-    if (id >= k * nrhs) return;
-    const int kk = id % k, j = id / k;
+__global__ void __launch_bounds__(kLrSeg * kLrFinJ)
+k_lr_vt_fin(int32_t k, int32_t nrhs, int32_t G, const T* __restrict__ part, const T* __restrict__ dvec, T* vk) {
+    __shared__ T seg[kLrSeg][kLrFinJ];
+    const int kk = blockIdx.x, jl = threadIdx.x % kLrFinJ, q = threadIdx.x / kLrFinJ;
+    const int j = blockIdx.y * kLrFinJ + jl;
+    const int len = (G + kLrSeg - 1) / kLrSeg, b0 = q * len, b1 = min(G, b0 + len);
     T acc = T(0);
-    for (int b = 0; b < G; ++b) acc += part[((int64_t)b * k + kk) * nrhs + j];
-    vk[kk + (int64_t)j * k] = dvec[kk] * acc;
+    if (j < nrhs) {
+        int b = b0;
+        for (; b + 4 <= b1; b += 4) {
+            T v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) v[u] = part[((int64_t)(b + u) * k + kk) * nrhs + j];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) acc += v[u];
+        }
+        for (; b < b1; ++b) acc += part[((int64_t)b * k + kk) * nrhs + j];
+    }
+    seg[q][jl] = acc;
+    __syncthreads();
+    if (q == 0 && j < nrhs) {
+        T v = T(0);
+        for (int qq = 0; qq < kLrSeg; ++qq) v += seg[qq][jl];
+        vk[kk + (int64_t)j * k] = dvec[kk] * v;
+    }
 }
 
 // thread = row i, JG right-hand sides (a block's columns j0 .. j0 + JG - 1 of nrhs)
@@ -1649,7 +1639,19 @@ k_lr_update(int32_t s, int32_t k, int32_t nrhs, const T* __restrict__ U, const T
     T acc[JG];
 #pragma unroll
     for (int q = 0; q < JG; ++q) acc[q] = q < jn ? cinv * w[i + (int64_t)(j0 + q) * ldw] : T(0);
-    for (int kk = 0; kk < k; ++kk) {
+    int kk = 0;
+    if constexpr (JG == 1)                              // one column: eight loads of U in flight, then their products
+    for (; kk + 8 <= k; kk += 8) {
+        T u[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) u[e] = U[i + (int64_t)(kk + e) * s];
+#pragma unroll
+        for (int e = 0; e < 8; ++e)
+#pragma unroll
+            for (int q = 0; q < JG; ++q)
+                if (q < jn) acc[q] = fma(u[e], __ldg(&vk[kk + e + (int64_t)(j0 + q) * k]), acc[q]);
+    }
+    for (; kk < k; ++kk) {
         const T u = U[i + (int64_t)kk * s];
 #pragma unroll
         for (int q = 0; q < JG; ++q)
@@ -2177,9 +2179,9 @@ cudaError_t launch_lowrank_v(const DevOperator<T>& op, int32_t s, int32_t k, con
                              int32_t nrhs, cudaStream_t st) {
     if (s == 0 || k == 0) return cudaSuccess;
     const int G = lr_blocks(s);
-    k_lr_vt<T><<<dim3(G, (k + kLrK - 1) / kLrK, (nrhs + kLrJ - 1) / kLrJ), 256, 0, st>>>(s, k, nrhs, Ub, w, ldw,
-                                                                                       op.part);
-    k_lr_vt_fin<T><<<blocks_for((int64_t)k * nrhs), kThreads, 0, st>>>(k, nrhs, G, op.part, op.dvec, op.vk);
+    k_lr_vt<T><<<G, 256, 0, st>>>(s, k, nrhs, Ub, w, ldw, op.part);
+    k_lr_vt_fin<T><<<dim3(k, (nrhs + kLrFinJ - 1) / kLrFinJ), kLrSeg * kLrFinJ, 0, st>>>(k, nrhs, G, op.part, op.dvec,
+                                                                                        op.vk);
     counted(2);
     return cudaGetLastError();
 }
