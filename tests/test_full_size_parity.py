@@ -69,10 +69,12 @@ def tol32(info):
 
 def its_tolerance(its):
     """Iterations the FP64 GPU CG may differ from the oracle's: one within Section 6's
-    300; beyond it, 0.5%.  The two sum in different orders, and once CG has lost
+    300; beyond it, 1.5%.  The two sum in different orders, and once CG has lost
     orthogonality (about a thousand iterations on the FV problem, coefficients
-    spanning 1e6) those roundings move the stopping step by a few iterations."""
-    return max(1, int(0.005 * its))
+    spanning 1e6) those roundings move the stopping step by about 1%: the oracle
+    stops at 997, two GPU builds differing only in the summation order of the
+    low-rank correction's U^T w at 999 and 1007."""
+    return max(1, int(0.015 * its))
 
 
 def cu(x):
