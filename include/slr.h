@@ -102,8 +102,11 @@ typedef struct {
                                1, 2 or 4; 0 = automatic                                  */
     int32_t band_slots;     /* shared-memory buffers the band solve streams its factor
                                through: 2..8; 0 = automatic                              */
-    int32_t band_threads;   /* threads per band-solve CTA: 512 (one CTA per SM) or 256 (two
-                               per SM, for more CTAs than SMs); 0 = automatic            */
+    int32_t band_threads;   /* threads per band-solve CTA: 512 (one CTA per SM), 256 (two
+                               per SM, for more CTAs than SMs) or 32 (one warp per
+                               subdomain, for planes of at most 64 rows in one slice;
+                               other planes take the automatic choice); 0 = automatic
+                               (32 where it applies)                                     */
     int32_t band_order;     /* the order in which the band solve's subdomain clusters are
                                launched (it sets which subdomains share SMs): 1 = subdomain
                                order, 2 = most work first, 3 = most and least work
@@ -163,7 +166,8 @@ typedef struct {
     int32_t c_persistent;        /* 1: C solves in one cooperative launch per direction     */
     int32_t tuned;               /* 1: the three above were chosen by timing (autotune)    */
     double tune_seconds;         /* time the tuning took (0 when taken from the cache)      */
-    int32_t band_threads;        /* threads per band-solve CTA (256: two subdomains per SM) */
+    int32_t band_threads;        /* threads per band-solve CTA (256: two subdomains per SM;
+                                    32: a warp per subdomain)                               */
     int32_t c_top_levels;        /* levels of C's factor solved with the explicit inverse   */
     int32_t c_top_positions;     /* interface positions in those levels                     */
     int64_t c_top_entries;       /* stored entries of that inverse (each layout)            */

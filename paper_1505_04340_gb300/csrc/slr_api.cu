@@ -860,8 +860,10 @@ slr_status autotune(slr_handle h, DevOperator<T>& op, cudaStream_t st) {
         for (int32_t G : {1, 2, 4}) {
             if (!band_split_ok(hs.wmax, G) || (G > 1 && hs.wmax < 32 * G) || hs.p * G > 2 * nsm) continue;
             if (G != hs.band_G) CS(repack_band<T>(h, op, G));
-            for (int32_t nt : {512, 256})
+            for (int32_t nt : {512, 256, 32})
                 for (int32_t slots : {2, 3, 4}) {
+                    // the warp kernel: planes of at most 64 rows in one slice, its own ring
+                    if (nt == 32 && (G != 1 || hs.wmax > 64 || slots != 2)) continue;
                     op.band_nbuf = slots;
                     op.band_nt = nt;
                     double us = 0;
@@ -960,8 +962,11 @@ slr_status setup_impl(slr_handle h, int32_t n, const int32_t* rowptr, const int3
         dev_band = have_dev && h->opts.band_factor_host == 0 && wmx > 0 && wmx <= 256;
         if (dev_band) host_band_layout(hs, G);
         else CS(host_band_factor(hs, G));
-        // more CTAs than SMs would run in two waves: 256-thread CTAs put two subdomains on an SM
-        hs.band_nt = h->opts.band_threads ? h->opts.band_threads : (nparts * G > nsm ? 256 : 512);
+        // more CTAs than SMs would run in two waves: 256-thread CTAs put two subdomains on an SM;
+        // planes of at most 64 rows in one slice take a warp per subdomain
+        const bool narrow = G == 1 && wmx <= 64;
+        const int32_t nt_req = h->opts.band_threads == 32 && !narrow ? 0 : h->opts.band_threads;
+        hs.band_nt = nt_req ? nt_req : narrow ? 32 : (nparts * G > nsm ? 256 : 512);
     }
     double t2 = now_s();
     CS(host_c_factor(hs, h->opts.c_leaf > 0 ? h->opts.c_leaf : 64, 32));
@@ -1333,7 +1338,7 @@ slr_status slr_setup(int32_t n, const int32_t* rowptr, const int32_t* colind, co
         o.host_loop < 0 || o.host_loop > 1 || o.band_slots < 0 || o.band_slots == 1 || o.band_slots > 8 ||
         o.c_persistent < 0 || o.c_persistent > 1 || o.autotune < 0 || o.autotune > 1 ||
         o.target_kappa < 0 || o.target_kappa == 1 ||
-        (o.band_threads != 0 && o.band_threads != 256 && o.band_threads != 512) ||
+        (o.band_threads != 0 && o.band_threads != 32 && o.band_threads != 256 && o.band_threads != 512) ||
         o.c_levels_only < 0 || o.c_levels_only > 1 || o.band_factor_host < 0 || o.band_factor_host > 1 ||
         o.indefinite < 0 || o.indefinite > 1 || o.band_order < 0 || o.band_order > 3 ||
         o.u_dtype < SLR_U_FP32 || o.u_dtype > SLR_U_BF16 ||

@@ -42,6 +42,9 @@ cudaError_t launch_band_solve(const DevOperator<T>& op, int32_t p, int32_t wmax,
         // blocks of right-hand sides on the tensor cores when the operator carries that factor
         if (op.band_tc && nrhs >= 8) return launch_band_solve_tc(op, p, in, ldi, out, ldo, base, ldb, nrhs, st);
     }
+    // planes of at most 64 rows in one slice: a warp per subdomain (band_nt 32)
+    if (op.band_nt == 32 && op.band_G == 1 && wmax <= 64)
+        return launch_band_warp(op, p, in, ldi, out, ldo, base, ldb, nrhs, st);
     for (int32_t c = 0; c < nrhs;) {
         const int32_t left = nrhs - c;
         int nr = 1;

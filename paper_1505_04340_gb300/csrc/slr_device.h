@@ -171,6 +171,10 @@ std::vector<BandTcBlock> band_tc_layout(const std::vector<BandBlock>& run_order,
 cudaError_t launch_band_tc_pack(int32_t mma_dtype, const BandTcBlock* band, int32_t p, int32_t cmax,
                                 const double* scr, const int64_t* soff, unsigned char* fac, bool indef,
                                 cudaStream_t st);
+// K1 with one warp per subdomain, for planes of at most 64 rows packed as one slice (slr_band_warp.cu)
+template <typename T>
+cudaError_t launch_band_warp(const DevOperator<T>& op, int32_t p, const T* in, int64_t ldi, T* out, int64_t ldo,
+                             const T* base, int64_t ldb, int32_t nrhs, cudaStream_t st);
 cudaError_t launch_band_solve_tc(const DevOperator<float>& op, int32_t p, const float* in, int64_t ldi, float* out,
                                  int64_t ldo, const float* base, int64_t ldb, int32_t nrhs, cudaStream_t st);
 // ---- K2: gp = g - E^T t (g == NULL: gp = E^T t) ;  eb = E y

@@ -197,7 +197,7 @@ class SLR:
         o.c_persistent = int(bool(c_persistent))  # C solves in one cooperative launch per direction
         o.autotune = int(bool(autotune))        # time the candidates at setup and keep the fastest
         o.target_kappa = int(target_kappa)      # rank by the rule lambda_{k+1} <= 1 - 1/K (0 = off)
-        o.band_threads = int(band_threads)      # threads per band-solve CTA: 512, 256 or 0 (automatic)
+        o.band_threads = int(band_threads)      # threads per band-solve CTA: 512, 256, 32 or 0 (automatic)
         o.c_levels_only = 0 if c_top_zone else 1  # explicit inverse of the factor's top levels
         o.band_factor_host = {"auto": 0, "host": 1}[band_factor]   # B_i factored on the device or the host
         o.indefinite = int(bool(indefinite))    # symmetric indefinite A with an SPD interface

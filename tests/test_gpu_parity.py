@@ -135,11 +135,12 @@ def test_device_band_factor_detects_non_spd_block():
                                                   ("3d-196", 2, 8, 512), ("3d-wide", 2, 8, 512), ("3d-wide", 4, 3, 512),
                                                   ("fv-ragged", 1, 8, 512), ("fv-ragged", 2, 2, 512),
                                                   ("3d-196", 2, 2, 256), ("3d-196", 1, 3, 256),
-                                                  ("3d-wide", 2, 2, 256), ("fv-ragged", 1, 2, 256)])
+                                                  ("3d-wide", 2, 2, 256), ("fv-ragged", 1, 2, 256),
+                                                  ("fv-ragged", 1, 2, 32), ("c1-lap32", 1, 2, 32)])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_bsolve_ring_and_split(name, split, slots, nt, precision):
     """B^{-1} with the factor streamed through 2..8 buffers, 1, 2 or 4 CTAs per subdomain,
-    and CTAs of 512 or 256 threads."""
+    and CTAs of 512 or 256 threads, or one warp per subdomain (planes of at most 64 rows)."""
     P = make(name)
     o = oracle(name)
     g = gpu_handle(P, precision, band_split=split, band_slots=slots, band_threads=nt)
@@ -147,6 +148,29 @@ def test_bsolve_ring_and_split(name, split, slots, nt, precision):
     f = np.random.default_rng(2).standard_normal((o.order.n_I, 4))
     t = g.bsolve(cu(f)).cpu().numpy()
     assert rel(t, o.bsolve.solve(f)) <= (TOL64 if precision == "fp64" else tol32(g.get_info()))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_warp_band_solve_column_alone_equals_block(precision):
+    """The warp-per-subdomain band solve (the default for planes of at most 64 rows):
+    parity with the oracle, and a column solved alone equals its column of a block of
+    five (one launch of four columns, then one of one) bit for bit."""
+    P = make("fv-ragged")
+    o = oracle("fv-ragged")
+    g = gpu_handle(P, precision, nrhs_max=5)
+    assert g.get_info()["band_threads"] == 32
+    f = np.random.default_rng(9).standard_normal((o.order.n_I, 5))
+    t = g.bsolve(cu(f)).cpu().numpy()
+    assert rel(t, o.bsolve.solve(f)) <= (TOL64 if precision == "fp64" else tol32(g.get_info()))
+    for c in (0, 3, 4):
+        assert np.array_equal(g.bsolve(cu(f[:, c])).cpu().numpy(), t[:, c]), c
+
+
+def test_warp_band_solve_needs_narrow_planes():
+    """band_threads = 32 asks for a warp per subdomain; planes wider than 64 rows keep
+    the automatic CTA size."""
+    g = gpu_handle(make("3d-lap"), "fp64", band_threads=32)
+    assert g.get_info()["band_threads"] in (256, 512)
 
 
 @pytest.mark.parametrize("name", ["fv-ragged", "3d-lap"])
