@@ -169,7 +169,7 @@ def test_warp_band_solve_column_alone_equals_block(precision):
 def test_warp_band_solve_needs_narrow_planes():
     """band_threads = 32 asks for a warp per subdomain; planes wider than 64 rows keep
     the automatic CTA size."""
-    g = gpu_handle(make("3d-lap"), "fp64", band_threads=32)
+    g = gpu_handle(make("3d-wide"), "fp64", band_threads=32)             # planes of 289 rows
     assert g.get_info()["band_threads"] in (256, 512)
 
 
