@@ -131,6 +131,7 @@ template <typename T>
 struct CView {
     int32_t s, nlev, nsteps;
     int64_t nrow;
+    int64_t wr;        // row stride of wbuf and tws: the call's right-hand sides are contiguous per row
     const int32_t *cperm, *c0, *rows, *seg_row, *lev_sn;
     const int64_t *r_off, *pan_off, *dinv_off, *seg_ptr;
     const T *panel, *dinv;
@@ -156,10 +157,11 @@ struct CView {
     long long spin;    // polls of a grid-barrier wait before it gives up
 };
 
-// sum of w[seg_row[e]] for e = e0 .. e1-1, in that order: indices and values are
+// sum of w[seg_row[e] wr] for e = e0 .. e1-1, in that order: indices and values are
 // loaded 8 at a time so that the two dependent loads are not paid per term
 template <typename T>
-__device__ __forceinline__ T gather_sum(const T* w, const int32_t* __restrict__ seg_row, int64_t e0, int64_t e1) {
+__device__ __forceinline__ T gather_sum(const T* w, int64_t wr, const int32_t* __restrict__ seg_row, int64_t e0,
+                                       int64_t e1) {
     T acc = T(0);
     for (int64_t e = e0; e < e1; e += 8) {
         int32_t idx[8];
@@ -167,7 +169,7 @@ __device__ __forceinline__ T gather_sum(const T* w, const int32_t* __restrict__ 
 #pragma unroll
         for (int u = 0; u < 8; ++u) idx[u] = e + u < e1 ? seg_row[e + u] : -1;
 #pragma unroll
-        for (int u = 0; u < 8; ++u) v[u] = idx[u] >= 0 ? w[idx[u]] : T(0);
+        for (int u = 0; u < 8; ++u) v[u] = idx[u] >= 0 ? w[(int64_t)idx[u] * wr] : T(0);
 #pragma unroll
         for (int u = 0; u < 8; ++u)
             if (e + u < e1) acc += v[u];
@@ -178,8 +180,8 @@ __device__ __forceinline__ T gather_sum(const T* w, const int32_t* __restrict__ 
 // entry pos of t = g - gathered panel products, right-hand side j
 template <typename T>
 __device__ __forceinline__ T t_entry(const CView<T>& cf, int32_t pos, const T* g, int64_t ldg, int j) {
-    const T* w = cf.wbuf + (int64_t)j * cf.nrow;
-    return g[cf.cperm[pos] + (int64_t)j * ldg] - gather_sum(w, cf.seg_row, cf.seg_ptr[pos], cf.seg_ptr[pos + 1]);
+    return g[cf.cperm[pos] + (int64_t)j * ldg] -
+           gather_sum(cf.wbuf + j, cf.wr, cf.seg_row, cf.seg_ptr[pos], cf.seg_ptr[pos + 1]);
 }
 
 // t at position pos for right-hand sides j .. j + nb - 1 (nb <= 8) into out[0 .. 8)
@@ -202,7 +204,7 @@ __device__ __forceinline__ void t_entry8(const CView<T>& cf, int32_t pos, const 
         for (int u = 0; u < 4; ++u)
 #pragma unroll
             for (int b = 0; b < 8; ++b)
-                v[u][b] = (idx[u] >= 0 && b < nb) ? cf.wbuf[idx[u] + (int64_t)(j + b) * cf.nrow] : T(0);
+                v[u][b] = (idx[u] >= 0 && b < nb) ? cf.wbuf[(int64_t)idx[u] * cf.wr + j + b] : T(0);
 #pragma unroll
         for (int u = 0; u < 4; ++u)
             if (idx[u] >= 0) {
@@ -257,8 +259,7 @@ __device__ void cfwd_task_rb(const CView<T>& cf, const int4 tk, bool pan, T* ts,
 #pragma unroll
     for (int b = 0; b < RB; ++b) {
         if (cf.tws) {                   // gathered once for the level (the same values)
-            const T* src = cf.tws + a0 + (int64_t)(j0 + b) * cf.s;
-            for (int i = threadIdx.x; i < nJ; i += NW * 32) ts[b * tstride + i] = src[i];
+            for (int i = threadIdx.x; i < nJ; i += NW * 32) ts[b * tstride + i] = cf.tws[(a0 + i) * cf.wr + j0 + b];
         } else {
             gather_t(cf, J, threadIdx.x, NW * 32, ts + b * tstride, g, ldg, j0 + b);
         }
@@ -288,7 +289,7 @@ __device__ void cfwd_task_rb(const CView<T>& cf, const int4 tk, bool pan, T* ts,
                 for (int b = 0; b < RB; ++b) acc[b] += pv * ts[b * tstride + c];
             }
             const T v = reduce_scatter<T, RB>(acc, lane);
-            if (rs_writer<RB>(lane)) cf.wbuf[cf.r_off[J] + p + (int64_t)(j0 + rs_index<RB>(lane)) * cf.nrow] = v;
+            if (rs_writer<RB>(lane)) cf.wbuf[(cf.r_off[J] + p) * cf.wr + j0 + rs_index<RB>(lane)] = v;
         }
     } else {
         const T* D = cf.dinv + cf.dinv_off[J];
@@ -390,8 +391,8 @@ __device__ void cfwd_task_blk(const CView<T>& cf, const int4 tk, bool pan, T* ts
     const int32_t J = tk.x, a0 = cf.c0[J], nJ = cf.c0[J + 1] - a0;
     const int ncl = pan ? nJ : tk.y + tk.z;        // columns the task reads
     for (int idx = threadIdx.x; idx < ncl * RP; idx += NW * 32) {
-        const int b = idx / ncl, i = idx - b * ncl;   // i fastest: coalesced reads of the gather
-        ts[i * RS + b] = b < nb ? cf.tws[a0 + i + (int64_t)(j0 + b) * cf.s] : T(0);
+        const int i = idx / RP, b = idx - i * RP;     // right-hand sides fastest: contiguous in the gather
+        ts[i * RS + b] = b < nb ? cf.tws[(int64_t)(a0 + i) * cf.wr + j0 + b] : T(0);
     }
     __syncthreads();
     if (pan) {
@@ -422,7 +423,7 @@ __device__ void cfwd_task_blk(const CView<T>& cf, const int4 tk, bool pan, T* ts
             for (; c < nJ; c += 32) madd(Pp[c], c);
             const T v = reduce_scatter<T, RP>(acc, lane);
             const int k = rs_index<RP>(lane);
-            if (rs_writer<RP>(lane) && k < nb) cf.wbuf[cf.r_off[J] + p + (int64_t)(j0 + k) * cf.nrow] = v;
+            if (rs_writer<RP>(lane) && k < nb) cf.wbuf[(cf.r_off[J] + p) * cf.wr + j0 + k] = v;
         }
     } else {
         const T* D = cf.dinv + cf.dinv_off[J];
@@ -798,7 +799,7 @@ __device__ void cfwd_small_tiled(const CView<T>& cf, int J, T* ts, const T* g, i
     const int32_t a0 = cf.c0[J], nJ = cf.c0[J + 1] - a0;
     const int32_t nr = (int32_t)(cf.r_off[J + 1] - cf.r_off[J]);
     const int32_t ND = (nJ + 31) & ~31, RV = ND + nr, ldp = small_ldp(nJ);
-    T* wb = cf.wbuf + cf.r_off[J];
+    T* wb = cf.wbuf + cf.r_off[J] * cf.wr;
     for (int j0 = 0; j0 < nrhs; j0 += RPM) {
         const int nb = min(RPM, nrhs - j0), RP = (nb + 7) & ~7, ngrp = RP / 8;
         for (int it = gt; it < nJ * ngrp; it += NT) {
@@ -852,7 +853,7 @@ __device__ void cfwd_small_tiled(const CView<T>& cf, int J, T* ts, const T* g, i
                     const int j = 8 * h + b;
                     if (j >= nb) continue;
                     if (kind[u] == 1 && r[u] < nJ) xf[a0 + r[u] + (int64_t)(j0 + j) * cf.s] = acc[u][b];
-                    else if (kind[u] == 2 && r[u] < RV) wb[(r[u] - ND) + (int64_t)(j0 + j) * cf.nrow] = acc[u][b];
+                    else if (kind[u] == 2 && r[u] < RV) wb[(int64_t)(r[u] - ND) * cf.wr + j0 + j] = acc[u][b];
                 }
         }
         group_sync<NT, GROUPS>();
@@ -915,7 +916,7 @@ __device__ void cfwd_small_cta(const CView<T>& cf, int J, T* ts, const T* g, int
                     const int b = lane % 8;
                     if (r < rtot && b < nb) {
                         if (r < nJ) xf[a0 + r + (int64_t)(j0 + 8 * h + b) * cf.s] = v;
-                        else cf.wbuf[cf.r_off[J] + (r - nJ) + (int64_t)(j0 + 8 * h + b) * cf.nrow] = v;
+                        else cf.wbuf[(cf.r_off[J] + (r - nJ)) * cf.wr + j0 + 8 * h + b] = v;
                     }
                 }
             }
@@ -953,7 +954,7 @@ __device__ void cfwd_small_cta(const CView<T>& cf, int J, T* ts, const T* g, int
 #pragma unroll
                         for (int b = 0; b < RB; ++b) acc[b] += a * ts[b * kSmallN + c];
                     }
-                    for (int b = 0; b < nb; ++b) cf.wbuf[cf.r_off[J] + (r - nJ) + (int64_t)(j0 + b) * cf.nrow] = acc[b];
+                    for (int b = 0; b < nb; ++b) cf.wbuf[(cf.r_off[J] + (r - nJ)) * cf.wr + j0 + b] = acc[b];
                 }
             }
         } else {
@@ -985,7 +986,7 @@ __device__ void cfwd_small_cta(const CView<T>& cf, int J, T* ts, const T* g, int
                         const int64_t r = r0 + u;
                         if (lane == 0 && r < rtot && b < nb) {
                             if (r < nJ) xf[a0 + r + (int64_t)(j0 + b) * cf.s] = v;
-                            else cf.wbuf[cf.r_off[J] + (r - nJ) + (int64_t)(j0 + b) * cf.nrow] = v;
+                            else cf.wbuf[(cf.r_off[J] + (r - nJ)) * cf.wr + j0 + b] = v;
                         }
                     }
             }
@@ -1227,11 +1228,11 @@ k_cfwd_gather(const CView<T> cf, int32_t s0, const T* g, int64_t ldg, int32_t nr
     const int32_t a0 = cf.c0[J], nJ = cf.c0[J + 1] - a0;
     const int64_t e = (int64_t)blockIdx.y * 256 + threadIdx.x;
     if (e >= (int64_t)nJ * nrhs) return;
-    const int32_t i = (int32_t)(e % nJ), j = (int32_t)(e / nJ);
+    const int32_t i = (int32_t)(e / nrhs), j = (int32_t)(e % nrhs);   // right-hand sides fastest
     const int32_t pos = a0 + i;
-    const T* w = cf.wbuf + (int64_t)j * cf.nrow;
-    cf.tws[pos + (int64_t)j * cf.s] =
-        g[cf.cperm[pos] + (int64_t)j * ldg] - gather_sum(w, cf.seg_row, cf.seg_ptr[pos], cf.seg_ptr[pos + 1]);
+    cf.tws[(int64_t)pos * cf.wr + j] =
+        g[cf.cperm[pos] + (int64_t)j * ldg] -
+        gather_sum(cf.wbuf + j, cf.wr, cf.seg_row, cf.seg_ptr[pos], cf.seg_ptr[pos + 1]);
 }
 
 // backward: one CTA per column task, 16 (FP32) or 8 (FP64) panel loads in flight per
@@ -1308,7 +1309,7 @@ k_ctop_gather(const CView<T> cf, const T* g, int64_t ldg, int32_t nrhs) {
     if (i >= (int64_t)cf.nT * nrhs) return;
     const int32_t la = (int32_t)(i % cf.nT), j = (int32_t)(i / cf.nT);
     cf.tT[i] = g[cf.cperm[cf.tpos[la]] + (int64_t)j * ldg] -
-               gather_sum(cf.wbuf + (int64_t)j * cf.nrow, cf.tseg_row, cf.tseg_ptr[la], cf.tseg_ptr[la + 1]);
+               gather_sum(cf.wbuf + j, cf.wr, cf.tseg_row, cf.tseg_ptr[la], cf.tseg_ptr[la + 1]);
 }
 
 // Adds the chunks' partial sums of a block once all its tasks have stored theirs:
@@ -1949,6 +1950,7 @@ CView<T> make_view(const DevCFactor<T>& cf, int32_t nsteps) {
     v.nlev = cf.top_lev;   // the level-scheduled part: levels below the top zone
     v.nsteps = nsteps;
     v.nrow = cf.nrow;
+    v.wr = 1;
     v.cperm = cf.cperm;
     v.c0 = cf.c0;
     v.rows = cf.rows;
@@ -2026,6 +2028,7 @@ cudaError_t launch_c_forward(const DevCFactor<T>& cf, const T* g_dd, int64_t ldg
                              cudaStream_t st) {
     if (nrhs > cf.ws_cols) return cudaErrorInvalidValue;
     CView<T> v = make_view(cf, cf.nsteps_fwd);
+    v.wr = nrhs;     // wbuf and tws: a call's right-hand sides contiguous per row (one line per gathered row)
     bool levels_done = cf.nsteps_fwd == 0;
     if (!levels_done && !cf.per_level) {
         // blocks of four right-hand sides share each matrix load when t_J of four fits
