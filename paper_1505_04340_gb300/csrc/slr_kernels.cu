@@ -132,6 +132,7 @@ struct CView {
     int32_t s, nlev, nsteps;
     int64_t nrow;
     int64_t wr;        // row stride of wbuf and tws: the call's right-hand sides are contiguous per row
+    int64_t xr;        // row stride of the backward's solution x (factor order; right-hand sides contiguous)
     const int32_t *cperm, *c0, *rows, *seg_row, *lev_sn;
     const int64_t *r_off, *pan_off, *dinv_off, *seg_ptr;
     const T *panel, *dinv;
@@ -486,7 +487,7 @@ __device__ void cbwd_task_rb(const CView<T>& cf, const int4 tk, T* us, T (*red)[
     const T* D = cf.dinv + cf.dinv_off[J];
     const int64_t chunk = (nr + NW - 1) / NW, pb = warp * chunk, pe = min(nr, pb + chunk);
     const T* y = yf + a0 + (int64_t)j0 * cf.s;
-    const T* x = xf + (int64_t)j0 * cf.s;
+    const T* x = xf + j0;                    // x(pos, b) at x[pos xr + b]
     for (int cc = warp; cc < tk.z; cc += NW) {
         const int c = tk.y + cc;
         const T* Dc = D + packed_col(c, nJ) - c;   // Dc[i] = (L_JJ^{-1})[i, c], i >= c
@@ -527,13 +528,13 @@ __device__ void cbwd_task_rb(const CView<T>& cf, const int4 tk, T* us, T (*red)[
 #pragma unroll
             for (int u = 0; u < DEPTH; ++u)
 #pragma unroll
-                for (int b = 0; b < RB; ++b) acc[b] += pv[u] * x[(int64_t)b * cf.s + rr[u]];
+                for (int b = 0; b < RB; ++b) acc[b] += pv[u] * x[(int64_t)rr[u] * cf.xr + b];
         }
         for (; p < pe; ++p) {
             const T pv = Pn[p * nJ];
             const int32_t r = R[p];
 #pragma unroll
-            for (int b = 0; b < RB; ++b) acc[b] += pv * x[(int64_t)b * cf.s + r];
+            for (int b = 0; b < RB; ++b) acc[b] += pv * x[(int64_t)r * cf.xr + b];
         }
     }
     if (red2) {
@@ -548,7 +549,7 @@ __device__ void cbwd_task_rb(const CView<T>& cf, const int4 tk, T* us, T (*red)[
 #pragma unroll 8
                 for (int w = 0; w < NW; ++w) v += red2[(w * RB + b) * 32 + lane];
                 const T r = us[b * 32 + lane] - v;
-                xf[a0 + jl + (int64_t)(j0 + b) * cf.s] = r;
+                xf[(int64_t)(a0 + jl) * cf.xr + j0 + b] = r;
                 if (y_dd) y_dd[cf.cperm[a0 + jl] + (int64_t)(j0 + b) * ldy] = r;
             }
         }
@@ -564,7 +565,7 @@ __device__ void cbwd_task_rb(const CView<T>& cf, const int4 tk, T* us, T (*red)[
 #pragma unroll 8
             for (int w = 0; w < NW; ++w) v += red[w][lane];
             const T r = us[b * 32 + lane] - v;
-            xf[a0 + jl + (int64_t)(j0 + b) * cf.s] = r;
+            xf[(int64_t)(a0 + jl) * cf.xr + j0 + b] = r;
             if (y_dd) y_dd[cf.cperm[a0 + jl] + (int64_t)(j0 + b) * ldy] = r;
         }
         __syncthreads();
@@ -592,7 +593,7 @@ __device__ void cbwd_task_blk(const CView<T>& cf, const int4 tk, T* us, T* xs, c
     const T* D = cf.dinv + cf.dinv_off[J];
     const int64_t chunk = (nr + NW - 1) / NW, pb = warp * chunk, pe = min(nr, pb + chunk);
     const T* y = yf + a0 + (int64_t)j0 * cf.s;
-    const T* x = xf + (int64_t)j0 * cf.s;
+    const T* x = xf + j0;                    // x(pos, b) at x[pos xr + b]
     // right-hand side b of the block (zero past nb)
     auto yv = [&](int b, int64_t i) { return b < nb ? y[(int64_t)b * cf.s + i] : T(0); };
     for (int cc = warp; cc < tk.z; cc += NW) {
@@ -631,7 +632,7 @@ __device__ void cbwd_task_blk(const CView<T>& cf, const int4 tk, T* us, T* xs, c
             for (int pp0 = 0; pp0 < nq; pp0 += 8) {
 #pragma unroll
                 for (int u = 0; u < 8; ++u)
-                    v[u] = (pp0 + u < nq && lane < nb) ? x[(int64_t)lane * cf.s + R[q0 + pp0 + u]] : T(0);
+                    v[u] = (pp0 + u < nq && lane < nb) ? x[(int64_t)R[q0 + pp0 + u] * cf.xr + lane] : T(0);
 #pragma unroll
                 for (int u = 0; u < 8; ++u)
                     if (pp0 + u < nq) xw[(pp0 + u) * RS + lane] = v[u];
@@ -662,7 +663,7 @@ __device__ void cbwd_task_blk(const CView<T>& cf, const int4 tk, T* us, T* xs, c
 #pragma unroll 8
             for (int w = 0; w < NW; ++w) v += xs[(w * RP + b) * 32 + lane];
             const T r = us[b * 32 + lane] - v;
-            xf[a0 + jl + (int64_t)(j0 + b) * cf.s] = r;
+            xf[(int64_t)(a0 + jl) * cf.xr + j0 + b] = r;
             if (y_dd) y_dd[cf.cperm[a0 + jl] + (int64_t)(j0 + b) * ldy] = r;
         }
     }
@@ -1036,7 +1037,7 @@ __device__ void cbwd_small_tiled(const CView<T>& cf, int J, T* vs, const T* yf, 
             for (int b = 0; b < 8; ++b) {
                 const int j = 8 * h + b;
                 v[b] = T(0);
-                if (j < nb) v[b] = r < nJ ? yf[src + (int64_t)(j0 + j) * cf.s] : -xf[src + (int64_t)(j0 + j) * cf.s];
+                if (j < nb) v[b] = r < nJ ? yf[src + (int64_t)(j0 + j) * cf.s] : -xf[src * cf.xr + j0 + j];
             }
 #pragma unroll
             for (int b = 0; b < 8; ++b) vs[r * RP + 8 * h + b] = v[b];
@@ -1090,7 +1091,7 @@ __device__ void cbwd_small_tiled(const CView<T>& cf, int J, T* vs, const T* yf, 
             const int c = idx / nb, j = idx - c * nb;
             T v = T(0);
             for (int qq = 0; qq < parts; ++qq) v += vs[((int64_t)qq * nJ + c) * RP + j];
-            xf[a0 + c + (int64_t)(j0 + j) * cf.s] = v;
+            xf[(int64_t)(a0 + c) * cf.xr + j0 + j] = v;
             if (y_dd) y_dd[cf.cperm[a0 + c] + (int64_t)(j0 + j) * ldy] = v;
         }
         group_sync<NT, GROUPS>();
@@ -1123,9 +1124,9 @@ __device__ void cbwd_small_cta(const CView<T>& cf, int J, T* vs, T* red, const T
     for (int j0 = 0; j0 < nrhs; j0 += RB) {
         const int nb = min(RB, nrhs - j0);
         for (int b = 0; b < nb; ++b) {
-            const T* x = xf + (int64_t)(j0 + b) * cf.s;
+            const T* x = xf + j0 + b;
             const T* y = yf + a0 + (int64_t)(j0 + b) * cf.s;
-            for (int64_t r = gt; r < rtot; r += NT) vs[b * VS + r] = r < nJ ? y[r] : -x[R[r - nJ]];
+            for (int64_t r = gt; r < rtot; r += NT) vs[b * VS + r] = r < nJ ? y[r] : -x[(int64_t)R[r - nJ] * cf.xr];
         }
         if (j0 == 0 && staged) stage_wait();
         group_sync<NT, GROUPS>();
@@ -1175,7 +1176,7 @@ __device__ void cbwd_small_cta(const CView<T>& cf, int J, T* vs, T* red, const T
             for (int b = 0; b < nb; ++b) {
                 T v = T(0);
                 for (int q = 0; q < parts; ++q) v += red[b * NT + q * P + cc];
-                xf[a0 + cc + (int64_t)(j0 + b) * cf.s] = v;
+                xf[(int64_t)(a0 + cc) * cf.xr + j0 + b] = v;
                 if (y_dd) y_dd[cf.cperm[a0 + cc] + (int64_t)(j0 + b) * ldy] = v;
             }
         group_sync<NT, GROUPS>();
@@ -1438,7 +1439,7 @@ k_ctop_bwd(const CView<T> cf, const T* yf, T* xf, T* y_dd, int64_t ldy, int32_t 
     }
     const int32_t a0 = cf.c0[J] + cb.y;
     last_task_sum(cf.tb_cnt + tk.x, cb.w, cf.tb_part + pofs, cf.tb_parts, cb.z, nrhs, [&](int c, int j, T v) {
-        xf[a0 + c + (int64_t)j * cf.s] = v;
+        xf[(int64_t)(a0 + c) * cf.xr + j] = v;
         if (y_dd) y_dd[cf.cperm[a0 + c] + (int64_t)j * ldy] = v;
     });
 }
@@ -1951,6 +1952,7 @@ CView<T> make_view(const DevCFactor<T>& cf, int32_t nsteps) {
     v.nsteps = nsteps;
     v.nrow = cf.nrow;
     v.wr = 1;
+    v.xr = 1;
     v.cperm = cf.cperm;
     v.c0 = cf.c0;
     v.rows = cf.rows;
@@ -2115,7 +2117,8 @@ template <typename T>
 cudaError_t launch_c_backward(const DevCFactor<T>& cf, const T* yf, T* xf, T* y_dd, int64_t ldy, int32_t nrhs,
                               cudaStream_t st) {
     if (cf.nT > 0 && nrhs > cf.ws_cols) return cudaErrorInvalidValue;
-    const CView<T> v = make_view(cf, cf.nsteps_bwd);
+    CView<T> v = make_view(cf, cf.nsteps_bwd);
+    v.xr = nrhs;     // the solution x (scratch): a call's right-hand sides contiguous per row
     if (cf.nT > 0) {
         k_ctop_bwd<T><<<cf.n_tb_tasks, kTopT, 0, st>>>(v, yf, xf, y_dd, ldy, nrhs);
         counted();
