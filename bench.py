@@ -109,7 +109,7 @@ class ClockSampler:
 
 # the source files of each kernel whose ncu traffic a committed summary records
 KERNEL_SOURCES = {
-    "band": ("slr_band_kernel.cuh", "slr_band.cu", "slr_band_half.cu"),
+    "band": ("slr_band_kernel.cuh", "slr_band_half.cu"),       # k_band_solve2 and its instantiations
     "band_tc": ("slr_band_tc.cu", "slr_tc.cuh"),
     "csolve": ("slr_kernels.cu",),
     "lowrank": ("slr_kernels.cu",),
