@@ -161,6 +161,11 @@ slr_status upload_operator(slr_handle h, DevOperator<T>& op, bool with_band) {
     d.nlev = c.nlev;
     d.lev_task_ptr = c.lev_task_ptr;
     CS(upload(h, &d.cperm, c.cperm));
+    {
+        std::vector<int32_t> ip(c.cperm.size());
+        for (size_t q = 0; q < c.cperm.size(); ++q) ip[c.cperm[q]] = (int32_t)q;
+        CS(upload(h, &d.ciperm, ip));
+    }
     CS(upload(h, &d.c0, c.c0));
     CS(upload(h, &d.r_off, c.r_off));
     CS(upload(h, &d.rows, c.rows));
@@ -241,6 +246,7 @@ slr_status upload_operator(slr_handle h, DevOperator<T>& op, bool with_band) {
                            h->stream));
     CS(dalloc(h, &d.wbuf, (size_t)std::max<int64_t>(d.nrow, 1) * r));
     CS(dalloc(h, &d.tws, (size_t)std::max<int64_t>(c.s, 1) * r));
+    CS(dalloc(h, &d.gfs, (size_t)std::max<int64_t>(c.s, 1) * r));
     d.lev_maxn.assign(c.nlev, 0);
     for (int32_t l = 0; l < c.nlev; ++l) {
         if (c.lev_small[l]) continue;

@@ -15,6 +15,7 @@ template <typename T>
 struct DevCFactor {
     int32_t s = 0, ns = 0, nlev = 0;
     int32_t* cperm = nullptr;      // factor position -> DD interface index
+    int32_t* ciperm = nullptr;     // DD interface index -> factor position
     int32_t* c0 = nullptr;         // [ns+1]
     int64_t* r_off = nullptr;      // [ns+1]
     int32_t* rows = nullptr;       // R_J
@@ -28,6 +29,7 @@ struct DevCFactor {
     int32_t max_n = 0;             // widest supernode (shared memory of a forward task: t_J)
     T* wbuf = nullptr;             // [nrow x nrhs_max] panel products M_J t_J of the forward solve
     T* tws = nullptr;              // [s x nrhs_max] t_J gathered once per level (per-level forward tasks)
+    T* gfs = nullptr;              // [s x nrhs_max] the forward's input g in factor order, a row per position
     std::vector<int32_t> lev_maxn; // widest supernode of each level (0 for the fused small levels)
     int4* tasks = nullptr;         // (supernode, first column, count <= 32, 0)
     int4* ptasks = nullptr;        // (supernode, first panel row, count <= 32, 0)

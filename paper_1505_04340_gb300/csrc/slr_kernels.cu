@@ -137,6 +137,8 @@ struct CView {
     const int64_t *r_off, *pan_off, *dinv_off, *seg_ptr;
     const T *panel, *dinv;
     T* wbuf;
+    const T* gf;       // the forward's input g in factor order, position pos's right-hand sides at pos wr,
+                       // or null: g is read through cperm
     T* tws;            // t_J of the level's supernodes gathered by k_cfwd_gather (s x nrhs), or null:
                        // each forward task gathers t_J itself
     const int4 *tasks, *ptasks;
@@ -178,10 +180,16 @@ __device__ __forceinline__ T gather_sum(const T* w, int64_t wr, const int32_t* _
     return acc;
 }
 
+// the forward's input at factor position pos, right-hand side j
+template <typename T>
+__device__ __forceinline__ T g_at(const CView<T>& cf, int32_t pos, const T* g, int64_t ldg, int j) {
+    return cf.gf ? cf.gf[(int64_t)pos * cf.wr + j] : g[cf.cperm[pos] + (int64_t)j * ldg];
+}
+
 // entry pos of t = g - gathered panel products, right-hand side j
 template <typename T>
 __device__ __forceinline__ T t_entry(const CView<T>& cf, int32_t pos, const T* g, int64_t ldg, int j) {
-    return g[cf.cperm[pos] + (int64_t)j * ldg] -
+    return g_at(cf, pos, g, ldg, j) -
            gather_sum(cf.wbuf + j, cf.wr, cf.seg_row, cf.seg_ptr[pos], cf.seg_ptr[pos + 1]);
 }
 
@@ -192,7 +200,6 @@ template <typename T>
 __device__ __forceinline__ void t_entry8(const CView<T>& cf, int32_t pos, const T* g, int64_t ldg, int j, int nb,
                                          T (&out)[8]) {
     const int64_t e0 = cf.seg_ptr[pos], e1 = cf.seg_ptr[pos + 1];
-    const int32_t gp = cf.cperm[pos];
     T acc[8];
 #pragma unroll
     for (int b = 0; b < 8; ++b) acc[b] = T(0);
@@ -214,7 +221,7 @@ __device__ __forceinline__ void t_entry8(const CView<T>& cf, int32_t pos, const 
             }
     }
 #pragma unroll
-    for (int b = 0; b < 8; ++b) out[b] = b < nb ? g[gp + (int64_t)(j + b) * ldg] - acc[b] : T(0);
+    for (int b = 0; b < 8; ++b) out[b] = b < nb ? g_at(cf, pos, g, ldg, j + b) - acc[b] : T(0);
 }
 
 // t_J = g_J - gathered panel products into ts[0 .. n_J) by NTH threads (thread gt)
@@ -1218,6 +1225,27 @@ k_cfwd_level_blk(const CView<T> cf, int32_t t0, int32_t p0, int32_t np, T* xf, i
     for (int j0 = 0; j0 < nrhs; j0 += RP) cfwd_task_blk<T, NW, RP>(cf, tk, pan, ts, red2, xf, j0, min(RP, nrhs - j0));
 }
 
+// gf[ciperm[i] wr + j] = g[i + j ldg]: the forward's input in factor order, a row per position.
+// A CTA takes 32 DD indices x 32 right-hand sides: it reads them along the indices (coalesced),
+// transposes them in shared memory and writes each factor-order row's right-hand sides together.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_cperm_g(int32_t s, int32_t nrhs, const int32_t* __restrict__ ciperm, const T* __restrict__ g, int64_t ldg, T* gf) {
+    __shared__ T tile[32][33];
+    const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 32, tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int j = j0 + ty + 8 * q, i = i0 + tx;
+        tile[ty + 8 * q][tx] = (i < s && j < nrhs) ? g[i + (int64_t)j * ldg] : T(0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int il = ty + 8 * q, i = i0 + il, j = j0 + tx;
+        if (i < s && j < nrhs) gf[(int64_t)ciperm[i] * nrhs + j] = tile[tx][il];
+    }
+}
+
 // t_J = g_J - (gathered panel products) for every supernode of a level, once, into
 // cf.tws: block (q, c) takes entries c * 256 .. c * 256 + 255 of the (position,
 // right-hand side) pairs of the level's q-th supernode.  The per-level forward tasks
@@ -1232,7 +1260,7 @@ k_cfwd_gather(const CView<T> cf, int32_t s0, const T* g, int64_t ldg, int32_t nr
     const int32_t i = (int32_t)(e / nrhs), j = (int32_t)(e % nrhs);   // right-hand sides fastest
     const int32_t pos = a0 + i;
     cf.tws[(int64_t)pos * cf.wr + j] =
-        g[cf.cperm[pos] + (int64_t)j * ldg] -
+        g_at(cf, pos, g, ldg, j) -
         gather_sum(cf.wbuf + j, cf.wr, cf.seg_row, cf.seg_ptr[pos], cf.seg_ptr[pos + 1]);
 }
 
@@ -1309,7 +1337,7 @@ k_ctop_gather(const CView<T> cf, const T* g, int64_t ldg, int32_t nrhs) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (int64_t)cf.nT * nrhs) return;
     const int32_t la = (int32_t)(i % cf.nT), j = (int32_t)(i / cf.nT);
-    cf.tT[i] = g[cf.cperm[cf.tpos[la]] + (int64_t)j * ldg] -
+    cf.tT[i] = g_at(cf, cf.tpos[la], g, ldg, j) -
                gather_sum(cf.wbuf + j, cf.wr, cf.tseg_row, cf.tseg_ptr[la], cf.tseg_ptr[la + 1]);
 }
 
@@ -1953,6 +1981,7 @@ CView<T> make_view(const DevCFactor<T>& cf, int32_t nsteps) {
     v.nrow = cf.nrow;
     v.wr = 1;
     v.xr = 1;
+    v.gf = nullptr;
     v.cperm = cf.cperm;
     v.c0 = cf.c0;
     v.rows = cf.rows;
@@ -2031,6 +2060,13 @@ cudaError_t launch_c_forward(const DevCFactor<T>& cf, const T* g_dd, int64_t ldg
     if (nrhs > cf.ws_cols) return cudaErrorInvalidValue;
     CView<T> v = make_view(cf, cf.nsteps_fwd);
     v.wr = nrhs;     // wbuf and tws: a call's right-hand sides contiguous per row (one line per gathered row)
+    if (nrhs >= 8 && cf.gfs && cf.s > 0) {
+        // blocks: g in factor order, a row per position, so every gather of g reads whole lines
+        k_cperm_g<T><<<dim3((cf.s + 31) / 32, (nrhs + 31) / 32), 256, 0, st>>>(cf.s, nrhs, cf.ciperm, g_dd, ldg,
+                                                                               cf.gfs);
+        counted();
+        v.gf = cf.gfs;
+    }
     bool levels_done = cf.nsteps_fwd == 0;
     if (!levels_done && !cf.per_level) {
         // blocks of four right-hand sides share each matrix load when t_J of four fits

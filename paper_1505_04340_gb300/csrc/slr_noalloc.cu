@@ -77,6 +77,7 @@ size_t carve(slr_handle h, DevOperator<T>& op, int32_t nrhs, unsigned char* base
     op.xf = c.take<T>(s * nrhs);
     op.cf.wbuf = c.take<T>(std::max<int64_t>(op.cf.nrow, 1) * nrhs);
     op.cf.tws = c.take<T>(s * nrhs);
+    op.cf.gfs = c.take<T>(s * nrhs);
     op.cf.ws_cols = nrhs;
     if (op.cf.nT > 0) {   // the top zone's workspaces; its counters are cleared before each apply
         op.cf.tT = c.take<T>((int64_t)op.cf.nT * nrhs);
