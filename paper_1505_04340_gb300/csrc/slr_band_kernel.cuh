@@ -28,7 +28,6 @@ constexpr int kMinSlot = 16 * 1024;   // bytes per ring slot at least
 inline size_t band_cap(int nt) { return nt == 512 ? 227 * 1024 : 112 * 1024; }
 constexpr int kRB = 8;             // row blocks of 32: at most 256 rows per slice
 constexpr long long kSpin = 1ll << 24;   // bounded mbarrier wait (about a second)
-constexpr int kBandPrefetch = 3;         // blocks of the factor prefetched into L2 ahead of the ring
 
 // ---- slice geometry (the host packer uses the same rules: band_* in slr_internal.h)
 // local row block with first plane row R0: columns it meets in an upper block
@@ -239,23 +238,8 @@ k_band_solve2(const BandBlock* __restrict__ blocks, const T* __restrict__ fac, c
     };
     // thread 0 issues chunks in stream order; its cursor is the next chunk to issue
     int cur_type = 1, cur_plane = 0, cur_ix = 0, issued = 0;
-    // the slice of the block kBandPrefetch blocks ahead of the one whose first chunk is
-    // issued is prefetched into L2 (a hint: no shared memory, no wait), so the ring's
-    // copies of it hit L2 instead of waiting on DRAM
-    auto prefetch_ahead = [&](int type, int plane) {
-        for (int d = 0; d < kBandPrefetch && plane >= 0; ++d) next_block(c, type, plane);
-        if (plane < 0) return;
-        const bool up = (type == 0 || type == 3);
-        const int nseg = up ? segU[kRB] : segL[kRB];
-        if (nseg == 0) return;
-        const int64_t e0 = q.base + (int64_t)plane * q.PS + block_off(q, type);
-        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(fac + e0),
-                     "r"((uint32_t)(nseg * 32 * (int)sizeof(T)))
-                     : "memory");
-    };
     auto issue_next = [&]() {
         if (cur_plane < 0) return;                 // past the end of the stream: nothing to copy
-        if (cur_ix == 0) prefetch_ahead(cur_type, cur_plane);
         int64_t e0, e1;
         chunk_src(cur_type, cur_plane, cur_ix, e0, e1);
         // whole segments of 32 values: start and size are multiples of 128 bytes

@@ -43,7 +43,6 @@ namespace {
 constexpr int kBtThreads = 256;
 constexpr int kSub = 4096;                 // bytes of one sub-tile (128 rows x 32 bytes)
 constexpr long long kBtSpin = 1ll << 24;   // polls of a bounded wait
-constexpr int kBtPrefetch = 2;             // blocks of the factor prefetched into L2 ahead of the ring
 
 template <int AB>
 struct BtType;
@@ -250,29 +249,12 @@ k_band_tc(const BandTcBlock* __restrict__ blocks, const unsigned char* __restric
 
     if (tid == 0) {
         // ---------------------------------------------------------------- producer
-        // a block's sub-tiles are one contiguous range of the factor
-        auto block_src = [&](int qq, int& nt_q) -> const unsigned char* {
-            const BtBlock bq = bt_block(qq, c);
-            nt_q = tiles_of(bq.type);
-            const int64_t bo = bq.type == 0 ? 0 : bq.type == 1 ? nU : bq.type == 2 ? nU + nL : nU + 2 * nL;
-            return fac + b.foff + ((int64_t)bq.plane * (2 * nU + 2 * nL) + bo) * kSub;
-        };
-        // the blocks kBtPrefetch ahead are prefetched into L2 (a hint: no shared memory, no
-        // wait), so that the ring's copies of them hit L2 instead of waiting on DRAM
-        auto prefetch = [&](int qq) {
-            if (qq >= nblk) return;
-            int ntp;
-            const unsigned char* sp = block_src(qq, ntp);
-            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(sp), "r"((uint32_t)(ntp * kSub))
-                         : "memory");
-        };
-        for (int qq = 1; qq <= kBtPrefetch; ++qq) prefetch(qq);
         int f = 0;
         for (int q = 0; q < nblk && !*abort_flag; ++q) {
             const BtBlock bk = bt_block(q, c);
-            int nt;
-            const unsigned char* src = block_src(q, nt);
-            prefetch(q + kBtPrefetch + 1);
+            const int nt = tiles_of(bk.type);
+            const int64_t boff = bk.type == 0 ? 0 : bk.type == 1 ? nU : bk.type == 2 ? nU + nL : nU + 2 * nL;
+            const unsigned char* src = fac + b.foff + ((int64_t)bk.plane * (2 * nU + 2 * nL) + boff) * kSub;
             for (int t0 = 0; t0 < nt; t0 += stiles, ++f) {
                 const int s = f % nslot;
                 if (f >= nslot && !tc::mbar_wait(&empty[s], (uint32_t)(((f / nslot) - 1) & 1), kBtSpin)) {

@@ -71,22 +71,8 @@ k_band_warp(const BandBlock* __restrict__ blocks, const T* __restrict__ fac, con
     // lane 0 issues the chunks in stream order (forward: D_0, then (O_J, D_J); backward:
     // D_{c-1}^T, then (O_{J+1}^T, D_J^T)); chunk k goes to slot k mod nbuf
     int cur_type = 1, cur_plane = 0, cur_ix = 0, issued = 0;
-    // the block kBandPrefetch blocks ahead of the one whose first chunk is issued is
-    // prefetched into L2 (a hint), so the ring's copies of it hit L2
-    auto prefetch_ahead = [&](int type, int plane) {
-        for (int d = 0; d < kBandPrefetch && plane >= 0; ++d) next_block(c, type, plane);
-        if (plane < 0) return;
-        const bool up = (type == 0 || type == 3);
-        const int nseg = up ? segU[2] : segL[2];
-        if (nseg == 0) return;
-        const int64_t e0 = q.base + (int64_t)plane * q.PS + block_off(q, type);
-        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(fac + e0),
-                     "r"((uint32_t)(nseg * 32 * (int)sizeof(T)))
-                     : "memory");
-    };
     auto issue_next = [&]() {
         if (cur_plane < 0) return;
-        if (cur_ix == 0) prefetch_ahead(cur_type, cur_plane);
         const bool up = (cur_type == 0 || cur_type == 3);
         const int nseg = up ? segU[2] : segL[2];
         const int64_t e0 = q.base + (int64_t)cur_plane * q.PS + block_off(q, cur_type) + (int64_t)cur_ix * per * 32;
