@@ -1605,6 +1605,27 @@ k_lr_vt(int32_t s, int32_t k, int32_t nrhs, const T* __restrict__ U, const T* __
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int R = (s + gridDim.x - 1) / gridDim.x;
     const int r0 = blockIdx.x * R, r1 = min(s, r0 + R);
+    if (nrhs == 1 && k <= 128) {
+        // one right-hand side: the warp's columns kk = warp + 8 q (q < 16) all at once, w read
+        // once per row and their loads of U in flight together; each sum has the operands and
+        // the tree of the block path below, so the bits are the same
+        T acc[16];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) acc[q] = T(0);
+        for (int i = r0 + lane; i < r1; i += 32) {
+            const T wv = w[i];
+            T u[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) u[q] = warp + 8 * q < k ? U[i + (int64_t)(warp + 8 * q) * s] : T(0);
+#pragma unroll
+            for (int q = 0; q < 16; ++q)
+                if (warp + 8 * q < k) acc[q] = fma(u[q], wv, acc[q]);
+        }
+        const T v = reduce_scatter<T, 16>(acc, lane);
+        const int kk = warp + 8 * rs_index<16>(lane);
+        if (rs_writer<16>(lane) && kk < k) part[(int64_t)blockIdx.x * k + kk] = v;
+        return;
+    }
     for (int kk = warp; kk < k; kk += 8) {
         const T* Uc = U + (int64_t)kk * s;
         for (int j0 = 0; j0 < nrhs; j0 += 8) {
