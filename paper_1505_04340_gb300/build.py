@@ -22,7 +22,7 @@ LIB = os.path.join(PKG, "lib", "libslr.so")
 
 CXX_SOURCES = ["slr_host.cpp"]
 CU_SOURCES = ["slr_kernels.cu", "slr_band.cu", "slr_band_half.cu", "slr_band_factor.cu", "slr_api.cu",
-              "slr_noalloc.cu", "slr_lowrank_tc.cu", "slr_band_tc.cu", "slr_band_warp.cu"]
+              "slr_noalloc.cu", "slr_lowrank_tc.cu", "slr_band_tc.cu", "slr_band_warp.cu", "slr_pcg.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -1009,13 +1009,17 @@ slr_status setup_impl(slr_handle h, int32_t n, const int32_t* rowptr, const int3
     const size_t nr = (size_t)std::max(1, n) * r;
     CS(dalloc(h, &h->px, nr));
     CS(dalloc(h, &h->pr, nr));
-    CS(dalloc(h, &h->pz, nr));
+    if (h->opts.precision == SLR_PREC_MIXED) {
+        CS(dalloc(h, &h->pr32, nr));
+        CS(dalloc(h, &h->pz32, nr));
+    } else {
+        CS(dalloc(h, &h->pz, nr));
+    }
     CS(dalloc(h, &h->pp, nr));
     CS(dalloc(h, &h->pq, nr));
-    if (h->opts.flexible_cg) CS(dalloc(h, &h->pzold, nr));
     CS(dalloc(h, &h->scal, (size_t)8 * r));
     CS(dalloc(h, &h->iflags, (size_t)4 * r + 4));
-    CS(dalloc(h, &h->dpart, (size_t)kRedBlocks * r));
+    CS(dalloc(h, &h->dpart, (size_t)2 * kRedBlocks * r));
     CK(cudaStreamSynchronize(st));
     double t4 = now_s();
     CS(run_lanczos(h, st));
@@ -1100,25 +1104,44 @@ slr_status check_handle(slr_handle h) {
 // One CG iteration is split in two parts (Section 6, preconditioned CG):
 //   update (every iteration after the first): z = M^{-1} r, rho' = r.z, beta, p = z + beta p
 //   test:   q = A p, alpha = rho / p.q, x += alpha p, r -= alpha q, r.r, convergence
+// The flexible beta (rho' - r.z_old) / rho takes r.z_old from the test part, which
+// forms it with the new r and the z still in place before the next apply replaces
+// it (no copy of z is kept).  With the single-precision preconditioner the CG
+// vectors stay FP64, the apply reads r rounded to FP32 (written by the r update)
+// and its z stays in FP32: widening z to FP64 is exact, so every product with it
+// equals the one with the converted vector.
+slr_status pcg_apply(slr_handle h, int32_t nrhs, cudaStream_t st) {
+    const int64_t nn = h->hs.n;
+    if (h->opts.precision == SLR_PREC_FP64) return run_apply<double>(h, h->op64, h->pr, nn, h->pz, nn, nrhs, st);
+    return run_apply<float>(h, h->op32, h->pr32, nn, h->pz32, nn, nrhs, st);
+}
+
 slr_status pcg_update_part(slr_handle h, int32_t nrhs, cudaStream_t st) {
     const int64_t nn = h->hs.n;
-    if (h->opts.flexible_cg)
-        CK(cudaMemcpyAsync(h->pzold, h->pz, sizeof(double) * nn * nrhs, cudaMemcpyDeviceToDevice, st));
-    CS(apply_any(h, h->pr, nn, h->pz, nn, nrhs, st));
-    CK(launch_dots(nn, nrhs, h->pr, nn, h->pz, nn, h->dpart, h->scal + 6, 8, st));        // rho_new
-    if (h->opts.flexible_cg) CK(launch_dots(nn, nrhs, h->pr, nn, h->pzold, nn, h->dpart, h->scal + 7, 8, st));
-    CK(launch_pcg_beta(nrhs, h->scal, h->iflags, h->opts.flexible_cg, st));
-    CK(launch_pcg_update_p(h->hs.n, nrhs, h->pp, h->pz, h->scal, h->iflags, st));
+    CS(pcg_apply(h, nrhs, st));
+    if (h->pz32) {
+        CK(launch_pcg_dot<float>(nn, nrhs, h->pr, h->pz32, h->dpart, h->scal + 6, 8, st));   // rho_new
+        CK(launch_pcg_beta(nrhs, h->scal, h->iflags, h->opts.flexible_cg, st));
+        CK(launch_pcg_update_pz<float>(nn, nrhs, h->pp, h->pz32, h->scal, h->iflags, st));
+    } else {
+        CK(launch_pcg_dot<double>(nn, nrhs, h->pr, h->pz, h->dpart, h->scal + 6, 8, st));
+        CK(launch_pcg_beta(nrhs, h->scal, h->iflags, h->opts.flexible_cg, st));
+        CK(launch_pcg_update_pz<double>(nn, nrhs, h->pp, h->pz, h->scal, h->iflags, st));
+    }
     return SLR_OK;
 }
 
 slr_status pcg_test_part(slr_handle h, int32_t nrhs, cudaStream_t st) {
     const int64_t nn = h->hs.n;
-    CK(launch_csr_spmv(h->hs.n, h->a_rp, h->a_ci, h->a_v, h->pp, nn, h->pq, nn, nrhs, st));   // q = A p
-    CK(launch_dots(nn, nrhs, h->pp, nn, h->pq, nn, h->dpart, h->scal + 1, 8, st));           // p.q
+    const bool fl = h->opts.flexible_cg != 0;
+    CK(launch_pcg_spmv_dot(nn, nrhs, h->a_rp, h->a_ci, h->a_v, h->pp, h->pq, h->dpart, h->scal, st));  // q, p.q
     CK(launch_pcg_alpha(nrhs, h->scal, h->iflags, st));
-    CK(launch_pcg_update_xr(h->hs.n, nrhs, h->px, h->pr, h->pp, h->pq, h->scal, h->iflags, st));
-    CK(launch_dots(nn, nrhs, h->pr, nn, h->pr, nn, h->dpart, h->scal + 3, 8, st));           // r.r
+    if (h->pz32)       // x, r, fl32(r), r.r and r.z_old
+        CK(launch_pcg_xr_dots<float>(nn, nrhs, h->px, h->pr, h->pp, h->pq, h->pr32, fl ? h->pz32 : nullptr,
+                                     h->scal, h->iflags, h->dpart, st));
+    else
+        CK(launch_pcg_xr_dots<double>(nn, nrhs, h->px, h->pr, h->pp, h->pq, nullptr, fl ? h->pz : nullptr,
+                                      h->scal, h->iflags, h->dpart, st));
     return SLR_OK;
 }
 
@@ -1458,9 +1481,16 @@ slr_status slr_pcg_solve(slr_handle h, const double* b, double* x, int32_t nrhs,
     CK(cudaMemsetAsync(h->px, 0, sizeof(double) * nn * nrhs, st));
     CK(launch_dots(nn, nrhs, h->pr, nn, h->pr, nn, h->dpart, h->scal + 4, 8, st));
     CK(launch_pcg_init(nrhs, h->scal, h->iflags, st));
-    CS(apply_any(h, h->pr, nn, h->pz, nn, nrhs, st));
-    CK(launch_dots(nn, nrhs, h->pr, nn, h->pz, nn, h->dpart, h->scal + 0, 8, st));
-    CK(cudaMemcpyAsync(h->pp, h->pz, sizeof(double) * nn * nrhs, cudaMemcpyDeviceToDevice, st));
+    if (h->pz32) {
+        CK(launch_convert<double, float>(nn, nrhs, h->pr, nn, h->pr32, nn, st));
+        CS(pcg_apply(h, nrhs, st));
+        CK(launch_pcg_dot<float>(nn, nrhs, h->pr, h->pz32, h->dpart, h->scal + 0, 8, st));
+        CK(launch_convert<float, double>(nn, nrhs, h->pz32, nn, h->pp, nn, st));                 // p = z
+    } else {
+        CS(pcg_apply(h, nrhs, st));
+        CK(launch_pcg_dot<double>(nn, nrhs, h->pr, h->pz, h->dpart, h->scal + 0, 8, st));
+        CK(cudaMemcpyAsync(h->pp, h->pz, sizeof(double) * nn * nrhs, cudaMemcpyDeviceToDevice, st));
+    }
     if (maxit > 0) {
         slr_handle_s::PcgGraph* gr = nullptr;
         // the graph is captured on first use for this right-hand-side count; if
@@ -1548,7 +1578,13 @@ slr_status slr_cg_slot_start(slr_handle h, int32_t slot, const double* b, double
     CK(launch_permute(n, 1, h->perm, b, nn, h->pr + off, nn, true, st));          // r = P b
     CK(cudaMemsetAsync(h->px + off, 0, sizeof(double) * nn, st));                 // x = 0
     CK(cudaMemsetAsync(h->pp + off, 0, sizeof(double) * nn, st));                 // p = 0
-    CK(cudaMemsetAsync(h->pz + off, 0, sizeof(double) * nn, st));                 // z = 0 (z_old of the first step)
+    if (h->pz32) {
+        CK(cudaMemsetAsync(h->pz32 + off, 0, sizeof(float) * nn, st));            // z = 0
+        CK(launch_convert<double, float>(nn, 1, h->pr + off, nn, h->pr32 + off, nn, st));   // fl32(r)
+    } else {
+        CK(cudaMemsetAsync(h->pz + off, 0, sizeof(double) * nn, st));             // z = 0
+    }
+    CK(cudaMemsetAsync(h->scal + 8 * slot + 7, 0, sizeof(double), st));           // r.z_old = 0 (z_old = 0)
     CK(launch_dots(nn, 1, h->pr + off, nn, h->pr + off, nn, h->dpart, h->scal + 8 * slot + 4, 8, st));   // b.b
     CK(launch_cg_slot_init(slot, tol, maxit, h->scal, h->iflags, h->slot_ctl, st));
     return SLR_OK;

@@ -115,7 +115,10 @@ struct slr_handle_s {
     int32_t *c_rp = nullptr, *c_ci = nullptr; double* c_v = nullptr;
     // PCG state (DD order, n x nrhs_max) and scalars
     int32_t *perm = nullptr, *a_rp = nullptr, *a_ci = nullptr; double* a_v = nullptr;
-    double *px = nullptr, *pr = nullptr, *pz = nullptr, *pp = nullptr, *pq = nullptr, *pzold = nullptr;
+    double *px = nullptr, *pr = nullptr, *pz = nullptr, *pp = nullptr, *pq = nullptr;
+    // single-precision preconditioner: r rounded to FP32 (the apply's input, written by
+    // the r update) and the apply's output z, kept in FP32 (pz is then not allocated)
+    float *pr32 = nullptr, *pz32 = nullptr;
     double *scal = nullptr;          // per-column scalars, see slr_api.cu
     double *dpart = nullptr;         // reduction partials
     int32_t *iflags = nullptr;       // per-column status words
@@ -272,6 +275,25 @@ cudaError_t launch_pcg_check_graph(int32_t nrhs, const double* scal, int32_t* fl
                                    cudaStream_t st);
 cudaError_t launch_pcg_update_p(int32_t n, int32_t nrhs, double* p, const double* z, const double* scal,
                                 const int32_t* flags, cudaStream_t st);
+// Fused CG vector kernels (slr_pcg.cu), column j of each vector at offset j n; the
+// dots use one fixed two-stage reduction whatever kernel forms them.
+// out[j stride] = a_j . b_j, b in FP64 or FP32 (widened before the product)
+template <typename TB>
+cudaError_t launch_pcg_dot(int64_t n, int32_t cols, const double* a, const TB* b, double* part, double* out,
+                           int32_t out_stride, cudaStream_t st);
+// q = A p (CSR) and scal[8 j + 1] = p_j . q_j
+cudaError_t launch_pcg_spmv_dot(int64_t n, int32_t nrhs, const int32_t* rp, const int32_t* ci, const double* v,
+                                const double* p, double* q, double* part, double* scal, cudaStream_t st);
+// active columns: x += alpha p, r -= alpha q, r32 = fl32(r) (r32 may be null); every column:
+// scal[8 j + 3] = r.r and, z not null, scal[8 j + 7] = r.z; part holds 2 nrhs kRedBlocks values
+template <typename TZ>
+cudaError_t launch_pcg_xr_dots(int64_t n, int32_t nrhs, double* x, double* r, const double* p, const double* q,
+                               float* r32, const TZ* z, double* scal, const int32_t* flags, double* part,
+                               cudaStream_t st);
+// active columns: p = z + beta p
+template <typename TZ>
+cudaError_t launch_pcg_update_pz(int64_t n, int32_t nrhs, double* p, const TZ* z, const double* scal,
+                                 const int32_t* flags, cudaStream_t st);
 // slot CG (continuous batching, slr_cg_*): start slot j; per-slot test after an iteration
 cudaError_t launch_cg_slot_init(int32_t j, double tol, int32_t maxit, double* scal, int32_t* flags, double* ctl,
                                cudaStream_t st);

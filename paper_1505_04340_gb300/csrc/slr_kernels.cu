@@ -81,28 +81,39 @@ __device__ __forceinline__ bool rs_writer(int lane) {
 // K1 (the batched band solve) lives in slr_band.cu.
 
 // ------------------------------------------------------------------ K2
-template <typename T>
-__global__ void k_gather_et(int32_t s, int32_t nrhs, const int32_t* __restrict__ rp,
-                            const int32_t* __restrict__ ci, const T* __restrict__ v, const T* g, int64_t ldg,
-                            const T* t, int64_t ldt, T* gp, int64_t ldgp) {
-    const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (int64_t)s * nrhs) return;
-    const int32_t i = (int32_t)(idx % s), j = (int32_t)(idx / s);
-    T acc = T(0);
-    for (int32_t q = rp[i]; q < rp[i + 1]; ++q) acc += v[q] * t[ci[q] + j * ldt];
-    gp[i + j * ldgp] = g ? g[i + j * ldg] - acc : acc;
-}
+// Y = A X for a block of columns (CSR A; given G: Y = G - A X), as the coupling
+// products E y and g - E^T t and the products with A and C use it.  A thread
+// takes one row for kSpCols columns, so the row's entries are read once per
+// group of columns; each column's sum runs over the row's entries in order
+// (the same sums, bit for bit, whatever the number of columns).
+constexpr int kSpCols = 8;
 
 template <typename T>
-__global__ void k_spmv(int32_t rows, int32_t nrhs, const int32_t* __restrict__ rp,
-                       const int32_t* __restrict__ ci, const T* __restrict__ v, const T* x, int64_t ldx,
-                       T* y, int64_t ldy) {
+__global__ void k_spmv_cols(int32_t rows, int32_t nrhs, const int32_t* __restrict__ rp,
+                            const int32_t* __restrict__ ci, const T* __restrict__ v, const T* x, int64_t ldx,
+                            const T* g, int64_t ldg, T* y, int64_t ldy) {
+    const int32_t ngr = (nrhs + kSpCols - 1) / kSpCols;
     const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (int64_t)rows * nrhs) return;
-    const int32_t i = (int32_t)(idx % rows), j = (int32_t)(idx / rows);
-    T acc = T(0);
-    for (int32_t q = rp[i]; q < rp[i + 1]; ++q) acc += v[q] * x[ci[q] + j * ldx];
-    y[i + j * ldy] = acc;
+    if (idx >= (int64_t)rows * ngr) return;
+    const int32_t i = (int32_t)(idx % rows), j0 = (int32_t)(idx / rows) * kSpCols;
+    const int nc = min(kSpCols, nrhs - j0);
+    T acc[kSpCols];
+#pragma unroll
+    for (int c = 0; c < kSpCols; ++c) acc[c] = T(0);
+    const int32_t e1 = rp[i + 1];
+    for (int32_t q = rp[i]; q < e1; ++q) {
+        const T a = v[q];
+        const int64_t col = ci[q];
+#pragma unroll
+        for (int c = 0; c < kSpCols; ++c)
+            if (c < nc) acc[c] += a * x[col + (int64_t)(j0 + c) * ldx];
+    }
+#pragma unroll
+    for (int c = 0; c < kSpCols; ++c)
+        if (c < nc) {
+            const int64_t o = (int64_t)(j0 + c);
+            y[i + o * ldy] = g ? g[i + o * ldg] - acc[c] : acc[c];
+        }
 }
 
 // ------------------------------------------------------------------ K3
@@ -1931,6 +1942,16 @@ inline unsigned blocks_for(int64_t n, int t = kThreads) { return (unsigned)((n +
 // every kernel launch of the library goes through this counter
 inline void counted(int n = 1) { count_launches(n); }
 
+template <typename T>
+cudaError_t spmv_cols(int32_t rows, int32_t nrhs, const int32_t* rp, const int32_t* ci, const T* v, const T* x,
+                      int64_t ldx, const T* g, int64_t ldg, T* y, int64_t ldy, cudaStream_t st) {
+    if (rows == 0 || nrhs == 0) return cudaSuccess;
+    const int64_t threads = (int64_t)rows * ((nrhs + kSpCols - 1) / kSpCols);
+    k_spmv_cols<T><<<blocks_for(threads), kThreads, 0, st>>>(rows, nrhs, rp, ci, v, x, ldx, g, ldg, y, ldy);
+    counted();
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------ launchers
@@ -1939,20 +1960,14 @@ template <typename T>
 cudaError_t launch_gather_et(const DevOperator<T>& op, int32_t s, const T* g, int64_t ldg, const T* t,
                              int64_t ldt, T* gp, int64_t ldgp, int32_t nrhs, cudaStream_t st) {
     if (s == 0) return cudaSuccess;
-    k_gather_et<T><<<blocks_for((int64_t)s * nrhs), kThreads, 0, st>>>(s, nrhs, op.et_rp, op.et_ci, op.et_v, g,
-                                                                        ldg, t, ldt, gp, ldgp);
-    counted();
-    return cudaGetLastError();
+    return spmv_cols<T>(s, nrhs, op.et_rp, op.et_ci, op.et_v, t, ldt, g, ldg, gp, ldgp, st);
 }
 
 template <typename T>
 cudaError_t launch_spmv_e(const DevOperator<T>& op, int32_t nI, const T* y, int64_t ldy, T* out, int64_t ldo,
                           int32_t nrhs, cudaStream_t st) {
     if (nI == 0) return cudaSuccess;
-    k_spmv<T><<<blocks_for((int64_t)nI * nrhs), kThreads, 0, st>>>(nI, nrhs, op.e_rp, op.e_ci, op.e_v, y, ldy,
-                                                                    out, ldo);
-    counted();
-    return cudaGetLastError();
+    return spmv_cols<T>(nI, nrhs, op.e_rp, op.e_ci, op.e_v, y, ldy, nullptr, 0, out, ldo, st);
 }
 
 // Grid of a persistent solve on the current device: one CTA per SM (fewer if
@@ -2300,9 +2315,7 @@ cudaError_t launch_permute(int32_t n, int32_t nrhs, const int32_t* idx, const do
 cudaError_t launch_csr_spmv(int32_t n, const int32_t* rp, const int32_t* ci, const double* v, const double* x,
                             int64_t ldx, double* y, int64_t ldy, int32_t nrhs, cudaStream_t st) {
     if (n == 0) return cudaSuccess;
-    k_spmv<double><<<blocks_for((int64_t)n * nrhs), kThreads, 0, st>>>(n, nrhs, rp, ci, v, x, ldx, y, ldy);
-    counted();
-    return cudaGetLastError();
+    return spmv_cols<double>(n, nrhs, rp, ci, v, x, ldx, nullptr, 0, y, ldy, st);
 }
 
 cudaError_t launch_dots(int64_t n, int32_t cols, const double* a, int64_t lda, const double* b, int64_t ldb,
