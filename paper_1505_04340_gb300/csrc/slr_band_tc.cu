@@ -212,10 +212,14 @@ k_band_tc(const BandTcBlock* __restrict__ blocks, const unsigned char* __restric
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tbase + 1);
     const int tid = threadIdx.x, warp = tid >> 5;
     const int nM = (W + 127) / 128;
-    // tensor memory: the accumulators (M-tile mt at column mt NP), then as many columns
+    // tensor memory: the accumulators (M-tile mt at column mt CS), then as many columns
     // holding the epilogue's global operand of a block (F_J, Y_J or the base), written
-    // by the epilogue threads while the block's MMAs run
-    const uint32_t acols = nM * NP <= 32 ? 32 : nM * NP <= 64 ? 64 : 128, ncol = 2 * acols;
+    // by the epilogue threads while the block's MMAs run.  The epilogue moves 32
+    // columns at a time, so an M-tile's columns are at least 32 wide (CS): with N = 16
+    // and two M-tiles, a stride of 16 would put the second tile's staged operand past
+    // the allocation, into the columns of the SM's other CTA.
+    constexpr uint32_t CS = NP < 32 ? 32 : NP;
+    const uint32_t acols = nM * CS <= 32 ? 32 : nM * CS <= 64 ? 64 : 128, ncol = 2 * acols;
     if (warp == 0) {
         tc::tmem_alloc(tbase, ncol);
         tc::tmem_relinquish();
@@ -302,7 +306,7 @@ k_band_tc(const BandTcBlock* __restrict__ blocks, const unsigned char* __restric
                         break;
                     }
                     const uint32_t sa = tc::smem_addr(ring + ((size_t)s * stiles + in_slot) * kSub);
-                    tc::mma<AB>(tmem + (uint32_t)(mt * NP), tc::smem_desc(sa, 128, 256),
+                    tc::mma<AB>(tmem + (uint32_t)(mt * CS), tc::smem_desc(sa, 128, 256),
                                 tc::smem_desc(vb + 256u * ks, 128, sbo_v), idesc, ks > bt_k0(upper, mt, KS));
                     const bool last_of_fill = in_slot == stiles - 1 || t == tiles_of(bk.type) - 1;
                     if (last_of_fill) tc::commit(&empty[s]);
@@ -361,7 +365,7 @@ k_band_tc(const BandTcBlock* __restrict__ blocks, const unsigned char* __restric
 #pragma unroll
                         for (int jj = 0; jj < 32; ++jj)
                             pv[jj] = (ok && c0 + jj < nrhs) ? srcb[row + (c0 + jj) * lds] : 0.0f;
-                        tc::tmem_st32(tmem + lane_addr + acols + (uint32_t)(mt * NP + c0), pv);
+                        tc::tmem_st32(tmem + lane_addr + acols + (uint32_t)(mt * CS + c0), pv);
                     }
                 }
             }
@@ -381,8 +385,8 @@ k_band_tc(const BandTcBlock* __restrict__ blocks, const unsigned char* __restric
 #pragma unroll
                 for (int c0 = 0; c0 < NP; c0 += 32) {
                     float v[32];
-                    tc::tmem_ld32(tmem + lane_addr + (uint32_t)(mt * NP + c0), v);
-                    const uint32_t pre_col = tmem + lane_addr + acols + (uint32_t)(mt * NP + c0);
+                    tc::tmem_ld32(tmem + lane_addr + (uint32_t)(mt * CS + c0), v);
+                    const uint32_t pre_col = tmem + lane_addr + acols + (uint32_t)(mt * CS + c0);
                     // v := pre - v (the operand's columns past nrhs were stored as zeros)
                     auto pre_minus = [&]() {
 #pragma unroll

@@ -153,6 +153,31 @@ def test_band_solve_on_tensor_cores_matches_oracle(name, mma, nrhs):
 
 
 @pytest.mark.parametrize("mma", ["tf32", "bf16"])
+@pytest.mark.parametrize("nrhs", [8, 16, 24])
+def test_band_solve_on_tensor_cores_two_ctas_per_sm(mma, nrhs):
+    """More subdomains (180) than SMs, so two CTAs share each SM, and planes of up
+    to 144 rows (two M-tiles of 128): the accumulators and staged operands of both
+    M-tiles of both CTAs must stay in their own tensor-memory columns, for N padded
+    to 16 (8 and 16 right-hand sides) as well as to 32.  A column written into the
+    other CTA's allocation moves the solve by O(1); the bound is the 16 u of the
+    small-case test.  The reference is the oracle's banded Cholesky solves alone
+    (its C factor is not needed here)."""
+    from oracle.slr_oracle import BSolver, dd_order, split_blocks
+    P = slrgen.make_problem("3d-many", (78, 78, 20), (6, 6, 5), 8, kind="laplacian", nrhs=1)
+    order = dd_order(P.rowptr, P.colind, P.part, P.nparts)
+    bs = BSolver(split_blocks(P.rowptr, P.colind, P.val, order)[0], order.int_off)
+    assert P.nparts > 152 and max(b.cb.shape[0] - 1 for b in bs.blocks) > 128
+    h = SLR(P.rowptr, P.colind, P.val, P.part, P.nparts, k=0, precision="mixed", nrhs_max=nrhs, band_mma=mma)
+    F = np.random.default_rng(23).standard_normal((order.n_I, nrhs))
+    T = h.bsolve(cu(F)).cpu().numpy()
+    To = np.stack([bs.solve(F[:, j]) for j in range(nrhs)], axis=1)
+    err = float((np.abs(T - To).max(axis=0) / np.abs(To).max(axis=0)).max())
+    print(f"{mma} nrhs {nrhs}: band solve error {err:.2e} (bound {16 * U_TC[mma]:.2e})")
+    assert err <= 16 * U_TC[mma]
+    h.close()
+
+
+@pytest.mark.parametrize("mma", ["tf32", "bf16"])
 def test_apply_with_tensor_core_band_solve(mma):
     """The whole apply (Eq. 4.1) with both B-solves on the tensor cores, the second
     one subtracting from its base (u = t - B^{-1} E y), against the same operator's
