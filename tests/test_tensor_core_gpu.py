@@ -177,6 +177,25 @@ def test_band_solve_on_tensor_cores_two_ctas_per_sm(mma, nrhs):
     h.close()
 
 
+def test_apply_does_not_depend_on_block_width():
+    """The whole mixed apply with tensor-core band solves and low-rank products, on
+    a workload with more subdomains than SMs and two M-tiles per plane: the first
+    8 and 16 columns of a 32-column block match the same columns applied alone.
+    Each output column of an MMA depends only on its own operand column, so the
+    agreement is exact in practice; the bound is the band solve's 16 u."""
+    P = slrgen.make_problem("3d-many", (78, 78, 20), (6, 6, 5), 8, kind="laplacian", nrhs=1)
+    h = SLR(P.rowptr, P.colind, P.val, P.part, P.nparts, k=8, precision="mixed", nrhs_max=32,
+            band_mma="tf32", u_dtype="tf32")
+    R = cu(np.random.default_rng(37).standard_normal((P.rowptr.size - 1, 32)))
+    z = h.apply(R).cpu().numpy()
+    for w in (8, 16):
+        zw = h.apply(R[:, :w].contiguous()).cpu().numpy()
+        err = float((np.abs(zw - z[:, :w]).max(axis=0) / np.abs(z[:, :w]).max(axis=0)).max())
+        print(f"first {w} of 32 columns vs alone: {err:.2e}")
+        assert err <= 16 * U_TC["tf32"]
+    h.close()
+
+
 @pytest.mark.parametrize("mma", ["tf32", "bf16"])
 def test_apply_with_tensor_core_band_solve(mma):
     """The whole apply (Eq. 4.1) with both B-solves on the tensor cores, the second
