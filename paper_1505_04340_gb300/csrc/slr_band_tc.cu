@@ -446,9 +446,11 @@ cudaError_t bt_launch(const DevOperator<float>& op, int32_t p, const float* in, 
     const int WK = bt_nk(op.band_tc_wmax, KS) * KS;
     const size_t vbytes = (size_t)NP * WK * E;
     const size_t fixed = vbytes + 8 * (2 * 8 + 3) + 16;
-    // ring: as many 4-sub-tile slots (16 KB) as fit, 2 .. 8, in the opt-in maximum or,
-    // with more subdomains than SMs, in half an SM (113 KB: two CTAs per SM, one wave)
-    const int stiles = 4;
+    // ring: as many 8-sub-tile slots (32 KB) as fit, 2 .. 8, in the opt-in maximum or,
+    // with more subdomains than SMs, in half an SM (113 KB: two CTAs per SM, one wave).
+    // Fewer, larger copies measured faster: on 3-D 96^3 with 32 columns two 32 KB slots
+    // took 1014 us per B-solve, five of 16 KB 1039 us, ten of 8 KB 1114 us.
+    const int stiles = 8;
     const size_t cap = (NP <= 32 && p > op.cf.nsm) ? 113 * 1024 : 227 * 1024;
     int nslot = fixed < cap ? (int)((cap - fixed) / ((size_t)stiles * kSub)) : 0;
     nslot = nslot > 8 ? 8 : nslot;

@@ -12,8 +12,8 @@
 //   r.z after an apply                    k_pcg_dot with z in the apply's precision
 //   p = z + beta p                        k_pcg_update_p with z in that precision
 //
-// Every dot product has a fixed reduction: block b of a column's G blocks (256;
-// 128 in the x/r update) sums the elements i = b*256 + t + m*256G (t its thread,
+// Every dot product has a fixed reduction: block b of a column's G blocks (128;
+// 256 in q = Ap) sums the elements i = b*256 + t + m*256G (t its thread,
 // m = 0, 1, ...) in that order per thread, then the block's warps by a butterfly
 // and the warp sums in order, then a final kernel sums the G block sums (lane l
 // the blocks l, l+32, ...; then a butterfly).  A column's dots do not depend on
@@ -55,9 +55,9 @@ __device__ __forceinline__ double pcg_block_sum(double v, double* red) {
 // at a time: the four elements' loads are issued together, their products
 // added in element order.
 constexpr int kUnroll = 4;
-// Blocks per column of the x/r update: fewer, longer-running blocks than the
-// other dots (measured 7% faster on 3-D 96^3 with 32 columns)
-constexpr int kXrBlocks = 128;
+// Blocks per column of the x/r update and of r.z: fewer, longer-running blocks
+// than q = Ap takes (measured 7% and 8% faster on 3-D 96^3 with 32 columns)
+constexpr int kDotBlocks = 128;
 
 // part[j G + b] = block b's share of sum_i a[i + j n] b[i + j n]
 template <typename TB>
@@ -252,10 +252,10 @@ template <typename TB>
 cudaError_t launch_pcg_dot(int64_t n, int32_t cols, const double* a, const TB* b, double* part, double* out,
                            int32_t out_stride, cudaStream_t st) {
     if (cols == 0) return cudaSuccess;
-    k_pcg_dot<TB><<<dim3(kRedBlocks, cols), kPcgThreads, 0, st>>>(n, a, b, part);
+    k_pcg_dot<TB><<<dim3(kDotBlocks, cols), kPcgThreads, 0, st>>>(n, a, b, part);
     count_launches(1);
     cudaError_t e = cudaGetLastError();
-    return e != cudaSuccess ? e : dot_final(cols, kRedBlocks, part, out, nullptr, out_stride, st);
+    return e != cudaSuccess ? e : dot_final(cols, kDotBlocks, part, out, nullptr, out_stride, st);
 }
 
 cudaError_t launch_pcg_spmv_dot(int64_t n, int32_t nrhs, const int32_t* rp, const int32_t* ci, const double* v,
@@ -274,10 +274,10 @@ cudaError_t launch_pcg_xr_dots(int64_t n, int32_t nrhs, double* x, double* r, co
                                float* r32, const TZ* z, double* scal, const int32_t* flags, double* part,
                                cudaStream_t st) {
     if (nrhs == 0) return cudaSuccess;
-    k_pcg_xr_dots<TZ><<<dim3(kXrBlocks, nrhs), kPcgThreads, 0, st>>>(n, x, r, p, q, r32, z, scal, flags, part);
+    k_pcg_xr_dots<TZ><<<dim3(kDotBlocks, nrhs), kPcgThreads, 0, st>>>(n, x, r, p, q, r32, z, scal, flags, part);
     count_launches(1);
     cudaError_t e = cudaGetLastError();
-    return e != cudaSuccess ? e : dot_final(nrhs, kXrBlocks, part, scal + 3, z ? scal + 7 : nullptr, 8, st);
+    return e != cudaSuccess ? e : dot_final(nrhs, kDotBlocks, part, scal + 3, z ? scal + 7 : nullptr, 8, st);
 }
 
 template <typename TZ>
