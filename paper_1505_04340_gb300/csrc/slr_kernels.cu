@@ -2144,19 +2144,34 @@ cudaError_t launch_c_forward(const DevCFactor<T>& cf, const T* g_dd, int64_t ldg
         }
         const bool wide = nt + np <= cf.nsm;
         // blocks of 8 or more with the level's gather: one pass per 32 (16 in the wide
-        // variant) right-hand sides when t_J of the level's widest supernode fits
+        // variant, 8 when the level's widest supernode leaves no room for 16) right-hand
+        // sides when t_J of that many fits; every variant forms the same sums in the same order
         if (nrhs >= 8 && vl.tws) {
             const int32_t ts_n = cf.lev_maxn[l] > 0 ? cf.lev_maxn[l] : cf.max_n;
-            const int rp = wide ? 16 : 32;
-            const size_t sm = ((size_t)ts_n * (rp + 4) + (size_t)(wide ? 32 : 8) * rp * 32) * sizeof(T);
-            const void* kb = wide ? (const void*)k_cfwd_level_blk<T, 32, 16> : (const void*)k_cfwd_level_blk<T, 8, 32>;
-            if (sm <= kLevSmem && (sm <= 48 * 1024 || raise_smem_once(kb))) {
-                if (wide)
-                    k_cfwd_level_blk<T, 32, 16><<<nt + np, 1024, sm, st>>>(vl, t0, p0, np, xf, nrhs, ts_n);
-                else
+            auto smem_for = [&](int rp, int nw) { return ((size_t)ts_n * (rp + 4) + (size_t)nw * rp * 32) * sizeof(T); };
+            auto fits = [&](size_t sm, const void* kb) {
+                return sm <= kLevSmem && (sm <= 48 * 1024 || raise_smem_once(kb));
+            };
+            if (!wide) {
+                const size_t sm = smem_for(32, 8);
+                if (fits(sm, (const void*)k_cfwd_level_blk<T, 8, 32>)) {
                     k_cfwd_level_blk<T, 8, 32><<<nt + np, 256, sm, st>>>(vl, t0, p0, np, xf, nrhs, ts_n);
-                counted();
-                continue;
+                    counted();
+                    continue;
+                }
+            } else {
+                size_t sm = smem_for(16, 32);
+                if (fits(sm, (const void*)k_cfwd_level_blk<T, 32, 16>)) {
+                    k_cfwd_level_blk<T, 32, 16><<<nt + np, 1024, sm, st>>>(vl, t0, p0, np, xf, nrhs, ts_n);
+                    counted();
+                    continue;
+                }
+                sm = smem_for(8, 32);
+                if (fits(sm, (const void*)k_cfwd_level_blk<T, 32, 8>)) {
+                    k_cfwd_level_blk<T, 32, 8><<<nt + np, 1024, sm, st>>>(vl, t0, p0, np, xf, nrhs, ts_n);
+                    counted();
+                    continue;
+                }
             }
         }
         // blocks of eight or four right-hand sides share each matrix load when t_J of that many fits
